@@ -1,0 +1,253 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these checks retypes the oracle's own formula: each one compares the
+oracle with an independent library routine (numpy SVD, pinv, FFT, eigvalsh),
+a closed form, or an identity the paper states. The "planted mistake" tests at
+the end show that a plausible slip in the oracle (dropped conjugate, wrong
+sign, missing lambda, transposed operand) makes one of these pins fail.
+"""
+import numpy as np
+import pytest
+
+import oracle.pinv_oracle as O
+from paper_2410_06129_gb300 import synth
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def _rand_complex(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def _small_plan(seed=7, side=8, coils=3, b0=True, traj="spiral"):
+    return synth.make_plan(side, coils, traj, 3, seed, 1e-3, samples=2 * side * side,
+                           interleaves=2, b0=b0)
+
+
+def _svd_tikhonov(E, lam, d):
+    """x = V diag(s / (s^2 + lam)) U^H d  (Eq. 4 spectrum + Eq. 6 load)."""
+    U, s, Vh = np.linalg.svd(E, full_matrices=False)
+    return Vh.conj().T @ ((s / (s * s + lam))[:, None] * (U.conj().T @ d))
+
+
+# ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tikhonov_matches_svd_random_matrix(seed):
+    """Eq. 6/8 via Cholesky equals the SVD-filtered solution (Section 3.2)."""
+    rng = np.random.default_rng(seed)
+    E = _rand_complex(rng, 70, 40)
+    d = _rand_complex(rng, 70, 3)
+    lam = 0.3
+    R, _ = O.recon_matrix(E, lam)
+    x = O.reconstruct(R, d)
+    ref = _svd_tikhonov(E, lam, d)
+    assert O.nrmse(x, ref) < 1e-12
+
+
+def test_tikhonov_matches_svd_encoding_matrix():
+    p = _small_plan()
+    E = O.plan_encode(p)
+    lam = O.lambda_abs(E, p.lambda_rel)
+    R, _ = O.recon_matrix(E, lam)
+    d = O.data_columns(p.data)
+    assert O.nrmse(O.reconstruct(R, d), _svd_tikhonov(E, lam, d)) < 1e-12
+
+
+def test_lambda_zero_is_moore_penrose():
+    """With lambda = 0 and full column rank, Recon = E^+ (Section 2.1)."""
+    rng = np.random.default_rng(3)
+    E = _rand_complex(rng, 60, 25)
+    R, _ = O.recon_matrix(E, 0.0)
+    assert O.nrmse(R, np.linalg.pinv(E)) < 1e-11
+
+
+def test_gram_eigenvalues_are_squared_singular_values():
+    """Eigenvalues of E^H E + lam I are sigma^2 + lam (Section 2.2)."""
+    p = _small_plan(seed=11)
+    E = O.plan_encode(p)
+    lam = O.lambda_abs(E, p.lambda_rel)
+    G = O.gram(E, lam)
+    ev = np.sort(np.linalg.eigvalsh(G))
+    sv = np.sort(np.linalg.svd(E, compute_uv=False) ** 2 + lam)
+    assert np.max(np.abs(ev - sv)) / sv[-1] < 1e-12
+
+
+# ---------------------------------------------------------------- closed form
+@pytest.mark.parametrize("side", [8, 16])
+def test_cartesian_closed_form(side):
+    """Fully sampled Cartesian: E^H E = N I and E^H d is an inverse DFT."""
+    k, _ = synth.cartesian(side)
+    vox = O.voxel_positions((side, side))
+    E = O.encode(k, vox)
+    N = side * side
+    lam = 0.25 * N
+    G = O.gram(E, lam)
+    assert np.max(np.abs(G - (N + lam) * np.eye(N))) < 1e-10 * N
+    rng = np.random.default_rng(side)
+    d = _rand_complex(rng, N)
+    R, _ = O.recon_matrix(E, lam)
+    x = R @ d
+    # closed form: x = E^H d / (N + lam) with E^H d = (-1)^(ix+iy) N ifft2(d (-1)^(jx+jy))
+    j = np.arange(side)
+    sgn = ((-1.0) ** (j[:, None] + j[None, :]))
+    dg = d.reshape(side, side)                     # [jy][jx]
+    adj = sgn * (N * np.fft.ifft2(dg * sgn))       # [iy][ix] (even side)
+    assert O.nrmse(x, adj.ravel() / (N + lam)) < 1e-12
+
+
+def test_lambda_closed_form_sos_coils():
+    """trace(E^H E)/N = M_k exactly for sum-of-squares normalised coils."""
+    p = _small_plan(seed=5, coils=4)
+    E = O.plan_encode(p)
+    assert abs(O.lambda_abs(E, 1.0) - p.n_samples) < 1e-10 * p.n_samples
+
+
+# ---------------------------------------------------------------- invariants
+def test_gram_hermitian_pd_and_cholesky():
+    p = _small_plan(seed=3)
+    E = O.plan_encode(p)
+    lam = O.lambda_abs(E, p.lambda_rel)
+    G = O.gram(E, lam)
+    assert np.max(np.abs(G - G.conj().T)) <= 1e-14 * np.max(np.abs(G))
+    L = O.cholesky(G)
+    assert np.allclose(np.triu(L, 1), 0)
+    assert np.max(np.abs(L @ L.conj().T - G)) < 1e-13 * np.max(np.abs(G))
+    assert np.all(np.real(np.diag(L)) ** 2 >= lam * (1 - 1e-12))
+    ref = np.linalg.cholesky(G)
+    assert np.max(np.abs(L - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_cholesky_rejects_indefinite():
+    G = np.diag([1.0, 2.0, -1.0, 3.0]).astype(np.complex128)
+    with pytest.raises(ValueError, match="pivot 2"):
+        O.cholesky(G)
+
+
+def test_normal_equation_residual_and_direct_solve():
+    p = _small_plan(seed=4)
+    E = O.plan_encode(p)
+    lam = O.lambda_abs(E, p.lambda_rel)
+    d = O.data_columns(p.data)
+    R, L = O.recon_matrix(E, lam)
+    x = O.reconstruct(R, d)
+    res = E.conj().T @ (d - E @ x) - lam * x
+    assert np.linalg.norm(res) / np.linalg.norm(E.conj().T @ d) < 1e-12
+    x2 = O.solve(E, L, d)
+    assert O.nrmse(x2, x) < 1e-12
+
+
+def test_srf_tikhonov_identity():
+    """SRF = Recon Encode = I - lam G^-1 exactly under Tikhonov (Eq. 9)."""
+    p = _small_plan(seed=6)
+    E = O.plan_encode(p)
+    lam = O.lambda_abs(E, p.lambda_rel)
+    R, L = O.recon_matrix(E, lam)
+    Ginv = O.gram_inverse(L)
+    S = O.srf(R, E)
+    assert np.max(np.abs(S + lam * Ginv - np.eye(E.shape[1]))) < 1e-11
+    assert np.max(np.abs(Ginv @ O.gram(E, lam) - np.eye(E.shape[1]))) < 1e-11
+
+
+def test_noise_matrix_white_noise_identity():
+    """X = Recon Recon^H = G^-1 - lam G^-2 for white noise (Eq. 10)."""
+    p = _small_plan(seed=8)
+    E = O.plan_encode(p)
+    lam = O.lambda_abs(E, p.lambda_rel)
+    R, L = O.recon_matrix(E, lam)
+    Ginv = O.gram_inverse(L)
+    X = O.noise_matrix(R, np.eye(E.shape[0]))
+    assert np.max(np.abs(X - (Ginv - lam * Ginv @ Ginv))) < 1e-11 * np.max(np.abs(Ginv))
+
+
+def test_coil_procedural_equals_stacked_and_hadamard():
+    """Eq. 11: sum_c E_c^H E_c = E^H E, and it equals (A^H A) o (S^H S)."""
+    p = _small_plan(seed=9, coils=4)
+    vox = O.voxel_positions(p.dims)
+    E = O.plan_encode(p)
+    G_stacked = E.conj().T @ E
+    G_proc = sum(
+        (lambda Ec: Ec.conj().T @ Ec)(O.encode(p.traj, vox, [s], p.b0_hz, p.times))
+        for s in p.coil_maps)
+    A = O.encode(p.traj, vox, None, p.b0_hz, p.times)
+    S = p.coil_maps
+    G_had = (A.conj().T @ A) * (S.conj().T @ S)
+    scale = np.max(np.abs(G_stacked))
+    assert np.max(np.abs(G_proc - G_stacked)) < 1e-12 * scale
+    assert np.max(np.abs(G_had - G_stacked)) < 1e-12 * scale
+
+
+def test_large_lambda_is_conjugate_phase():
+    """lam -> inf: lam * x -> E^H d (Section 2.2, conjugate phase)."""
+    p = _small_plan(seed=10)
+    E = O.plan_encode(p)
+    d = O.data_columns(p.data)
+    lam = 1e8 * O.lambda_abs(E, 1.0)
+    R, _ = O.recon_matrix(E, lam)
+    assert O.nrmse(lam * (R @ d), E.conj().T @ d) < 1e-6
+
+
+def test_encode_sign_and_b0_term_against_direct_sum():
+    """One entry of E evaluated by hand from the composite factor product."""
+    p = _small_plan(seed=12, coils=2)
+    vox = O.voxel_positions(p.dims)
+    E = O.encode(p.traj, vox, p.coil_maps, p.b0_hz, p.times)
+    Mk = p.n_samples
+    for (c, m, n) in [(0, 0, 0), (1, Mk - 1, 17), (1, 5, 63), (0, 77, 40)]:
+        ph = -2 * np.pi * (p.traj[m] @ vox[n] + p.b0_hz[n] * p.times[m])
+        want = p.coil_maps[c, n] * complex(np.cos(ph), np.sin(ph))
+        assert abs(E[c * Mk + m, n] - want) < 1e-13
+
+
+def test_voxel_positions_convention():
+    r = O.voxel_positions((4, 2))
+    assert r.shape == (8, 2)
+    assert np.allclose(r[0], [-0.5, -0.5]) and np.allclose(r[1], [-0.25, -0.5])
+    assert np.allclose(r[4], [-0.5, 0.0])
+    assert np.allclose(r, synth.voxel_positions((4, 2)))
+
+
+# ---------------------------------------------------------------- planted mistakes
+def _bad_cholesky_no_conj(G):
+    n = G.shape[0]
+    L = np.zeros_like(G, dtype=np.complex128)
+    for j in range(n):
+        L[j, j] = np.sqrt(np.real(G[j, j]) - np.sum(np.abs(L[j, :j]) ** 2))
+        L[j + 1:, j] = (G[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / L[j, j]
+    return L
+
+
+def _bad_back_sub_transposed(L, B):
+    X = np.zeros_like(B, dtype=np.complex128)
+    for i in range(L.shape[0] - 1, -1, -1):
+        X[i] = (B[i] - L[i + 1:, i] @ X[i + 1:]) / L[i, i]
+    return X
+
+
+@pytest.mark.parametrize("mutation", ["chol_no_conj", "no_lambda", "back_sub_no_conj"])
+def test_planted_mistake_fails_svd_pin(monkeypatch, mutation):
+    rng = np.random.default_rng(42)
+    E = _rand_complex(rng, 50, 20)
+    d = _rand_complex(rng, 50, 2)
+    lam = 0.5
+    if mutation == "chol_no_conj":
+        monkeypatch.setattr(O, "cholesky", _bad_cholesky_no_conj)
+    elif mutation == "no_lambda":
+        monkeypatch.setattr(O, "gram", lambda E, lam: E.conj().T @ E)
+    else:
+        monkeypatch.setattr(O, "back_substitution_h", _bad_back_sub_transposed)
+    L = O.cholesky(O.gram(E, lam))
+    x = O.back_substitution_h(L, O.forward_substitution(L, E.conj().T @ d))
+    assert O.nrmse(x, _svd_tikhonov(E, lam, d)) > 1e-6
+
+
+def test_planted_sign_flip_fails_cartesian_pin():
+    side = 8
+    k, _ = synth.cartesian(side)
+    vox = O.voxel_positions((side, side))
+    E_bad = np.conj(O.encode(k, vox))          # exp(+i2pi k.r)
+    rng = np.random.default_rng(1)
+    d = _rand_complex(rng, side * side)
+    j = np.arange(side)
+    sgn = ((-1.0) ** (j[:, None] + j[None, :]))
+    adj = sgn * (side * side * np.fft.ifft2(d.reshape(side, side) * sgn))
+    assert O.nrmse(E_bad.conj().T @ d, adj.ravel()) > 1e-3
