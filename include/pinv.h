@@ -1,0 +1,194 @@
+/*
+ * pinv.h - C ABI of the GB300 Pinv-Recon library (explicit Tikhonov-regularised
+ * pseudoinverse MRI reconstruction, arXiv 2410.06129).
+ *
+ * The forward model is data = Encode x image (Eq. 1) with
+ *     Encode[(c, m), n] = s_c(r_n) * exp(-i 2 pi (k_m . r_n + df_n t_m))
+ * (Fourier term Eq. 2; coil-sensitivity and B0 off-resonance factors of
+ * Section 3.3, multiplied as in the composite encoding of Section 3.3).
+ * A plan holds one trajectory/coil/B0 configuration. Building it forms
+ *     G = Encode^H Encode + lambda I                      (Eq. 6)
+ *     G = L L^H                                           (Eq. 8)
+ *     Recon = (L^-1)^H L^-1 Encode^H                      (Eq. 8)
+ * and applying it computes image = Recon x data for a batch of frames (Eq. 3),
+ * or, for factor-only plans, image = G^-1 (sum_c Encode_c^H data_c)
+ * (Section 3.3, last paragraph).
+ *
+ * Conventions
+ *   - Complex numbers are interleaved (re, im). c64 = 2 x float, c128 = 2 x double.
+ *   - Voxels lie on a Cartesian grid: voxel with grid index (ix, iy, iz) sits at
+ *     r = ((i - dims/2) / dims) * fov per dimension; the flat grid index is
+ *     (iz * dims[1] + iy) * dims[0] + ix (x fastest). A plan reconstructs either
+ *     the whole grid or an explicit voxel list (mask / over-discretised subset).
+ *   - k is in cycles per unit length of fov (cycles/FOV when fov = 1).
+ *   - lambda is the diagonal load itself (the paper writes it lambda^2).
+ *   - Data batches are [F][C][M_k] (frame-major, coil, sample); images [F][N].
+ *
+ * Ownership and errors
+ *   - Host arrays in pinv_plan_desc are copied during pinv_plan_create; the
+ *     caller keeps ownership and may free them when it returns.
+ *   - Device buffers passed to pinv_apply belong to the caller and must stay
+ *     valid until the work enqueued on the given stream has completed.
+ *   - Streams are cudaStream_t values passed as void*; NULL is the legacy
+ *     default stream.
+ *   - Every call returns a pinv_status and never aborts. pinv_last_error()
+ *     returns a thread-local message for the last failing call on that thread.
+ *   - Errors found on the device (a non-positive Cholesky pivot, a bounded
+ *     wait that gave up) are recorded in the plan's device status word and
+ *     returned by pinv_plan_sync().
+ *   - A plan may be used from one host thread at a time.
+ */
+#ifndef PINV_H
+#define PINV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PINV_OK = 0,
+    PINV_ERR_INVALID_ARG = 1,  /* bad descriptor or argument */
+    PINV_ERR_OOM = 2,          /* device allocation failed */
+    PINV_ERR_BUDGET = 3,       /* would exceed a memory budget (serving) */
+    PINV_ERR_NOT_PD = 4,       /* G not positive definite; info = failing pivot */
+    PINV_ERR_NOT_BUILT = 5,    /* apply/export before a successful build */
+    PINV_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+    PINV_ERR_CUDA = 7,         /* CUDA runtime error (message has details) */
+    PINV_ERR_INTERNAL = 8,
+    PINV_ERR_UNSUPPORTED = 9   /* valid request this build does not implement */
+} pinv_status;
+
+typedef enum {
+    PINV_FP64 = 0,          /* every stage in FP64 (SIMT DFMA) */
+    PINV_MIXED_BF16X3 = 1,  /* tensor-core stages in split BF16, 2 slices / 3 products,
+                               FP32 accumulation, FP64 panels, FP64-residual refinement */
+    PINV_MIXED_BF16X6 = 2   /* as above with 3 slices / 6 products */
+} pinv_precision;
+
+typedef enum {
+    PINV_LAMBDA_ABS = 0,            /* lambda used as given */
+    PINV_LAMBDA_REL_MEAN_DIAG = 1   /* lambda * trace(E^H E) / N (mean diagonal of E^H E) */
+} pinv_lambda_mode;
+
+typedef enum { PINV_C64 = 0, PINV_C128 = 1 } pinv_dtype;
+
+typedef enum {
+    PINV_RECON_AUTO = -1,   /* explicit Recon if it fits the plan's footprint rule */
+    PINV_RECON_NONE = 0,    /* factor-only: keep L and G^-1, apply via E^H data */
+    PINV_RECON_STORE = 1    /* form and keep Recon = E^+ */
+} pinv_recon_mode;
+
+typedef struct {
+    int ndim;                     /* 1, 2 or 3 */
+    int dims[3];                  /* grid size per dimension (unused entries 1) */
+    double fov[3];                /* field of view per dimension (unused entries 1.0) */
+    const int64_t* voxel_index;   /* optional [N] flat grid indices; NULL = whole grid */
+    int64_t n_vox;                /* N (must be prod(dims) when voxel_index is NULL) */
+    int64_t n_samples;            /* M_k, samples per coil */
+    const double* traj;           /* [M_k][ndim] k-space positions */
+    int n_coils;                  /* C >= 1 */
+    const double* coil_maps;      /* [C][N] complex128, or NULL when C == 1 (s = 1) */
+    const double* b0_hz;          /* optional [N] off-resonance in Hz */
+    const double* times;          /* [M_k] sample times in s; required iff b0_hz != NULL */
+    double lambda;                /* diagonal load, see lambda_mode */
+    int lambda_mode;              /* pinv_lambda_mode */
+    int precision;                /* pinv_precision */
+    int recon_mode;               /* pinv_recon_mode */
+    int refine_max_iters;         /* mixed plans: max refinement steps per apply (0 = none) */
+    double refine_tol;            /* mixed plans: stop when ||r|| / ||E^H d|| <= tol */
+} pinv_plan_desc;
+
+typedef struct {
+    int64_t n_vox, n_samples, n_rows;   /* N, M_k, M = C * M_k */
+    int n_coils, precision, has_recon;
+    double lambda_abs;                  /* diagonal load actually used */
+    double min_pivot, max_pivot;        /* min / max of diag(L) (real, positive) */
+    size_t bytes_device;                /* device memory held by the plan */
+    size_t bytes_recon;                 /* of which Recon (E^+) */
+    double ms_tables, ms_gram, ms_chol, ms_inverse, ms_recon;  /* last build, CUDA events */
+    int info;                           /* failing pivot index (PINV_ERR_NOT_PD), else -1 */
+    int last_refine_iters;              /* refinement steps taken by the last apply */
+    double last_refine_resid;           /* ||r|| / ||E^H d|| after the last apply's refinement */
+} pinv_plan_info_t;
+
+typedef struct pinv_plan pinv_plan;
+
+/* Library version as 10000 * major + 100 * minor + patch. */
+int pinv_version(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all plans, all threads). Lets callers count the library's launches in a
+ * timed region. */
+unsigned long long pinv_kernel_launches(void);
+
+/* Thread-local message describing the last error on this thread ("" if none). */
+const char* pinv_last_error(void);
+
+/*
+ * Validate the descriptor, copy its arrays to the device on `stream` and
+ * compute lambda. Builds nothing yet. Errors: INVALID_ARG (bad sizes, missing
+ * times with b0_hz, C > 1 without coil maps, voxel index out of range),
+ * OOM, CUDA. On success *out owns device memory until pinv_plan_destroy.
+ */
+pinv_status pinv_plan_create(const pinv_plan_desc* desc, void* stream, pinv_plan** out);
+
+/*
+ * Enqueue the build on `stream`: phase tables, Gram G = E^H E + lambda I
+ * (E generated on the fly, coils folded in as the Hadamard product of the
+ * coil-independent Gram with sum_c conj(s_c) s_c^T), blocked Cholesky G = L L^H,
+ * G^-1 = (L^-1)^H L^-1, and (unless factor-only) Recon = G^-1 E^H (Eq. 6, 8).
+ * Asynchronous: call pinv_plan_sync to learn whether G was positive definite.
+ */
+pinv_status pinv_build(pinv_plan* plan, void* stream);
+
+/*
+ * Wait for all work the plan enqueued, read its device status word and
+ * return it: OK, NOT_PD (info = failing pivot), TIMEOUT or CUDA.
+ */
+pinv_status pinv_plan_sync(pinv_plan* plan);
+
+/*
+ * image = Recon x data for n_frames frames (Eq. 3), or G^-1 E^H data for
+ * factor-only plans (Section 3.3). d_data: device [F][C][M_k], d_image:
+ * device [F][N], both of `dtype` (pinv_dtype). Mixed-precision plans refine
+ * each frame with FP64 residuals r = E^H (d - E x) - lambda x up to
+ * refine_max_iters times. n_frames == 0 is a no-op. Uses plan-owned
+ * scratch sized on first use; concurrent applies of one plan must be
+ * serialised on one stream.
+ */
+pinv_status pinv_apply(pinv_plan* plan, const void* d_data, void* d_image, int64_t n_frames,
+                       int dtype, void* stream);
+
+/* Matrices a plan can export (device copies into caller buffers). */
+typedef enum {
+    PINV_EXPORT_GRAM = 0,    /* [N][N] c128: lower triangle of G (upper left untouched) */
+    PINV_EXPORT_CHOL = 1,    /* [N][N] c128: lower triangle of L */
+    PINV_EXPORT_GINV = 2,    /* [N][N] c128: G^-1, full */
+    PINV_EXPORT_RECON = 3    /* [N][C*M_k]: Recon = E^+, c128 (FP64 plans) or c64 (mixed) */
+} pinv_export_what;
+
+/*
+ * Copy an internal matrix into the caller's device buffer `dst` of `bytes`
+ * bytes, on `stream`. INVALID_ARG if bytes is too small, NOT_BUILT before a
+ * build, UNSUPPORTED for RECON on factor-only plans. The Gram is kept only
+ * until the Cholesky overwrites it unless the plan was built after
+ * pinv_plan_keep_gram(plan, 1).
+ */
+pinv_status pinv_plan_export(const pinv_plan* plan, int what, void* dst, size_t bytes, void* stream);
+
+/* Keep a copy of G (before factorisation) for export and diagnostics. */
+pinv_status pinv_plan_keep_gram(pinv_plan* plan, int keep);
+
+/* Sizes, lambda, pivots and per-stage timings of the last build. */
+pinv_status pinv_plan_info(const pinv_plan* plan, pinv_plan_info_t* out);
+
+/* Free the plan and its device memory (synchronises the plan's work). NULL is a no-op. */
+void pinv_plan_destroy(pinv_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PINV_H */

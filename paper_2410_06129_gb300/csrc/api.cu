@@ -1,0 +1,539 @@
+// C ABI of the Pinv-Recon library: plan creation, build, apply, export.
+//
+// A plan owns the device copies of its encoding description (trajectory
+// tables, voxel coordinates, coil maps, B0 table), the factor L (stored over
+// G), G^-1 and optionally Recon = E^+. Building enqueues the stages on the
+// caller's stream; nothing blocks until pinv_plan_sync.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "pinv_internal.h"
+
+using namespace pinv;
+
+namespace {
+thread_local std::string g_err;
+
+pinv_status fail(pinv_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+pinv_status cuda_fail(cudaError_t e, const char* where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PINV_ERR_OOM : PINV_ERR_CUDA;
+}
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+}  // namespace
+
+struct pinv_plan {
+    int ndim = 0;
+    int dims[3] = {1, 1, 1};
+    double fov[3] = {1, 1, 1};
+    int64_t N = 0, Mk = 0, M = 0;
+    int C = 1;
+    double lambda_abs = 0;
+    int precision = PINV_FP64;
+    int recon = 1;
+    int refine_iters = 0;
+    double refine_tol = 0;
+    bool keep_gram = false;
+    bool built = false;
+
+    std::vector<void*> allocs;
+    size_t bytes = 0, bytes_recon = 0;
+
+    EncodeDev enc{};
+    double* traj = nullptr;
+    double2* G = nullptr;      // Gram, then L in place (lower)
+    double2* Gkeep = nullptr;  // copy of G if requested
+    double2* Dinv = nullptr;   // inverses of the diagonal blocks
+    double2* Ginv = nullptr;   // full G^-1
+    void* R = nullptr;         // Recon [N][M], c128 (FP64) or c64 (mixed)
+    DevStatus* st = nullptr;
+
+    // apply scratch (grown on demand)
+    int64_t scratch_frames = 0;
+    double2 *d128 = nullptr, *x128 = nullptr, *u128 = nullptr, *r128 = nullptr;
+    float2 *d64 = nullptr, *x64 = nullptr;
+    double* norms = nullptr;
+    std::vector<void*> scratch;
+
+    cudaEvent_t ev[6] = {};
+    int last_refine_iters = 0;
+    double last_refine_resid = 0;
+    int info = -1;
+
+    pinv_status alloc(void** p, size_t n, const char* what) {
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(p, n);
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            return fail(e == cudaErrorMemoryAllocation ? PINV_ERR_OOM : PINV_ERR_CUDA,
+                        std::string("cudaMalloc(") + what + ", " + std::to_string(n) + " B): " +
+                            cudaGetErrorString(e));
+        }
+        allocs.push_back(*p);
+        bytes += n;
+        return PINV_OK;
+    }
+    ~pinv_plan() {
+        for (void* p : scratch) cudaFree(p);
+        for (void* p : allocs) cudaFree(p);
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+namespace pinv {
+std::atomic<unsigned long long> g_launches{0};
+}
+
+extern "C" {
+
+int pinv_version(void) { return 100; }
+
+unsigned long long pinv_kernel_launches(void) { return g_launches.load(); }
+
+const char* pinv_last_error(void) { return g_err.c_str(); }
+
+static pinv_status reset_status(pinv_plan* p, cudaStream_t s) {
+    DevStatus h{};
+    h.not_pd_pivot = INT_MAX;
+    h.timeout_site = 0;
+    h.error_code = 0;
+    h.min_pivot = INFINITY;
+    h.max_pivot = 0.0;
+    // small pageable copy: the staging makes it safe to return immediately
+    CK(cudaMemcpyAsync(p->st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    return PINV_OK;
+}
+
+pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** out) {
+    g_err.clear();
+    if (!d || !out) return fail(PINV_ERR_INVALID_ARG, "null descriptor or output pointer");
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d->ndim < 1 || d->ndim > 3) return fail(PINV_ERR_INVALID_ARG, "ndim must be 1, 2 or 3");
+    int64_t grid = 1;
+    for (int i = 0; i < d->ndim; ++i) {
+        if (d->dims[i] < 1) return fail(PINV_ERR_INVALID_ARG, "dims must be >= 1");
+        grid *= d->dims[i];
+    }
+    if (d->n_vox < 1) return fail(PINV_ERR_INVALID_ARG, "n_vox must be >= 1");
+    if (!d->voxel_index && d->n_vox != grid)
+        return fail(PINV_ERR_INVALID_ARG, "n_vox must equal prod(dims) without voxel_index");
+    if (d->n_samples < 1 || !d->traj) return fail(PINV_ERR_INVALID_ARG, "need n_samples >= 1 and traj");
+    if (d->n_coils < 1) return fail(PINV_ERR_INVALID_ARG, "n_coils must be >= 1");
+    if (d->n_coils > 1 && !d->coil_maps) return fail(PINV_ERR_INVALID_ARG, "n_coils > 1 needs coil_maps");
+    if (d->b0_hz && !d->times) return fail(PINV_ERR_INVALID_ARG, "b0_hz needs times");
+    if (d->precision < PINV_FP64 || d->precision > PINV_MIXED_BF16X6)
+        return fail(PINV_ERR_INVALID_ARG, "unknown precision");
+    if (d->precision != PINV_FP64 && !tc_available())
+        return fail(PINV_ERR_UNSUPPORTED, "mixed precision needs the tcgen05 kernels (sm_103a)");
+    if (d->lambda_mode != PINV_LAMBDA_ABS && d->lambda_mode != PINV_LAMBDA_REL_MEAN_DIAG)
+        return fail(PINV_ERR_INVALID_ARG, "unknown lambda_mode");
+    if (!(d->lambda >= 0.0) || !std::isfinite(d->lambda))
+        return fail(PINV_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+    if (d->refine_max_iters < 0) return fail(PINV_ERR_INVALID_ARG, "refine_max_iters must be >= 0");
+    for (int64_t i = 0; i < d->n_samples * d->ndim; ++i)
+        if (!std::isfinite(d->traj[i])) return fail(PINV_ERR_INVALID_ARG, "non-finite trajectory");
+
+    auto* p = new pinv_plan();
+    auto cleanup = [&](pinv_status st) { delete p; return st; };
+    p->ndim = d->ndim;
+    for (int i = 0; i < 3; ++i) {
+        p->dims[i] = i < d->ndim ? d->dims[i] : 1;
+        p->fov[i] = i < d->ndim ? d->fov[i] : 1.0;
+    }
+    p->N = d->n_vox;
+    p->Mk = d->n_samples;
+    p->C = d->n_coils;
+    p->M = p->Mk * p->C;
+    p->precision = d->precision;
+    p->refine_iters = d->refine_max_iters;
+    p->refine_tol = d->refine_tol;
+
+    // voxel grid coordinates
+    std::vector<int> ijk(3 * p->N);
+    for (int64_t n = 0; n < p->N; ++n) {
+        int64_t g = d->voxel_index ? d->voxel_index[n] : n;
+        if (g < 0 || g >= grid) return cleanup(fail(PINV_ERR_INVALID_ARG, "voxel_index out of range"));
+        ijk[3 * n + 0] = (int)(g % p->dims[0]);
+        ijk[3 * n + 1] = (int)((g / p->dims[0]) % p->dims[1]);
+        ijk[3 * n + 2] = (int)(g / ((int64_t)p->dims[0] * p->dims[1]));
+    }
+    // lambda: trace(E^H E) / N = M_k * mean_n sum_c |s_c(n)|^2 since |A| = 1
+    double sos = (double)p->N;
+    if (d->coil_maps) {
+        sos = 0.0;
+        for (int64_t i = 0; i < 2 * p->N * p->C; ++i) {
+            double v = d->coil_maps[i];
+            if (!std::isfinite(v)) return cleanup(fail(PINV_ERR_INVALID_ARG, "non-finite coil map"));
+            sos += v * v;
+        }
+    }
+    p->lambda_abs = d->lambda_mode == PINV_LAMBDA_ABS ? d->lambda
+                                                      : d->lambda * (double)p->Mk * sos / (double)p->N;
+    // B0: distinct sample times
+    std::vector<double> tuniq;
+    std::vector<int> tidx;
+    if (d->b0_hz) {
+        std::map<double, int> idx;
+        for (int64_t m = 0; m < p->Mk; ++m) idx.emplace(d->times[m], 0);
+        int u = 0;
+        for (auto& kv : idx) { kv.second = u++; tuniq.push_back(kv.first); }
+        tidx.resize(p->Mk);
+        for (int64_t m = 0; m < p->Mk; ++m) tidx[m] = idx[d->times[m]];
+        double tab_bytes = (double)tuniq.size() * (double)p->N * 24.0;
+        if (tab_bytes > 16e9)
+            return cleanup(fail(PINV_ERR_UNSUPPORTED, "too many distinct sample times for the B0 table"));
+    }
+
+    pinv_status st;
+#define AL(ptr, n, what)                                               \
+    do {                                                               \
+        st = p->alloc((void**)&(ptr), (size_t)(n), what);             \
+        if (st != PINV_OK) return cleanup(st);                        \
+    } while (0)
+#define CKC(call)                                                      \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return cleanup(cuda_fail(e_, #call));  \
+    } while (0)
+
+    EncodeDev& e = p->enc;
+    e.N = p->N;
+    e.Mk = p->Mk;
+    e.C = p->C;
+    e.nx = p->dims[0];
+    e.ny = p->dims[1];
+    e.nz = p->dims[2];
+    AL(p->traj, sizeof(double) * p->Mk * p->ndim, "traj");
+    double2 *ex, *ey, *ez;
+    float2 *ex32, *ey32, *ez32;
+    AL(ex, sizeof(double2) * p->Mk * e.nx, "ex");
+    AL(ey, sizeof(double2) * p->Mk * e.ny, "ey");
+    AL(ez, sizeof(double2) * p->Mk * e.nz, "ez");
+    AL(ex32, sizeof(float2) * p->Mk * e.nx, "ex32");
+    AL(ey32, sizeof(float2) * p->Mk * e.ny, "ey32");
+    AL(ez32, sizeof(float2) * p->Mk * e.nz, "ez32");
+    int* vox;
+    AL(vox, sizeof(int) * 3 * p->N, "vox");
+    AL(p->st, sizeof(DevStatus), "status");
+    e.ex = ex; e.ey = ey; e.ez = ez;
+    e.ex32 = ex32; e.ey32 = ey32; e.ez32 = ez32;
+    e.vox_ijk = vox;
+    // inputs travel through pageable memory; the stream sync below makes the
+    // host arrays free to reuse when this call returns
+    CKC(cudaMemcpyAsync(p->traj, d->traj, sizeof(double) * p->Mk * p->ndim, cudaMemcpyHostToDevice, s));
+    CKC(cudaMemcpyAsync(vox, ijk.data(), sizeof(int) * 3 * p->N, cudaMemcpyHostToDevice, s));
+    if (d->coil_maps) {
+        double2* cm;
+        float2* cm32;
+        AL(cm, sizeof(double2) * p->C * p->N, "coils");
+        AL(cm32, sizeof(float2) * p->C * p->N, "coils32");
+        CKC(cudaMemcpyAsync(cm, d->coil_maps, sizeof(double2) * p->C * p->N, cudaMemcpyHostToDevice, s));
+        CKC(launch_to_f32(cm, cm32, p->C * p->N, s));
+        e.coils = cm;
+        e.coils32 = cm32;
+    }
+    if (d->b0_hz) {
+        int T = (int)tuniq.size();
+        double *b0, *tu;
+        double2* tab;
+        float2* tab32;
+        int* ti;
+        AL(b0, sizeof(double) * p->N, "b0");
+        AL(tu, sizeof(double) * T, "tuniq");
+        AL(tab, sizeof(double2) * T * p->N, "b0tab");
+        AL(tab32, sizeof(float2) * T * p->N, "b0tab32");
+        AL(ti, sizeof(int) * p->Mk, "tidx");
+        CKC(cudaMemcpyAsync(b0, d->b0_hz, sizeof(double) * p->N, cudaMemcpyHostToDevice, s));
+        CKC(cudaMemcpyAsync(tu, tuniq.data(), sizeof(double) * T, cudaMemcpyHostToDevice, s));
+        CKC(cudaMemcpyAsync(ti, tidx.data(), sizeof(int) * p->Mk, cudaMemcpyHostToDevice, s));
+        CKC(launch_b0_table(b0, tu, T, p->N, tab, tab32, s));
+        e.b0tab = tab;
+        e.b0tab32 = tab32;
+        e.tidx = ti;
+    }
+    CKC(launch_tables(p->traj, p->ndim, p->Mk, p->dims, p->fov, ex, ey, ez, ex32, ey32, ez32, s));
+    // factor storage
+    int64_t nblk = (p->N + 63) / 64;
+    AL(p->G, sizeof(double2) * p->N * p->N, "G");
+    AL(p->Dinv, sizeof(double2) * nblk * 64 * 64, "Dinv");
+    AL(p->Ginv, sizeof(double2) * p->N * p->N, "Ginv");
+    int rm = d->recon_mode;
+    if (rm == PINV_RECON_AUTO) {
+        size_t rb = (size_t)p->N * p->M * (p->precision == PINV_FP64 ? 16 : 8);
+        rm = rb <= ((size_t)64 << 30) ? 1 : 0;
+    }
+    p->recon = rm ? 1 : 0;
+    if (p->recon) {
+        size_t rb = (size_t)p->N * p->M * (p->precision == PINV_FP64 ? sizeof(double2) : sizeof(float2));
+        AL(p->R, rb, "Recon");
+        p->bytes_recon = rb;
+    }
+    for (auto& ev : p->ev) CKC(cudaEventCreate(&ev));
+    pinv_status rs = reset_status(p, s);
+    if (rs != PINV_OK) return cleanup(rs);
+    CKC(cudaStreamSynchronize(s));
+#undef AL
+#undef CKC
+    *out = p;
+    return PINV_OK;
+}
+
+pinv_status pinv_plan_keep_gram(pinv_plan* p, int keep) {
+    if (!p) return fail(PINV_ERR_INVALID_ARG, "null plan");
+    p->keep_gram = keep != 0;
+    return PINV_OK;
+}
+
+pinv_status pinv_build(pinv_plan* p, void* stream) {
+    g_err.clear();
+    if (!p) return fail(PINV_ERR_INVALID_ARG, "null plan");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->built = false;
+    pinv_status rs = reset_status(p, s);
+    if (rs != PINV_OK) return rs;
+    if (p->keep_gram && !p->Gkeep) {
+        pinv_status st = p->alloc((void**)&p->Gkeep, sizeof(double2) * p->N * p->N, "Gkeep");
+        if (st != PINV_OK) return st;
+    }
+    const int64_t N = p->N, ld = p->N;
+    const bool mixed = p->precision != PINV_FP64;
+    const int slices = p->precision == PINV_MIXED_BF16X6 ? 3 : 2;
+    CK(cudaEventRecord(p->ev[0], s));
+    CK(cudaEventRecord(p->ev[1], s));  // tables were built at plan creation
+    if (mixed) CK(launch_gram_tc(p->enc, p->lambda_abs, slices, p->G, ld, p->st, s));
+    else CK(launch_gram64(p->enc, p->lambda_abs, p->G, ld, s));
+    if (p->Gkeep) CK(cudaMemcpyAsync(p->Gkeep, p->G, sizeof(double2) * N * N, cudaMemcpyDeviceToDevice, s));
+    CK(cudaEventRecord(p->ev[2], s));
+    CK(launch_potrf64(p->G, N, ld, p->Dinv, p->st, s));
+    CK(launch_pivot_stats(p->G, N, ld, p->st, s));
+    CK(cudaEventRecord(p->ev[3], s));
+    double2* W = nullptr;
+    CK(cudaMallocAsync((void**)&W, sizeof(double2) * N * N, s));
+    CK(launch_trtri64(p->G, N, ld, p->Dinv, W, s));
+    CK(launch_lauum64(W, N, ld, p->Ginv, s));
+    CK(cudaFreeAsync(W, s));
+    CK(cudaEventRecord(p->ev[4], s));
+    if (p->recon) {
+        if (mixed) CK(launch_recon_tc(p->enc, p->Ginv, ld, slices, (float2*)p->R, p->st, s));
+        else CK(launch_recon64(p->enc, p->Ginv, ld, (double2*)p->R, s));
+    }
+    CK(cudaEventRecord(p->ev[5], s));
+    p->built = true;
+    return PINV_OK;
+}
+
+pinv_status pinv_plan_sync(pinv_plan* p) {
+    if (!p) return fail(PINV_ERR_INVALID_ARG, "null plan");
+    CK(cudaEventSynchronize(p->ev[5]));
+    CK(cudaDeviceSynchronize());
+    DevStatus h{};
+    CK(cudaMemcpy(&h, p->st, sizeof(h), cudaMemcpyDeviceToHost));
+    p->info = -1;
+    if (h.not_pd_pivot != INT_MAX) {
+        p->info = h.not_pd_pivot;
+        p->built = false;
+        return fail(PINV_ERR_NOT_PD, "Gram matrix not positive definite at pivot " +
+                                         std::to_string(h.not_pd_pivot) + " (increase lambda)");
+    }
+    if (h.timeout_site) {
+        p->built = false;
+        return fail(PINV_ERR_TIMEOUT, "a bounded device wait gave up (site " +
+                                          std::to_string(h.timeout_site) + ")");
+    }
+    if (h.error_code) {
+        p->built = false;
+        return fail(PINV_ERR_INTERNAL, "device error code " + std::to_string(h.error_code));
+    }
+    return PINV_OK;
+}
+
+static pinv_status ensure_scratch(pinv_plan* p, int64_t F) {
+    if (F <= p->scratch_frames) return PINV_OK;
+    for (void* q : p->scratch) cudaFree(q);
+    p->scratch.clear();
+    auto get = [&](void** q, size_t n) -> pinv_status {
+        cudaError_t e = cudaMalloc(q, n);
+        if (e != cudaSuccess) return cuda_fail(e, "apply scratch");
+        p->scratch.push_back(*q);
+        return PINV_OK;
+    };
+    pinv_status st;
+    if ((st = get((void**)&p->d128, sizeof(double2) * F * p->M)) != PINV_OK) return st;
+    if ((st = get((void**)&p->u128, sizeof(double2) * F * p->M)) != PINV_OK) return st;
+    if ((st = get((void**)&p->x128, sizeof(double2) * F * p->N)) != PINV_OK) return st;
+    if ((st = get((void**)&p->r128, sizeof(double2) * F * p->N)) != PINV_OK) return st;
+    if ((st = get((void**)&p->d64, sizeof(float2) * F * p->M)) != PINV_OK) return st;
+    if ((st = get((void**)&p->x64, sizeof(float2) * F * p->N)) != PINV_OK) return st;
+    if ((st = get((void**)&p->norms, sizeof(double) * 2 * F)) != PINV_OK) return st;
+    p->scratch_frames = F;
+    return PINV_OK;
+}
+
+pinv_status pinv_apply(pinv_plan* p, const void* d_data, void* d_image, int64_t F, int dtype,
+                       void* stream) {
+    g_err.clear();
+    if (!p) return fail(PINV_ERR_INVALID_ARG, "null plan");
+    if (F < 0) return fail(PINV_ERR_INVALID_ARG, "n_frames < 0");
+    if (dtype != PINV_C64 && dtype != PINV_C128) return fail(PINV_ERR_INVALID_ARG, "dtype");
+    if (!p->built) return fail(PINV_ERR_NOT_BUILT, "plan not built");
+    if (F == 0) return PINV_OK;
+    if (!d_data || !d_image) return fail(PINV_ERR_INVALID_ARG, "null data or image");
+    cudaStream_t s = (cudaStream_t)stream;
+    pinv_status st = ensure_scratch(p, F);
+    if (st != PINV_OK) return st;
+    const int64_t N = p->N, M = p->M;
+    const bool mixed = p->precision != PINV_FP64;
+    p->last_refine_iters = 0;
+    p->last_refine_resid = 0;
+
+    // FP64 data view
+    const double2* D = nullptr;
+    auto need_d128 = [&]() -> pinv_status {
+        if (D) return PINV_OK;
+        if (dtype == PINV_C128) D = (const double2*)d_data;
+        else {
+            CK(launch_c64_to_c128((const float2*)d_data, p->d128, F * M, s));
+            D = p->d128;
+        }
+        return PINV_OK;
+    };
+    double2* X = dtype == PINV_C128 ? (double2*)d_image : p->x128;
+
+    if (!mixed) {
+        if ((st = need_d128()) != PINV_OK) return st;
+        if (p->recon) {
+            CK(launch_apply64((const double2*)p->R, N, M, D, F, X, s));
+        } else {
+            CK(launch_adjoint64(p->enc, D, F, 0.0, nullptr, p->r128, s));
+            CK(launch_hemv64(p->Ginv, N, N, p->r128, F, nullptr, X, s));
+        }
+    } else {
+        // initial image from the mixed-precision operator
+        if (p->recon) {
+            const float2* D32 = (const float2*)d_data;
+            if (dtype == PINV_C128) {
+                CK(launch_c128_to_c64((const double2*)d_data, p->d64, F * M, s));
+                D32 = p->d64;
+            }
+            CK(launch_apply32((const float2*)p->R, N, M, D32, F, p->x64, s));
+            CK(launch_c64_to_c128(p->x64, X, F * N, s));
+        } else {
+            if ((st = need_d128()) != PINV_OK) return st;
+            CK(launch_adjoint64(p->enc, D, F, 0.0, nullptr, p->r128, s));
+            CK(launch_hemv64(p->Ginv, N, N, p->r128, F, nullptr, X, s));
+        }
+    }
+    {
+        // FP64 residual refinement: r = E^H (d - E x) - lambda x, x += Ginv r.
+        // Mixed plans need it to reach FP64-level accuracy; FP64 plans may use
+        // it to remove the explicit inverse's extra rounding (kappa(G) u).
+        if (p->refine_iters > 0) {
+            if ((st = need_d128()) != PINV_OK) return st;
+            std::vector<double> h(2 * F);
+            CK(launch_adjoint64(p->enc, D, F, 0.0, nullptr, p->r128, s));  // b = E^H d
+            CK(launch_frame_norms(p->r128, F, N, p->norms + F, s));
+            for (int it = 0; it < p->refine_iters; ++it) {
+                CK(launch_forward64(p->enc, X, F, D, p->u128, s));           // u = d - E x
+                CK(launch_adjoint64(p->enc, p->u128, F, p->lambda_abs, X, p->r128, s));
+                CK(launch_frame_norms(p->r128, F, N, p->norms, s));
+                CK(launch_hemv64(p->Ginv, N, N, p->r128, F, X, X, s));      // x += Ginv r
+                CK(cudaMemcpyAsync(h.data(), p->norms, sizeof(double) * 2 * F, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                double worst = 0;
+                for (int64_t f = 0; f < F; ++f)
+                    worst = std::max(worst, std::sqrt(h[f] / std::max(h[F + f], 1e-300)));
+                p->last_refine_iters = it + 1;
+                p->last_refine_resid = worst;
+                if (worst <= p->refine_tol) break;
+            }
+        }
+    }
+    if (dtype == PINV_C64) CK(launch_c128_to_c64(X, (float2*)d_image, F * N, s));
+    return PINV_OK;
+}
+
+pinv_status pinv_plan_export(const pinv_plan* p, int what, void* dst, size_t bytes, void* stream) {
+    g_err.clear();
+    if (!p || !dst) return fail(PINV_ERR_INVALID_ARG, "null plan or destination");
+    if (!p->built) return fail(PINV_ERR_NOT_BUILT, "plan not built");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t nn = sizeof(double2) * p->N * p->N;
+    const void* src = nullptr;
+    size_t need = nn;
+    switch (what) {
+        case PINV_EXPORT_GRAM:
+            if (!p->Gkeep) return fail(PINV_ERR_NOT_BUILT, "Gram not kept (pinv_plan_keep_gram before build)");
+            src = p->Gkeep;
+            break;
+        case PINV_EXPORT_CHOL: src = p->G; break;
+        case PINV_EXPORT_GINV: src = p->Ginv; break;
+        case PINV_EXPORT_RECON:
+            if (!p->recon) return fail(PINV_ERR_UNSUPPORTED, "factor-only plan has no Recon");
+            src = p->R;
+            need = p->bytes_recon;
+            break;
+        default: return fail(PINV_ERR_INVALID_ARG, "unknown export");
+    }
+    if (bytes < need) return fail(PINV_ERR_INVALID_ARG, "destination too small");
+    if (what == PINV_EXPORT_CHOL) {
+        CK(launch_copy_lower(p->G, p->N, p->N, (double2*)dst, s));
+    } else {
+        CK(cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToDevice, s));
+    }
+    return PINV_OK;
+}
+
+pinv_status pinv_plan_info(const pinv_plan* p, pinv_plan_info_t* o) {
+    if (!p || !o) return fail(PINV_ERR_INVALID_ARG, "null plan or output");
+    std::memset(o, 0, sizeof(*o));
+    o->n_vox = p->N;
+    o->n_samples = p->Mk;
+    o->n_rows = p->M;
+    o->n_coils = p->C;
+    o->precision = p->precision;
+    o->has_recon = p->recon;
+    o->lambda_abs = p->lambda_abs;
+    o->bytes_device = p->bytes;
+    o->bytes_recon = p->bytes_recon;
+    o->info = p->info;
+    o->last_refine_iters = p->last_refine_iters;
+    o->last_refine_resid = p->last_refine_resid;
+    if (p->built) {
+        CK(cudaEventSynchronize(p->ev[5]));
+        float t[5] = {0};
+        for (int i = 0; i < 5; ++i) CK(cudaEventElapsedTime(&t[i], p->ev[i], p->ev[i + 1]));
+        o->ms_tables = t[0];
+        o->ms_gram = t[1];
+        o->ms_chol = t[2];
+        o->ms_inverse = t[3];
+        o->ms_recon = t[4];
+        DevStatus h{};
+        CK(cudaMemcpy(&h, p->st, sizeof(h), cudaMemcpyDeviceToHost));
+        o->min_pivot = h.min_pivot;
+        o->max_pivot = h.max_pivot;
+    }
+    return PINV_OK;
+}
+
+void pinv_plan_destroy(pinv_plan* p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "pinv.h"
+
+namespace pinv {
+
+// Kernels launched by this library in this process (reported to callers).
+extern std::atomic<unsigned long long> g_launches;
+inline void note_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------
+// Device-side encoding description: everything a kernel needs to generate an
+// element of the coil-independent encoding A[m][n] = exp(-i2pi(k_m.r_n + df_n t_m))
+// and the coil factor s_c(n), without ever storing A or E.
+// ---------------------------------------------------------------------------
+struct EncodeDev {
+    int64_t N;        // voxels
+    int64_t Mk;       // samples per coil
+    int C;            // coils
+    int nx, ny, nz;   // separable table widths (1 for unused dimensions)
+    const double2* ex;      // [Mk][nx] exp(-i2pi kx_m x_ix)
+    const double2* ey;      // [Mk][ny]
+    const double2* ez;      // [Mk][nz]
+    const int* vox_ijk;     // [N][3] grid coordinates of voxel n
+    const double2* b0tab;   // [T][N] exp(-i2pi df_n t_u) or nullptr
+    const int* tidx;        // [Mk] index u of t_m in b0tab, or nullptr
+    const double2* coils;   // [C][N] s_c(n) or nullptr (C == 1, s = 1)
+    // single-precision copies for the tensor-core producers
+    const float2* ex32;
+    const float2* ey32;
+    const float2* ez32;
+    const float2* b0tab32;
+    const float2* coils32;
+};
+
+// Device status word of a plan.
+struct DevStatus {
+    int not_pd_pivot;   // smallest failing pivot index, INT_MAX if none
+    int timeout_site;   // nonzero if a bounded wait gave up
+    int error_code;     // other device-detected error
+    int pad;
+    double min_pivot;   // min diag(L) as ordered bits (set by panel kernels)
+    double max_pivot;
+};
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+__host__ __device__ inline double2 zmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ inline double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ inline void zfma(double2& acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+
+// Coil-independent encoding element A[m][n] in FP64.
+__device__ inline double2 gen_a64(const EncodeDev& e, int64_t m, int64_t n) {
+    const int* g = e.vox_ijk + 3 * n;
+    double2 v = e.ex[m * e.nx + g[0]];
+    if (e.ny > 1) v = zmul(v, e.ey[m * e.ny + g[1]]);
+    if (e.nz > 1) v = zmul(v, e.ez[m * e.nz + g[2]]);
+    if (e.b0tab) v = zmul(v, e.b0tab[(int64_t)e.tidx[m] * e.N + n]);
+    return v;
+}
+
+// Encoding element E[(c, m)][n] = s_c(n) A[m][n] in FP64.
+__device__ inline double2 gen_e64(const EncodeDev& e, int c, int64_t m, int64_t n) {
+    double2 v = gen_a64(e, m, n);
+    if (e.coils) v = zmul(v, e.coils[(int64_t)c * e.N + n]);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 kernels (zgemm64.cu, chol64.cu, tables.cu)
+// ---------------------------------------------------------------------------
+cudaError_t launch_tables(const double* traj, int ndim, int64_t Mk, const int* dims,
+                          const double* fov, double2* ex, double2* ey, double2* ez,
+                          float2* ex32, float2* ey32, float2* ez32, cudaStream_t s);
+cudaError_t launch_b0_table(const double* b0, const double* tuniq, int T, int64_t N,
+                            double2* tab, float2* tab32, cudaStream_t s);
+cudaError_t launch_to_f32(const double2* src, float2* dst, int64_t n, cudaStream_t s);
+cudaError_t launch_fill_identity(double2* W, int64_t N, int64_t ld, cudaStream_t s);
+
+// Gram G = (A^H A) o (S^H S) + lambda I, lower tiles, FP64.
+cudaError_t launch_gram64(const EncodeDev& e, double lambda, double2* G, int64_t ld, cudaStream_t s);
+// Cholesky in place on the lower triangle of G (FP64, blocked, nb = 64).
+cudaError_t launch_potrf64(double2* G, int64_t N, int64_t ld, double2* Dinv, DevStatus* st,
+                           cudaStream_t s);
+// W = L^-1 (lower), using the diagonal-block inverses Dinv from the factorisation.
+cudaError_t launch_trtri64(const double2* L, int64_t N, int64_t ld, const double2* Dinv,
+                           double2* W, cudaStream_t s);
+// Ginv = W^H W, full Hermitian matrix.
+cudaError_t launch_lauum64(const double2* W, int64_t N, int64_t ld, double2* Ginv, cudaStream_t s);
+// Recon[n][(c,m)] = sum_n' Ginv[n][n'] conj(E[(c,m)][n']), FP64.
+cudaError_t launch_recon64(const EncodeDev& e, const double2* Ginv, int64_t ld, double2* R,
+                           cudaStream_t s);
+// X[f][n] = sum_j R[n][j] D[f][j] (R row-major [N][M], D [F][M]), FP64.
+cudaError_t launch_apply64(const double2* R, int64_t N, int64_t M, const double2* D, int64_t F,
+                           double2* X, cudaStream_t s);
+// Y[f][n] = sum_j conj(E[j][n]) D[f][j] - lam * Xsub[f][n] (Xsub may be null), FP64.
+cudaError_t launch_adjoint64(const EncodeDev& e, const double2* D, int64_t F, double lam,
+                             const double2* Xsub, double2* Y, cudaStream_t s);
+// U[f][j] = Dsub[f][j] - sum_n E[j][n] X[f][n] (Dsub may be null: U = -E X), FP64.
+cudaError_t launch_forward64(const EncodeDev& e, const double2* X, int64_t F, const double2* Dsub,
+                             double2* U, cudaStream_t s);
+// Y[f][n] = Yadd[f][n] + sum_n' H[n][n'] X[f][n'] (H full [N][N]), FP64.
+cudaError_t launch_hemv64(const double2* H, int64_t N, int64_t ld, const double2* X, int64_t F,
+                          const double2* Yadd, double2* Y, cudaStream_t s);
+// Copy the lower triangle of G (incl. diagonal) to L, zeroing the upper triangle.
+cudaError_t launch_copy_lower(const double2* G, int64_t N, int64_t ld, double2* L, cudaStream_t s);
+// Pivot extrema of diag(L) into st->min_pivot / max_pivot.
+cudaError_t launch_pivot_stats(const double2* L, int64_t N, int64_t ld, DevStatus* st,
+                               cudaStream_t s);
+// Conversions between c64 and c128 frame buffers.
+cudaError_t launch_c64_to_c128(const float2* a, double2* b, int64_t n, cudaStream_t s);
+cudaError_t launch_c128_to_c64(const double2* a, float2* b, int64_t n, cudaStream_t s);
+// Per-frame squared norms: out[f] = sum_n |X[f][n]|^2 (FP64).
+cudaError_t launch_frame_norms(const double2* X, int64_t F, int64_t n, double* out, cudaStream_t s);
+// X += Y (FP64, n elements)
+cudaError_t launch_zaxpy(double2* X, const double2* Y, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Mixed-precision (tcgen05, split BF16) kernels (tc_gemm.cu)
+// ---------------------------------------------------------------------------
+// Gram in split BF16 on tcgen05 tensor cores; result written as FP64 lower tiles.
+cudaError_t launch_gram_tc(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld,
+                           DevStatus* st, cudaStream_t s);
+// Recon in split BF16 on tcgen05: R[n][(c,m)] = sum_n' Ginv[n][n'] conj(E[(c,m)][n']), c64 out.
+cudaError_t launch_recon_tc(const EncodeDev& e, const double2* Ginv, int64_t ld, int slices,
+                            float2* R, DevStatus* st, cudaStream_t s);
+// X[f][n] = sum_j R[n][j] D[f][j], c64 (R c64 [N][M], D c64 [F][M]).
+cudaError_t launch_apply32(const float2* R, int64_t N, int64_t M, const float2* D, int64_t F,
+                           float2* X, cudaStream_t s);
+bool tc_available();
+
+}  // namespace pinv
