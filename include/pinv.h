@@ -124,6 +124,10 @@ int pinv_version(void);
  * timed region. */
 unsigned long long pinv_kernel_launches(void);
 
+/* 1 if the current device runs this build's tensor-core (tcgen05, sm_103a)
+ * kernels, which mixed-precision plans need; 0 otherwise. */
+int pinv_tc_available(void);
+
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char* pinv_last_error(void);
 
@@ -167,7 +171,8 @@ typedef enum {
     PINV_EXPORT_GRAM = 0,    /* [N][N] c128: lower triangle of G (upper left untouched) */
     PINV_EXPORT_CHOL = 1,    /* [N][N] c128: lower triangle of L */
     PINV_EXPORT_GINV = 2,    /* [N][N] c128: G^-1, full */
-    PINV_EXPORT_RECON = 3    /* [N][C*M_k]: Recon = E^+, c128 (FP64 plans) or c64 (mixed) */
+    PINV_EXPORT_RECON = 3,   /* [N][C*M_k]: Recon = E^+, c128 (FP64 plans) or c64 (mixed) */
+    PINV_EXPORT_LINV = 4     /* [N][N] c128: W = L^-1 (mixed plans; UNSUPPORTED for FP64 plans) */
 } pinv_export_what;
 
 /*

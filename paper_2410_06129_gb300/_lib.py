@@ -21,7 +21,7 @@ FP64, MIXED_BF16X3, MIXED_BF16X6 = 0, 1, 2
 LAMBDA_ABS, LAMBDA_REL_MEAN_DIAG = 0, 1
 C64, C128 = 0, 1
 RECON_AUTO, RECON_NONE, RECON_STORE = -1, 0, 1
-EXPORT_GRAM, EXPORT_CHOL, EXPORT_GINV, EXPORT_RECON = 0, 1, 2, 3
+EXPORT_GRAM, EXPORT_CHOL, EXPORT_GINV, EXPORT_RECON, EXPORT_LINV = 0, 1, 2, 3, 4
 
 _STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "BUDGET", 4: "NOT_PD", 5: "NOT_BUILT",
                  6: "TIMEOUT", 7: "CUDA", 8: "INTERNAL", 9: "UNSUPPORTED"}
@@ -64,6 +64,7 @@ _VP = C.c_void_p
 SIGNATURES = {
     "pinv_version": (C.c_int, []),
     "pinv_kernel_launches": (C.c_ulonglong, []),
+    "pinv_tc_available": (C.c_int, []),
     "pinv_last_error": (C.c_char_p, []),
     "pinv_plan_create": (C.c_int, [C.POINTER(PlanDesc), _VP, C.POINTER(_VP)]),
     "pinv_build": (C.c_int, [_VP, _VP]),

@@ -57,7 +57,8 @@ struct pinv_plan {
     double2* G = nullptr;      // Gram, then L in place (lower)
     double2* Gkeep = nullptr;  // copy of G if requested
     double2* Dinv = nullptr;   // inverses of the diagonal blocks
-    double2* Ginv = nullptr;   // full G^-1
+    double2* Ginv = nullptr;   // full G^-1 (FP64 plans)
+    double2* W = nullptr;      // L^-1, lower (mixed plans)
     void* R = nullptr;         // Recon [N][M], c128 (FP64) or c64 (mixed)
     DevStatus* st = nullptr;
 
@@ -271,7 +272,8 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
     int64_t nblk = (p->N + 63) / 64;
     AL(p->G, sizeof(double2) * p->N * p->N, "G");
     AL(p->Dinv, sizeof(double2) * nblk * 64 * 64, "Dinv");
-    AL(p->Ginv, sizeof(double2) * p->N * p->N, "Ginv");
+    if (p->precision == PINV_FP64) AL(p->Ginv, sizeof(double2) * p->N * p->N, "Ginv");
+    else AL(p->W, sizeof(double2) * p->N * p->N, "W");
     int rm = d->recon_mode;
     if (rm == PINV_RECON_AUTO) {
         size_t rb = (size_t)p->N * p->M * (p->precision == PINV_FP64 ? 16 : 8);
@@ -319,19 +321,44 @@ pinv_status pinv_build(pinv_plan* p, void* stream) {
     else CK(launch_gram64(p->enc, p->lambda_abs, p->G, ld, s));
     if (p->Gkeep) CK(cudaMemcpyAsync(p->Gkeep, p->G, sizeof(double2) * N * N, cudaMemcpyDeviceToDevice, s));
     CK(cudaEventRecord(p->ev[2], s));
-    CK(launch_potrf64(p->G, N, ld, p->Dinv, p->st, s));
-    CK(launch_pivot_stats(p->G, N, ld, p->st, s));
-    CK(cudaEventRecord(p->ev[3], s));
-    double2* W = nullptr;
-    CK(cudaMallocAsync((void**)&W, sizeof(double2) * N * N, s));
-    CK(launch_trtri64(p->G, N, ld, p->Dinv, W, s));
-    CK(launch_lauum64(W, N, ld, p->Ginv, s));
-    CK(cudaFreeAsync(W, s));
-    CK(cudaEventRecord(p->ev[4], s));
-    if (p->recon) {
-        if (mixed) CK(launch_recon_tc(p->enc, p->Ginv, ld, slices, (float2*)p->R, p->st, s));
-        else CK(launch_recon64(p->enc, p->Ginv, ld, (double2*)p->R, s));
+    if (mixed) {
+        // FP64 diagonal panels, tensor-core panel solves / trailing updates,
+        // then the triangular inverse and G^-1 = W^H W on tensor cores
+        const int64_t nblk = (N + 63) / 64;
+        float2 *L32 = nullptr, *D32 = nullptr, *W32 = nullptr;
+        CK(cudaMallocAsync((void**)&L32, sizeof(float2) * N * N, s));
+        CK(cudaMallocAsync((void**)&D32, sizeof(float2) * nblk * 64 * 64, s));
+        CK(launch_potrf_tc(p->G, N, ld, p->Dinv, D32, L32, slices, p->st, s));
+        CK(launch_pivot_stats(p->G, N, ld, p->st, s));
+        CK(cudaEventRecord(p->ev[3], s));
+        CK(cudaMallocAsync((void**)&W32, sizeof(float2) * N * N, s));
+        CK(launch_trtri_tc(L32, N, D32, p->W, W32, slices, p->st, s));
+        CK(cudaFreeAsync(D32, s));
+        CK(cudaFreeAsync(L32, s));
+        CK(cudaEventRecord(p->ev[4], s));
+        if (p->recon) {
+            // Recon = W^H (W E^H) (Eq. 8) through an [N][M] c64 intermediate
+            float2* T = nullptr;
+            CK(cudaMallocAsync((void**)&T, sizeof(float2) * N * p->M, s));
+            CK(launch_recon_tc(p->enc, W32, T, slices, (float2*)p->R, p->st, s));
+            CK(cudaFreeAsync(T, s));
+        }
+        CK(cudaFreeAsync(W32, s));
+        CK(cudaEventRecord(p->ev[5], s));
+        p->built = true;
+        return PINV_OK;
+    } else {
+        CK(launch_potrf64(p->G, N, ld, p->Dinv, p->st, s));
+        CK(launch_pivot_stats(p->G, N, ld, p->st, s));
+        CK(cudaEventRecord(p->ev[3], s));
+        double2* W = nullptr;
+        CK(cudaMallocAsync((void**)&W, sizeof(double2) * N * N, s));
+        CK(launch_trtri64(p->G, N, ld, p->Dinv, W, s));
+        CK(launch_lauum64(W, N, ld, p->Ginv, s));
+        CK(cudaFreeAsync(W, s));
     }
+    CK(cudaEventRecord(p->ev[4], s));
+    if (p->recon) CK(launch_recon64(p->enc, p->Ginv, ld, (double2*)p->R, s));
     CK(cudaEventRecord(p->ev[5], s));
     p->built = true;
     return PINV_OK;
@@ -433,9 +460,11 @@ pinv_status pinv_apply(pinv_plan* p, const void* d_data, void* d_image, int64_t 
             CK(launch_apply32((const float2*)p->R, N, M, D32, F, p->x64, s));
             CK(launch_c64_to_c128(p->x64, X, F * N, s));
         } else {
+            // factor-only: x = W^H (W (E^H d)) with the mixed factor's inverse W
             if ((st = need_d128()) != PINV_OK) return st;
             CK(launch_adjoint64(p->enc, D, F, 0.0, nullptr, p->r128, s));
-            CK(launch_hemv64(p->Ginv, N, N, p->r128, F, nullptr, X, s));
+            CK(launch_trmv64(p->W, N, p->r128, F, p->u128, s));
+            CK(launch_trmv_h64(p->W, N, p->u128, F, nullptr, X, s));
         }
     }
     {
@@ -444,20 +473,33 @@ pinv_status pinv_apply(pinv_plan* p, const void* d_data, void* d_image, int64_t 
         // it to remove the explicit inverse's extra rounding (kappa(G) u).
         if (p->refine_iters > 0) {
             if ((st = need_d128()) != PINV_OK) return st;
+            // The stopping rule ||r|| / ||E^H d|| <= tol needs E^H d and a host
+            // read per step; with tol == 0 a fixed number of steps runs without either.
+            const bool stop_rule = p->refine_tol > 0.0;
             std::vector<double> h(2 * F);
-            CK(launch_adjoint64(p->enc, D, F, 0.0, nullptr, p->r128, s));  // b = E^H d
-            CK(launch_frame_norms(p->r128, F, N, p->norms + F, s));
+            if (stop_rule) {
+                CK(launch_adjoint64(p->enc, D, F, 0.0, nullptr, p->r128, s));  // b = E^H d
+                CK(launch_frame_norms(p->r128, F, N, p->norms + F, s));
+            }
             for (int it = 0; it < p->refine_iters; ++it) {
                 CK(launch_forward64(p->enc, X, F, D, p->u128, s));           // u = d - E x
                 CK(launch_adjoint64(p->enc, p->u128, F, p->lambda_abs, X, p->r128, s));
-                CK(launch_frame_norms(p->r128, F, N, p->norms, s));
-                CK(launch_hemv64(p->Ginv, N, N, p->r128, F, X, X, s));      // x += Ginv r
+                if (stop_rule) CK(launch_frame_norms(p->r128, F, N, p->norms, s));
+                if (mixed) {
+                    // x += W^H (W r) in FP64: never through an explicitly formed
+                    // low-precision G^-1, whose error the correction would amplify by kappa(G)
+                    CK(launch_trmv64(p->W, N, p->r128, F, p->u128, s));
+                    CK(launch_trmv_h64(p->W, N, p->u128, F, X, X, s));
+                } else {
+                    CK(launch_hemv64(p->Ginv, N, N, p->r128, F, X, X, s));  // x += Ginv r
+                }
+                p->last_refine_iters = it + 1;
+                if (!stop_rule) continue;
                 CK(cudaMemcpyAsync(h.data(), p->norms, sizeof(double) * 2 * F, cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
                 double worst = 0;
                 for (int64_t f = 0; f < F; ++f)
                     worst = std::max(worst, std::sqrt(h[f] / std::max(h[F + f], 1e-300)));
-                p->last_refine_iters = it + 1;
                 p->last_refine_resid = worst;
                 if (worst <= p->refine_tol) break;
             }
@@ -482,6 +524,10 @@ pinv_status pinv_plan_export(const pinv_plan* p, int what, void* dst, size_t byt
             break;
         case PINV_EXPORT_CHOL: src = p->G; break;
         case PINV_EXPORT_GINV: src = p->Ginv; break;
+        case PINV_EXPORT_LINV:
+            if (!p->W) return fail(PINV_ERR_UNSUPPORTED, "only mixed-precision plans keep L^-1");
+            src = p->W;
+            break;
         case PINV_EXPORT_RECON:
             if (!p->recon) return fail(PINV_ERR_UNSUPPORTED, "factor-only plan has no Recon");
             src = p->R;
@@ -492,6 +538,9 @@ pinv_status pinv_plan_export(const pinv_plan* p, int what, void* dst, size_t byt
     if (bytes < need) return fail(PINV_ERR_INVALID_ARG, "destination too small");
     if (what == PINV_EXPORT_CHOL) {
         CK(launch_copy_lower(p->G, p->N, p->N, (double2*)dst, s));
+    } else if (what == PINV_EXPORT_GINV && !p->Ginv) {
+        // mixed plans keep W = L^-1; G^-1 = W^H W is formed in FP64 on request
+        CK(launch_lauum64(p->W, p->N, p->N, (double2*)dst, s));
     } else {
         CK(cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToDevice, s));
     }

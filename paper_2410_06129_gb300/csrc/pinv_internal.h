@@ -104,6 +104,10 @@ cudaError_t launch_trtri64(const double2* L, int64_t N, int64_t ld, const double
                            double2* W, cudaStream_t s);
 // Ginv = W^H W, full Hermitian matrix.
 cudaError_t launch_lauum64(const double2* W, int64_t N, int64_t ld, double2* Ginv, cudaStream_t s);
+// One 64x64 diagonal block of the blocked Cholesky (FP64, in shared memory):
+// factor in place, check pivots, write the block inverse (and an FP32 copy).
+cudaError_t launch_potrf_diag(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv,
+                              float2* Dinv32, DevStatus* st, cudaStream_t s);
 // Recon[n][(c,m)] = sum_n' Ginv[n][n'] conj(E[(c,m)][n']), FP64.
 cudaError_t launch_recon64(const EncodeDev& e, const double2* Ginv, int64_t ld, double2* R,
                            cudaStream_t s);
@@ -138,12 +142,25 @@ cudaError_t launch_zaxpy(double2* X, const double2* Y, int64_t n, cudaStream_t s
 // Gram in split BF16 on tcgen05 tensor cores; result written as FP64 lower tiles.
 cudaError_t launch_gram_tc(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld,
                            DevStatus* st, cudaStream_t s);
-// Recon in split BF16 on tcgen05: R[n][(c,m)] = sum_n' Ginv[n][n'] conj(E[(c,m)][n']), c64 out.
-cudaError_t launch_recon_tc(const EncodeDev& e, const double2* Ginv, int64_t ld, int slices,
-                            float2* R, DevStatus* st, cudaStream_t s);
+// Recon = W^H (W E^H) in split BF16 on tcgen05 (W = L^-1 in FP32, T = W E^H
+// scratch [N][M] c64), c64 out.
+cudaError_t launch_recon_tc(const EncodeDev& e, const float2* W32, float2* T, int slices, float2* R,
+                            DevStatus* st, cudaStream_t s);
+// Y[f] = W X[f] (lower W), and Y[f] = Yadd[f] + W^H X[f], FP64.
+cudaError_t launch_trmv64(const double2* W, int64_t N, const double2* X, int64_t F, double2* Y,
+                          cudaStream_t s);
+cudaError_t launch_trmv_h64(const double2* W, int64_t N, const double2* X, int64_t F, const double2* Yadd,
+                            double2* Y, cudaStream_t s);
 // X[f][n] = sum_j R[n][j] D[f][j], c64 (R c64 [N][M], D c64 [F][M]).
 cudaError_t launch_apply32(const float2* R, int64_t N, int64_t M, const float2* D, int64_t F,
                            float2* X, cudaStream_t s);
+// Blocked Cholesky with FP64 diagonal panels and tensor-core panel solves and
+// trailing updates; L32 receives an FP32 copy of L ([N][N], lower part).
+cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, float2* Dinv32, float2* L32,
+                            int slices, DevStatus* st, cudaStream_t s);
+// W = L^-1 (FP64 storage, tensor-core updates) and its FP32 copy W32.
+cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, double2* W, float2* W32,
+                            int slices, DevStatus* st, cudaStream_t s);
 bool tc_available();
 
 }  // namespace pinv

@@ -1,0 +1,386 @@
+// Split-BF16 complex contraction engine on the 5th-generation tensor cores.
+//
+// A CTA computes a 128 x 128 tile of a complex product C[i][j] = sum_k a(i,k) b(k,j).
+//
+// Real embedding. Each complex operand value is split into S bf16 slices
+// (v = v0 + v1 [+ v2], each slice the bf16 rounding of what the previous ones
+// left). Per 16-wide complex k chunk the A tile holds rows [Ar | Ai] and the B
+// tile holds, for every output column j, the rows [Br | -Bi] (real output) and
+// [Bi | Br] (imaginary output). One M = 128, N = 256, K = 16 MMA pair therefore
+// produces Cr and Ci side by side:
+//     Cr = Ar Br - Ai Bi,   Ci = Ar Bi + Ai Br,
+// with 4 real MACs per complex MAC and no wasted products. Slice pairs kept:
+// (0,0) (0,1) (1,0) for two slices; plus (0,2) (2,0) (1,1) for three.
+//
+// Accumulation. The tensor core's FP32 accumulation truncates (measured: a
+// bias that grows linearly with the number of accumulation steps). The MMAs
+// therefore accumulate at most DRAIN stages into a 256-column TMEM buffer; the
+// producer warps then add the buffer into a running total held in the other
+// 256 TMEM columns (tcgen05.ld, round-to-nearest FP32 add, tcgen05.st) while
+// the MMA issuer waits. The relative bias stays near 3 * DRAIN * 2^-24
+// regardless of K.
+//
+// Roles. 8 producer warps generate or load operand values (problem functors
+// a8 / b8 return 8 consecutive k for one row or column), split them and write
+// the canonical K-major no-swizzle layout into a ring of shared-memory stages.
+// One thread issues tcgen05.mma and commits stages back to the producers and
+// full buffers to the drains. The producer warps also run the epilogue from
+// the TMEM total. Every mbarrier wait is bounded by a clock64
+// limit: on expiry the CTA raises an abort flag, stops, waits (bounded) for its
+// issued MMAs, frees TMEM and records the failure in the plan's status word.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "pinv_internal.h"
+
+namespace pinv {
+namespace tc {
+
+constexpr int BM = 128;          // complex rows per tile (MMA M)
+constexpr int BN = 128;          // complex columns per tile (MMA N = 2 * BN)
+constexpr int KC = 16;           // complex k per stage
+constexpr int NPW = 8;           // producer / drain / epilogue warps
+constexpr int NTHREADS = (NPW + 1) * 32;
+constexpr int DRAIN = 8;         // stages per TMEM accumulation group
+constexpr long long WAIT_LIMIT = 4000000000LL;  // clock64 cycles, about 2 s
+
+constexpr int ROWB = 2 * KC * 2;                 // bytes per embedded row: K' = 32 bf16
+constexpr int A_SL = BM * ROWB;                  // 8 KiB
+constexpr int B_SL = 2 * BN * ROWB;              // 16 KiB
+constexpr int SLICE = A_SL + B_SL;               // 24 KiB per slice per stage
+
+template <int S>
+struct Cfg {
+    static constexpr int STAGES = S == 3 ? 3 : 4;
+    static constexpr int STAGE_BYTES = S * SLICE;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+    static constexpr int NPAIRS = S == 3 ? 6 : 3;
+};
+static_assert(DRAIN >= 4, "drain group must outlast the stage ring");
+
+// instruction descriptor, kind::f16: D f32, A/B bf16, K-major, N = 256, M = 128
+constexpr uint32_t IDESC =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * BN) >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+// slice pairs in decreasing weight: (0,0) (0,1) (1,0) (0,2) (2,0) (1,1)
+__host__ __device__ constexpr int pair_a(int q) { return q == 2 ? 1 : q == 4 ? 2 : q == 5 ? 1 : 0; }
+__host__ __device__ constexpr int pair_b(int q) { return q == 1 ? 1 : q == 3 ? 2 : q == 5 ? 1 : 0; }
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ inline void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if the limit expired or another role raised abort.
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (abort_flag && *abort_flag) return false;
+        if (clock64() - t0 > WAIT_LIMIT) {
+            if (abort_flag) *abort_flag = 1;
+            return false;
+        }
+    }
+}
+__device__ inline void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ inline void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ inline void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ inline void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// shared-memory matrix descriptor: canonical K-major layout without swizzle
+__device__ inline uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    return d;                // base offset 0, layout type 0 (no swizzle)
+}
+
+__device__ inline void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ inline void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ inline void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ inline void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// byte offset of (row r, 8-wide k' group g in 0..3) in a [R][32] K-major no-swizzle tile
+__device__ inline uint32_t koff(int r, int g) { return (uint32_t)((r >> 3) * 512 + g * 128 + (r & 7) * 16); }
+
+// split 8 floats into S bf16 slices, packed 2 per word: w[s][0..3]
+template <int S>
+__device__ inline void split8(float (&x)[8], uint32_t (&w)[S][4]) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * t], x[2 * t + 1]);
+            if (s + 1 < S) {
+                const float2 back = __bfloat1622float2(h);
+                x[2 * t] -= back.x;
+                x[2 * t + 1] -= back.y;
+            }
+            w[s][t] = *reinterpret_cast<uint32_t*>(&h);
+        }
+    }
+}
+
+template <int S>
+__device__ inline void store_slices(uint8_t* p, const uint32_t (&w)[S][4], uint32_t flip) {
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+        *reinterpret_cast<uint4*>(p + s * SLICE) =
+            make_uint4(w[s][0] ^ flip, w[s][1] ^ flip, w[s][2] ^ flip, w[s][3] ^ flip);
+}
+
+__device__ inline void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ inline void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+constexpr uint32_t TOTAL_COL = 2 * BN;  // running total after the MMA buffer
+
+// Add this warp's part of the MMA buffer (32 rows x 64 complex columns: real
+// parts at col0, imaginary at col0 + BN) into the running total.
+__device__ inline void drain_to_total(uint32_t taddr_row, bool first) {
+#pragma unroll
+    for (int part = 0; part < 8; ++part) {
+        const uint32_t col = (uint32_t)((part & 4) ? BN : 0) + 16u * (part & 3);
+        uint32_t b[16], t[16];
+        tmem_ld16(taddr_row + col, b);
+        if (!first) tmem_ld16(taddr_row + TOTAL_COL + col, t);
+        tmem_wait_ld();
+        if (!first) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) b[i] = __float_as_uint(__uint_as_float(b[i]) + __uint_as_float(t[i]));
+        }
+        tmem_st16(taddr_row + TOTAL_COL + col, b);
+    }
+    tmem_wait_st();
+}
+
+template <int S, class P>
+__global__ void __launch_bounds__(NTHREADS, 1) k_tc(P p, DevStatus* st, int site) {
+    using CF = Cfg<S>;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full_bar[CF::STAGES], empty_bar[CF::STAGES];
+    __shared__ uint64_t tfull, tempty, done_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_flag;
+
+    int64_t i0, j0, kb, ke;
+    if (!p.tile(i0, j0, kb, ke)) return;  // uniform per CTA
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = (int)((ke - kb + KC - 1) / KC);
+    const int ngroups = (nk + DRAIN - 1) / DRAIN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CF::STAGES; ++s) {
+            mbar_init(&full_bar[s], NPW * 32);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&tfull, 1);
+        mbar_init(&tempty, NPW * 32);
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == NPW) tmem_alloc(&tmem_base_sh, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp < NPW) {
+        // ---------------- producers, drains, epilogue
+        const int q = warp & 3, h = warp >> 2;
+        const uint32_t taddr_row = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(64 * h);
+        int drained = 0;
+        bool ok = true;
+        auto drain = [&](int g) -> bool {
+            if (!mbar_wait(&tfull, (uint32_t)g & 1u, &abort_flag)) return false;
+            tc_fence_after();
+            drain_to_total(taddr_row, g == 0);
+            tc_fence_before();
+            mbar_arrive(&tempty);
+            return true;
+        };
+        const int ua = threadIdx.x;  // A unit: row ua & 127, k group ua >> 7
+        const int ubr = threadIdx.x & (BN - 1), ubg = threadIdx.x >> 7;
+        for (int kt = 0; kt < nk && ok; ++kt) {
+            // the MMA cannot start group g + 1 until group g is drained; drain it
+            // before the ring can only advance past that point
+            while (drained < ngroups && (drained + 1) * DRAIN + CF::STAGES - 1 <= kt) {
+                if (!(ok = drain(drained))) break;
+                ++drained;
+            }
+            if (!ok) break;
+            const int s = kt % CF::STAGES;
+            const uint32_t ph = (uint32_t)(kt / CF::STAGES) & 1u;
+            if (kt >= CF::STAGES && !(ok = mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag))) break;
+            uint8_t* base = smem + s * CF::STAGE_BYTES;
+            const int64_t k0 = kb + (int64_t)kt * KC;
+            {
+                float2 v[8];
+                const int r = ua & (BM - 1), g = ua >> 7;
+                p.a8(i0 + r, k0 + 8 * g, ke, v);
+                float re[8], im[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) { re[t] = v[t].x; im[t] = v[t].y; }
+                uint32_t wr[S][4], wi[S][4];
+                split8<S>(re, wr);
+                split8<S>(im, wi);
+                store_slices<S>(base + koff(r, g), wr, 0u);
+                store_slices<S>(base + koff(r, g + 2), wi, 0u);
+            }
+            {
+                float2 v[8];
+                p.b8(j0 + ubr, k0 + 8 * ubg, ke, v);
+                float re[8], im[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) { re[t] = v[t].x; im[t] = v[t].y; }
+                uint32_t wr[S][4], wi[S][4];
+                split8<S>(re, wr);
+                split8<S>(im, wi);
+                uint8_t* bb = base + A_SL;
+                store_slices<S>(bb + koff(ubr, ubg), wr, 0u);                 // [Br | -Bi]
+                store_slices<S>(bb + koff(ubr, ubg + 2), wi, 0x80008000u);
+                store_slices<S>(bb + koff(BN + ubr, ubg), wi, 0u);            // [Bi |  Br]
+                store_slices<S>(bb + koff(BN + ubr, ubg + 2), wr, 0u);
+            }
+            fence_proxy_async();
+            mbar_arrive(&full_bar[s]);
+        }
+        while (ok && drained < ngroups) {
+            ok = drain(drained);
+            ++drained;
+        }
+        if (ok && !abort_flag) {
+            tc_fence_after();
+            const int64_t gi = i0 + q * 32 + lane;
+#pragma unroll 1
+            for (int part = 0; part < 4; ++part) {
+                uint32_t cr[16], ci[16];
+                if (nk > 0) {
+                    tmem_ld16(taddr_row + TOTAL_COL + 16 * part, cr);
+                    tmem_ld16(taddr_row + TOTAL_COL + BN + 16 * part, ci);
+                    tmem_wait_ld();
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) cr[t] = ci[t] = 0u;
+                }
+                if (p.row_ok(gi)) {
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        const int64_t gj = j0 + 64 * h + 16 * part + t;
+                        if (p.col_ok(gj))
+                            p.store(gi, gj, make_float2(__uint_as_float(cr[t]), __uint_as_float(ci[t])));
+                    }
+                }
+            }
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issuer
+        for (int kt = 0; kt < nk; ++kt) {
+            const int g = kt / DRAIN;
+            const bool first = (kt % DRAIN) == 0;
+            if (first && g >= 1 && !mbar_wait(&tempty, (uint32_t)(g - 1) & 1u, &abort_flag)) break;
+            const int s = kt % CF::STAGES;
+            const uint32_t ph = (uint32_t)(kt / CF::STAGES) & 1u;
+            if (!mbar_wait(&full_bar[s], ph, &abort_flag)) break;
+            tc_fence_after();
+            const uint32_t sbase = smem_u32(smem + s * CF::STAGE_BYTES);
+#pragma unroll
+            for (int pq = 0; pq < CF::NPAIRS; ++pq) {
+                const uint32_t a = sbase + pair_a(pq) * SLICE;
+                const uint32_t bsl = sbase + pair_b(pq) * SLICE + A_SL;
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const uint64_t da = sdesc(a + kk * 256, 128, 512);
+                    const uint64_t db = sdesc(bsl + kk * 256, 128, 512);
+                    mma_bf16(tmem, da, db, IDESC, (first && pq == 0 && kk == 0) ? 0u : 1u);
+                }
+            }
+            mma_commit(&empty_bar[s]);
+            if ((kt % DRAIN) == DRAIN - 1 || kt == nk - 1) mma_commit(&tfull);
+        }
+        mma_commit(&done_bar);  // completes when every MMA issued above has finished
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == NPW) {
+        mbar_wait(&done_bar, 0, nullptr);  // no MMA may still write TMEM when it is released
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+    if (threadIdx.x == 0 && abort_flag) atomicMax(&st->timeout_site, site);
+}
+
+template <int S, class P>
+static cudaError_t launch(const P& p, dim3 grid, DevStatus* st, int site, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc<S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<S>::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+    k_tc<S, P><<<grid, NTHREADS, Cfg<S>::SMEM, s>>>(p, st, site);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tc
+}  // namespace pinv

@@ -1,20 +1,476 @@
-// Mixed-precision tensor-core kernels (placeholder until the tcgen05 path lands).
-#include "pinv_internal.h"
+// Mixed-precision stages of the build on the tcgen05 split-BF16 engine
+// (tc_engine.cuh): Gram, blocked-Cholesky panel solves and trailing updates,
+// the triangular inverse and Recon = (L^-1)^H L^-1 E^H (Eq. 8), plus the c64
+// SIMT apply used when frames are few.
+//
+// Every problem supplies tile(), a8()/b8() (8 consecutive k of one row of A or
+// one column of B, zero outside the problem), row_ok()/col_ok() and store().
+#include <algorithm>
+
+#include "tc_engine.cuh"
 
 namespace pinv {
+namespace tc {
 
-bool tc_available() { return false; }
+// ------------------------------------------------------------------ FP32 helpers
+__device__ inline float2 cmulf(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ inline float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
-cudaError_t launch_gram_tc(const EncodeDev&, double, int, double2*, int64_t, DevStatus*, cudaStream_t) {
-    return cudaErrorNotSupported;
+// A[m][n] = exp(-i2pi(k_m . r_n + df_n t_m)) from the single-precision tables
+__device__ inline float2 gen_a32(const EncodeDev& e, int64_t m, int64_t n) {
+    const int* g = e.vox_ijk + 3 * n;
+    float2 v = e.ex32[m * e.nx + g[0]];
+    if (e.ny > 1) v = cmulf(v, e.ey32[m * e.ny + g[1]]);
+    if (e.nz > 1) v = cmulf(v, e.ez32[m * e.nz + g[2]]);
+    if (e.b0tab32) v = cmulf(v, e.b0tab32[(int64_t)e.tidx[m] * e.N + n]);
+    return v;
 }
-cudaError_t launch_recon_tc(const EncodeDev&, const double2*, int64_t, int, float2*, DevStatus*,
-                            cudaStream_t) {
-    return cudaErrorNotSupported;
+
+// conj(E[(c,m)][n]) for 8 consecutive voxels n (zero past ke or outside M)
+__device__ inline void gen_eh8(const EncodeDev& e, int64_t j, int64_t n0, int64_t ke, float2 (&v)[8]) {
+    const int64_t M = e.Mk * e.C;
+    const int c = (int)(j / e.Mk);
+    const int64_t m = j - (int64_t)c * e.Mk;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int64_t n = n0 + t;
+        if (j < M && n < ke) {
+            float2 a = gen_a32(e, m, n);
+            if (e.coils32) a = cmulf(a, e.coils32[(int64_t)c * e.N + n]);
+            v[t] = conjf2(a);
+        } else {
+            v[t] = make_float2(0.f, 0.f);
+        }
+    }
 }
-cudaError_t launch_apply32(const float2*, int64_t, int64_t, const float2*, int64_t, float2*,
-                           cudaStream_t) {
-    return cudaErrorNotSupported;
+
+// 8 consecutive FP32 complex values p[0..7] (zero past `avail`)
+__device__ inline void load8f(const float2* p, int avail, float2 (&v)[8]) {
+    if (avail >= 8 && (((uintptr_t)p) & 15) == 0) {
+        const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float4 w = __ldg(q + t);
+            v[2 * t] = make_float2(w.x, w.y);
+            v[2 * t + 1] = make_float2(w.z, w.w);
+        }
+        return;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = t < avail ? p[t] : make_float2(0.f, 0.f);
+}
+
+// 8 values down a column: p[0], p[ld], ..., p[7 ld] (zero past `avail`)
+__device__ inline void load8col(const float2* p, int64_t ld, int avail, float2 (&v)[8]) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = t < avail ? __ldg(p + t * ld) : make_float2(0.f, 0.f);
+}
+
+// ------------------------------------------------------------------ Gram (Eq. 6, Eq. 11)
+// G[i][j] = (sum_m conj(A[m][i]) A[m][j]) * (sum_c conj(s_c(i)) s_c(j)) + lam delta_ij, lower part
+struct GramTC {
+    EncodeDev e;
+    double lam;
+    double2* G;
+    int64_t ld;
+    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = (int64_t)blockIdx.y * BM;
+        j0 = (int64_t)blockIdx.x * BN;
+        kb = 0;
+        ke = e.Mk;
+        return j0 <= i0 + BM - 1;  // tile touches the lower triangle
+    }
+    __device__ void a8(int64_t i, int64_t k0, int64_t ke, float2 (&v)[8]) const {
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            v[t] = (i < e.N && k0 + t < ke) ? conjf2(gen_a32(e, k0 + t, i)) : make_float2(0.f, 0.f);
+    }
+    __device__ void b8(int64_t j, int64_t k0, int64_t ke, float2 (&v)[8]) const {
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            v[t] = (j < e.N && k0 + t < ke) ? gen_a32(e, k0 + t, j) : make_float2(0.f, 0.f);
+    }
+    __device__ bool row_ok(int64_t i) const { return i < e.N; }
+    __device__ bool col_ok(int64_t j) const { return j < e.N; }
+    __device__ void store(int64_t i, int64_t j, float2 v) const {
+        if (j > i) return;
+        if (i == j) {
+            // every encoding element is a unit phasor, so (A^H A)_ii = M_k exactly;
+            // the diagonal is written in FP64 rather than from the accumulator
+            double s = 1.0;
+            if (e.coils) {
+                s = 0.0;
+                for (int c = 0; c < e.C; ++c) {
+                    const double2 a = e.coils[(int64_t)c * e.N + i];
+                    s += a.x * a.x + a.y * a.y;
+                }
+            }
+            G[i * ld + i] = make_double2((double)e.Mk * s + lam, 0.0);
+            return;
+        }
+        if (e.coils32) {
+            float2 sc = make_float2(0.f, 0.f);
+            for (int c = 0; c < e.C; ++c) {
+                const float2 a = conjf2(e.coils32[(int64_t)c * e.N + i]);
+                const float2 b = e.coils32[(int64_t)c * e.N + j];
+                sc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, sc.x));
+                sc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, sc.y));
+            }
+            v = cmulf(v, sc);
+        }
+        G[i * ld + j] = make_double2((double)v.x, (double)v.y);
+    }
+};
+
+// ------------------------------------------------------------------ blocked Cholesky
+// Panel solve L[i][k0+j] = sum_k G[i][k0+k] conj(Dinv[j][k]) below the diagonal
+// block. P is the FP32 copy of the panel (row i at P + i * ldp); the result
+// goes to G (FP64) and back to P for the trailing update.
+struct TrsmTC {
+    float2* P;
+    int64_t ldp;
+    const float2* Dinv32;  // [64][64]
+    double2* G;
+    int64_t ld, N, k0, nbk;
+    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = k0 + nbk + (int64_t)blockIdx.y * BM;
+        j0 = 0;
+        kb = 0;
+        ke = nbk;
+        return i0 < N;
+    }
+    __device__ void a8(int64_t i, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(P + i * ldp + k, i < N ? (int)(ke - k) : 0, v);
+    }
+    __device__ void b8(int64_t j, int64_t k, int64_t ke, float2 (&v)[8]) const {
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            v[t] = (j < nbk && k + t < ke) ? conjf2(Dinv32[j * 64 + k + t]) : make_float2(0.f, 0.f);
+    }
+    __device__ bool row_ok(int64_t i) const { return i < N; }
+    __device__ bool col_ok(int64_t j) const { return j < nbk; }
+    __device__ void store(int64_t i, int64_t j, float2 v) const {
+        G[i * ld + k0 + j] = make_double2(v.x, v.y);
+        P[i * ldp + j] = v;
+    }
+};
+
+// Trailing update G[i][j] -= sum_k P[i][k] conj(P[j][k]) on lower tiles (i, j >= t0).
+struct HerkTC {
+    const float2* P;
+    int64_t ldp;
+    double2* G;
+    int64_t ld, N, nbk, t0;
+    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = t0 + (int64_t)blockIdx.y * BM;
+        j0 = t0 + (int64_t)blockIdx.x * BN;
+        kb = 0;
+        ke = nbk;
+        return i0 < N && j0 < N && j0 <= i0 + BM - 1;
+    }
+    __device__ void a8(int64_t i, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(P + i * ldp + k, i < N ? (int)(ke - k) : 0, v);
+    }
+    __device__ void b8(int64_t j, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(P + j * ldp + k, j < N ? (int)(ke - k) : 0, v);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t].y = -v[t].y;
+    }
+    __device__ bool row_ok(int64_t i) const { return i < N; }
+    __device__ bool col_ok(int64_t j) const { return j < N; }
+    __device__ void store(int64_t i, int64_t j, float2 v) const {
+        if (j > i) return;
+        const double2 g = G[i * ld + j];
+        G[i * ld + j] = make_double2(g.x - (double)v.x, g.y - (double)v.y);
+    }
+};
+
+// ------------------------------------------------------------------ W = L^-1
+// W[k0+i][j] = sum_k Dinv[i][k] W[k0+k][j] for j < k0 + nbk (in place on a block row).
+struct TrtriDiagTC {
+    const float2* Dinv32;
+    double2* W;
+    int64_t ld, N, k0, nbk;
+    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = 0;
+        j0 = (int64_t)blockIdx.x * BN;
+        kb = 0;
+        ke = nbk;
+        return true;
+    }
+    __device__ void a8(int64_t i, int64_t k, int64_t ke, float2 (&v)[8]) const {
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            v[t] = (i < nbk && k + t < ke) ? Dinv32[i * 64 + k + t] : make_float2(0.f, 0.f);
+    }
+    __device__ void b8(int64_t j, int64_t k, int64_t ke, float2 (&v)[8]) const {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (j < k0 + nbk && k + t < ke) {
+                const double2 w = W[(k0 + k + t) * ld + j];
+                v[t] = make_float2((float)w.x, (float)w.y);
+            } else {
+                v[t] = make_float2(0.f, 0.f);
+            }
+        }
+    }
+    __device__ bool row_ok(int64_t i) const { return i < nbk; }
+    __device__ bool col_ok(int64_t j) const { return j < k0 + nbk; }
+    __device__ void store(int64_t i, int64_t j, float2 v) const {
+        W[(k0 + i) * ld + j] = make_double2(v.x, v.y);
+    }
+};
+
+// W[i][j] -= sum_k L[i][k0+k] W[k0+k][j] for i >= k0 + nbk, j < k0 + nbk.
+struct TrtriUpdTC {
+    const float2* L32;
+    int64_t ldl;
+    double2* W;
+    int64_t ld, N, k0, nbk;
+    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = k0 + nbk + (int64_t)blockIdx.y * BM;
+        j0 = (int64_t)blockIdx.x * BN;
+        kb = 0;
+        ke = nbk;
+        return i0 < N;
+    }
+    __device__ void a8(int64_t i, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(L32 + i * ldl + k0 + k, i < N ? (int)(ke - k) : 0, v);
+    }
+    __device__ void b8(int64_t j, int64_t k, int64_t ke, float2 (&v)[8]) const {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (j < k0 + nbk && k + t < ke) {
+                const double2 w = W[(k0 + k + t) * ld + j];
+                v[t] = make_float2((float)w.x, (float)w.y);
+            } else {
+                v[t] = make_float2(0.f, 0.f);
+            }
+        }
+    }
+    __device__ bool row_ok(int64_t i) const { return i < N; }
+    __device__ bool col_ok(int64_t j) const { return j < k0 + nbk; }
+    __device__ void store(int64_t i, int64_t j, float2 v) const {
+        const double2 w = W[i * ld + j];
+        W[i * ld + j] = make_double2(w.x - (double)v.x, w.y - (double)v.y);
+    }
+};
+
+// ------------------------------------------------------------------ Recon = W^H (W E^H)
+// T[n][j] = sum_{k <= n} W[n][k] conj(E[j][k])     (j = c * M_k + m)
+struct ReconStep1TC {
+    EncodeDev e;
+    const float2* W32;
+    float2* T;
+    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        j0 = (int64_t)blockIdx.x * BN;
+        i0 = (int64_t)blockIdx.y * BM;
+        kb = 0;
+        ke = i0 + BM < e.N ? i0 + BM : e.N;  // W is lower triangular
+        return true;
+    }
+    __device__ void a8(int64_t i, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(W32 + i * e.N + k, i < e.N ? (int)(ke - k) : 0, v);
+    }
+    __device__ void b8(int64_t j, int64_t k, int64_t ke, float2 (&v)[8]) const { gen_eh8(e, j, k, ke, v); }
+    __device__ bool row_ok(int64_t i) const { return i < e.N; }
+    __device__ bool col_ok(int64_t j) const { return j < e.Mk * e.C; }
+    __device__ void store(int64_t i, int64_t j, float2 v) const { T[i * (e.Mk * e.C) + j] = v; }
+};
+
+// R[n][j] = sum_{k >= n} conj(W[k][n]) T[k][j]; row tiles vary fastest so the
+// CTAs in flight share one column panel of T in L2.
+struct ReconStep2TC {
+    const float2* W32;
+    const float2* T;
+    float2* R;
+    int64_t N, M;
+    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = (int64_t)blockIdx.x * BM;
+        j0 = (int64_t)blockIdx.y * BN;
+        kb = i0;  // W is lower triangular
+        ke = N;
+        return true;
+    }
+    __device__ void a8(int64_t i, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8col(W32 + k * N + i, N, i < N ? (int)(ke - k) : 0, v);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t].y = -v[t].y;
+    }
+    __device__ void b8(int64_t j, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8col(T + k * M + j, M, j < M ? (int)(ke - k) : 0, v);
+    }
+    __device__ bool row_ok(int64_t i) const { return i < N; }
+    __device__ bool col_ok(int64_t j) const { return j < M; }
+    __device__ void store(int64_t i, int64_t j, float2 v) const { R[i * M + j] = v; }
+};
+
+}  // namespace tc
+
+// FP32 copy of a block of an FP64 matrix: dst[r][c] = src[r][c] for r in [r0, r1), c in [c0, c1)
+__global__ void k_block_to_f32(const double2* __restrict__ src, int64_t ld, int64_t r0, int64_t r1, int64_t c0,
+                               int64_t c1, float2* __restrict__ dst, int64_t ldd) {
+    const int64_t w = c1 - c0;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (r1 - r0) * w) return;
+    const int64_t r = r0 + idx / w, c = c0 + idx % w;
+    const double2 v = src[r * ld + c];
+    dst[r * ldd + c] = make_float2((float)v.x, (float)v.y);
+}
+
+static cudaError_t block_to_f32(const double2* src, int64_t ld, int64_t r0, int64_t r1, int64_t c0, int64_t c1,
+                                float2* dst, int64_t ldd, cudaStream_t s) {
+    const int64_t n = (r1 - r0) * (c1 - c0);
+    if (n <= 0) return cudaSuccess;
+    k_block_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, ld, r0, r1, c0, c1, dst, ldd);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <class P>
+static cudaError_t run(const P& p, dim3 grid, int slices, DevStatus* st, int site, cudaStream_t s) {
+    return slices == 3 ? tc::launch<3>(p, grid, st, site, s) : tc::launch<2>(p, grid, st, site, s);
+}
+
+static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+cudaError_t launch_gram_tc(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld,
+                           DevStatus* st, cudaStream_t s) {
+    tc::GramTC p{e, lambda, G, ld};
+    return run(p, dim3(cdiv(e.N, tc::BN), cdiv(e.N, tc::BM)), slices, st, 1, s);
+}
+
+cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, float2* Dinv32, float2* L32,
+                            int slices, DevStatus* st, cudaStream_t s) {
+    constexpr int NBK = 64;
+    for (int64_t k0 = 0; k0 < N; k0 += NBK) {
+        const int64_t nbk = std::min<int64_t>(NBK, N - k0);
+        const int64_t kb = k0 / NBK;
+        cudaError_t e = launch_potrf_diag(G, ld, N, k0, Dinv + kb * NBK * NBK, Dinv32 + kb * NBK * NBK, st, s);
+        if (e != cudaSuccess) return e;
+        e = block_to_f32(G, ld, k0, N, k0, k0 + nbk, L32, N, s);
+        if (e != cudaSuccess) return e;
+        const int64_t rest = N - k0 - nbk;
+        if (rest <= 0) break;
+        tc::TrsmTC tp{L32 + k0, N, Dinv32 + kb * NBK * NBK, G, ld, N, k0, nbk};
+        if ((e = run(tp, dim3(1, cdiv(rest, tc::BM)), slices, st, 3, s)) != cudaSuccess) return e;
+        tc::HerkTC hp{L32 + k0, N, G, ld, N, nbk, k0 + nbk};
+        if ((e = run(hp, dim3(cdiv(rest, tc::BN), cdiv(rest, tc::BM)), slices, st, 4, s)) != cudaSuccess)
+            return e;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, double2* W, float2* W32,
+                            int slices, DevStatus* st, cudaStream_t s) {
+    constexpr int NBK = 64;
+    cudaError_t e = launch_fill_identity(W, N, N, s);
+    if (e != cudaSuccess) return e;
+    for (int64_t k0 = 0; k0 < N; k0 += NBK) {
+        const int64_t nbk = std::min<int64_t>(NBK, N - k0);
+        const int64_t ncol = k0 + nbk;
+        tc::TrtriDiagTC dp{Dinv32 + (k0 / NBK) * NBK * NBK, W, N, N, k0, nbk};
+        if ((e = run(dp, dim3(cdiv(ncol, tc::BN), 1), slices, st, 5, s)) != cudaSuccess) return e;
+        const int64_t rest = N - ncol;
+        if (rest <= 0) break;
+        tc::TrtriUpdTC up{L32, N, W, N, N, k0, nbk};
+        if ((e = run(up, dim3(cdiv(ncol, tc::BN), cdiv(rest, tc::BM)), slices, st, 6, s)) != cudaSuccess)
+            return e;
+    }
+    return launch_to_f32(W, W32, N * N, s);
+}
+
+cudaError_t launch_recon_tc(const EncodeDev& e, const float2* W32, float2* T, int slices, float2* R,
+                            DevStatus* st, cudaStream_t s) {
+    const int64_t M = e.Mk * e.C;
+    tc::ReconStep1TC p1{e, W32, T};
+    cudaError_t err = run(p1, dim3(cdiv(M, tc::BN), cdiv(e.N, tc::BM)), slices, st, 2, s);
+    if (err != cudaSuccess) return err;
+    tc::ReconStep2TC p2{W32, T, R, e.N, M};
+    return run(p2, dim3(cdiv(e.N, tc::BM), cdiv(M, tc::BN)), slices, st, 8, s);
+}
+
+bool tc_available() {
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) return false;
+    return major == 10 && minor == 3;
+}
+
+// ------------------------------------------------------------------ FP32 SIMT apply
+// X[f][n] = sum_j R[n][j] D[f][j] for c64 Recon and data (frames along the tile's columns).
+template <int BMv, int BNv, int TM, int TN, int BKv>
+__global__ void __launch_bounds__(256) k_apply32(const float2* __restrict__ R, int64_t N, int64_t M,
+                                                 const float2* __restrict__ D, int64_t F, float2* __restrict__ X) {
+    constexpr int TX = BNv / TN, TY = BMv / TM;
+    static_assert(TX * TY == 256, "256 threads");
+    __shared__ float2 As[BKv][BMv + 1];
+    __shared__ float2 Bs[BKv][BNv + 1];
+    const int64_t i0 = (int64_t)blockIdx.y * BMv, j0 = (int64_t)blockIdx.x * BNv;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    float2 acc[TM][TN];
+#pragma unroll
+    for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[r][c] = make_float2(0.f, 0.f);
+    for (int64_t k0 = 0; k0 < M; k0 += BKv) {
+        for (int e = tid; e < BKv * BMv; e += 256) {
+            const int kk = e % BKv, ii = e / BKv;
+            const int64_t gi = i0 + ii, gk = k0 + kk;
+            As[kk][ii] = (gi < N && gk < M) ? R[gi * M + gk] : make_float2(0.f, 0.f);
+        }
+        for (int e = tid; e < BKv * BNv; e += 256) {
+            const int kk = e % BKv, jj = e / BKv;
+            const int64_t gj = j0 + jj, gk = k0 + kk;
+            Bs[kk][jj] = (gj < F && gk < M) ? D[gj * M + gk] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < BKv; ++kk) {
+            float2 av[TM], bv[TN];
+#pragma unroll
+            for (int r = 0; r < TM; ++r) av[r] = As[kk][ty + TY * r];
+#pragma unroll
+            for (int c = 0; c < TN; ++c) bv[c] = Bs[kk][tx + TX * c];
+#pragma unroll
+            for (int r = 0; r < TM; ++r)
+#pragma unroll
+                for (int c = 0; c < TN; ++c) {
+                    acc[r][c].x = fmaf(av[r].x, bv[c].x, fmaf(-av[r].y, bv[c].y, acc[r][c].x));
+                    acc[r][c].y = fmaf(av[r].x, bv[c].y, fmaf(av[r].y, bv[c].x, acc[r][c].y));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+            const int64_t gi = i0 + ty + TY * r, gj = j0 + tx + TX * c;
+            if (gi < N && gj < F) X[gj * N + gi] = acc[r][c];
+        }
+}
+
+cudaError_t launch_apply32(const float2* R, int64_t N, int64_t M, const float2* D, int64_t F, float2* X,
+                           cudaStream_t s) {
+    if (F == 0) return cudaSuccess;
+    if (F >= 48) {
+        dim3 grid(cdiv(F, 64), cdiv(N, 64));
+        k_apply32<64, 64, 4, 4, 32><<<grid, 256, 0, s>>>(R, N, M, D, F, X);
+    } else if (F >= 8) {
+        dim3 grid(cdiv(F, 16), cdiv(N, 64));
+        k_apply32<64, 16, 4, 1, 32><<<grid, 256, 0, s>>>(R, N, M, D, F, X);
+    } else {
+        dim3 grid((unsigned)F, cdiv(N, 256));
+        k_apply32<256, 1, 1, 1, 16><<<grid, 256, 0, s>>>(R, N, M, D, F, X);
+    }
+    note_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace pinv
+
+extern "C" int pinv_tc_available(void) { return pinv::tc_available() ? 1 : 0; }

@@ -173,7 +173,7 @@ struct HerkP {
 // Unblocked Cholesky of one diagonal block in shared memory, plus the inverse
 // of the resulting triangular block (used by the panel solve and the inverse).
 __global__ void __launch_bounds__(256) k_potrf_diag(double2* G, int64_t ld, int64_t N, int64_t k0,
-                                                    double2* Dinv, DevStatus* st) {
+                                                    double2* Dinv, float2* Dinv32, DevStatus* st) {
     extern __shared__ double2 sm[];
     double2* A = sm;               // [NB][NB]
     double2* X = sm + NB * NB;     // [NB][NB] inverse
@@ -234,12 +234,13 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double2* G, int64_t ld, int6
     for (int e = tid; e < NB * NB; e += 256) {
         int i = e / NB, j = e % NB;
         Dinv[e] = X[e];
+        if (Dinv32) Dinv32[e] = make_float2((float)X[e].x, (float)X[e].y);
         if (i < nb && j < nb && j <= i) G[(k0 + i) * ld + k0 + j] = A[e];
     }
 }
 
-cudaError_t launch_potrf64(double2* G, int64_t N, int64_t ld, double2* Dinv, DevStatus* st,
-                           cudaStream_t s) {
+cudaError_t launch_potrf_diag(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv,
+                              float2* Dinv32, DevStatus* st, cudaStream_t s) {
     static bool attr = false;
     size_t smem = 2 * NB * NB * sizeof(double2);
     if (!attr) {
@@ -248,11 +249,18 @@ cudaError_t launch_potrf64(double2* G, int64_t N, int64_t ld, double2* Dinv, Dev
         if (err != cudaSuccess) return err;
         attr = true;
     }
+    k_potrf_diag<<<1, 256, smem, s>>>(G, ld, N, k0, Dinv, Dinv32, st);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_potrf64(double2* G, int64_t N, int64_t ld, double2* Dinv, DevStatus* st,
+                           cudaStream_t s) {
     for (int64_t k0 = 0; k0 < N; k0 += NB) {
         int64_t nbk = std::min<int64_t>(NB, N - k0);
         double2* Dk = Dinv + (k0 / NB) * NB * NB;
-        k_potrf_diag<<<1, 256, smem, s>>>(G, ld, N, k0, Dk, st);
-        note_launch();
+        cudaError_t err = launch_potrf_diag(G, ld, N, k0, Dk, nullptr, st, s);
+        if (err != cudaSuccess) return err;
         int64_t rest = N - k0 - nbk;
         if (rest <= 0) break;
         TrsmP tp{G, ld, N, k0, nbk, Dk};
@@ -575,6 +583,68 @@ cudaError_t launch_hemv64(const double2* H, int64_t N, int64_t ld, const double2
     int64_t bm, bn;
     frame_shape(F, bm, bn);
     HemvP p{H, X, Yadd, Y, N, ld, F, bm, bn};
+    return launch_frames(p, N, F, s);
+}
+
+// Y[f][n] = sum_{k <= n} W[n][k] X[f][k] for lower-triangular W (zeros above stored)
+struct TrmvP {
+    static constexpr bool A_KFAST = true, B_KFAST = true;
+    const double2* W;
+    const double2* X;
+    double2* Y;
+    int64_t N, F, bm, bn;
+    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        frame_tile(bm, bn, i0, j0);
+        kb = 0;
+        ke = i0 + bm < N ? i0 + bm : N;
+        return true;
+    }
+    __device__ bool a_ok(int64_t i) const { return i < N; }
+    __device__ bool b_ok(int64_t j) const { return j < F; }
+    __device__ double2 a(int64_t i, int64_t k) const { return W[i * N + k]; }
+    __device__ double2 b(int64_t k, int64_t j) const { return X[j * N + k]; }
+    __device__ void store(int64_t i, int64_t j, double2 v) const { Y[j * N + i] = v; }
+};
+
+// Y[f][n] = Yadd[f][n] + sum_{k >= n} conj(W[k][n]) X[f][k]
+struct TrmvHP {
+    static constexpr bool A_KFAST = false, B_KFAST = true;
+    const double2* W;
+    const double2* X;
+    const double2* Yadd;
+    double2* Y;
+    int64_t N, F, bm, bn;
+    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        frame_tile(bm, bn, i0, j0);
+        kb = i0;
+        ke = N;
+        return true;
+    }
+    __device__ bool a_ok(int64_t i) const { return i < N; }
+    __device__ bool b_ok(int64_t j) const { return j < F; }
+    __device__ double2 a(int64_t i, int64_t k) const { return zconj(W[k * N + i]); }
+    __device__ double2 b(int64_t k, int64_t j) const { return X[j * N + k]; }
+    __device__ void store(int64_t i, int64_t j, double2 v) const {
+        if (Yadd) v = zadd(v, Yadd[j * N + i]);
+        Y[j * N + i] = v;
+    }
+};
+
+cudaError_t launch_trmv64(const double2* W, int64_t N, const double2* X, int64_t F, double2* Y,
+                          cudaStream_t s) {
+    if (F == 0) return cudaSuccess;
+    int64_t bm, bn;
+    frame_shape(F, bm, bn);
+    TrmvP p{W, X, Y, N, F, bm, bn};
+    return launch_frames(p, N, F, s);
+}
+
+cudaError_t launch_trmv_h64(const double2* W, int64_t N, const double2* X, int64_t F, const double2* Yadd,
+                            double2* Y, cudaStream_t s) {
+    if (F == 0) return cudaSuccess;
+    int64_t bm, bn;
+    frame_shape(F, bm, bn);
+    TrmvHP p{W, X, Yadd, Y, N, F, bm, bn};
     return launch_frames(p, N, F, s);
 }
 

@@ -1,0 +1,106 @@
+"""Mixed-precision (split-BF16 tcgen05) path vs the FP64 oracle.
+
+Bars:
+  * images after FP64-residual refinement: NRMSE <= 1e-4 (the mixed target);
+  * the tensor-core Gram: relative Frobenius error within the split/FP32
+    accumulation bound (2 slices ~ 2^-17 per product, 3 slices ~ 2^-24);
+  * the tensor-core Recon kernel, isolated: Recon vs G^-1 (the plan's own, in
+    FP64) times E^H from the oracle, same bounds.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle.pinv_oracle as O  # noqa: E402
+from paper_2410_06129_gb300 import _lib as L  # noqa: E402
+from paper_2410_06129_gb300 import synth  # noqa: E402
+from tests._ref import oracle_all, rel  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+SPLIT_TOL = {L.MIXED_BF16X3: 1e-4, L.MIXED_BF16X6: 2e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_tc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if not L.load().pinv_tc_available():
+        pytest.skip("tcgen05 kernels need sm_103a")
+
+
+def _plan(p, **kw):
+    from paper_2410_06129_gb300.plan import Plan
+    return Plan.from_inputs(p, **kw)
+
+
+@pytest.mark.parametrize("prec", [L.MIXED_BF16X6, L.MIXED_BF16X3])
+def test_gram_tc_small_ragged(prec):
+    """N = 400 (3 row tiles of 128 + tail, 2 column tiles of 256), 2 coils, B0."""
+    p = synth.make_plan(20, 2, "spiral", 1, 2101, 1e-3, samples=800, interleaves=2, b0=True)
+    ref = oracle_all(p)
+    pl = _plan(p, precision=prec, keep_gram=True, refine_max_iters=0).build()
+    G = pl.export(L.EXPORT_GRAM).cpu().numpy()
+    assert rel(np.tril(G), np.tril(ref.G)) < SPLIT_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [L.MIXED_BF16X6, L.MIXED_BF16X3])
+def test_recon_tc_isolated(prec):
+    """Recon = W^H (W E^H) with the plan's own W = L^-1: isolates the tensor-core kernels.
+
+    Bound: each of the two products carries a relative error of the split
+    arithmetic (SPLIT_TOL, taken per product) on its inputs' magnitudes, so the
+    error relative to Recon is at most ~ SPLIT_TOL * ||W|| ||W E^H|| / ||Recon||
+    (the cancellation factor, about kappa(L)), computed here from the data.
+    """
+    p = synth.make_plan(16, 3, "radial", 1, 2102, 1e-3, b0=True, spokes=20, per_spoke=33)
+    pl = _plan(p, precision=prec, refine_max_iters=0).build()
+    W = pl.export(L.EXPORT_LINV).cpu().numpy()
+    R = pl.export(L.EXPORT_RECON).cpu().numpy()
+    E = O.plan_encode(p)
+    T = W @ E.conj().T
+    want = W.conj().T @ T
+    amp = np.linalg.norm(W) * np.linalg.norm(T) / np.linalg.norm(want)
+    assert rel(R, want) < SPLIT_TOL[prec] * max(1.0, amp)
+    assert np.allclose(np.triu(W, 1), 0)
+
+
+@pytest.mark.parametrize("prec,iters", [(L.MIXED_BF16X6, 2), (L.MIXED_BF16X3, 4)])
+def test_images_after_refinement_cfg2_reduced(prec, iters):
+    """Workload 2 shrunk to 24x24 (kappa(G) ~ 4e5): NRMSE <= 1e-4 after refinement."""
+    p = synth.config(2, reduced=True)
+    ref = oracle_all(p)
+    pl = _plan(p, precision=prec, refine_max_iters=iters, refine_tol=1e-9).build()
+    x = pl.apply(torch.from_numpy(p.data).cuda()).cpu().numpy()
+    info = pl.info()
+    assert rel(x, ref.images) <= 1e-4, (rel(x, ref.images), info)
+    assert info["last_refine_iters"] >= 1
+
+
+def test_images_cfg1_full_complex64_io():
+    """Workload 1 at full size with complex64 data in and out."""
+    p = synth.config(1)
+    ref = oracle_all(p)
+    pl = _plan(p, precision=L.MIXED_BF16X6, refine_max_iters=2).build()
+    d = torch.from_numpy(p.data.astype(np.complex64)).cuda()
+    x = pl.apply(d)
+    assert x.dtype == torch.complex64
+    ref32 = O.solve(ref.E, ref.L, O.data_columns(p.data.astype(np.complex64))).T
+    assert rel(x.cpu().numpy(), ref32) <= 1e-4
+
+
+def test_b0_radial_reduced_cfg5():
+    """Workload 5 shrunk to 32x32: 8 coils, radial, B0 +-50 Hz, 4 us dwell."""
+    p = synth.config(5, reduced=True)
+    ref = oracle_all(p)
+    pl = _plan(p, precision=L.MIXED_BF16X6, refine_max_iters=3, refine_tol=1e-9).build()
+    x = pl.apply(torch.from_numpy(p.data).cuda()).cpu().numpy()
+    assert rel(x, ref.images) <= 1e-4
+
+
+def test_factor_only_mixed():
+    p = synth.make_plan(16, 4, "spiral", 2, 2103, 1e-3, samples=512, interleaves=2, b0=True)
+    ref = oracle_all(p)
+    pl = _plan(p, precision=L.MIXED_BF16X6, recon_mode=L.RECON_NONE, refine_max_iters=2).build()
+    x = pl.apply(torch.from_numpy(p.data).cuda()).cpu().numpy()
+    assert rel(x, ref.images) <= 1e-4
