@@ -193,6 +193,46 @@ pinv_status pinv_plan_info(const pinv_plan* plan, pinv_plan_info_t* out);
 /* Free the plan and its device memory (synchronises the plan's work). NULL is a no-op. */
 void pinv_plan_destroy(pinv_plan* plan);
 
+/* Size of the fixed device scratch array behind pinv_apply_noalloc (64 MiB). */
+#define PINV_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/*
+ * Same result as pinv_apply, for callers that cannot allocate device memory
+ * when they reconstruct. Examples are a scanner's real-time loop running
+ * under a fixed, pre-reserved memory budget, or an application whose device
+ * memory belongs to another allocator that must not be bypassed. A cudaMalloc
+ * there can also stall the device while it synchronises and break the loop's
+ * latency. The paper has no counterpart; this is an interface for such
+ * callers.
+ *
+ * pinv_apply grows plan-owned scratch on first use. This call instead takes
+ * its scratch from one file-scope device array of PINV_NOALLOC_SCRATCH_BYTES.
+ * That array exists once on every GPU that loads the library and is held until
+ * the process exits. The call allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *
+ * Scratch needed, rounded per buffer to 256 B:
+ *   16 F M   when dtype is c64 and the plan is FP64, factor-only or refined;
+ *   16 F N   when dtype is c64;
+ *   16 F M   when refining, or for mixed factor-only plans;
+ *   16 F N   when refining, or for factor-only plans;
+ *    8 F M   for mixed plans with Recon and c128 data;
+ *    8 F N   for mixed plans with Recon;
+ *   16 F     when the refinement's stopping rule (refine_tol > 0) is on.
+ * A call that needs more fails with PINV_ERR_INVALID_ARG and a message giving
+ * the size; split the frames over several calls.
+ *
+ * The first call on a device resolves the array's device address there (once
+ * per device, with that device current). Make that first call before any
+ * stream capture. Every call shares the array, and it keeps the last call's
+ * contents; nothing in it needs to start at zero, since each buffer is fully
+ * written before it is read. Calls whose GPU work overlaps (other streams or
+ * host threads) race on the array. Arguments and errors are otherwise those of
+ * pinv_apply.
+ */
+pinv_status pinv_apply_noalloc(pinv_plan* plan, const void* d_data, void* d_image, int64_t n_frames,
+                               int dtype, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,7 +74,9 @@ SIGNATURES = {
     "pinv_plan_keep_gram": (C.c_int, [_VP, C.c_int]),
     "pinv_plan_info": (C.c_int, [_VP, C.POINTER(PlanInfo)]),
     "pinv_plan_destroy": (None, [_VP]),
+    "pinv_apply_noalloc": (C.c_int, [_VP, _VP, _VP, C.c_int64, C.c_int, _VP]),
 }
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _lib = None
 
