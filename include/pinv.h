@@ -97,9 +97,15 @@ typedef struct {
     int lambda_mode;              /* pinv_lambda_mode */
     int precision;                /* pinv_precision */
     int recon_mode;               /* pinv_recon_mode */
-    int refine_max_iters;         /* mixed plans: max refinement steps per apply (0 = none) */
-    double refine_tol;            /* mixed plans: stop when ||r|| / ||E^H d|| <= tol */
+    int refine_max_iters;         /* refinement steps per apply (0 = none) */
+    double refine_tol;            /* stop when ||r|| / ||E^H d|| <= tol (0 = run all steps) */
+    int refine_residual;          /* mixed plans: pinv_residual arithmetic of the residual */
 } pinv_plan_desc;
+
+typedef enum {
+    PINV_RESIDUAL_DOUBLE_FLOAT = 0, /* r in double-float (hi + lo floats, ~44 bits) on the FP32 units */
+    PINV_RESIDUAL_FP64 = 1          /* r in FP64 (DFMA); FP64 plans always use this */
+} pinv_residual;
 
 typedef struct {
     int64_t n_vox, n_samples, n_rows;   /* N, M_k, M = C * M_k */
@@ -217,7 +223,7 @@ void pinv_plan_destroy(pinv_plan* plan);
  *   16 F M   when refining, or for mixed factor-only plans;
  *   16 F N   when refining, or for factor-only plans;
  *    8 F M   for mixed plans with Recon and c128 data;
- *    8 F N   for mixed plans with Recon;
+ *    8 F N   for mixed plans with Recon, or refined with the double-float residual;
  *   16 F     when the refinement's stopping rule (refine_tol > 0) is on.
  * A call that needs more fails with PINV_ERR_INVALID_ARG and a message giving
  * the size; split the frames over several calls.

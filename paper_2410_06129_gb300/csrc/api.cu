@@ -104,6 +104,9 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
     p->precision = d->precision;
     p->refine_iters = d->refine_max_iters;
     p->refine_tol = d->refine_tol;
+    if (d->refine_residual != PINV_RESIDUAL_DOUBLE_FLOAT && d->refine_residual != PINV_RESIDUAL_FP64)
+        return cleanup(fail(PINV_ERR_INVALID_ARG, "unknown refine_residual"));
+    p->refine_residual = p->precision == PINV_FP64 ? PINV_RESIDUAL_FP64 : d->refine_residual;
 
     // voxel grid coordinates
     std::vector<int> ijk(3 * p->N);
@@ -209,12 +212,41 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
         e.tidx = ti;
     }
     CKC(launch_tables(p->traj, p->ndim, p->Mk, p->dims, p->fov, ex, ey, ez, ex32, ey32, ez32, s));
+    if (p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT) {
+        // double-float copies of the tables for the refinement residual
+        float4 *xdf, *ydf, *zdf;
+        AL(xdf, sizeof(float4) * p->Mk * e.nx, "exdf");
+        AL(ydf, sizeof(float4) * p->Mk * e.ny, "eydf");
+        AL(zdf, sizeof(float4) * p->Mk * e.nz, "ezdf");
+        CKC(launch_to_df(ex, xdf, p->Mk * e.nx, s));
+        CKC(launch_to_df(ey, ydf, p->Mk * e.ny, s));
+        CKC(launch_to_df(ez, zdf, p->Mk * e.nz, s));
+        e.exdf = xdf;
+        e.eydf = ydf;
+        e.ezdf = zdf;
+        if (e.b0tab) {
+            const int64_t nt = (int64_t)tuniq.size() * p->N;
+            float4* bdf;
+            AL(bdf, sizeof(float4) * nt, "b0df");
+            CKC(launch_to_df(e.b0tab, bdf, nt, s));
+            e.b0df = bdf;
+        }
+        if (e.coils) {
+            float4* cdf;
+            AL(cdf, sizeof(float4) * p->C * p->N, "coilsdf");
+            CKC(launch_to_df(e.coils, cdf, p->C * p->N, s));
+            e.coilsdf = cdf;
+        }
+    }
     // factor storage
     int64_t nblk = (p->N + 63) / 64;
     AL(p->G, sizeof(double2) * p->N * p->N, "G");
     AL(p->Dinv, sizeof(double2) * nblk * 64 * 64, "Dinv");
     if (p->precision == PINV_FP64) AL(p->Ginv, sizeof(double2) * p->N * p->N, "Ginv");
-    else AL(p->W, sizeof(double2) * p->N * p->N, "W");
+    else {
+        AL(p->W, sizeof(double2) * p->N * p->N, "W");
+        AL(p->W32, sizeof(float2) * p->N * p->N, "W32");
+    }
     int rm = d->recon_mode;
     if (rm == PINV_RECON_AUTO) {
         size_t rb = (size_t)p->N * p->M * (p->precision == PINV_FP64 ? 16 : 8);
@@ -266,13 +298,12 @@ pinv_status pinv_build(pinv_plan* p, void* stream) {
         // FP64 diagonal panels, tensor-core panel solves / trailing updates,
         // then the triangular inverse and G^-1 = W^H W on tensor cores
         const int64_t nblk = (N + 63) / 64;
-        float2 *L32 = nullptr, *D32 = nullptr, *W32 = nullptr;
+        float2 *L32 = nullptr, *D32 = nullptr, *W32 = p->W32;
         CK(cudaMallocAsync((void**)&L32, sizeof(float2) * N * N, s));
         CK(cudaMallocAsync((void**)&D32, sizeof(float2) * nblk * 64 * 64, s));
         CK(launch_potrf_tc(p->G, N, ld, p->Dinv, D32, L32, slices, p->st, s));
         CK(launch_pivot_stats(p->G, N, ld, p->st, s));
         CK(cudaEventRecord(p->ev[3], s));
-        CK(cudaMallocAsync((void**)&W32, sizeof(float2) * N * N, s));
         CK(launch_trtri_tc(L32, N, D32, p->W, W32, slices, p->st, s));
         CK(cudaFreeAsync(D32, s));
         CK(cudaFreeAsync(L32, s));
@@ -284,7 +315,6 @@ pinv_status pinv_build(pinv_plan* p, void* stream) {
             CK(launch_recon_tc(p->enc, W32, T, slices, (float2*)p->R, p->st, s));
             CK(cudaFreeAsync(T, s));
         }
-        CK(cudaFreeAsync(W32, s));
         CK(cudaEventRecord(p->ev[5], s));
         p->built = true;
         return PINV_OK;
@@ -422,11 +452,20 @@ pinv_status pinv_apply(pinv_plan* p, const void* d_data, void* d_image, int64_t 
                 CK(launch_adjoint64(p->enc, D, F, 0.0, nullptr, p->r128, s));  // b = E^H d
                 CK(launch_frame_norms(p->r128, F, N, p->norms + F, s));
             }
+            const bool dfres = mixed && p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT;
             for (int it = 0; it < p->refine_iters; ++it) {
-                CK(launch_forward64(p->enc, X, F, D, p->u128, s));           // u = d - E x
-                CK(launch_adjoint64(p->enc, p->u128, F, p->lambda_abs, X, p->r128, s));
+                if (dfres) {
+                    CK(launch_forward_df(p->enc, X, F, D, p->u128, s));      // u = d - E x
+                    CK(launch_adjoint_df(p->enc, p->u128, F, p->lambda_abs, X, p->r128, s));
+                } else {
+                    CK(launch_forward64(p->enc, X, F, D, p->u128, s));       // u = d - E x
+                    CK(launch_adjoint64(p->enc, p->u128, F, p->lambda_abs, X, p->r128, s));
+                }
                 if (stop_rule) CK(launch_frame_norms(p->r128, F, N, p->norms, s));
-                if (mixed) {
+                if (dfres) {
+                    // the correction only preconditions the next residual: FP32 W suffices
+                    CK(launch_correct32(p->W32, N, p->r128, F, p->x64, X, s));
+                } else if (mixed) {
                     // x += W^H (W r) in FP64: never through an explicitly formed
                     // low-precision G^-1, whose error the correction would amplify by kappa(G)
                     CK(launch_trmv64(p->W, N, p->r128, F, p->u128, s));

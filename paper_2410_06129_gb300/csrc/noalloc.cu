@@ -86,6 +86,7 @@ extern "C" pinv_status pinv_apply_noalloc(pinv_plan* p, const void* d_data, void
     const bool mixed = p->precision != PINV_FP64;
     const bool refine = p->refine_iters > 0;
     const bool stop_rule = refine && p->refine_tol > 0.0;
+    const bool dfres = mixed && p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT;
 
     // which scratch buffers this call needs (same roles as pinv_apply's)
     const bool need_d128 = dtype == PINV_C64 && (!mixed || !p->recon || refine);
@@ -93,7 +94,7 @@ extern "C" pinv_status pinv_apply_noalloc(pinv_plan* p, const void* d_data, void
     const bool need_u128 = refine || (mixed && !p->recon);
     const bool need_r128 = refine || !p->recon;
     const bool need_d64 = mixed && p->recon && dtype == PINV_C128;
-    const bool need_x64 = mixed && p->recon;
+    const bool need_x64 = mixed && (p->recon || (refine && dfres));
     Carver size{nullptr};
     if (need_d128) size.take<double2>((size_t)(F * M));
     if (need_x128) size.take<double2>((size_t)(F * N));
@@ -157,10 +158,17 @@ extern "C" pinv_status pinv_apply_noalloc(pinv_plan* p, const void* d_data, void
             CKN(launch_frame_norms(r128, F, N, norms + F, s));
         }
         for (int it = 0; it < p->refine_iters; ++it) {
-            CKN(launch_forward64(p->enc, X, F, D, u128, s));  // u = d - E x
-            CKN(launch_adjoint64(p->enc, u128, F, p->lambda_abs, X, r128, s));
+            if (dfres) {
+                CKN(launch_forward_df(p->enc, X, F, D, u128, s));  // u = d - E x
+                CKN(launch_adjoint_df(p->enc, u128, F, p->lambda_abs, X, r128, s));
+            } else {
+                CKN(launch_forward64(p->enc, X, F, D, u128, s));
+                CKN(launch_adjoint64(p->enc, u128, F, p->lambda_abs, X, r128, s));
+            }
             if (stop_rule) CKN(launch_frame_norms(r128, F, N, norms, s));
-            if (mixed) {
+            if (dfres) {
+                CKN(launch_correct32(p->W32, N, r128, F, x64, X, s));
+            } else if (mixed) {
                 CKN(launch_trmv64(p->W, N, r128, F, u128, s));
                 CKN(launch_trmv_h64(p->W, N, u128, F, X, X, s));
             } else {

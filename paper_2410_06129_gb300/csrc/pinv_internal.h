@@ -38,6 +38,12 @@ struct EncodeDev {
     const float2* ez32;
     const float2* b0tab32;
     const float2* coils32;
+    // double-float copies (re.hi, re.lo, im.hi, im.lo) for the refinement residual
+    const float4* exdf;
+    const float4* eydf;
+    const float4* ezdf;
+    const float4* b0df;
+    const float4* coilsdf;
 };
 
 // Device status word of a plan.
@@ -162,5 +168,19 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
 cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, double2* W, float2* W32,
                             int slices, DevStatus* st, cudaStream_t s);
 bool tc_available();
+
+// ---------------------------------------------------------------------------
+// Double-float refinement residual and FP32 correction (dfgemm.cu)
+// ---------------------------------------------------------------------------
+cudaError_t launch_to_df(const double2* src, float4* dst, int64_t n, cudaStream_t s);
+// U[f] = D[f] - E X[f], double-float arithmetic, FP64 in/out
+cudaError_t launch_forward_df(const EncodeDev& e, const double2* X, int64_t F, const double2* D, double2* U,
+                              cudaStream_t s);
+// R[f] = E^H U[f] - lam X[f] (X may be null), double-float arithmetic, FP64 in/out
+cudaError_t launch_adjoint_df(const EncodeDev& e, const double2* U, int64_t F, double lam, const double2* X,
+                              double2* R, cudaStream_t s);
+// X[f] += W^H (W R[f]) in FP32 with scratch T [F][N]
+cudaError_t launch_correct32(const float2* W32, int64_t N, const double2* R, int64_t F, float2* T, double2* X,
+                             cudaStream_t s);
 
 }  // namespace pinv

@@ -22,6 +22,7 @@ struct pinv_plan {
     int recon = 1;
     int refine_iters = 0;
     double refine_tol = 0;
+    int refine_residual = PINV_RESIDUAL_DOUBLE_FLOAT;
     bool keep_gram = false;
     bool built = false;
 
@@ -35,6 +36,7 @@ struct pinv_plan {
     double2* Dinv = nullptr;   // inverses of the diagonal blocks
     double2* Ginv = nullptr;   // full G^-1 (FP64 plans)
     double2* W = nullptr;      // L^-1, lower (mixed plans)
+    float2* W32 = nullptr;     // FP32 copy of W (mixed plans)
     void* R = nullptr;         // Recon [N][M], c128 (FP64) or c64 (mixed)
     pinv::DevStatus* st = nullptr;
 

@@ -416,13 +416,15 @@ cudaError_t launch_recon64(const EncodeDev& e, const double2* Ginv, int64_t ld, 
 // ---------------------------------------------------------------------------
 template <class P>
 static cudaError_t launch_frames(P p, int64_t rows, int64_t F, cudaStream_t s) {
+    // 16-row tiles: the FP64 units, not shared memory, bound these kernels, so
+    // narrow tiles cost nothing per flop and give N / 16 CTAs instead of N / 64
     if (F >= 48) {
-        dim3 grid((unsigned)((F + 63) / 64), (unsigned)((rows + 63) / 64));
-        k_ztile<64, 64, 4, 4><<<grid, 256, 0, s>>>(p);
+        dim3 grid((unsigned)((F + 63) / 64), (unsigned)((rows + 15) / 16));
+        k_ztile<16, 64, 1, 4><<<grid, 256, 0, s>>>(p);
         note_launch();
     } else if (F >= 8) {
-        dim3 grid((unsigned)((F + 15) / 16), (unsigned)((rows + 63) / 64));
-        k_ztile<64, 16, 4, 1><<<grid, 256, 0, s>>>(p);
+        dim3 grid((unsigned)((F + 15) / 16), (unsigned)((rows + 15) / 16));
+        k_ztile<16, 16, 1, 1><<<grid, 256, 0, s>>>(p);
         note_launch();
     } else {
         dim3 grid((unsigned)F, (unsigned)((rows + 255) / 256));
@@ -461,8 +463,8 @@ struct ApplyP {
 };
 
 static void frame_shape(int64_t F, int64_t& bm, int64_t& bn) {
-    if (F >= 48) { bm = 64; bn = 64; }
-    else if (F >= 8) { bm = 64; bn = 16; }
+    if (F >= 48) { bm = 16; bn = 64; }
+    else if (F >= 8) { bm = 16; bn = 16; }
     else { bm = 256; bn = 1; }
 }
 

@@ -25,7 +25,8 @@ class Plan:
     def __init__(self, dims, traj, coil_maps=None, b0_hz=None, times=None, lam=1e-3,
                  lambda_mode=L.LAMBDA_REL_MEAN_DIAG, precision=L.FP64,
                  recon_mode=L.RECON_STORE, voxel_index=None, fov=None,
-                 refine_max_iters=None, refine_tol=0.0, keep_gram=False, stream=None):
+                 refine_max_iters=None, refine_tol=0.0, refine_residual=L.RESIDUAL_DOUBLE_FLOAT,
+                 keep_gram=False, stream=None):
         lib = L.load()
         if refine_max_iters is None:
             # one FP64 refinement step brings the FP64 explicit-inverse image to
@@ -33,7 +34,7 @@ class Plan:
             refine_max_iters = 1 if precision == L.FP64 else 3
         desc, self._keep = L.make_desc(dims, traj, coil_maps, b0_hz, times, lam, lambda_mode,
                                        precision, recon_mode, voxel_index, fov,
-                                       refine_max_iters, refine_tol)
+                                       refine_max_iters, refine_tol, refine_residual)
         h = C.c_void_p()
         L.check(lib.pinv_plan_create(C.byref(desc), _stream_handle(stream), C.byref(h)))
         self._h = h

@@ -77,6 +77,20 @@ def test_images_after_refinement_cfg2_reduced(prec, iters):
     assert info["last_refine_iters"] >= 1
 
 
+@pytest.mark.parametrize("residual", [L.RESIDUAL_DOUBLE_FLOAT, L.RESIDUAL_FP64])
+def test_refinement_residual_arithmetic(residual):
+    """Double-float and FP64 residuals both reach the mixed bar, and agree."""
+    p = synth.config(2, reduced=True)
+    ref = oracle_all(p)
+    pl = _plan(p, precision=L.MIXED_BF16X6, refine_max_iters=3, refine_residual=residual).build()
+    x = pl.apply(torch.from_numpy(p.data).cuda()).cpu().numpy()
+    assert rel(x, ref.images) <= 1e-4
+    if residual == L.RESIDUAL_DOUBLE_FLOAT:
+        pl64 = _plan(p, precision=L.MIXED_BF16X6, refine_max_iters=3, refine_residual=L.RESIDUAL_FP64).build()
+        x64 = pl64.apply(torch.from_numpy(p.data).cuda()).cpu().numpy()
+        assert rel(x, x64) <= 1e-6
+
+
 def test_images_cfg1_full_complex64_io():
     """Workload 1 at full size with complex64 data in and out."""
     p = synth.config(1)
