@@ -163,6 +163,7 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
     e.nx = p->dims[0];
     e.ny = p->dims[1];
     e.nz = p->dims[2];
+    e.full_grid = d->voxel_index ? 0 : 1;
     AL(p->traj, sizeof(double) * p->Mk * p->ndim, "traj");
     double2 *ex, *ey, *ez;
     float2 *ex32, *ey32, *ez32;
@@ -212,6 +213,29 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
         e.tidx = ti;
     }
     CKC(launch_tables(p->traj, p->ndim, p->Mk, p->dims, p->fov, ex, ey, ez, ex32, ey32, ez32, s));
+    if (p->precision != PINV_FP64) {
+        // sample-contiguous copies of the FP32 tables for the tensor-core producers
+        const int64_t Mkp = (p->Mk + 7) / 8 * 8;
+        float2 *xt, *yt, *zt;
+        AL(xt, sizeof(float2) * Mkp * e.nx, "ext32");
+        AL(yt, sizeof(float2) * Mkp * e.ny, "eyt32");
+        AL(zt, sizeof(float2) * Mkp * e.nz, "ezt32");
+        CKC(launch_transpose32(ex32, p->Mk, e.nx, xt, Mkp, s));
+        CKC(launch_transpose32(ey32, p->Mk, e.ny, yt, Mkp, s));
+        CKC(launch_transpose32(ez32, p->Mk, e.nz, zt, Mkp, s));
+        e.ext32 = xt;
+        e.eyt32 = yt;
+        e.ezt32 = zt;
+        e.Mkp = Mkp;
+        if (e.b0tab32) {
+            const int T = (int)tuniq.size();
+            float2* bt;
+            AL(bt, sizeof(float2) * T * p->N, "b0t32");
+            CKC(launch_transpose32(e.b0tab32, T, p->N, bt, T, s));
+            e.b0t32 = bt;
+            e.T = T;
+        }
+    }
     if (p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT) {
         // double-float copies of the tables for the refinement residual
         float4 *xdf, *ydf, *zdf;
@@ -310,9 +334,12 @@ pinv_status pinv_build(pinv_plan* p, void* stream) {
         CK(cudaEventRecord(p->ev[4], s));
         if (p->recon) {
             // Recon = W^H (W E^H) (Eq. 8) through an [N][M] c64 intermediate
-            float2* T = nullptr;
+            float2 *T = nullptr, *WT32 = nullptr;
             CK(cudaMallocAsync((void**)&T, sizeof(float2) * N * p->M, s));
-            CK(launch_recon_tc(p->enc, W32, T, slices, (float2*)p->R, p->st, s));
+            CK(cudaMallocAsync((void**)&WT32, sizeof(float2) * N * N, s));
+            CK(launch_transpose32(W32, N, N, WT32, N, s));
+            CK(launch_recon_tc(p->enc, W32, WT32, T, slices, (float2*)p->R, p->st, s));
+            CK(cudaFreeAsync(WT32, s));
             CK(cudaFreeAsync(T, s));
         }
         CK(cudaEventRecord(p->ev[5], s));

@@ -38,6 +38,16 @@ struct EncodeDev {
     const float2* ez32;
     const float2* b0tab32;
     const float2* coils32;
+    // sample-contiguous FP32 copies for the tensor-core producers:
+    // ext32[ix][m] = ex32[m][ix] (rows padded with zeros to Mkp = 8 * ceil(Mk / 8)),
+    // b0t32[n][u] = b0tab32[u][n] (T distinct sample times)
+    const float2* ext32;
+    const float2* eyt32;
+    const float2* ezt32;
+    const float2* b0t32;
+    int64_t Mkp;
+    int T;
+    int full_grid;          // voxels are the whole grid in flat order (no voxel list)
     // double-float copies (re.hi, re.lo, im.hi, im.lo) for the refinement residual
     const float4* exdf;
     const float4* eydf;
@@ -98,6 +108,10 @@ cudaError_t launch_tables(const double* traj, int ndim, int64_t Mk, const int* d
 cudaError_t launch_b0_table(const double* b0, const double* tuniq, int T, int64_t N,
                             double2* tab, float2* tab32, cudaStream_t s);
 cudaError_t launch_to_f32(const double2* src, float2* dst, int64_t n, cudaStream_t s);
+// dst[c][r] = src[r][c] for an FP32 [rows][cols] matrix; dst rows have stride ldd >= rows,
+// the padding columns rows..ldd-1 are zero-filled.
+cudaError_t launch_transpose32(const float2* src, int64_t rows, int64_t cols, float2* dst, int64_t ldd,
+                               cudaStream_t s);
 cudaError_t launch_fill_identity(double2* W, int64_t N, int64_t ld, cudaStream_t s);
 
 // Gram G = (A^H A) o (S^H S) + lambda I, lower tiles, FP64.
@@ -150,8 +164,8 @@ cudaError_t launch_gram_tc(const EncodeDev& e, double lambda, int slices, double
                            DevStatus* st, cudaStream_t s);
 // Recon = W^H (W E^H) in split BF16 on tcgen05 (W = L^-1 in FP32, T = W E^H
 // scratch [N][M] c64), c64 out.
-cudaError_t launch_recon_tc(const EncodeDev& e, const float2* W32, float2* T, int slices, float2* R,
-                            DevStatus* st, cudaStream_t s);
+cudaError_t launch_recon_tc(const EncodeDev& e, const float2* W32, const float2* WT32, float2* T, int slices,
+                            float2* R, DevStatus* st, cudaStream_t s);
 // Y[f] = W X[f] (lower W), and Y[f] = Yadd[f] + W^H X[f], FP64.
 cudaError_t launch_trmv64(const double2* W, int64_t N, const double2* X, int64_t F, double2* Y,
                           cudaStream_t s);

@@ -177,3 +177,32 @@ cudaError_t launch_zaxpy(double2* X, const double2* Y, int64_t n, cudaStream_t s
 }
 
 }  // namespace pinv
+
+namespace pinv {
+
+// Tiled transpose through shared memory: dst[c][r] = src[r][c], zero padding for r in [rows, ldd).
+__global__ void k_transpose32(const float2* __restrict__ src, int64_t rows, int64_t cols,
+                              float2* __restrict__ dst, int64_t ldd) {
+    __shared__ float2 t[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int dy = threadIdx.y; dy < 32; dy += 8) {
+        const int64_t r = r0 + dy, c = c0 + threadIdx.x;
+        t[dy][threadIdx.x] = (r < rows && c < cols) ? src[r * cols + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int dy = threadIdx.y; dy < 32; dy += 8) {
+        const int64_t c = c0 + dy, r = r0 + threadIdx.x;
+        if (c < cols && r < ldd) dst[c * ldd + r] = t[threadIdx.x][dy];
+    }
+}
+
+cudaError_t launch_transpose32(const float2* src, int64_t rows, int64_t cols, float2* dst, int64_t ldd,
+                               cudaStream_t s) {
+    if (rows == 0 || cols == 0) return cudaSuccess;
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((ldd + 31) / 32));
+    k_transpose32<<<grid, dim3(32, 8), 0, s>>>(src, rows, cols, dst, ldd);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace pinv

@@ -20,8 +20,9 @@
 // the MMA issuer waits. The relative bias stays near 3 * DRAIN * 2^-24
 // regardless of K.
 //
-// Roles. 8 producer warps generate or load operand values (problem functors
-// a8 / b8 return 8 consecutive k for one row or column), split them and write
+// Roles. 8 producer warps generate or load operand values (problem functors:
+// row_a / row_b build a per-thread context once per tile, a8 / b8 then return
+// 8 consecutive k for that row or column), split them and write
 // the canonical K-major no-swizzle layout into a ring of shared-memory stages.
 // One thread issues tcgen05.mma and commits stages back to the producers and
 // full buffers to the drains. The producer warps also run the epilogue from
@@ -258,6 +259,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(P p, DevStatus* st, int site
         };
         const int ua = threadIdx.x;  // A unit: row ua & 127, k group ua >> 7
         const int ubr = threadIdx.x & (BN - 1), ubg = threadIdx.x >> 7;
+        // per-thread operand contexts (row pointers, table rows) fixed for the tile
+        const auto ra = p.row_a(i0 + (ua & (BM - 1)));
+        const auto rb = p.row_b(j0 + ubr);
         for (int kt = 0; kt < nk && ok; ++kt) {
             // the MMA cannot start group g + 1 until group g is drained; drain it
             // before the ring can only advance past that point
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(P p, DevStatus* st, int site
             {
                 float2 v[8];
                 const int r = ua & (BM - 1), g = ua >> 7;
-                p.a8(i0 + r, k0 + 8 * g, ke, v);
+                p.a8(ra, k0 + 8 * g, ke, v);
                 float re[8], im[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) { re[t] = v[t].x; im[t] = v[t].y; }
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(P p, DevStatus* st, int site
             }
             {
                 float2 v[8];
-                p.b8(j0 + ubr, k0 + 8 * ubg, ke, v);
+                p.b8(rb, k0 + 8 * ubg, ke, v);
                 float re[8], im[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) { re[t] = v[t].x; im[t] = v[t].y; }

@@ -3,8 +3,10 @@
 // the triangular inverse and Recon = (L^-1)^H L^-1 E^H (Eq. 8), plus the c64
 // SIMT apply used when frames are few.
 //
-// Every problem supplies tile(), a8()/b8() (8 consecutive k of one row of A or
-// one column of B, zero outside the problem), row_ok()/col_ok() and store().
+// Every problem supplies tile(); row_a()/row_b(), a per-thread context built
+// once per tile (a row pointer, or the phase-table rows of one voxel or one
+// sample); a8()/b8(), 8 consecutive k of that row of A or column of B, zero
+// outside the problem; row_ok()/col_ok() and store().
 #include <algorithm>
 
 #include "tc_engine.cuh"
@@ -18,54 +20,159 @@ __device__ inline float2 cmulf(float2 a, float2 b) {
 }
 __device__ inline float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
-// A[m][n] = exp(-i2pi(k_m . r_n + df_n t_m)) from the single-precision tables
-__device__ inline float2 gen_a32(const EncodeDev& e, int64_t m, int64_t n) {
-    const int* g = e.vox_ijk + 3 * n;
-    float2 v = e.ex32[m * e.nx + g[0]];
-    if (e.ny > 1) v = cmulf(v, e.ey32[m * e.ny + g[1]]);
-    if (e.nz > 1) v = cmulf(v, e.ez32[m * e.nz + g[2]]);
-    if (e.b0tab32) v = cmulf(v, e.b0tab32[(int64_t)e.tidx[m] * e.N + n]);
-    return v;
-}
-
-// conj(E[(c,m)][n]) for 8 consecutive voxels n (zero past ke or outside M)
-__device__ inline void gen_eh8(const EncodeDev& e, int64_t j, int64_t n0, int64_t ke, float2 (&v)[8]) {
-    const int64_t M = e.Mk * e.C;
-    const int c = (int)(j / e.Mk);
-    const int64_t m = j - (int64_t)c * e.Mk;
+// 8 consecutive values from a 16-byte aligned address
+__device__ inline void ld8a(const float2* p, float2 (&v)[8]) {
+    const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        const int64_t n = n0 + t;
-        if (j < M && n < ke) {
-            float2 a = gen_a32(e, m, n);
-            if (e.coils32) a = cmulf(a, e.coils32[(int64_t)c * e.N + n]);
-            v[t] = conjf2(a);
-        } else {
-            v[t] = make_float2(0.f, 0.f);
-        }
+    for (int t = 0; t < 4; ++t) {
+        const float4 w = __ldg(q + t);
+        v[2 * t] = make_float2(w.x, w.y);
+        v[2 * t + 1] = make_float2(w.z, w.w);
     }
 }
 
 // 8 consecutive FP32 complex values p[0..7] (zero past `avail`)
 __device__ inline void load8f(const float2* p, int avail, float2 (&v)[8]) {
     if (avail >= 8 && (((uintptr_t)p) & 15) == 0) {
-        const float4* q = reinterpret_cast<const float4*>(p);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const float4 w = __ldg(q + t);
-            v[2 * t] = make_float2(w.x, w.y);
-            v[2 * t + 1] = make_float2(w.z, w.w);
-        }
+        ld8a(p, v);
         return;
     }
 #pragma unroll
-    for (int t = 0; t < 8; ++t) v[t] = t < avail ? p[t] : make_float2(0.f, 0.f);
+    for (int t = 0; t < 8; ++t) v[t] = t < avail ? __ldg(p + t) : make_float2(0.f, 0.f);
 }
 
 // 8 values down a column: p[0], p[ld], ..., p[7 ld] (zero past `avail`)
 __device__ inline void load8col(const float2* p, int64_t ld, int avail, float2 (&v)[8]) {
 #pragma unroll
     for (int t = 0; t < 8; ++t) v[t] = t < avail ? __ldg(p + t * ld) : make_float2(0.f, 0.f);
+}
+
+// A row of a memory operand: pointer to its first element and a validity flag.
+struct RowPtr {
+    const float2* p;
+    int ok;
+};
+
+// ------------------------------------------------------------------ generated encoding
+// Phase-table rows of one voxel n, for 8 consecutive samples m at a time:
+// A[m][n] = ex[m][ix] ey[m][iy] ez[m][iz] b0[u(m)][n] from the sample-contiguous tables.
+struct VoxRow {
+    const float2* x;
+    const float2* y;
+    const float2* z;
+    const float2* b;
+    int ok;
+};
+__device__ inline VoxRow vox_row(const EncodeDev& e, int64_t n) {
+    VoxRow r;
+    r.ok = n < e.N;
+    const int64_t nn = r.ok ? n : 0;
+    const int* g = e.vox_ijk + 3 * nn;
+    r.x = e.ext32 + (int64_t)__ldg(g) * e.Mkp;
+    r.y = e.ny > 1 ? e.eyt32 + (int64_t)__ldg(g + 1) * e.Mkp : nullptr;
+    r.z = e.nz > 1 ? e.ezt32 + (int64_t)__ldg(g + 2) * e.Mkp : nullptr;
+    r.b = e.b0t32 ? e.b0t32 + nn * e.T : nullptr;
+    return r;
+}
+// A[m0 .. m0+7][n] (m0 a multiple of 8; table rows are padded to a multiple of 8)
+__device__ inline void gen_a8_samples(const EncodeDev& e, const VoxRow& r, int64_t m0, int64_t ke,
+                                      float2 (&v)[8]) {
+    ld8a(r.x + m0, v);
+    if (r.y) {
+        float2 w[8];
+        ld8a(r.y + m0, w);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = cmulf(v[t], w[t]);
+    }
+    if (r.z) {
+        float2 w[8];
+        ld8a(r.z + m0, w);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = cmulf(v[t], w[t]);
+    }
+    if (r.b) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int u = m0 + t < ke ? __ldg(e.tidx + m0 + t) : 0;
+            v[t] = cmulf(v[t], __ldg(r.b + u));
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+        if (!r.ok || m0 + t >= ke) v[t] = make_float2(0.f, 0.f);
+}
+
+// One column j = (c, m) of E^H, for 8 consecutive voxels at a time:
+// conj(s_c(n) A[m][n]) from the voxel-contiguous tables ex32[m][ix] etc.
+struct EhCol {
+    const float2* x;
+    const float2* y;
+    const float2* z;
+    const float2* c;
+    const float2* b;
+    int ok;
+};
+__device__ inline EhCol eh_col(const EncodeDev& e, int64_t j) {
+    EhCol r;
+    const int64_t M = e.Mk * e.C;
+    r.ok = j < M;
+    const int64_t jj = r.ok ? j : 0;
+    const int c = (int)(jj / e.Mk);
+    const int64_t m = jj - (int64_t)c * e.Mk;
+    r.x = e.ex32 + m * e.nx;
+    r.y = e.ey32 + m * e.ny;
+    r.z = e.ez32 + m * e.nz;
+    r.c = e.coils32 ? e.coils32 + (int64_t)c * e.N : nullptr;
+    r.b = e.b0tab32 ? e.b0tab32 + (int64_t)__ldg(e.tidx + m) * e.N : nullptr;
+    return r;
+}
+__device__ inline void gen_eh8_voxels(const EncodeDev& e, const EhCol& r, int64_t n0, int64_t ke,
+                                      float2 (&v)[8]) {
+    if (!r.ok) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = make_float2(0.f, 0.f);
+        return;
+    }
+    if (e.full_grid && (e.nx & 7) == 0 && n0 + 8 <= ke) {
+        // 8 voxels on one grid line: contiguous ix, shared iy and iz
+        const int64_t ix0 = n0 % e.nx, rest = n0 / e.nx;
+        ld8a(r.x + ix0, v);
+        float2 sc = make_float2(1.f, 0.f);
+        if (e.ny > 1) sc = __ldg(r.y + rest % e.ny);
+        if (e.nz > 1) sc = cmulf(sc, __ldg(r.z + rest / e.ny));
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = cmulf(v[t], sc);
+        if (r.b) {
+            float2 w[8];
+            ld8a(r.b + n0, w);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = cmulf(v[t], w[t]);
+        }
+        if (r.c) {
+            float2 w[8];
+            ld8a(r.c + n0, w);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = cmulf(v[t], w[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = conjf2(v[t]);
+        return;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int64_t n = n0 + t;
+        if (n < ke) {
+            const int* g = e.vox_ijk + 3 * n;
+            float2 a = __ldg(r.x + __ldg(g));
+            if (e.ny > 1) a = cmulf(a, __ldg(r.y + __ldg(g + 1)));
+            if (e.nz > 1) a = cmulf(a, __ldg(r.z + __ldg(g + 2)));
+            if (r.b) a = cmulf(a, __ldg(r.b + n));
+            if (r.c) a = cmulf(a, __ldg(r.c + n));
+            v[t] = conjf2(a);
+        } else {
+            v[t] = make_float2(0.f, 0.f);
+        }
+    }
 }
 
 // ------------------------------------------------------------------ Gram (Eq. 6, Eq. 11)
@@ -82,15 +189,15 @@ struct GramTC {
         ke = e.Mk;
         return j0 <= i0 + BM - 1;  // tile touches the lower triangle
     }
-    __device__ void a8(int64_t i, int64_t k0, int64_t ke, float2 (&v)[8]) const {
+    __device__ VoxRow row_a(int64_t i) const { return vox_row(e, i); }
+    __device__ VoxRow row_b(int64_t j) const { return vox_row(e, j); }
+    __device__ void a8(const VoxRow& r, int64_t k0, int64_t ke, float2 (&v)[8]) const {
+        gen_a8_samples(e, r, k0, ke, v);
 #pragma unroll
-        for (int t = 0; t < 8; ++t)
-            v[t] = (i < e.N && k0 + t < ke) ? conjf2(gen_a32(e, k0 + t, i)) : make_float2(0.f, 0.f);
+        for (int t = 0; t < 8; ++t) v[t].y = -v[t].y;
     }
-    __device__ void b8(int64_t j, int64_t k0, int64_t ke, float2 (&v)[8]) const {
-#pragma unroll
-        for (int t = 0; t < 8; ++t)
-            v[t] = (j < e.N && k0 + t < ke) ? gen_a32(e, k0 + t, j) : make_float2(0.f, 0.f);
+    __device__ void b8(const VoxRow& r, int64_t k0, int64_t ke, float2 (&v)[8]) const {
+        gen_a8_samples(e, r, k0, ke, v);
     }
     __device__ bool row_ok(int64_t i) const { return i < e.N; }
     __device__ bool col_ok(int64_t j) const { return j < e.N; }
@@ -141,8 +248,10 @@ struct TrsmTC {
         ke = nbk;
         return i0 < N;
     }
-    __device__ void a8(int64_t i, int64_t k, int64_t ke, float2 (&v)[8]) const {
-        load8f(P + i * ldp + k, i < N ? (int)(ke - k) : 0, v);
+    __device__ RowPtr row_a(int64_t i) const { return RowPtr{P + (i < N ? i : 0) * ldp, i < N}; }
+    __device__ int64_t row_b(int64_t j) const { return j; }
+    __device__ void a8(const RowPtr& r, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(r.p + k, r.ok ? (int)(ke - k) : 0, v);
     }
     __device__ void b8(int64_t j, int64_t k, int64_t ke, float2 (&v)[8]) const {
 #pragma unroll
@@ -170,11 +279,13 @@ struct HerkTC {
         ke = nbk;
         return i0 < N && j0 < N && j0 <= i0 + BM - 1;
     }
-    __device__ void a8(int64_t i, int64_t k, int64_t ke, float2 (&v)[8]) const {
-        load8f(P + i * ldp + k, i < N ? (int)(ke - k) : 0, v);
+    __device__ RowPtr row_a(int64_t i) const { return RowPtr{P + (i < N ? i : 0) * ldp, i < N}; }
+    __device__ RowPtr row_b(int64_t j) const { return RowPtr{P + (j < N ? j : 0) * ldp, j < N}; }
+    __device__ void a8(const RowPtr& r, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(r.p + k, r.ok ? (int)(ke - k) : 0, v);
     }
-    __device__ void b8(int64_t j, int64_t k, int64_t ke, float2 (&v)[8]) const {
-        load8f(P + j * ldp + k, j < N ? (int)(ke - k) : 0, v);
+    __device__ void b8(const RowPtr& r, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(r.p + k, r.ok ? (int)(ke - k) : 0, v);
 #pragma unroll
         for (int t = 0; t < 8; ++t) v[t].y = -v[t].y;
     }
@@ -200,6 +311,8 @@ struct TrtriDiagTC {
         ke = nbk;
         return true;
     }
+    __device__ int64_t row_a(int64_t i) const { return i; }
+    __device__ int64_t row_b(int64_t j) const { return j; }
     __device__ void a8(int64_t i, int64_t k, int64_t ke, float2 (&v)[8]) const {
 #pragma unroll
         for (int t = 0; t < 8; ++t)
@@ -236,8 +349,10 @@ struct TrtriUpdTC {
         ke = nbk;
         return i0 < N;
     }
-    __device__ void a8(int64_t i, int64_t k, int64_t ke, float2 (&v)[8]) const {
-        load8f(L32 + i * ldl + k0 + k, i < N ? (int)(ke - k) : 0, v);
+    __device__ RowPtr row_a(int64_t i) const { return RowPtr{L32 + (i < N ? i : 0) * ldl + k0, i < N}; }
+    __device__ int64_t row_b(int64_t j) const { return j; }
+    __device__ void a8(const RowPtr& r, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(r.p + k, r.ok ? (int)(ke - k) : 0, v);
     }
     __device__ void b8(int64_t j, int64_t k, int64_t ke, float2 (&v)[8]) const {
 #pragma unroll
@@ -271,19 +386,24 @@ struct ReconStep1TC {
         ke = i0 + BM < e.N ? i0 + BM : e.N;  // W is lower triangular
         return true;
     }
-    __device__ void a8(int64_t i, int64_t k, int64_t ke, float2 (&v)[8]) const {
-        load8f(W32 + i * e.N + k, i < e.N ? (int)(ke - k) : 0, v);
+    __device__ RowPtr row_a(int64_t i) const { return RowPtr{W32 + (i < e.N ? i : 0) * e.N, i < e.N}; }
+    __device__ EhCol row_b(int64_t j) const { return eh_col(e, j); }
+    __device__ void a8(const RowPtr& r, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(r.p + k, r.ok ? (int)(ke - k) : 0, v);
     }
-    __device__ void b8(int64_t j, int64_t k, int64_t ke, float2 (&v)[8]) const { gen_eh8(e, j, k, ke, v); }
+    __device__ void b8(const EhCol& c, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        gen_eh8_voxels(e, c, k, ke, v);
+    }
     __device__ bool row_ok(int64_t i) const { return i < e.N; }
     __device__ bool col_ok(int64_t j) const { return j < e.Mk * e.C; }
     __device__ void store(int64_t i, int64_t j, float2 v) const { T[i * (e.Mk * e.C) + j] = v; }
 };
 
-// R[n][j] = sum_{k >= n} conj(W[k][n]) T[k][j]; row tiles vary fastest so the
-// CTAs in flight share one column panel of T in L2.
+// R[n][j] = sum_{k >= n} conj(W[k][n]) T[k][j] with WT = W^T (so W's column n is
+// WT's row n, read contiguously); row tiles vary fastest so the CTAs in flight
+// share one column panel of T in L2.
 struct ReconStep2TC {
-    const float2* W32;
+    const float2* WT32;
     const float2* T;
     float2* R;
     int64_t N, M;
@@ -294,13 +414,15 @@ struct ReconStep2TC {
         ke = N;
         return true;
     }
-    __device__ void a8(int64_t i, int64_t k, int64_t ke, float2 (&v)[8]) const {
-        load8col(W32 + k * N + i, N, i < N ? (int)(ke - k) : 0, v);
+    __device__ RowPtr row_a(int64_t i) const { return RowPtr{WT32 + (i < N ? i : 0) * N, i < N}; }
+    __device__ RowPtr row_b(int64_t j) const { return RowPtr{T + (j < M ? j : 0), j < M}; }
+    __device__ void a8(const RowPtr& r, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(r.p + k, r.ok ? (int)(ke - k) : 0, v);
 #pragma unroll
         for (int t = 0; t < 8; ++t) v[t].y = -v[t].y;
     }
-    __device__ void b8(int64_t j, int64_t k, int64_t ke, float2 (&v)[8]) const {
-        load8col(T + k * M + j, M, j < M ? (int)(ke - k) : 0, v);
+    __device__ void b8(const RowPtr& r, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8col(r.p + k * M, M, r.ok ? (int)(ke - k) : 0, v);
     }
     __device__ bool row_ok(int64_t i) const { return i < N; }
     __device__ bool col_ok(int64_t j) const { return j < M; }
@@ -382,13 +504,13 @@ cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, 
     return launch_to_f32(W, W32, N * N, s);
 }
 
-cudaError_t launch_recon_tc(const EncodeDev& e, const float2* W32, float2* T, int slices, float2* R,
-                            DevStatus* st, cudaStream_t s) {
+cudaError_t launch_recon_tc(const EncodeDev& e, const float2* W32, const float2* WT32, float2* T, int slices,
+                            float2* R, DevStatus* st, cudaStream_t s) {
     const int64_t M = e.Mk * e.C;
     tc::ReconStep1TC p1{e, W32, T};
     cudaError_t err = run(p1, dim3(cdiv(M, tc::BN), cdiv(e.N, tc::BM)), slices, st, 2, s);
     if (err != cudaSuccess) return err;
-    tc::ReconStep2TC p2{W32, T, R, e.N, M};
+    tc::ReconStep2TC p2{WT32, T, R, e.N, M};
     return run(p2, dim3(cdiv(e.N, tc::BM), cdiv(M, tc::BN)), slices, st, 8, s);
 }
 

@@ -216,18 +216,33 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double2* G, int64_t ld, int6
         }
         __syncthreads();
     }
-    // X = A^-1 by forward substitution, one column per thread
-    if (tid < NB) {
-        int c = tid;
+    // X = A^-1 by forward substitution down each column. Four lanes of one
+    // warp share a column: each sums every fourth term of the row's dot
+    // product (independent FMA chains), a shuffle combines them, and the
+    // column's X values stay visible inside the warp.
+    {
+        const int c = tid >> 2, q = tid & 3;
         for (int i = 0; i < NB; ++i) {
-            if (i < c) { X[i * NB + c] = make_double2(0.0, 0.0); continue; }
-            double2 acc = make_double2(i == c ? 1.0 : 0.0, 0.0);
-            for (int k = c; k < i; ++k) {
-                double2 l = A[i * NB + k];
-                zfma(acc, make_double2(-l.x, -l.y), X[k * NB + c]);
+            double2 part = make_double2(0.0, 0.0);
+            if (i > c) {
+                for (int k = c + q; k < i; k += 4) {
+                    const double2 l = A[i * NB + k];
+                    zfma(part, l, X[k * NB + c]);
+                }
             }
-            double dii = A[i * NB + i].x;
-            X[i * NB + c] = make_double2(acc.x / dii, acc.y / dii);
+            part.x += __shfl_xor_sync(0xffffffffu, part.x, 1);
+            part.y += __shfl_xor_sync(0xffffffffu, part.y, 1);
+            part.x += __shfl_xor_sync(0xffffffffu, part.x, 2);
+            part.y += __shfl_xor_sync(0xffffffffu, part.y, 2);
+            if (q == 0) {
+                double2 v = make_double2(0.0, 0.0);
+                if (i >= c) {
+                    const double dii = A[i * NB + i].x;
+                    v = make_double2(((i == c ? 1.0 : 0.0) - part.x) / dii, -part.y / dii);
+                }
+                X[i * NB + c] = v;
+            }
+            __syncwarp();
         }
     }
     __syncthreads();
