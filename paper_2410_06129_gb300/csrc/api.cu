@@ -176,6 +176,9 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
     int* vox;
     AL(vox, sizeof(int) * 3 * p->N, "vox");
     AL(p->st, sizeof(DevStatus), "status");
+    CKC(cudaMallocHost((void**)&p->st_host, sizeof(DevStatus)));
+    *p->st_host = DevStatus{};
+    p->st_host->not_pd_pivot = INT_MAX;
     e.ex = ex; e.ey = ey; e.ez = ez;
     e.ex32 = ex32; e.ey32 = ey32; e.ez32 = ez32;
     e.vox_ijk = vox;
@@ -342,6 +345,7 @@ pinv_status pinv_build(pinv_plan* p, void* stream) {
             CK(cudaFreeAsync(WT32, s));
             CK(cudaFreeAsync(T, s));
         }
+        CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
         CK(cudaEventRecord(p->ev[5], s));
         p->built = true;
         return PINV_OK;
@@ -357,6 +361,7 @@ pinv_status pinv_build(pinv_plan* p, void* stream) {
     }
     CK(cudaEventRecord(p->ev[4], s));
     if (p->recon) CK(launch_recon64(p->enc, p->Ginv, ld, (double2*)p->R, s));
+    CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(p->ev[5], s));
     p->built = true;
     return PINV_OK;
@@ -364,10 +369,11 @@ pinv_status pinv_build(pinv_plan* p, void* stream) {
 
 pinv_status pinv_plan_sync(pinv_plan* p) {
     if (!p) return fail(PINV_ERR_INVALID_ARG, "null plan");
+    // the build's last step copies the status word to pinned host memory
+    // before its completion event, so no device-wide synchronisation is needed
     CK(cudaEventSynchronize(p->ev[5]));
-    CK(cudaDeviceSynchronize());
-    DevStatus h{};
-    CK(cudaMemcpy(&h, p->st, sizeof(h), cudaMemcpyDeviceToHost));
+    CK(cudaGetLastError());
+    const DevStatus h = *p->st_host;
     p->info = -1;
     if (h.not_pd_pivot != INT_MAX) {
         p->info = h.not_pd_pivot;
@@ -384,135 +390,6 @@ pinv_status pinv_plan_sync(pinv_plan* p) {
         p->built = false;
         return fail(PINV_ERR_INTERNAL, "device error code " + std::to_string(h.error_code));
     }
-    return PINV_OK;
-}
-
-static pinv_status ensure_scratch(pinv_plan* p, int64_t F) {
-    if (F <= p->scratch_frames) return PINV_OK;
-    for (void* q : p->scratch) cudaFree(q);
-    p->scratch.clear();
-    auto get = [&](void** q, size_t n) -> pinv_status {
-        cudaError_t e = cudaMalloc(q, n);
-        if (e != cudaSuccess) return cuda_fail(e, "apply scratch");
-        p->scratch.push_back(*q);
-        return PINV_OK;
-    };
-    pinv_status st;
-    if ((st = get((void**)&p->d128, sizeof(double2) * F * p->M)) != PINV_OK) return st;
-    if ((st = get((void**)&p->u128, sizeof(double2) * F * p->M)) != PINV_OK) return st;
-    if ((st = get((void**)&p->x128, sizeof(double2) * F * p->N)) != PINV_OK) return st;
-    if ((st = get((void**)&p->r128, sizeof(double2) * F * p->N)) != PINV_OK) return st;
-    if ((st = get((void**)&p->d64, sizeof(float2) * F * p->M)) != PINV_OK) return st;
-    if ((st = get((void**)&p->x64, sizeof(float2) * F * p->N)) != PINV_OK) return st;
-    if ((st = get((void**)&p->norms, sizeof(double) * 2 * F)) != PINV_OK) return st;
-    p->scratch_frames = F;
-    return PINV_OK;
-}
-
-pinv_status pinv_apply(pinv_plan* p, const void* d_data, void* d_image, int64_t F, int dtype,
-                       void* stream) {
-    g_err.clear();
-    if (!p) return fail(PINV_ERR_INVALID_ARG, "null plan");
-    if (F < 0) return fail(PINV_ERR_INVALID_ARG, "n_frames < 0");
-    if (dtype != PINV_C64 && dtype != PINV_C128) return fail(PINV_ERR_INVALID_ARG, "dtype");
-    if (!p->built) return fail(PINV_ERR_NOT_BUILT, "plan not built");
-    if (F == 0) return PINV_OK;
-    if (!d_data || !d_image) return fail(PINV_ERR_INVALID_ARG, "null data or image");
-    cudaStream_t s = (cudaStream_t)stream;
-    pinv_status st = ensure_scratch(p, F);
-    if (st != PINV_OK) return st;
-    const int64_t N = p->N, M = p->M;
-    const bool mixed = p->precision != PINV_FP64;
-    p->last_refine_iters = 0;
-    p->last_refine_resid = 0;
-
-    // FP64 data view
-    const double2* D = nullptr;
-    auto need_d128 = [&]() -> pinv_status {
-        if (D) return PINV_OK;
-        if (dtype == PINV_C128) D = (const double2*)d_data;
-        else {
-            CK(launch_c64_to_c128((const float2*)d_data, p->d128, F * M, s));
-            D = p->d128;
-        }
-        return PINV_OK;
-    };
-    double2* X = dtype == PINV_C128 ? (double2*)d_image : p->x128;
-
-    if (!mixed) {
-        if ((st = need_d128()) != PINV_OK) return st;
-        if (p->recon) {
-            CK(launch_apply64((const double2*)p->R, N, M, D, F, X, s));
-        } else {
-            CK(launch_adjoint64(p->enc, D, F, 0.0, nullptr, p->r128, s));
-            CK(launch_hemv64(p->Ginv, N, N, p->r128, F, nullptr, X, s));
-        }
-    } else {
-        // initial image from the mixed-precision operator
-        if (p->recon) {
-            const float2* D32 = (const float2*)d_data;
-            if (dtype == PINV_C128) {
-                CK(launch_c128_to_c64((const double2*)d_data, p->d64, F * M, s));
-                D32 = p->d64;
-            }
-            CK(launch_apply32((const float2*)p->R, N, M, D32, F, p->x64, s));
-            CK(launch_c64_to_c128(p->x64, X, F * N, s));
-        } else {
-            // factor-only: x = W^H (W (E^H d)) with the mixed factor's inverse W
-            if ((st = need_d128()) != PINV_OK) return st;
-            CK(launch_adjoint64(p->enc, D, F, 0.0, nullptr, p->r128, s));
-            CK(launch_trmv64(p->W, N, p->r128, F, p->u128, s));
-            CK(launch_trmv_h64(p->W, N, p->u128, F, nullptr, X, s));
-        }
-    }
-    {
-        // FP64 residual refinement: r = E^H (d - E x) - lambda x, x += Ginv r.
-        // Mixed plans need it to reach FP64-level accuracy; FP64 plans may use
-        // it to remove the explicit inverse's extra rounding (kappa(G) u).
-        if (p->refine_iters > 0) {
-            if ((st = need_d128()) != PINV_OK) return st;
-            // The stopping rule ||r|| / ||E^H d|| <= tol needs E^H d and a host
-            // read per step; with tol == 0 a fixed number of steps runs without either.
-            const bool stop_rule = p->refine_tol > 0.0;
-            std::vector<double> h(2 * F);
-            if (stop_rule) {
-                CK(launch_adjoint64(p->enc, D, F, 0.0, nullptr, p->r128, s));  // b = E^H d
-                CK(launch_frame_norms(p->r128, F, N, p->norms + F, s));
-            }
-            const bool dfres = mixed && p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT;
-            for (int it = 0; it < p->refine_iters; ++it) {
-                if (dfres) {
-                    CK(launch_forward_df(p->enc, X, F, D, p->u128, s));      // u = d - E x
-                    CK(launch_adjoint_df(p->enc, p->u128, F, p->lambda_abs, X, p->r128, s));
-                } else {
-                    CK(launch_forward64(p->enc, X, F, D, p->u128, s));       // u = d - E x
-                    CK(launch_adjoint64(p->enc, p->u128, F, p->lambda_abs, X, p->r128, s));
-                }
-                if (stop_rule) CK(launch_frame_norms(p->r128, F, N, p->norms, s));
-                if (dfres) {
-                    // the correction only preconditions the next residual: FP32 W suffices
-                    CK(launch_correct32(p->W32, N, p->r128, F, p->x64, X, s));
-                } else if (mixed) {
-                    // x += W^H (W r) in FP64: never through an explicitly formed
-                    // low-precision G^-1, whose error the correction would amplify by kappa(G)
-                    CK(launch_trmv64(p->W, N, p->r128, F, p->u128, s));
-                    CK(launch_trmv_h64(p->W, N, p->u128, F, X, X, s));
-                } else {
-                    CK(launch_hemv64(p->Ginv, N, N, p->r128, F, X, X, s));  // x += Ginv r
-                }
-                p->last_refine_iters = it + 1;
-                if (!stop_rule) continue;
-                CK(cudaMemcpyAsync(h.data(), p->norms, sizeof(double) * 2 * F, cudaMemcpyDeviceToHost, s));
-                CK(cudaStreamSynchronize(s));
-                double worst = 0;
-                for (int64_t f = 0; f < F; ++f)
-                    worst = std::max(worst, std::sqrt(h[f] / std::max(h[F + f], 1e-300)));
-                p->last_refine_resid = worst;
-                if (worst <= p->refine_tol) break;
-            }
-        }
-    }
-    if (dtype == PINV_C64) CK(launch_c128_to_c64(X, (float2*)d_image, F * N, s));
     return PINV_OK;
 }
 
@@ -578,8 +455,7 @@ pinv_status pinv_plan_info(const pinv_plan* p, pinv_plan_info_t* o) {
         o->ms_chol = t[2];
         o->ms_inverse = t[3];
         o->ms_recon = t[4];
-        DevStatus h{};
-        CK(cudaMemcpy(&h, p->st, sizeof(h), cudaMemcpyDeviceToHost));
+        const DevStatus h = *p->st_host;
         o->min_pivot = h.min_pivot;
         o->max_pivot = h.max_pivot;
     }

@@ -1,0 +1,198 @@
+// Applying a built plan: image = Recon x data (Eq. 3), or G^-1 E^H data for
+// factor-only plans (Section 3.3), followed by residual refinement.
+//
+// apply_impl allocates nothing: its scratch comes from the caller, carved
+// from one contiguous region by apply_scratch_layout. pinv_apply uses a
+// plan-owned region grown on demand, pinv_apply_noalloc a fixed device array,
+// and the serving loop one region per slot.
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "plan_impl.h"
+
+namespace pinv {
+
+namespace {
+pinv_status cuda_err(cudaError_t e, const char* where) {
+    return set_error(e == cudaErrorMemoryAllocation ? PINV_ERR_OOM : PINV_ERR_CUDA,
+                     std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CKA(call)                                              \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_err(e_, #call);     \
+    } while (0)
+
+// Sequential 256-byte-aligned carving of a region (base == nullptr: sizing only).
+struct Carver {
+    unsigned char* base;
+    size_t used = 0;
+    template <class T>
+    T* take(size_t count) {
+        used = (used + 255) & ~size_t(255);
+        T* q = reinterpret_cast<T*>(base ? base + used : nullptr);
+        used += count * sizeof(T);
+        return q;
+    }
+};
+}  // namespace
+
+size_t apply_scratch_layout(const pinv_plan* p, int64_t F, int dtype, void* base, ApplyScratch* sc) {
+    const int64_t N = p->N, M = p->M;
+    const bool mixed = p->precision != PINV_FP64;
+    const bool refine = p->refine_iters > 0;
+    const bool stop_rule = refine && p->refine_tol > 0.0;
+    const bool dfres = mixed && p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT;
+    // which buffers an apply needs: FP64 copy of c64 data, FP64 image for c64
+    // output, the refinement's data-space and image-space residuals, the mixed
+    // path's c64 data / image / correction buffers, and the per-frame norms
+    const bool need_d128 = dtype == PINV_C64 && (!mixed || !p->recon || refine);
+    const bool need_x128 = dtype == PINV_C64;
+    const bool need_u128 = refine || (mixed && !p->recon);
+    const bool need_r128 = refine || !p->recon;
+    const bool need_d64 = mixed && p->recon && dtype == PINV_C128;
+    const bool need_x64 = mixed && (p->recon || (refine && dfres));
+    Carver cv{static_cast<unsigned char*>(base)};
+    ApplyScratch s{};
+    s.d128 = need_d128 ? cv.take<double2>((size_t)(F * M)) : nullptr;
+    s.x128 = need_x128 ? cv.take<double2>((size_t)(F * N)) : nullptr;
+    s.u128 = need_u128 ? cv.take<double2>((size_t)(F * M)) : nullptr;
+    s.r128 = need_r128 ? cv.take<double2>((size_t)(F * N)) : nullptr;
+    s.d64 = need_d64 ? cv.take<float2>((size_t)(F * M)) : nullptr;
+    s.x64 = need_x64 ? cv.take<float2>((size_t)(F * N)) : nullptr;
+    s.norms = stop_rule ? cv.take<double>((size_t)(2 * F)) : nullptr;
+    if (sc) *sc = s;
+    return cv.used;
+}
+
+pinv_status apply_check(const pinv_plan* p, const void* d_data, void* d_image, int64_t F, int dtype) {
+    if (!p) return set_error(PINV_ERR_INVALID_ARG, "null plan");
+    if (F < 0) return set_error(PINV_ERR_INVALID_ARG, "n_frames < 0");
+    if (dtype != PINV_C64 && dtype != PINV_C128) return set_error(PINV_ERR_INVALID_ARG, "dtype");
+    if (!p->built) return set_error(PINV_ERR_NOT_BUILT, "plan not built");
+    if (F > 0 && (!d_data || !d_image)) return set_error(PINV_ERR_INVALID_ARG, "null data or image");
+    return PINV_OK;
+}
+
+pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t F, int dtype, cudaStream_t s,
+                       const ApplyScratch& sc) {
+    if (F == 0) return PINV_OK;
+    const int64_t N = p->N, M = p->M;
+    const bool mixed = p->precision != PINV_FP64;
+    const bool refine = p->refine_iters > 0;
+    const bool stop_rule = refine && p->refine_tol > 0.0;
+    const bool dfres = mixed && p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT;
+    p->last_refine_iters = 0;
+    p->last_refine_resid = 0;
+
+    // FP64 view of the data
+    const double2* D = nullptr;
+    if (dtype == PINV_C128) {
+        D = (const double2*)d_data;
+    } else if (sc.d128) {
+        CKA(launch_c64_to_c128((const float2*)d_data, sc.d128, F * M, s));
+        D = sc.d128;
+    }
+    double2* X = dtype == PINV_C128 ? (double2*)d_image : sc.x128;
+
+    if (!mixed) {
+        if (p->recon) {
+            CKA(launch_apply64((const double2*)p->R, N, M, D, F, X, s));
+        } else {
+            CKA(launch_adjoint64(p->enc, D, F, 0.0, nullptr, sc.r128, s));
+            CKA(launch_hemv64(p->Ginv, N, N, sc.r128, F, nullptr, X, s));
+        }
+    } else if (p->recon) {
+        // initial image from the mixed-precision Recon
+        const float2* D32 = (const float2*)d_data;
+        if (dtype == PINV_C128) {
+            CKA(launch_c128_to_c64((const double2*)d_data, sc.d64, F * M, s));
+            D32 = sc.d64;
+        }
+        CKA(launch_apply32((const float2*)p->R, N, M, D32, F, sc.x64, s));
+        CKA(launch_c64_to_c128(sc.x64, X, F * N, s));
+    } else {
+        // factor-only: x = W^H (W (E^H d)) with the mixed factor's inverse W
+        CKA(launch_adjoint64(p->enc, D, F, 0.0, nullptr, sc.r128, s));
+        CKA(launch_trmv64(p->W, N, sc.r128, F, sc.u128, s));
+        CKA(launch_trmv_h64(p->W, N, sc.u128, F, nullptr, X, s));
+    }
+
+    // Residual refinement: r = E^H (d - E x) - lambda x, then x += G^-1 r.
+    // Mixed plans need it to reach FP64-level accuracy; FP64 plans may use it
+    // to remove the explicit inverse's extra rounding (kappa(G) u). With
+    // refine_tol == 0 a fixed number of steps runs without host reads.
+    if (refine) {
+        if (stop_rule) {
+            CKA(launch_adjoint64(p->enc, D, F, 0.0, nullptr, sc.r128, s));  // b = E^H d
+            CKA(launch_frame_norms(sc.r128, F, N, sc.norms + F, s));
+        }
+        for (int it = 0; it < p->refine_iters; ++it) {
+            if (dfres) {
+                CKA(launch_forward_df(p->enc, X, F, D, sc.u128, s));  // u = d - E x
+                CKA(launch_adjoint_df(p->enc, sc.u128, F, p->lambda_abs, X, sc.r128, s));
+            } else {
+                CKA(launch_forward64(p->enc, X, F, D, sc.u128, s));
+                CKA(launch_adjoint64(p->enc, sc.u128, F, p->lambda_abs, X, sc.r128, s));
+            }
+            if (stop_rule) CKA(launch_frame_norms(sc.r128, F, N, sc.norms, s));
+            if (dfres) {
+                // the correction only preconditions the next residual: FP32 W suffices
+                CKA(launch_correct32(p->W32, N, sc.r128, F, sc.x64, X, s));
+            } else if (mixed) {
+                // x += W^H (W r) in FP64: never through an explicitly formed low-precision
+                // G^-1, whose error the correction would amplify by kappa(G)
+                CKA(launch_trmv64(p->W, N, sc.r128, F, sc.u128, s));
+                CKA(launch_trmv_h64(p->W, N, sc.u128, F, X, X, s));
+            } else {
+                CKA(launch_hemv64(p->Ginv, N, N, sc.r128, F, X, X, s));
+            }
+            p->last_refine_iters = it + 1;
+            if (!stop_rule) continue;
+            // per-frame ||r|| / ||E^H d||, read back in fixed-size chunks (no allocation)
+            double worst = 0.0, hn[128], hb[128];
+            for (int64_t f0 = 0; f0 < F; f0 += 128) {
+                const int64_t nf = std::min<int64_t>(128, F - f0);
+                CKA(cudaMemcpyAsync(hn, sc.norms + f0, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
+                CKA(cudaMemcpyAsync(hb, sc.norms + F + f0, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
+                CKA(cudaStreamSynchronize(s));
+                for (int64_t f = 0; f < nf; ++f)
+                    worst = std::max(worst, std::sqrt(hn[f] / std::max(hb[f], 1e-300)));
+            }
+            p->last_refine_resid = worst;
+            if (worst <= p->refine_tol) break;
+        }
+    }
+    if (dtype == PINV_C64) CKA(launch_c128_to_c64(X, (float2*)d_image, F * N, s));
+    return PINV_OK;
+}
+
+}  // namespace pinv
+
+using namespace pinv;
+
+extern "C" pinv_status pinv_apply(pinv_plan* p, const void* d_data, void* d_image, int64_t F, int dtype,
+                                  void* stream) {
+    pinv_status st = apply_check(p, d_data, d_image, F, dtype);
+    if (st != PINV_OK || F == 0) return st;
+    const size_t need = apply_scratch_layout(p, F, dtype, nullptr, nullptr);
+    if (need > p->scratch_bytes) {
+        // grow the plan-owned scratch (stream-ordered with this apply)
+        if (p->scratch_buf) {
+            cudaError_t e = cudaFree(p->scratch_buf);
+            p->scratch_buf = nullptr;
+            p->scratch_bytes = 0;
+            if (e != cudaSuccess) return cuda_err(e, "cudaFree(apply scratch)");
+        }
+        cudaError_t e = cudaMalloc(&p->scratch_buf, need);
+        if (e != cudaSuccess) {
+            p->scratch_buf = nullptr;
+            return cuda_err(e, "cudaMalloc(apply scratch)");
+        }
+        p->scratch_bytes = need;
+    }
+    ApplyScratch sc;
+    apply_scratch_layout(p, F, dtype, p->scratch_buf, &sc);
+    return apply_impl(p, d_data, d_image, F, dtype, (cudaStream_t)stream, sc);
+}

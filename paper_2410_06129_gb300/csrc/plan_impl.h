@@ -1,4 +1,5 @@
-// Definition of the opaque pinv_plan handle, shared by the C ABI's translation units.
+// Definition of the opaque pinv_plan handle and the apply entry points shared
+// by the C ABI's translation units.
 #pragma once
 
 #include <string>
@@ -6,9 +7,32 @@
 
 #include "pinv_internal.h"
 
+struct pinv_plan;
+
 namespace pinv {
 // Record an error message for pinv_last_error() and return the status.
 pinv_status set_error(pinv_status st, const std::string& msg);
+
+// Scratch buffers of one apply, carved from one contiguous device region.
+struct ApplyScratch {
+    double2* d128;  // FP64 copy of c64 data [F][M]
+    double2* x128;  // FP64 image for c64 output [F][N]
+    double2* u128;  // data-space residual / trmv temporary [F][M]
+    double2* r128;  // image-space residual [F][N]
+    float2* d64;    // c64 copy of c128 data [F][M]
+    float2* x64;    // c64 image / FP32 correction temporary [F][N]
+    double* norms;  // per-frame squared norms [2F]
+};
+// Bytes an apply of F frames of `dtype` needs; with base != nullptr also
+// carves the region at base into *sc.
+size_t apply_scratch_layout(const pinv_plan* p, int64_t F, int dtype, void* base, ApplyScratch* sc);
+// Argument checks shared by the apply entry points.
+pinv_status apply_check(const pinv_plan* p, const void* d_data, void* d_image, int64_t F, int dtype);
+// image = Recon x data (or G^-1 E^H data) plus refinement on stream s, using
+// only the given scratch: no allocation, no host synchronisation unless the
+// refinement's stopping rule (refine_tol > 0) is on.
+pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t F, int dtype, cudaStream_t s,
+                       const ApplyScratch& sc);
 }  // namespace pinv
 
 struct pinv_plan {
@@ -38,14 +62,12 @@ struct pinv_plan {
     double2* W = nullptr;      // L^-1, lower (mixed plans)
     float2* W32 = nullptr;     // FP32 copy of W (mixed plans)
     void* R = nullptr;         // Recon [N][M], c128 (FP64) or c64 (mixed)
-    pinv::DevStatus* st = nullptr;
+    pinv::DevStatus* st = nullptr;        // device status word
+    pinv::DevStatus* st_host = nullptr;   // pinned copy, written at the end of each build
 
-    // apply scratch (grown on demand)
-    int64_t scratch_frames = 0;
-    double2 *d128 = nullptr, *x128 = nullptr, *u128 = nullptr, *r128 = nullptr;
-    float2 *d64 = nullptr, *x64 = nullptr;
-    double* norms = nullptr;
-    std::vector<void*> scratch;
+    // pinv_apply's scratch region, grown on demand
+    void* scratch_buf = nullptr;
+    size_t scratch_bytes = 0;
 
     cudaEvent_t ev[6] = {};
     int last_refine_iters = 0;
@@ -58,18 +80,18 @@ struct pinv_plan {
         if (e != cudaSuccess) {
             *p = nullptr;
             return pinv::set_error(e == cudaErrorMemoryAllocation ? PINV_ERR_OOM : PINV_ERR_CUDA,
-                        std::string("cudaMalloc(") + what + ", " + std::to_string(n) + " B): " +
-                            cudaGetErrorString(e));
+                                   std::string("cudaMalloc(") + what + ", " + std::to_string(n) + " B): " +
+                                       cudaGetErrorString(e));
         }
         allocs.push_back(*p);
         bytes += n;
         return PINV_OK;
     }
     ~pinv_plan() {
-        for (void* p : scratch) cudaFree(p);
+        if (scratch_buf) cudaFree(scratch_buf);
         for (void* p : allocs) cudaFree(p);
+        if (st_host) cudaFreeHost(st_host);
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
     }
 };
-

@@ -188,6 +188,11 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double2* G, int64_t ld, int6
         A[e] = v;
     }
     __syncthreads();
+    // Right-looking, two barriers per column. Phase 1: thread 0 takes the
+    // pivot (one rsqrt, no division) while the other threads scale the
+    // previous column by its reciprocal pivot. Phase 2: the trailing update
+    // uses the still unscaled column j with the factor 1 / d_j.
+    __shared__ double rdiag[NB];  // 1 / L_jj
     for (int j = 0; j < NB; ++j) {
         if (tid == 0) {
             double d = A[j * NB + j].x;
@@ -196,21 +201,25 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double2* G, int64_t ld, int6
                 bad = 1;
                 d = 1.0;
             }
-            A[j * NB + j] = make_double2(sqrt(d), 0.0);
+            const double r = rsqrt(d);
+            A[j * NB + j] = make_double2(d * r, 0.0);
+            rdiag[j] = r;
+        } else if (j > 0) {
+            const double r = rdiag[j - 1];
+            for (int i = j + tid - 1; i < NB; i += 255) {
+                const double2 v = A[i * NB + j - 1];
+                A[i * NB + j - 1] = make_double2(v.x * r, v.y * r);
+            }
         }
         __syncthreads();
-        double dj = A[j * NB + j].x;
-        for (int i = j + 1 + tid; i < NB; i += 256) {
-            double2 v = A[i * NB + j];
-            A[i * NB + j] = make_double2(v.x / dj, v.y / dj);
-        }
-        __syncthreads();
-        int rem = NB - j - 1;
+        const double r2 = rdiag[j] * rdiag[j];
+        const int rem = NB - j - 1;
         for (int e = tid; e < rem * rem; e += 256) {
-            int i = j + 1 + e / rem, k = j + 1 + e % rem;
+            const int i = j + 1 + e / rem, k = j + 1 + e % rem;
             if (k <= i) {
+                const double2 a = A[i * NB + j];
                 double2 v = A[i * NB + k];
-                zfma(v, make_double2(-A[i * NB + j].x, -A[i * NB + j].y), zconj(A[k * NB + j]));
+                zfma(v, make_double2(-a.x * r2, -a.y * r2), zconj(A[k * NB + j]));
                 A[i * NB + k] = v;
             }
         }
@@ -237,8 +246,8 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double2* G, int64_t ld, int6
             if (q == 0) {
                 double2 v = make_double2(0.0, 0.0);
                 if (i >= c) {
-                    const double dii = A[i * NB + i].x;
-                    v = make_double2(((i == c ? 1.0 : 0.0) - part.x) / dii, -part.y / dii);
+                    const double ri = rdiag[i];
+                    v = make_double2(((i == c ? 1.0 : 0.0) - part.x) * ri, -part.y * ri);
                 }
                 X[i * NB + c] = v;
             }
