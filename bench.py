@@ -100,6 +100,13 @@ def _dist():
     return ws, rank, local
 
 
+def _footprint(d):
+    """Resident bytes of a mixed serving plan: Recon (c64), G/L, W and its FP32 copy."""
+    N = d["side"] ** 2
+    M = d["samples"] * d["n_coils"]
+    return N * M * 8 + N * N * 40 + (64 << 20)
+
+
 def oracle_sample_step(side=32):
     """One bounded sample of the workload through the FP64 oracle.
 
@@ -156,6 +163,72 @@ def run_reference(args):
     return 0
 
 
+SERVE_BUDGET_FULL = 120e9  # bytes of resident plans for the full serving workload
+
+
+def run_serve(prec, refine, side_div, rate_hz, duration_s, budget, max_slots, recon_mode,
+              check_plans=0, seed=4100):
+    """Serving loop on the Poisson trace of the 32-plan serving workload.
+
+    Requests arrive at their trace times (host thread sleeping until each
+    arrival), each one of 32 registered plans with 1-64 frames of complex64
+    k-space already resident in HBM; plans are built on admission and
+    evicted LRU under `budget`. Returns the server's latency statistics.
+    """
+    import torch
+
+    from paper_2410_06129_gb300 import _lib as L
+    from paper_2410_06129_gb300 import synth
+    from paper_2410_06129_gb300.plan import Plan
+    from paper_2410_06129_gb300.serve import Server
+
+    descs = synth.serve_plans(side_div=side_div)
+    geo = [synth.serve_plan_inputs(d) for d in descs]
+    trace = synth.serve_trace(rate_hz, duration_s, len(geo), seed=seed)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    datas = [torch.randn((64, p.n_coils * p.n_samples), generator=gen, device="cuda",
+                         dtype=torch.complex64) for p in geo]
+    torch.cuda.synchronize()
+    with Server(budget_bytes=int(budget), max_slots=max_slots) as sv:
+        ids = [sv.register_inputs(p, precision=prec, refine_max_iters=refine, recon_mode=recon_mode)
+               for p in geo]
+        tickets = []
+        t0 = time.perf_counter()
+        for t_arr, i, F in trace:
+            dt = t0 + t_arr - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(sv.enqueue(ids[i], datas[i][:F], sync_inputs=False))
+        status = [sv.wait(t, timeout=3600.0) for t, _ in tickets]
+        wall = time.perf_counter() - t0
+        st = sv.stats()
+        # accuracy of served images against FP64 plans on the same data
+        worst = None
+        if check_plans:
+            seen = []
+            for (t, out), (_, i, F) in zip(tickets, trace):
+                if i in seen or len(seen) >= check_plans:
+                    continue
+                seen.append(i)
+                with Plan.from_inputs(geo[i], precision=L.FP64, recon_mode=L.RECON_NONE) as p64:
+                    p64.build()
+                    x64 = p64.apply(datas[i][:F].to(torch.complex128))
+                e = float(torch.linalg.norm(out.to(torch.complex128) - x64) / torch.linalg.norm(x64))
+                worst = e if worst is None else max(worst, e)
+    frames = float(st["frames"])
+    return {
+        "requests": len(trace), "ok": int(sum(s == L.OK for s in status)), "failed": int(st["failed"]),
+        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
+        "frames_per_s": frames / st["span_s"] if st["span_s"] > 0 else None,
+        "frames": frames, "builds": int(st["builds"]), "evictions": int(st["evictions"]),
+        "wall_s": wall, "trace_s": duration_s, "rate_hz": rate_hz, "slots": max_slots,
+        "budget_gb": budget / 1e9, "refine_steps": refine,
+        "recon": "explicit" if recon_mode == L.RECON_STORE else "factor-only",
+        "nrmse_vs_fp64_max": worst, "nrmse_plans_checked": check_plans,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -169,6 +242,15 @@ def main():
     ap.add_argument("--refine", type=int, default=3, help="FP64-residual refinement steps (mixed)")
     ap.add_argument("--side", type=int, default=64,
                     help="image side; 64 is the benchmark workload, smaller sides are for profiling")
+    ap.add_argument("--serve", default="half", choices=["off", "half", "full"],
+                    help="serving trace: 'full' = 32 plans of side 32-128 under a 120 GB budget, "
+                         "'half' = the same plans at half the side under the same budget fraction")
+    ap.add_argument("--serve-duration", type=float, default=3.0, help="seconds of Poisson arrivals")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-refine", type=int, default=3)
+    ap.add_argument("--serve-fp64-duration", type=float, default=1.0,
+                    help="seconds of the same trace served by FP64 plans (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -307,6 +389,24 @@ def main():
                "sample": f"full FP64 oracle pipeline at 32x32 (N=1024, 8 coils, M=16384, 64 frames), "
                          f"{t:.2f} s x{scale:.0f} by N^2 M cost"}
 
+    serve = None
+    if rank == 0 and args.serve != "off":
+        full = args.serve == "full"
+        div = 1 if full else 2
+        from paper_2410_06129_gb300 import synth as _sy
+        fp_full = sum(_footprint(d) for d in _sy.serve_plans())
+        fp_this = sum(_footprint(d) for d in _sy.serve_plans(side_div=div))
+        budget = SERVE_BUDGET_FULL * fp_this / fp_full
+        serve = {"workload": ("32 plans, side 32-128" if full else "32 plans, side 16-64 (cfg side / 2)")
+                 + ", 1-16 coils, 1-2 x N samples per coil, Poisson arrivals, 1-64 c64 frames",
+                 "budget_rule": "120 GB x (this plan set's footprint / the full set's)"}
+        serve["mixed"] = run_serve(prec, args.serve_refine if prec != L.FP64 else 0, div, args.serve_rate,
+                                   args.serve_duration, budget, args.serve_slots,
+                                   L.RECON_STORE, check_plans=4)
+        if prec != L.FP64 and args.serve_fp64_duration > 0:
+            serve["fp64"] = run_serve(L.FP64, 0, div, args.serve_rate, args.serve_fp64_duration, budget,
+                                      args.serve_slots, L.RECON_NONE)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": build_s / ws, "unit": "s", "n_gpus": ws, "steps": args.steps,
@@ -327,6 +427,10 @@ def main():
             "clocks": clk.summary(), "wall_s_timed": wall,
         }
         line.update(res)
+        if serve is not None:
+            line["serve"] = serve
+            line["serve_p50_ms"] = serve["mixed"]["p50_ms"]
+            line["serve_p99_ms"] = serve["mixed"]["p99_ms"]
         print(json.dumps(line), flush=True)
     plan.close()
     if ws > 1:

@@ -199,6 +199,67 @@ pinv_status pinv_plan_info(const pinv_plan* plan, pinv_plan_info_t* out);
 /* Free the plan and its device memory (synchronises the plan's work). NULL is a no-op. */
 void pinv_plan_destroy(pinv_plan* plan);
 
+/* ------------------------------------------------------------------------
+ * Serving loop. Recon is built from the trajectory and encoding physics
+ * before data arrive and each acquisition then needs only image = Recon x data
+ * (Section 4.5, Section 5). A server keeps the factored plans of registered
+ * encodings resident in device memory under a byte budget and serves
+ * reconstruction requests as they arrive (continuous batching):
+ *   - requests are admitted in arrival order into up to max_slots slots, each
+ *     with its own stream and scratch, so work of different requests and of
+ *     plan builds overlaps on the device;
+ *   - a request whose plan is not resident builds it first on a separate build
+ *     stream; idle resident plans are evicted least recently used first to
+ *     fit the budget; a plan that cannot fit fails its request with
+ *     PINV_ERR_BUDGET, and a plan whose Gram is not positive definite fails its
+ *     requests with PINV_ERR_NOT_PD; other requests are unaffected;
+ *   - a request's image is computed exactly as pinv_apply would compute it,
+ *     whatever else is in flight.
+ * One worker thread per server issues all CUDA work; the calls below only
+ * queue, poll or wait and are safe from any host thread. Registered plans run
+ * their refinement with a fixed number of steps (refine_tol is ignored) so the
+ * worker never blocks on a host read.
+ * ---------------------------------------------------------------------- */
+typedef struct pinv_server pinv_server;
+
+/* Completion callback, called on the server's worker thread just before the
+ * request counts as finished; it must not call the server's wait functions. */
+typedef void (*pinv_done_cb)(uint64_t ticket, pinv_status status, void* user);
+
+typedef struct {
+    uint64_t completed, failed, builds, evictions;
+    double frames;                    /* frames reconstructed by completed requests */
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* enqueue -> completion latency */
+    double span_s;                    /* first enqueue to last completion */
+    size_t resident_bytes;            /* device bytes held by resident plans */
+    int resident_plans, queued;
+} pinv_server_stats_t;
+
+/* Create a server on the current device. hbm_budget_bytes bounds the bytes of
+ * resident plans; max_slots (1..64) bounds the requests in flight. */
+pinv_status pinv_server_create(size_t hbm_budget_bytes, int max_slots, pinv_server** out);
+
+/* Register an encoding (descriptor arrays are copied); no device work yet. */
+pinv_status pinv_serve_register(pinv_server* server, const pinv_plan_desc* desc, int* plan_id);
+
+/* Queue image = Recon x data for n_frames frames of device buffers d_data
+ * [F][C][M_k] and d_image [F][N] of `dtype`; the buffers must stay valid until
+ * the request finishes. Returns at once with a ticket. */
+pinv_status pinv_serve_enqueue(pinv_server* server, int plan_id, const void* d_data, void* d_image,
+                               int64_t n_frames, int dtype, pinv_done_cb cb, void* user, uint64_t* ticket);
+
+/* Non-blocking: *done = 1 and *result = its status once the request finished. */
+pinv_status pinv_serve_poll(pinv_server* server, uint64_t ticket, int* done, pinv_status* result);
+
+/* Block until the request finished (PINV_ERR_TIMEOUT after timeout_s seconds). */
+pinv_status pinv_serve_wait(pinv_server* server, uint64_t ticket, double timeout_s, pinv_status* result);
+
+/* Counters and latency percentiles of the requests completed so far. */
+pinv_status pinv_server_stats(pinv_server* server, pinv_server_stats_t* out);
+
+/* Finish queued requests, stop the worker and free every resident plan. */
+void pinv_server_destroy(pinv_server* server);
+
 /* Size of the fixed device scratch array behind pinv_apply_noalloc (64 MiB). */
 #define PINV_NOALLOC_SCRATCH_BYTES (64u << 20)
 

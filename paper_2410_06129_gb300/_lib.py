@@ -61,6 +61,21 @@ class PlanInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerStats(C.Structure):
+    _fields_ = [
+        ("completed", C.c_uint64), ("failed", C.c_uint64), ("builds", C.c_uint64),
+        ("evictions", C.c_uint64), ("frames", C.c_double), ("p50_ms", C.c_double),
+        ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
+        ("span_s", C.c_double), ("resident_bytes", C.c_size_t), ("resident_plans", C.c_int),
+        ("queued", C.c_int),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+DONE_CB = C.CFUNCTYPE(None, C.c_uint64, C.c_int, C.c_void_p)
+
 # Symbols declared in include/pinv.h: name -> (restype, argtypes)
 _VP = C.c_void_p
 SIGNATURES = {
@@ -77,6 +92,14 @@ SIGNATURES = {
     "pinv_plan_info": (C.c_int, [_VP, C.POINTER(PlanInfo)]),
     "pinv_plan_destroy": (None, [_VP]),
     "pinv_apply_noalloc": (C.c_int, [_VP, _VP, _VP, C.c_int64, C.c_int, _VP]),
+    "pinv_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(_VP)]),
+    "pinv_serve_register": (C.c_int, [_VP, C.POINTER(PlanDesc), C.POINTER(C.c_int)]),
+    "pinv_serve_enqueue": (C.c_int, [_VP, C.c_int, _VP, _VP, C.c_int64, C.c_int, _VP, _VP,
+                                     C.POINTER(C.c_uint64)]),
+    "pinv_serve_poll": (C.c_int, [_VP, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "pinv_serve_wait": (C.c_int, [_VP, C.c_uint64, C.c_double, C.POINTER(C.c_int)]),
+    "pinv_server_stats": (C.c_int, [_VP, C.POINTER(ServerStats)]),
+    "pinv_server_destroy": (None, [_VP]),
 }
 NOALLOC_SCRATCH_BYTES = 64 << 20
 

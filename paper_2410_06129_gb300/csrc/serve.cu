@@ -1,0 +1,456 @@
+// Continuous-batching serving loop for Pinv-Recon plans.
+//
+// Reconstruction is split the way the paper motivates it (Section 4.5): Recon
+// is built from the trajectory and encoding physics before data arrive, and
+// each acquisition then only needs image = Recon x data. A server keeps the
+// factored plans of registered trajectories resident in HBM under a byte
+// budget and serves reconstruction requests as they arrive:
+//
+//   * one worker thread issues every CUDA call; callers only queue requests;
+//   * requests are admitted in arrival order into up to `max_slots` slots,
+//     each with its own stream and scratch, so the work of several requests
+//     (and of a plan build) overlaps on the device;
+//   * a request whose plan is not resident triggers its build on a separate
+//     build stream; the request's slot waits on the build's event, other slots
+//     keep running. To make room, idle resident plans are evicted least
+//     recently used first; a plan that cannot fit fails its request with
+//     PINV_ERR_BUDGET;
+//   * completion is detected with events; latency runs from enqueue to the
+//     moment the worker sees the request's event complete.
+// Each request's result is computed by the same kernels in the same order as
+// a standalone pinv_apply, so it does not depend on what else is in flight.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "plan_impl.h"
+
+using namespace pinv;
+
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// A registered trajectory/encoding: owned copy of its descriptor and its
+// resident plan, if any.
+struct Registered {
+    pinv_plan_desc desc{};
+    std::vector<double> traj, coils, b0, times;
+    std::vector<int64_t> vox;
+    pinv_plan* plan = nullptr;
+    cudaEvent_t ready = nullptr;  // recorded on the build stream after the build
+    size_t bytes = 0;             // device bytes held while resident
+    uint64_t last_use = 0;        // LRU clock
+    int inflight = 0;             // requests submitted to slots and not yet completed
+    pinv_status failed = PINV_OK; // set once a build of this encoding failed (e.g. NOT_PD)
+};
+
+struct Request {
+    uint64_t ticket = 0;
+    int plan_id = -1;
+    const void* data = nullptr;
+    void* image = nullptr;
+    int64_t frames = 0;
+    int dtype = PINV_C64;
+    pinv_done_cb cb = nullptr;
+    void* user = nullptr;
+    double t_enqueue = 0;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    bool busy = false;
+    Request req;
+    pinv_status submit_status = PINV_OK;
+};
+
+}  // namespace
+
+struct pinv_server {
+    size_t budget = 0;
+    int device = 0;
+    std::vector<Registered> plans;
+    std::deque<Request> queue;
+    std::vector<Slot> slots;
+    std::unordered_map<uint64_t, pinv_status> finished;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    cudaStream_t build_stream = nullptr;
+    uint64_t next_ticket = 1, lru_clock = 0;
+    size_t resident_bytes = 0;
+    // statistics
+    std::vector<double> latency_ms;
+    uint64_t completed = 0, failed = 0, builds = 0, evictions = 0;
+    double frames = 0, t_first = 0, t_last = 0;
+
+    void run();
+    bool dispatch_one(std::unique_lock<std::mutex>& lk);
+    bool reap(std::unique_lock<std::mutex>& lk);
+    pinv_status make_resident(Registered& r, int id, bool* defer);
+    void evict(Registered& v);
+    void finish(const Request& q, pinv_status st, std::unique_lock<std::mutex>& lk);
+};
+
+namespace {
+
+// Device bytes a plan keeps while resident (its build transients are not counted).
+size_t plan_footprint(const pinv_plan_desc& d) {
+    const double N = (double)d.n_vox, M = (double)d.n_samples * d.n_coils;
+    const bool fp64 = d.precision == PINV_FP64;
+    double b = N * N * 16.0;                  // G / L
+    b += fp64 ? N * N * 16.0 : N * N * 24.0;  // G^-1, or W and its FP32 copy
+    int recon = d.recon_mode;
+    if (recon == PINV_RECON_AUTO) recon = N * M * (fp64 ? 16.0 : 8.0) <= 64.0 * (1ull << 30);
+    if (recon) b += N * M * (fp64 ? 16.0 : 8.0);
+    int width = 0;
+    for (int i = 0; i < d.ndim; ++i) width += d.dims[i];
+    b += (double)d.n_samples * width * 64.0 + N * d.n_coils * 40.0 + N * 64.0 + (double)(64u << 20);
+    return (size_t)b;
+}
+
+}  // namespace
+
+void pinv_server::finish(const Request& q, pinv_status st, std::unique_lock<std::mutex>& lk) {
+    const double t = now_s();
+    // the callback runs before the request counts as finished, so a waiter
+    // that returns may release whatever the callback uses
+    if (q.cb) {
+        lk.unlock();
+        q.cb(q.ticket, st, q.user);
+        lk.lock();
+    }
+    finished[q.ticket] = st;
+    if (st == PINV_OK) {
+        ++completed;
+        frames += (double)q.frames;
+        latency_ms.push_back((t - q.t_enqueue) * 1e3);
+        t_last = t;
+    } else {
+        ++failed;
+    }
+    cv_done.notify_all();
+}
+
+void pinv_server::evict(Registered& v) {
+    delete v.plan;  // no request of it is in flight (inflight == 0)
+    v.plan = nullptr;
+    resident_bytes -= v.bytes;
+    v.bytes = 0;
+}
+
+// Make plan `id` resident, building it on the build stream. *defer is set when
+// it does not fit now but will once requests in flight have finished.
+pinv_status pinv_server::make_resident(Registered& r, int id, bool* defer) {
+    *defer = false;
+    if (r.plan) return PINV_OK;
+    const size_t need = plan_footprint(r.desc);
+    if (need > budget) return set_error(PINV_ERR_BUDGET, "plan footprint exceeds the server's HBM budget");
+    while (resident_bytes + need > budget) {
+        // least recently used idle plan
+        int victim = -1;
+        size_t busy_bytes = 0;
+        for (int i = 0; i < (int)plans.size(); ++i) {
+            const Registered& c = plans[i];
+            if (i == id || !c.plan) continue;
+            if (c.inflight > 0) {
+                busy_bytes += c.bytes;
+                continue;
+            }
+            if (victim < 0 || c.last_use < plans[victim].last_use) victim = i;
+        }
+        if (victim < 0) {
+            *defer = busy_bytes > 0;
+            return *defer ? PINV_OK : set_error(PINV_ERR_BUDGET, "no idle plan to evict within the HBM budget");
+        }
+        evict(plans[victim]);
+        ++evictions;
+    }
+    pinv_plan* p = nullptr;
+    pinv_status st = pinv_plan_create(&r.desc, build_stream, &p);
+    if (st != PINV_OK) return st;
+    st = pinv_build(p, build_stream);
+    if (st != PINV_OK) {
+        delete p;
+        return st;
+    }
+    cudaError_t e = cudaEventRecord(r.ready, build_stream);
+    if (e != cudaSuccess) {
+        delete p;
+        return set_error(PINV_ERR_CUDA, cudaGetErrorString(e));
+    }
+    r.plan = p;
+    r.bytes = std::max(need, p->bytes);
+    resident_bytes += r.bytes;
+    ++builds;
+    return PINV_OK;
+}
+
+// Submit the oldest queued request to a free slot. Returns true if it did work.
+bool pinv_server::dispatch_one(std::unique_lock<std::mutex>& lk) {
+    if (queue.empty()) return false;
+    Slot* slot = nullptr;
+    for (auto& s : slots)
+        if (!s.busy) { slot = &s; break; }
+    if (!slot) return false;
+    Request q = queue.front();
+    Registered& r = plans[q.plan_id];
+    bool defer = false;
+    pinv_status st = r.failed != PINV_OK ? r.failed : make_resident(r, q.plan_id, &defer);
+    if (defer) return false;  // head of the queue waits until a slot completes
+    queue.pop_front();
+    if (st == PINV_OK) st = apply_check(r.plan, q.data, q.image, q.frames, q.dtype);
+    if (st == PINV_OK && q.frames > 0) {
+        const size_t need = apply_scratch_layout(r.plan, q.frames, q.dtype, nullptr, nullptr);
+        if (need > slot->scratch_bytes) {
+            if (slot->scratch) cudaFree(slot->scratch);
+            slot->scratch = nullptr;
+            slot->scratch_bytes = 0;
+            if (cudaMalloc(&slot->scratch, need) != cudaSuccess) st = set_error(PINV_ERR_OOM, "slot scratch");
+            else slot->scratch_bytes = need;
+        }
+        if (st == PINV_OK) {
+            ApplyScratch sc;
+            apply_scratch_layout(r.plan, q.frames, q.dtype, slot->scratch, &sc);
+            if (cudaStreamWaitEvent(slot->stream, r.ready, 0) != cudaSuccess)
+                st = set_error(PINV_ERR_CUDA, "cudaStreamWaitEvent");
+            else
+                st = apply_impl(r.plan, q.data, q.image, q.frames, q.dtype, slot->stream, sc);
+        }
+    }
+    if (st == PINV_OK && cudaEventRecord(slot->done, slot->stream) != cudaSuccess)
+        st = set_error(PINV_ERR_CUDA, "cudaEventRecord");
+    if (st != PINV_OK) {
+        finish(q, st, lk);
+        return true;
+    }
+    r.inflight++;
+    r.last_use = ++lru_clock;
+    slot->busy = true;
+    slot->req = q;
+    return true;
+}
+
+// Complete every slot whose event has fired. Returns true if it did work.
+bool pinv_server::reap(std::unique_lock<std::mutex>& lk) {
+    bool any = false;
+    for (auto& s : slots) {
+        if (!s.busy) continue;
+        const cudaError_t e = cudaEventQuery(s.done);
+        if (e == cudaErrorNotReady) continue;
+        s.busy = false;
+        Registered& r = plans[s.req.plan_id];
+        r.inflight--;
+        pinv_status st = PINV_OK;
+        if (e != cudaSuccess) {
+            st = set_error(PINV_ERR_CUDA, cudaGetErrorString(e));
+        } else if (r.failed != PINV_OK) {
+            st = r.failed;
+        } else if (r.plan && r.plan->st_host->not_pd_pivot != INT_MAX) {
+            // the build behind this request found a non-positive pivot: later
+            // requests of this encoding fail at once, and the plan is dropped
+            st = r.failed = PINV_ERR_NOT_PD;
+        } else if (r.plan && r.plan->st_host->timeout_site) {
+            st = PINV_ERR_TIMEOUT;
+        }
+        if (r.failed != PINV_OK && r.plan && r.inflight == 0) evict(r);
+        const Request q = s.req;
+        finish(q, st, lk);
+        any = true;
+    }
+    return any;
+}
+
+void pinv_server::run() {
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(mu);
+    while (true) {
+        bool work = reap(lk);
+        while (dispatch_one(lk)) work = true;
+        bool busy = false;
+        for (auto& s : slots) busy = busy || s.busy;
+        if (stop && !busy && queue.empty()) break;
+        if (!work) {
+            if (busy) cv_work.wait_for(lk, std::chrono::microseconds(50));
+            else cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+        }
+    }
+}
+
+extern "C" {
+
+pinv_status pinv_server_create(size_t hbm_budget_bytes, int max_slots, pinv_server** out) {
+    if (!out || max_slots < 1 || max_slots > 64 || hbm_budget_bytes == 0)
+        return set_error(PINV_ERR_INVALID_ARG, "need out, 1 <= max_slots <= 64 and a nonzero budget");
+    *out = nullptr;
+    auto* sv = new pinv_server();
+    sv->budget = hbm_budget_bytes;
+    if (cudaGetDevice(&sv->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sv->build_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete sv;
+        return set_error(PINV_ERR_CUDA, "server stream creation failed");
+    }
+    sv->slots.resize(max_slots);
+    for (auto& s : sv->slots) {
+        if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+            delete sv;
+            return set_error(PINV_ERR_CUDA, "slot stream creation failed");
+        }
+    }
+    sv->worker = std::thread([sv] { sv->run(); });
+    *out = sv;
+    return PINV_OK;
+}
+
+pinv_status pinv_serve_register(pinv_server* sv, const pinv_plan_desc* d, int* plan_id) {
+    if (!sv || !d || !plan_id) return set_error(PINV_ERR_INVALID_ARG, "null argument");
+    if (d->ndim < 1 || d->ndim > 3 || d->n_vox < 1 || d->n_samples < 1 || d->n_coils < 1 || !d->traj)
+        return set_error(PINV_ERR_INVALID_ARG, "bad descriptor");
+    Registered r;
+    r.desc = *d;
+    r.desc.refine_tol = 0.0;  // fixed refinement steps: the worker never waits on a host read
+    r.traj.assign(d->traj, d->traj + d->n_samples * d->ndim);
+    r.desc.traj = r.traj.data();
+    if (d->coil_maps) {
+        r.coils.assign(d->coil_maps, d->coil_maps + 2 * d->n_vox * d->n_coils);
+        r.desc.coil_maps = r.coils.data();
+    }
+    if (d->b0_hz) {
+        if (!d->times) return set_error(PINV_ERR_INVALID_ARG, "b0_hz needs times");
+        r.b0.assign(d->b0_hz, d->b0_hz + d->n_vox);
+        r.times.assign(d->times, d->times + d->n_samples);
+        r.desc.b0_hz = r.b0.data();
+        r.desc.times = r.times.data();
+    }
+    if (d->voxel_index) {
+        r.vox.assign(d->voxel_index, d->voxel_index + d->n_vox);
+        r.desc.voxel_index = r.vox.data();
+    }
+    std::unique_lock<std::mutex> lk(sv->mu);
+    // the event is created here, on the caller's thread, with the server's device current
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != sv->device) cudaSetDevice(sv->device);
+    const cudaError_t e = cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming);
+    if (dev != sv->device) cudaSetDevice(dev);
+    if (e != cudaSuccess) return set_error(PINV_ERR_CUDA, "event creation failed");
+    sv->plans.push_back(std::move(r));
+    // vector growth moved the owned arrays; re-point each descriptor at its own copies
+    for (auto& p : sv->plans) {
+        p.desc.traj = p.traj.data();
+        if (!p.coils.empty()) p.desc.coil_maps = p.coils.data();
+        if (!p.b0.empty()) { p.desc.b0_hz = p.b0.data(); p.desc.times = p.times.data(); }
+        if (!p.vox.empty()) p.desc.voxel_index = p.vox.data();
+    }
+    *plan_id = (int)sv->plans.size() - 1;
+    return PINV_OK;
+}
+
+pinv_status pinv_serve_enqueue(pinv_server* sv, int plan_id, const void* d_data, void* d_image, int64_t n_frames,
+                               int dtype, pinv_done_cb cb, void* user, uint64_t* ticket) {
+    if (!sv || !ticket) return set_error(PINV_ERR_INVALID_ARG, "null argument");
+    Request q;
+    q.plan_id = plan_id;
+    q.data = d_data;
+    q.image = d_image;
+    q.frames = n_frames;
+    q.dtype = dtype;
+    q.cb = cb;
+    q.user = user;
+    q.t_enqueue = now_s();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (plan_id < 0 || plan_id >= (int)sv->plans.size()) return set_error(PINV_ERR_INVALID_ARG, "unknown plan");
+        if (sv->stop) return set_error(PINV_ERR_INVALID_ARG, "server is shutting down");
+        q.ticket = sv->next_ticket++;
+        *ticket = q.ticket;
+        if (sv->t_first == 0) sv->t_first = q.t_enqueue;
+        sv->queue.push_back(q);
+    }
+    sv->cv_work.notify_one();
+    return PINV_OK;
+}
+
+pinv_status pinv_serve_poll(pinv_server* sv, uint64_t ticket, int* done, pinv_status* result) {
+    if (!sv || !done) return set_error(PINV_ERR_INVALID_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->finished.find(ticket);
+    *done = it != sv->finished.end();
+    if (*done && result) *result = it->second;
+    return PINV_OK;
+}
+
+pinv_status pinv_serve_wait(pinv_server* sv, uint64_t ticket, double timeout_s, pinv_status* result) {
+    if (!sv) return set_error(PINV_ERR_INVALID_ARG, "null server");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    const bool ok = sv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
+                                         [&] { return sv->finished.count(ticket) > 0; });
+    if (!ok) return set_error(PINV_ERR_TIMEOUT, "request not finished within the timeout");
+    if (result) *result = sv->finished[ticket];
+    return PINV_OK;
+}
+
+pinv_status pinv_server_stats(pinv_server* sv, pinv_server_stats_t* o) {
+    if (!sv || !o) return set_error(PINV_ERR_INVALID_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    std::memset(o, 0, sizeof(*o));
+    o->completed = sv->completed;
+    o->failed = sv->failed;
+    o->builds = sv->builds;
+    o->evictions = sv->evictions;
+    o->frames = sv->frames;
+    o->resident_bytes = sv->resident_bytes;
+    for (auto& p : sv->plans) o->resident_plans += p.plan != nullptr;
+    o->queued = (int)sv->queue.size();
+    if (!sv->latency_ms.empty()) {
+        std::vector<double> v = sv->latency_ms;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) { return v[std::min(v.size() - 1, (size_t)(q * (double)(v.size() - 1) + 0.5))]; };
+        o->p50_ms = pct(0.50);
+        o->p99_ms = pct(0.99);
+        o->max_ms = v.back();
+        double s = 0;
+        for (double x : v) s += x;
+        o->mean_ms = s / (double)v.size();
+        o->span_s = sv->t_last - sv->t_first;
+    }
+    return PINV_OK;
+}
+
+void pinv_server_destroy(pinv_server* sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    cudaSetDevice(sv->device);
+    cudaDeviceSynchronize();
+    for (auto& p : sv->plans) {
+        delete p.plan;
+        if (p.ready) cudaEventDestroy(p.ready);
+    }
+    for (auto& s : sv->slots) {
+        if (s.scratch) cudaFree(s.scratch);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.stream) cudaStreamDestroy(s.stream);
+    }
+    if (sv->build_stream) cudaStreamDestroy(sv->build_stream);
+    delete sv;
+}
+
+}  // extern "C"

@@ -242,6 +242,9 @@ def make_plan(side: int, n_coils: int, traj: str, n_frames: int, seed: int,
     maps = coil_maps(dims, n_coils, rng) if n_coils > 1 else None
     b0map = b0_map(dims, rng) if b0 else None
     times = (s_idx * DWELL_S).astype(np.float64) if b0 else None
+    if n_frames == 0:  # geometry only (e.g. serving plans, whose data are drawn per request)
+        return PlanInputs(dims=dims, traj=k, coil_maps=maps, b0_hz=b0map, times=times,
+                          lambda_rel=lambda_rel, data=None, truth=None, name=name)
     e = ellipses(rng)
     data = kspace_data(e, k, N, n_coils, n_frames, rng, noise_frac)
     truth = np.stack([phantom_image(e, dims, f) for f in range(n_frames)])
@@ -292,18 +295,27 @@ def config(i: int, reduced: bool = False, frames: int | None = None) -> PlanInpu
     raise ValueError(i)
 
 
-def serve_plans(reduced: bool = False, n: int = 32) -> list:
-    """Plan descriptors (no data) of the serving workload, seed 4000."""
+def serve_plans(reduced: bool = False, n: int = 32, side_div: int = 1) -> list:
+    """Plan descriptors (no data) of the serving workload, seed 4000.
+
+    side_div > 1 divides every image side (same draws, so the same mix of
+    sizes, coil counts and trajectories at a smaller scale)."""
     rng = np.random.default_rng(4000)
     out = []
     for p in range(n):
-        side = int(rng.choice([32, 48, 64, 96, 128] if not reduced else [8, 12, 16]))
+        side = int(rng.choice([32, 48, 64, 96, 128] if not reduced else [8, 12, 16])) // side_div
         C = int(rng.choice([1, 2, 4, 8, 16] if not reduced else [1, 2, 4]))
         mult = int(rng.integers(1, 3))
         kind = "spiral" if p % 2 == 0 else "radial"
         out.append(dict(side=side, n_coils=C, traj=kind, samples=mult * side * side,
                         seed=4000 + p + 1, lambda_rel=1e-3))
     return out
+
+
+def serve_plan_inputs(d: dict) -> PlanInputs:
+    """Geometry (trajectory, coil maps, lambda) of one serve_plans() entry."""
+    return make_plan(d["side"], d["n_coils"], d["traj"], 0, d["seed"], d["lambda_rel"],
+                     samples=d["samples"], name=f"serve.{d['seed'] - 4000}")
 
 
 def serve_trace(rate_hz: float, duration_s: float, n_plans: int, seed: int = 4100,

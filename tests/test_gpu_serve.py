@@ -1,0 +1,189 @@
+"""Serving loop (pinv_server_*) on the GPU.
+
+A request's image must not depend on what else the server runs: every
+result served in a mix of plans, precisions and frame counts is compared
+bit for bit with a standalone pinv_apply of the same plan, which the other
+GPU tests hold to the oracle. One FP64 result is also checked against the
+oracle directly. Failures (budget, non-positive-definite Gram) stay with
+their own requests.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2410_06129_gb300 import _lib as L  # noqa: E402
+from paper_2410_06129_gb300 import synth  # noqa: E402
+from tests._ref import oracle_all, rel  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib_built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    L.load()
+
+
+def _cases():
+    """(inputs, plan keyword arguments): FP64 explicit, FP64 factor-only with
+    B0, and (where tcgen05 is present) a mixed split-BF16 plan."""
+    cases = [
+        (synth.make_plan(16, 2, "spiral", 3, 2101, 1e-3, samples=512, interleaves=1),
+         dict(precision=L.FP64)),
+        (synth.make_plan(20, 4, "radial", 3, 2102, 1e-3, b0=True, spokes=16, per_spoke=40),
+         dict(precision=L.FP64, recon_mode=L.RECON_NONE)),
+    ]
+    if L.load().pinv_tc_available():
+        cases.append((synth.make_plan(24, 4, "spiral", 3, 2103, 1e-4, samples=1152, interleaves=2),
+                      dict(precision=L.MIXED_BF16X6)))
+    return cases
+
+
+def _standalone(p, kw, data):
+    from paper_2410_06129_gb300.plan import Plan
+    pl = Plan.from_inputs(p, **kw).build()
+    x = pl.apply(data)
+    torch.cuda.synchronize()
+    pl.close()
+    return x
+
+
+def _requests(cases):
+    """Interleaved requests over all plans: varying frame counts and dtypes."""
+    reqs = []
+    for r in range(4):
+        for i, (p, _) in enumerate(cases):
+            F = 1 + (r + i) % 3
+            d = torch.from_numpy(p.data[:F]).cuda()
+            if (r + i) % 2:
+                d = d.to(torch.complex64)
+            reqs.append((i, d))
+    return reqs
+
+
+def test_serve_mix_matches_standalone_apply():
+    from paper_2410_06129_gb300.serve import Server
+    cases = _cases()
+    reqs = _requests(cases)
+    expect = [_standalone(cases[i][0], cases[i][1], d) for i, d in reqs]
+    seen = []
+    lock = threading.Lock()
+
+    def cb(t, st):
+        with lock:
+            seen.append((t, st))
+
+    with Server(budget_bytes=8 << 30, max_slots=3) as sv:
+        ids = [sv.register_inputs(p, **kw) for p, kw in cases]
+        tickets = [sv.enqueue(ids[i], d, callback=cb) for i, d in reqs]
+        for t, _ in tickets:
+            assert sv.wait(t) == L.OK
+        for t, _ in tickets:
+            assert sv.poll(t) == (True, L.OK)
+        st = sv.stats()
+    for (t, out), x in zip(tickets, expect):
+        assert out.dtype == x.dtype
+        assert torch.equal(out, x), f"ticket {t} differs from a standalone apply"
+    assert sorted(seen) == sorted((t, L.OK) for t, _ in tickets)
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["builds"] == len(cases) and st["evictions"] == 0
+    assert st["frames"] == sum(d.shape[0] for _, d in reqs)
+    assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
+    assert st["resident_plans"] == len(cases) and st["queued"] == 0
+
+
+def test_serve_fp64_result_matches_oracle():
+    from paper_2410_06129_gb300.serve import Server
+    p, kw = _cases()[0]
+    ref = oracle_all(p)
+    with Server(budget_bytes=1 << 30, max_slots=2) as sv:
+        pid = sv.register_inputs(p, **kw)
+        t, out = sv.enqueue(pid, torch.from_numpy(p.data).cuda())
+        assert sv.wait(t) == L.OK
+    assert rel(out.cpu().numpy(), ref.images) < 1e-10
+
+
+def _resident_bytes(p, kw):
+    from paper_2410_06129_gb300.serve import Server
+    with Server(budget_bytes=8 << 30, max_slots=1) as sv:
+        pid = sv.register_inputs(p, **kw)
+        t, _ = sv.enqueue(pid, torch.from_numpy(p.data[:1]).cuda())
+        assert sv.wait(t) == L.OK
+        return sv.stats()["resident_bytes"]
+
+
+def test_serve_lru_eviction_under_budget():
+    """A budget that holds one plan at a time: alternating requests rebuild and
+    evict, requests wait for in-flight work instead of failing, and results
+    stay identical to standalone applies."""
+    from paper_2410_06129_gb300.serve import Server
+    cases = _cases()[:2]
+    b = [_resident_bytes(p, kw) for p, kw in cases]
+    budget = int(1.25 * max(b))
+    assert budget < sum(b)
+    order = [0, 1, 0, 1, 0]
+    datas = [torch.from_numpy(cases[i][0].data[:2]).cuda() for i in order]
+    expect = [_standalone(cases[i][0], cases[i][1], d) for i, d in zip(order, datas)]
+    with Server(budget_bytes=budget, max_slots=4) as sv:
+        ids = [sv.register_inputs(p, **kw) for p, kw in cases]
+        tickets = [sv.enqueue(ids[i], d) for i, d in zip(order, datas)]
+        assert [sv.wait(t) for t, _ in tickets] == [L.OK] * len(order)
+        st = sv.stats()
+    for (_, out), x in zip(tickets, expect):
+        assert torch.equal(out, x)
+    assert st["builds"] == len(order) and st["evictions"] == len(order) - 1
+    assert st["resident_plans"] == 1 and st["resident_bytes"] <= budget
+
+
+def test_serve_budget_too_small_fails_request_only():
+    from paper_2410_06129_gb300.serve import Server
+    p, kw = _cases()[0]
+    with Server(budget_bytes=1 << 20, max_slots=2) as sv:
+        pid = sv.register_inputs(p, **kw)
+        t, _ = sv.enqueue(pid, torch.from_numpy(p.data[:1]).cuda())
+        assert sv.wait(t) == L.ERR_BUDGET
+        st = sv.stats()
+    assert st["failed"] == 1 and st["completed"] == 0 and st["builds"] == 0
+
+
+def test_serve_not_pd_plan_fails_its_requests_only():
+    """lambda = 0 and a voxel that no coil sees make G singular: the plan's
+    requests fail with NOT_PD, requests of a good plan around them succeed."""
+    from paper_2410_06129_gb300.serve import Server
+    bad = synth.make_plan(12, 2, "spiral", 1, 1901, 0.0, samples=512, interleaves=1)
+    maps = bad.coil_maps.copy()
+    maps[:, 70] = 0.0
+    good, gkw = _cases()[0]
+    dg = torch.from_numpy(good.data[:2]).cuda()
+    db = torch.from_numpy(bad.data[:1]).cuda()
+    expect = _standalone(good, gkw, dg)
+    with Server(budget_bytes=4 << 30, max_slots=3) as sv:
+        ib = sv.register(bad.dims, bad.traj, maps, lam=0.0, lambda_mode=L.LAMBDA_ABS)
+        ig = sv.register_inputs(good, **gkw)
+        tickets = [sv.enqueue(ib, db), sv.enqueue(ig, dg), sv.enqueue(ib, db), sv.enqueue(ig, dg)]
+        res = [sv.wait(t) for t, _ in tickets]
+        late, _ = sv.enqueue(ib, db)
+        res.append(sv.wait(late))
+        st = sv.stats()
+    assert res == [L.ERR_NOT_PD, L.OK, L.ERR_NOT_PD, L.OK, L.ERR_NOT_PD]
+    assert torch.equal(tickets[1][1], expect) and torch.equal(tickets[3][1], expect)
+    assert st["failed"] == 3 and st["completed"] == 2
+    assert st["resident_plans"] == 1  # the singular plan was dropped
+
+
+def test_serve_zero_frames_and_bad_plan_id():
+    from paper_2410_06129_gb300.serve import Server
+    p, kw = _cases()[0]
+    with Server(budget_bytes=1 << 30, max_slots=1) as sv:
+        pid = sv.register_inputs(p, **kw)
+        t, out = sv.enqueue(pid, torch.zeros((0, p.data[0].size), dtype=torch.complex128, device="cuda"))
+        assert sv.wait(t) == L.OK and out.shape == (0, int(np.prod(p.dims)))
+        with pytest.raises(KeyError):
+            sv.enqueue(pid + 7, torch.from_numpy(p.data[:1]).cuda())
+        with pytest.raises(L.PinvError, match="INVALID_ARG"):
+            L.check(L.load().pinv_serve_enqueue(sv._h, pid + 7, None, None, 1, L.C128, None, None,
+                                                L.C.byref(L.C.c_uint64())))
