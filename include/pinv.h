@@ -102,9 +102,18 @@ typedef struct {
     int refine_residual;          /* mixed plans: pinv_residual arithmetic of the residual */
 } pinv_plan_desc;
 
+/* How the refinement forms the normal-equation residual r = E^H (d - E x) - lambda x.
+ * DOUBLE_FLOAT and FP64 generate E twice per step (2 N M F complex MACs).
+ * TOEPLITZ uses the identity r = E^H d - G x with the exact Gram G: without B0
+ * and with voxels on the grid, (A^H A)[n][n'] depends only on the grid offset
+ * between n and n' (Eq. 2), so G is formed in FP64 from a (2n_x-1)(2n_y-1)(2n_z-1)
+ * table and the coil products at build time and stored as double-float
+ * [N][N] (16 N^2 bytes); each apply forms E^H d once (double-float) and each
+ * step costs N^2 F complex MACs. Plans with b0_hz reject TOEPLITZ. */
 typedef enum {
     PINV_RESIDUAL_DOUBLE_FLOAT = 0, /* r in double-float (hi + lo floats, ~44 bits) on the FP32 units */
-    PINV_RESIDUAL_FP64 = 1          /* r in FP64 (DFMA); FP64 plans always use this */
+    PINV_RESIDUAL_FP64 = 1,         /* r in FP64 (DFMA); FP64 plans always use this */
+    PINV_RESIDUAL_TOEPLITZ = 2      /* r = E^H d - G x, exact G from the Toeplitz table, double-float */
 } pinv_residual;
 
 typedef struct {
@@ -178,7 +187,8 @@ typedef enum {
     PINV_EXPORT_CHOL = 1,    /* [N][N] c128: lower triangle of L */
     PINV_EXPORT_GINV = 2,    /* [N][N] c128: G^-1, full */
     PINV_EXPORT_RECON = 3,   /* [N][C*M_k]: Recon = E^+, c128 (FP64 plans) or c64 (mixed) */
-    PINV_EXPORT_LINV = 4     /* [N][N] c128: W = L^-1 (mixed plans; UNSUPPORTED for FP64 plans) */
+    PINV_EXPORT_LINV = 4,    /* [N][N] c128: W = L^-1 (mixed plans; UNSUPPORTED for FP64 plans) */
+    PINV_EXPORT_GRAM_EXACT = 5 /* [N][N] c128: the exact Gram of TOEPLITZ-residual plans, full */
 } pinv_export_what;
 
 /*

@@ -21,8 +21,9 @@ FP64, MIXED_BF16X3, MIXED_BF16X6 = 0, 1, 2
 LAMBDA_ABS, LAMBDA_REL_MEAN_DIAG = 0, 1
 C64, C128 = 0, 1
 RECON_AUTO, RECON_NONE, RECON_STORE = -1, 0, 1
-RESIDUAL_DOUBLE_FLOAT, RESIDUAL_FP64 = 0, 1
-EXPORT_GRAM, EXPORT_CHOL, EXPORT_GINV, EXPORT_RECON, EXPORT_LINV = 0, 1, 2, 3, 4
+RESIDUAL_DOUBLE_FLOAT, RESIDUAL_FP64, RESIDUAL_TOEPLITZ = 0, 1, 2
+RESIDUAL_AUTO = -1  # binding-side default: TOEPLITZ without B0, else DOUBLE_FLOAT
+EXPORT_GRAM, EXPORT_CHOL, EXPORT_GINV, EXPORT_RECON, EXPORT_LINV, EXPORT_GRAM_EXACT = 0, 1, 2, 3, 4, 5
 
 _STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "BUDGET", 4: "NOT_PD", 5: "NOT_BUILT",
                  6: "TIMEOUT", 7: "CUDA", 8: "INTERNAL", 9: "UNSUPPORTED"}
@@ -136,7 +137,7 @@ def _dptr(a: np.ndarray | None, ctype):
 def make_desc(dims, traj, coil_maps=None, b0_hz=None, times=None, lam=1e-3,
               lambda_mode=LAMBDA_REL_MEAN_DIAG, precision=FP64, recon_mode=RECON_STORE,
               voxel_index=None, fov=None, refine_max_iters=0, refine_tol=0.0,
-              refine_residual=RESIDUAL_DOUBLE_FLOAT):
+              refine_residual=RESIDUAL_AUTO):
     """Build a PlanDesc plus the numpy arrays that must outlive the create call."""
     dims = [int(d) for d in dims]
     ndim = len(dims)
@@ -172,5 +173,7 @@ def make_desc(dims, traj, coil_maps=None, b0_hz=None, times=None, lam=1e-3,
     d.recon_mode = int(recon_mode)
     d.refine_max_iters = int(refine_max_iters)
     d.refine_tol = float(refine_tol)
+    if refine_residual == RESIDUAL_AUTO:
+        refine_residual = RESIDUAL_DOUBLE_FLOAT if b0_hz is not None else RESIDUAL_TOEPLITZ
     d.refine_residual = int(refine_residual)
     return d, keep

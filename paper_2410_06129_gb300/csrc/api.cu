@@ -104,9 +104,13 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
     p->precision = d->precision;
     p->refine_iters = d->refine_max_iters;
     p->refine_tol = d->refine_tol;
-    if (d->refine_residual != PINV_RESIDUAL_DOUBLE_FLOAT && d->refine_residual != PINV_RESIDUAL_FP64)
+    if (d->refine_residual != PINV_RESIDUAL_DOUBLE_FLOAT && d->refine_residual != PINV_RESIDUAL_FP64 &&
+        d->refine_residual != PINV_RESIDUAL_TOEPLITZ)
         return cleanup(fail(PINV_ERR_INVALID_ARG, "unknown refine_residual"));
+    if (d->refine_residual == PINV_RESIDUAL_TOEPLITZ && d->b0_hz && p->precision != PINV_FP64)
+        return cleanup(fail(PINV_ERR_UNSUPPORTED, "the Toeplitz residual needs a plan without B0"));
     p->refine_residual = p->precision == PINV_FP64 ? PINV_RESIDUAL_FP64 : d->refine_residual;
+    const bool toeplitz = p->refine_residual == PINV_RESIDUAL_TOEPLITZ;
 
     // voxel grid coordinates
     std::vector<int> ijk(3 * p->N);
@@ -239,8 +243,8 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
             e.T = T;
         }
     }
-    if (p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT) {
-        // double-float copies of the tables for the refinement residual
+    if (p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT || toeplitz) {
+        // double-float copies of the tables for the refinement residual / E^H d
         float4 *xdf, *ydf, *zdf;
         AL(xdf, sizeof(float4) * p->Mk * e.nx, "exdf");
         AL(ydf, sizeof(float4) * p->Mk * e.ny, "eydf");
@@ -273,6 +277,10 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
     else {
         AL(p->W, sizeof(double2) * p->N * p->N, "W");
         AL(p->W32, sizeof(float2) * p->N * p->N, "W32");
+    }
+    if (toeplitz) {
+        AL(p->Ttab, sizeof(double2) * (2 * e.nx - 1) * (2 * e.ny - 1) * (2 * e.nz - 1), "Toeplitz table");
+        AL(p->Gx, sizeof(float4) * p->N * p->N, "exact Gram");
     }
     int rm = d->recon_mode;
     if (rm == PINV_RECON_AUTO) {
@@ -320,6 +328,14 @@ pinv_status pinv_build(pinv_plan* p, void* stream) {
     if (mixed) CK(launch_gram_tc(p->enc, p->lambda_abs, slices, p->G, ld, p->st, s));
     else CK(launch_gram64(p->enc, p->lambda_abs, p->G, ld, s));
     if (p->Gkeep) CK(cudaMemcpyAsync(p->Gkeep, p->G, sizeof(double2) * N * N, cudaMemcpyDeviceToDevice, s));
+    if (p->Gx) {
+        // exact Gram for the refinement residual (Toeplitz table, then coil products)
+        double2* work = nullptr;
+        CK(cudaMallocAsync((void**)&work, toeplitz_work_bytes(p->enc), s));
+        CK(launch_toeplitz64(p->enc, work, p->Ttab, s));
+        CK(cudaFreeAsync(work, s));
+        CK(launch_gram_exact(p->enc, p->Ttab, p->lambda_abs, p->Gx, s));
+    }
     CK(cudaEventRecord(p->ev[2], s));
     if (mixed) {
         // FP64 diagonal panels, tensor-core panel solves / trailing updates,
@@ -412,6 +428,10 @@ pinv_status pinv_plan_export(const pinv_plan* p, int what, void* dst, size_t byt
             if (!p->W) return fail(PINV_ERR_UNSUPPORTED, "only mixed-precision plans keep L^-1");
             src = p->W;
             break;
+        case PINV_EXPORT_GRAM_EXACT:
+            if (!p->Gx) return fail(PINV_ERR_UNSUPPORTED, "only TOEPLITZ-residual plans keep the exact Gram");
+            src = p->Gx;
+            break;
         case PINV_EXPORT_RECON:
             if (!p->recon) return fail(PINV_ERR_UNSUPPORTED, "factor-only plan has no Recon");
             src = p->R;
@@ -422,6 +442,8 @@ pinv_status pinv_plan_export(const pinv_plan* p, int what, void* dst, size_t byt
     if (bytes < need) return fail(PINV_ERR_INVALID_ARG, "destination too small");
     if (what == PINV_EXPORT_CHOL) {
         CK(launch_copy_lower(p->G, p->N, p->N, (double2*)dst, s));
+    } else if (what == PINV_EXPORT_GRAM_EXACT) {
+        CK(launch_from_df(p->Gx, p->N * p->N, (double2*)dst, s));
     } else if (what == PINV_EXPORT_GINV && !p->Ginv) {
         // mixed plans keep W = L^-1; G^-1 = W^H W is formed in FP64 on request
         CK(launch_lauum64(p->W, p->N, p->N, (double2*)dst, s));

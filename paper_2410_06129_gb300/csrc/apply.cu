@@ -38,30 +38,48 @@ struct Carver {
 };
 }  // namespace
 
+// Which arithmetic an apply of plan p runs (shared by the layout and the apply).
+struct ApplyModes {
+    bool mixed, refine, stop_rule, toep, dfres, fpres, need_b;
+};
+static ApplyModes apply_modes(const pinv_plan* p) {
+    ApplyModes m;
+    m.mixed = p->precision != PINV_FP64;
+    m.refine = p->refine_iters > 0;
+    m.stop_rule = m.refine && p->refine_tol > 0.0;
+    m.toep = m.mixed && p->refine_residual == PINV_RESIDUAL_TOEPLITZ;
+    m.dfres = m.mixed && p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT;
+    m.fpres = m.mixed && p->refine_residual == PINV_RESIDUAL_FP64;
+    // E^H d formed once in double-float: the exact-Gram residual needs it, and
+    // mixed factor-only plans start from x = W^H W E^H d
+    m.need_b = (m.toep && m.refine) || (m.mixed && !p->recon && !m.fpres);
+    return m;
+}
+
 size_t apply_scratch_layout(const pinv_plan* p, int64_t F, int dtype, void* base, ApplyScratch* sc) {
     const int64_t N = p->N, M = p->M;
-    const bool mixed = p->precision != PINV_FP64;
-    const bool refine = p->refine_iters > 0;
-    const bool stop_rule = refine && p->refine_tol > 0.0;
-    const bool dfres = mixed && p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT;
-    // which buffers an apply needs: FP64 copy of c64 data, FP64 image for c64
-    // output, the refinement's data-space and image-space residuals, the mixed
-    // path's c64 data / image / correction buffers, and the per-frame norms
-    const bool need_d128 = dtype == PINV_C64 && (!mixed || !p->recon || refine);
+    const ApplyModes md = apply_modes(p);
+    // FP64 copy of c64 data (every path but the mixed Recon-only apply reads
+    // it), FP64 image for c64 output, data-space residual (E-generating
+    // residuals and the FP64 factor-only temporary), image-space residual,
+    // E^H d, the mixed path's c64 data / image / correction temporaries, and
+    // the per-frame norms of the stopping rule
+    const bool need_d128 = dtype == PINV_C64 && (!md.mixed || !p->recon || md.refine);
     const bool need_x128 = dtype == PINV_C64;
-    const bool need_u128 = refine || (mixed && !p->recon);
-    const bool need_r128 = refine || !p->recon;
-    const bool need_d64 = mixed && p->recon && dtype == PINV_C128;
-    const bool need_x64 = mixed && (p->recon || (refine && dfres));
+    const bool need_u128 = (md.refine && !md.toep) || (md.fpres && !p->recon);
+    const bool need_r128 = md.refine || !p->recon;
+    const bool need_d64 = md.mixed && p->recon && dtype == PINV_C128;
+    const bool need_x64 = md.mixed && (p->recon || md.dfres || md.toep);
     Carver cv{static_cast<unsigned char*>(base)};
     ApplyScratch s{};
     s.d128 = need_d128 ? cv.take<double2>((size_t)(F * M)) : nullptr;
     s.x128 = need_x128 ? cv.take<double2>((size_t)(F * N)) : nullptr;
     s.u128 = need_u128 ? cv.take<double2>((size_t)(F * M)) : nullptr;
     s.r128 = need_r128 ? cv.take<double2>((size_t)(F * N)) : nullptr;
+    s.b128 = md.need_b ? cv.take<double2>((size_t)(F * N)) : nullptr;
     s.d64 = need_d64 ? cv.take<float2>((size_t)(F * M)) : nullptr;
     s.x64 = need_x64 ? cv.take<float2>((size_t)(F * N)) : nullptr;
-    s.norms = stop_rule ? cv.take<double>((size_t)(2 * F)) : nullptr;
+    s.norms = md.stop_rule ? cv.take<double>((size_t)(2 * F)) : nullptr;
     if (sc) *sc = s;
     return cv.used;
 }
@@ -79,10 +97,7 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
                        const ApplyScratch& sc) {
     if (F == 0) return PINV_OK;
     const int64_t N = p->N, M = p->M;
-    const bool mixed = p->precision != PINV_FP64;
-    const bool refine = p->refine_iters > 0;
-    const bool stop_rule = refine && p->refine_tol > 0.0;
-    const bool dfres = mixed && p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT;
+    const ApplyModes md = apply_modes(p);
     p->last_refine_iters = 0;
     p->last_refine_resid = 0;
 
@@ -96,7 +111,8 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
     }
     double2* X = dtype == PINV_C128 ? (double2*)d_image : sc.x128;
 
-    if (!mixed) {
+    if (md.need_b) CKA(launch_adjoint_df(p->enc, D, F, 0.0, nullptr, sc.b128, s));  // b = E^H d
+    if (!md.mixed) {
         if (p->recon) {
             CKA(launch_apply64((const double2*)p->R, N, M, D, F, X, s));
         } else {
@@ -112,35 +128,45 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
         }
         CKA(launch_apply32((const float2*)p->R, N, M, D32, F, sc.x64, s));
         CKA(launch_c64_to_c128(sc.x64, X, F * N, s));
-    } else {
-        // factor-only: x = W^H (W (E^H d)) with the mixed factor's inverse W
+    } else if (md.fpres) {
+        // factor-only, FP64 throughout: x = W^H (W (E^H d))
         CKA(launch_adjoint64(p->enc, D, F, 0.0, nullptr, sc.r128, s));
         CKA(launch_trmv64(p->W, N, sc.r128, F, sc.u128, s));
         CKA(launch_trmv_h64(p->W, N, sc.u128, F, nullptr, X, s));
+    } else {
+        // factor-only: x = W^H (W b) with b = E^H d in double-float
+        CKA(cudaMemsetAsync(X, 0, sizeof(double2) * F * N, s));
+        CKA(launch_correct32(p->W32, N, sc.b128, F, sc.x64, X, s));
     }
 
-    // Residual refinement: r = E^H (d - E x) - lambda x, then x += G^-1 r.
-    // Mixed plans need it to reach FP64-level accuracy; FP64 plans may use it
-    // to remove the explicit inverse's extra rounding (kappa(G) u). With
-    // refine_tol == 0 a fixed number of steps runs without host reads.
-    if (refine) {
-        if (stop_rule) {
-            CKA(launch_adjoint64(p->enc, D, F, 0.0, nullptr, sc.r128, s));  // b = E^H d
-            CKA(launch_frame_norms(sc.r128, F, N, sc.norms + F, s));
+    // Residual refinement: r = E^H (d - E x) - lambda x (= E^H d - G x), then
+    // x += G^-1 r. Mixed plans need it to reach FP64-level accuracy; FP64 plans
+    // may use it to remove the explicit inverse's extra rounding (kappa(G) u).
+    // With refine_tol == 0 a fixed number of steps runs without host reads.
+    if (md.refine) {
+        if (md.stop_rule) {
+            if (md.need_b) {
+                CKA(launch_frame_norms(sc.b128, F, N, sc.norms + F, s));
+            } else {
+                CKA(launch_adjoint64(p->enc, D, F, 0.0, nullptr, sc.r128, s));  // b = E^H d
+                CKA(launch_frame_norms(sc.r128, F, N, sc.norms + F, s));
+            }
         }
         for (int it = 0; it < p->refine_iters; ++it) {
-            if (dfres) {
+            if (md.toep) {
+                CKA(launch_gram_resid_df(p->Gx, N, sc.b128, X, F, sc.r128, s));  // r = b - G x
+            } else if (md.dfres) {
                 CKA(launch_forward_df(p->enc, X, F, D, sc.u128, s));  // u = d - E x
                 CKA(launch_adjoint_df(p->enc, sc.u128, F, p->lambda_abs, X, sc.r128, s));
             } else {
                 CKA(launch_forward64(p->enc, X, F, D, sc.u128, s));
                 CKA(launch_adjoint64(p->enc, sc.u128, F, p->lambda_abs, X, sc.r128, s));
             }
-            if (stop_rule) CKA(launch_frame_norms(sc.r128, F, N, sc.norms, s));
-            if (dfres) {
+            if (md.stop_rule) CKA(launch_frame_norms(sc.r128, F, N, sc.norms, s));
+            if (md.dfres || md.toep) {
                 // the correction only preconditions the next residual: FP32 W suffices
                 CKA(launch_correct32(p->W32, N, sc.r128, F, sc.x64, X, s));
-            } else if (mixed) {
+            } else if (md.mixed) {
                 // x += W^H (W r) in FP64: never through an explicitly formed low-precision
                 // G^-1, whose error the correction would amplify by kappa(G)
                 CKA(launch_trmv64(p->W, N, sc.r128, F, sc.u128, s));
@@ -149,7 +175,7 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
                 CKA(launch_hemv64(p->Ginv, N, N, sc.r128, F, X, X, s));
             }
             p->last_refine_iters = it + 1;
-            if (!stop_rule) continue;
+            if (!md.stop_rule) continue;
             // per-frame ||r|| / ||E^H d||, read back in fixed-size chunks (no allocation)
             double worst = 0.0, hn[128], hb[128];
             for (int64_t f0 = 0; f0 < F; f0 += 128) {

@@ -218,6 +218,71 @@ cudaError_t launch_adjoint_df(const EncodeDev& e, const double2* U, int64_t F, d
     return launch_df(AdjointDF{e, U, X, R, lam, F}, e.N, F, s);
 }
 
+// ------------------------------------------------------------------ exact Gram residual
+// Exact Gram for B0-free plans, G[n][n'] = T[i_n - i_n'] sum_c conj(s_c(n)) s_c(n')
+// + lambda delta, formed in FP64 from the Toeplitz table and stored as
+// double-float pairs [N][N] (both triangles). The residual of the normal
+// equations is then r = E^H d - G x with E^H d formed once per apply.
+__global__ void k_gram_exact(EncodeDev e, const double2* T, double lam, float4* G) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // n'
+    const int64_t i = blockIdx.y;                                         // n
+    if (j >= e.N) return;
+    const int* gi = e.vox_ijk + 3 * i;
+    const int* gj = e.vox_ijk + 3 * j;
+    const int64_t Tx = 2 * e.nx - 1, Ty = 2 * e.ny - 1;
+    const int64_t t = ((int64_t)(gi[2] - gj[2] + e.nz - 1) * Ty + (gi[1] - gj[1] + e.ny - 1)) * Tx +
+                      (gi[0] - gj[0] + e.nx - 1);
+    double2 v = T[t];
+    if (e.coils) {
+        double2 sc = make_double2(0.0, 0.0);
+        for (int c = 0; c < e.C; ++c)
+            zfma(sc, zconj(e.coils[(int64_t)c * e.N + i]), e.coils[(int64_t)c * e.N + j]);
+        v = zmul(v, sc);
+    }
+    if (i == j) v.x += lam;
+    G[i * e.N + j] = to_df(v);
+}
+
+cudaError_t launch_gram_exact(const EncodeDev& e, const double2* T, double lam, float4* G, cudaStream_t s) {
+    dim3 grid((unsigned)((e.N + 255) / 256), (unsigned)e.N);
+    k_gram_exact<<<grid, 256, 0, s>>>(e, T, lam, G);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// R[f][n] = B[f][n] - sum_n' G[n][n'] X[f][n'], G Hermitian (read as conj(G[n'][n]))
+struct GramResidDF {
+    const float4* G;
+    const double2* B;
+    const double2* X;
+    double2* R;
+    int64_t N, F;
+    __device__ int64_t K() const { return N; }
+    __device__ bool a_ok(int64_t i) const { return i < N; }
+    __device__ bool b_ok(int64_t j) const { return j < F; }
+    __device__ float4 a(int64_t i, int64_t k) const { return cdf_conj(G[k * N + i]); }
+    __device__ float4 b(int64_t k, int64_t j) const { return to_df(X[j * N + k]); }
+    __device__ void store(int64_t i, int64_t j, double2 v) const { R[j * N + i] = zsub(B[j * N + i], v); }
+};
+
+cudaError_t launch_gram_resid_df(const float4* G, int64_t N, const double2* B, const double2* X, int64_t F,
+                                 double2* R, cudaStream_t s) {
+    if (F == 0) return cudaSuccess;
+    return launch_df(GramResidDF{G, B, X, R, N, F}, N, F, s);
+}
+
+__global__ void k_from_df(const float4* a, int64_t n, double2* b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = from_df(a[i]);
+}
+
+cudaError_t launch_from_df(const float4* a, int64_t n, double2* b, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_from_df<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, n, b);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ FP32 correction x += W^H (W r)
 template <int BM, int BN, int TM, int TN, class P, int BK = 16>
 __global__ void __launch_bounds__(256) k_ctile(P p) {

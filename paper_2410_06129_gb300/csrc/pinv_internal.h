@@ -188,6 +188,13 @@ bool tc_available();
 // ---------------------------------------------------------------------------
 cudaError_t launch_to_df(const double2* src, float4* dst, int64_t n, cudaStream_t s);
 // U[f] = D[f] - E X[f], double-float arithmetic, FP64 in/out
+// exact Gram of B0-free grid plans (Toeplitz table, FP64; stored double-float)
+size_t toeplitz_work_bytes(const EncodeDev& e);
+cudaError_t launch_toeplitz64(const EncodeDev& e, double2* work, double2* T, cudaStream_t s);
+cudaError_t launch_gram_exact(const EncodeDev& e, const double2* T, double lam, float4* G, cudaStream_t s);
+cudaError_t launch_gram_resid_df(const float4* G, int64_t N, const double2* B, const double2* X, int64_t F,
+                                 double2* R, cudaStream_t s);
+cudaError_t launch_from_df(const float4* a, int64_t n, double2* b, cudaStream_t s);
 cudaError_t launch_forward_df(const EncodeDev& e, const double2* X, int64_t F, const double2* D, double2* U,
                               cudaStream_t s);
 // R[f] = E^H U[f] - lam X[f] (X may be null), double-float arithmetic, FP64 in/out

@@ -19,6 +19,7 @@ struct ApplyScratch {
     double2* x128;  // FP64 image for c64 output [F][N]
     double2* u128;  // data-space residual / trmv temporary [F][M]
     double2* r128;  // image-space residual [F][N]
+    double2* b128;  // E^H d [F][N] (factor-only and exact-Gram refinement)
     float2* d64;    // c64 copy of c128 data [F][M]
     float2* x64;    // c64 image / FP32 correction temporary [F][N]
     double* norms;  // per-frame squared norms [2F]
@@ -62,6 +63,8 @@ struct pinv_plan {
     double2* W = nullptr;      // L^-1, lower (mixed plans)
     float2* W32 = nullptr;     // FP32 copy of W (mixed plans)
     void* R = nullptr;         // Recon [N][M], c128 (FP64) or c64 (mixed)
+    double2* Ttab = nullptr;   // Toeplitz table of A^H A (TOEPLITZ residual)
+    float4* Gx = nullptr;      // exact Gram, double-float [N][N] (TOEPLITZ residual)
     pinv::DevStatus* st = nullptr;        // device status word
     pinv::DevStatus* st_host = nullptr;   // pinned copy, written at the end of each build
 

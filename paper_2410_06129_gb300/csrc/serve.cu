@@ -115,6 +115,7 @@ size_t plan_footprint(const pinv_plan_desc& d) {
     int recon = d.recon_mode;
     if (recon == PINV_RECON_AUTO) recon = N * M * (fp64 ? 16.0 : 8.0) <= 64.0 * (1ull << 30);
     if (recon) b += N * M * (fp64 ? 16.0 : 8.0);
+    if (!fp64 && d.refine_residual == PINV_RESIDUAL_TOEPLITZ) b += N * N * 16.0;  // exact Gram
     int width = 0;
     for (int i = 0; i < d.ndim; ++i) width += d.dims[i];
     b += (double)d.n_samples * width * 64.0 + N * d.n_coils * 40.0 + N * 64.0 + (double)(64u << 20);

@@ -125,6 +125,79 @@ cudaError_t launch_gram64(const EncodeDev& e, double lambda, double2* G, int64_t
 }
 
 // ---------------------------------------------------------------------------
+// Toeplitz table of A^H A for voxels on the grid without B0: (A^H A)[n][n']
+// depends only on the index offset (i_n - i_n') per axis, so
+//   T[dz][dy][dx] = sum_m q_x(m, dx) q_y(m, dy) q_z(m, dz),
+//   q(m, d) = exp(+i 2 pi k_m d fov / n_axis),
+// over offsets -(n-1)..(n-1) per axis ((2n-1) entries, dx fastest). q comes
+// from the phase table as conj(e[m][d]) e[m][0] (d >= 0) or conj(e[m][0])
+// e[m][-d] (d < 0), i.e. from the same pair of encoding elements the Gram
+// entry multiplies. Split over samples (blockIdx.z) into partial tables that
+// k_sum_parts adds in a fixed order, so the result is deterministic.
+// ---------------------------------------------------------------------------
+__device__ inline double2 toep_q(const double2* tab, int n, int64_t m, int d) {
+    if (n == 1) return make_double2(1.0, 0.0);
+    const double2* row = tab + m * n;
+    return d >= 0 ? zmul(zconj(row[d]), row[0]) : zmul(zconj(row[0]), row[-d]);
+}
+
+struct ToeplitzP {
+    static constexpr bool A_KFAST = false, B_KFAST = false;
+    EncodeDev e;
+    double2* parts;   // [splits][Tyz][Tx]
+    int64_t Tx, Ty, Tyz, chunk;
+    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = (int64_t)blockIdx.y * 64;
+        j0 = (int64_t)blockIdx.x * 64;
+        kb = (int64_t)blockIdx.z * chunk;
+        ke = kb + chunk < e.Mk ? kb + chunk : e.Mk;
+        return true;
+    }
+    __device__ bool a_ok(int64_t i) const { return i < Tx; }
+    __device__ bool b_ok(int64_t j) const { return j < Tyz; }
+    __device__ double2 a(int64_t i, int64_t m) const { return toep_q(e.ex, e.nx, m, (int)i - (e.nx - 1)); }
+    __device__ double2 b(int64_t m, int64_t j) const {
+        const int dy = (int)(j % Ty) - (e.ny - 1), dz = (int)(j / Ty) - (e.nz - 1);
+        return zmul(toep_q(e.ey, e.ny, m, dy), toep_q(e.ez, e.nz, m, dz));
+    }
+    __device__ void store(int64_t i, int64_t j, double2 v) const {
+        parts[((int64_t)blockIdx.z * Tyz + j) * Tx + i] = v;
+    }
+};
+
+__global__ void k_sum_parts(const double2* parts, int splits, int64_t n, double2* T) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 v = parts[i];
+    for (int z = 1; z < splits; ++z) v = zadd(v, parts[(int64_t)z * n + i]);
+    T[i] = v;
+}
+
+size_t toeplitz_work_bytes(const EncodeDev& e) {
+    const int64_t n = (int64_t)(2 * e.nx - 1) * (2 * e.ny - 1) * (2 * e.nz - 1);
+    return (size_t)n * sizeof(double2) * 64;  // at most 64 partial tables
+}
+
+cudaError_t launch_toeplitz64(const EncodeDev& e, double2* work, double2* T, cudaStream_t s) {
+    const int64_t Tx = 2 * e.nx - 1, Ty = 2 * e.ny - 1, Tyz = Ty * (2 * e.nz - 1);
+    const int64_t tiles = ((Tx + 63) / 64) * ((Tyz + 63) / 64);
+    // enough sample splits for about two CTAs per SM, each at least 256 samples
+    int64_t splits = (2 * 152 + tiles - 1) / tiles;
+    splits = std::min<int64_t>(splits, std::max<int64_t>(1, e.Mk / 256));
+    splits = std::max<int64_t>(1, std::min<int64_t>(splits, 64));
+    const int64_t chunk = (e.Mk + splits - 1) / splits;
+    splits = (e.Mk + chunk - 1) / chunk;
+    ToeplitzP p{e, work, Tx, Ty, Tyz, chunk};
+    dim3 grid((unsigned)((Tyz + 63) / 64), (unsigned)((Tx + 63) / 64), (unsigned)splits);
+    k_ztile<64, 64, 4, 4><<<grid, 256, 0, s>>>(p);
+    note_launch();
+    const int64_t n = Tx * Tyz;
+    k_sum_parts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(work, (int)splits, n, T);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Blocked Cholesky pieces
 // ---------------------------------------------------------------------------
 // panel solve: L[i][k0+j] = sum_k G[i][k0+k] conj(Dinv[j][k]) for rows i >= k0+NB

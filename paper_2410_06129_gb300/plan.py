@@ -25,7 +25,7 @@ class Plan:
     def __init__(self, dims, traj, coil_maps=None, b0_hz=None, times=None, lam=1e-3,
                  lambda_mode=L.LAMBDA_REL_MEAN_DIAG, precision=L.FP64,
                  recon_mode=L.RECON_STORE, voxel_index=None, fov=None,
-                 refine_max_iters=None, refine_tol=0.0, refine_residual=L.RESIDUAL_DOUBLE_FLOAT,
+                 refine_max_iters=None, refine_tol=0.0, refine_residual=L.RESIDUAL_AUTO,
                  keep_gram=False, stream=None):
         lib = L.load()
         if refine_max_iters is None:

@@ -26,7 +26,7 @@ class Server:
     def register(self, dims, traj, coil_maps=None, b0_hz=None, times=None, lam=1e-3,
                  lambda_mode=L.LAMBDA_REL_MEAN_DIAG, precision=L.FP64, recon_mode=L.RECON_STORE,
                  voxel_index=None, fov=None, refine_max_iters=None,
-                 refine_residual=L.RESIDUAL_DOUBLE_FLOAT) -> int:
+                 refine_residual=L.RESIDUAL_AUTO) -> int:
         if refine_max_iters is None:
             refine_max_iters = 1 if precision == L.FP64 else 3
         desc, keep = L.make_desc(dims, traj, coil_maps, b0_hz, times, lam, lambda_mode, precision,
