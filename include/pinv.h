@@ -210,6 +210,46 @@ pinv_status pinv_plan_info(const pinv_plan* plan, pinv_plan_info_t* out);
 void pinv_plan_destroy(pinv_plan* plan);
 
 /* ------------------------------------------------------------------------
+ * Batches. Many slices, time series or trajectories of uneven size, each its
+ * own plan, built and applied together. The build runs every plan's
+ * tensor-core Gram as one persistent launch, every plan's Recon as two more
+ * (T = W E^H, then W^H T; Eq. 8), and the per-plan Cholesky and triangular
+ * inverse concurrently on per-plan streams in between. The apply runs every
+ * plan's apply concurrently. With PINV_BATCH_GRAPH the build sequence is
+ * captured into a CUDA graph on the second pinv_batch_build call and replayed
+ * from then on; the apply sequence is captured on first use and again
+ * whenever its buffers, frame counts or dtype change. Graph capture needs a
+ * created stream (not the legacy default stream); applies of plans with a
+ * refinement stopping rule (refine_tol > 0) read the host and run uncaptured.
+ * Results are bit-identical to pinv_build / pinv_apply on each plan.
+ * The plans stay owned by the caller and must outlive the batch; while in a
+ * batch they should not be built or applied on their own concurrently.
+ * ---------------------------------------------------------------------- */
+typedef struct pinv_batch pinv_batch;
+#define PINV_BATCH_GRAPH 1
+
+/* Group n_plans plans of one precision (all FP64, or all mixed with the same
+ * slice count). Allocates the batch's tensor-core intermediates (W E^H and W^T
+ * for explicit-Recon plans: 8 N (M + N) bytes per plan). */
+pinv_status pinv_batch_create(pinv_plan* const* plans, int n_plans, int flags, pinv_batch** out);
+
+/* Build every plan (asynchronous on `stream`; errors via pinv_batch_sync). */
+pinv_status pinv_batch_build(pinv_batch* batch, void* cuda_stream);
+
+/* image_i = Recon_i x data_i (+ refinement) for every plan i: d_data[i] is
+ * [n_frames[i]][C_i][M_k,i] and d_image[i] is [n_frames[i]][N_i], device
+ * buffers of `dtype` owned by the caller. */
+pinv_status pinv_batch_apply(pinv_batch* batch, const void* const* d_data, void* const* d_image,
+                             const int64_t* n_frames, int dtype, void* cuda_stream);
+
+/* Wait for the batch's last build; returns the first plan's failure (its
+ * index in *failed_plan, -1 if none) or a batched-launch timeout. */
+pinv_status pinv_batch_sync(pinv_batch* batch, int* failed_plan);
+
+/* Free the batch (not its plans). NULL is a no-op. */
+void pinv_batch_destroy(pinv_batch* batch);
+
+/* ------------------------------------------------------------------------
  * Serving loop. Recon is built from the trajectory and encoding physics
  * before data arrive and each acquisition then needs only image = Recon x data
  * (Section 4.5, Section 5). A server keeps the factored plans of registered

@@ -93,6 +93,11 @@ SIGNATURES = {
     "pinv_plan_info": (C.c_int, [_VP, C.POINTER(PlanInfo)]),
     "pinv_plan_destroy": (None, [_VP]),
     "pinv_apply_noalloc": (C.c_int, [_VP, _VP, _VP, C.c_int64, C.c_int, _VP]),
+    "pinv_batch_create": (C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, C.POINTER(_VP)]),
+    "pinv_batch_build": (C.c_int, [_VP, _VP]),
+    "pinv_batch_apply": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(C.c_int64), C.c_int, _VP]),
+    "pinv_batch_sync": (C.c_int, [_VP, C.POINTER(C.c_int)]),
+    "pinv_batch_destroy": (None, [_VP]),
     "pinv_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(_VP)]),
     "pinv_serve_register": (C.c_int, [_VP, C.POINTER(PlanDesc), C.POINTER(C.c_int)]),
     "pinv_serve_enqueue": (C.c_int, [_VP, C.c_int, _VP, _VP, C.c_int64, C.c_int, _VP, _VP,
@@ -103,6 +108,7 @@ SIGNATURES = {
     "pinv_server_destroy": (None, [_VP]),
 }
 NOALLOC_SCRATCH_BYTES = 64 << 20
+BATCH_GRAPH = 1
 
 _lib = None
 

@@ -40,6 +40,95 @@ std::atomic<unsigned long long> g_launches{0};
 pinv_status set_error(pinv_status st, const std::string& msg) { return fail(st, msg); }
 }
 
+namespace pinv {
+
+pinv_status reset_status(pinv_plan* p, cudaStream_t s) {
+    CK(launch_reset_status(p->st, s));
+    return PINV_OK;
+}
+
+pinv_status build_begin(pinv_plan* p, cudaStream_t s) {
+    p->built = false;
+    pinv_status rs = reset_status(p, s);
+    if (rs != PINV_OK) return rs;
+    if (p->keep_gram && !p->Gkeep) {
+        pinv_status st = p->alloc((void**)&p->Gkeep, sizeof(double2) * p->N * p->N, "Gkeep");
+        if (st != PINV_OK) return st;
+    }
+    return PINV_OK;
+}
+
+pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
+    const int64_t N = p->N, ld = p->N;
+    if (main_gram) {
+        if (p->precision != PINV_FP64) CK(launch_gram_tc(p->enc, p->lambda_abs, p->slices(), p->G, ld, p->st, s));
+        else CK(launch_gram64(p->enc, p->lambda_abs, p->G, ld, s));
+    }
+    if (p->Gkeep) CK(cudaMemcpyAsync(p->Gkeep, p->G, sizeof(double2) * N * N, cudaMemcpyDeviceToDevice, s));
+    if (p->Gx) {
+        // exact Gram for the refinement residual (Toeplitz table, then coil products)
+        double2* work = nullptr;
+        CK(cudaMallocAsync((void**)&work, toeplitz_work_bytes(p->enc), s));
+        CK(launch_toeplitz64(p->enc, work, p->Ttab, s));
+        CK(cudaFreeAsync(work, s));
+        CK(launch_gram_exact(p->enc, p->Ttab, p->lambda_abs, p->Gx, s));
+    }
+    return PINV_OK;
+}
+
+pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events) {
+    const int64_t N = p->N, ld = p->N;
+    if (p->precision != PINV_FP64) {
+        // FP64 diagonal panels, tensor-core panel solves / trailing updates,
+        // then the triangular inverse W = L^-1 on tensor cores
+        const int64_t nblk = (N + 63) / 64;
+        float2 *L32 = nullptr, *D32 = nullptr;
+        CK(cudaMallocAsync((void**)&L32, sizeof(float2) * N * N, s));
+        CK(cudaMallocAsync((void**)&D32, sizeof(float2) * nblk * 64 * 64, s));
+        CK(launch_potrf_tc(p->G, N, ld, p->Dinv, D32, L32, p->slices(), p->st, s));
+        CK(launch_pivot_stats(p->G, N, ld, p->st, s));
+        if (events) CK(cudaEventRecord(p->ev[3], s));
+        CK(launch_trtri_tc(L32, N, D32, p->W, p->W32, p->slices(), p->st, s));
+        CK(cudaFreeAsync(D32, s));
+        CK(cudaFreeAsync(L32, s));
+    } else {
+        CK(launch_potrf64(p->G, N, ld, p->Dinv, p->st, s));
+        CK(launch_pivot_stats(p->G, N, ld, p->st, s));
+        if (events) CK(cudaEventRecord(p->ev[3], s));
+        double2* W = nullptr;
+        CK(cudaMallocAsync((void**)&W, sizeof(double2) * N * N, s));
+        CK(launch_trtri64(p->G, N, ld, p->Dinv, W, s));
+        CK(launch_lauum64(W, N, ld, p->Ginv, s));
+        CK(cudaFreeAsync(W, s));
+    }
+    return PINV_OK;
+}
+
+pinv_status build_recon(pinv_plan* p, cudaStream_t s) {
+    if (!p->recon) return PINV_OK;
+    const int64_t N = p->N;
+    if (p->precision != PINV_FP64) {
+        // Recon = W^H (W E^H) (Eq. 8) through an [N][M] c64 intermediate
+        float2 *T = nullptr, *WT32 = nullptr;
+        CK(cudaMallocAsync((void**)&T, sizeof(float2) * N * p->M, s));
+        CK(cudaMallocAsync((void**)&WT32, sizeof(float2) * N * N, s));
+        CK(launch_transpose32(p->W32, N, N, WT32, N, s));
+        CK(launch_recon_tc(p->enc, p->W32, WT32, T, p->slices(), (float2*)p->R, p->st, s));
+        CK(cudaFreeAsync(WT32, s));
+        CK(cudaFreeAsync(T, s));
+    } else {
+        CK(launch_recon64(p->enc, p->Ginv, N, (double2*)p->R, s));
+    }
+    return PINV_OK;
+}
+
+pinv_status build_end(pinv_plan* p, cudaStream_t s) {
+    CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    return PINV_OK;
+}
+
+}  // namespace pinv
+
 extern "C" {
 
 int pinv_version(void) { return 100; }
@@ -47,18 +136,6 @@ int pinv_version(void) { return 100; }
 unsigned long long pinv_kernel_launches(void) { return g_launches.load(); }
 
 const char* pinv_last_error(void) { return g_err.c_str(); }
-
-static pinv_status reset_status(pinv_plan* p, cudaStream_t s) {
-    DevStatus h{};
-    h.not_pd_pivot = INT_MAX;
-    h.timeout_site = 0;
-    h.error_code = 0;
-    h.min_pivot = INFINITY;
-    h.max_pivot = 0.0;
-    // small pageable copy: the staging makes it safe to return immediately
-    CK(cudaMemcpyAsync(p->st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
-    return PINV_OK;
-}
 
 pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** out) {
     g_err.clear();
@@ -313,71 +390,16 @@ pinv_status pinv_build(pinv_plan* p, void* stream) {
     g_err.clear();
     if (!p) return fail(PINV_ERR_INVALID_ARG, "null plan");
     cudaStream_t s = (cudaStream_t)stream;
-    p->built = false;
-    pinv_status rs = reset_status(p, s);
-    if (rs != PINV_OK) return rs;
-    if (p->keep_gram && !p->Gkeep) {
-        pinv_status st = p->alloc((void**)&p->Gkeep, sizeof(double2) * p->N * p->N, "Gkeep");
-        if (st != PINV_OK) return st;
-    }
-    const int64_t N = p->N, ld = p->N;
-    const bool mixed = p->precision != PINV_FP64;
-    const int slices = p->precision == PINV_MIXED_BF16X6 ? 3 : 2;
+    pinv_status st = build_begin(p, s);
+    if (st != PINV_OK) return st;
     CK(cudaEventRecord(p->ev[0], s));
     CK(cudaEventRecord(p->ev[1], s));  // tables were built at plan creation
-    if (mixed) CK(launch_gram_tc(p->enc, p->lambda_abs, slices, p->G, ld, p->st, s));
-    else CK(launch_gram64(p->enc, p->lambda_abs, p->G, ld, s));
-    if (p->Gkeep) CK(cudaMemcpyAsync(p->Gkeep, p->G, sizeof(double2) * N * N, cudaMemcpyDeviceToDevice, s));
-    if (p->Gx) {
-        // exact Gram for the refinement residual (Toeplitz table, then coil products)
-        double2* work = nullptr;
-        CK(cudaMallocAsync((void**)&work, toeplitz_work_bytes(p->enc), s));
-        CK(launch_toeplitz64(p->enc, work, p->Ttab, s));
-        CK(cudaFreeAsync(work, s));
-        CK(launch_gram_exact(p->enc, p->Ttab, p->lambda_abs, p->Gx, s));
-    }
+    if ((st = build_gram(p, s, true)) != PINV_OK) return st;
     CK(cudaEventRecord(p->ev[2], s));
-    if (mixed) {
-        // FP64 diagonal panels, tensor-core panel solves / trailing updates,
-        // then the triangular inverse and G^-1 = W^H W on tensor cores
-        const int64_t nblk = (N + 63) / 64;
-        float2 *L32 = nullptr, *D32 = nullptr, *W32 = p->W32;
-        CK(cudaMallocAsync((void**)&L32, sizeof(float2) * N * N, s));
-        CK(cudaMallocAsync((void**)&D32, sizeof(float2) * nblk * 64 * 64, s));
-        CK(launch_potrf_tc(p->G, N, ld, p->Dinv, D32, L32, slices, p->st, s));
-        CK(launch_pivot_stats(p->G, N, ld, p->st, s));
-        CK(cudaEventRecord(p->ev[3], s));
-        CK(launch_trtri_tc(L32, N, D32, p->W, W32, slices, p->st, s));
-        CK(cudaFreeAsync(D32, s));
-        CK(cudaFreeAsync(L32, s));
-        CK(cudaEventRecord(p->ev[4], s));
-        if (p->recon) {
-            // Recon = W^H (W E^H) (Eq. 8) through an [N][M] c64 intermediate
-            float2 *T = nullptr, *WT32 = nullptr;
-            CK(cudaMallocAsync((void**)&T, sizeof(float2) * N * p->M, s));
-            CK(cudaMallocAsync((void**)&WT32, sizeof(float2) * N * N, s));
-            CK(launch_transpose32(W32, N, N, WT32, N, s));
-            CK(launch_recon_tc(p->enc, W32, WT32, T, slices, (float2*)p->R, p->st, s));
-            CK(cudaFreeAsync(WT32, s));
-            CK(cudaFreeAsync(T, s));
-        }
-        CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-        CK(cudaEventRecord(p->ev[5], s));
-        p->built = true;
-        return PINV_OK;
-    } else {
-        CK(launch_potrf64(p->G, N, ld, p->Dinv, p->st, s));
-        CK(launch_pivot_stats(p->G, N, ld, p->st, s));
-        CK(cudaEventRecord(p->ev[3], s));
-        double2* W = nullptr;
-        CK(cudaMallocAsync((void**)&W, sizeof(double2) * N * N, s));
-        CK(launch_trtri64(p->G, N, ld, p->Dinv, W, s));
-        CK(launch_lauum64(W, N, ld, p->Ginv, s));
-        CK(cudaFreeAsync(W, s));
-    }
+    if ((st = build_factor(p, s, true)) != PINV_OK) return st;
     CK(cudaEventRecord(p->ev[4], s));
-    if (p->recon) CK(launch_recon64(p->enc, p->Ginv, ld, (double2*)p->R, s));
-    CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    if ((st = build_recon(p, s)) != PINV_OK) return st;
+    if ((st = build_end(p, s)) != PINV_OK) return st;
     CK(cudaEventRecord(p->ev[5], s));
     p->built = true;
     return PINV_OK;

@@ -188,6 +188,31 @@ bool tc_available();
 // ---------------------------------------------------------------------------
 cudaError_t launch_to_df(const double2* src, float4* dst, int64_t n, cudaStream_t s);
 // U[f] = D[f] - E X[f], double-float arithmetic, FP64 in/out
+cudaError_t launch_reset_status(DevStatus* st, cudaStream_t s);
+
+// Several plans' tensor-core Gram or Recon in one persistent launch. The
+// problem descriptors are uploaded once (tc_multi_create) and stay valid
+// while the plans and buffers they point to live.
+struct TcPlanArgs {
+    const EncodeDev* e;
+    double lam;
+    double2* G;           // Gram output (lower tiles), ld = N
+    const float2* W32;    // W = L^-1, FP32 [N][N]
+    const float2* WT32;   // W^T, FP32 [N][N]
+    float2* T;            // W E^H intermediate [N][M]
+    float2* R;            // Recon [N][M]
+};
+enum TcMultiKind { TC_MULTI_GRAM = 0, TC_MULTI_RECON1 = 1, TC_MULTI_RECON2 = 2 };
+struct TcMulti {
+    void* buf = nullptr;
+    int kind = 0, n = 0;
+    int64_t items = 0;
+    size_t off_start = 0, off_gx = 0;
+};
+cudaError_t tc_multi_create(int kind, const TcPlanArgs* args, int n, TcMulti* out);
+cudaError_t tc_multi_launch(const TcMulti& m, int slices, DevStatus* st, cudaStream_t s);
+void tc_multi_free(TcMulti* m);
+
 // exact Gram of B0-free grid plans (Toeplitz table, FP64; stored double-float)
 size_t toeplitz_work_bytes(const EncodeDev& e);
 cudaError_t launch_toeplitz64(const EncodeDev& e, double2* work, double2* T, cudaStream_t s);

@@ -34,6 +34,18 @@ pinv_status apply_check(const pinv_plan* p, const void* d_data, void* d_image, i
 // refinement's stopping rule (refine_tol > 0) is on.
 pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t F, int dtype, cudaStream_t s,
                        const ApplyScratch& sc);
+
+// Build stages, in order (pinv_build runs them all on one stream; the batch
+// runs the tensor-core Gram and Recon of several plans as shared launches).
+pinv_status reset_status(pinv_plan* p, cudaStream_t s);
+pinv_status build_begin(pinv_plan* p, cudaStream_t s);
+// main_gram: the plan's own Gram launch (false when a batched launch formed G)
+pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram);
+// Cholesky, pivot statistics and the inverse (W = L^-1, or G^-1 for FP64 plans)
+pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events);
+pinv_status build_recon(pinv_plan* p, cudaStream_t s);
+// status word to pinned host memory
+pinv_status build_end(pinv_plan* p, cudaStream_t s);
 }  // namespace pinv
 
 struct pinv_plan {
@@ -76,6 +88,8 @@ struct pinv_plan {
     int last_refine_iters = 0;
     double last_refine_resid = 0;
     int info = -1;
+
+    int slices() const { return precision == PINV_MIXED_BF16X6 ? 3 : 2; }
 
     pinv_status alloc(void** p, size_t n, const char* what) {
         if (n == 0) n = 16;

@@ -7,6 +7,8 @@
 // Section 3.3, exp(-i2pi df_n t_m), depends on the sample only through its
 // time; samples sharing a time (same position within a readout) share a row.
 // Arguments are reduced modulo one cycle in FP64 before sincospi.
+#include <climits>
+
 #include "pinv_internal.h"
 
 namespace pinv {
@@ -201,6 +203,22 @@ cudaError_t launch_transpose32(const float2* src, int64_t rows, int64_t cols, fl
     if (rows == 0 || cols == 0) return cudaSuccess;
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((ldd + 31) / 32));
     k_transpose32<<<grid, dim3(32, 8), 0, s>>>(src, rows, cols, dst, ldd);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// status word back to "no error" (a kernel, so that builds can be captured in graphs)
+__global__ void k_reset_status(DevStatus* st) {
+    st->not_pd_pivot = INT_MAX;
+    st->timeout_site = 0;
+    st->error_code = 0;
+    st->pad = 0;
+    st->min_pivot = INFINITY;
+    st->max_pivot = 0.0;
+}
+
+cudaError_t launch_reset_status(DevStatus* st, cudaStream_t s) {
+    k_reset_status<<<1, 1, 0, s>>>(st);
     note_launch();
     return cudaGetLastError();
 }

@@ -210,8 +210,44 @@ __device__ inline void drain_to_total(uint32_t taddr_row, bool first) {
     tmem_wait_st();
 }
 
-template <int S, class P>
-__global__ void __launch_bounds__(NTHREADS, 1) k_tc(P p, DevStatus* st, int site) {
+// Tile schedulers of the persistent kernel: item t -> (problem, bx, by).
+// OneProblem covers a gx x gy grid of tiles of one problem; ManyProblems
+// concatenates the tile grids of several problems (e.g. one per plan of a
+// batch) held in device memory.
+template <class P>
+struct OneProblem {
+    P p;
+    int64_t gx, n;
+    __device__ int64_t count() const { return n; }
+    __device__ const P& get(int64_t t, int64_t& bx, int64_t& by) const {
+        bx = t % gx;
+        by = t / gx;
+        return p;
+    }
+};
+
+template <class P>
+struct ManyProblems {
+    const P* probs;         // [n]
+    const int64_t* start;   // [n + 1], first item of each problem
+    const int64_t* gx;      // [n], tile-grid width of each problem
+    int n;
+    __device__ int64_t count() const { return start[n]; }
+    __device__ const P& get(int64_t t, int64_t& bx, int64_t& by) const {
+        int i = 0;
+        while (i + 1 < n && start[i + 1] <= t) ++i;
+        const int64_t l = t - start[i];
+        bx = l % gx[i];
+        by = l / gx[i];
+        return probs[i];
+    }
+};
+
+// Persistent kernel: each CTA walks items blockIdx.x, blockIdx.x + gridDim.x, ...
+// The stage ring and the TMEM accumulation groups run on counters that continue
+// across tiles, so barriers are initialised and TMEM allocated once per CTA.
+template <int S, class Sched>
+__global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, int site) {
     using CF = Cfg<S>;
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[CF::STAGES], empty_bar[CF::STAGES];
@@ -219,12 +255,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(P p, DevStatus* st, int site
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_flag;
 
-    int64_t i0, j0, kb, ke;
-    if (!p.tile(i0, j0, kb, ke)) return;  // uniform per CTA
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = (int)((ke - kb + KC - 1) / KC);
-    const int ngroups = (nk + DRAIN - 1) / DRAIN;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < CF::STAGES; ++s) {
@@ -242,125 +274,141 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(P p, DevStatus* st, int site
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
+    const int q = warp & 3, h = warp >> 2;
+    const uint32_t taddr_row = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(64 * h);
 
-    if (warp < NPW) {
-        // ---------------- producers, drains, epilogue
-        const int q = warp & 3, h = warp >> 2;
-        const uint32_t taddr_row = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(64 * h);
-        int drained = 0;
-        bool ok = true;
-        auto drain = [&](int g) -> bool {
-            if (!mbar_wait(&tfull, (uint32_t)g & 1u, &abort_flag)) return false;
-            tc_fence_after();
-            drain_to_total(taddr_row, g == 0);
-            tc_fence_before();
-            mbar_arrive(&tempty);
-            return true;
-        };
-        const int ua = threadIdx.x;  // A unit: row ua & 127, k group ua >> 7
-        const int ubr = threadIdx.x & (BN - 1), ubg = threadIdx.x >> 7;
-        // per-thread operand contexts (row pointers, table rows) fixed for the tile
-        const auto ra = p.row_a(i0 + (ua & (BM - 1)));
-        const auto rb = p.row_b(j0 + ubr);
-        for (int kt = 0; kt < nk && ok; ++kt) {
-            // the MMA cannot start group g + 1 until group g is drained; drain it
-            // before the ring can only advance past that point
-            while (drained < ngroups && (drained + 1) * DRAIN + CF::STAGES - 1 <= kt) {
-                if (!(ok = drain(drained))) break;
+    const int64_t items = sch.count();
+    uint32_t kq = 0, gq = 0;  // stages and accumulation groups used by earlier tiles
+    for (int64_t t = blockIdx.x; t < items; t += gridDim.x) {
+        int64_t bx, by;
+        const auto& p = sch.get(t, bx, by);
+        int64_t i0, j0, kb, ke;
+        if (!p.tile(bx, by, i0, j0, kb, ke)) continue;  // uniform per CTA
+        const int nk = ke > kb ? (int)((ke - kb + KC - 1) / KC) : 0;
+        const int ngroups = (nk + DRAIN - 1) / DRAIN;
+
+        if (warp < NPW) {
+            // ---------------- producers, drains, epilogue
+            int drained = 0;
+            bool ok = true;
+            auto drain = [&](int g) -> bool {
+                if (!mbar_wait(&tfull, (gq + (uint32_t)g) & 1u, &abort_flag)) return false;
+                tc_fence_after();
+                drain_to_total(taddr_row, g == 0);
+                tc_fence_before();
+                mbar_arrive(&tempty);
+                return true;
+            };
+            const int ua = threadIdx.x;  // A unit: row ua & 127, k group ua >> 7
+            const int ubr = threadIdx.x & (BN - 1), ubg = threadIdx.x >> 7;
+            // per-thread operand contexts (row pointers, table rows) fixed for the tile
+            const auto ra = p.row_a(i0 + (ua & (BM - 1)));
+            const auto rb = p.row_b(j0 + ubr);
+            for (int kt = 0; kt < nk && ok; ++kt) {
+                // the MMA cannot start group g + 1 until group g is drained; drain it
+                // before the ring can only advance past that point
+                while (drained < ngroups && (drained + 1) * DRAIN + CF::STAGES - 1 <= kt) {
+                    if (!(ok = drain(drained))) break;
+                    ++drained;
+                }
+                if (!ok) break;
+                const uint32_t kg = kq + (uint32_t)kt;
+                const int s = (int)(kg % CF::STAGES);
+                const uint32_t ph = (kg / CF::STAGES) & 1u;
+                if (kg >= CF::STAGES && !(ok = mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag))) break;
+                uint8_t* base = smem + s * CF::STAGE_BYTES;
+                const int64_t k0 = kb + (int64_t)kt * KC;
+                {
+                    float2 v[8];
+                    const int r = ua & (BM - 1), g = ua >> 7;
+                    p.a8(ra, k0 + 8 * g, ke, v);
+                    float re[8], im[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) { re[u] = v[u].x; im[u] = v[u].y; }
+                    uint32_t wr[S][4], wi[S][4];
+                    split8<S>(re, wr);
+                    split8<S>(im, wi);
+                    store_slices<S>(base + koff(r, g), wr, 0u);
+                    store_slices<S>(base + koff(r, g + 2), wi, 0u);
+                }
+                {
+                    float2 v[8];
+                    p.b8(rb, k0 + 8 * ubg, ke, v);
+                    float re[8], im[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) { re[u] = v[u].x; im[u] = v[u].y; }
+                    uint32_t wr[S][4], wi[S][4];
+                    split8<S>(re, wr);
+                    split8<S>(im, wi);
+                    uint8_t* bb = base + A_SL;
+                    store_slices<S>(bb + koff(ubr, ubg), wr, 0u);                 // [Br | -Bi]
+                    store_slices<S>(bb + koff(ubr, ubg + 2), wi, 0x80008000u);
+                    store_slices<S>(bb + koff(BN + ubr, ubg), wi, 0u);            // [Bi |  Br]
+                    store_slices<S>(bb + koff(BN + ubr, ubg + 2), wr, 0u);
+                }
+                fence_proxy_async();
+                mbar_arrive(&full_bar[s]);
+            }
+            while (ok && drained < ngroups) {
+                ok = drain(drained);
                 ++drained;
             }
-            if (!ok) break;
-            const int s = kt % CF::STAGES;
-            const uint32_t ph = (uint32_t)(kt / CF::STAGES) & 1u;
-            if (kt >= CF::STAGES && !(ok = mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag))) break;
-            uint8_t* base = smem + s * CF::STAGE_BYTES;
-            const int64_t k0 = kb + (int64_t)kt * KC;
-            {
-                float2 v[8];
-                const int r = ua & (BM - 1), g = ua >> 7;
-                p.a8(ra, k0 + 8 * g, ke, v);
-                float re[8], im[8];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) { re[t] = v[t].x; im[t] = v[t].y; }
-                uint32_t wr[S][4], wi[S][4];
-                split8<S>(re, wr);
-                split8<S>(im, wi);
-                store_slices<S>(base + koff(r, g), wr, 0u);
-                store_slices<S>(base + koff(r, g + 2), wi, 0u);
-            }
-            {
-                float2 v[8];
-                p.b8(rb, k0 + 8 * ubg, ke, v);
-                float re[8], im[8];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) { re[t] = v[t].x; im[t] = v[t].y; }
-                uint32_t wr[S][4], wi[S][4];
-                split8<S>(re, wr);
-                split8<S>(im, wi);
-                uint8_t* bb = base + A_SL;
-                store_slices<S>(bb + koff(ubr, ubg), wr, 0u);                 // [Br | -Bi]
-                store_slices<S>(bb + koff(ubr, ubg + 2), wi, 0x80008000u);
-                store_slices<S>(bb + koff(BN + ubr, ubg), wi, 0u);            // [Bi |  Br]
-                store_slices<S>(bb + koff(BN + ubr, ubg + 2), wr, 0u);
-            }
-            fence_proxy_async();
-            mbar_arrive(&full_bar[s]);
-        }
-        while (ok && drained < ngroups) {
-            ok = drain(drained);
-            ++drained;
-        }
-        if (ok && !abort_flag) {
-            tc_fence_after();
-            const int64_t gi = i0 + q * 32 + lane;
+            if (ok && !abort_flag) {
+                tc_fence_after();
+                const int64_t gi = i0 + q * 32 + lane;
 #pragma unroll 1
-            for (int part = 0; part < 4; ++part) {
-                uint32_t cr[16], ci[16];
-                if (nk > 0) {
-                    tmem_ld16(taddr_row + TOTAL_COL + 16 * part, cr);
-                    tmem_ld16(taddr_row + TOTAL_COL + BN + 16 * part, ci);
-                    tmem_wait_ld();
-                } else {
+                for (int part = 0; part < 4; ++part) {
+                    uint32_t cr[16], ci[16];
+                    if (nk > 0) {
+                        tmem_ld16(taddr_row + TOTAL_COL + 16 * part, cr);
+                        tmem_ld16(taddr_row + TOTAL_COL + BN + 16 * part, ci);
+                        tmem_wait_ld();
+                    } else {
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) cr[t] = ci[t] = 0u;
-                }
-                if (p.row_ok(gi)) {
+                        for (int u = 0; u < 16; ++u) cr[u] = ci[u] = 0u;
+                    }
+                    if (p.row_ok(gi)) {
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) {
-                        const int64_t gj = j0 + 64 * h + 16 * part + t;
-                        if (p.col_ok(gj))
-                            p.store(gi, gj, make_float2(__uint_as_float(cr[t]), __uint_as_float(ci[t])));
+                        for (int u = 0; u < 16; ++u) {
+                            const int64_t gj = j0 + 64 * h + 16 * part + u;
+                            if (p.col_ok(gj))
+                                p.store(gi, gj, make_float2(__uint_as_float(cr[u]), __uint_as_float(ci[u])));
+                        }
                     }
                 }
             }
-        }
-    } else if (lane == 0) {
-        // ---------------- MMA issuer
-        for (int kt = 0; kt < nk; ++kt) {
-            const int g = kt / DRAIN;
-            const bool first = (kt % DRAIN) == 0;
-            if (first && g >= 1 && !mbar_wait(&tempty, (uint32_t)(g - 1) & 1u, &abort_flag)) break;
-            const int s = kt % CF::STAGES;
-            const uint32_t ph = (uint32_t)(kt / CF::STAGES) & 1u;
-            if (!mbar_wait(&full_bar[s], ph, &abort_flag)) break;
-            tc_fence_after();
-            const uint32_t sbase = smem_u32(smem + s * CF::STAGE_BYTES);
+        } else if (lane == 0) {
+            // ---------------- MMA issuer
+            for (int kt = 0; kt < nk; ++kt) {
+                const uint32_t g = gq + (uint32_t)(kt / DRAIN);
+                const bool first = (kt % DRAIN) == 0;
+                if (first && g >= 1 && !mbar_wait(&tempty, (g - 1) & 1u, &abort_flag)) break;
+                const uint32_t kg = kq + (uint32_t)kt;
+                const int s = (int)(kg % CF::STAGES);
+                const uint32_t ph = (kg / CF::STAGES) & 1u;
+                if (!mbar_wait(&full_bar[s], ph, &abort_flag)) break;
+                tc_fence_after();
+                const uint32_t sbase = smem_u32(smem + s * CF::STAGE_BYTES);
 #pragma unroll
-            for (int pq = 0; pq < CF::NPAIRS; ++pq) {
-                const uint32_t a = sbase + pair_a(pq) * SLICE;
-                const uint32_t bsl = sbase + pair_b(pq) * SLICE + A_SL;
+                for (int pq = 0; pq < CF::NPAIRS; ++pq) {
+                    const uint32_t a = sbase + pair_a(pq) * SLICE;
+                    const uint32_t bsl = sbase + pair_b(pq) * SLICE + A_SL;
 #pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                    const uint64_t da = sdesc(a + kk * 256, 128, 512);
-                    const uint64_t db = sdesc(bsl + kk * 256, 128, 512);
-                    mma_bf16(tmem, da, db, IDESC, (first && pq == 0 && kk == 0) ? 0u : 1u);
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint64_t da = sdesc(a + kk * 256, 128, 512);
+                        const uint64_t db = sdesc(bsl + kk * 256, 128, 512);
+                        mma_bf16(tmem, da, db, IDESC, (first && pq == 0 && kk == 0) ? 0u : 1u);
+                    }
                 }
+                mma_commit(&empty_bar[s]);
+                if ((kt % DRAIN) == DRAIN - 1 || kt == nk - 1) mma_commit(&tfull);
             }
-            mma_commit(&empty_bar[s]);
-            if ((kt % DRAIN) == DRAIN - 1 || kt == nk - 1) mma_commit(&tfull);
         }
-        mma_commit(&done_bar);  // completes when every MMA issued above has finished
+        kq += (uint32_t)nk;
+        gq += (uint32_t)ngroups;
+        if (abort_flag) break;
     }
+    if (warp == NPW && lane == 0) mma_commit(&done_bar);  // completes when every issued MMA has finished
 
     tc_fence_before();
     __syncthreads();
@@ -372,18 +420,37 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(P p, DevStatus* st, int site
     if (threadIdx.x == 0 && abort_flag) atomicMax(&st->timeout_site, site);
 }
 
-template <int S, class P>
-static cudaError_t launch(const P& p, dim3 grid, DevStatus* st, int site, cudaStream_t s) {
+int sm_count();
+
+template <int S, class Sched>
+static cudaError_t launch_sched(const Sched& sch, int64_t items, DevStatus* st, int site, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc<S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<S>::SMEM);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_tc<S, Sched>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<S>::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-    k_tc<S, P><<<grid, NTHREADS, Cfg<S>::SMEM, s>>>(p, st, site);
+    if (items == 0) return cudaSuccess;
+    const int64_t ctas = items < sm_count() ? items : sm_count();
+    k_tc<S, Sched><<<(unsigned)ctas, NTHREADS, Cfg<S>::SMEM, s>>>(sch, st, site);
     note_launch();
     return cudaGetLastError();
+}
+
+// One problem over a grid.x x grid.y grid of tiles (bx = x, by = y).
+template <int S, class P>
+static cudaError_t launch(const P& p, dim3 grid, DevStatus* st, int site, cudaStream_t s) {
+    const int64_t n = (int64_t)grid.x * grid.y;
+    return launch_sched<S>(OneProblem<P>{p, (int64_t)grid.x, n}, n, st, site, s);
+}
+
+// Several problems of one kind in one persistent launch; the arrays live in
+// device memory (filled by the caller), items = start[n].
+template <int S, class P>
+static cudaError_t launch_many(const P* probs, const int64_t* start, const int64_t* gx, int n, int64_t items,
+                               DevStatus* st, int site, cudaStream_t s) {
+    return launch_sched<S>(ManyProblems<P>{probs, start, gx, n}, items, st, site, s);
 }
 
 }  // namespace tc

@@ -8,6 +8,7 @@
 // sample); a8()/b8(), 8 consecutive k of that row of A or column of B, zero
 // outside the problem; row_ok()/col_ok() and store().
 #include <algorithm>
+#include <vector>
 
 #include "tc_engine.cuh"
 
@@ -182,9 +183,9 @@ struct GramTC {
     double lam;
     double2* G;
     int64_t ld;
-    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
-        i0 = (int64_t)blockIdx.y * BM;
-        j0 = (int64_t)blockIdx.x * BN;
+    __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = by * BM;
+        j0 = bx * BN;
         kb = 0;
         ke = e.Mk;
         return j0 <= i0 + BM - 1;  // tile touches the lower triangle
@@ -241,8 +242,8 @@ struct TrsmTC {
     const float2* Dinv32;  // [64][64]
     double2* G;
     int64_t ld, N, k0, nbk;
-    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
-        i0 = k0 + nbk + (int64_t)blockIdx.y * BM;
+    __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = k0 + nbk + by * BM;
         j0 = 0;
         kb = 0;
         ke = nbk;
@@ -272,9 +273,9 @@ struct HerkTC {
     int64_t ldp;
     double2* G;
     int64_t ld, N, nbk, t0;
-    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
-        i0 = t0 + (int64_t)blockIdx.y * BM;
-        j0 = t0 + (int64_t)blockIdx.x * BN;
+    __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = t0 + by * BM;
+        j0 = t0 + bx * BN;
         kb = 0;
         ke = nbk;
         return i0 < N && j0 < N && j0 <= i0 + BM - 1;
@@ -304,9 +305,9 @@ struct TrtriDiagTC {
     const float2* Dinv32;
     double2* W;
     int64_t ld, N, k0, nbk;
-    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+    __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
         i0 = 0;
-        j0 = (int64_t)blockIdx.x * BN;
+        j0 = bx * BN;
         kb = 0;
         ke = nbk;
         return true;
@@ -342,9 +343,9 @@ struct TrtriUpdTC {
     int64_t ldl;
     double2* W;
     int64_t ld, N, k0, nbk;
-    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
-        i0 = k0 + nbk + (int64_t)blockIdx.y * BM;
-        j0 = (int64_t)blockIdx.x * BN;
+    __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = k0 + nbk + by * BM;
+        j0 = bx * BN;
         kb = 0;
         ke = nbk;
         return i0 < N;
@@ -379,9 +380,9 @@ struct ReconStep1TC {
     EncodeDev e;
     const float2* W32;
     float2* T;
-    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
-        j0 = (int64_t)blockIdx.x * BN;
-        i0 = (int64_t)blockIdx.y * BM;
+    __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        j0 = bx * BN;
+        i0 = by * BM;
         kb = 0;
         ke = i0 + BM < e.N ? i0 + BM : e.N;  // W is lower triangular
         return true;
@@ -407,9 +408,9 @@ struct ReconStep2TC {
     const float2* T;
     float2* R;
     int64_t N, M;
-    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
-        i0 = (int64_t)blockIdx.x * BM;
-        j0 = (int64_t)blockIdx.y * BN;
+    __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = bx * BM;
+        j0 = by * BN;
         kb = i0;  // W is lower triangular
         ke = N;
         return true;
@@ -513,6 +514,88 @@ cudaError_t launch_recon_tc(const EncodeDev& e, const float2* W32, const float2*
     tc::ReconStep2TC p2{WT32, T, R, e.N, M};
     return run(p2, dim3(cdiv(e.N, tc::BM), cdiv(M, tc::BN)), slices, st, 8, s);
 }
+
+// ------------------------------------------------------------------ batched launches
+cudaError_t tc_multi_create(int kind, const TcPlanArgs* a, int n, TcMulti* out) {
+    *out = TcMulti{};
+    out->kind = kind;
+    out->n = n;
+    std::vector<int64_t> start(n + 1, 0), gx(n, 1);
+    std::vector<unsigned char> probs;  // problem descriptors, stride sizeof(problem)
+    for (int i = 0; i < n; ++i) {
+        const EncodeDev& e = *a[i].e;
+        const int64_t M = e.Mk * e.C;
+        int64_t gxi = 1, gyi = 1;
+        if (kind == TC_MULTI_GRAM) {
+            gxi = cdiv(e.N, tc::BN);
+            gyi = cdiv(e.N, tc::BM);
+            tc::GramTC p{e, a[i].lam, a[i].G, e.N};
+            probs.insert(probs.end(), (unsigned char*)&p, (unsigned char*)&p + sizeof(p));
+        } else if (kind == TC_MULTI_RECON1) {
+            gxi = cdiv(M, tc::BN);
+            gyi = cdiv(e.N, tc::BM);
+            tc::ReconStep1TC p{e, a[i].W32, a[i].T};
+            probs.insert(probs.end(), (unsigned char*)&p, (unsigned char*)&p + sizeof(p));
+        } else {
+            gxi = cdiv(e.N, tc::BM);
+            gyi = cdiv(M, tc::BN);
+            tc::ReconStep2TC p{a[i].WT32, a[i].T, a[i].R, e.N, M};
+            probs.insert(probs.end(), (unsigned char*)&p, (unsigned char*)&p + sizeof(p));
+        }
+        gx[i] = gxi;
+        start[i + 1] = start[i] + gxi * gyi;
+    }
+    out->items = start[n];
+    out->off_start = (probs.size() + 255) & ~(size_t)255;
+    out->off_gx = out->off_start + ((sizeof(int64_t) * (n + 1) + 255) & ~(size_t)255);
+    const size_t bytes = out->off_gx + sizeof(int64_t) * n;
+    cudaError_t e = cudaMalloc(&out->buf, bytes);
+    if (e != cudaSuccess) return e;
+    unsigned char* b = (unsigned char*)out->buf;
+    if ((e = cudaMemcpy(b, probs.data(), probs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(b + out->off_start, start.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return e;
+    return cudaMemcpy(b + out->off_gx, gx.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice);
+}
+
+template <int S>
+static cudaError_t multi_launch_s(const TcMulti& m, DevStatus* st, cudaStream_t s) {
+    const unsigned char* b = (const unsigned char*)m.buf;
+    const int64_t* start = (const int64_t*)(b + m.off_start);
+    const int64_t* gx = (const int64_t*)(b + m.off_gx);
+    if (m.kind == TC_MULTI_GRAM)
+        return tc::launch_many<S>((const tc::GramTC*)b, start, gx, m.n, m.items, st, 1, s);
+    if (m.kind == TC_MULTI_RECON1)
+        return tc::launch_many<S>((const tc::ReconStep1TC*)b, start, gx, m.n, m.items, st, 2, s);
+    return tc::launch_many<S>((const tc::ReconStep2TC*)b, start, gx, m.n, m.items, st, 8, s);
+}
+
+cudaError_t tc_multi_launch(const TcMulti& m, int slices, DevStatus* st, cudaStream_t s) {
+    if (m.n == 0 || m.items == 0) return cudaSuccess;
+    return slices == 3 ? multi_launch_s<3>(m, st, s) : multi_launch_s<2>(m, st, s);
+}
+
+void tc_multi_free(TcMulti* m) {
+    if (m->buf) cudaFree(m->buf);
+    *m = TcMulti{};
+}
+
+namespace tc {
+// SMs of the current device (persistent grids hold one CTA per SM)
+int sm_count() {
+    static int cached_dev = -1, cached = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev != cached_dev) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+        cached = n;
+        cached_dev = dev;
+    }
+    return cached;
+}
+}  // namespace tc
 
 bool tc_available() {
     int dev = 0, major = 0, minor = 0;

@@ -282,8 +282,8 @@ def config(i: int, reduced: bool = False, frames: int | None = None) -> PlanInpu
             C = int(rng.integers(1, 9))
             kind = "spiral" if rng.uniform() < 0.5 else "radial"
             mult = int(rng.integers(1, 5))
-            plans.append(make_plan(side, C, kind, frames or (256 if not reduced else 4),
-                                   3000 + p + 1, 1e-3, samples=mult * side * side,
+            nf = (256 if not reduced else 4) if frames is None else frames
+            plans.append(make_plan(side, C, kind, nf, 3000 + p + 1, 1e-3, samples=mult * side * side,
                                    name=f"cfg3.{p}"))
         return plans
     if i == 4:
