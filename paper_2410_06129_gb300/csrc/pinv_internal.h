@@ -64,6 +64,9 @@ struct DevStatus {
     int pad;
     double min_pivot;   // min diag(L) as ordered bits (set by panel kernels)
     double max_pivot;
+    // tile counter of the persistent tensor-core kernel running on this plan's
+    // stream (next item, CTAs finished); the last CTA of a launch zeroes both
+    unsigned long long sched_next, sched_done;
 };
 
 // ---------------------------------------------------------------------------

@@ -215,6 +215,8 @@ __global__ void k_reset_status(DevStatus* st) {
     st->pad = 0;
     st->min_pivot = INFINITY;
     st->max_pivot = 0.0;
+    st->sched_next = 0;
+    st->sched_done = 0;
 }
 
 cudaError_t launch_reset_status(DevStatus* st, cudaStream_t s) {

@@ -214,12 +214,16 @@ __device__ inline void drain_to_total(uint32_t taddr_row, bool first) {
 // OneProblem covers a gx x gy grid of tiles of one problem; ManyProblems
 // concatenates the tile grids of several problems (e.g. one per plan of a
 // batch) held in device memory.
+// rev: hand out items last to first (the longest tiles of a triangular
+// operand first, so they do not form the tail).
 template <class P>
 struct OneProblem {
     P p;
     int64_t gx, n;
+    bool rev;
     __device__ int64_t count() const { return n; }
     __device__ const P& get(int64_t t, int64_t& bx, int64_t& by) const {
+        if (rev) t = n - 1 - t;
         bx = t % gx;
         by = t / gx;
         return p;
@@ -232,8 +236,14 @@ struct ManyProblems {
     const int64_t* start;   // [n + 1], first item of each problem
     const int64_t* gx;      // [n], tile-grid width of each problem
     int n;
+    bool rev;
     __device__ int64_t count() const { return start[n]; }
     __device__ const P& get(int64_t t, int64_t& bx, int64_t& by) const {
+        if (rev) {  // last tile of each problem first, problems in order
+            int i = 0;
+            while (i + 1 < n && start[i + 1] <= t) ++i;
+            t = start[i] + (start[i + 1] - 1 - t);
+        }
         int i = 0;
         while (i + 1 < n && start[i + 1] <= t) ++i;
         const int64_t l = t - start[i];
@@ -243,9 +253,12 @@ struct ManyProblems {
     }
 };
 
-// Persistent kernel: each CTA walks items blockIdx.x, blockIdx.x + gridDim.x, ...
-// The stage ring and the TMEM accumulation groups run on counters that continue
-// across tiles, so barriers are initialised and TMEM allocated once per CTA.
+// Persistent kernel: each CTA takes the next item from a global counter (in
+// the plan's status block) until none is left, so uneven tiles balance across
+// SMs. The stage ring and the TMEM accumulation groups run on counters that
+// continue across tiles, so barriers are initialised and TMEM allocated once
+// per CTA. The last CTA to finish zeroes the item counter for the next launch
+// on the same stream.
 template <int S, class Sched>
 __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, int site) {
     using CF = Cfg<S>;
@@ -254,6 +267,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, in
     __shared__ uint64_t tfull, tempty, done_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_flag;
+    __shared__ long long next_item;
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -267,6 +281,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, in
         mbar_init(&tempty, NPW * 32);
         mbar_init(&done_bar, 1);
         abort_flag = 0;
+        next_item = (long long)atomicAdd(&st->sched_next, 1ull);
         fence_barrier_init();
     }
     if (warp == NPW) tmem_alloc(&tmem_base_sh, 512);
@@ -279,11 +294,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, in
 
     const int64_t items = sch.count();
     uint32_t kq = 0, gq = 0;  // stages and accumulation groups used by earlier tiles
-    for (int64_t t = blockIdx.x; t < items; t += gridDim.x) {
+    for (int64_t t = next_item;; ) {
+        if (t >= items) break;
         int64_t bx, by;
         const auto& p = sch.get(t, bx, by);
         int64_t i0, j0, kb, ke;
-        if (!p.tile(bx, by, i0, j0, kb, ke)) continue;  // uniform per CTA
+        if (!p.tile(bx, by, i0, j0, kb, ke)) {  // empty tile (uniform per CTA)
+            __syncthreads();
+            if (threadIdx.x == 0) next_item = (long long)atomicAdd(&st->sched_next, 1ull);
+            __syncthreads();
+            t = next_item;
+            continue;
+        }
         const int nk = ke > kb ? (int)((ke - kb + KC - 1) / KC) : 0;
         const int ngroups = (nk + DRAIN - 1) / DRAIN;
 
@@ -406,7 +428,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, in
         }
         kq += (uint32_t)nk;
         gq += (uint32_t)ngroups;
-        if (abort_flag) break;
+        // next item: every thread has read next_item for this tile
+        __syncthreads();
+        if (threadIdx.x == 0) next_item = abort_flag ? (long long)items : (long long)atomicAdd(&st->sched_next, 1ull);
+        __syncthreads();
+        t = next_item;
     }
     if (warp == NPW && lane == 0) mma_commit(&done_bar);  // completes when every issued MMA has finished
 
@@ -417,7 +443,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, in
         tc_fence_after();
         tmem_dealloc(tmem, 512);
     }
-    if (threadIdx.x == 0 && abort_flag) atomicMax(&st->timeout_site, site);
+    if (threadIdx.x == 0) {
+        if (abort_flag) atomicMax(&st->timeout_site, site);
+        // the last CTA out resets the item counter: all others have stopped taking items
+        __threadfence();
+        if (atomicAdd(&st->sched_done, 1ull) == (unsigned long long)gridDim.x - 1) {
+            st->sched_next = 0;
+            st->sched_done = 0;
+            __threadfence();
+        }
+    }
 }
 
 int sm_count();
@@ -438,19 +473,20 @@ static cudaError_t launch_sched(const Sched& sch, int64_t items, DevStatus* st, 
     return cudaGetLastError();
 }
 
-// One problem over a grid.x x grid.y grid of tiles (bx = x, by = y).
+// One problem over a grid.x x grid.y grid of tiles (bx = x, by = y). Launches
+// sharing a status block must run one after another (one stream).
 template <int S, class P>
-static cudaError_t launch(const P& p, dim3 grid, DevStatus* st, int site, cudaStream_t s) {
+static cudaError_t launch(const P& p, dim3 grid, DevStatus* st, int site, cudaStream_t s, bool rev = false) {
     const int64_t n = (int64_t)grid.x * grid.y;
-    return launch_sched<S>(OneProblem<P>{p, (int64_t)grid.x, n}, n, st, site, s);
+    return launch_sched<S>(OneProblem<P>{p, (int64_t)grid.x, n, rev}, n, st, site, s);
 }
 
 // Several problems of one kind in one persistent launch; the arrays live in
 // device memory (filled by the caller), items = start[n].
 template <int S, class P>
 static cudaError_t launch_many(const P* probs, const int64_t* start, const int64_t* gx, int n, int64_t items,
-                               DevStatus* st, int site, cudaStream_t s) {
-    return launch_sched<S>(ManyProblems<P>{probs, start, gx, n}, items, st, site, s);
+                               DevStatus* st, int site, cudaStream_t s, bool rev = false) {
+    return launch_sched<S>(ManyProblems<P>{probs, start, gx, n, rev}, items, st, site, s);
 }
 
 }  // namespace tc

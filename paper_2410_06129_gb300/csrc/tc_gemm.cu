@@ -453,8 +453,9 @@ static cudaError_t block_to_f32(const double2* src, int64_t ld, int64_t r0, int6
 }
 
 template <class P>
-static cudaError_t run(const P& p, dim3 grid, int slices, DevStatus* st, int site, cudaStream_t s) {
-    return slices == 3 ? tc::launch<3>(p, grid, st, site, s) : tc::launch<2>(p, grid, st, site, s);
+static cudaError_t run(const P& p, dim3 grid, int slices, DevStatus* st, int site, cudaStream_t s,
+                       bool rev = false) {
+    return slices == 3 ? tc::launch<3>(p, grid, st, site, s, rev) : tc::launch<2>(p, grid, st, site, s, rev);
 }
 
 static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
@@ -509,7 +510,8 @@ cudaError_t launch_recon_tc(const EncodeDev& e, const float2* W32, const float2*
                             float2* R, DevStatus* st, cudaStream_t s) {
     const int64_t M = e.Mk * e.C;
     tc::ReconStep1TC p1{e, W32, T};
-    cudaError_t err = run(p1, dim3(cdiv(M, tc::BN), cdiv(e.N, tc::BM)), slices, st, 2, s);
+    // step-1 tiles get longer with the row (W is lower triangular): longest first
+    cudaError_t err = run(p1, dim3(cdiv(M, tc::BN), cdiv(e.N, tc::BM)), slices, st, 2, s, true);
     if (err != cudaSuccess) return err;
     tc::ReconStep2TC p2{WT32, T, R, e.N, M};
     return run(p2, dim3(cdiv(e.N, tc::BM), cdiv(M, tc::BN)), slices, st, 8, s);
@@ -522,7 +524,16 @@ cudaError_t tc_multi_create(int kind, const TcPlanArgs* a, int n, TcMulti* out) 
     out->n = n;
     std::vector<int64_t> start(n + 1, 0), gx(n, 1);
     std::vector<unsigned char> probs;  // problem descriptors, stride sizeof(problem)
-    for (int i = 0; i < n; ++i) {
+    // plans with the longest tiles first (K per tile: M_k for the Gram, up to N for Recon)
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const int64_t kx = kind == TC_MULTI_GRAM ? a[x].e->Mk : a[x].e->N;
+        const int64_t ky = kind == TC_MULTI_GRAM ? a[y].e->Mk : a[y].e->N;
+        return kx > ky;
+    });
+    for (int ii = 0; ii < n; ++ii) {
+        const int i = order[ii];
         const EncodeDev& e = *a[i].e;
         const int64_t M = e.Mk * e.C;
         int64_t gxi = 1, gyi = 1;
@@ -542,8 +553,8 @@ cudaError_t tc_multi_create(int kind, const TcPlanArgs* a, int n, TcMulti* out) 
             tc::ReconStep2TC p{a[i].WT32, a[i].T, a[i].R, e.N, M};
             probs.insert(probs.end(), (unsigned char*)&p, (unsigned char*)&p + sizeof(p));
         }
-        gx[i] = gxi;
-        start[i + 1] = start[i] + gxi * gyi;
+        gx[ii] = gxi;
+        start[ii + 1] = start[ii] + gxi * gyi;
     }
     out->items = start[n];
     out->off_start = (probs.size() + 255) & ~(size_t)255;
@@ -567,7 +578,7 @@ static cudaError_t multi_launch_s(const TcMulti& m, DevStatus* st, cudaStream_t 
     if (m.kind == TC_MULTI_GRAM)
         return tc::launch_many<S>((const tc::GramTC*)b, start, gx, m.n, m.items, st, 1, s);
     if (m.kind == TC_MULTI_RECON1)
-        return tc::launch_many<S>((const tc::ReconStep1TC*)b, start, gx, m.n, m.items, st, 2, s);
+        return tc::launch_many<S>((const tc::ReconStep1TC*)b, start, gx, m.n, m.items, st, 2, s, true);
     return tc::launch_many<S>((const tc::ReconStep2TC*)b, start, gx, m.n, m.items, st, 8, s);
 }
 
