@@ -489,6 +489,7 @@ def main():
             "clocks": clk.summary(), "wall_s_timed": wall,
         }
         line.update(res)
+        line["autotune"] = L.autotune_report()
         if batch is not None:
             line["batch"] = batch
         if serve is not None:

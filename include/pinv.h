@@ -310,6 +310,15 @@ pinv_status pinv_server_stats(pinv_server* server, pinv_server_stats_t* out);
 /* Finish queued requests, stop the worker and free every resident plan. */
 void pinv_server_destroy(pinv_server* server);
 
+/* Launch-shape autotuner. The apply-side kernels (Recon x data, the
+ * double-float residual and E^H d, the FP32 correction) offer several tile
+ * shapes per size class; the first launch of a class times each candidate on
+ * its stream and keeps the fastest (PINV_AUTOTUNE=0 in the environment turns
+ * this off). Candidates differ in speed only: every output is summed in the
+ * same order. Writes a one-line summary of the choices made so far into buf
+ * (NUL-terminated, truncated to bytes) and returns its full length. */
+size_t pinv_autotune_report(char* buf, size_t bytes);
+
 /* Size of the fixed device scratch array behind pinv_apply_noalloc (64 MiB). */
 #define PINV_NOALLOC_SCRATCH_BYTES (64u << 20)
 

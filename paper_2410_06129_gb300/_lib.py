@@ -93,6 +93,7 @@ SIGNATURES = {
     "pinv_plan_info": (C.c_int, [_VP, C.POINTER(PlanInfo)]),
     "pinv_plan_destroy": (None, [_VP]),
     "pinv_apply_noalloc": (C.c_int, [_VP, _VP, _VP, C.c_int64, C.c_int, _VP]),
+    "pinv_autotune_report": (C.c_size_t, [C.c_char_p, C.c_size_t]),
     "pinv_batch_create": (C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, C.POINTER(_VP)]),
     "pinv_batch_build": (C.c_int, [_VP, _VP]),
     "pinv_batch_apply": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(C.c_int64), C.c_int, _VP]),
@@ -127,6 +128,12 @@ def load(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def autotune_report() -> str:
+    buf = C.create_string_buffer(8192)
+    load().pinv_autotune_report(buf, 8192)
+    return buf.value.decode()
 
 
 def check(status: int):

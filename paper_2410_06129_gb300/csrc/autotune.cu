@@ -1,0 +1,106 @@
+// Launch-shape autotuner for the frame kernels (apply, residual, correction).
+//
+// A kernel family offers several tile shapes for one size class (rows and
+// frame count, bucketed by powers of two). The first launch of a class on a
+// device times every candidate with CUDA events on the launching stream (one
+// warm-up run, then two timed runs each) and keeps the fastest; later launches
+// reuse the choice. Every candidate of a family sums each output over k in
+// the same order, so the choice changes speed, never results, and the timed
+// runs only rewrite the same outputs. While a stream is being captured into a
+// graph nothing can be timed: an untuned class then uses candidate 0 without
+// caching it. PINV_AUTOTUNE=0 in the environment disables tuning.
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "pinv_internal.h"
+
+namespace pinv {
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;   // key -> chosen candidate
+std::map<std::string, float> g_tune_ms;
+
+int bucket(int64_t v) {
+    int b = 0;
+    while (b < 62 && (int64_t(1) << b) < v) ++b;
+    return b;
+}
+
+bool tuning_enabled() {
+    const char* v = std::getenv("PINV_AUTOTUNE");
+    return !(v && std::strcmp(v, "0") == 0);
+}
+}  // namespace
+
+int tune_pick(const char* family, int64_t rows, int64_t F, int ncand, const TuneRun& run, cudaStream_t s) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const std::string key = std::string(family) + " rows~2^" + std::to_string(bucket(rows)) + " F~2^" +
+                            std::to_string(bucket(F)) + " dev" + std::to_string(dev);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) return it->second;
+    }
+    if (ncand <= 1 || !tuning_enabled()) return 0;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return 0;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return 0;
+    }
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int c = 0; c < ncand; ++c) {
+        if (run(c) != cudaSuccess) {  // a shape this device cannot launch
+            cudaGetLastError();
+            continue;
+        }
+        cudaEventRecord(e0, s);
+        const bool ok = run(c) == cudaSuccess && run(c) == cudaSuccess;
+        cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !ok) {
+            cudaGetLastError();
+            continue;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+    g_tune_ms[key] = best_ms / 2.f;
+    return best;
+}
+
+std::string tune_report() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    std::string out;
+    for (auto& kv : g_tune) {
+        if (!out.empty()) out += "; ";
+        out += kv.first + " -> " + std::to_string(kv.second) + " (" + std::to_string(g_tune_ms[kv.first]) + " ms)";
+    }
+    return out;
+}
+
+}  // namespace pinv
+
+extern "C" size_t pinv_autotune_report(char* buf, size_t bytes) {
+    const std::string r = pinv::tune_report();
+    if (buf && bytes) {
+        const size_t n = r.size() < bytes - 1 ? r.size() : bytes - 1;
+        std::memcpy(buf, r.data(), n);
+        buf[n] = '\0';
+    }
+    return r.size();
+}

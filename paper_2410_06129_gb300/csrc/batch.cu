@@ -292,6 +292,8 @@ pinv_status pinv_batch_apply(pinv_batch* b, const void* const* d_data, void* con
     }
     if (!b->graph_apply) return apply_sequence(b, d_data, d_image, n_frames, dtype, s);
     if (grown || !b->apply_exec || key != b->apply_key) {
+        // one eager run first: it tunes launch shapes, which cannot be timed under capture
+        STB(apply_sequence(b, d_data, d_image, n_frames, dtype, s));
         STB(capture(s, &b->apply_exec, &b->apply_launches,
                     [&] { return apply_sequence(b, d_data, d_image, n_frames, dtype, s); }));
         b->apply_key = key;

@@ -12,6 +12,8 @@
 //
 // The correction step x += W^H (W r) only preconditions the next residual, so
 // it runs in plain FP32 (tile engine k_ctile).
+#include <climits>
+
 #include "pinv_internal.h"
 
 namespace pinv {
@@ -190,32 +192,61 @@ struct AdjointDF {
     }
 };
 
-template <class P>
-static cudaError_t launch_df(P p, int64_t rows, int64_t F, cudaStream_t s) {
-    if (F >= 48) {
-        dim3 grid((unsigned)((F + 63) / 64), (unsigned)((rows + 15) / 16));
-        k_dftile<16, 64, 1, 4><<<grid, 256, 0, s>>>(p);
-    } else if (F >= 8) {
-        dim3 grid((unsigned)((F + 15) / 16), (unsigned)((rows + 15) / 16));
-        k_dftile<16, 16, 1, 1><<<grid, 256, 0, s>>>(p);
-    } else {
-        dim3 grid((unsigned)((F + 3) / 4), (unsigned)((rows + 63) / 64));
-        k_dftile<64, 4, 1, 1><<<grid, 256, 0, s>>>(p);
-    }
+template <int BM, int BN, int TM, int TN, class P>
+static cudaError_t df_shape(const P& p, int64_t rows, int64_t F, cudaStream_t s) {
+    dim3 grid((unsigned)((F + BN - 1) / BN), (unsigned)((rows + BM - 1) / BM));
+    k_dftile<BM, BN, TM, TN, P><<<grid, 256, 0, s>>>(p);
     note_launch();
     return cudaGetLastError();
+}
+
+// Tile shape per frame-count class, chosen by the autotuner among candidates
+// that all sum over k in the same order.
+template <class P>
+static cudaError_t launch_df(P p, int64_t rows, int64_t F, cudaStream_t s, const char* family) {
+    if (F >= 48) {
+        auto run = [&](int c) -> cudaError_t {
+            switch (c) {
+                case 1: return df_shape<32, 64, 2, 4>(p, rows, F, s);
+                case 2: return df_shape<64, 64, 4, 4>(p, rows, F, s);
+                case 3: return df_shape<32, 32, 2, 2>(p, rows, F, s);
+                case 4: return df_shape<64, 32, 4, 2>(p, rows, F, s);
+                default: return df_shape<16, 64, 1, 4>(p, rows, F, s);
+            }
+        };
+        return run(tune_pick(family, rows, F, 5, run, s));
+    }
+    if (F >= 8) {
+        auto run = [&](int c) -> cudaError_t {
+            switch (c) {
+                case 1: return df_shape<32, 16, 2, 1>(p, rows, F, s);
+                case 2: return df_shape<64, 16, 4, 1>(p, rows, F, s);
+                case 3: return df_shape<32, 32, 2, 2>(p, rows, F, s);
+                default: return df_shape<16, 16, 1, 1>(p, rows, F, s);
+            }
+        };
+        return run(tune_pick(family, rows, F, 4, run, s));
+    }
+    auto run = [&](int c) -> cudaError_t {
+        switch (c) {
+            case 1: return df_shape<128, 4, 2, 1>(p, rows, F, s);
+            case 2: return df_shape<128, 2, 1, 1>(p, rows, F, s);
+            default: return df_shape<64, 4, 1, 1>(p, rows, F, s);
+        }
+    };
+    return run(tune_pick(family, rows, F, 3, run, s));
 }
 
 cudaError_t launch_forward_df(const EncodeDev& e, const double2* X, int64_t F, const double2* D, double2* U,
                               cudaStream_t s) {
     if (F == 0) return cudaSuccess;
-    return launch_df(ForwardDF{e, X, D, U, F}, e.Mk * e.C, F, s);
+    return launch_df(ForwardDF{e, X, D, U, F}, e.Mk * e.C, F, s, "forward_df");
 }
 
 cudaError_t launch_adjoint_df(const EncodeDev& e, const double2* U, int64_t F, double lam, const double2* X,
                               double2* R, cudaStream_t s) {
     if (F == 0) return cudaSuccess;
-    return launch_df(AdjointDF{e, U, X, R, lam, F}, e.N, F, s);
+    return launch_df(AdjointDF{e, U, X, R, lam, F}, e.N, F, s, "adjoint_df");
 }
 
 // ------------------------------------------------------------------ exact Gram residual
@@ -268,7 +299,7 @@ struct GramResidDF {
 cudaError_t launch_gram_resid_df(const float4* G, int64_t N, const double2* B, const double2* X, int64_t F,
                                  double2* R, cudaStream_t s) {
     if (F == 0) return cudaSuccess;
-    return launch_df(GramResidDF{G, B, X, R, N, F}, N, F, s);
+    return launch_df(GramResidDF{G, B, X, R, N, F}, N, F, s, "gram_resid_df");
 }
 
 __global__ void k_from_df(const float4* a, int64_t n, double2* b) {
@@ -279,6 +310,145 @@ __global__ void k_from_df(const float4* a, int64_t n, double2* b) {
 cudaError_t launch_from_df(const float4* a, int64_t n, double2* b, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_from_df<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, n, b);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ diagonal Cholesky blocks
+// The mixed path's 64 x 64 diagonal blocks: G_kk = L_kk L_kk^H and
+// Dinv = L_kk^-1, in double-float (about 44 significant bits) on the FP32
+// units. GB300 issues about 2 DFMA per clock per SM, so the same block in FP64
+// takes ~5x longer, and these blocks are the sequential chain of the blocked
+// Cholesky. Storage stays FP64. Only the 64 pivots use FP64 (one rsqrt each).
+namespace {
+constexpr int NBD = 64;
+__device__ inline float4 df_scale(float4 a, float rh, float rl) {  // complex DF times real DF
+    float xh, xl, yh, yl;
+    df_mul(a.x, a.y, rh, rl, xh, xl);
+    df_mul(a.z, a.w, rh, rl, yh, yl);
+    return make_float4(xh, xl, yh, yl);
+}
+__device__ inline float4 df_norm(float4 a) {  // renormalise both (hi, lo) pairs
+    float h, l;
+    fast_two_sum(a.x, a.y, h, l);
+    a.x = h;
+    a.y = l;
+    fast_two_sum(a.z, a.w, h, l);
+    a.z = h;
+    a.w = l;
+    return a;
+}
+__device__ inline float4 df_cadd(float4 a, float4 b) {
+    float rh, rl, ih, il;
+    df_add(a.x, a.y, b.x, b.y, rh, rl);
+    df_add(a.z, a.w, b.z, b.w, ih, il);
+    return make_float4(rh, rl, ih, il);
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0,
+                                                       double2* Dinv, float2* Dinv32, DevStatus* st) {
+    extern __shared__ float4 smd[];
+    float4* A = smd;               // [NBD][NBD]
+    float4* X = smd + NBD * NBD;   // [NBD][NBD] inverse
+    __shared__ float2 rdiag[NBD];  // 1 / L_jj as (hi, lo)
+    __shared__ int bad;
+    const int tid = threadIdx.x;
+    const int nb = (int)((N - k0) < NBD ? (N - k0) : NBD);
+    if (tid == 0) bad = (st->not_pd_pivot != INT_MAX) ? 1 : 0;
+    for (int e = tid; e < NBD * NBD; e += 256) {
+        const int i = e / NBD, j = e % NBD;
+        double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
+        if (i < nb && j < nb && j <= i) v = G[(k0 + i) * ld + k0 + j];
+        A[e] = to_df(v);
+    }
+    __syncthreads();
+    // Right-looking, two barriers per column: thread 0 takes pivot j while the
+    // others scale column j - 1 by its reciprocal pivot; then the trailing
+    // update uses the unscaled column j with the factor 1 / d_j.
+    for (int j = 0; j < NBD; ++j) {
+        if (tid == 0) {
+            const float4 a = A[j * NBD + j];
+            double d = (double)a.x + (double)a.y;
+            if (!(d > 0.0) || !isfinite(d)) {
+                if (!bad) atomicMin(&st->not_pd_pivot, (int)(k0 + j));
+                bad = 1;
+                d = 1.0;
+            }
+            const double r = rsqrt(d);
+            A[j * NBD + j] = to_df(make_double2(d * r, 0.0));
+            const float rh = (float)r;
+            rdiag[j] = make_float2(rh, (float)(r - (double)rh));
+        } else if (j > 0) {
+            const float2 r = rdiag[j - 1];
+            for (int i = j + tid - 1; i < NBD; i += 255) A[i * NBD + j - 1] = df_norm(df_scale(A[i * NBD + j - 1], r.x, r.y));
+        }
+        __syncthreads();
+        float r2h, r2l;
+        df_mul(rdiag[j].x, rdiag[j].y, rdiag[j].x, rdiag[j].y, r2h, r2l);
+        const int rem = NBD - j - 1;
+        for (int e = tid; e < rem * rem; e += 256) {
+            const int i = j + 1 + e / rem, k = j + 1 + e % rem;
+            if (k <= i) {
+                float4 c = df_scale(A[i * NBD + j], -r2h, -r2l);
+                float4 v = A[i * NBD + k];
+                cacc(v, c, cdf_conj(A[k * NBD + j]));
+                A[i * NBD + k] = df_norm(v);
+            }
+        }
+        __syncthreads();
+    }
+    // X = A^-1 by forward substitution down each column; four lanes share a
+    // column (every fourth term of the dot product), combined by shuffles.
+    {
+        const int c = tid >> 2, q = tid & 3;
+        for (int i = 0; i < NBD; ++i) {
+            float4 part = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i > c)
+                for (int k = c + q; k < i; k += 4) cacc(part, A[i * NBD + k], X[k * NBD + c]);
+            part = df_norm(part);
+#pragma unroll
+            for (int m = 1; m <= 2; m <<= 1) {
+                float4 o;
+                o.x = __shfl_xor_sync(0xffffffffu, part.x, m);
+                o.y = __shfl_xor_sync(0xffffffffu, part.y, m);
+                o.z = __shfl_xor_sync(0xffffffffu, part.z, m);
+                o.w = __shfl_xor_sync(0xffffffffu, part.w, m);
+                part = df_cadd(part, o);
+            }
+            if (q == 0) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i >= c) {
+                    float4 t = make_float4(-part.x, -part.y, -part.z, -part.w);
+                    if (i == c) t = df_cadd(t, make_float4(1.f, 0.f, 0.f, 0.f));
+                    v = df_norm(df_scale(t, rdiag[i].x, rdiag[i].y));
+                }
+                X[i * NBD + c] = v;
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < NBD * NBD; e += 256) {
+        const int i = e / NBD, j = e % NBD;
+        const double2 x = from_df(X[e]);
+        Dinv[e] = x;
+        if (Dinv32) Dinv32[e] = make_float2((float)x.x, (float)x.y);
+        if (i < nb && j < nb && j <= i) G[(k0 + i) * ld + k0 + j] = from_df(A[e]);
+    }
+}
+
+cudaError_t launch_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv, float2* Dinv32,
+                                 DevStatus* st, cudaStream_t s) {
+    static bool attr = false;
+    const size_t smem = 2 * NBD * NBD * sizeof(float4);
+    if (!attr) {
+        cudaError_t err =
+            cudaFuncSetAttribute(k_potrf_diag_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        attr = true;
+    }
+    k_potrf_diag_df<<<1, 256, smem, s>>>(G, ld, N, k0, Dinv, Dinv32, st);
     note_launch();
     return cudaGetLastError();
 }
@@ -383,26 +553,51 @@ struct TrmvH32 {
     }
 };
 
-template <class P>
-static cudaError_t launch_c(P p, int64_t rows, int64_t F, cudaStream_t s) {
-    if (F >= 48) {
-        dim3 grid((unsigned)((F + 63) / 64), (unsigned)((rows + 63) / 64));
-        k_ctile<64, 64, 4, 4><<<grid, 256, 0, s>>>(p);
-    } else if (F >= 8) {
-        dim3 grid((unsigned)((F + 15) / 16), (unsigned)((rows + 15) / 16));
-        k_ctile<16, 16, 1, 1><<<grid, 256, 0, s>>>(p);
-    } else {
-        dim3 grid((unsigned)((F + 3) / 4), (unsigned)((rows + 63) / 64));
-        k_ctile<64, 4, 1, 1><<<grid, 256, 0, s>>>(p);
-    }
+template <int BM, int BN, int TM, int TN, class P>
+static cudaError_t c_shape(const P& p, int64_t rows, int64_t F, cudaStream_t s) {
+    dim3 grid((unsigned)((F + BN - 1) / BN), (unsigned)((rows + BM - 1) / BM));
+    k_ctile<BM, BN, TM, TN><<<grid, 256, 0, s>>>(p);
     note_launch();
     return cudaGetLastError();
+}
+
+// family != nullptr: autotuned (only for problems whose launches can be
+// repeated, i.e. that overwrite their output)
+template <class P>
+static cudaError_t launch_c(P p, int64_t rows, int64_t F, cudaStream_t s, const char* family = nullptr) {
+    if (F >= 48) {
+        auto run = [&](int c) -> cudaError_t {
+            switch (c) {
+                case 1: return c_shape<32, 64, 2, 4>(p, rows, F, s);
+                case 2: return c_shape<128, 64, 8, 4>(p, rows, F, s);
+                default: return c_shape<64, 64, 4, 4>(p, rows, F, s);
+            }
+        };
+        return run(family ? tune_pick(family, rows, F, 3, run, s) : 0);
+    }
+    if (F >= 8) {
+        auto run = [&](int c) -> cudaError_t {
+            switch (c) {
+                case 1: return c_shape<32, 16, 2, 1>(p, rows, F, s);
+                case 2: return c_shape<64, 16, 4, 1>(p, rows, F, s);
+                default: return c_shape<16, 16, 1, 1>(p, rows, F, s);
+            }
+        };
+        return run(family ? tune_pick(family, rows, F, 3, run, s) : 0);
+    }
+    auto run = [&](int c) -> cudaError_t {
+        switch (c) {
+            case 1: return c_shape<128, 4, 2, 1>(p, rows, F, s);
+            default: return c_shape<64, 4, 1, 1>(p, rows, F, s);
+        }
+    };
+    return run(family ? tune_pick(family, rows, F, 2, run, s) : 0);
 }
 
 cudaError_t launch_correct32(const float2* W32, int64_t N, const double2* R, int64_t F, float2* T, double2* X,
                              cudaStream_t s) {
     if (F == 0) return cudaSuccess;
-    cudaError_t e = launch_c(Trmv32{W32, R, T, N, F}, N, F, s);
+    cudaError_t e = launch_c(Trmv32{W32, R, T, N, F}, N, F, s, "trmv32");
     if (e != cudaSuccess) return e;
     return launch_c(TrmvH32{W32, T, X, N, F}, N, F, s);
 }

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <functional>
 #include <string>
 
 #include "pinv.h"
@@ -129,6 +130,14 @@ cudaError_t launch_trtri64(const double2* L, int64_t N, int64_t ld, const double
 cudaError_t launch_lauum64(const double2* W, int64_t N, int64_t ld, double2* Ginv, cudaStream_t s);
 // One 64x64 diagonal block of the blocked Cholesky (FP64, in shared memory):
 // factor in place, check pivots, write the block inverse (and an FP32 copy).
+// Launch-shape autotuner: run(c) launches candidate c of a kernel family on
+// stream s; returns the fastest candidate for this size class (cached).
+using TuneRun = std::function<cudaError_t(int)>;
+int tune_pick(const char* family, int64_t rows, int64_t F, int ncand, const TuneRun& run, cudaStream_t s);
+
+// mixed path: the same diagonal block in double-float on the FP32 units
+cudaError_t launch_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv, float2* Dinv32,
+                                 DevStatus* st, cudaStream_t s);
 cudaError_t launch_potrf_diag(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv,
                               float2* Dinv32, DevStatus* st, cudaStream_t s);
 // Recon[n][(c,m)] = sum_n' Ginv[n][n'] conj(E[(c,m)][n']), FP64.

@@ -472,7 +472,8 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
     for (int64_t k0 = 0; k0 < N; k0 += NBK) {
         const int64_t nbk = std::min<int64_t>(NBK, N - k0);
         const int64_t kb = k0 / NBK;
-        cudaError_t e = launch_potrf_diag(G, ld, N, k0, Dinv + kb * NBK * NBK, Dinv32 + kb * NBK * NBK, st, s);
+        cudaError_t e =
+            launch_potrf_diag_df(G, ld, N, k0, Dinv + kb * NBK * NBK, Dinv32 + kb * NBK * NBK, st, s);
         if (e != cudaSuccess) return e;
         e = block_to_f32(G, ld, k0, N, k0, k0 + nbk, L32, N, s);
         if (e != cudaSuccess) return e;
@@ -670,21 +671,48 @@ __global__ void __launch_bounds__(256) k_apply32(const float2* __restrict__ R, i
         }
 }
 
+template <int BMv, int BNv, int TM, int TN, int BKv>
+static cudaError_t apply32_shape(const float2* R, int64_t N, int64_t M, const float2* D, int64_t F, float2* X,
+                                 cudaStream_t s) {
+    dim3 grid(cdiv(F, BNv), cdiv(N, BMv));
+    k_apply32<BMv, BNv, TM, TN, BKv><<<grid, 256, 0, s>>>(R, N, M, D, F, X);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Tile shape per frame-count class, chosen by the autotuner (all candidates
+// sum over the rows of Recon in the same order).
 cudaError_t launch_apply32(const float2* R, int64_t N, int64_t M, const float2* D, int64_t F, float2* X,
                            cudaStream_t s) {
     if (F == 0) return cudaSuccess;
     if (F >= 48) {
-        dim3 grid(cdiv(F, 64), cdiv(N, 64));
-        k_apply32<64, 64, 4, 4, 32><<<grid, 256, 0, s>>>(R, N, M, D, F, X);
-    } else if (F >= 8) {
-        dim3 grid(cdiv(F, 16), cdiv(N, 64));
-        k_apply32<64, 16, 4, 1, 32><<<grid, 256, 0, s>>>(R, N, M, D, F, X);
-    } else {
-        dim3 grid((unsigned)F, cdiv(N, 256));
-        k_apply32<256, 1, 1, 1, 16><<<grid, 256, 0, s>>>(R, N, M, D, F, X);
+        auto run = [&](int c) -> cudaError_t {
+            switch (c) {
+                case 1: return apply32_shape<128, 64, 8, 4, 16>(R, N, M, D, F, X, s);
+                case 2: return apply32_shape<32, 64, 2, 4, 32>(R, N, M, D, F, X, s);
+                case 3: return apply32_shape<64, 32, 4, 2, 32>(R, N, M, D, F, X, s);
+                default: return apply32_shape<64, 64, 4, 4, 32>(R, N, M, D, F, X, s);
+            }
+        };
+        return run(tune_pick("apply32", N, F, 4, run, s));
     }
-    note_launch();
-    return cudaGetLastError();
+    if (F >= 8) {
+        auto run = [&](int c) -> cudaError_t {
+            switch (c) {
+                case 1: return apply32_shape<128, 16, 8, 1, 16>(R, N, M, D, F, X, s);
+                case 2: return apply32_shape<32, 16, 2, 1, 32>(R, N, M, D, F, X, s);
+                default: return apply32_shape<64, 16, 4, 1, 32>(R, N, M, D, F, X, s);
+            }
+        };
+        return run(tune_pick("apply32", N, F, 3, run, s));
+    }
+    auto run = [&](int c) -> cudaError_t {
+        switch (c) {
+            case 1: return apply32_shape<128, 2, 1, 1, 16>(R, N, M, D, F, X, s);
+            default: return apply32_shape<256, 1, 1, 1, 16>(R, N, M, D, F, X, s);
+        }
+    };
+    return run(tune_pick("apply32", N, F, 2, run, s));
 }
 
 }  // namespace pinv
