@@ -403,6 +403,15 @@ def main():
                 "issued_tflops": 6 * flops_recon / (ms_recon / 1e3) / 1e12}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
+    if prec != L.FP64:
+        # DRAM bytes (read + write) of the two mixed Recon launches measured by ncu at
+        # 48x48, 8 coils (N = 2304, M = 36864); Recon traffic grows with N*M (T and
+        # Recon are [N][M]), so it is scaled to this workload. Valid for the current
+        # Recon kernels only.
+        nm_ref, bytes_ref = 2304.0 * 36864.0, 38490368 + 632123392 + 770332672 + 649221888
+        roof["traffic"] = bytes_ref * (float(N) * M / nm_ref) / 2
+        roof["traffic_source"] = "ncu dram bytes at 48x48 scaled by N*M, mean per launch"
+        roof["algorithmic_bytes"] = 3.0 * N * M * 8 / 2
     roof["ms_per_launch"] = ms_recon
 
     res = {}
