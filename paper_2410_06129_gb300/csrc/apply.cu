@@ -80,6 +80,11 @@ size_t apply_scratch_layout(const pinv_plan* p, int64_t F, int dtype, void* base
     s.d64 = need_d64 ? cv.take<float2>((size_t)(F * M)) : nullptr;
     s.x64 = need_x64 ? cv.take<float2>((size_t)(F * N)) : nullptr;
     s.norms = md.stop_rule ? cv.take<double>((size_t)(2 * F)) : nullptr;
+    if (md.dfres || md.toep || md.need_b) {
+        // E^H u (rows N, length M), E x (rows M, length N), G x (rows N, length N)
+        const size_t w = std::max(df_work_elems(N, F, M), std::max(df_work_elems(M, F, N), df_work_elems(N, F, N)));
+        s.dfw = w ? cv.take<float4>(w) : nullptr;
+    }
     if (sc) *sc = s;
     return cv.used;
 }
@@ -111,7 +116,7 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
     }
     double2* X = dtype == PINV_C128 ? (double2*)d_image : sc.x128;
 
-    if (md.need_b) CKA(launch_adjoint_df(p->enc, D, F, 0.0, nullptr, sc.b128, s));  // b = E^H d
+    if (md.need_b) CKA(launch_adjoint_df(p->enc, D, F, 0.0, nullptr, sc.b128, s, sc.dfw));  // b = E^H d
     if (!md.mixed) {
         if (p->recon) {
             CKA(launch_apply64((const double2*)p->R, N, M, D, F, X, s));
@@ -154,10 +159,10 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
         }
         for (int it = 0; it < p->refine_iters; ++it) {
             if (md.toep) {
-                CKA(launch_gram_resid_df(p->Gx, N, sc.b128, X, F, sc.r128, s));  // r = b - G x
+                CKA(launch_gram_resid_df(p->Gx, N, sc.b128, X, F, sc.r128, s, sc.dfw));  // r = b - G x
             } else if (md.dfres) {
-                CKA(launch_forward_df(p->enc, X, F, D, sc.u128, s));  // u = d - E x
-                CKA(launch_adjoint_df(p->enc, sc.u128, F, p->lambda_abs, X, sc.r128, s));
+                CKA(launch_forward_df(p->enc, X, F, D, sc.u128, s, sc.dfw));  // u = d - E x
+                CKA(launch_adjoint_df(p->enc, sc.u128, F, p->lambda_abs, X, sc.r128, s, sc.dfw));
             } else {
                 CKA(launch_forward64(p->enc, X, F, D, sc.u128, s));
                 CKA(launch_adjoint64(p->enc, sc.u128, F, p->lambda_abs, X, sc.r128, s));

@@ -12,6 +12,7 @@
 //
 // The correction step x += W^H (W r) only preconditions the next residual, so
 // it runs in plain FP32 (tile engine k_ctile).
+#include <algorithm>
 #include <climits>
 
 #include "pinv_internal.h"
@@ -96,30 +97,37 @@ __device__ inline float4 gen_e_df(const EncodeDev& e, int c, int64_t m, int64_t 
 }
 
 // ------------------------------------------------------------------ double-float tile engine
+// C[i][j] = sum_k a(i,k) b(k,j) over rows i, frames j. With a split of the k
+// range over blockIdx.z (part != nullptr), each CTA writes its unreduced
+// double-float partial to part[z][j][i] and k_df_reduce adds the partials in
+// order z = 0, 1, ...; the split count depends only on the problem size, so a
+// given problem always sums in the same order whatever tile shape runs it.
 template <int BM, int BN, int TM, int TN, class P, int BK = 16>
-__global__ void __launch_bounds__(256) k_dftile(P p) {
+__global__ void __launch_bounds__(256) k_dftile(P p, float4* part, int64_t chunk, int64_t rows, int64_t F) {
     constexpr int TX = BN / TN, TY = BM / TM;
     static_assert(TX * TY == 256, "256 threads");
     __shared__ float4 As[BK][BM];
     __shared__ float4 Bs[BK][BN];
     const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
     const int64_t K = p.K();
+    const int64_t kb = (int64_t)blockIdx.z * chunk;
+    const int64_t ke = kb + chunk < K ? kb + chunk : K;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     float4 acc[TM][TN];
 #pragma unroll
     for (int r = 0; r < TM; ++r)
 #pragma unroll
         for (int c = 0; c < TN; ++c) acc[r][c] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int64_t k0 = 0; k0 < K; k0 += BK) {
+    for (int64_t k0 = kb; k0 < ke; k0 += BK) {
         for (int e = tid; e < BK * BM; e += 256) {
             const int ii = e % BM, kk = e / BM;
             const int64_t gi = i0 + ii, gk = k0 + kk;
-            As[kk][ii] = (gk < K && p.a_ok(gi)) ? p.a(gi, gk) : make_float4(0.f, 0.f, 0.f, 0.f);
+            As[kk][ii] = (gk < ke && p.a_ok(gi)) ? p.a(gi, gk) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         for (int e = tid; e < BK * BN; e += 256) {
             const int kk = e % BK, jj = e / BK;
             const int64_t gj = j0 + jj, gk = k0 + kk;
-            Bs[kk][jj] = (gk < K && p.b_ok(gj)) ? p.b(gk, gj) : make_float4(0.f, 0.f, 0.f, 0.f);
+            Bs[kk][jj] = (gk < ke && p.b_ok(gj)) ? p.b(gk, gj) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncthreads();
 #pragma unroll 2
@@ -141,8 +149,26 @@ __global__ void __launch_bounds__(256) k_dftile(P p) {
 #pragma unroll
         for (int c = 0; c < TN; ++c) {
             const int64_t gi = i0 + ty + TY * r, gj = j0 + tx + TX * c;
-            if (p.a_ok(gi) && p.b_ok(gj)) p.store(gi, gj, from_df(acc[r][c]));
+            if (!(p.a_ok(gi) && p.b_ok(gj))) continue;
+            if (part) part[((int64_t)blockIdx.z * F + gj) * rows + gi] = acc[r][c];
+            else p.store(gi, gj, from_df(acc[r][c]));
         }
+}
+
+template <class P>
+__global__ void k_df_reduce(P p, const float4* part, int splits, int64_t rows, int64_t F) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * F) return;
+    const int64_t i = idx % rows, j = idx / rows;
+    float4 a = part[j * rows + i];
+    for (int z = 1; z < splits; ++z) {
+        const float4 b = part[((int64_t)z * F + j) * rows + i];
+        float rh, rl, ih, il;
+        df_add(a.x, a.y, b.x, b.y, rh, rl);
+        df_add(a.z, a.w, b.z, b.w, ih, il);
+        a = make_float4(rh, rl, ih, il);
+    }
+    p.store(i, j, from_df(a));
 }
 
 // U[f][(c,m)] = D[f][(c,m)] - sum_n E[(c,m)][n] X[f][n]
@@ -192,61 +218,88 @@ struct AdjointDF {
     }
 };
 
+// Split count of the k range for a double-float frame product of `rows` rows,
+// F frames and length K: about four CTAs per SM on a reference tiling of
+// 16 x 64 (independent of the tuned shape), chunks of at least 512.
+int df_splits(int64_t rows, int64_t F, int64_t K) {
+    const int64_t tiles = ((rows + 15) / 16) * ((F + 63) / 64);
+    int64_t sp = (600 + tiles - 1) / tiles;
+    sp = std::min<int64_t>(sp, K / 512);
+    sp = std::min<int64_t>(std::max<int64_t>(sp, 1), 32);
+    return (int)sp;
+}
+
+size_t df_work_elems(int64_t rows, int64_t F, int64_t K) {
+    const int sp = df_splits(rows, F, K);
+    return sp > 1 ? (size_t)sp * (size_t)rows * (size_t)F : 0;
+}
+
 template <int BM, int BN, int TM, int TN, class P>
-static cudaError_t df_shape(const P& p, int64_t rows, int64_t F, cudaStream_t s) {
-    dim3 grid((unsigned)((F + BN - 1) / BN), (unsigned)((rows + BM - 1) / BM));
-    k_dftile<BM, BN, TM, TN, P><<<grid, 256, 0, s>>>(p);
+static cudaError_t df_shape(const P& p, int64_t rows, int64_t F, int sp, int64_t chunk, float4* work,
+                            cudaStream_t s) {
+    dim3 grid((unsigned)((F + BN - 1) / BN), (unsigned)((rows + BM - 1) / BM), (unsigned)sp);
+    k_dftile<BM, BN, TM, TN, P><<<grid, 256, 0, s>>>(p, sp > 1 ? work : nullptr, chunk, rows, F);
     note_launch();
     return cudaGetLastError();
 }
 
 // Tile shape per frame-count class, chosen by the autotuner among candidates
-// that all sum over k in the same order.
+// that all sum over k in the same order (same split, same chunks).
 template <class P>
-static cudaError_t launch_df(P p, int64_t rows, int64_t F, cudaStream_t s, const char* family) {
+static cudaError_t launch_df(P p, int64_t rows, int64_t F, int64_t K, cudaStream_t s, const char* family,
+                             float4* work) {
+    const int sp = df_splits(rows, F, K);
+    if (sp > 1 && !work) return cudaErrorInvalidValue;
+    const int64_t chunk = ((K + sp - 1) / sp + 15) / 16 * 16;
+    cudaError_t err;
     if (F >= 48) {
         auto run = [&](int c) -> cudaError_t {
             switch (c) {
-                case 1: return df_shape<32, 64, 2, 4>(p, rows, F, s);
-                case 2: return df_shape<64, 64, 4, 4>(p, rows, F, s);
-                case 3: return df_shape<32, 32, 2, 2>(p, rows, F, s);
-                case 4: return df_shape<64, 32, 4, 2>(p, rows, F, s);
-                default: return df_shape<16, 64, 1, 4>(p, rows, F, s);
+                case 1: return df_shape<32, 64, 2, 4>(p, rows, F, sp, chunk, work, s);
+                case 2: return df_shape<64, 64, 4, 4>(p, rows, F, sp, chunk, work, s);
+                case 3: return df_shape<32, 32, 2, 2>(p, rows, F, sp, chunk, work, s);
+                case 4: return df_shape<64, 32, 4, 2>(p, rows, F, sp, chunk, work, s);
+                default: return df_shape<16, 64, 1, 4>(p, rows, F, sp, chunk, work, s);
             }
         };
-        return run(tune_pick(family, rows, F, 5, run, s));
-    }
-    if (F >= 8) {
+        err = run(tune_pick(family, rows, F, 5, run, s));
+    } else if (F >= 8) {
         auto run = [&](int c) -> cudaError_t {
             switch (c) {
-                case 1: return df_shape<32, 16, 2, 1>(p, rows, F, s);
-                case 2: return df_shape<64, 16, 4, 1>(p, rows, F, s);
-                case 3: return df_shape<32, 32, 2, 2>(p, rows, F, s);
-                default: return df_shape<16, 16, 1, 1>(p, rows, F, s);
+                case 1: return df_shape<32, 16, 2, 1>(p, rows, F, sp, chunk, work, s);
+                case 2: return df_shape<64, 16, 4, 1>(p, rows, F, sp, chunk, work, s);
+                case 3: return df_shape<32, 32, 2, 2>(p, rows, F, sp, chunk, work, s);
+                default: return df_shape<16, 16, 1, 1>(p, rows, F, sp, chunk, work, s);
             }
         };
-        return run(tune_pick(family, rows, F, 4, run, s));
+        err = run(tune_pick(family, rows, F, 4, run, s));
+    } else {
+        auto run = [&](int c) -> cudaError_t {
+            switch (c) {
+                case 1: return df_shape<128, 4, 2, 1>(p, rows, F, sp, chunk, work, s);
+                case 2: return df_shape<128, 2, 1, 1>(p, rows, F, sp, chunk, work, s);
+                default: return df_shape<64, 4, 1, 1>(p, rows, F, sp, chunk, work, s);
+            }
+        };
+        err = run(tune_pick(family, rows, F, 3, run, s));
     }
-    auto run = [&](int c) -> cudaError_t {
-        switch (c) {
-            case 1: return df_shape<128, 4, 2, 1>(p, rows, F, s);
-            case 2: return df_shape<128, 2, 1, 1>(p, rows, F, s);
-            default: return df_shape<64, 4, 1, 1>(p, rows, F, s);
-        }
-    };
-    return run(tune_pick(family, rows, F, 3, run, s));
+    if (err != cudaSuccess || sp == 1) return err;
+    const int64_t n = rows * F;
+    k_df_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, work, sp, rows, F);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_forward_df(const EncodeDev& e, const double2* X, int64_t F, const double2* D, double2* U,
-                              cudaStream_t s) {
+                              cudaStream_t s, float4* work) {
     if (F == 0) return cudaSuccess;
-    return launch_df(ForwardDF{e, X, D, U, F}, e.Mk * e.C, F, s, "forward_df");
+    return launch_df(ForwardDF{e, X, D, U, F}, e.Mk * e.C, F, e.N, s, "forward_df", work);
 }
 
 cudaError_t launch_adjoint_df(const EncodeDev& e, const double2* U, int64_t F, double lam, const double2* X,
-                              double2* R, cudaStream_t s) {
+                              double2* R, cudaStream_t s, float4* work) {
     if (F == 0) return cudaSuccess;
-    return launch_df(AdjointDF{e, U, X, R, lam, F}, e.N, F, s, "adjoint_df");
+    return launch_df(AdjointDF{e, U, X, R, lam, F}, e.N, F, e.Mk * e.C, s, "adjoint_df", work);
 }
 
 // ------------------------------------------------------------------ exact Gram residual
@@ -297,9 +350,9 @@ struct GramResidDF {
 };
 
 cudaError_t launch_gram_resid_df(const float4* G, int64_t N, const double2* B, const double2* X, int64_t F,
-                                 double2* R, cudaStream_t s) {
+                                 double2* R, cudaStream_t s, float4* work) {
     if (F == 0) return cudaSuccess;
-    return launch_df(GramResidDF{G, B, X, R, N, F}, N, F, s, "gram_resid_df");
+    return launch_df(GramResidDF{G, B, X, R, N, F}, N, F, N, s, "gram_resid_df", work);
 }
 
 __global__ void k_from_df(const float4* a, int64_t n, double2* b) {

@@ -225,18 +225,22 @@ cudaError_t tc_multi_create(int kind, const TcPlanArgs* args, int n, TcMulti* ou
 cudaError_t tc_multi_launch(const TcMulti& m, int slices, DevStatus* st, cudaStream_t s);
 void tc_multi_free(TcMulti* m);
 
+// double-float frame products split their k range over CTAs; `work` holds
+// df_work_elems() partials (float4) when the split count is above one
+size_t df_work_elems(int64_t rows, int64_t F, int64_t K);
+
 // exact Gram of B0-free grid plans (Toeplitz table, FP64; stored double-float)
 size_t toeplitz_work_bytes(const EncodeDev& e);
 cudaError_t launch_toeplitz64(const EncodeDev& e, double2* work, double2* T, cudaStream_t s);
 cudaError_t launch_gram_exact(const EncodeDev& e, const double2* T, double lam, float4* G, cudaStream_t s);
 cudaError_t launch_gram_resid_df(const float4* G, int64_t N, const double2* B, const double2* X, int64_t F,
-                                 double2* R, cudaStream_t s);
+                                 double2* R, cudaStream_t s, float4* work);
 cudaError_t launch_from_df(const float4* a, int64_t n, double2* b, cudaStream_t s);
 cudaError_t launch_forward_df(const EncodeDev& e, const double2* X, int64_t F, const double2* D, double2* U,
-                              cudaStream_t s);
+                              cudaStream_t s, float4* work);
 // R[f] = E^H U[f] - lam X[f] (X may be null), double-float arithmetic, FP64 in/out
 cudaError_t launch_adjoint_df(const EncodeDev& e, const double2* U, int64_t F, double lam, const double2* X,
-                              double2* R, cudaStream_t s);
+                              double2* R, cudaStream_t s, float4* work);
 // X[f] += W^H (W R[f]) in FP32 with scratch T [F][N]
 cudaError_t launch_correct32(const float2* W32, int64_t N, const double2* R, int64_t F, float2* T, double2* X,
                              cudaStream_t s);

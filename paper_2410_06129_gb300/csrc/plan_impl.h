@@ -23,6 +23,7 @@ struct ApplyScratch {
     float2* d64;    // c64 copy of c128 data [F][M]
     float2* x64;    // c64 image / FP32 correction temporary [F][N]
     double* norms;  // per-frame squared norms [2F]
+    float4* dfw;    // partial sums of the split double-float products
 };
 // Bytes an apply of F frames of `dtype` needs; with base != nullptr also
 // carves the region at base into *sc.
