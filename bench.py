@@ -285,6 +285,49 @@ def run_batch(prec, refine, steps, warmup, frames=256, seed=3100):
             "gpu_launches_per_step": int(launches), "steps": steps}
 
 
+def run_cfg5(prec, refine, frames=64, seed=5100):
+    """Workload 5: 192x192 (N = 36864), 8 coils, 384 radial spokes x 125 samples
+    (M = 384000), B0 +-50 Hz, lambda_rel 1e-4, 64 complex64 frames; factor-only
+    (Recon would be 113 GB). One build, then the apply timed on its second run.
+    Without an oracle at this size, accuracy is reported as the refinement's
+    final residual ||E^H (d - E x) - lambda x|| / ||E^H d|| (largest over frames)."""
+    import torch
+
+    from paper_2410_06129_gb300 import _lib as L
+    from paper_2410_06129_gb300 import synth
+    from paper_2410_06129_gb300.plan import Plan
+
+    geo = synth.config(5, frames=0)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    data = torch.randn((frames, geo.n_coils * geo.n_samples), generator=gen, device="cuda", dtype=torch.complex64)
+    out = torch.empty((frames, geo.n_vox), dtype=torch.complex64, device="cuda")
+    stream = torch.cuda.current_stream()
+    with Plan.from_inputs(geo, precision=prec, recon_mode=L.RECON_NONE, refine_max_iters=refine,
+                          refine_tol=1e-300) as plan:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.build_async(stream)
+        e1.record(stream)
+        plan.sync()
+        torch.cuda.synchronize()
+        build_s = e0.elapsed_time(e1) / 1e3
+        inf = plan.info()
+        plan.apply(data, out)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        plan.apply(data, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        apply_s = e0.elapsed_time(e1) / 1e3
+        inf2 = plan.info()
+    return {"workload": "192x192 (N=36864), 8 coils, 384 radial spokes x 125 samples (M=384000), B0 +-50 Hz, "
+                        f"lambda 1e-4 mean diag, {frames} c64 frames, factor-only",
+            "build_s": build_s, "stage_ms": {k: inf[k] for k in ("ms_gram", "ms_chol", "ms_inverse", "ms_recon")},
+            "apply_s": apply_s, "frames_per_s": frames / apply_s, "refine_steps": refine,
+            "final_residual_ratio": inf2["last_refine_resid"], "bytes_device": inf["bytes_device"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -307,6 +350,8 @@ def main():
     ap.add_argument("--serve-refine", type=int, default=3)
     ap.add_argument("--batch", default="on", choices=["on", "off"],
                     help="workload 3: 16 uneven plans x 256 frames as one graph-replayed batch")
+    ap.add_argument("--cfg5", default="off", choices=["on", "off"],
+                    help="workload 5 (192x192, B0, factor-only): one build and one timed apply")
     ap.add_argument("--serve-fp64-duration", type=float, default=1.0,
                     help="seconds of the same trace served by FP64 plans (0 = skip)")
     args = ap.parse_args()
@@ -474,6 +519,10 @@ def main():
             serve["fp64"] = run_serve(L.FP64, 0, div, args.serve_rate, args.serve_fp64_duration, budget,
                                       args.serve_slots, L.RECON_NONE)
 
+    cfg5 = None
+    if rank == 0 and args.cfg5 == "on":
+        cfg5 = run_cfg5(prec, refine if prec != L.FP64 else 1)
+
     batch = None
     if rank == 0 and args.batch == "on" and prec != L.FP64:
         batch = run_batch(prec, refine, steps=2, warmup=2)
@@ -501,6 +550,8 @@ def main():
         line["autotune"] = L.autotune_report()
         if batch is not None:
             line["batch"] = batch
+        if cfg5 is not None:
+            line["cfg5"] = cfg5
         if serve is not None:
             line["serve"] = serve
             line["serve_p50_ms"] = serve["mixed"]["p50_ms"]

@@ -8,7 +8,8 @@
 // the same order, so the choice changes speed, never results, and the timed
 // runs only rewrite the same outputs. While a stream is being captured into a
 // graph nothing can be timed: an untuned class then uses candidate 0 without
-// caching it. PINV_AUTOTUNE=0 in the environment disables tuning.
+// caching it. A class whose default shape runs longer than 100 ms keeps it
+// untimed. PINV_AUTOTUNE=0 in the environment disables tuning.
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -58,9 +59,18 @@ int tune_pick(const char* family, int64_t rows, int64_t F, int ncand, const Tune
     int best = 0;
     float best_ms = 1e30f;
     for (int c = 0; c < ncand; ++c) {
+        cudaEventRecord(e0, s);
         if (run(c) != cudaSuccess) {  // a shape this device cannot launch
             cudaGetLastError();
             continue;
+        }
+        cudaEventRecord(e1, s);
+        float warm = 0.f;
+        if (c == 0 && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&warm, e0, e1) == cudaSuccess &&
+            warm > 100.f) {
+            // launches this long are not worth timing five ways; keep the default shape
+            best_ms = 2.f * warm;
+            break;
         }
         cudaEventRecord(e0, s);
         const bool ok = run(c) == cudaSuccess && run(c) == cudaSuccess;

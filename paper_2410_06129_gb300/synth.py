@@ -267,12 +267,12 @@ def config(i: int, reduced: bool = False, frames: int | None = None) -> PlanInpu
     """
     if i == 1:
         side = 24 if reduced else 32
-        return make_plan(side, 1, "spiral", frames or 1, 1000, 1e-3,
+        return make_plan(side, 1, "spiral", 1 if frames is None else frames, 1000, 1e-3,
                          samples=2 * side * side, interleaves=1, name="cfg1")
     if i == 2:
         side = 24 if reduced else 64
         spi = 2048 if not reduced else (2 * side * side) // 4
-        return make_plan(side, 8, "spiral", frames or (4 if reduced else 64), 2000, 1e-4,
+        return make_plan(side, 8, "spiral", (4 if reduced else 64) if frames is None else frames, 2000, 1e-4,
                          samples=4 * spi, interleaves=4, name="cfg2")
     if i == 3:
         rng = np.random.default_rng(3000)
@@ -290,8 +290,8 @@ def config(i: int, reduced: bool = False, frames: int | None = None) -> PlanInpu
         return serve_plans(reduced=reduced)
     if i == 5:
         side, P, S = (192, 384, 125) if not reduced else (32, 64, 40)
-        return make_plan(side, 8, "radial", frames or (64 if not reduced else 2), 5000, 1e-4,
-                         b0=True, spokes=P, per_spoke=S, name="cfg5")
+        nf = (64 if not reduced else 2) if frames is None else frames
+        return make_plan(side, 8, "radial", nf, 5000, 1e-4, b0=True, spokes=P, per_spoke=S, name="cfg5")
     raise ValueError(i)
 
 
