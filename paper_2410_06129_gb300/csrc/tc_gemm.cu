@@ -267,18 +267,19 @@ struct TrsmTC {
     }
 };
 
-// Trailing update G[i][j] -= sum_k P[i][k] conj(P[j][k]) on lower tiles (i, j >= t0).
+// Trailing update G[i][j] -= sum_k P[i][k] conj(P[j][k]) on lower tiles, rows
+// i >= t0 and columns t0 <= j < jmax (jmax < N restricts it to a panel).
 struct HerkTC {
     const float2* P;
     int64_t ldp;
     double2* G;
-    int64_t ld, N, nbk, t0;
+    int64_t ld, N, nbk, t0, jmax;
     __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
         i0 = t0 + by * BM;
         j0 = t0 + bx * BN;
         kb = 0;
         ke = nbk;
-        return i0 < N && j0 < N && j0 <= i0 + BM - 1;
+        return i0 < N && j0 < jmax && j0 <= i0 + BM - 1;
     }
     __device__ RowPtr row_a(int64_t i) const { return RowPtr{P + (i < N ? i : 0) * ldp, i < N}; }
     __device__ RowPtr row_b(int64_t j) const { return RowPtr{P + (j < N ? j : 0) * ldp, j < N}; }
@@ -291,7 +292,7 @@ struct HerkTC {
         for (int t = 0; t < 8; ++t) v[t].y = -v[t].y;
     }
     __device__ bool row_ok(int64_t i) const { return i < N; }
-    __device__ bool col_ok(int64_t j) const { return j < N; }
+    __device__ bool col_ok(int64_t j) const { return j < jmax; }
     __device__ void store(int64_t i, int64_t j, float2 v) const {
         if (j > i) return;
         const double2 g = G[i * ld + j];
@@ -337,20 +338,20 @@ struct TrtriDiagTC {
     }
 };
 
-// W[i][j] -= sum_k L[i][k0+k] W[k0+k][j] for i >= k0 + nbk, j < k0 + nbk.
+// W[i][j] -= sum_k L[i][k0+k] W[k0+k][j] for k0 + nbk <= i < imax, j < k0 + nbk.
 struct TrtriUpdTC {
     const float2* L32;
     int64_t ldl;
     double2* W;
-    int64_t ld, N, k0, nbk;
+    int64_t ld, N, k0, nbk, imax;
     __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
         i0 = k0 + nbk + by * BM;
         j0 = bx * BN;
         kb = 0;
         ke = nbk;
-        return i0 < N;
+        return i0 < imax;
     }
-    __device__ RowPtr row_a(int64_t i) const { return RowPtr{L32 + (i < N ? i : 0) * ldl + k0, i < N}; }
+    __device__ RowPtr row_a(int64_t i) const { return RowPtr{L32 + (i < imax ? i : 0) * ldl + k0, i < imax}; }
     __device__ int64_t row_b(int64_t j) const { return j; }
     __device__ void a8(const RowPtr& r, int64_t k, int64_t ke, float2 (&v)[8]) const {
         load8f(r.p + k, r.ok ? (int)(ke - k) : 0, v);
@@ -366,7 +367,7 @@ struct TrtriUpdTC {
             }
         }
     }
-    __device__ bool row_ok(int64_t i) const { return i < N; }
+    __device__ bool row_ok(int64_t i) const { return i < imax; }
     __device__ bool col_ok(int64_t j) const { return j < k0 + nbk; }
     __device__ void store(int64_t i, int64_t j, float2 v) const {
         const double2 w = W[i * ld + j];
@@ -466,43 +467,70 @@ cudaError_t launch_gram_tc(const EncodeDev& e, double lambda, int slices, double
     return run(p, dim3(cdiv(e.N, tc::BN), cdiv(e.N, tc::BM)), slices, st, 1, s);
 }
 
+// Two-level blocking: 64-wide diagonal blocks inside 256-wide panels. Inside a
+// panel each step updates only the panel's remaining columns (K = 64); the
+// trailing matrix gets one update per panel with K = 256, so its tiles run
+// 16 tensor-core stages instead of 4 and G is read and written a quarter as
+// often.
+constexpr int NBK = 64, NBP = 256;
+
 cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, float2* Dinv32, float2* L32,
                             int slices, DevStatus* st, cudaStream_t s) {
-    constexpr int NBK = 64;
-    for (int64_t k0 = 0; k0 < N; k0 += NBK) {
-        const int64_t nbk = std::min<int64_t>(NBK, N - k0);
-        const int64_t kb = k0 / NBK;
-        cudaError_t e =
-            launch_potrf_diag_df(G, ld, N, k0, Dinv + kb * NBK * NBK, Dinv32 + kb * NBK * NBK, st, s);
-        if (e != cudaSuccess) return e;
-        e = block_to_f32(G, ld, k0, N, k0, k0 + nbk, L32, N, s);
-        if (e != cudaSuccess) return e;
-        const int64_t rest = N - k0 - nbk;
-        if (rest <= 0) break;
-        tc::TrsmTC tp{L32 + k0, N, Dinv32 + kb * NBK * NBK, G, ld, N, k0, nbk};
-        if ((e = run(tp, dim3(1, cdiv(rest, tc::BM)), slices, st, 3, s)) != cudaSuccess) return e;
-        tc::HerkTC hp{L32 + k0, N, G, ld, N, nbk, k0 + nbk};
-        if ((e = run(hp, dim3(cdiv(rest, tc::BN), cdiv(rest, tc::BM)), slices, st, 4, s)) != cudaSuccess)
-            return e;
+    for (int64_t p0 = 0; p0 < N; p0 += NBP) {
+        const int64_t pend = std::min<int64_t>(N, p0 + NBP);
+        for (int64_t k0 = p0; k0 < pend; k0 += NBK) {
+            const int64_t nbk = std::min<int64_t>(NBK, N - k0);
+            const int64_t kb = k0 / NBK;
+            cudaError_t e =
+                launch_potrf_diag_df(G, ld, N, k0, Dinv + kb * NBK * NBK, Dinv32 + kb * NBK * NBK, st, s);
+            if (e != cudaSuccess) return e;
+            e = block_to_f32(G, ld, k0, N, k0, k0 + nbk, L32, N, s);
+            if (e != cudaSuccess) return e;
+            const int64_t rest = N - k0 - nbk;
+            if (rest <= 0) break;
+            tc::TrsmTC tp{L32 + k0, N, Dinv32 + kb * NBK * NBK, G, ld, N, k0, nbk};
+            if ((e = run(tp, dim3(1, cdiv(rest, tc::BM)), slices, st, 3, s)) != cudaSuccess) return e;
+            const int64_t t0 = k0 + nbk;
+            if (t0 < pend) {  // the panel's remaining columns, all rows below
+                tc::HerkTC hp{L32 + k0, N, G, ld, N, nbk, t0, pend};
+                if ((e = run(hp, dim3(cdiv(pend - t0, tc::BN), cdiv(N - t0, tc::BM)), slices, st, 4, s)) !=
+                    cudaSuccess)
+                    return e;
+            }
+        }
+        if (pend < N) {  // trailing matrix, K = panel width
+            tc::HerkTC hp{L32 + p0, N, G, ld, N, pend - p0, pend, N};
+            cudaError_t e = run(hp, dim3(cdiv(N - pend, tc::BN), cdiv(N - pend, tc::BM)), slices, st, 4, s);
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaGetLastError();
 }
 
+// W = L^-1 by blocked forward substitution on I, with the same two levels:
+// inside a 256-row panel each 64-row step updates the panel's rows only; the
+// rows below get one update per panel with K = 256.
 cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, double2* W, float2* W32,
                             int slices, DevStatus* st, cudaStream_t s) {
-    constexpr int NBK = 64;
     cudaError_t e = launch_fill_identity(W, N, N, s);
     if (e != cudaSuccess) return e;
-    for (int64_t k0 = 0; k0 < N; k0 += NBK) {
-        const int64_t nbk = std::min<int64_t>(NBK, N - k0);
-        const int64_t ncol = k0 + nbk;
-        tc::TrtriDiagTC dp{Dinv32 + (k0 / NBK) * NBK * NBK, W, N, N, k0, nbk};
-        if ((e = run(dp, dim3(cdiv(ncol, tc::BN), 1), slices, st, 5, s)) != cudaSuccess) return e;
-        const int64_t rest = N - ncol;
-        if (rest <= 0) break;
-        tc::TrtriUpdTC up{L32, N, W, N, N, k0, nbk};
-        if ((e = run(up, dim3(cdiv(ncol, tc::BN), cdiv(rest, tc::BM)), slices, st, 6, s)) != cudaSuccess)
-            return e;
+    for (int64_t p0 = 0; p0 < N; p0 += NBP) {
+        const int64_t pend = std::min<int64_t>(N, p0 + NBP);
+        for (int64_t k0 = p0; k0 < pend; k0 += NBK) {
+            const int64_t nbk = std::min<int64_t>(NBK, N - k0);
+            const int64_t ncol = k0 + nbk;
+            tc::TrtriDiagTC dp{Dinv32 + (k0 / NBK) * NBK * NBK, W, N, N, k0, nbk};
+            if ((e = run(dp, dim3(cdiv(ncol, tc::BN), 1), slices, st, 5, s)) != cudaSuccess) return e;
+            if (ncol >= pend) continue;
+            tc::TrtriUpdTC up{L32, N, W, N, N, k0, nbk, pend};
+            if ((e = run(up, dim3(cdiv(ncol, tc::BN), cdiv(pend - ncol, tc::BM)), slices, st, 6, s)) != cudaSuccess)
+                return e;
+        }
+        if (pend < N) {
+            tc::TrtriUpdTC up{L32, N, W, N, N, p0, pend - p0, N};
+            if ((e = run(up, dim3(cdiv(pend, tc::BN), cdiv(N - pend, tc::BM)), slices, st, 6, s)) != cudaSuccess)
+                return e;
+        }
     }
     return launch_to_f32(W, W32, N * N, s);
 }
