@@ -222,6 +222,7 @@ def run_serve(prec, refine, side_div, rate_hz, duration_s, budget, max_slots, re
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
         "frames_per_s": frames / st["span_s"] if st["span_s"] > 0 else None,
         "frames": frames, "builds": int(st["builds"]), "evictions": int(st["evictions"]),
+        "recon_drops": int(st["recon_drops"]),
         "wall_s": wall, "trace_s": duration_s, "rate_hz": rate_hz, "slots": max_slots,
         "budget_gb": budget / 1e9, "refine_steps": refine,
         "recon": "explicit" if recon_mode == L.RECON_STORE else "factor-only",

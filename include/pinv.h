@@ -100,6 +100,11 @@ typedef struct {
     int refine_max_iters;         /* refinement steps per apply (0 = none) */
     double refine_tol;            /* stop when ||r|| / ||E^H d|| <= tol (0 = run all steps) */
     int refine_residual;          /* mixed plans: pinv_residual arithmetic of the residual */
+    int lean;                     /* 1: G / L (and the FP64 W of mixed plans whose residual is not
+                                     FP64) exist only during pinv_build; the plan then keeps only
+                                     what its apply reads (56 -> 24 bytes per N^2 entry for a mixed
+                                     TOEPLITZ plan). Exports of L, W and G^-1 (mixed), maps and
+                                     batches are then unavailable. 0: keep them. */
 } pinv_plan_desc;
 
 /* How the refinement forms the normal-equation residual r = E^H (d - E x) - lambda x.
@@ -259,12 +264,16 @@ void pinv_batch_destroy(pinv_batch* batch);
  *     with its own stream and scratch, so work of different requests and of
  *     plan builds overlaps on the device;
  *   - a request whose plan is not resident builds it first on a separate build
- *     stream; idle resident plans are evicted least recently used first to
- *     fit the budget; a plan that cannot fit fails its request with
- *     PINV_ERR_BUDGET, and a plan whose Gram is not positive definite fails its
- *     requests with PINV_ERR_NOT_PD; other requests are unaffected;
- *   - a request's image is computed exactly as pinv_apply would compute it,
- *     whatever else is in flight.
+ *     stream. Room is made in tiers, least recently used first: idle plans
+ *     drop their Recon (they keep serving from their factors, x = W^H W E^H d
+ *     plus refinement), then idle plans are evicted; a plan whose Recon does
+ *     not fit is built factor-only. A plan that cannot fit even factor-only
+ *     fails its request with PINV_ERR_BUDGET, and a plan whose Gram is not
+ *     positive definite fails its requests with PINV_ERR_NOT_PD; other
+ *     requests are unaffected;
+ *   - a request's image is computed exactly as pinv_apply would compute it on
+ *     the plan in its current form (with or without Recon), whatever else is
+ *     in flight.
  * One worker thread per server issues all CUDA work; the calls below only
  * queue, poll or wait and are safe from any host thread. Registered plans run
  * their refinement with a fixed number of steps (refine_tol is ignored) so the
@@ -283,6 +292,7 @@ typedef struct {
     double span_s;                    /* first enqueue to last completion */
     size_t resident_bytes;            /* device bytes held by resident plans */
     int resident_plans, queued;
+    uint64_t recon_drops;             /* Recons dropped to make room (plans kept their factors) */
 } pinv_server_stats_t;
 
 /* Create a server on the current device. hbm_budget_bytes bounds the bytes of
@@ -318,6 +328,23 @@ void pinv_server_destroy(pinv_server* server);
  * same order. Writes a one-line summary of the choices made so far into buf
  * (NUL-terminated, truncated to bytes) and returns its full length. */
 size_t pinv_autotune_report(char* buf, size_t bytes);
+
+/* Per-voxel image-quality maps (Section 2.5), written to d_out [N] (device
+ * float64) on `stream`:
+ *   PINV_MAP_SRF   the SRF map, diag(Recon x Encode) (Eq. 9) = 1 - lambda diag(G^-1);
+ *   PINV_MAP_NOISE the noise map, diag(Recon Psi Recon^H) (Eq. 10). With psi == NULL
+ *                  the data noise is white (Psi = I) and the map is
+ *                  diag(G^-1) - lambda diag(G^-2). Otherwise psi is a host
+ *                  [C][C] complex128 coil noise covariance applied to every
+ *                  sample (Psi = psi (x) I), and the map is formed from the
+ *                  stored Recon (PINV_ERR_UNSUPPORTED for factor-only plans).
+ * FP64 plans use their FP64 G^-1. Mixed plans with the TOEPLITZ residual refine
+ * G^-1 with refine_max_iters double-float steps (temporary memory about
+ * 56 N^2 bytes); other mixed plans use W^H W from their split-precision factor
+ * (its error, up to kappa(G) times the split rounding, carries into the map).
+ * Coil-covariance maps carry the precision of the stored Recon. */
+typedef enum { PINV_MAP_SRF = 0, PINV_MAP_NOISE = 1 } pinv_map_what;
+pinv_status pinv_plan_map(pinv_plan* plan, int what, const double* psi, double* d_out, void* cuda_stream);
 
 /* Size of the fixed device scratch array behind pinv_apply_noalloc (64 MiB). */
 #define PINV_NOALLOC_SCRATCH_BYTES (64u << 20)

@@ -43,7 +43,7 @@ class PlanDesc(C.Structure):
         ("b0_hz", C.POINTER(C.c_double)), ("times", C.POINTER(C.c_double)),
         ("lambda_", C.c_double), ("lambda_mode", C.c_int), ("precision", C.c_int),
         ("recon_mode", C.c_int), ("refine_max_iters", C.c_int), ("refine_tol", C.c_double),
-        ("refine_residual", C.c_int),
+        ("refine_residual", C.c_int), ("lean", C.c_int),
     ]
 
 
@@ -68,7 +68,7 @@ class ServerStats(C.Structure):
         ("evictions", C.c_uint64), ("frames", C.c_double), ("p50_ms", C.c_double),
         ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
         ("span_s", C.c_double), ("resident_bytes", C.c_size_t), ("resident_plans", C.c_int),
-        ("queued", C.c_int),
+        ("queued", C.c_int), ("recon_drops", C.c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -93,6 +93,7 @@ SIGNATURES = {
     "pinv_plan_info": (C.c_int, [_VP, C.POINTER(PlanInfo)]),
     "pinv_plan_destroy": (None, [_VP]),
     "pinv_apply_noalloc": (C.c_int, [_VP, _VP, _VP, C.c_int64, C.c_int, _VP]),
+    "pinv_plan_map": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_double), _VP, _VP]),
     "pinv_autotune_report": (C.c_size_t, [C.c_char_p, C.c_size_t]),
     "pinv_batch_create": (C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, C.POINTER(_VP)]),
     "pinv_batch_build": (C.c_int, [_VP, _VP]),
@@ -110,6 +111,7 @@ SIGNATURES = {
 }
 NOALLOC_SCRATCH_BYTES = 64 << 20
 BATCH_GRAPH = 1
+MAP_SRF, MAP_NOISE = 0, 1
 
 _lib = None
 
@@ -150,7 +152,7 @@ def _dptr(a: np.ndarray | None, ctype):
 def make_desc(dims, traj, coil_maps=None, b0_hz=None, times=None, lam=1e-3,
               lambda_mode=LAMBDA_REL_MEAN_DIAG, precision=FP64, recon_mode=RECON_STORE,
               voxel_index=None, fov=None, refine_max_iters=0, refine_tol=0.0,
-              refine_residual=RESIDUAL_AUTO):
+              refine_residual=RESIDUAL_AUTO, lean=False):
     """Build a PlanDesc plus the numpy arrays that must outlive the create call."""
     dims = [int(d) for d in dims]
     ndim = len(dims)
@@ -189,4 +191,5 @@ def make_desc(dims, traj, coil_maps=None, b0_hz=None, times=None, lam=1e-3,
     if refine_residual == RESIDUAL_AUTO:
         refine_residual = RESIDUAL_DOUBLE_FLOAT if b0_hz is not None else RESIDUAL_TOEPLITZ
     d.refine_residual = int(refine_residual)
+    d.lean = 1 if lean else 0
     return d, keep

@@ -51,6 +51,10 @@ pinv_status build_begin(pinv_plan* p, cudaStream_t s) {
     p->built = false;
     pinv_status rs = reset_status(p, s);
     if (rs != PINV_OK) return rs;
+    if (p->lean) {  // stream-ordered temporaries, released by build_end
+        CK(cudaMallocAsync((void**)&p->G, sizeof(double2) * p->N * p->N, s));
+        if (p->lean_w()) CK(cudaMallocAsync((void**)&p->W, sizeof(double2) * p->N * p->N, s));
+    }
     if (p->keep_gram && !p->Gkeep) {
         pinv_status st = p->alloc((void**)&p->Gkeep, sizeof(double2) * p->N * p->N, "Gkeep");
         if (st != PINV_OK) return st;
@@ -124,6 +128,14 @@ pinv_status build_recon(pinv_plan* p, cudaStream_t s) {
 
 pinv_status build_end(pinv_plan* p, cudaStream_t s) {
     CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    if (p->lean) {
+        CK(cudaFreeAsync(p->G, s));
+        p->G = nullptr;
+        if (p->lean_w()) {
+            CK(cudaFreeAsync(p->W, s));
+            p->W = nullptr;
+        }
+    }
     return PINV_OK;
 }
 
@@ -188,6 +200,7 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
         return cleanup(fail(PINV_ERR_UNSUPPORTED, "the Toeplitz residual needs a plan without B0"));
     p->refine_residual = p->precision == PINV_FP64 ? PINV_RESIDUAL_FP64 : d->refine_residual;
     const bool toeplitz = p->refine_residual == PINV_RESIDUAL_TOEPLITZ;
+    p->lean = d->lean != 0;
 
     // voxel grid coordinates
     std::vector<int> ijk(3 * p->N);
@@ -348,11 +361,11 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
     }
     // factor storage
     int64_t nblk = (p->N + 63) / 64;
-    AL(p->G, sizeof(double2) * p->N * p->N, "G");
+    if (!p->lean) AL(p->G, sizeof(double2) * p->N * p->N, "G");
     AL(p->Dinv, sizeof(double2) * nblk * 64 * 64, "Dinv");
     if (p->precision == PINV_FP64) AL(p->Ginv, sizeof(double2) * p->N * p->N, "Ginv");
     else {
-        AL(p->W, sizeof(double2) * p->N * p->N, "W");
+        if (!p->lean_w()) AL(p->W, sizeof(double2) * p->N * p->N, "W");
         AL(p->W32, sizeof(float2) * p->N * p->N, "W32");
     }
     if (toeplitz) {
@@ -444,10 +457,16 @@ pinv_status pinv_plan_export(const pinv_plan* p, int what, void* dst, size_t byt
             if (!p->Gkeep) return fail(PINV_ERR_NOT_BUILT, "Gram not kept (pinv_plan_keep_gram before build)");
             src = p->Gkeep;
             break;
-        case PINV_EXPORT_CHOL: src = p->G; break;
-        case PINV_EXPORT_GINV: src = p->Ginv; break;
+        case PINV_EXPORT_CHOL:
+            if (!p->G) return fail(PINV_ERR_UNSUPPORTED, "a lean plan keeps no Cholesky factor");
+            src = p->G;
+            break;
+        case PINV_EXPORT_GINV:
+            if (!p->Ginv && !p->W) return fail(PINV_ERR_UNSUPPORTED, "a lean mixed plan keeps no FP64 inverse");
+            src = p->Ginv;
+            break;
         case PINV_EXPORT_LINV:
-            if (!p->W) return fail(PINV_ERR_UNSUPPORTED, "only mixed-precision plans keep L^-1");
+            if (!p->W) return fail(PINV_ERR_UNSUPPORTED, "only mixed-precision plans that are not lean keep L^-1");
             src = p->W;
             break;
         case PINV_EXPORT_GRAM_EXACT:

@@ -186,6 +186,7 @@ pinv_status pinv_batch_create(pinv_plan* const* plans, int n, int flags, pinv_ba
     for (int i = 0; i < n; ++i) {
         pinv_plan* p = b->plans[i];
         if (!p) return bad(set_error(PINV_ERR_INVALID_ARG, "null plan in batch"));
+        if (p->lean) return bad(set_error(PINV_ERR_INVALID_ARG, "lean plans move their buffers between builds"));
         for (int j = 0; j < i; ++j)
             if (b->plans[j] == p) return bad(set_error(PINV_ERR_INVALID_ARG, "plan listed twice"));
         if ((p->precision != PINV_FP64) != b->mixed || (b->mixed && p->slices() != b->slices))

@@ -62,6 +62,7 @@ struct pinv_plan {
     double refine_tol = 0;
     int refine_residual = PINV_RESIDUAL_DOUBLE_FLOAT;
     bool keep_gram = false;
+    bool lean = false;  // G and W are build temporaries
     bool built = false;
 
     std::vector<void*> allocs;
@@ -91,6 +92,23 @@ struct pinv_plan {
     int info = -1;
 
     int slices() const { return precision == PINV_MIXED_BF16X6 ? 3 : 2; }
+    // a lean mixed plan keeps only W32 when its residual does not use the FP64 W
+    bool lean_w() const { return lean && precision != PINV_FP64 && refine_residual != PINV_RESIDUAL_FP64; }
+
+    // Free the stored Recon; later applies take the factor-only path (x from
+    // W^H W E^H d, then the same refinement). Returns the bytes released.
+    size_t drop_recon() {
+        if (!recon || !R) return 0;
+        cudaFree(R);
+        for (auto& a : allocs)
+            if (a == R) a = nullptr;
+        const size_t b = bytes_recon;
+        bytes -= b;
+        bytes_recon = 0;
+        R = nullptr;
+        recon = 0;
+        return b;
+    }
 
     pinv_status alloc(void** p, size_t n, const char* what) {
         if (n == 0) n = 16;
@@ -107,7 +125,8 @@ struct pinv_plan {
     }
     ~pinv_plan() {
         if (scratch_buf) cudaFree(scratch_buf);
-        for (void* p : allocs) cudaFree(p);
+        for (void* p : allocs)
+            if (p) cudaFree(p);
         if (st_host) cudaFreeHost(st_host);
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);

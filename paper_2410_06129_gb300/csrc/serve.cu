@@ -93,7 +93,7 @@ struct pinv_server {
     size_t resident_bytes = 0;
     // statistics
     std::vector<double> latency_ms;
-    uint64_t completed = 0, failed = 0, builds = 0, evictions = 0;
+    uint64_t completed = 0, failed = 0, builds = 0, evictions = 0, recon_drops = 0;
     double frames = 0, t_first = 0, t_last = 0;
 
     void run();
@@ -106,20 +106,23 @@ struct pinv_server {
 
 namespace {
 
-// Device bytes a plan keeps while resident (its build transients are not counted).
-size_t plan_footprint(const pinv_plan_desc& d) {
-    const double N = (double)d.n_vox, M = (double)d.n_samples * d.n_coils;
+// Device bytes a plan keeps while resident (its build transients are not
+// counted): factors, exact Gram, phase tables and, if stored, Recon.
+size_t plan_footprint(const pinv_plan_desc& d, bool with_recon) {
+    const double N = (double)d.n_vox, Mk = (double)d.n_samples, M = Mk * d.n_coils;
     const bool fp64 = d.precision == PINV_FP64;
-    double b = N * N * 16.0;                  // G / L
-    b += fp64 ? N * N * 16.0 : N * N * 24.0;  // G^-1, or W and its FP32 copy
+    // lean plans: G^-1 (FP64), or W32 (+ the FP64 W for an FP64 residual)
+    double b = fp64 ? N * N * 16.0 : N * N * 8.0;
+    if (!fp64 && d.refine_residual == PINV_RESIDUAL_FP64) b += N * N * 16.0;
+    if (!fp64 && d.refine_residual == PINV_RESIDUAL_TOEPLITZ) b += N * N * 16.0;  // exact Gram
     int recon = d.recon_mode;
     if (recon == PINV_RECON_AUTO) recon = N * M * (fp64 ? 16.0 : 8.0) <= 64.0 * (1ull << 30);
-    if (recon) b += N * M * (fp64 ? 16.0 : 8.0);
-    if (!fp64 && d.refine_residual == PINV_RESIDUAL_TOEPLITZ) b += N * N * 16.0;  // exact Gram
+    if (recon && with_recon) b += N * M * (fp64 ? 16.0 : 8.0);
     int width = 0;
     for (int i = 0; i < d.ndim; ++i) width += d.dims[i];
-    b += (double)d.n_samples * width * 64.0 + N * d.n_coils * 40.0 + N * 64.0 + (double)(64u << 20);
-    return (size_t)b;
+    b += Mk * width * 48.0 + N * d.n_coils * 40.0 + N * 64.0;  // tables (c128, c64, double-float, transposed)
+    if (d.b0_hz) b += Mk * 8.0 + N * 48.0 * std::min(Mk, 4096.0);
+    return (size_t)b + (1u << 20);
 }
 
 }  // namespace
@@ -152,35 +155,50 @@ void pinv_server::evict(Registered& v) {
     v.bytes = 0;
 }
 
-// Make plan `id` resident, building it on the build stream. *defer is set when
-// it does not fit now but will once requests in flight have finished.
+// Make plan `id` resident, building it on the build stream. Room is made in
+// tiers: first the Recon of idle plans is dropped (least recently used
+// first; they keep serving from their factors), then idle plans are evicted.
+// A plan whose Recon does not fit is built factor-only. *defer is set when
+// the plan does not fit now but will once requests in flight have finished.
 pinv_status pinv_server::make_resident(Registered& r, int id, bool* defer) {
     *defer = false;
     if (r.plan) return PINV_OK;
-    const size_t need = plan_footprint(r.desc);
-    if (need > budget) return set_error(PINV_ERR_BUDGET, "plan footprint exceeds the server's HBM budget");
-    while (resident_bytes + need > budget) {
-        // least recently used idle plan
-        int victim = -1;
-        size_t busy_bytes = 0;
+    const size_t need_full = plan_footprint(r.desc, true), need_fac = plan_footprint(r.desc, false);
+    if (need_fac > budget) return set_error(PINV_ERR_BUDGET, "plan footprint exceeds the server's HBM budget");
+    auto lru_idle = [&](bool with_recon) {
+        int v = -1;
         for (int i = 0; i < (int)plans.size(); ++i) {
             const Registered& c = plans[i];
-            if (i == id || !c.plan) continue;
-            if (c.inflight > 0) {
-                busy_bytes += c.bytes;
-                continue;
-            }
-            if (victim < 0 || c.last_use < plans[victim].last_use) victim = i;
+            if (i == id || !c.plan || c.inflight > 0 || (with_recon && !c.plan->recon)) continue;
+            if (v < 0 || c.last_use < plans[v].last_use) v = i;
         }
-        if (victim < 0) {
-            *defer = busy_bytes > 0;
-            return *defer ? PINV_OK : set_error(PINV_ERR_BUDGET, "no idle plan to evict within the HBM budget");
-        }
-        evict(plans[victim]);
+        return v;
+    };
+    while (resident_bytes + need_full > budget) {  // tier 1: idle Recons
+        const int v = lru_idle(true);
+        if (v < 0) break;
+        const size_t freed = plans[v].plan->drop_recon();
+        plans[v].bytes -= std::min(plans[v].bytes, freed);
+        resident_bytes -= std::min(resident_bytes, freed);
+        ++recon_drops;
+    }
+    while (resident_bytes + need_fac > budget) {  // tier 2: idle plans
+        const int v = lru_idle(false);
+        if (v < 0) break;
+        evict(plans[v]);
         ++evictions;
     }
+    if (resident_bytes + need_fac > budget) {
+        size_t busy = 0;
+        for (auto& c : plans) busy += c.inflight > 0 ? c.bytes : 0;
+        *defer = busy > 0;
+        return *defer ? PINV_OK : set_error(PINV_ERR_BUDGET, "no idle plan to evict within the HBM budget");
+    }
+    pinv_plan_desc d = r.desc;
+    const bool full = resident_bytes + need_full <= budget;
+    if (!full) d.recon_mode = PINV_RECON_NONE;
     pinv_plan* p = nullptr;
-    pinv_status st = pinv_plan_create(&r.desc, build_stream, &p);
+    pinv_status st = pinv_plan_create(&d, build_stream, &p);
     if (st != PINV_OK) return st;
     st = pinv_build(p, build_stream);
     if (st != PINV_OK) {
@@ -193,7 +211,7 @@ pinv_status pinv_server::make_resident(Registered& r, int id, bool* defer) {
         return set_error(PINV_ERR_CUDA, cudaGetErrorString(e));
     }
     r.plan = p;
-    r.bytes = std::max(need, p->bytes);
+    r.bytes = std::max(full ? need_full : need_fac, p->bytes);
     resident_bytes += r.bytes;
     ++builds;
     return PINV_OK;
@@ -323,6 +341,7 @@ pinv_status pinv_serve_register(pinv_server* sv, const pinv_plan_desc* d, int* p
     Registered r;
     r.desc = *d;
     r.desc.refine_tol = 0.0;  // fixed refinement steps: the worker never waits on a host read
+    r.desc.lean = 1;          // resident plans keep only what an apply reads
     r.traj.assign(d->traj, d->traj + d->n_samples * d->ndim);
     r.desc.traj = r.traj.data();
     if (d->coil_maps) {
@@ -412,6 +431,7 @@ pinv_status pinv_server_stats(pinv_server* sv, pinv_server_stats_t* o) {
     o->failed = sv->failed;
     o->builds = sv->builds;
     o->evictions = sv->evictions;
+    o->recon_drops = sv->recon_drops;
     o->frames = sv->frames;
     o->resident_bytes = sv->resident_bytes;
     for (auto& p : sv->plans) o->resident_plans += p.plan != nullptr;

@@ -26,7 +26,7 @@ class Plan:
                  lambda_mode=L.LAMBDA_REL_MEAN_DIAG, precision=L.FP64,
                  recon_mode=L.RECON_STORE, voxel_index=None, fov=None,
                  refine_max_iters=None, refine_tol=0.0, refine_residual=L.RESIDUAL_AUTO,
-                 keep_gram=False, stream=None):
+                 keep_gram=False, lean=False, stream=None):
         lib = L.load()
         if refine_max_iters is None:
             # one FP64 refinement step brings the FP64 explicit-inverse image to
@@ -34,7 +34,7 @@ class Plan:
             refine_max_iters = 1 if precision == L.FP64 else 3
         desc, self._keep = L.make_desc(dims, traj, coil_maps, b0_hz, times, lam, lambda_mode,
                                        precision, recon_mode, voxel_index, fov,
-                                       refine_max_iters, refine_tol, refine_residual)
+                                       refine_max_iters, refine_tol, refine_residual, lean)
         h = C.c_void_p()
         L.check(lib.pinv_plan_create(C.byref(desc), _stream_handle(stream), C.byref(h)))
         self._h = h
@@ -96,6 +96,17 @@ class Plan:
         nbytes = t.numel() * t.element_size()
         L.check(L.load().pinv_plan_export(self._h, what, t.data_ptr(), nbytes, _stream_handle(stream)))
         return t
+
+    def map(self, what: int, psi=None, stream=None) -> torch.Tensor:
+        """Per-voxel SRF (L.MAP_SRF) or noise (L.MAP_NOISE) map, float64 [N];
+        psi: optional [C][C] coil noise covariance (noise map only)."""
+        out = torch.empty(self.n_vox, dtype=torch.float64, device="cuda")
+        ptr = None
+        if psi is not None:
+            self._psi = np.ascontiguousarray(psi, dtype=np.complex128)
+            ptr = self._psi.ctypes.data_as(C.POINTER(C.c_double))
+        L.check(L.load().pinv_plan_map(self._h, int(what), ptr, out.data_ptr(), _stream_handle(stream)))
+        return out
 
     def info(self) -> dict:
         inf = L.PlanInfo()

@@ -31,6 +31,7 @@ class Server:
             refine_max_iters = 1 if precision == L.FP64 else 3
         desc, keep = L.make_desc(dims, traj, coil_maps, b0_hz, times, lam, lambda_mode, precision,
                                  recon_mode, voxel_index, fov, refine_max_iters, 0.0, refine_residual)
+        # the server keeps plans lean: only what an apply reads stays resident
         pid = C.c_int()
         L.check(L.load().pinv_serve_register(self._h, C.byref(desc), C.byref(pid)))
         self._shapes[pid.value] = (int(desc.n_vox), int(desc.n_samples) * int(desc.n_coils))

@@ -117,13 +117,13 @@ def _resident_bytes(p, kw):
 
 
 def test_serve_lru_eviction_under_budget():
-    """A budget that holds one plan at a time: alternating requests rebuild and
-    evict, requests wait for in-flight work instead of failing, and results
-    stay identical to standalone applies."""
+    """A budget that holds one (factor-only) plan at a time: alternating
+    requests rebuild and evict, requests wait for in-flight work instead of
+    failing, and results stay identical to standalone applies."""
     from paper_2410_06129_gb300.serve import Server
-    cases = _cases()[:2]
+    cases = [(p, dict(kw, recon_mode=L.RECON_NONE)) for p, kw in _cases()[:2]]
     b = [_resident_bytes(p, kw) for p, kw in cases]
-    budget = int(1.25 * max(b))
+    budget = max(b) + min(b) // 2  # the larger plan fits, both do not
     assert budget < sum(b)
     order = [0, 1, 0, 1, 0]
     datas = [torch.from_numpy(cases[i][0].data[:2]).cuda() for i in order]
@@ -137,6 +137,37 @@ def test_serve_lru_eviction_under_budget():
         assert torch.equal(out, x)
     assert st["builds"] == len(order) and st["evictions"] == len(order) - 1
     assert st["resident_plans"] == 1 and st["resident_bytes"] <= budget
+
+
+def test_serve_drops_recon_before_evicting():
+    """A budget with room for both plans' factors but one Recon: the idle
+    plan's Recon is dropped, nothing is evicted, and that plan then serves from
+    its factors exactly as a standalone factor-only plan does."""
+    from paper_2410_06129_gb300.serve import Server
+    (p0, _), (p1, _) = _cases()[0], (synth.make_plan(18, 2, "spiral", 2, 2105, 1e-3, samples=648,
+                                                     interleaves=1), {})
+    full = dict(precision=L.FP64, recon_mode=L.RECON_STORE)
+    fac = dict(precision=L.FP64, recon_mode=L.RECON_NONE)
+    f0, f1, c0 = _resident_bytes(p0, full), _resident_bytes(p1, full), _resident_bytes(p0, fac)
+    budget = c0 + f1 + (f0 - c0) // 2
+    d0 = torch.from_numpy(p0.data[:2]).cuda()
+    d1 = torch.from_numpy(p1.data[:2]).cuda()
+    want0_full = _standalone(p0, full, d0)
+    want0_fac = _standalone(p0, fac, d0)
+    want1 = _standalone(p1, full, d1)
+    with Server(budget_bytes=budget, max_slots=2) as sv:
+        i0, i1 = sv.register_inputs(p0, **full), sv.register_inputs(p1, **full)
+        outs = []
+        for pid, d in ((i0, d0), (i1, d1), (i0, d0)):
+            t, o = sv.enqueue(pid, d)
+            assert sv.wait(t) == L.OK
+            outs.append(o)
+        st = sv.stats()
+    assert torch.equal(outs[0], want0_full)
+    assert torch.equal(outs[1], want1)
+    assert torch.equal(outs[2], want0_fac)
+    assert st["recon_drops"] == 1 and st["evictions"] == 0 and st["builds"] == 2
+    assert st["resident_bytes"] <= budget
 
 
 def test_serve_budget_too_small_fails_request_only():

@@ -116,3 +116,20 @@ def test_toeplitz_needs_b0_free_plan():
                refine_residual=L.RESIDUAL_DOUBLE_FLOAT).build()
     with pytest.raises(L.PinvError, match="UNSUPPORTED"):
         pl.export(L.EXPORT_GRAM_EXACT)
+
+
+def test_lean_plan_same_images_less_memory():
+    """A lean plan drops G / L and the FP64 W after its build: same images bit
+    for bit, N^2 x 32 bytes less device memory, no L / W exports."""
+    p = synth.config(2, reduced=True)
+    d = torch.from_numpy(p.data).cuda()
+    full = _plan(p.dims, p.traj, p.coil_maps, lam=p.lambda_rel, refine_max_iters=3).build()
+    lean = _plan(p.dims, p.traj, p.coil_maps, lam=p.lambda_rel, refine_max_iters=3, lean=True).build()
+    assert torch.equal(full.apply(d), lean.apply(d))
+    N = p.n_vox
+    assert full.info()["bytes_device"] - lean.info()["bytes_device"] == 32 * N * N
+    for what in (L.EXPORT_CHOL, L.EXPORT_LINV, L.EXPORT_GINV):
+        with pytest.raises(L.PinvError, match="UNSUPPORTED"):
+            lean.export(what)
+    lean.build()  # rebuild allocates the temporaries again
+    assert torch.equal(full.apply(d), lean.apply(d))
