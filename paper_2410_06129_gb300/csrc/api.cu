@@ -212,14 +212,23 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
         ijk[3 * n + 2] = (int)(g / ((int64_t)p->dims[0] * p->dims[1]));
     }
     // lambda: trace(E^H E) / N = M_k * mean_n sum_c |s_c(n)|^2 since |A| = 1
-    double sos = (double)p->N;
+    double sos = (double)p->N, smax = 1.0;
     if (d->coil_maps) {
         sos = 0.0;
+        smax = 0.0;
         for (int64_t i = 0; i < 2 * p->N * p->C; ++i) {
             double v = d->coil_maps[i];
             if (!std::isfinite(v)) return cleanup(fail(PINV_ERR_INVALID_ARG, "non-finite coil map"));
             sos += v * v;
         }
+        for (int64_t i = 0; i < p->N * p->C; ++i)
+            smax = std::max(smax, std::hypot(d->coil_maps[2 * i], d->coil_maps[2 * i + 1]));
+    }
+    // |E| = |s_c(n)| (|A| = 1): the exponent bounding every component of E
+    {
+        int ex = 0;
+        const double mant = smax > 0.0 ? std::frexp(smax * (1.0 + 1e-12), &ex) : 0.0;
+        p->eexp = smax > 0.0 ? (mant == 0.5 ? ex - 1 : ex) : 0;
     }
     p->lambda_abs = d->lambda_mode == PINV_LAMBDA_ABS ? d->lambda
                                                       : d->lambda * (double)p->Mk * sos / (double)p->N;

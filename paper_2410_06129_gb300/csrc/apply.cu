@@ -81,8 +81,13 @@ size_t apply_scratch_layout(const pinv_plan* p, int64_t F, int dtype, void* base
     s.x64 = need_x64 ? cv.take<float2>((size_t)(F * N)) : nullptr;
     s.norms = md.stop_rule ? cv.take<double>((size_t)(2 * F)) : nullptr;
     if (md.dfres || md.toep || md.need_b) {
-        // E^H u (rows N, length M), E x (rows M, length N), G x (rows N, length N)
-        const size_t w = std::max(df_work_elems(N, F, M), std::max(df_work_elems(M, F, N), df_work_elems(N, F, N)));
+        // E^H u (rows N, length M), E x (rows M, length N), G x (rows N, length N),
+        // and the exact tensor-core E^H d
+        size_t w = std::max(df_work_elems(N, F, M), std::max(df_work_elems(M, F, N), df_work_elems(N, F, N)));
+        if (md.need_b && exact_adjoint_ok(p->enc, F)) {
+            w = std::max(w, exact_work_elems(N, F, M));
+            s.fexp = cv.take<int>((size_t)F);
+        }
         s.dfw = w ? cv.take<float4>(w) : nullptr;
     }
     if (sc) *sc = s;
@@ -116,7 +121,10 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
     }
     double2* X = dtype == PINV_C128 ? (double2*)d_image : sc.x128;
 
-    if (md.need_b) CKA(launch_adjoint_df(p->enc, D, F, 0.0, nullptr, sc.b128, s, sc.dfw));  // b = E^H d
+    if (md.need_b) {  // b = E^H d, exactly on the tensor cores where possible
+        if (sc.fexp) CKA(launch_adjoint_exact(p->enc, p->eexp, D, F, sc.fexp, sc.b128, sc.dfw, p->st, s));
+        else CKA(launch_adjoint_df(p->enc, D, F, 0.0, nullptr, sc.b128, s, sc.dfw));
+    }
     if (!md.mixed) {
         if (p->recon) {
             CKA(launch_apply64((const double2*)p->R, N, M, D, F, X, s));

@@ -1,0 +1,88 @@
+// Double-float arithmetic: every value an unevaluated sum of two floats
+// (hi + lo, about 44-48 significant bits) on the FP32 units. Products use the
+// exact FMA product error, sums use TwoSum; accumulators keep a compensated
+// (hi, lo) pair. Complex values are float4 (re.hi, re.lo, im.hi, im.lo).
+#pragma once
+
+#include "pinv_internal.h"
+
+namespace pinv {
+
+// ------------------------------------------------------------------ double-float arithmetic
+__device__ inline float4 to_df(double2 v) {
+    const float rh = (float)v.x, ih = (float)v.y;
+    return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+__device__ inline double2 from_df(float4 a) {
+    return make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
+}
+__device__ inline void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ inline void fast_two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    e = b - (s - a);
+}
+// (xh + xl)(yh + yl) as a normalised pair
+__device__ inline void df_mul(float xh, float xl, float yh, float yl, float& rh, float& rl) {
+    const float p = xh * yh;
+    float e = fmaf(xh, yh, -p);
+    e = fmaf(xh, yl, e);
+    e = fmaf(xl, yh, e);
+    fast_two_sum(p, e, rh, rl);
+}
+__device__ inline void df_add(float ah, float al, float bh, float bl, float& rh, float& rl) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e += al + bl;
+    fast_two_sum(s, e, rh, rl);
+}
+// complex double-float product, layout (re.hi, re.lo, im.hi, im.lo)
+__device__ inline float4 cdf_mul(float4 a, float4 b) {
+    float p1h, p1l, p2h, p2l, p3h, p3l, p4h, p4l, rh, rl, ih, il;
+    df_mul(a.x, a.y, b.x, b.y, p1h, p1l);
+    df_mul(a.z, a.w, b.z, b.w, p2h, p2l);
+    df_mul(a.x, a.y, b.z, b.w, p3h, p3l);
+    df_mul(a.z, a.w, b.x, b.y, p4h, p4l);
+    df_add(p1h, p1l, -p2h, -p2l, rh, rl);
+    df_add(p3h, p3l, p4h, p4l, ih, il);
+    return make_float4(rh, rl, ih, il);
+}
+__device__ inline float4 cdf_conj(float4 a) { return make_float4(a.x, a.y, -a.z, -a.w); }
+// H + L += x * y (x, y double-float reals)
+__device__ inline void acc_prod(float& H, float& L, float xh, float xl, float yh, float yl) {
+    const float p = xh * yh;
+    float e = fmaf(xh, yh, -p);
+    e = fmaf(xh, yl, e);
+    e = fmaf(xl, yh, e);
+    float s, t;
+    two_sum(H, p, s, t);
+    H = s;
+    L += t + e;
+}
+// complex accumulate acc += a * b, acc = (re.H, re.L, im.H, im.L)
+__device__ inline void cacc(float4& acc, float4 a, float4 b) {
+    acc_prod(acc.x, acc.y, a.x, a.y, b.x, b.y);
+    acc_prod(acc.x, acc.y, -a.z, -a.w, b.z, b.w);
+    acc_prod(acc.z, acc.w, a.x, a.y, b.z, b.w);
+    acc_prod(acc.z, acc.w, a.z, a.w, b.x, b.y);
+}
+
+// encoding element A[m][n] and E[(c,m)][n] from the double-float tables
+__device__ inline float4 gen_a_df(const EncodeDev& e, int64_t m, int64_t n) {
+    const int* g = e.vox_ijk + 3 * n;
+    float4 v = e.exdf[m * e.nx + g[0]];
+    if (e.ny > 1) v = cdf_mul(v, e.eydf[m * e.ny + g[1]]);
+    if (e.nz > 1) v = cdf_mul(v, e.ezdf[m * e.nz + g[2]]);
+    if (e.b0df) v = cdf_mul(v, e.b0df[(int64_t)e.tidx[m] * e.N + n]);
+    return v;
+}
+__device__ inline float4 gen_e_df(const EncodeDev& e, int c, int64_t m, int64_t n) {
+    float4 v = gen_a_df(e, m, n);
+    if (e.coilsdf) v = cdf_mul(v, e.coilsdf[(int64_t)c * e.N + n]);
+    return v;
+}
+
+}  // namespace pinv

@@ -229,6 +229,13 @@ void tc_multi_free(TcMulti* m);
 // df_work_elems() partials (float4) when the split count is above one
 size_t df_work_elems(int64_t rows, int64_t F, int64_t K);
 
+// E^H d exactly on the tensor cores (fixed-point digits; B0-free plans, F >= 16).
+// |E| <= 2^eexp; fexp: [F] per-frame exponents (written here); work: partials.
+bool exact_adjoint_ok(const EncodeDev& e, int64_t F);
+size_t exact_work_elems(int64_t N, int64_t F, int64_t M);
+cudaError_t launch_adjoint_exact(const EncodeDev& e, int eexp, const double2* D, int64_t F, int* fexp,
+                                 double2* B, float4* work, DevStatus* st, cudaStream_t s);
+
 // exact Gram of B0-free grid plans (Toeplitz table, FP64; stored double-float)
 size_t toeplitz_work_bytes(const EncodeDev& e);
 cudaError_t launch_toeplitz64(const EncodeDev& e, double2* work, double2* T, cudaStream_t s);

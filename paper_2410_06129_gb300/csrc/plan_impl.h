@@ -24,6 +24,7 @@ struct ApplyScratch {
     float2* x64;    // c64 image / FP32 correction temporary [F][N]
     double* norms;  // per-frame squared norms [2F]
     float4* dfw;    // partial sums of the split double-float products
+    int* fexp;      // per-frame exponents of the data [F] (exact tensor-core E^H d)
 };
 // Bytes an apply of F frames of `dtype` needs; with base != nullptr also
 // carves the region at base into *sc.
@@ -56,6 +57,7 @@ struct pinv_plan {
     int64_t N = 0, Mk = 0, M = 0;
     int C = 1;
     double lambda_abs = 0;
+    int eexp = 0;  // every component of E is at most 2^eexp in magnitude
     int precision = PINV_FP64;
     int recon = 1;
     int refine_iters = 0;

@@ -1,0 +1,398 @@
+// E^H d formed exactly on the tensor cores (fixed-point digit splitting).
+//
+// b[f][n] = sum_j conj(E[j][n]) d[f][j] must be accurate to about 1e-10
+// relative for the refinement (its fixed point solves G x = b; errors in b
+// grow by kappa(G)). The double-float SIMT kernel reaches that at 48 FP32
+// instructions per complex MAC; this kernel reaches it with bf16 MMAs whose
+// every product and partial sum is an exact integer:
+//
+//  * Each real operand value x, scaled by a power of two so |x| <= 1 (E by the
+//    largest coil-map component, data by the largest component of its frame),
+//    is written as x = sum_i x_i 2^(-6-7i), i = 0..5, with integer digits
+//    |x_i| <= 64 (exact in bf16); the remainder is below 2^-42.
+//  * Digit products x_i y_j are integers of at most 12 bits, exact in the FP32
+//    accumulator, and so is every partial sum below 2^24. Pairs with the same
+//    weight class w = i + j accumulate in one TMEM region (six regions of 64
+//    columns); the 21 pairs with w <= 5 are kept (dropped pairs weigh below
+//    2^-42 relative).
+//  * Every DRAIN stages (each class sum then stays below 2^24) the producer
+//    warps read the six regions, scale class w by 2^(-12-7w) (exact) and add
+//    it into double-float accumulators held in registers.
+//
+// Tiles are 128 voxels x 32 frames (MMA M = 128, N = 64: real and imaginary
+// output columns side by side, as in the split-BF16 engine); the sample range
+// is split over CTAs and the double-float partials reduced in a fixed order.
+// Plans without B0 only (E from the separable phase tables and coil maps).
+#include <algorithm>
+
+#include "df.cuh"
+#include "tc_engine.cuh"
+
+namespace pinv {
+namespace tcx {
+
+using namespace tc;
+
+constexpr int XM = 128;        // voxels per tile
+constexpr int XN = 32;         // frames per tile (MMA N = 64)
+constexpr int XKC = 16;        // complex samples per stage
+constexpr int NDIG = 6;        // digits per real value
+constexpr int NCLS = 6;        // weight classes kept (i + j <= 5)
+constexpr int XDRAIN = 16;     // stages per exact accumulation group
+constexpr int XSTAGES = 3;
+constexpr int XA_SL = XM * 64;         // one digit slice of A: 128 rows x 32 bf16 = 8 KiB
+constexpr int XB_SL = 2 * XN * 64;     // one digit slice of B: 64 stacked rows x 32 bf16 = 4 KiB
+constexpr int XSTAGE = NDIG * (XA_SL + XB_SL);  // 72 KiB
+constexpr int XSMEM = XSTAGES * XSTAGE + 1024;
+constexpr uint32_t XIDESC =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * XN) >> 3) << 17) | ((uint32_t)(XM >> 4) << 24);
+// Per class and group: at most 6 pairs x 32 products x XDRAIN stages, each below 2^12.
+static_assert(NCLS * 32 * XDRAIN * 4096 < (1 << 24), "exact class sums");
+
+__device__ inline float rint_f(float x) { return rintf(x); }
+
+// Digits of 8 double-float values (h, l) times `scale` (a power of two),
+// written slice by slice: w[t] packs values 2t, 2t+1 of digit `dig` as bf16.
+struct Digits8 {
+    float rh[8], rl[8];
+    __device__ void init(const float (&h)[8], const float (&l)[8], float scale) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            rh[t] = h[t] * (scale * 64.f);
+            rl[t] = l[t] * (scale * 64.f);
+        }
+    }
+    // next digit of every value, packed in 4 words; the remainder moves up by 2^7
+    __device__ void next(uint32_t (&w)[4], uint32_t flip) {
+        float d[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            d[t] = rint_f(rh[t]);
+            const float r = rh[t] - d[t];  // exact: d is the nearest integer
+            float s, e;
+            two_sum(r, rl[t], s, e);
+            rh[t] = s * 128.f;
+            rl[t] = e * 128.f;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            __nv_bfloat162 v = __floats2bfloat162_rn(d[2 * t], d[2 * t + 1]);  // exact: |d| <= 64
+            w[t] = *reinterpret_cast<uint32_t*>(&v) ^ flip;
+        }
+    }
+};
+
+struct XArgs {
+    EncodeDev e;
+    const double2* D;   // data [F][M], FP64 view
+    const int* fexp;    // per-frame exponent: |d_f| <= 2^fexp
+    int eexp;           // |E| <= 2^eexp
+    int64_t F, M;
+    int64_t chunk;      // samples per split (multiple of XKC)
+    float4* part;       // [splits][F][N] double-float partials, or null (one split)
+    double2* B;         // output [F][N] when part is null
+};
+
+// conj(E[j][n]) for 8 consecutive samples j of voxel n, double-float (re, im split)
+__device__ inline void gen_eh8(const EncodeDev& e, int64_t n, int64_t j0, int64_t je, float (&reh)[8],
+                               float (&rel)[8], float (&imh)[8], float (&iml)[8]) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int64_t j = j0 + t;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n < e.N && j < je) {
+            const int c = (int)(j / e.Mk);
+            v = cdf_conj(gen_e_df(e, c, j - (int64_t)c * e.Mk, n));
+        }
+        reh[t] = v.x;
+        rel[t] = v.y;
+        imh[t] = v.z;
+        iml[t] = v.w;
+    }
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) k_adjoint_exact(XArgs a, DevStatus* st) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full_bar[XSTAGES], empty_bar[XSTAGES];
+    __shared__ uint64_t tfull, tempty, done_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_flag;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t N = a.e.N;
+    const int64_t n0 = (int64_t)blockIdx.y * XM, f0 = (int64_t)blockIdx.x * XN;
+    const int64_t kb = (int64_t)blockIdx.z * a.chunk;
+    const int64_t ke = kb + a.chunk < a.M ? kb + a.chunk : a.M;
+    const int nk = ke > kb ? (int)((ke - kb + XKC - 1) / XKC) : 0;
+    const int ngroups = (nk + XDRAIN - 1) / XDRAIN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < XSTAGES; ++s) {
+            mbar_init(&full_bar[s], NPW * 32);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&tfull, 1);
+        mbar_init(&tempty, NPW * 32);
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == NPW) tmem_alloc(&tmem_base_sh, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp < NPW) {
+        // ---------------- producers, drains, epilogue
+        const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter, half of the 32 frames
+        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+        float acc[4][16];  // re.hi, re.lo, im.hi, im.lo for this thread's 16 frames
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc[0][u] = acc[1][u] = acc[2][u] = acc[3][u] = 0.f;
+        bool ok = true;
+        int drained = 0;
+        auto drain = [&](int g) -> bool {
+            if (!mbar_wait(&tfull, (uint32_t)g & 1u, &abort_flag)) return false;
+            tc_fence_after();
+#pragma unroll 1
+            for (int w = 0; w < NCLS; ++w) {
+                uint32_t vr[16], vi[16];
+                tmem_ld16(trow + (uint32_t)(64 * w + 16 * h), vr);
+                tmem_ld16(trow + (uint32_t)(64 * w + XN + 16 * h), vi);
+                tmem_wait_ld();
+                const float sc = __int_as_float((127 - 12 - 7 * w) << 23);  // 2^(-12-7w)
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    float s, e;
+                    two_sum(acc[0][u], __uint_as_float(vr[u]) * sc, s, e);
+                    acc[0][u] = s;
+                    acc[1][u] += e;
+                    two_sum(acc[2][u], __uint_as_float(vi[u]) * sc, s, e);
+                    acc[2][u] = s;
+                    acc[3][u] += e;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty);
+            return true;
+        };
+        const float escale = __int_as_float((127 - a.eexp) << 23);
+        // A unit: voxel row ua & 127, 8 samples of k-group ua >> 7
+        const int ua = threadIdx.x, ra = ua & (XM - 1), ga = ua >> 7;
+        const int64_t nrow = n0 + ra;
+        // B unit (threads 0..63): frame column ub & 31, k-group ub >> 5
+        const int ub = threadIdx.x, cb = ub & (XN - 1), gb = ub >> 5;
+        const int64_t fcol = f0 + cb;
+        const bool bunit = ub < 2 * XN;
+        const float dscale = (bunit && fcol < a.F) ? __int_as_float((127 - a.fexp[fcol]) << 23) : 1.f;
+        for (int kt = 0; kt < nk && ok; ++kt) {
+            while (drained < ngroups && (drained + 1) * XDRAIN + XSTAGES - 1 <= kt) {
+                if (!(ok = drain(drained))) break;
+                ++drained;
+            }
+            if (!ok) break;
+            const int s = kt % XSTAGES;
+            const uint32_t ph = (uint32_t)(kt / XSTAGES) & 1u;
+            if (kt >= XSTAGES && !(ok = mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag))) break;
+            uint8_t* base = smem + s * XSTAGE;
+            const int64_t k0 = kb + (int64_t)kt * XKC;
+            {
+                float reh[8], rel[8], imh[8], iml[8];
+                gen_eh8(a.e, nrow, k0 + 8 * ga, ke, reh, rel, imh, iml);
+                Digits8 dr, di;
+                dr.init(reh, rel, escale);
+                di.init(imh, iml, escale);
+#pragma unroll
+                for (int dg = 0; dg < NDIG; ++dg) {
+                    uint32_t w[4];
+                    dr.next(w, 0u);
+                    *reinterpret_cast<uint4*>(base + dg * XA_SL + koff(ra, ga)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    di.next(w, 0u);
+                    *reinterpret_cast<uint4*>(base + dg * XA_SL + koff(ra, ga + 2)) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            if (bunit) {
+                float reh[8], rel[8], imh[8], iml[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int64_t j = k0 + 8 * gb + t;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (fcol < a.F && j < ke) v = to_df(a.D[fcol * a.M + j]);
+                    reh[t] = v.x;
+                    rel[t] = v.y;
+                    imh[t] = v.z;
+                    iml[t] = v.w;
+                }
+                Digits8 dr, di;
+                dr.init(reh, rel, dscale);
+                di.init(imh, iml, dscale);
+                uint8_t* bb = base + NDIG * XA_SL;
+#pragma unroll
+                for (int dg = 0; dg < NDIG; ++dg) {
+                    uint32_t wr[4], wi[4];
+                    dr.next(wr, 0u);
+                    di.next(wi, 0u);
+                    uint8_t* sl = bb + dg * XB_SL;
+                    *reinterpret_cast<uint4*>(sl + koff(cb, gb)) = make_uint4(wr[0], wr[1], wr[2], wr[3]);  // [Br|-Bi]
+                    *reinterpret_cast<uint4*>(sl + koff(cb, gb + 2)) =
+                        make_uint4(wi[0] ^ 0x80008000u, wi[1] ^ 0x80008000u, wi[2] ^ 0x80008000u, wi[3] ^ 0x80008000u);
+                    *reinterpret_cast<uint4*>(sl + koff(XN + cb, gb)) = make_uint4(wi[0], wi[1], wi[2], wi[3]);  // [Bi|Br]
+                    *reinterpret_cast<uint4*>(sl + koff(XN + cb, gb + 2)) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+                }
+            }
+            fence_proxy_async();
+            mbar_arrive(&full_bar[s]);
+        }
+        while (ok && drained < ngroups) {
+            ok = drain(drained);
+            ++drained;
+        }
+        if (ok && !abort_flag) {
+            // this thread: voxel n0 + q*32 + lane, frames f0 + 16h .. +15
+            const int64_t n = n0 + q * 32 + lane;
+            if (n < N) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int64_t f = f0 + 16 * h + u;
+                    if (f >= a.F) continue;
+                    const float sc = __int_as_float((127 + a.eexp + a.fexp[f]) << 23);
+                    float4 v = make_float4(acc[0][u] * sc, acc[1][u] * sc, acc[2][u] * sc, acc[3][u] * sc);
+                    if (a.part)
+                        a.part[((int64_t)blockIdx.z * a.F + f) * N + n] = v;
+                    else
+                        a.B[f * N + n] = from_df(v);
+                }
+            }
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issuer: 21 digit pairs per stage, class w = i + j into region w
+        for (int kt = 0; kt < nk; ++kt) {
+            const int g = kt / XDRAIN;
+            const bool first = (kt % XDRAIN) == 0;
+            if (first && g >= 1 && !mbar_wait(&tempty, (uint32_t)(g - 1) & 1u, &abort_flag)) break;
+            const int s = kt % XSTAGES;
+            const uint32_t ph = (uint32_t)(kt / XSTAGES) & 1u;
+            if (!mbar_wait(&full_bar[s], ph, &abort_flag)) break;
+            tc_fence_after();
+            const uint32_t abase = smem_u32(smem + s * XSTAGE);
+            const uint32_t bbase = abase + NDIG * XA_SL;
+#pragma unroll
+            for (int w = 0; w < NCLS; ++w) {
+#pragma unroll
+                for (int i = 0; i <= w; ++i) {
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint64_t da = sdesc(abase + i * XA_SL + kk * 256, 128, 512);
+                        const uint64_t db = sdesc(bbase + (w - i) * XB_SL + kk * 256, 128, 512);
+                        mma_bf16(tmem + (uint32_t)(64 * w), da, db, XIDESC, (first && i == 0 && kk == 0) ? 0u : 1u);
+                    }
+                }
+            }
+            mma_commit(&empty_bar[s]);
+            if ((kt % XDRAIN) == XDRAIN - 1 || kt == nk - 1) mma_commit(&tfull);
+        }
+        mma_commit(&done_bar);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == NPW) {
+        mbar_wait(&done_bar, 0, nullptr);
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+    if (threadIdx.x == 0 && abort_flag) atomicMax(&st->timeout_site, 20);
+}
+
+// store functor for the ordered reduction of the partials
+struct BStore {
+    double2* B;
+    int64_t N;
+    __device__ void store(int64_t i, int64_t j, double2 v) const { B[j * N + i] = v; }
+};
+
+__global__ void k_exact_reduce(BStore o, const float4* part, int splits, int64_t rows, int64_t F) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * F) return;
+    const int64_t i = idx % rows, j = idx / rows;
+    float4 a = part[j * rows + i];
+    for (int z = 1; z < splits; ++z) {
+        const float4 b = part[((int64_t)z * F + j) * rows + i];
+        float rh, rl, ih, il;
+        df_add(a.x, a.y, b.x, b.y, rh, rl);
+        df_add(a.z, a.w, b.z, b.w, ih, il);
+        a = make_float4(rh, rl, ih, il);
+    }
+    o.store(i, j, from_df(a));
+}
+
+// per-frame exponent: |re|, |im| of frame f all <= 2^fexp[f]
+__global__ void k_frame_exp(const double2* D, int64_t M, int* fexp) {
+    __shared__ double red[256];
+    const int64_t f = blockIdx.x;
+    double m = 0.0;
+    for (int64_t j = threadIdx.x; j < M; j += blockDim.x) {
+        const double2 v = D[f * M + j];
+        m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int ex = 0;
+        const double mant = m > 0.0 ? frexp(red[0], &ex) : 0.0;
+        if (mant == 0.5) --ex;  // exact powers of two need no extra bit
+        fexp[f] = m > 0.0 ? ex : 0;
+    }
+}
+
+}  // namespace tcx
+
+int exact_splits(int64_t N, int64_t F, int64_t M) {
+    const int64_t tiles = ((N + tcx::XM - 1) / tcx::XM) * ((F + tcx::XN - 1) / tcx::XN);
+    int64_t sp = (2 * 152 + tiles - 1) / tiles;
+    sp = std::min<int64_t>(sp, std::max<int64_t>(1, M / (tcx::XKC * tcx::XDRAIN * 2)));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 32));
+}
+
+size_t exact_work_elems(int64_t N, int64_t F, int64_t M) {
+    const int sp = exact_splits(N, F, M);
+    return sp > 1 ? (size_t)sp * (size_t)N * (size_t)F : 0;
+}
+
+bool exact_adjoint_ok(const EncodeDev& e, int64_t F) { return !e.b0df && !e.b0tab && F >= 16 && tc_available(); }
+
+cudaError_t launch_adjoint_exact(const EncodeDev& e, int eexp, const double2* D, int64_t F, int* fexp,
+                                 double2* B, float4* work, DevStatus* st, cudaStream_t s) {
+    if (F == 0) return cudaSuccess;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t err = cudaFuncSetAttribute(tcx::k_adjoint_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               tcx::XSMEM);
+        if (err != cudaSuccess) return err;
+        attr = true;
+    }
+    const int64_t M = e.Mk * e.C;
+    tcx::k_frame_exp<<<(unsigned)F, 256, 0, s>>>(D, M, fexp);
+    note_launch();
+    const int sp = exact_splits(e.N, F, M);
+    if (sp > 1 && !work) return cudaErrorInvalidValue;
+    const int64_t chunk = ((M + sp - 1) / sp + tcx::XKC - 1) / tcx::XKC * tcx::XKC;
+    tcx::XArgs a{e, D, fexp, eexp, F, M, chunk, sp > 1 ? work : nullptr, B};
+    dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN), (unsigned)((e.N + tcx::XM - 1) / tcx::XM), (unsigned)sp);
+    tcx::k_adjoint_exact<<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
+    note_launch();
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess || sp == 1) return err;
+    const int64_t n = e.N * F;
+    tcx::k_exact_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tcx::BStore{B, e.N}, work, sp, e.N, F);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace pinv

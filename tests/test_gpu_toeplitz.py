@@ -133,3 +133,19 @@ def test_lean_plan_same_images_less_memory():
             lean.export(what)
     lean.build()  # rebuild allocates the temporaries again
     assert torch.equal(full.apply(d), lean.apply(d))
+
+
+@pytest.mark.parametrize("side,frames,samples", [(20, 40, 1200), (24, 16, 1152)])
+def test_exact_tensor_core_adjoint_many_frames(side, frames, samples):
+    """With 16 or more frames E^H d runs exactly on the tensor cores
+    (fixed-point digits): ragged voxels (N = 400), frames (40 = 32 + 8) and
+    samples. Images meet the mixed bar against the oracle and agree with the
+    same frames applied a few at a time (double-float E^H d)."""
+    p = synth.make_plan(side, 4, "spiral", frames, 2601 + side, 1e-4, samples=samples, interleaves=2)
+    ref = oracle_all(p)
+    pl = _plan(p.dims, p.traj, p.coil_maps, lam=p.lambda_rel, refine_max_iters=3).build()
+    d = torch.from_numpy(p.data).cuda()
+    x = pl.apply(d).cpu().numpy()
+    assert rel(x, ref.images) <= 1e-5
+    x_small = np.concatenate([pl.apply(d[i:i + 8]).cpu().numpy() for i in range(0, frames, 8)])
+    assert rel(x, x_small) <= 1e-5
