@@ -354,6 +354,19 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
         e.exdf = xdf;
         e.eydf = ydf;
         e.ezdf = zdf;
+        if (!d->b0_hz && e.Mkp > 0) {
+            // sample-contiguous copies for the exact tensor-core E^H d
+            float4 *xt, *yt, *zt;
+            AL(xt, sizeof(float4) * e.Mkp * e.nx, "extdf");
+            AL(yt, sizeof(float4) * e.Mkp * e.ny, "eytdf");
+            AL(zt, sizeof(float4) * e.Mkp * e.nz, "eztdf");
+            CKC(launch_transpose_df(xdf, p->Mk, e.nx, xt, e.Mkp, s));
+            CKC(launch_transpose_df(ydf, p->Mk, e.ny, yt, e.Mkp, s));
+            CKC(launch_transpose_df(zdf, p->Mk, e.nz, zt, e.Mkp, s));
+            e.extdf = xt;
+            e.eytdf = yt;
+            e.eztdf = zt;
+        }
         if (e.b0tab) {
             const int64_t nt = (int64_t)tuniq.size() * p->N;
             float4* bdf;

@@ -85,7 +85,7 @@ size_t apply_scratch_layout(const pinv_plan* p, int64_t F, int dtype, void* base
         // and the exact tensor-core E^H d
         size_t w = std::max(df_work_elems(N, F, M), std::max(df_work_elems(M, F, N), df_work_elems(N, F, N)));
         if (md.need_b && exact_adjoint_ok(p->enc, F)) {
-            w = std::max(w, exact_work_elems(N, F, M));
+            w = std::max(w, exact_work_elems(p->enc, F));
             s.fexp = cv.take<int>((size_t)F);
         }
         s.dfw = w ? cv.take<float4>(w) : nullptr;
@@ -122,7 +122,7 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
     double2* X = dtype == PINV_C128 ? (double2*)d_image : sc.x128;
 
     if (md.need_b) {  // b = E^H d, exactly on the tensor cores where possible
-        if (sc.fexp) CKA(launch_adjoint_exact(p->enc, p->eexp, D, F, sc.fexp, sc.b128, sc.dfw, p->st, s));
+        if (sc.fexp) CKA(launch_adjoint_exact(p->enc, D, F, sc.fexp, sc.b128, sc.dfw, p->st, s));
         else CKA(launch_adjoint_df(p->enc, D, F, 0.0, nullptr, sc.b128, s, sc.dfw));
     }
     if (!md.mixed) {

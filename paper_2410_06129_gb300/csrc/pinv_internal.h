@@ -50,6 +50,11 @@ struct EncodeDev {
     int T;
     int full_grid;          // voxels are the whole grid in flat order (no voxel list)
     // double-float copies (re.hi, re.lo, im.hi, im.lo) for the refinement residual
+    // sample-contiguous double-float tables extdf[ix][m] (rows of Mkp, zero
+    // padded), for the exact tensor-core E^H d of plans without B0
+    const float4* extdf;
+    const float4* eytdf;
+    const float4* eztdf;
     const float4* exdf;
     const float4* eydf;
     const float4* ezdf;
@@ -230,11 +235,13 @@ void tc_multi_free(TcMulti* m);
 size_t df_work_elems(int64_t rows, int64_t F, int64_t K);
 
 // E^H d exactly on the tensor cores (fixed-point digits; B0-free plans, F >= 16).
-// |E| <= 2^eexp; fexp: [F] per-frame exponents (written here); work: partials.
+// fexp: [F] per-frame exponents (written here); work: partials.
 bool exact_adjoint_ok(const EncodeDev& e, int64_t F);
-size_t exact_work_elems(int64_t N, int64_t F, int64_t M);
-cudaError_t launch_adjoint_exact(const EncodeDev& e, int eexp, const double2* D, int64_t F, int* fexp,
-                                 double2* B, float4* work, DevStatus* st, cudaStream_t s);
+size_t exact_work_elems(const EncodeDev& e, int64_t F);
+cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F, int* fexp, double2* B,
+                                 float4* work, DevStatus* st, cudaStream_t s);
+cudaError_t launch_transpose_df(const float4* src, int64_t rows, int64_t cols, float4* dst, int64_t ldd,
+                                cudaStream_t s);
 
 // exact Gram of B0-free grid plans (Toeplitz table, FP64; stored double-float)
 size_t toeplitz_work_bytes(const EncodeDev& e);

@@ -225,4 +225,22 @@ cudaError_t launch_reset_status(DevStatus* st, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// dst[c][r] = src[r][c] for double-float tables, rows padded with zeros to ldd
+__global__ void k_transpose_df(const float4* __restrict__ src, int64_t rows, int64_t cols, float4* __restrict__ dst,
+                               int64_t ldd) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= cols * ldd) return;
+    const int64_t c = idx / ldd, r = idx % ldd;
+    dst[idx] = r < rows ? src[r * cols + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+cudaError_t launch_transpose_df(const float4* src, int64_t rows, int64_t cols, float4* dst, int64_t ldd,
+                                cudaStream_t s) {
+    const int64_t n = cols * ldd;
+    if (n == 0) return cudaSuccess;
+    k_transpose_df<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, rows, cols, dst, ldd);
+    note_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace pinv

@@ -6,10 +6,14 @@
 // instructions per complex MAC; this kernel reaches it with bf16 MMAs whose
 // every product and partial sum is an exact integer:
 //
-//  * Each real operand value x, scaled by a power of two so |x| <= 1 (E by the
-//    largest coil-map component, data by the largest component of its frame),
-//    is written as x = sum_i x_i 2^(-6-7i), i = 0..5, with integer digits
-//    |x_i| <= 64 (exact in bf16); the remainder is below 2^-42.
+//  * The coil factor is taken out: the sample range is split at coil
+//    boundaries, each CTA forms sum_m conj(A[m][n]) d_c[f][m] with the
+//    coil-free |A| = 1, and multiplies its double-float partial by
+//    conj(s_c(n)) before the ordered reduction over all splits.
+//  * Each real operand value x, scaled by a power of two so |x| <= 1 (A needs
+//    none; data by the largest component of its frame), is written as
+//    x = sum_i x_i 2^(-6-7i), i = 0..5, with integer digits |x_i| <= 64
+//    (exact in bf16); the remainder is below 2^-42.
 //  * Digit products x_i y_j are integers of at most 12 bits, exact in the FP32
 //    accumulator, and so is every partial sum below 2^24. Pairs with the same
 //    weight class w = i + j accumulate in one TMEM region (six regions of 64
@@ -62,15 +66,16 @@ struct Digits8 {
             rl[t] = l[t] * (scale * 64.f);
         }
     }
-    // next digit of every value, packed in 4 words; the remainder moves up by 2^7
+    // next digit of every value, packed in 4 words; the remainder moves up by 2^7.
+    // (rh, rl) stays a normalised pair, so r = rh - d is either 0 or at least
+    // ulp(rh) > |rl| and the fast two-sum is exact.
     __device__ void next(uint32_t (&w)[4], uint32_t flip) {
         float d[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             d[t] = rint_f(rh[t]);
-            const float r = rh[t] - d[t];  // exact: d is the nearest integer
             float s, e;
-            two_sum(r, rl[t], s, e);
+            fast_two_sum(rh[t] - d[t], rl[t], s, e);  // rh - d is exact
             rh[t] = s * 128.f;
             rl[t] = e * 128.f;
         }
@@ -86,28 +91,43 @@ struct XArgs {
     EncodeDev e;
     const double2* D;   // data [F][M], FP64 view
     const int* fexp;    // per-frame exponent: |d_f| <= 2^fexp
-    int eexp;           // |E| <= 2^eexp
     int64_t F, M;
-    int64_t chunk;      // samples per split (multiple of XKC)
-    float4* part;       // [splits][F][N] double-float partials, or null (one split)
+    int64_t chunk;      // samples per split (multiple of XKC); splits never cross a coil
+    int sub;            // splits per coil
+    float4* part;       // [C * sub][F][N] double-float partials, or null (one split, no coil maps)
     double2* B;         // output [F][N] when part is null
 };
 
-// conj(E[j][n]) for 8 consecutive samples j of voxel n, double-float (re, im split)
-__device__ inline void gen_eh8(const EncodeDev& e, int64_t n, int64_t j0, int64_t je, float (&reh)[8],
+// conj(A[m][n]) for 8 consecutive samples m (< mend) of voxel n, double-float,
+// from the sample-contiguous tables (rows of Mkp, m a multiple of 8)
+__device__ inline void gen_ah8(const EncodeDev& e, int64_t n, int64_t m, int64_t mend, float (&reh)[8],
                                float (&rel)[8], float (&imh)[8], float (&iml)[8]) {
+    float4 v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (n < e.N && m < mend) {  // m is a multiple of 8 below M_k, so m + 7 < Mkp
+        const int* g = e.vox_ijk + 3 * n;
+        const float4* px = e.extdf + (int64_t)g[0] * e.Mkp + m;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = px[t];
+        if (e.ny > 1) {
+            const float4* py = e.eytdf + (int64_t)g[1] * e.Mkp + m;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = cdf_mul(v[t], py[t]);
+        }
+        if (e.nz > 1) {
+            const float4* pz = e.eztdf + (int64_t)g[2] * e.Mkp + m;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = cdf_mul(v[t], pz[t]);
+        }
+    }
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-        const int64_t j = j0 + t;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (n < e.N && j < je) {
-            const int c = (int)(j / e.Mk);
-            v = cdf_conj(gen_e_df(e, c, j - (int64_t)c * e.Mk, n));
-        }
-        reh[t] = v.x;
-        rel[t] = v.y;
-        imh[t] = v.z;
-        iml[t] = v.w;
+        const bool in = n < e.N && m + t < mend;
+        reh[t] = in ? v[t].x : 0.f;
+        rel[t] = in ? v[t].y : 0.f;
+        imh[t] = in ? -v[t].z : 0.f;  // conjugate
+        iml[t] = in ? -v[t].w : 0.f;
     }
 }
 
@@ -121,9 +141,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_adjoint_exact(XArgs a, DevStatu
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t N = a.e.N;
     const int64_t n0 = (int64_t)blockIdx.y * XM, f0 = (int64_t)blockIdx.x * XN;
-    const int64_t kb = (int64_t)blockIdx.z * a.chunk;
-    const int64_t ke = kb + a.chunk < a.M ? kb + a.chunk : a.M;
-    const int nk = ke > kb ? (int)((ke - kb + XKC - 1) / XKC) : 0;
+    const int coil = (int)blockIdx.z / a.sub;
+    const int64_t Mk = a.e.Mk;
+    const int64_t mb = (int64_t)((int)blockIdx.z % a.sub) * a.chunk;   // sample range inside the coil
+    const int64_t me = mb + a.chunk < Mk ? mb + a.chunk : Mk;
+    const int nk = me > mb ? (int)((me - mb + XKC - 1) / XKC) : 0;
     const int ngroups = (nk + XDRAIN - 1) / XDRAIN;
 
     if (threadIdx.x == 0) {
@@ -177,7 +199,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_adjoint_exact(XArgs a, DevStatu
             mbar_arrive(&tempty);
             return true;
         };
-        const float escale = __int_as_float((127 - a.eexp) << 23);
         // A unit: voxel row ua & 127, 8 samples of k-group ua >> 7
         const int ua = threadIdx.x, ra = ua & (XM - 1), ga = ua >> 7;
         const int64_t nrow = n0 + ra;
@@ -196,13 +217,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_adjoint_exact(XArgs a, DevStatu
             const uint32_t ph = (uint32_t)(kt / XSTAGES) & 1u;
             if (kt >= XSTAGES && !(ok = mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag))) break;
             uint8_t* base = smem + s * XSTAGE;
-            const int64_t k0 = kb + (int64_t)kt * XKC;
+            const int64_t m0 = mb + (int64_t)kt * XKC;  // sample index inside the coil
             {
                 float reh[8], rel[8], imh[8], iml[8];
-                gen_eh8(a.e, nrow, k0 + 8 * ga, ke, reh, rel, imh, iml);
+                gen_ah8(a.e, nrow, m0 + 8 * ga, me, reh, rel, imh, iml);
                 Digits8 dr, di;
-                dr.init(reh, rel, escale);
-                di.init(imh, iml, escale);
+                dr.init(reh, rel, 1.f);
+                di.init(imh, iml, 1.f);
 #pragma unroll
                 for (int dg = 0; dg < NDIG; ++dg) {
                     uint32_t w[4];
@@ -217,9 +238,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_adjoint_exact(XArgs a, DevStatu
                 float reh[8], rel[8], imh[8], iml[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
-                    const int64_t j = k0 + 8 * gb + t;
+                    const int64_t m = m0 + 8 * gb + t;
                     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (fcol < a.F && j < ke) v = to_df(a.D[fcol * a.M + j]);
+                    if (fcol < a.F && m < me) v = to_df(a.D[fcol * a.M + (int64_t)coil * Mk + m]);
                     reh[t] = v.x;
                     rel[t] = v.y;
                     imh[t] = v.z;
@@ -253,12 +274,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_adjoint_exact(XArgs a, DevStatu
             // this thread: voxel n0 + q*32 + lane, frames f0 + 16h .. +15
             const int64_t n = n0 + q * 32 + lane;
             if (n < N) {
+                float4 cs = make_float4(1.f, 0.f, 0.f, 0.f);
+                if (a.e.coilsdf) cs = cdf_conj(a.e.coilsdf[(int64_t)coil * N + n]);
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     const int64_t f = f0 + 16 * h + u;
                     if (f >= a.F) continue;
-                    const float sc = __int_as_float((127 + a.eexp + a.fexp[f]) << 23);
+                    const float sc = __int_as_float((127 + a.fexp[f]) << 23);
                     float4 v = make_float4(acc[0][u] * sc, acc[1][u] * sc, acc[2][u] * sc, acc[3][u] * sc);
+                    if (a.e.coilsdf) v = cdf_mul(v, cs);
                     if (a.part)
                         a.part[((int64_t)blockIdx.z * a.F + f) * N + n] = v;
                     else
@@ -353,22 +377,26 @@ __global__ void k_frame_exp(const double2* D, int64_t M, int* fexp) {
 
 }  // namespace tcx
 
-int exact_splits(int64_t N, int64_t F, int64_t M) {
-    const int64_t tiles = ((N + tcx::XM - 1) / tcx::XM) * ((F + tcx::XN - 1) / tcx::XN);
+// splits per coil: about two CTAs per SM over all coils, chunks of at least
+// two accumulation groups
+static int exact_sub(const EncodeDev& e, int64_t F) {
+    const int64_t tiles = ((e.N + tcx::XM - 1) / tcx::XM) * ((F + tcx::XN - 1) / tcx::XN) * e.C;
     int64_t sp = (2 * 152 + tiles - 1) / tiles;
-    sp = std::min<int64_t>(sp, std::max<int64_t>(1, M / (tcx::XKC * tcx::XDRAIN * 2)));
+    sp = std::min<int64_t>(sp, std::max<int64_t>(1, e.Mk / (tcx::XKC * tcx::XDRAIN * 2)));
     return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 32));
 }
 
-size_t exact_work_elems(int64_t N, int64_t F, int64_t M) {
-    const int sp = exact_splits(N, F, M);
-    return sp > 1 ? (size_t)sp * (size_t)N * (size_t)F : 0;
+size_t exact_work_elems(const EncodeDev& e, int64_t F) {
+    const int64_t splits = (int64_t)exact_sub(e, F) * e.C;
+    return splits > 1 || e.coilsdf ? (size_t)splits * (size_t)e.N * (size_t)F : 0;
 }
 
-bool exact_adjoint_ok(const EncodeDev& e, int64_t F) { return !e.b0df && !e.b0tab && F >= 16 && tc_available(); }
+bool exact_adjoint_ok(const EncodeDev& e, int64_t F) {
+    return e.extdf && !e.b0df && !e.b0tab && F >= 16 && tc_available();
+}
 
-cudaError_t launch_adjoint_exact(const EncodeDev& e, int eexp, const double2* D, int64_t F, int* fexp,
-                                 double2* B, float4* work, DevStatus* st, cudaStream_t s) {
+cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F, int* fexp, double2* B,
+                                 float4* work, DevStatus* st, cudaStream_t s) {
     if (F == 0) return cudaSuccess;
     static bool attr = false;
     if (!attr) {
@@ -380,17 +408,19 @@ cudaError_t launch_adjoint_exact(const EncodeDev& e, int eexp, const double2* D,
     const int64_t M = e.Mk * e.C;
     tcx::k_frame_exp<<<(unsigned)F, 256, 0, s>>>(D, M, fexp);
     note_launch();
-    const int sp = exact_splits(e.N, F, M);
-    if (sp > 1 && !work) return cudaErrorInvalidValue;
-    const int64_t chunk = ((M + sp - 1) / sp + tcx::XKC - 1) / tcx::XKC * tcx::XKC;
-    tcx::XArgs a{e, D, fexp, eexp, F, M, chunk, sp > 1 ? work : nullptr, B};
-    dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN), (unsigned)((e.N + tcx::XM - 1) / tcx::XM), (unsigned)sp);
+    const int sub = exact_sub(e, F);
+    const int64_t splits = (int64_t)sub * e.C;
+    const bool partials = splits > 1 || e.coilsdf;
+    if (partials && !work) return cudaErrorInvalidValue;
+    const int64_t chunk = ((e.Mk + sub - 1) / sub + tcx::XKC - 1) / tcx::XKC * tcx::XKC;
+    tcx::XArgs a{e, D, fexp, F, M, chunk, sub, partials ? work : nullptr, B};
+    dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN), (unsigned)((e.N + tcx::XM - 1) / tcx::XM), (unsigned)splits);
     tcx::k_adjoint_exact<<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
     note_launch();
     cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess || sp == 1) return err;
+    if (err != cudaSuccess || !partials) return err;
     const int64_t n = e.N * F;
-    tcx::k_exact_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tcx::BStore{B, e.N}, work, sp, e.N, F);
+    tcx::k_exact_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tcx::BStore{B, e.N}, work, (int)splits, e.N, F);
     note_launch();
     return cudaGetLastError();
 }
