@@ -80,6 +80,10 @@ size_t apply_scratch_layout(const pinv_plan* p, int64_t F, int dtype, void* base
     s.d64 = need_d64 ? cv.take<float2>((size_t)(F * M)) : nullptr;
     s.x64 = need_x64 ? cv.take<float2>((size_t)(F * N)) : nullptr;
     s.norms = md.stop_rule ? cv.take<double>((size_t)(2 * F)) : nullptr;
+    if (md.mixed && p->recon && apply_tc_ok(F)) {
+        s.apw = cv.take<float2>(apply_tc_work_elems(N, M, F));
+        s.sched = cv.take<DevStatus>(1);
+    }
     if (md.dfres || md.toep || md.need_b) {
         // E^H u (rows N, length M), E x (rows M, length N), G x (rows N, length N),
         // and the exact tensor-core E^H d
@@ -139,7 +143,12 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
             CKA(launch_c128_to_c64((const double2*)d_data, sc.d64, F * M, s));
             D32 = sc.d64;
         }
-        CKA(launch_apply32((const float2*)p->R, N, M, D32, F, sc.x64, s));
+        // the refinement removes this product's rounding: split-BF16 on the tensor cores
+        if (sc.apw) {
+            CKA(cudaMemsetAsync(sc.sched, 0, sizeof(DevStatus), s));
+            CKA(launch_apply_tc((const float2*)p->R, N, M, D32, F, sc.x64, sc.apw, p->slices(), sc.sched, s));
+        }
+        else CKA(launch_apply32((const float2*)p->R, N, M, D32, F, sc.x64, s));
         CKA(launch_c64_to_c128(sc.x64, X, F * N, s));
     } else if (md.fpres) {
         // factor-only, FP64 throughout: x = W^H (W (E^H d))

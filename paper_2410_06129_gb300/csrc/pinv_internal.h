@@ -243,6 +243,13 @@ cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F
 cudaError_t launch_transpose_df(const float4* src, int64_t rows, int64_t cols, float4* dst, int64_t ldd,
                                 cudaStream_t s);
 
+// Recon x data (c64) on the tensor cores, split-BF16, for F >= 16 frames (in
+// chunks of 128); the sample range is split over tiles with FP32 partials in `work`.
+bool apply_tc_ok(int64_t F);
+size_t apply_tc_work_elems(int64_t N, int64_t M, int64_t F);
+cudaError_t launch_apply_tc(const float2* R, int64_t N, int64_t M, const float2* D, int64_t F, float2* X,
+                            float2* work, int slices, DevStatus* st, cudaStream_t s);
+
 // exact Gram of B0-free grid plans (Toeplitz table, FP64; stored double-float)
 size_t toeplitz_work_bytes(const EncodeDev& e);
 cudaError_t launch_toeplitz64(const EncodeDev& e, double2* work, double2* T, cudaStream_t s);

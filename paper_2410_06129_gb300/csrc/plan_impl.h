@@ -25,6 +25,9 @@ struct ApplyScratch {
     double* norms;  // per-frame squared norms [2F]
     float4* dfw;    // partial sums of the split double-float products
     int* fexp;      // per-frame exponents of the data [F] (exact tensor-core E^H d)
+    float2* apw;    // partials of the tensor-core Recon x data
+    DevStatus* sched;  // tile counter of that launch: one per scratch region, since
+                       // applies of one plan may run concurrently on several streams
 };
 // Bytes an apply of F frames of `dtype` needs; with base != nullptr also
 // carves the region at base into *sc.

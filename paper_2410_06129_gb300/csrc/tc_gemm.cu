@@ -645,6 +645,42 @@ bool tc_available() {
     return major == 10 && minor == 3;
 }
 
+namespace tc {
+// ------------------------------------------------------------------ Recon x data on the tensor cores
+// X[f][n] = sum_j Recon[n][j] D[f][j] for frames f < F <= BN. The sample range is
+// split over tile columns: column tile bx covers frames 0..BN-1 of split bx
+// (samples [bx * chunk, ...)), whose FP32 partials go to part[bx][f][n].
+struct ApplyTC {
+    const float2* R;   // Recon [N][M], c64
+    const float2* D;   // data [F][M], c64
+    float2* part;      // [splits][F][N]
+    int64_t N, M, F, chunk;
+    __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = by * BM;
+        j0 = bx * BN;
+        kb = bx * chunk;
+        ke = kb + chunk < M ? kb + chunk : M;
+        return true;
+    }
+    __device__ RowPtr row_a(int64_t i) const { return RowPtr{R + (i < N ? i : 0) * M, i < N}; }
+    __device__ RowPtr row_b(int64_t j) const {
+        const int64_t f = j % BN;
+        return RowPtr{D + (f < F ? f : 0) * M, f < F};
+    }
+    __device__ void a8(const RowPtr& r, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(r.p + k, r.ok ? (int)(ke - k) : 0, v);
+    }
+    __device__ void b8(const RowPtr& r, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(r.p + k, r.ok ? (int)(ke - k) : 0, v);
+    }
+    __device__ bool row_ok(int64_t i) const { return i < N; }
+    __device__ bool col_ok(int64_t j) const { return j % BN < F; }
+    __device__ void store(int64_t i, int64_t j, float2 v) const {
+        part[((j / BN) * F + j % BN) * N + i] = v;
+    }
+};
+}  // namespace tc
+
 // ------------------------------------------------------------------ FP32 SIMT apply
 // X[f][n] = sum_j R[n][j] D[f][j] for c64 Recon and data (frames along the tile's columns).
 template <int BMv, int BNv, int TM, int TN, int BKv>
@@ -706,6 +742,50 @@ static cudaError_t apply32_shape(const float2* R, int64_t N, int64_t M, const fl
     k_apply32<BMv, BNv, TM, TN, BKv><<<grid, 256, 0, s>>>(R, N, M, D, F, X);
     note_launch();
     return cudaGetLastError();
+}
+
+__global__ void k_apply_reduce(const float2* __restrict__ part, int splits, int64_t n, float2* __restrict__ X) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float2 a = part[i];
+    for (int z = 1; z < splits; ++z) {
+        const float2 b = part[(int64_t)z * n + i];
+        a.x += b.x;
+        a.y += b.y;
+    }
+    X[i] = a;
+}
+
+// splits of the sample range: about two tiles per SM, chunks of at least 1024 samples
+int apply_tc_splits(int64_t N, int64_t M) {
+    const int64_t rows = (N + tc::BM - 1) / tc::BM;
+    int64_t sp = (2 * 152 + rows - 1) / rows;
+    sp = std::min<int64_t>(sp, std::max<int64_t>(1, M / 1024));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 64));
+}
+
+bool apply_tc_ok(int64_t F) { return F >= 16 && tc_available(); }
+
+size_t apply_tc_work_elems(int64_t N, int64_t M, int64_t F) {
+    return (size_t)apply_tc_splits(N, M) * (size_t)N * (size_t)std::min<int64_t>(F, tc::BN);
+}
+
+// frames in chunks of BN (one column tile per split)
+cudaError_t launch_apply_tc(const float2* R, int64_t N, int64_t M, const float2* D, int64_t F, float2* X,
+                            float2* work, int slices, DevStatus* st, cudaStream_t s) {
+    const int sp = apply_tc_splits(N, M);
+    const int64_t chunk = ((M + sp - 1) / sp + tc::KC - 1) / tc::KC * tc::KC;
+    for (int64_t f0 = 0; f0 < F; f0 += tc::BN) {
+        const int64_t Fc = std::min<int64_t>(tc::BN, F - f0);
+        tc::ApplyTC p{R, D + f0 * M, work, N, M, Fc, chunk};
+        cudaError_t e = run(p, dim3((unsigned)sp, cdiv(N, tc::BM)), slices, st, 9, s);
+        if (e != cudaSuccess) return e;
+        const int64_t n = N * Fc;
+        k_apply_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(work, sp, n, X + f0 * N);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Tile shape per frame-count class, chosen by the autotuner (all candidates

@@ -149,3 +149,22 @@ def test_exact_tensor_core_adjoint_many_frames(side, frames, samples):
     assert rel(x, ref.images) <= 1e-5
     x_small = np.concatenate([pl.apply(d[i:i + 8]).cpu().numpy() for i in range(0, frames, 8)])
     assert rel(x, x_small) <= 1e-5
+
+
+@pytest.mark.parametrize("frames", [24, 150])
+def test_tensor_core_recon_apply_matches_fp32_apply(frames):
+    """Recon x data for 16 or more frames runs split-BF16 on the tensor cores
+    (sample range split over tiles, frames in blocks of 128); without
+    refinement it agrees with the FP32 SIMT product used for fewer frames."""
+    p = synth.make_plan(20, 3, "spiral", frames, 2701, 1e-3, samples=1100, interleaves=2)
+    pl = _plan(p.dims, p.traj, p.coil_maps, lam=p.lambda_rel, refine_max_iters=0).build()
+    d = torch.from_numpy(p.data.astype(np.complex64)).cuda()
+    x_tc = pl.apply(d).cpu().numpy()
+    x_32 = np.concatenate([pl.apply(d[i:i + 8]).cpu().numpy() for i in range(0, frames, 8)])
+    # both are FP32-class sums of M terms: bound sqrt(M) 2^-24 times the cancellation
+    # ratio || |R| |d| || / || R d || of this product
+    R = pl.export(L.EXPORT_RECON).cpu().numpy().astype(np.complex128)
+    dd = p.data.astype(np.complex64).reshape(frames, -1).astype(np.complex128).T
+    amp = np.linalg.norm(np.abs(R) @ np.abs(dd)) / np.linalg.norm(R @ dd)
+    bound = 4 * np.sqrt(R.shape[1]) * 2.0 ** -24 * amp
+    assert rel(x_tc, x_32) <= bound, (rel(x_tc, x_32), bound)
