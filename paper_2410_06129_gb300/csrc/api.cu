@@ -76,6 +76,7 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
         CK(launch_toeplitz64(p->enc, work, p->Ttab, s));
         CK(cudaFreeAsync(work, s));
         CK(launch_gram_exact(p->enc, p->Ttab, p->lambda_abs, p->Gx, s));
+        if (p->Gd) CK(launch_gram_digits(p->Gx, N, p->eG, p->Gd, s));
     }
     return PINV_OK;
 }
@@ -393,6 +394,8 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
     if (toeplitz) {
         AL(p->Ttab, sizeof(double2) * (2 * e.nx - 1) * (2 * e.ny - 1) * (2 * e.nz - 1), "Toeplitz table");
         AL(p->Gx, sizeof(float4) * p->N * p->N, "exact Gram");
+        AL(p->Gd, gram_digit_bytes(p->N), "exact Gram digits");
+        AL(p->eG, sizeof(int), "exact Gram exponent");
     }
     int rm = d->recon_mode;
     if (rm == PINV_RECON_AUTO) {

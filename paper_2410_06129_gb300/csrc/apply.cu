@@ -90,6 +90,7 @@ size_t apply_scratch_layout(const pinv_plan* p, int64_t F, int dtype, void* base
         size_t w = std::max(df_work_elems(N, F, M), std::max(df_work_elems(M, F, N), df_work_elems(N, F, N)));
         if (md.need_b && exact_adjoint_ok(p->enc, F)) {
             w = std::max(w, exact_work_elems(p->enc, F));
+            if (md.toep && p->Gd) w = std::max(w, resid_exact_work_elems(N, F));
             s.fexp = cv.take<int>((size_t)F);
         }
         s.dfw = w ? cv.take<float4>(w) : nullptr;
@@ -175,7 +176,9 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
             }
         }
         for (int it = 0; it < p->refine_iters; ++it) {
-            if (md.toep) {
+            if (md.toep && sc.fexp && p->Gd) {  // r = b - G x, exactly on the tensor cores
+                CKA(launch_gram_resid_exact(p->Gd, p->eG, N, sc.b128, X, F, sc.fexp, sc.r128, sc.dfw, p->st, s));
+            } else if (md.toep) {
                 CKA(launch_gram_resid_df(p->Gx, N, sc.b128, X, F, sc.r128, s, sc.dfw));  // r = b - G x
             } else if (md.dfres) {
                 CKA(launch_forward_df(p->enc, X, F, D, sc.u128, s, sc.dfw));  // u = d - E x

@@ -250,6 +250,15 @@ size_t apply_tc_work_elems(int64_t N, int64_t M, int64_t F);
 cudaError_t launch_apply_tc(const float2* R, int64_t N, int64_t M, const float2* D, int64_t F, float2* X,
                             float2* work, int slices, DevStatus* st, cudaStream_t s);
 
+// r = b - G x exactly on the tensor cores, from digit tiles of the exact Gram
+// (gram_digit_bytes(N) bytes, written by launch_gram_digits at build time)
+size_t gram_digit_bytes(int64_t N);
+cudaError_t launch_gram_digits(const float4* G, int64_t N, int* eG, uint8_t* Gd, cudaStream_t s);
+size_t resid_exact_work_elems(int64_t N, int64_t F);
+cudaError_t launch_gram_resid_exact(const uint8_t* Gd, const int* eG, int64_t N, const double2* Bv,
+                                    const double2* X, int64_t F, int* fexp, double2* R, float4* work,
+                                    DevStatus* st, cudaStream_t s);
+
 // exact Gram of B0-free grid plans (Toeplitz table, FP64; stored double-float)
 size_t toeplitz_work_bytes(const EncodeDev& e);
 cudaError_t launch_toeplitz64(const EncodeDev& e, double2* work, double2* T, cudaStream_t s);

@@ -84,6 +84,8 @@ struct pinv_plan {
     void* R = nullptr;         // Recon [N][M], c128 (FP64) or c64 (mixed)
     double2* Ttab = nullptr;   // Toeplitz table of A^H A (TOEPLITZ residual)
     float4* Gx = nullptr;      // exact Gram, double-float [N][N] (TOEPLITZ residual)
+    uint8_t* Gd = nullptr;     // its fixed-point digit tiles for the tensor-core residual
+    int* eG = nullptr;         // |G| <= 2^eG (device)
     pinv::DevStatus* st = nullptr;        // device status word
     pinv::DevStatus* st_host = nullptr;   // pinned copy, written at the end of each build
 

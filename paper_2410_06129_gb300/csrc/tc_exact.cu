@@ -89,13 +89,16 @@ struct Digits8 {
 
 struct XArgs {
     EncodeDev e;
-    const double2* D;   // data [F][M], FP64 view
-    const int* fexp;    // per-frame exponent: |d_f| <= 2^fexp
+    const double2* D;   // adjoint: data [F][M]; Gram residual: x [F][N] (FP64)
+    const int* fexp;    // per-frame exponent: |D_f| <= 2^fexp
     int64_t F, M;
-    int64_t chunk;      // samples per split (multiple of XKC); splits never cross a coil
-    int sub;            // splits per coil
-    float4* part;       // [C * sub][F][N] double-float partials, or null (one split, no coil maps)
+    int64_t chunk;      // k per split (multiple of XKC); adjoint splits never cross a coil
+    int sub;            // adjoint: splits per coil
+    float4* part;       // [splits][F][N] double-float partials, or null (one split, no coil maps)
     double2* B;         // output [F][N] when part is null
+    const uint8_t* Gd;  // Gram residual: digit tiles of G ([row block][k block][digit] x 8 KiB)
+    const int* eG;      // Gram residual: |G| <= 2^eG
+    int64_t KB;         // Gram residual: k blocks of 16 per row block
 };
 
 // conj(A[m][n]) for 8 consecutive samples m (< mend) of voxel n, double-float,
@@ -131,7 +134,10 @@ __device__ inline void gen_ah8(const EncodeDev& e, int64_t n, int64_t m, int64_t
     }
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1) k_adjoint_exact(XArgs a, DevStatus* st) {
+// GRAM = false: b = E^H d (A generated). GRAM = true: G x with the digits of G
+// precomputed in tile layout (A copied) and x as the B operand.
+template <bool GRAM>
+__global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[XSTAGES], empty_bar[XSTAGES];
     __shared__ uint64_t tfull, tempty, done_bar;
@@ -141,9 +147,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_adjoint_exact(XArgs a, DevStatu
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t N = a.e.N;
     const int64_t n0 = (int64_t)blockIdx.y * XM, f0 = (int64_t)blockIdx.x * XN;
-    const int coil = (int)blockIdx.z / a.sub;
-    const int64_t Mk = a.e.Mk;
-    const int64_t mb = (int64_t)((int)blockIdx.z % a.sub) * a.chunk;   // sample range inside the coil
+    // k range [mb, me): adjoint samples inside coil `coil`, or Gram columns
+    const int coil = GRAM ? 0 : (int)blockIdx.z / a.sub;
+    const int64_t Mk = GRAM ? N : a.e.Mk;
+    const int64_t mb = GRAM ? (int64_t)blockIdx.z * a.chunk : (int64_t)((int)blockIdx.z % a.sub) * a.chunk;
     const int64_t me = mb + a.chunk < Mk ? mb + a.chunk : Mk;
     const int nk = me > mb ? (int)((me - mb + XKC - 1) / XKC) : 0;
     const int ngroups = (nk + XDRAIN - 1) / XDRAIN;
@@ -217,8 +224,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_adjoint_exact(XArgs a, DevStatu
             const uint32_t ph = (uint32_t)(kt / XSTAGES) & 1u;
             if (kt >= XSTAGES && !(ok = mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag))) break;
             uint8_t* base = smem + s * XSTAGE;
-            const int64_t m0 = mb + (int64_t)kt * XKC;  // sample index inside the coil
-            {
+            const int64_t m0 = mb + (int64_t)kt * XKC;  // k index (sample inside the coil, or Gram column)
+            if (GRAM) {
+                // digit tile of rows n0.., columns m0..m0+15: NDIG x 8 KiB, copied as is
+                const uint4* src = reinterpret_cast<const uint4*>(
+                    a.Gd + ((int64_t)blockIdx.y * a.KB + m0 / XKC) * (int64_t)(NDIG * XA_SL));
+                uint4* dst = reinterpret_cast<uint4*>(base);
+                constexpr int NV = NDIG * XA_SL / 16 / (NPW * 32);  // 12 vectors per thread
+                uint4 v[NV];
+#pragma unroll
+                for (int u = 0; u < NV; ++u) v[u] = src[u * NPW * 32 + threadIdx.x];
+#pragma unroll
+                for (int u = 0; u < NV; ++u) dst[u * NPW * 32 + threadIdx.x] = v[u];
+            } else {
                 float reh[8], rel[8], imh[8], iml[8];
                 gen_ah8(a.e, nrow, m0 + 8 * ga, me, reh, rel, imh, iml);
                 Digits8 dr, di;
@@ -240,7 +258,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_adjoint_exact(XArgs a, DevStatu
                 for (int t = 0; t < 8; ++t) {
                     const int64_t m = m0 + 8 * gb + t;
                     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (fcol < a.F && m < me) v = to_df(a.D[fcol * a.M + (int64_t)coil * Mk + m]);
+                    if (fcol < a.F && m < me) v = to_df(a.D[fcol * a.M + (int64_t)coil * Mk + m]);  // Gram: M = N
                     reh[t] = v.x;
                     rel[t] = v.y;
                     imh[t] = v.z;
@@ -275,14 +293,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_adjoint_exact(XArgs a, DevStatu
             const int64_t n = n0 + q * 32 + lane;
             if (n < N) {
                 float4 cs = make_float4(1.f, 0.f, 0.f, 0.f);
-                if (a.e.coilsdf) cs = cdf_conj(a.e.coilsdf[(int64_t)coil * N + n]);
+                if (!GRAM && a.e.coilsdf) cs = cdf_conj(a.e.coilsdf[(int64_t)coil * N + n]);
+                const int eA = GRAM ? *a.eG : 0;
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     const int64_t f = f0 + 16 * h + u;
                     if (f >= a.F) continue;
-                    const float sc = __int_as_float((127 + a.fexp[f]) << 23);
+                    const float sc = __int_as_float((127 + eA + a.fexp[f]) << 23);
                     float4 v = make_float4(acc[0][u] * sc, acc[1][u] * sc, acc[2][u] * sc, acc[3][u] * sc);
-                    if (a.e.coilsdf) v = cdf_mul(v, cs);
+                    if (!GRAM && a.e.coilsdf) v = cdf_mul(v, cs);
                     if (a.part)
                         a.part[((int64_t)blockIdx.z * a.F + f) * N + n] = v;
                     else
@@ -352,6 +371,81 @@ __global__ void k_exact_reduce(BStore o, const float4* part, int splits, int64_t
     o.store(i, j, from_df(a));
 }
 
+// r[f][n] = b[f][n] - sum_z part[z][f][n], partials added in order
+__global__ void k_resid_reduce(const double2* b, const float4* part, int splits, int64_t N, int64_t F,
+                               double2* r) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * F) return;
+    float4 a = part[idx];
+    for (int z = 1; z < splits; ++z) {
+        const float4 c = part[(int64_t)z * N * F + idx];
+        float rh, rl, ih, il;
+        df_add(a.x, a.y, c.x, c.y, rh, rl);
+        df_add(a.z, a.w, c.z, c.w, ih, il);
+        a = make_float4(rh, rl, ih, il);
+    }
+    const double2 g = from_df(a), bb = b[idx];
+    r[idx] = make_double2(bb.x - g.x, bb.y - g.y);
+}
+
+// |G| <= 2^eG from the largest diagonal entry (G Hermitian positive definite)
+__global__ void k_gram_exp(const float4* G, int64_t N, int* eG) {
+    __shared__ double red[256];
+    double m = 0.0;
+    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+        const float4 g = G[n * N + n];
+        m = fmax(m, fabs((double)g.x + (double)g.y));
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int ex = 0;
+        const double mant = red[0] > 0.0 ? frexp(red[0], &ex) : 0.0;
+        if (mant == 0.5) --ex;
+        *eG = red[0] > 0.0 ? ex : 0;
+    }
+}
+
+// Digit tiles of G: one thread per (row n, 8 columns); every position of the
+// padded [RB * 128][KB * 16] array is written (zeros outside N x N).
+__global__ void k_gram_digits(const float4* G, int64_t N, int64_t KB, const int* eG, uint8_t* Gd) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t RB = (N + XM - 1) / XM;
+    if (idx >= RB * XM * KB * 2) return;
+    const int64_t n = idx / (KB * 2), rem = idx % (KB * 2);
+    const int64_t kb = rem / 2;
+    const int g = (int)(rem % 2);
+    const int64_t c0 = kb * XKC + 8 * g;
+    float reh[8], rel[8], imh[8], iml[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n < N && c0 + t < N) v = G[n * N + c0 + t];
+        reh[t] = v.x;
+        rel[t] = v.y;
+        imh[t] = v.z;
+        iml[t] = v.w;
+    }
+    const float scale = __int_as_float((127 - *eG) << 23);
+    Digits8 dr, di;
+    dr.init(reh, rel, scale);
+    di.init(imh, iml, scale);
+    uint8_t* tile = Gd + ((n / XM) * KB + kb) * (int64_t)(NDIG * XA_SL);
+    const int r = (int)(n % XM);
+#pragma unroll
+    for (int dg = 0; dg < NDIG; ++dg) {
+        uint32_t w[4];
+        dr.next(w, 0u);
+        *reinterpret_cast<uint4*>(tile + dg * XA_SL + koff(r, g)) = make_uint4(w[0], w[1], w[2], w[3]);
+        di.next(w, 0u);
+        *reinterpret_cast<uint4*>(tile + dg * XA_SL + koff(r, g + 2)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
 // per-frame exponent: |re|, |im| of frame f all <= 2^fexp[f]
 __global__ void k_frame_exp(const double2* D, int64_t M, int* fexp) {
     __shared__ double red[256];
@@ -395,16 +489,21 @@ bool exact_adjoint_ok(const EncodeDev& e, int64_t F) {
     return e.extdf && !e.b0df && !e.b0tab && F >= 16 && tc_available();
 }
 
+template <bool GRAM>
+static cudaError_t exact_attr() {
+    static bool attr = false;
+    if (attr) return cudaSuccess;
+    cudaError_t err =
+        cudaFuncSetAttribute(tcx::k_exact<GRAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcx::XSMEM);
+    if (err == cudaSuccess) attr = true;
+    return err;
+}
+
 cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F, int* fexp, double2* B,
                                  float4* work, DevStatus* st, cudaStream_t s) {
     if (F == 0) return cudaSuccess;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t err = cudaFuncSetAttribute(tcx::k_adjoint_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               tcx::XSMEM);
-        if (err != cudaSuccess) return err;
-        attr = true;
-    }
+    cudaError_t aerr = exact_attr<false>();
+    if (aerr != cudaSuccess) return aerr;
     const int64_t M = e.Mk * e.C;
     tcx::k_frame_exp<<<(unsigned)F, 256, 0, s>>>(D, M, fexp);
     note_launch();
@@ -413,14 +512,63 @@ cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F
     const bool partials = splits > 1 || e.coilsdf;
     if (partials && !work) return cudaErrorInvalidValue;
     const int64_t chunk = ((e.Mk + sub - 1) / sub + tcx::XKC - 1) / tcx::XKC * tcx::XKC;
-    tcx::XArgs a{e, D, fexp, F, M, chunk, sub, partials ? work : nullptr, B};
+    tcx::XArgs a{e, D, fexp, F, M, chunk, sub, partials ? work : nullptr, B, nullptr, nullptr, 0};
     dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN), (unsigned)((e.N + tcx::XM - 1) / tcx::XM), (unsigned)splits);
-    tcx::k_adjoint_exact<<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
+    tcx::k_exact<false><<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
     note_launch();
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess || !partials) return err;
     const int64_t n = e.N * F;
     tcx::k_exact_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tcx::BStore{B, e.N}, work, (int)splits, e.N, F);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ exact Gram residual
+size_t gram_digit_bytes(int64_t N) {
+    const int64_t RB = (N + tcx::XM - 1) / tcx::XM, KB = (N + tcx::XKC - 1) / tcx::XKC;
+    return (size_t)RB * (size_t)KB * (size_t)(tcx::NDIG * tcx::XA_SL);
+}
+
+cudaError_t launch_gram_digits(const float4* G, int64_t N, int* eG, uint8_t* Gd, cudaStream_t s) {
+    tcx::k_gram_exp<<<1, 256, 0, s>>>(G, N, eG);
+    note_launch();
+    const int64_t KB = (N + tcx::XKC - 1) / tcx::XKC, RB = (N + tcx::XM - 1) / tcx::XM;
+    const int64_t n = RB * tcx::XM * KB * 2;
+    tcx::k_gram_digits<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(G, N, KB, eG, Gd);
+    note_launch();
+    return cudaGetLastError();
+}
+
+static int resid_splits(int64_t N, int64_t F) {
+    const int64_t tiles = ((N + tcx::XM - 1) / tcx::XM) * ((F + tcx::XN - 1) / tcx::XN);
+    int64_t sp = (2 * 152 + tiles - 1) / tiles;
+    sp = std::min<int64_t>(sp, std::max<int64_t>(1, N / (tcx::XKC * tcx::XDRAIN * 2)));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 32));
+}
+
+size_t resid_exact_work_elems(int64_t N, int64_t F) { return (size_t)resid_splits(N, F) * (size_t)N * (size_t)F; }
+
+cudaError_t launch_gram_resid_exact(const uint8_t* Gd, const int* eG, int64_t N, const double2* Bv,
+                                    const double2* X, int64_t F, int* fexp, double2* R, float4* work,
+                                    DevStatus* st, cudaStream_t s) {
+    if (F == 0) return cudaSuccess;
+    cudaError_t err = exact_attr<true>();
+    if (err != cudaSuccess) return err;
+    tcx::k_frame_exp<<<(unsigned)F, 256, 0, s>>>(X, N, fexp);
+    note_launch();
+    const int sp = resid_splits(N, F);
+    const int64_t chunk = ((N + sp - 1) / sp + tcx::XKC - 1) / tcx::XKC * tcx::XKC;
+    EncodeDev e{};
+    e.N = N;
+    const int64_t KB = (N + tcx::XKC - 1) / tcx::XKC;
+    tcx::XArgs a{e, X, fexp, F, N, chunk, 1, work, nullptr, Gd, eG, KB};
+    dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN), (unsigned)((N + tcx::XM - 1) / tcx::XM), (unsigned)sp);
+    tcx::k_exact<true><<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
+    note_launch();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const int64_t n = N * F;
+    tcx::k_resid_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Bv, work, sp, N, F, R);
     note_launch();
     return cudaGetLastError();
 }
