@@ -102,8 +102,9 @@ typedef struct {
     int refine_residual;          /* mixed plans: pinv_residual arithmetic of the residual */
     int lean;                     /* 1: G / L (and the FP64 W of mixed plans whose residual is not
                                      FP64) exist only during pinv_build; the plan then keeps only
-                                     what its apply reads (80 -> 48 bytes per N^2 entry for a mixed
-                                     TOEPLITZ plan). Exports of L, W and G^-1 (mixed), maps and
+                                     what its apply reads (80 -> 32 bytes per N^2 entry for a mixed
+                                     TOEPLITZ plan, which also drops its double-float exact Gram).
+                                     Exports of L, W, G^-1 (mixed) and the exact Gram, maps and
                                      batches are then unavailable. 0: keep them. */
 } pinv_plan_desc;
 
@@ -114,9 +115,9 @@ typedef struct {
  * between n and n' (Eq. 2), so G is formed in FP64 from a (2n_x-1)(2n_y-1)(2n_z-1)
  * table and the coil products at build time and stored as double-float
  * [N][N] (16 N^2 bytes) plus fixed-point digit tiles (24 N^2 bytes); each
- * apply forms E^H d once and each step costs N^2 F complex MACs. With 16 or
- * more frames E^H d and G x run exactly on the tensor cores (integer digit
- * products), otherwise in double-float. Plans with b0_hz reject TOEPLITZ. */
+ * apply forms E^H d once and each step costs N^2 F complex MACs. G x runs
+ * exactly on the tensor cores (integer digit products); E^H d too with 16 or
+ * more frames, otherwise in double-float. Plans with b0_hz reject TOEPLITZ. */
 typedef enum {
     PINV_RESIDUAL_DOUBLE_FLOAT = 0, /* r in double-float (hi + lo floats, ~44 bits) on the FP32 units */
     PINV_RESIDUAL_FP64 = 1,         /* r in FP64 (DFMA); FP64 plans always use this */

@@ -54,6 +54,7 @@ pinv_status build_begin(pinv_plan* p, cudaStream_t s) {
     if (p->lean) {  // stream-ordered temporaries, released by build_end
         CK(cudaMallocAsync((void**)&p->G, sizeof(double2) * p->N * p->N, s));
         if (p->lean_w()) CK(cudaMallocAsync((void**)&p->W, sizeof(double2) * p->N * p->N, s));
+        if (p->lean_gx()) CK(cudaMallocAsync((void**)&p->Gx, sizeof(float4) * p->N * p->N, s));
     }
     if (p->keep_gram && !p->Gkeep) {
         pinv_status st = p->alloc((void**)&p->Gkeep, sizeof(double2) * p->N * p->N, "Gkeep");
@@ -70,7 +71,8 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
     }
     if (p->Gkeep) CK(cudaMemcpyAsync(p->Gkeep, p->G, sizeof(double2) * N * N, cudaMemcpyDeviceToDevice, s));
     if (p->Gx) {
-        // exact Gram for the refinement residual (Toeplitz table, then coil products)
+        // exact Gram for the refinement residual (Toeplitz table, then coil products,
+        // then its digit tiles)
         double2* work = nullptr;
         CK(cudaMallocAsync((void**)&work, toeplitz_work_bytes(p->enc), s));
         CK(launch_toeplitz64(p->enc, work, p->Ttab, s));
@@ -135,6 +137,10 @@ pinv_status build_end(pinv_plan* p, cudaStream_t s) {
         if (p->lean_w()) {
             CK(cudaFreeAsync(p->W, s));
             p->W = nullptr;
+        }
+        if (p->lean_gx()) {
+            CK(cudaFreeAsync(p->Gx, s));
+            p->Gx = nullptr;
         }
     }
     return PINV_OK;
@@ -393,7 +399,7 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
     }
     if (toeplitz) {
         AL(p->Ttab, sizeof(double2) * (2 * e.nx - 1) * (2 * e.ny - 1) * (2 * e.nz - 1), "Toeplitz table");
-        AL(p->Gx, sizeof(float4) * p->N * p->N, "exact Gram");
+        if (!p->lean_gx()) AL(p->Gx, sizeof(float4) * p->N * p->N, "exact Gram");
         AL(p->Gd, gram_digit_bytes(p->N), "exact Gram digits");
         AL(p->eG, sizeof(int), "exact Gram exponent");
     }
@@ -495,7 +501,7 @@ pinv_status pinv_plan_export(const pinv_plan* p, int what, void* dst, size_t byt
             src = p->W;
             break;
         case PINV_EXPORT_GRAM_EXACT:
-            if (!p->Gx) return fail(PINV_ERR_UNSUPPORTED, "only TOEPLITZ-residual plans keep the exact Gram");
+            if (!p->Gx) return fail(PINV_ERR_UNSUPPORTED, "only TOEPLITZ-residual plans that are not lean keep the exact Gram");
             src = p->Gx;
             break;
         case PINV_EXPORT_RECON:

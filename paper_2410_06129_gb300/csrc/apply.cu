@@ -88,11 +88,12 @@ size_t apply_scratch_layout(const pinv_plan* p, int64_t F, int dtype, void* base
         // E^H u (rows N, length M), E x (rows M, length N), G x (rows N, length N),
         // and the exact tensor-core E^H d
         size_t w = std::max(df_work_elems(N, F, M), std::max(df_work_elems(M, F, N), df_work_elems(N, F, N)));
-        if (md.need_b && exact_adjoint_ok(p->enc, F)) {
-            w = std::max(w, exact_work_elems(p->enc, F));
-            if (md.toep && p->Gd) w = std::max(w, resid_exact_work_elems(N, F));
-            s.fexp = cv.take<int>((size_t)F);
-        }
+        const bool xadj = md.need_b && exact_adjoint_ok(p->enc, F);
+        const bool xres = md.toep && md.refine && p->Gd;
+        if (xadj) w = std::max(w, exact_work_elems(p->enc, F));
+        if (xres) w = std::max(w, resid_exact_work_elems(N, F));
+        if (xadj || xres) s.fexp = cv.take<int>((size_t)F);
+        s.xadj = xadj;
         s.dfw = w ? cv.take<float4>(w) : nullptr;
     }
     if (sc) *sc = s;
@@ -127,7 +128,7 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
     double2* X = dtype == PINV_C128 ? (double2*)d_image : sc.x128;
 
     if (md.need_b) {  // b = E^H d, exactly on the tensor cores where possible
-        if (sc.fexp) CKA(launch_adjoint_exact(p->enc, D, F, sc.fexp, sc.b128, sc.dfw, p->st, s));
+        if (sc.xadj) CKA(launch_adjoint_exact(p->enc, D, F, sc.fexp, sc.b128, sc.dfw, p->st, s));
         else CKA(launch_adjoint_df(p->enc, D, F, 0.0, nullptr, sc.b128, s, sc.dfw));
     }
     if (!md.mixed) {
@@ -176,7 +177,7 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
             }
         }
         for (int it = 0; it < p->refine_iters; ++it) {
-            if (md.toep && sc.fexp && p->Gd) {  // r = b - G x, exactly on the tensor cores
+            if (md.toep && p->Gd) {  // r = b - G x, exactly on the tensor cores
                 CKA(launch_gram_resid_exact(p->Gd, p->eG, N, sc.b128, X, F, sc.fexp, sc.r128, sc.dfw, p->st, s));
             } else if (md.toep) {
                 CKA(launch_gram_resid_df(p->Gx, N, sc.b128, X, F, sc.r128, s, sc.dfw));  // r = b - G x

@@ -24,7 +24,8 @@ struct ApplyScratch {
     float2* x64;    // c64 image / FP32 correction temporary [F][N]
     double* norms;  // per-frame squared norms [2F]
     float4* dfw;    // partial sums of the split double-float products
-    int* fexp;      // per-frame exponents of the data [F] (exact tensor-core E^H d)
+    int* fexp;      // per-frame exponents of the data / image [F] (exact tensor-core products)
+    bool xadj;      // E^H d by the exact tensor-core kernel
     float2* apw;    // partials of the tensor-core Recon x data
     DevStatus* sched;  // tile counter of that launch: one per scratch region, since
                        // applies of one plan may run concurrently on several streams
@@ -101,6 +102,8 @@ struct pinv_plan {
     int slices() const { return precision == PINV_MIXED_BF16X6 ? 3 : 2; }
     // a lean mixed plan keeps only W32 when its residual does not use the FP64 W
     bool lean_w() const { return lean && precision != PINV_FP64 && refine_residual != PINV_RESIDUAL_FP64; }
+    // a lean TOEPLITZ plan keeps only the digit tiles of its exact Gram
+    bool lean_gx() const { return lean && refine_residual == PINV_RESIDUAL_TOEPLITZ && precision != PINV_FP64; }
 
     // Free the stored Recon; later applies take the factor-only path (x from
     // W^H W E^H d, then the same refinement). Returns the bytes released.

@@ -114,7 +114,7 @@ size_t plan_footprint(const pinv_plan_desc& d, bool with_recon) {
     // lean plans: G^-1 (FP64), or W32 (+ the FP64 W for an FP64 residual)
     double b = fp64 ? N * N * 16.0 : N * N * 8.0;
     if (!fp64 && d.refine_residual == PINV_RESIDUAL_FP64) b += N * N * 16.0;
-    if (!fp64 && d.refine_residual == PINV_RESIDUAL_TOEPLITZ) b += N * N * 40.0;  // exact Gram + its digits
+    if (!fp64 && d.refine_residual == PINV_RESIDUAL_TOEPLITZ) b += N * N * 24.0;  // exact Gram digits
     int recon = d.recon_mode;
     if (recon == PINV_RECON_AUTO) recon = N * M * (fp64 ? 16.0 : 8.0) <= 64.0 * (1ull << 30);
     if (recon && with_recon) b += N * M * (fp64 ? 16.0 : 8.0);

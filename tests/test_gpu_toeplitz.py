@@ -119,16 +119,17 @@ def test_toeplitz_needs_b0_free_plan():
 
 
 def test_lean_plan_same_images_less_memory():
-    """A lean plan drops G / L and the FP64 W after its build: same images bit
-    for bit, N^2 x 32 bytes less device memory, no L / W exports."""
+    """A lean plan drops G / L, the FP64 W and the double-float exact Gram after
+    its build: same images bit for bit, N^2 x 48 bytes less device memory, no
+    L / W / exact-Gram exports."""
     p = synth.config(2, reduced=True)
     d = torch.from_numpy(p.data).cuda()
     full = _plan(p.dims, p.traj, p.coil_maps, lam=p.lambda_rel, refine_max_iters=3).build()
     lean = _plan(p.dims, p.traj, p.coil_maps, lam=p.lambda_rel, refine_max_iters=3, lean=True).build()
     assert torch.equal(full.apply(d), lean.apply(d))
     N = p.n_vox
-    assert full.info()["bytes_device"] - lean.info()["bytes_device"] == 32 * N * N
-    for what in (L.EXPORT_CHOL, L.EXPORT_LINV, L.EXPORT_GINV):
+    assert full.info()["bytes_device"] - lean.info()["bytes_device"] == 48 * N * N
+    for what in (L.EXPORT_CHOL, L.EXPORT_LINV, L.EXPORT_GINV, L.EXPORT_GRAM_EXACT):
         with pytest.raises(L.PinvError, match="UNSUPPORTED"):
             lean.export(what)
     lean.build()  # rebuild allocates the temporaries again
