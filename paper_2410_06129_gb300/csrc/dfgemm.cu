@@ -298,6 +298,7 @@ cudaError_t launch_from_df(const float4* a, int64_t n, double2* b, cudaStream_t 
 // Cholesky. Storage stays FP64. Only the 64 pivots use FP64 (one rsqrt each).
 namespace {
 constexpr int NBD = 64;
+constexpr int DIAG_THREADS = 1024;  // 16 lanes per column in the inverse
 __device__ inline float4 df_scale(float4 a, float rh, float rl) {  // complex DF times real DF
     float xh, xl, yh, yl;
     df_mul(a.x, a.y, rh, rl, xh, xl);
@@ -322,7 +323,7 @@ __device__ inline float4 df_cadd(float4 a, float4 b) {
 }
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0,
+__global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0,
                                                        double2* Dinv, float2* Dinv32, DevStatus* st) {
     extern __shared__ float4 smd[];
     float4* A = smd;               // [NBD][NBD]
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(256) k_potrf_diag_df(double2* G, int64_t ld, i
     const int tid = threadIdx.x;
     const int nb = (int)((N - k0) < NBD ? (N - k0) : NBD);
     if (tid == 0) bad = (st->not_pd_pivot != INT_MAX) ? 1 : 0;
-    for (int e = tid; e < NBD * NBD; e += 256) {
+    for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
         const int i = e / NBD, j = e % NBD;
         double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
         if (i < nb && j < nb && j <= i) v = G[(k0 + i) * ld + k0 + j];
@@ -357,13 +358,14 @@ __global__ void __launch_bounds__(256) k_potrf_diag_df(double2* G, int64_t ld, i
             rdiag[j] = make_float2(rh, (float)(r - (double)rh));
         } else if (j > 0) {
             const float2 r = rdiag[j - 1];
-            for (int i = j + tid - 1; i < NBD; i += 255) A[i * NBD + j - 1] = df_norm(df_scale(A[i * NBD + j - 1], r.x, r.y));
+            for (int i = j + tid - 1; i < NBD; i += DIAG_THREADS - 1)
+                A[i * NBD + j - 1] = df_norm(df_scale(A[i * NBD + j - 1], r.x, r.y));
         }
         __syncthreads();
         float r2h, r2l;
         df_mul(rdiag[j].x, rdiag[j].y, rdiag[j].x, rdiag[j].y, r2h, r2l);
         const int rem = NBD - j - 1;
-        for (int e = tid; e < rem * rem; e += 256) {
+        for (int e = tid; e < rem * rem; e += DIAG_THREADS) {
             const int i = j + 1 + e / rem, k = j + 1 + e % rem;
             if (k <= i) {
                 float4 c = df_scale(A[i * NBD + j], -r2h, -r2l);
@@ -374,17 +376,18 @@ __global__ void __launch_bounds__(256) k_potrf_diag_df(double2* G, int64_t ld, i
         }
         __syncthreads();
     }
-    // X = A^-1 by forward substitution down each column; four lanes share a
-    // column (every fourth term of the dot product), combined by shuffles.
+    // X = A^-1 by forward substitution down each column; LPC lanes share a
+    // column (every LPC-th term of the dot product), combined by shuffles.
     {
-        const int c = tid >> 2, q = tid & 3;
+        constexpr int LPC = DIAG_THREADS / NBD;
+        const int c = tid / LPC, q = tid % LPC;
         for (int i = 0; i < NBD; ++i) {
             float4 part = make_float4(0.f, 0.f, 0.f, 0.f);
             if (i > c)
-                for (int k = c + q; k < i; k += 4) cacc(part, A[i * NBD + k], X[k * NBD + c]);
+                for (int k = c + q; k < i; k += LPC) cacc(part, A[i * NBD + k], X[k * NBD + c]);
             part = df_norm(part);
 #pragma unroll
-            for (int m = 1; m <= 2; m <<= 1) {
+            for (int m = 1; m < LPC; m <<= 1) {
                 float4 o;
                 o.x = __shfl_xor_sync(0xffffffffu, part.x, m);
                 o.y = __shfl_xor_sync(0xffffffffu, part.y, m);
@@ -405,7 +408,7 @@ __global__ void __launch_bounds__(256) k_potrf_diag_df(double2* G, int64_t ld, i
         }
     }
     __syncthreads();
-    for (int e = tid; e < NBD * NBD; e += 256) {
+    for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
         const int i = e / NBD, j = e % NBD;
         const double2 x = from_df(X[e]);
         Dinv[e] = x;
@@ -424,7 +427,7 @@ cudaError_t launch_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0, 
         if (err != cudaSuccess) return err;
         attr = true;
     }
-    k_potrf_diag_df<<<1, 256, smem, s>>>(G, ld, N, k0, Dinv, Dinv32, st);
+    k_potrf_diag_df<<<1, DIAG_THREADS, smem, s>>>(G, ld, N, k0, Dinv, Dinv32, st);
     note_launch();
     return cudaGetLastError();
 }
