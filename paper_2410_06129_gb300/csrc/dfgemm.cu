@@ -323,14 +323,35 @@ __device__ inline float4 df_cadd(float4 a, float4 b) {
 }
 }  // namespace
 
+// 1 / sqrt(d) for a positive double-float d: FP32 estimate and one Newton
+// step in double-float (error about the square of the estimate's, ~2^-44)
+__device__ inline float2 df_rsqrt(float dh, float dl) {
+    const float r0 = rsqrtf(dh);
+    float sh, sl, th, tl, uh, ul;
+    df_mul(r0, 0.f, r0, 0.f, sh, sl);          // r0^2
+    df_mul(dh, dl, sh, sl, th, tl);            // d r0^2
+    df_add(1.f, 0.f, -th, -tl, uh, ul);        // 1 - d r0^2
+    df_mul(uh, ul, 0.5f * r0, 0.f, th, tl);    // r0 (1 - d r0^2) / 2
+    df_add(r0, 0.f, th, tl, uh, ul);
+    return make_float2(uh, ul);
+}
+
+// Blocked 64 x 64: four 16-wide panels. For each panel one warp factors the
+// 16 x 16 diagonal block (warp-synchronous, column by column), then all threads
+// solve the rows below against it and update the trailing block. The inverse
+// is blocked the same way: the four diagonal 16 x 16 inverses in parallel
+// (one warp each), then block diagonals d = 1..3 with
+// X_qp = -X_qq (sum_{r=p}^{q-1} L_qr X_rp).
+constexpr int PB = 16;  // panel width
 __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0,
-                                                       double2* Dinv, float2* Dinv32, DevStatus* st) {
+                                                             double2* Dinv, float2* Dinv32, DevStatus* st) {
     extern __shared__ float4 smd[];
-    float4* A = smd;               // [NBD][NBD]
-    float4* X = smd + NBD * NBD;   // [NBD][NBD] inverse
-    __shared__ float2 rdiag[NBD];  // 1 / L_jj as (hi, lo)
+    float4* A = smd;                  // [NBD][NBD]
+    float4* X = smd + NBD * NBD;      // [NBD][NBD] inverse
+    __shared__ float4 T[3][PB][PB];   // block sums of the current diagonal level
+    __shared__ float2 rdiag[NBD];     // 1 / L_jj as (hi, lo)
     __shared__ int bad;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nb = (int)((N - k0) < NBD ? (N - k0) : NBD);
     if (tid == 0) bad = (st->not_pd_pivot != INT_MAX) ? 1 : 0;
     for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
@@ -338,76 +359,119 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
         double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
         if (i < nb && j < nb && j <= i) v = G[(k0 + i) * ld + k0 + j];
         A[e] = to_df(v);
+        X[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    // Right-looking, two barriers per column: thread 0 takes pivot j while the
-    // others scale column j - 1 by its reciprocal pivot; then the trailing
-    // update uses the unscaled column j with the factor 1 / d_j.
-    for (int j = 0; j < NBD; ++j) {
-        if (tid == 0) {
-            const float4 a = A[j * NBD + j];
-            double d = (double)a.x + (double)a.y;
-            if (!(d > 0.0) || !isfinite(d)) {
-                if (!bad) atomicMin(&st->not_pd_pivot, (int)(k0 + j));
-                bad = 1;
-                d = 1.0;
-            }
-            const double r = rsqrt(d);
-            A[j * NBD + j] = to_df(make_double2(d * r, 0.0));
-            const float rh = (float)r;
-            rdiag[j] = make_float2(rh, (float)(r - (double)rh));
-        } else if (j > 0) {
-            const float2 r = rdiag[j - 1];
-            for (int i = j + tid - 1; i < NBD; i += DIAG_THREADS - 1)
-                A[i * NBD + j - 1] = df_norm(df_scale(A[i * NBD + j - 1], r.x, r.y));
-        }
-        __syncthreads();
-        float r2h, r2l;
-        df_mul(rdiag[j].x, rdiag[j].y, rdiag[j].x, rdiag[j].y, r2h, r2l);
-        const int rem = NBD - j - 1;
-        for (int e = tid; e < rem * rem; e += DIAG_THREADS) {
-            const int i = j + 1 + e / rem, k = j + 1 + e % rem;
-            if (k <= i) {
-                float4 c = df_scale(A[i * NBD + j], -r2h, -r2l);
-                float4 v = A[i * NBD + k];
-                cacc(v, c, cdf_conj(A[k * NBD + j]));
-                A[i * NBD + k] = df_norm(v);
-            }
-        }
-        __syncthreads();
-    }
-    // X = A^-1 by forward substitution down each column; LPC lanes share a
-    // column (every LPC-th term of the dot product), combined by shuffles.
-    {
-        constexpr int LPC = DIAG_THREADS / NBD;
-        const int c = tid / LPC, q = tid % LPC;
-        for (int i = 0; i < NBD; ++i) {
-            float4 part = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (i > c)
-                for (int k = c + q; k < i; k += LPC) cacc(part, A[i * NBD + k], X[k * NBD + c]);
-            part = df_norm(part);
-#pragma unroll
-            for (int m = 1; m < LPC; m <<= 1) {
-                float4 o;
-                o.x = __shfl_xor_sync(0xffffffffu, part.x, m);
-                o.y = __shfl_xor_sync(0xffffffffu, part.y, m);
-                o.z = __shfl_xor_sync(0xffffffffu, part.z, m);
-                o.w = __shfl_xor_sync(0xffffffffu, part.w, m);
-                part = df_cadd(part, o);
-            }
-            if (q == 0) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (i >= c) {
-                    float4 t = make_float4(-part.x, -part.y, -part.z, -part.w);
-                    if (i == c) t = df_cadd(t, make_float4(1.f, 0.f, 0.f, 0.f));
-                    v = df_norm(df_scale(t, rdiag[i].x, rdiag[i].y));
+
+    for (int p0 = 0; p0 < NBD; p0 += PB) {
+        if (warp == 0) {
+            // 16 x 16 diagonal block, right-looking; lane l owns row p0 + (l & 15)
+            for (int c = 0; c < PB; ++c) {
+                const int jc = p0 + c;
+                float2 r = make_float2(0.f, 0.f);
+                if (lane == 0) {
+                    const float4 a = A[jc * NBD + jc];
+                    float dh = a.x, dl = a.y;
+                    if (!((double)dh + (double)dl > 0.0) || !isfinite(dh)) {
+                        if (!bad) atomicMin(&st->not_pd_pivot, (int)(k0 + jc));
+                        bad = 1;
+                        dh = 1.f;
+                        dl = 0.f;
+                    }
+                    r = df_rsqrt(dh, dl);
+                    float lh, ll;
+                    df_mul(dh, dl, r.x, r.y, lh, ll);  // L_jj = d / sqrt(d)
+                    A[jc * NBD + jc] = make_float4(lh, ll, 0.f, 0.f);
+                    rdiag[jc] = r;
                 }
-                X[i * NBD + c] = v;
+                r.x = __shfl_sync(0xffffffffu, r.x, 0);
+                r.y = __shfl_sync(0xffffffffu, r.y, 0);
+                // scale column c below the diagonal inside the block
+                const int i = p0 + (lane & (PB - 1));
+                if (lane < PB && i > jc) A[i * NBD + jc] = df_norm(df_scale(A[i * NBD + jc], r.x, r.y));
+                __syncwarp();
+                // trailing update inside the block: rows and columns c+1..15
+                for (int e = lane; e < PB * PB; e += 32) {
+                    const int ii = p0 + e / PB, kk = p0 + e % PB;
+                    if (kk > jc && ii >= kk) {
+                        float4 v = A[ii * NBD + kk];
+                        const float4 a = A[ii * NBD + jc], b = A[kk * NBD + jc];
+                        cacc(v, make_float4(-a.x, -a.y, -a.z, -a.w), cdf_conj(b));
+                        A[ii * NBD + kk] = df_norm(v);
+                    }
+                }
+                __syncwarp();
             }
-            __syncwarp();
+        }
+        __syncthreads();
+        // rows below the panel: solve x L_pp^H = a for each row (one thread per row)
+        const int rows_below = NBD - p0 - PB;
+        if (tid < rows_below) {  // in place: x_c overwrites A[i][p0 + c] once known
+            const int i = p0 + PB + tid;
+            for (int c = 0; c < PB; ++c) {
+                float4 v = A[i * NBD + p0 + c];
+                for (int c2 = 0; c2 < c; ++c2) {
+                    const float4 x = A[i * NBD + p0 + c2], l = A[(p0 + c) * NBD + p0 + c2];
+                    cacc(v, make_float4(-x.x, -x.y, -x.z, -x.w), cdf_conj(l));
+                }
+                A[i * NBD + p0 + c] = df_norm(df_scale(df_norm(v), rdiag[p0 + c].x, rdiag[p0 + c].y));
+            }
+        }
+        __syncthreads();
+        // trailing update of the lower block below and right of the panel (K = 16)
+        if (rows_below > 0) {
+            for (int e = tid; e < rows_below * rows_below; e += DIAG_THREADS) {
+                const int ii = p0 + PB + e / rows_below, kk = p0 + PB + e % rows_below;
+                if (kk > ii) continue;
+                float4 v = A[ii * NBD + kk];
+#pragma unroll
+                for (int c = 0; c < PB; ++c) {
+                    const float4 a = A[ii * NBD + p0 + c], b = A[kk * NBD + p0 + c];
+                    cacc(v, make_float4(-a.x, -a.y, -a.z, -a.w), cdf_conj(b));
+                }
+                A[ii * NBD + kk] = df_norm(v);
+            }
+        }
+        __syncthreads();
+    }
+
+    // inverse: diagonal blocks, one warp each (lane = column of the block)
+    if (warp < NBD / PB && lane < PB) {
+        const int p0 = warp * PB, c = p0 + lane;
+        for (int i = p0; i < p0 + PB; ++i) {
+            float4 v = make_float4(i == c ? 1.f : 0.f, 0.f, 0.f, 0.f);
+            for (int k = c; k < i; ++k) {
+                const float4 l = A[i * NBD + k];
+                cacc(v, make_float4(-l.x, -l.y, -l.z, -l.w), X[k * NBD + c]);
+            }
+            X[i * NBD + c] = i >= c ? df_norm(df_scale(df_norm(v), rdiag[i].x, rdiag[i].y)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncwarp(0x0000ffffu);
         }
     }
     __syncthreads();
+    // off-diagonal blocks, one block diagonal at a time
+    for (int d = 1; d < NBD / PB; ++d) {
+        const int npairs = NBD / PB - d;
+        // T_qp = sum_{r=p}^{q-1} L_qr X_rp   (q = p + d)
+        for (int e = tid; e < npairs * PB * PB; e += DIAG_THREADS) {
+            const int pr = e / (PB * PB), ii = (e / PB) % PB, cc = e % PB;
+            const int p = pr, q = p + d;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int k = p * PB; k < q * PB; ++k) cacc(v, A[(q * PB + ii) * NBD + k], X[k * NBD + p * PB + cc]);
+            T[pr][ii][cc] = df_norm(v);
+        }
+        __syncthreads();
+        // X_qp = -X_qq T_qp
+        for (int e = tid; e < npairs * PB * PB; e += DIAG_THREADS) {
+            const int pr = e / (PB * PB), ii = (e / PB) % PB, cc = e % PB;
+            const int p = pr, q = p + d;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int k = 0; k <= ii; ++k) cacc(v, X[(q * PB + ii) * NBD + q * PB + k], T[pr][k][cc]);
+            v = df_norm(v);
+            X[(q * PB + ii) * NBD + p * PB + cc] = make_float4(-v.x, -v.y, -v.z, -v.w);
+        }
+        __syncthreads();
+    }
     for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
         const int i = e / NBD, j = e % NBD;
         const double2 x = from_df(X[e]);
