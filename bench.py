@@ -460,6 +460,21 @@ def main():
         roof["algorithmic_bytes"] = 3.0 * N * M * 8 / 2
     roof["ms_per_launch"] = ms_recon
 
+    # the tensor-core Gram kernels alone (operand table + Gram launch + split sum)
+    gram = None
+    if prec != L.FP64:
+        ms_gk = statistics.mean(i["ms_gram_kernel"] for i in infos)
+        nt, kcn = -(-N // 128), -(-inp.n_samples // 16)
+        pairs = 6 if prec == L.MIXED_BF16X6 else 3
+        # per lower tile and 16-sample chunk: pairs x 2 MMAs of M 128, N 256, K 16
+        issued = (nt * (nt + 1) // 2) * kcn * pairs * 2 * (2.0 * 128 * 256 * 16)
+        useful = 8.0 * N * (N + 1) / 2 * inp.n_samples
+        pk = peaks.get("bf16_tflops_sustained", 1700.0)
+        gram = {"kernel": "gram_tc (split-BF16 tcgen05, bulk-copied operand table)", "ms": ms_gk,
+                "issued_tflops": issued / (ms_gk / 1e3) / 1e12, "useful_tflops": useful / (ms_gk / 1e3) / 1e12,
+                "peak": pk, "peak_source": f"{peak_src} bf16_tflops_sustained"}
+        gram["frac_issued"] = gram["issued_tflops"] / pk
+
     res = {}
     # accuracy vs the FP64 GPU path (mixed plans)
     if prec != L.FP64 and not args.no_fp64_check and rank == 0:
@@ -544,6 +559,7 @@ def main():
                          "inverse": statistics.mean(i["ms_inverse"] for i in infos),
                          "recon": statistics.mean(i["ms_recon"] for i in infos)},
             "refine_steps": refine,
+            "gram_kernel": gram,
             "roofline": roof, "gpu_launches": int(launches), "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk.summary(), "wall_s_timed": wall,
         }

@@ -135,6 +135,7 @@ typedef struct {
     int info;                           /* failing pivot index (PINV_ERR_NOT_PD), else -1 */
     int last_refine_iters;              /* refinement steps taken by the last apply */
     double last_refine_resid;           /* ||r|| / ||E^H d|| after the last apply's refinement */
+    double ms_gram_kernel;              /* of ms_gram: the tensor-core (mixed) or FP64 Gram kernels alone */
 } pinv_plan_info_t;
 
 typedef struct pinv_plan pinv_plan;

@@ -6,6 +6,7 @@
 // caller's stream; nothing blocks until pinv_plan_sync.
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -65,10 +66,26 @@ pinv_status build_begin(pinv_plan* p, cudaStream_t s) {
 
 pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
     const int64_t N = p->N, ld = p->N;
+    CK(cudaEventRecord(p->ev[6], s));
     if (main_gram) {
-        if (p->precision != PINV_FP64) CK(launch_gram_tc(p->enc, p->lambda_abs, p->slices(), p->G, ld, p->st, s));
-        else CK(launch_gram64(p->enc, p->lambda_abs, p->G, ld, s));
+        if (p->precision == PINV_FP64) {
+            CK(launch_gram64(p->enc, p->lambda_abs, p->G, ld, s));
+        } else {
+            // bulk-fed Gram from a split operand table; without room for the table
+            // (or with PINV_GRAM_BULK=0) the kernel generates its operands itself
+            void* work = nullptr;
+            const char* env = std::getenv("PINV_GRAM_BULK");
+            const bool bulk = !(env && std::strcmp(env, "0") == 0);
+            if (bulk && cudaMallocAsync(&work, gram_bulk_bytes(p->enc, p->slices()), s) == cudaSuccess) {
+                CK(launch_gram_bulk(p->enc, p->lambda_abs, p->slices(), p->G, ld, work, p->st, s));
+                CK(cudaFreeAsync(work, s));
+            } else {
+                cudaGetLastError();
+                CK(launch_gram_tc(p->enc, p->lambda_abs, p->slices(), p->G, ld, p->st, s));
+            }
+        }
     }
+    CK(cudaEventRecord(p->ev[7], s));
     if (p->Gkeep) CK(cudaMemcpyAsync(p->Gkeep, p->G, sizeof(double2) * N * N, cudaMemcpyDeviceToDevice, s));
     if (p->Gx) {
         // exact Gram for the refinement residual (Toeplitz table, then coil products,
@@ -549,6 +566,12 @@ pinv_status pinv_plan_info(const pinv_plan* p, pinv_plan_info_t* o) {
         o->ms_chol = t[2];
         o->ms_inverse = t[3];
         o->ms_recon = t[4];
+        float tg = 0.f;
+        if (cudaEventElapsedTime(&tg, p->ev[6], p->ev[7]) != cudaSuccess) {
+            cudaGetLastError();
+            tg = 0.f;
+        }
+        o->ms_gram_kernel = tg;
         const DevStatus h = *p->st_host;
         o->min_pivot = h.min_pivot;
         o->max_pivot = h.max_pivot;

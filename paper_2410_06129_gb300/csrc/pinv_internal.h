@@ -179,6 +179,11 @@ cudaError_t launch_zaxpy(double2* X, const double2* Y, int64_t n, cudaStream_t s
 // Gram in split BF16 on tcgen05 tensor cores; result written as FP64 lower tiles.
 cudaError_t launch_gram_tc(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld,
                            DevStatus* st, cudaStream_t s);
+// Bulk-fed Gram: the split encoding table (and, for a split sample range, the
+// partial sums) in `work` of gram_bulk_bytes(); same result layout as launch_gram_tc.
+size_t gram_bulk_bytes(const EncodeDev& e, int slices);
+cudaError_t launch_gram_bulk(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld, void* work,
+                             DevStatus* st, cudaStream_t s);
 // Recon = W^H (W E^H) in split BF16 on tcgen05 (W = L^-1 in FP32, T = W E^H
 // scratch [N][M] c64), c64 out.
 cudaError_t launch_recon_tc(const EncodeDev& e, const float2* W32, const float2* WT32, float2* T, int slices,

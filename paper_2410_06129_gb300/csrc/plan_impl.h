@@ -94,7 +94,7 @@ struct pinv_plan {
     void* scratch_buf = nullptr;
     size_t scratch_bytes = 0;
 
-    cudaEvent_t ev[6] = {};
+    cudaEvent_t ev[8] = {};  // build stages 0-5; 6-7 around the Gram kernels
     int last_refine_iters = 0;
     double last_refine_resid = 0;
     int info = -1;

@@ -29,9 +29,21 @@
 // the TMEM total. Every mbarrier wait is bounded by a clock64
 // limit: on expiry the CTA raises an abort flag, stops, waits (bounded) for its
 // issued MMAs, frees TMEM and records the failure in the plan's status word.
+//
+// Bulk-fed problems (kBulk = true) keep their operands in global memory already
+// split and laid out as stage tiles (bulk_a: one 8 KiB A slice tile, bulk_b: one
+// 16 KiB B slice tile). A tenth warp then loads each stage with asynchronous
+// bulk copies (cp.async.bulk, completion counted in bytes on the stage's full
+// barrier), and nothing passes through registers. The MMA accumulator is
+// double-buffered (two 256-column halves of TMEM, group g in half g & 1), and
+// the running total lives in the eight drain warps' registers, so the MMAs do
+// not wait while a group is drained; the sums are the same (group sums added in
+// order with round-to-nearest FP32 adds).
 #pragma once
 
 #include <cuda_bf16.h>
+
+#include <type_traits>
 
 #include "pinv_internal.h"
 
@@ -63,6 +75,14 @@ static_assert(DRAIN >= 4, "drain group must outlast the stage ring");
 // instruction descriptor, kind::f16: D f32, A/B bf16, K-major, N = 256, M = 128
 constexpr uint32_t IDESC =
     (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * BN) >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+// problems that declare `static constexpr bool kBulk = true` are bulk-fed
+template <class P, class = void>
+struct IsBulk : std::false_type {};
+template <class P>
+struct IsBulk<P, std::void_t<decltype(P::kBulk)>> : std::integral_constant<bool, P::kBulk> {};
+
+constexpr int NTHREADS_BULK = NTHREADS + 32;  // + one loader warp
 
 // slice pairs in decreasing weight: (0,0) (0,1) (1,0) (0,2) (2,0) (1,1)
 __host__ __device__ constexpr int pair_a(int q) { return q == 2 ? 1 : q == 4 ? 2 : q == 5 ? 1 : 0; }
@@ -105,6 +125,22 @@ __device__ inline void fence_proxy_async() { asm volatile("fence.proxy.async.sha
 __device__ inline void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// expect `bytes` of asynchronous copies on this phase, with this thread's arrival
+__device__ inline void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16),
+// completing `bytes` on the mbarrier
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
 
 __device__ inline void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
@@ -210,6 +246,35 @@ __device__ inline void drain_to_total(uint32_t taddr_row, bool first) {
     tmem_wait_st();
 }
 
+// Bulk mode: add (or, for a tile's first group, copy) this warp's part of an
+// MMA buffer into the running total in registers: tot[0..63] real parts of the
+// warp's 64 columns, tot[64..127] imaginary parts.
+__device__ inline void drain_to_regs(uint32_t taddr_buf, float (&tot)[128], bool first) {
+#pragma unroll
+    for (int part = 0; part < 8; ++part) {
+        uint32_t b[16];
+        tmem_ld16(taddr_buf + (uint32_t)((part & 4) ? BN : 0) + 16u * (part & 3), b);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            float& t = tot[16 * part + i];
+            t = first ? __uint_as_float(b[i]) : t + __uint_as_float(b[i]);
+        }
+    }
+}
+
+// ... and write the totals back to TMEM (the same columns of a free buffer) for the epilogue
+__device__ inline void regs_to_tmem(uint32_t taddr_buf, const float (&tot)[128]) {
+#pragma unroll
+    for (int part = 0; part < 8; ++part) {
+        uint32_t b[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) b[i] = __float_as_uint(tot[16 * part + i]);
+        tmem_st16(taddr_buf + (uint32_t)((part & 4) ? BN : 0) + 16u * (part & 3), b);
+    }
+    tmem_wait_st();
+}
+
 // Tile schedulers of the persistent kernel: item t -> (problem, bx, by).
 // OneProblem covers a gx x gy grid of tiles of one problem; ManyProblems
 // concatenates the tile grids of several problems (e.g. one per plan of a
@@ -218,6 +283,7 @@ __device__ inline void drain_to_total(uint32_t taddr_row, bool first) {
 // operand first, so they do not form the tail).
 template <class P>
 struct OneProblem {
+    using Prob = P;
     P p;
     int64_t gx, n;
     bool rev;
@@ -232,6 +298,7 @@ struct OneProblem {
 
 template <class P>
 struct ManyProblems {
+    using Prob = P;
     const P* probs;         // [n]
     const int64_t* start;   // [n + 1], first item of each problem
     const int64_t* gx;      // [n], tile-grid width of each problem
@@ -455,22 +522,201 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, in
     }
 }
 
+// Persistent kernel for bulk-fed problems. Warps 0-7 drain the MMA buffers into
+// register totals and run the epilogue, warp 8 issues the MMAs, warp 9 loads
+// the stages. Item scheduling, the stage ring and the bounded waits follow k_tc.
+template <int S, class Sched>
+__global__ void __launch_bounds__(NTHREADS_BULK, 1) k_tc_bulk(Sched sch, DevStatus* st, int site) {
+    using CF = Cfg<S>;
+    constexpr uint32_t STAGE_TX = (uint32_t)CF::STAGE_BYTES;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full_bar[CF::STAGES], empty_bar[CF::STAGES];
+    __shared__ uint64_t tfull[2], tempty[2], done_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_flag;
+    __shared__ long long next_item;
+
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CF::STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);  // the loader's arrival plus the stage's bytes
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], NPW * 32);
+        }
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
+        next_item = (long long)atomicAdd(&st->sched_next, 1ull);
+        fence_barrier_init();
+    }
+    if (warp == NPW) tmem_alloc(&tmem_base_sh, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+    const int q = warp & 3, h = (warp >> 2) & 1;
+    const uint32_t taddr_row = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(64 * h);
+
+    const int64_t items = sch.count();
+    uint32_t kq = 0, gq = 0;  // stages and accumulation groups used by earlier tiles
+    uint32_t issued = 0;      // stages the loader has started
+    for (int64_t t = next_item;;) {
+        if (t >= items) break;
+        int64_t bx, by;
+        const auto& p = sch.get(t, bx, by);
+        int64_t i0, j0, kb, ke;
+        if (!p.tile(bx, by, i0, j0, kb, ke)) {
+            __syncthreads();
+            if (threadIdx.x == 0) next_item = (long long)atomicAdd(&st->sched_next, 1ull);
+            __syncthreads();
+            t = next_item;
+            continue;
+        }
+        const int nk = ke > kb ? (int)((ke - kb + KC - 1) / KC) : 0;
+        const int ngroups = (nk + DRAIN - 1) / DRAIN;
+
+        if (warp < NPW) {
+            // ---------------- drains and epilogue
+            float tot[128];
+#pragma unroll
+            for (int u = 0; u < 128; ++u) tot[u] = 0.f;
+            bool ok = true;
+            for (int g = 0; g < ngroups; ++g) {
+                const uint32_t G = gq + (uint32_t)g, b = G & 1u;
+                if (!(ok = mbar_wait(&tfull[b], (G >> 1) & 1u, &abort_flag))) break;
+                tc_fence_after();
+                drain_to_regs(taddr_row + 2u * BN * b, tot, g == 0);
+                tc_fence_before();
+                mbar_arrive(&tempty[b]);
+            }
+            if (ok && !abort_flag) {
+                // every group is drained and the MMAs of the next tile wait for the
+                // tile barrier, so buffer 0 is free to hold the totals
+                regs_to_tmem(taddr_row, tot);
+                const int64_t gi = i0 + q * 32 + lane;
+#pragma unroll 1
+                for (int part = 0; part < 4; ++part) {
+                    uint32_t cr[16], ci[16];
+                    tmem_ld16(taddr_row + 16 * part, cr);
+                    tmem_ld16(taddr_row + BN + 16 * part, ci);
+                    tmem_wait_ld();
+                    if (p.row_ok(gi)) {
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            const int64_t gj = j0 + 64 * h + 16 * part + u;
+                            if (p.col_ok(gj))
+                                p.store(gi, gj, make_float2(__uint_as_float(cr[u]), __uint_as_float(ci[u])));
+                        }
+                    }
+                }
+                tc_fence_before();
+            }
+        } else if (warp == NPW && lane == 0) {
+            // ---------------- MMA issuer
+            for (int kt = 0; kt < nk; ++kt) {
+                const uint32_t G = gq + (uint32_t)(kt / DRAIN), b = G & 1u;
+                const bool first = (kt % DRAIN) == 0;
+                // buffer b was last used by group G - 2: it must be drained
+                if (first && G >= 2 && !mbar_wait(&tempty[b], ((G >> 1) - 1u) & 1u, &abort_flag)) break;
+                const uint32_t kg = kq + (uint32_t)kt;
+                const int s = (int)(kg % CF::STAGES);
+                const uint32_t ph = (kg / CF::STAGES) & 1u;
+                if (!mbar_wait(&full_bar[s], ph, &abort_flag)) break;
+                tc_fence_after();
+                const uint32_t sbase = smem_u32(smem + s * CF::STAGE_BYTES);
+                const uint32_t dcol = tmem + 2u * BN * b;
+#pragma unroll
+                for (int pq = 0; pq < CF::NPAIRS; ++pq) {
+                    const uint32_t a = sbase + pair_a(pq) * SLICE;
+                    const uint32_t bsl = sbase + pair_b(pq) * SLICE + A_SL;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint64_t da = sdesc(a + kk * 256, 128, 512);
+                        const uint64_t db = sdesc(bsl + kk * 256, 128, 512);
+                        mma_bf16(dcol, da, db, IDESC, (first && pq == 0 && kk == 0) ? 0u : 1u);
+                    }
+                }
+                mma_commit(&empty_bar[s]);
+                if ((kt % DRAIN) == DRAIN - 1 || kt == nk - 1) mma_commit(&tfull[b]);
+            }
+        } else if (warp == NPW + 1 && lane == 0) {
+            // ---------------- loader
+            const int64_t kc0 = kb / KC;
+            for (int kt = 0; kt < nk; ++kt) {
+                const uint32_t kg = kq + (uint32_t)kt;
+                const int s = (int)(kg % CF::STAGES);
+                const uint32_t ph = (kg / CF::STAGES) & 1u;
+                if (kg >= CF::STAGES && !mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) break;
+                uint8_t* base = smem + s * CF::STAGE_BYTES;
+                mbar_arrive_expect_tx(&full_bar[s], STAGE_TX);
+#pragma unroll
+                for (int sl = 0; sl < S; ++sl) {
+                    bulk_g2s(base + sl * SLICE, p.bulk_a(i0, kc0 + kt, sl), A_SL, &full_bar[s]);
+                    bulk_g2s(base + sl * SLICE + A_SL, p.bulk_b(j0, kc0 + kt, sl), B_SL, &full_bar[s]);
+                }
+                issued = kg + 1;
+            }
+        }
+        kq += (uint32_t)nk;
+        gq += (uint32_t)ngroups;
+        __syncthreads();
+        if (threadIdx.x == 0) next_item = abort_flag ? (long long)items : (long long)atomicAdd(&st->sched_next, 1ull);
+        __syncthreads();
+        t = next_item;
+    }
+    if (warp == NPW && lane == 0) mma_commit(&done_bar);
+    if (warp == NPW + 1 && lane == 0) {
+        // copies still in flight (only after an abort): wait, bounded, for their bytes
+        for (uint32_t kg = issued > (uint32_t)CF::STAGES ? issued - CF::STAGES : 0u; kg < issued; ++kg)
+            mbar_wait(&full_bar[kg % CF::STAGES], (kg / CF::STAGES) & 1u, nullptr);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == NPW) {
+        mbar_wait(&done_bar, 0, nullptr);
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+    if (threadIdx.x == 0) {
+        if (abort_flag) atomicMax(&st->timeout_site, site);
+        __threadfence();
+        if (atomicAdd(&st->sched_done, 1ull) == (unsigned long long)gridDim.x - 1) {
+            st->sched_next = 0;
+            st->sched_done = 0;
+            __threadfence();
+        }
+    }
+}
+
 int sm_count();
 
-template <int S, class Sched>
-static cudaError_t launch_sched(const Sched& sch, int64_t items, DevStatus* st, int site, cudaStream_t s) {
-    static bool attr = false;
+template <class K, class... A>
+static cudaError_t launch_persistent(K kern, int threads, int smem, bool& attr, int64_t items, cudaStream_t s,
+                                     const A&... args) {
     if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_tc<S, Sched>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<S>::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     if (items == 0) return cudaSuccess;
     const int64_t ctas = items < sm_count() ? items : sm_count();
-    k_tc<S, Sched><<<(unsigned)ctas, NTHREADS, Cfg<S>::SMEM, s>>>(sch, st, site);
+    kern<<<(unsigned)ctas, threads, smem, s>>>(args...);
     note_launch();
     return cudaGetLastError();
+}
+
+template <int S, class Sched>
+static cudaError_t launch_sched(const Sched& sch, int64_t items, DevStatus* st, int site, cudaStream_t s) {
+    static bool attr = false;
+    if constexpr (IsBulk<typename Sched::Prob>::value)
+        return launch_persistent(k_tc_bulk<S, Sched>, NTHREADS_BULK, Cfg<S>::SMEM, attr, items, s, sch, st, site);
+    else
+        return launch_persistent(k_tc<S, Sched>, NTHREADS, Cfg<S>::SMEM, attr, items, s, sch, st, site);
 }
 
 // One problem over a grid.x x grid.y grid of tiles (bx = x, by = y). Launches

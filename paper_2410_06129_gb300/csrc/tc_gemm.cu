@@ -75,9 +75,15 @@ __device__ inline VoxRow vox_row(const EncodeDev& e, int64_t n) {
     r.b = e.b0t32 ? e.b0t32 + nn * e.T : nullptr;
     return r;
 }
-// A[m0 .. m0+7][n] (m0 a multiple of 8; table rows are padded to a multiple of 8)
+// A[m0 .. m0+7][n] (m0 a multiple of 8, ke <= M_k; table rows are padded to a
+// multiple of 8, so m0 < ke keeps all eight reads inside the row)
 __device__ inline void gen_a8_samples(const EncodeDev& e, const VoxRow& r, int64_t m0, int64_t ke,
                                       float2 (&v)[8]) {
+    if (!r.ok || m0 >= ke) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = make_float2(0.f, 0.f);
+        return;
+    }
     ld8a(r.x + m0, v);
     if (r.y) {
         float2 w[8];
@@ -177,7 +183,38 @@ __device__ inline void gen_eh8_voxels(const EncodeDev& e, const EhCol& r, int64_
 }
 
 // ------------------------------------------------------------------ Gram (Eq. 6, Eq. 11)
-// G[i][j] = (sum_m conj(A[m][i]) A[m][j]) * (sum_c conj(s_c(i)) s_c(j)) + lam delta_ij, lower part
+// G[i][j] = (sum_m conj(A[m][i]) A[m][j]) * (sum_c conj(s_c(i)) s_c(j)) + lam delta_ij, lower part.
+// v is the sample sum (A^H A)_ij; j > i is not stored.
+__device__ inline void gram_store(const EncodeDev& e, double lam, double2* G, int64_t ld, int64_t i, int64_t j,
+                                  float2 v) {
+    if (j > i) return;
+    if (i == j) {
+        // every encoding element is a unit phasor, so (A^H A)_ii = M_k exactly;
+        // the diagonal is written in FP64 rather than from the accumulator
+        double s = 1.0;
+        if (e.coils) {
+            s = 0.0;
+            for (int c = 0; c < e.C; ++c) {
+                const double2 a = e.coils[(int64_t)c * e.N + i];
+                s += a.x * a.x + a.y * a.y;
+            }
+        }
+        G[i * ld + i] = make_double2((double)e.Mk * s + lam, 0.0);
+        return;
+    }
+    if (e.coils32) {
+        float2 sc = make_float2(0.f, 0.f);
+        for (int c = 0; c < e.C; ++c) {
+            const float2 a = conjf2(e.coils32[(int64_t)c * e.N + i]);
+            const float2 b = e.coils32[(int64_t)c * e.N + j];
+            sc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, sc.x));
+            sc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, sc.y));
+        }
+        v = cmulf(v, sc);
+    }
+    G[i * ld + j] = make_double2((double)v.x, (double)v.y);
+}
+
 struct GramTC {
     EncodeDev e;
     double lam;
@@ -202,33 +239,88 @@ struct GramTC {
     }
     __device__ bool row_ok(int64_t i) const { return i < e.N; }
     __device__ bool col_ok(int64_t j) const { return j < e.N; }
+    __device__ void store(int64_t i, int64_t j, float2 v) const { gram_store(e, lam, G, ld, i, j, v); }
+};
+
+// ------------------------------------------------------------------ Gram, bulk-fed
+// The encoding A is generated once into a table of stage tiles, each split into
+// S bf16 slices: block (row tile rt, sample chunk kc, slice s), 16 KiB, holds
+// T1 = rows [Re A | -Im A] over the chunk's 16 samples (the A operand conj(A)
+// and the first half of the B operand) and T2 = rows [Im A | Re A] (the second
+// half of the B operand), both in the stage layout. The Gram kernel then only
+// copies: per stage T1 of row tile i and T1|T2 of column tile j, per slice.
+// Items are (split, i, j) with the sample range cut into `splits` parts (so
+// that the last wave of tiles is not mostly idle), visited in bands of GBAND
+// row tiles, column-major inside a band (the tiles running at one time share
+// few rows and columns, which stay in L2). With one split the epilogue writes G
+// directly; otherwise it writes FP32 partial sums that k_gram_finalize adds in
+// split order.
+constexpr int GBAND = 8;
+constexpr int64_t TAB_BLOCK = 2 * A_SL;
+
+template <int S>
+__global__ void __launch_bounds__(256) k_gram_tab(EncodeDev e, int64_t kcn, uint8_t* tab) {
+    const int64_t kc = blockIdx.x, rt = blockIdx.y;
+    const int r = threadIdx.x & (BM - 1), g = threadIdx.x >> 7;
+    float2 v[8];
+    gen_a8_samples(e, vox_row(e, rt * BM + r), kc * KC + 8 * g, e.Mk, v);
+    float re[8], im[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) { re[u] = v[u].x; im[u] = v[u].y; }
+    uint32_t wr[S][4], wi[S][4];
+    split8<S>(re, wr);
+    split8<S>(im, wi);
+    uint8_t* blk = tab + (rt * kcn + kc) * S * TAB_BLOCK;
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+        uint8_t* b = blk + sl * TAB_BLOCK;
+        const uint32_t f = 0x80008000u;
+        *reinterpret_cast<uint4*>(b + koff(r, g)) = make_uint4(wr[sl][0], wr[sl][1], wr[sl][2], wr[sl][3]);
+        *reinterpret_cast<uint4*>(b + koff(r, g + 2)) =
+            make_uint4(wi[sl][0] ^ f, wi[sl][1] ^ f, wi[sl][2] ^ f, wi[sl][3] ^ f);
+        *reinterpret_cast<uint4*>(b + A_SL + koff(r, g)) = make_uint4(wi[sl][0], wi[sl][1], wi[sl][2], wi[sl][3]);
+        *reinterpret_cast<uint4*>(b + A_SL + koff(r, g + 2)) =
+            make_uint4(wr[sl][0], wr[sl][1], wr[sl][2], wr[sl][3]);
+    }
+}
+
+struct GramBulk {
+    static constexpr bool kBulk = true;
+    EncodeDev e;
+    double lam;
+    double2* G;          // splits == 1: the lower part of G
+    int64_t ld;
+    float2* part;        // splits > 1: partial sums [split][NP][NP], NP = nt * BM
+    const uint8_t* tab;  // [nt][kcn][S] blocks
+    int64_t nt, kcn, kcs;  // row tiles, sample chunks, chunks per split
+    int S, splits;
+    __device__ bool tile(int64_t bx, int64_t, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        const int64_t per = nt * nt;
+        const int64_t sp = bx / per, l = bx - sp * per;
+        const int64_t band = l / (GBAND * nt), l2 = l - band * GBAND * nt;
+        const int64_t hgt = nt - band * GBAND < GBAND ? nt - band * GBAND : GBAND;
+        const int64_t jt = l2 / hgt, it = band * GBAND + l2 % hgt;
+        i0 = (sp * nt + it) * BM;  // the split rides on the row coordinate
+        j0 = jt * BN;
+        kb = sp * kcs * KC;
+        ke = ((sp + 1) * kcs < kcn ? (sp + 1) * kcs : kcn) * KC;
+        return jt <= it && kb < ke;
+    }
+    __device__ const uint8_t* bulk_a(int64_t i0, int64_t kc, int sl) const {
+        return tab + ((((i0 / BM) % nt) * kcn + kc) * S + sl) * TAB_BLOCK;
+    }
+    __device__ const uint8_t* bulk_b(int64_t j0, int64_t kc, int sl) const {
+        return tab + (((j0 / BN) * kcn + kc) * S + sl) * TAB_BLOCK;
+    }
+    __device__ bool row_ok(int64_t i) const { return i % (nt * BM) < e.N; }
+    __device__ bool col_ok(int64_t j) const { return j < e.N; }
     __device__ void store(int64_t i, int64_t j, float2 v) const {
-        if (j > i) return;
-        if (i == j) {
-            // every encoding element is a unit phasor, so (A^H A)_ii = M_k exactly;
-            // the diagonal is written in FP64 rather than from the accumulator
-            double s = 1.0;
-            if (e.coils) {
-                s = 0.0;
-                for (int c = 0; c < e.C; ++c) {
-                    const double2 a = e.coils[(int64_t)c * e.N + i];
-                    s += a.x * a.x + a.y * a.y;
-                }
-            }
-            G[i * ld + i] = make_double2((double)e.Mk * s + lam, 0.0);
-            return;
-        }
-        if (e.coils32) {
-            float2 sc = make_float2(0.f, 0.f);
-            for (int c = 0; c < e.C; ++c) {
-                const float2 a = conjf2(e.coils32[(int64_t)c * e.N + i]);
-                const float2 b = e.coils32[(int64_t)c * e.N + j];
-                sc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, sc.x));
-                sc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, sc.y));
-            }
-            v = cmulf(v, sc);
-        }
-        G[i * ld + j] = make_double2((double)v.x, (double)v.y);
+        const int64_t np = nt * BM, il = i % np;
+        if (j > il) return;
+        if (splits > 1)
+            part[i * np + j] = v;
+        else
+            gram_store(e, lam, G, ld, il, j, v);
     }
 };
 
@@ -465,6 +557,77 @@ cudaError_t launch_gram_tc(const EncodeDev& e, double lambda, int slices, double
                            DevStatus* st, cudaStream_t s) {
     tc::GramTC p{e, lambda, G, ld};
     return run(p, dim3(cdiv(e.N, tc::BN), cdiv(e.N, tc::BM)), slices, st, 1, s);
+}
+
+// G[i][j] (j <= i) from the partial sample sums of the bulk Gram, added in split order
+__global__ void k_gram_finalize(EncodeDev e, double lam, const float2* __restrict__ part, int splits, int64_t np,
+                                double2* G, int64_t ld) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= e.N * e.N) return;
+    const int64_t i = idx / e.N, j = idx - i * e.N;
+    if (j > i) return;
+    float2 v = part[i * np + j];
+    for (int sp = 1; sp < splits; ++sp) {
+        const float2 w = part[(sp * np + i) * np + j];
+        v.x += w.x;
+        v.y += w.y;
+    }
+    tc::gram_store(e, lam, G, ld, i, j, v);
+}
+
+namespace {
+struct GramBulkShape {
+    int64_t nt, kcn, kcs;
+    int splits;
+};
+// sample-range splits: the fewest (up to 4) that fill the last wave of tiles to 90 %
+GramBulkShape gram_bulk_shape(const EncodeDev& e) {
+    GramBulkShape g;
+    g.nt = (e.N + tc::BM - 1) / tc::BM;
+    g.kcn = (e.Mk + tc::KC - 1) / tc::KC;
+    const int64_t tiles = g.nt * (g.nt + 1) / 2, sms = tc::sm_count();
+    g.splits = 1;
+    for (int sp = 1; sp <= 4; ++sp) {
+        const int64_t items = tiles * sp, waves = (items + sms - 1) / sms;
+        g.splits = sp;
+        if ((double)items >= 0.9 * (double)(waves * sms) || g.kcn < 64 * (sp + 1)) break;
+    }
+    g.kcs = (g.kcn + g.splits - 1) / g.splits;
+    return g;
+}
+}  // namespace
+
+size_t gram_bulk_bytes(const EncodeDev& e, int slices) {
+    const GramBulkShape g = gram_bulk_shape(e);
+    const size_t np = (size_t)g.nt * tc::BM;
+    return (size_t)g.nt * g.kcn * slices * tc::TAB_BLOCK + (g.splits > 1 ? g.splits * np * np * sizeof(float2) : 0);
+}
+
+cudaError_t launch_gram_bulk(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld, void* work,
+                             DevStatus* st, cudaStream_t s) {
+    const GramBulkShape g = gram_bulk_shape(e);
+    uint8_t* tab = (uint8_t*)work;
+    const size_t tab_bytes = (size_t)g.nt * g.kcn * slices * tc::TAB_BLOCK;
+    float2* part = g.splits > 1 ? (float2*)(tab + tab_bytes) : nullptr;
+    const dim3 tg((unsigned)g.kcn, (unsigned)g.nt);
+    if (slices == 3)
+        tc::k_gram_tab<3><<<tg, 256, 0, s>>>(e, g.kcn, tab);
+    else
+        tc::k_gram_tab<2><<<tg, 256, 0, s>>>(e, g.kcn, tab);
+    note_launch();
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    tc::GramBulk p{e, lambda, G, ld, part, tab, g.nt, g.kcn, g.kcs, slices, g.splits};
+    const int64_t items = g.splits * g.nt * g.nt;
+    if ((err = run(p, dim3((unsigned)items, 1), slices, st, 1, s)) != cudaSuccess) return err;
+    if (g.splits > 1) {
+        const int64_t n = e.N * e.N;
+        k_gram_finalize<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(e, lambda, part, g.splits, g.nt * tc::BM, G,
+                                                                     ld);
+        note_launch();
+        err = cudaGetLastError();
+    }
+    return err;
 }
 
 // Two-level blocking: 64-wide diagonal blocks inside 256-wide panels. Inside a

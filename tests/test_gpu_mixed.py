@@ -44,6 +44,32 @@ def test_gram_tc_small_ragged(prec):
     assert rel(np.tril(G), np.tril(ref.G)) < SPLIT_TOL[prec]
 
 
+def _gram(p, prec):
+    pl = _plan(p, precision=prec, keep_gram=True, refine_max_iters=0).build()
+    return np.tril(pl.export(L.EXPORT_GRAM).cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", [L.MIXED_BF16X6, L.MIXED_BF16X3])
+def test_gram_bulk_bit_identical_to_generated(prec, monkeypatch):
+    """One sample split: the bulk-fed Gram copies the very slices the generating
+    kernel writes and sums them in the same MMA and drain order, so G is the same
+    bit for bit. M_k = 808 (a last sample chunk half full), N = 441 (ragged)."""
+    p = synth.make_plan(21, 2, "spiral", 1, 2107, 1e-3, samples=808, interleaves=2, b0=True)
+    g_bulk = _gram(p, prec)
+    monkeypatch.setenv("PINV_GRAM_BULK", "0")
+    g_gen = _gram(p, prec)
+    assert np.array_equal(g_bulk, g_gen)
+    assert rel(g_bulk, np.tril(oracle_all(p).G)) < SPLIT_TOL[prec]
+
+
+def test_gram_bulk_split_samples():
+    """32x32, 4 coils, 4096 samples: 36 lower tiles are too few for the SMs, so
+    the sample range is cut into parts whose FP32 partial sums are added in
+    order; G stays within the split bound of the oracle."""
+    p = synth.make_plan(32, 4, "spiral", 1, 2111, 1e-4, samples=4096, interleaves=2)
+    assert rel(_gram(p, L.MIXED_BF16X6), np.tril(oracle_all(p).G)) < SPLIT_TOL[L.MIXED_BF16X6]
+
+
 @pytest.mark.parametrize("prec", [L.MIXED_BF16X6, L.MIXED_BF16X3])
 def test_recon_tc_isolated(prec):
     """Recon = W^H (W E^H) with the plan's own W = L^-1: isolates the tensor-core kernels.
