@@ -429,35 +429,39 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         build_s, apply_s, step_s = t.tolist()
 
-    # dominant kernel: Recon formation (one launch per build)
+    # dominant kernel: Recon formation
     N, M = inp.n_vox, inp.n_samples * inp.n_coils
-    ms_recon = statistics.mean(i["ms_recon"] for i in infos) / (1 if prec == L.FP64 else 2)
     ms_gram = statistics.mean(i["ms_gram"] for i in infos)
-    flops_recon = 8.0 * N * N * M / (1 if prec == L.FP64 else 2)  # per launch
+    ms_recon_stage = statistics.mean(i["ms_recon"] for i in infos)
     peaks, peak_src = _peaks()
     if prec == L.FP64:
-        roof = {"kernel": "recon (FP64 SIMT, generated E^H)", "bound": "alu",
+        ms_recon = ms_recon_stage
+        flops_recon = 8.0 * N * N * M  # one launch
+        roof = {"kernel": "recon (FP64 SIMT, generated E^H)", "bound": "alu", "launches": 1,
                 "achieved": flops_recon / (ms_recon / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"}
     else:
+        # two triangular products, each N^2 M / 2 CMAC, over `chunks` ranges of samples:
+        # 2 x chunks launches of equal work; the stage time also holds the operand-table
+        # kernels, so the per-launch rate below is a lower bound
+        nt, mt = -(-N // 128), -(-M // 128)
+        slices = 3 if prec == L.MIXED_BF16X6 else 2
+        per_tile = 2 * (nt * 8) * slices * 8192  # ET + TT bytes per 128 samples (4 GiB per chunk)
+        cap = max(1, (4 << 30) // per_tile)
+        chunks = -(-mt // cap)
+        launches_r = 2 * chunks
+        ms_recon = ms_recon_stage / launches_r
+        flops_recon = 8.0 * N * N * M / launches_r
         pk = peaks.get("bf16_tflops_sustained", 1700.0)
-        # two launches of equal work (W E^H, then W^H T), each N^2 M / 2 CMAC
-        roof = {"kernel": "recon_tc (split-BF16 tcgen05; W E^H then W^H T, E generated)",
-                "bound": "tensor", "launches": 2,
+        roof = {"kernel": "recon_tc (split-BF16 tcgen05, bulk-copied operand tables: "
+                          "T^T = conj(E) W^T, then Recon^T = T^T conj(W))",
+                "bound": "tensor", "launches": launches_r,
                 "achieved": flops_recon / (ms_recon / 1e3) / 1e12, "peak": pk, "unit": "TFLOP/s",
                 "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "issued_tflops": 6 * flops_recon / (ms_recon / 1e3) / 1e12}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    if prec != L.FP64:
-        # DRAM bytes (read + write) of the two mixed Recon launches measured by ncu at
-        # 48x48, 8 coils (N = 2304, M = 36864); Recon traffic grows with N*M (T and
-        # Recon are [N][M]), so it is scaled to this workload. Valid for the current
-        # Recon kernels only.
-        nm_ref, bytes_ref = 2304.0 * 36864.0, 38490368 + 632123392 + 770332672 + 649221888
-        roof["traffic"] = bytes_ref * (float(N) * M / nm_ref) / 2
-        roof["traffic_source"] = "ncu dram bytes at 48x48 scaled by N*M, mean per launch"
-        roof["algorithmic_bytes"] = 3.0 * N * M * 8 / 2
+    roof["traffic_source"] = "not measured for the current kernels"
     roof["ms_per_launch"] = ms_recon
 
     # the tensor-core Gram kernels alone (operand table + Gram launch + split sum)

@@ -132,14 +132,25 @@ pinv_status build_recon(pinv_plan* p, cudaStream_t s) {
     if (!p->recon) return PINV_OK;
     const int64_t N = p->N;
     if (p->precision != PINV_FP64) {
-        // Recon = W^H (W E^H) (Eq. 8) through an [N][M] c64 intermediate
-        float2 *T = nullptr, *WT32 = nullptr;
-        CK(cudaMallocAsync((void**)&T, sizeof(float2) * N * p->M, s));
-        CK(cudaMallocAsync((void**)&WT32, sizeof(float2) * N * N, s));
-        CK(launch_transpose32(p->W32, N, N, WT32, N, s));
-        CK(launch_recon_tc(p->enc, p->W32, WT32, T, p->slices(), (float2*)p->R, p->st, s));
-        CK(cudaFreeAsync(WT32, s));
-        CK(cudaFreeAsync(T, s));
+        // Recon = W^H (W E^H) (Eq. 8): bulk-fed from split operand tables, or (no
+        // room for the tables, or PINV_RECON_BULK=0) with operands generated in the
+        // kernels through an [N][M] c64 intermediate
+        void* work = nullptr;
+        const char* env = std::getenv("PINV_RECON_BULK");
+        const bool bulk = !(env && std::strcmp(env, "0") == 0);
+        if (bulk && cudaMallocAsync(&work, recon_bulk_bytes(p->enc, p->slices()), s) == cudaSuccess) {
+            CK(launch_recon_bulk(p->enc, p->W32, p->slices(), (float2*)p->R, work, p->st, s));
+            CK(cudaFreeAsync(work, s));
+        } else {
+            cudaGetLastError();
+            float2 *T = nullptr, *WT32 = nullptr;
+            CK(cudaMallocAsync((void**)&T, sizeof(float2) * N * p->M, s));
+            CK(cudaMallocAsync((void**)&WT32, sizeof(float2) * N * N, s));
+            CK(launch_transpose32(p->W32, N, N, WT32, N, s));
+            CK(launch_recon_tc(p->enc, p->W32, WT32, T, p->slices(), (float2*)p->R, p->st, s));
+            CK(cudaFreeAsync(WT32, s));
+            CK(cudaFreeAsync(T, s));
+        }
     } else {
         CK(launch_recon64(p->enc, p->Ginv, N, (double2*)p->R, s));
     }

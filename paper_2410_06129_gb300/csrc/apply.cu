@@ -80,10 +80,11 @@ size_t apply_scratch_layout(const pinv_plan* p, int64_t F, int dtype, void* base
     s.d64 = need_d64 ? cv.take<float2>((size_t)(F * M)) : nullptr;
     s.x64 = need_x64 ? cv.take<float2>((size_t)(F * N)) : nullptr;
     s.norms = md.stop_rule ? cv.take<double>((size_t)(2 * F)) : nullptr;
-    if (md.mixed && p->recon && apply_tc_ok(F)) {
-        s.apw = cv.take<float2>(apply_tc_work_elems(N, M, F));
-        s.sched = cv.take<DevStatus>(1);
-    }
+    const bool atc = md.mixed && p->recon && apply_tc_ok(F);
+    const bool ctc = md.mixed && (md.dfres || md.toep || !p->recon) && correct_tc_ok(F);
+    if (atc) s.apw = cv.take<float2>(apply_tc_work_elems(N, M, F));
+    if (ctc) s.cw = cv.take<float2>(correct_tc_work_elems(N, F));
+    if (atc || ctc) s.sched = cv.take<DevStatus>(1);
     if (md.dfres || md.toep || md.need_b) {
         // E^H u (rows N, length M), E x (rows M, length N), G x (rows N, length N),
         // and the exact tensor-core E^H d
@@ -126,6 +127,12 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
         D = sc.d128;
     }
     double2* X = dtype == PINV_C128 ? (double2*)d_image : sc.x128;
+    if (sc.sched) CKA(cudaMemsetAsync(sc.sched, 0, sizeof(DevStatus), s));
+    // x += W^H (W r) with the FP32 W: on the tensor cores for 16 or more frames
+    auto correct = [&](const double2* r) -> cudaError_t {
+        if (sc.cw) return launch_correct_tc(p->W32, N, r, F, sc.x64, X, sc.cw, p->slices(), sc.sched, s);
+        return launch_correct32(p->W32, N, r, F, sc.x64, X, s);
+    };
 
     if (md.need_b) {  // b = E^H d, exactly on the tensor cores where possible
         if (sc.xadj) CKA(launch_adjoint_exact(p->enc, D, F, sc.fexp, sc.b128, sc.dfw, p->st, s));
@@ -147,7 +154,6 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
         }
         // the refinement removes this product's rounding: split-BF16 on the tensor cores
         if (sc.apw) {
-            CKA(cudaMemsetAsync(sc.sched, 0, sizeof(DevStatus), s));
             CKA(launch_apply_tc((const float2*)p->R, N, M, D32, F, sc.x64, sc.apw, p->slices(), sc.sched, s));
         }
         else CKA(launch_apply32((const float2*)p->R, N, M, D32, F, sc.x64, s));
@@ -160,7 +166,7 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
     } else {
         // factor-only: x = W^H (W b) with b = E^H d in double-float
         CKA(cudaMemsetAsync(X, 0, sizeof(double2) * F * N, s));
-        CKA(launch_correct32(p->W32, N, sc.b128, F, sc.x64, X, s));
+        CKA(correct(sc.b128));
     }
 
     // Residual refinement: r = E^H (d - E x) - lambda x (= E^H d - G x), then
@@ -191,7 +197,7 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
             if (md.stop_rule) CKA(launch_frame_norms(sc.r128, F, N, sc.norms, s));
             if (md.dfres || md.toep) {
                 // the correction only preconditions the next residual: FP32 W suffices
-                CKA(launch_correct32(p->W32, N, sc.r128, F, sc.x64, X, s));
+                CKA(correct(sc.r128));
             } else if (md.mixed) {
                 // x += W^H (W r) in FP64: never through an explicitly formed low-precision
                 // G^-1, whose error the correction would amplify by kappa(G)

@@ -2,8 +2,9 @@
 //
 // A batch groups existing plans (many slices, time series or trajectories).
 // Its build runs the dominant tensor-core work of all plans as shared
-// persistent launches: one launch forms every plan's Gram, one forms every
-// plan's T = W E^H and one every plan's Recon = W^H T; the sequential
+// persistent launches: one launch forms every plan's Gram, and per chunk of
+// samples one launch forms every plan's T = W E^H and one every plan's
+// Recon = W^H T (all bulk-fed from per-plan operand tables); the sequential
 // Cholesky and triangular inverse of each plan run concurrently on per-plan
 // streams between them. Its apply runs every plan's apply (Recon x data plus
 // refinement) concurrently on the per-plan streams. With PINV_BATCH_GRAPH the
@@ -27,10 +28,11 @@ struct pinv_batch {
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr;
-    // tensor-core intermediates of the explicit-Recon plans (T = W E^H, W^T)
+    // per-plan operand tables (the Gram's, then the Recon's, in the same memory)
     void* work = nullptr;
-    std::vector<float2*> T, WT32;
-    TcMulti gram, rec1, rec2;
+    std::vector<void*> pwork;
+    TcMulti gram;
+    std::vector<TcMulti> rec1, rec2;  // per chunk of samples
     DevStatus* st = nullptr;
     DevStatus* st_host = nullptr;
     // graphs: the build is captured on its second call (the first runs
@@ -50,8 +52,8 @@ pinv_batch::~pinv_batch() {
     if (build_exec) cudaGraphExecDestroy(build_exec);
     if (apply_exec) cudaGraphExecDestroy(apply_exec);
     tc_multi_free(&gram);
-    tc_multi_free(&rec1);
-    tc_multi_free(&rec2);
+    for (auto& m : rec1) tc_multi_free(&m);
+    for (auto& m : rec2) tc_multi_free(&m);
     if (work) cudaFree(work);
     for (void* p : scratch)
         if (p) cudaFree(p);
@@ -100,17 +102,27 @@ pinv_status build_sequence(pinv_batch* b, cudaStream_t s) {
     CKB(launch_reset_status(b->st, s));
     for (auto* p : b->plans) STB(build_begin(p, s));
     if (b->mixed) {
+        const size_t n = b->plans.size();
+        for (size_t i = 0; i < n; ++i) CKB(gram_bulk_table(b->plans[i]->enc, b->slices, b->pwork[i], s));
         CKB(tc_multi_launch(b->gram, b->slices, b->st, s));  // every plan's Gram
-        for (auto* p : b->plans) STB(build_gram(p, s, false));
+        for (size_t i = 0; i < n; ++i) {
+            pinv_plan* p = b->plans[i];
+            CKB(gram_bulk_finish(p->enc, p->lambda_abs, b->slices, p->G, p->N, b->pwork[i], s));
+            STB(build_gram(p, s, false));
+        }
         STB(fork_all(b, s));
-        for (size_t i = 0; i < b->plans.size(); ++i) {
+        for (size_t i = 0; i < n; ++i) {
             pinv_plan* p = b->plans[i];
             STB(build_factor(p, b->side[i], false));
-            if (p->recon) CKB(launch_transpose32(p->W32, p->N, p->N, b->WT32[i], p->N, b->side[i]));
+            if (p->recon) CKB(recon_bulk_wtables(p->enc, p->W32, b->slices, b->pwork[i], b->side[i]));
         }
         STB(join_all(b, s));
-        CKB(tc_multi_launch(b->rec1, b->slices, b->st, s));  // every plan's W E^H
-        CKB(tc_multi_launch(b->rec2, b->slices, b->st, s));  // every plan's W^H (W E^H)
+        for (size_t c = 0; c < b->rec1.size(); ++c) {
+            for (size_t i = 0; i < n; ++i)
+                if (b->plans[i]->recon) CKB(recon_bulk_et(b->plans[i]->enc, b->slices, b->pwork[i], (int64_t)c, s));
+            CKB(tc_multi_launch(b->rec1[c], b->slices, b->st, s));  // every plan's W E^H over chunk c
+            CKB(tc_multi_launch(b->rec2[c], b->slices, b->st, s));  // every plan's W^H (W E^H)
+        }
     } else {
         STB(fork_all(b, s));
         for (size_t i = 0; i < b->plans.size(); ++i) {
@@ -207,39 +219,38 @@ pinv_status pinv_batch_create(pinv_plan* const* plans, int n, int flags, pinv_ba
             cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess)
             return bad(set_error(PINV_ERR_CUDA, "batch stream creation failed"));
     if (b->mixed) {
-        // workspace for T = W E^H and W^T of the explicit-Recon plans
+        // operand tables of every plan: the Gram's, then (same memory) the Recon's
         size_t bytes = 0;
-        std::vector<size_t> offT(n, 0), offW(n, 0);
+        std::vector<size_t> off(n, 0);
+        int64_t chunks = 0;
         for (int i = 0; i < n; ++i) {
             const pinv_plan* p = b->plans[i];
-            if (!p->recon) continue;
-            offT[i] = bytes;
-            bytes += ((size_t)p->N * p->M * sizeof(float2) + 255) & ~(size_t)255;
-            offW[i] = bytes;
-            bytes += ((size_t)p->N * p->N * sizeof(float2) + 255) & ~(size_t)255;
+            size_t need = gram_bulk_bytes(p->enc, b->slices);
+            if (p->recon) {
+                need = std::max(need, recon_bulk_bytes(p->enc, b->slices));
+                chunks = std::max(chunks, recon_bulk_chunks(p->enc, b->slices));
+            }
+            off[i] = bytes;
+            bytes += (need + 255) & ~(size_t)255;
         }
-        if (bytes) {
-            const cudaError_t e = cudaMalloc(&b->work, bytes);
-            if (e != cudaSuccess) return bad(cuda_err(e, "batch workspace"));
-        }
-        b->T.assign(n, nullptr);
-        b->WT32.assign(n, nullptr);
+        cudaError_t e = cudaMalloc(&b->work, bytes);
+        if (e != cudaSuccess) return bad(cuda_err(e, "batch workspace"));
         std::vector<TcPlanArgs> all, rec;
         for (int i = 0; i < n; ++i) {
             pinv_plan* p = b->plans[i];
-            TcPlanArgs a{&p->enc, p->lambda_abs, p->G, p->W32, nullptr, nullptr, (float2*)p->R};
-            if (p->recon) {
-                b->T[i] = (float2*)((unsigned char*)b->work + offT[i]);
-                b->WT32[i] = (float2*)((unsigned char*)b->work + offW[i]);
-                a.T = b->T[i];
-                a.WT32 = b->WT32[i];
-                rec.push_back(a);
-            }
+            b->pwork.push_back((unsigned char*)b->work + off[i]);
+            const TcPlanArgs a{&p->enc, p->lambda_abs, p->G, p->W32, (float2*)p->R, b->pwork[i]};
             all.push_back(a);
+            if (p->recon) rec.push_back(a);
         }
-        cudaError_t e = tc_multi_create(TC_MULTI_GRAM, all.data(), (int)all.size(), &b->gram);
-        if (e == cudaSuccess && !rec.empty()) e = tc_multi_create(TC_MULTI_RECON1, rec.data(), (int)rec.size(), &b->rec1);
-        if (e == cudaSuccess && !rec.empty()) e = tc_multi_create(TC_MULTI_RECON2, rec.data(), (int)rec.size(), &b->rec2);
+        e = tc_multi_create(TC_MULTI_GRAM, all.data(), (int)all.size(), b->slices, 0, &b->gram);
+        b->rec1.resize(chunks);
+        b->rec2.resize(chunks);
+        for (int64_t c = 0; c < chunks && e == cudaSuccess; ++c) {
+            e = tc_multi_create(TC_MULTI_RECON1, rec.data(), (int)rec.size(), b->slices, c, &b->rec1[c]);
+            if (e == cudaSuccess)
+                e = tc_multi_create(TC_MULTI_RECON2, rec.data(), (int)rec.size(), b->slices, c, &b->rec2[c]);
+        }
         if (e != cudaSuccess) return bad(cuda_err(e, "batch descriptors"));
     }
     *out = b;

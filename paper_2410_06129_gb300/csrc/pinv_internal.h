@@ -188,6 +188,11 @@ cudaError_t launch_gram_bulk(const EncodeDev& e, double lambda, int slices, doub
 // scratch [N][M] c64), c64 out.
 cudaError_t launch_recon_tc(const EncodeDev& e, const float2* W32, const float2* WT32, float2* T, int slices,
                             float2* R, DevStatus* st, cudaStream_t s);
+// Bulk-fed Recon from split operand tables in `work` of recon_bulk_bytes()
+// (processed in chunks of samples); same result as launch_recon_tc.
+size_t recon_bulk_bytes(const EncodeDev& e, int slices);
+cudaError_t launch_recon_bulk(const EncodeDev& e, const float2* W32, int slices, float2* R, void* work,
+                              DevStatus* st, cudaStream_t s);
 // Y[f] = W X[f] (lower W), and Y[f] = Yadd[f] + W^H X[f], FP64.
 cudaError_t launch_trmv64(const double2* W, int64_t N, const double2* X, int64_t F, double2* Y,
                           cudaStream_t s);
@@ -220,9 +225,8 @@ struct TcPlanArgs {
     double lam;
     double2* G;           // Gram output (lower tiles), ld = N
     const float2* W32;    // W = L^-1, FP32 [N][N]
-    const float2* WT32;   // W^T, FP32 [N][N]
-    float2* T;            // W E^H intermediate [N][M]
     float2* R;            // Recon [N][M]
+    void* work;           // operand tables: gram_bulk_bytes() for the Gram, recon_bulk_bytes() for Recon
 };
 enum TcMultiKind { TC_MULTI_GRAM = 0, TC_MULTI_RECON1 = 1, TC_MULTI_RECON2 = 2 };
 struct TcMulti {
@@ -231,8 +235,18 @@ struct TcMulti {
     int64_t items = 0;
     size_t off_start = 0, off_gx = 0;
 };
-cudaError_t tc_multi_create(int kind, const TcPlanArgs* args, int n, TcMulti* out);
+// Shared persistent launches of bulk-fed problems over several plans: every
+// plan's Gram, or the two Recon steps over sample chunk `chunk` of every plan
+// that has it. The per-plan stages around them (tables, split sums) are the
+// gram_bulk_* / recon_bulk_* calls.
+cudaError_t tc_multi_create(int kind, const TcPlanArgs* args, int n, int slices, int64_t chunk, TcMulti* out);
 cudaError_t tc_multi_launch(const TcMulti& m, int slices, DevStatus* st, cudaStream_t s);
+cudaError_t gram_bulk_table(const EncodeDev& e, int slices, void* work, cudaStream_t s);
+cudaError_t gram_bulk_finish(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld, void* work,
+                             cudaStream_t s);
+int64_t recon_bulk_chunks(const EncodeDev& e, int slices);
+cudaError_t recon_bulk_wtables(const EncodeDev& e, const float2* W32, int slices, void* work, cudaStream_t s);
+cudaError_t recon_bulk_et(const EncodeDev& e, int slices, void* work, int64_t chunk, cudaStream_t s);
 void tc_multi_free(TcMulti* m);
 
 // double-float frame products split their k range over CTAs; `work` holds
@@ -279,5 +293,11 @@ cudaError_t launch_adjoint_df(const EncodeDev& e, const double2* U, int64_t F, d
 // X[f] += W^H (W R[f]) in FP32 with scratch T [F][N]
 cudaError_t launch_correct32(const float2* W32, int64_t N, const double2* R, int64_t F, float2* T, double2* X,
                              cudaStream_t s);
+// The same correction on the tensor cores (split-BF16, split-K with ordered
+// partial sums; `work` of correct_tc_work_elems() float2), for 16 or more frames.
+bool correct_tc_ok(int64_t F);
+size_t correct_tc_work_elems(int64_t N, int64_t F);
+cudaError_t launch_correct_tc(const float2* W32, int64_t N, const double2* R, int64_t F, float2* T, double2* X,
+                              float2* work, int slices, DevStatus* sched, cudaStream_t s);
 
 }  // namespace pinv

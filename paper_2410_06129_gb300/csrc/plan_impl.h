@@ -27,7 +27,8 @@ struct ApplyScratch {
     int* fexp;      // per-frame exponents of the data / image [F] (exact tensor-core products)
     bool xadj;      // E^H d by the exact tensor-core kernel
     float2* apw;    // partials of the tensor-core Recon x data
-    DevStatus* sched;  // tile counter of that launch: one per scratch region, since
+    float2* cw;     // partials of the tensor-core correction x += W^H (W r)
+    DevStatus* sched;  // tile counter of those launches: one per scratch region, since
                        // applies of one plan may run concurrently on several streams
 };
 // Bytes an apply of F frames of `dtype` needs; with base != nullptr also

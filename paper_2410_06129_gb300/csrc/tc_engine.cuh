@@ -82,6 +82,17 @@ struct IsBulk : std::false_type {};
 template <class P>
 struct IsBulk<P, std::void_t<decltype(P::kBulk)>> : std::integral_constant<bool, P::kBulk> {};
 
+// ... a bulk problem may write its results 16 columns at a time (store16) and
+// ask for its B tiles to be kept in L2 (kHintB)
+template <class P, class = void>
+struct HasStore16 : std::false_type {};
+template <class P>
+struct HasStore16<P, std::void_t<decltype(&P::store16)>> : std::true_type {};
+template <class P, class = void>
+struct HintB : std::false_type {};
+template <class P>
+struct HintB<P, std::void_t<decltype(P::kHintB)>> : std::integral_constant<bool, P::kHintB> {};
+
 constexpr int NTHREADS_BULK = NTHREADS + 32;  // + one loader warp
 
 // slice pairs in decreasing weight: (0,0) (0,1) (1,0) (0,2) (2,0) (1,1)
@@ -140,6 +151,19 @@ __device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+// ... with an L2 eviction-priority policy (createpolicy)
+__device__ inline void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+__device__ inline uint64_t policy_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
 }
 
 __device__ inline void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
@@ -604,7 +628,15 @@ __global__ void __launch_bounds__(NTHREADS_BULK, 1) k_tc_bulk(Sched sch, DevStat
                     tmem_ld16(taddr_row + 16 * part, cr);
                     tmem_ld16(taddr_row + BN + 16 * part, ci);
                     tmem_wait_ld();
-                    if (p.row_ok(gi)) {
+                    if constexpr (HasStore16<std::remove_cv_t<std::remove_reference_t<decltype(p)>>>::value) {
+                        float re[16], im[16];
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            re[u] = __uint_as_float(cr[u]);
+                            im[u] = __uint_as_float(ci[u]);
+                        }
+                        p.store16(gi, j0 + 64 * h + 16 * part, re, im);
+                    } else if (p.row_ok(gi)) {
 #pragma unroll
                         for (int u = 0; u < 16; ++u) {
                             const int64_t gj = j0 + 64 * h + 16 * part + u;
@@ -645,6 +677,8 @@ __global__ void __launch_bounds__(NTHREADS_BULK, 1) k_tc_bulk(Sched sch, DevStat
             }
         } else if (warp == NPW + 1 && lane == 0) {
             // ---------------- loader
+            using PT = std::remove_cv_t<std::remove_reference_t<decltype(p)>>;
+            const uint64_t pol = HintB<PT>::value ? policy_evict_last() : 0ull;
             const int64_t kc0 = kb / KC;
             for (int kt = 0; kt < nk; ++kt) {
                 const uint32_t kg = kq + (uint32_t)kt;
@@ -656,7 +690,10 @@ __global__ void __launch_bounds__(NTHREADS_BULK, 1) k_tc_bulk(Sched sch, DevStat
 #pragma unroll
                 for (int sl = 0; sl < S; ++sl) {
                     bulk_g2s(base + sl * SLICE, p.bulk_a(i0, kc0 + kt, sl), A_SL, &full_bar[s]);
-                    bulk_g2s(base + sl * SLICE + A_SL, p.bulk_b(j0, kc0 + kt, sl), B_SL, &full_bar[s]);
+                    if constexpr (HintB<PT>::value)
+                        bulk_g2s_hint(base + sl * SLICE + A_SL, p.bulk_b(j0, kc0 + kt, sl), B_SL, &full_bar[s], pol);
+                    else
+                        bulk_g2s(base + sl * SLICE + A_SL, p.bulk_b(j0, kc0 + kt, sl), B_SL, &full_bar[s]);
                 }
                 issued = kg + 1;
             }

@@ -8,6 +8,7 @@
 // sample); a8()/b8(), 8 consecutive k of that row of A or column of B, zero
 // outside the problem; row_ok()/col_ok() and store().
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "tc_engine.cuh"
@@ -256,32 +257,69 @@ struct GramTC {
 // directly; otherwise it writes FP32 partial sums that k_gram_finalize adds in
 // split order.
 constexpr int GBAND = 8;
-constexpr int64_t TAB_BLOCK = 2 * A_SL;
+constexpr int64_t TAB_BLOCK = B_SL;  // one B slice tile (the A slice tile is its first half)
 
+// Operand tables hold stage tiles, one per (tile, 16-wide k chunk, slice):
+// A tiles (A_SL bytes) rows [re | im] of a(i, k); B tiles (B_SL bytes) rows
+// [re | -im] then [im | re] of b(k, j). A thread writes 8 consecutive k
+// (group g = 0 or 1 of the chunk) of row r in every slice.
+template <int S>
+__device__ inline void tab_split(const float2 (&v)[8], uint32_t (&wr)[S][4], uint32_t (&wi)[S][4]) {
+    float re[8], im[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        re[u] = v[u].x;
+        im[u] = v[u].y;
+    }
+    split8<S>(re, wr);
+    split8<S>(im, wi);
+}
+__device__ inline void st16(uint8_t* p, const uint32_t (&w)[4], uint32_t flip) {
+    *reinterpret_cast<uint4*>(p) = make_uint4(w[0] ^ flip, w[1] ^ flip, w[2] ^ flip, w[3] ^ flip);
+}
+template <int S>
+__device__ inline void put_a(uint8_t* blk, int r, int g, const float2 (&v)[8]) {
+    uint32_t wr[S][4], wi[S][4];
+    tab_split<S>(v, wr, wi);
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+        st16(blk + sl * A_SL + koff(r, g), wr[sl], 0u);
+        st16(blk + sl * A_SL + koff(r, g + 2), wi[sl], 0u);
+    }
+}
+template <int S>
+__device__ inline void put_b(uint8_t* blk, int r, int g, const float2 (&v)[8]) {
+    uint32_t wr[S][4], wi[S][4];
+    tab_split<S>(v, wr, wi);
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+        uint8_t* b = blk + sl * B_SL;
+        st16(b + koff(r, g), wr[sl], 0u);
+        st16(b + koff(r, g + 2), wi[sl], 0x80008000u);
+        st16(b + A_SL + koff(r, g), wi[sl], 0u);
+        st16(b + A_SL + koff(r, g + 2), wr[sl], 0u);
+    }
+}
+
+// Item l of a rows x cols tile grid, in bands of GBAND row tiles and
+// column-major inside a band: the tiles running at one time share few rows and
+// columns, whose operand tiles then stay in L2.
+__device__ inline void band_tile(int64_t l, int64_t rows, int64_t cols, int64_t& rt, int64_t& ct) {
+    const int64_t band = l / (GBAND * cols), l2 = l - band * GBAND * cols;
+    const int64_t hgt = rows - band * GBAND < GBAND ? rows - band * GBAND : GBAND;
+    ct = l2 / hgt;
+    rt = band * GBAND + l2 % hgt;
+}
+
+// Gram table: the B tiles of b(m, n) = A[m][n] over row tiles of voxels and
+// chunks of 16 samples; their first halves are the A tiles of conj(A).
 template <int S>
 __global__ void __launch_bounds__(256) k_gram_tab(EncodeDev e, int64_t kcn, uint8_t* tab) {
     const int64_t kc = blockIdx.x, rt = blockIdx.y;
     const int r = threadIdx.x & (BM - 1), g = threadIdx.x >> 7;
     float2 v[8];
     gen_a8_samples(e, vox_row(e, rt * BM + r), kc * KC + 8 * g, e.Mk, v);
-    float re[8], im[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) { re[u] = v[u].x; im[u] = v[u].y; }
-    uint32_t wr[S][4], wi[S][4];
-    split8<S>(re, wr);
-    split8<S>(im, wi);
-    uint8_t* blk = tab + (rt * kcn + kc) * S * TAB_BLOCK;
-#pragma unroll
-    for (int sl = 0; sl < S; ++sl) {
-        uint8_t* b = blk + sl * TAB_BLOCK;
-        const uint32_t f = 0x80008000u;
-        *reinterpret_cast<uint4*>(b + koff(r, g)) = make_uint4(wr[sl][0], wr[sl][1], wr[sl][2], wr[sl][3]);
-        *reinterpret_cast<uint4*>(b + koff(r, g + 2)) =
-            make_uint4(wi[sl][0] ^ f, wi[sl][1] ^ f, wi[sl][2] ^ f, wi[sl][3] ^ f);
-        *reinterpret_cast<uint4*>(b + A_SL + koff(r, g)) = make_uint4(wi[sl][0], wi[sl][1], wi[sl][2], wi[sl][3]);
-        *reinterpret_cast<uint4*>(b + A_SL + koff(r, g + 2)) =
-            make_uint4(wr[sl][0], wr[sl][1], wr[sl][2], wr[sl][3]);
-    }
+    put_b<S>(tab + (rt * kcn + kc) * S * B_SL, r, g, v);
 }
 
 struct GramBulk {
@@ -296,10 +334,9 @@ struct GramBulk {
     int S, splits;
     __device__ bool tile(int64_t bx, int64_t, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
         const int64_t per = nt * nt;
-        const int64_t sp = bx / per, l = bx - sp * per;
-        const int64_t band = l / (GBAND * nt), l2 = l - band * GBAND * nt;
-        const int64_t hgt = nt - band * GBAND < GBAND ? nt - band * GBAND : GBAND;
-        const int64_t jt = l2 / hgt, it = band * GBAND + l2 % hgt;
+        const int64_t sp = bx / per;
+        int64_t it, jt;
+        band_tile(bx - sp * per, nt, nt, it, jt);
         i0 = (sp * nt + it) * BM;  // the split rides on the row coordinate
         j0 = jt * BN;
         kb = sp * kcs * KC;
@@ -322,6 +359,184 @@ struct GramBulk {
         else
             gram_store(e, lam, G, ld, il, j, v);
     }
+};
+
+// ------------------------------------------------------------------ refinement correction
+// x += W^H (W r) for a block of frames (F <= BN), in two split-K products whose
+// partial sums (one per range of k, `chunk` wide) are added in order afterwards:
+//   CorrW   T[f][i]  = sum_{k <= i} W[i][k] r[f][k]
+//   CorrWH  X[f][n] += sum_{k >= n} conj(W[k][n]) T[f][k]
+// The column coordinate carries the k range: column j is frame j % BN of split j / BN.
+__device__ inline void load8d(const double2* p, int avail, float2 (&v)[8]) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const double2 a = t < avail ? p[t] : make_double2(0.0, 0.0);
+        v[t] = make_float2((float)a.x, (float)a.y);
+    }
+}
+struct CorrW {
+    const float2* W;
+    const double2* R;  // [F][N]
+    float2* part;      // [splits][F][N]
+    int64_t N, F, chunk;
+    __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = by * BM;
+        j0 = bx * BN;
+        kb = bx * chunk;
+        ke = kb + chunk;
+        const int64_t kmax = i0 + BM < N ? i0 + BM : N;  // W is lower triangular
+        if (ke > kmax) ke = kmax;
+        return kb < ke;
+    }
+    __device__ RowPtr row_a(int64_t i) const { return RowPtr{W + (i < N ? i : 0) * N, i < N}; }
+    __device__ int64_t row_b(int64_t j) const { return j % BN; }
+    __device__ void a8(const RowPtr& r, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(r.p + k, r.ok ? (int)(ke - k) : 0, v);
+    }
+    __device__ void b8(int64_t f, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8d(R + (f < F ? f : 0) * N + k, f < F ? (int)(ke - k) : 0, v);
+    }
+    __device__ bool row_ok(int64_t i) const { return i < N; }
+    __device__ bool col_ok(int64_t j) const { return j % BN < F; }
+    __device__ void store(int64_t i, int64_t j, float2 v) const { part[((j / BN) * F + j % BN) * N + i] = v; }
+};
+struct CorrWH {
+    const float2* W;
+    const float2* T;  // [F][N]
+    float2* part;     // [splits][F][N]
+    int64_t N, F, chunk;
+    __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        i0 = by * BM;
+        j0 = bx * BN;
+        kb = bx * chunk;
+        if (kb < i0) kb = i0;  // W is lower triangular: k >= n
+        ke = (bx + 1) * chunk < N ? (bx + 1) * chunk : N;
+        return kb < ke;
+    }
+    __device__ int64_t row_a(int64_t i) const { return i; }
+    __device__ int64_t row_b(int64_t j) const { return j % BN; }
+    __device__ void a8(int64_t n, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8col(W + k * N + (n < N ? n : 0), N, n < N ? (int)(ke - k) : 0, v);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t].y = -v[t].y;
+    }
+    __device__ void b8(int64_t f, int64_t k, int64_t ke, float2 (&v)[8]) const {
+        load8f(T + (f < F ? f : 0) * N + k, f < F ? (int)(ke - k) : 0, v);
+    }
+    __device__ bool row_ok(int64_t i) const { return i < N; }
+    __device__ bool col_ok(int64_t j) const { return j % BN < F; }
+    __device__ void store(int64_t i, int64_t j, float2 v) const { part[((j / BN) * F + j % BN) * N + i] = v; }
+};
+
+// ------------------------------------------------------------------ Recon, bulk-fed
+// Recon = W^H (W E^H) (Eq. 8) computed transposed, sample rows by voxel columns,
+// over one range of samples (a chunk of row tiles) at a time:
+//   step 1  T^T[j][i] = sum_k conj(E[j][k]) W[i][k]     (k < i0 + 128: W is lower)
+//   step 2  Recon[n][j] = sum_k T^T[j][k] conj(W[k][n])  (k >= n0)
+// Operand tables: ET (A tiles of conj(E), generated from the phase tables), WB1
+// and WB2 (B tiles of W[i][k] and conj(W[k][n]), from the FP32 W) and TT (A
+// tiles of T^T, written split by the step-1 epilogue: T never exists in FP32).
+template <int S>
+__global__ void __launch_bounds__(256) k_tab_et(EncodeDev e, int64_t kcn, int64_t j_off, uint8_t* tab) {
+    const int64_t kc = blockIdx.x, rt = blockIdx.y;
+    const int r = threadIdx.x & (BM - 1), g = threadIdx.x >> 7;
+    float2 v[8];
+    gen_eh8_voxels(e, eh_col(e, j_off + rt * BM + r), kc * KC + 8 * g, e.N, v);
+    put_a<S>(tab + (rt * kcn + kc) * S * A_SL, r, g, v);
+}
+
+// WB1 (lower = 1): b(k, i) = W[i][k]; WB2 (lower = 0): b(k, n) = conj(W[k][n]).
+// Only the chunks the triangular products read are written.
+template <int S>
+__global__ void __launch_bounds__(256) k_tab_w(const float2* __restrict__ W32, int64_t N, int64_t kcn, int lower,
+                                               uint8_t* tab) {
+    const int64_t kc = blockIdx.x, ct = blockIdx.y;
+    if (lower ? kc * KC >= (ct + 1) * BN : (kc + 1) * KC <= ct * BN) return;
+    const int r = threadIdx.x & (BM - 1), g = threadIdx.x >> 7;
+    const int64_t col = ct * BN + r, k0 = kc * KC + 8 * g;
+    const int avail = col < N && k0 < N ? (int)(N - k0) : 0;
+    float2 v[8];
+    if (lower) {
+        load8f(W32 + (col < N ? col : 0) * N + (k0 < N ? k0 : 0), avail, v);
+    } else {
+        load8col(W32 + (k0 < N ? k0 : 0) * N + (col < N ? col : 0), N, avail, v);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t].y = -v[t].y;
+    }
+    put_b<S>(tab + (ct * kcn + kc) * S * B_SL, r, g, v);
+}
+
+struct ReconB1 {
+    static constexpr bool kBulk = true;
+    static constexpr bool kHintB = true;
+    const uint8_t* et;
+    const uint8_t* wb;
+    uint8_t* tt;
+    int64_t rows, nt, kcn;  // sample tiles in the chunk, voxel tiles, voxel chunks
+    int S;
+    __device__ bool tile(int64_t bx, int64_t, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        int64_t rt, ct;
+        band_tile(bx, rows, nt, rt, ct);
+        ct = nt - 1 - ct;  // the longest tiles of a band first
+        i0 = rt * BM;
+        j0 = ct * BN;
+        kb = 0;
+        ke = (ct + 1) * BN;
+        return true;
+    }
+    __device__ const uint8_t* bulk_a(int64_t i0, int64_t kc, int sl) const {
+        return et + (((i0 / BM) * kcn + kc) * S + sl) * A_SL;
+    }
+    __device__ const uint8_t* bulk_b(int64_t j0, int64_t kc, int sl) const {
+        return wb + (((j0 / BN) * kcn + kc) * S + sl) * B_SL;
+    }
+    // row i of T^T, voxels j0 .. j0 + 15 (one chunk of TT), split into S slices
+    __device__ void store16(int64_t i, int64_t j0, const float (&re)[16], const float (&im)[16]) const {
+        uint8_t* blk = tt + ((i / BM) * kcn + j0 / KC) * S * A_SL;
+        const int r = (int)(i % BM);
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = make_float2(re[8 * g + u], im[8 * g + u]);
+            if (S == 3)
+                put_a<3>(blk, r, g, v);
+            else
+                put_a<2>(blk, r, g, v);
+        }
+    }
+    __device__ bool row_ok(int64_t) const { return true; }
+    __device__ bool col_ok(int64_t) const { return true; }
+    __device__ void store(int64_t, int64_t, float2) const {}
+};
+
+struct ReconB2 {
+    static constexpr bool kBulk = true;
+    static constexpr bool kHintB = true;
+    const uint8_t* tt;
+    const uint8_t* wb;
+    float2* R;
+    int64_t rows, nt, kcn;
+    int64_t N, M, j_off, mvalid;  // Recon is [N][M]; this chunk holds samples j_off .. j_off + mvalid - 1
+    int S;
+    __device__ bool tile(int64_t bx, int64_t, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        int64_t rt, ct;
+        band_tile(bx, rows, nt, rt, ct);
+        i0 = rt * BM;
+        j0 = ct * BN;
+        kb = ct * BN;
+        ke = nt * BN;
+        return true;
+    }
+    __device__ const uint8_t* bulk_a(int64_t i0, int64_t kc, int sl) const {
+        return tt + (((i0 / BM) * kcn + kc) * S + sl) * A_SL;
+    }
+    __device__ const uint8_t* bulk_b(int64_t j0, int64_t kc, int sl) const {
+        return wb + (((j0 / BN) * kcn + kc) * S + sl) * B_SL;
+    }
+    __device__ bool row_ok(int64_t i) const { return i < mvalid; }
+    __device__ bool col_ok(int64_t j) const { return j < N; }
+    __device__ void store(int64_t i, int64_t j, float2 v) const { R[j * M + j_off + i] = v; }
 };
 
 // ------------------------------------------------------------------ blocked Cholesky
@@ -579,9 +794,10 @@ namespace {
 struct GramBulkShape {
     int64_t nt, kcn, kcs;
     int splits;
+    size_t tab_bytes, part_bytes;
 };
 // sample-range splits: the fewest (up to 4) that fill the last wave of tiles to 90 %
-GramBulkShape gram_bulk_shape(const EncodeDev& e) {
+GramBulkShape gram_bulk_shape(const EncodeDev& e, int slices) {
     GramBulkShape g;
     g.nt = (e.N + tc::BM - 1) / tc::BM;
     g.kcn = (e.Mk + tc::KC - 1) / tc::KC;
@@ -593,41 +809,56 @@ GramBulkShape gram_bulk_shape(const EncodeDev& e) {
         if ((double)items >= 0.9 * (double)(waves * sms) || g.kcn < 64 * (sp + 1)) break;
     }
     g.kcs = (g.kcn + g.splits - 1) / g.splits;
+    const size_t np = (size_t)g.nt * tc::BM;
+    g.tab_bytes = (size_t)g.nt * g.kcn * slices * tc::B_SL;
+    g.part_bytes = g.splits > 1 ? g.splits * np * np * sizeof(float2) : 0;
     return g;
+}
+tc::GramBulk gram_bulk_problem(const EncodeDev& e, double lam, int slices, double2* G, int64_t ld, void* work,
+                               int64_t* items) {
+    const GramBulkShape g = gram_bulk_shape(e, slices);
+    uint8_t* tab = (uint8_t*)work;
+    float2* part = g.splits > 1 ? (float2*)(tab + g.tab_bytes) : nullptr;
+    *items = g.splits * g.nt * g.nt;
+    return tc::GramBulk{e, lam, G, ld, part, tab, g.nt, g.kcn, g.kcs, slices, g.splits};
 }
 }  // namespace
 
 size_t gram_bulk_bytes(const EncodeDev& e, int slices) {
-    const GramBulkShape g = gram_bulk_shape(e);
-    const size_t np = (size_t)g.nt * tc::BM;
-    return (size_t)g.nt * g.kcn * slices * tc::TAB_BLOCK + (g.splits > 1 ? g.splits * np * np * sizeof(float2) : 0);
+    const GramBulkShape g = gram_bulk_shape(e, slices);
+    return g.tab_bytes + g.part_bytes;
+}
+
+cudaError_t gram_bulk_table(const EncodeDev& e, int slices, void* work, cudaStream_t s) {
+    const GramBulkShape g = gram_bulk_shape(e, slices);
+    const dim3 tg((unsigned)g.kcn, (unsigned)g.nt);
+    if (slices == 3)
+        tc::k_gram_tab<3><<<tg, 256, 0, s>>>(e, g.kcn, (uint8_t*)work);
+    else
+        tc::k_gram_tab<2><<<tg, 256, 0, s>>>(e, g.kcn, (uint8_t*)work);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t gram_bulk_finish(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld, void* work,
+                             cudaStream_t s) {
+    const GramBulkShape g = gram_bulk_shape(e, slices);
+    if (g.splits <= 1) return cudaSuccess;
+    const int64_t n = e.N * e.N;
+    k_gram_finalize<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        e, lambda, (const float2*)((uint8_t*)work + g.tab_bytes), g.splits, g.nt * tc::BM, G, ld);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gram_bulk(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld, void* work,
                              DevStatus* st, cudaStream_t s) {
-    const GramBulkShape g = gram_bulk_shape(e);
-    uint8_t* tab = (uint8_t*)work;
-    const size_t tab_bytes = (size_t)g.nt * g.kcn * slices * tc::TAB_BLOCK;
-    float2* part = g.splits > 1 ? (float2*)(tab + tab_bytes) : nullptr;
-    const dim3 tg((unsigned)g.kcn, (unsigned)g.nt);
-    if (slices == 3)
-        tc::k_gram_tab<3><<<tg, 256, 0, s>>>(e, g.kcn, tab);
-    else
-        tc::k_gram_tab<2><<<tg, 256, 0, s>>>(e, g.kcn, tab);
-    note_launch();
-    cudaError_t err = cudaGetLastError();
+    cudaError_t err = gram_bulk_table(e, slices, work, s);
     if (err != cudaSuccess) return err;
-    tc::GramBulk p{e, lambda, G, ld, part, tab, g.nt, g.kcn, g.kcs, slices, g.splits};
-    const int64_t items = g.splits * g.nt * g.nt;
+    int64_t items = 0;
+    const tc::GramBulk p = gram_bulk_problem(e, lambda, slices, G, ld, work, &items);
     if ((err = run(p, dim3((unsigned)items, 1), slices, st, 1, s)) != cudaSuccess) return err;
-    if (g.splits > 1) {
-        const int64_t n = e.N * e.N;
-        k_gram_finalize<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(e, lambda, part, g.splits, g.nt * tc::BM, G,
-                                                                     ld);
-        note_launch();
-        err = cudaGetLastError();
-    }
-    return err;
+    return gram_bulk_finish(e, lambda, slices, G, ld, work, s);
 }
 
 // Two-level blocking: 64-wide diagonal blocks inside 256-wide panels. Inside a
@@ -709,12 +940,191 @@ cudaError_t launch_recon_tc(const EncodeDev& e, const float2* W32, const float2*
     return run(p2, dim3(cdiv(e.N, tc::BM), cdiv(M, tc::BN)), slices, st, 8, s);
 }
 
+namespace {
+struct ReconBulkShape {
+    int64_t nt, kcn, mt, rows, chunks;  // voxel tiles, voxel chunks, sample tiles, sample tiles per chunk
+    size_t wb_bytes, et_bytes;
+};
+// ET + TT of one chunk of samples: 4 GiB, or PINV_RECON_CHUNK_MB
+size_t recon_chunk_bytes() {
+    const char* v = std::getenv("PINV_RECON_CHUNK_MB");
+    const long mb = v ? std::atol(v) : 0;
+    return mb > 0 ? (size_t)mb << 20 : size_t(4) << 30;
+}
+ReconBulkShape recon_bulk_shape(const EncodeDev& e, int slices) {
+    ReconBulkShape r;
+    r.nt = (e.N + tc::BM - 1) / tc::BM;
+    r.kcn = r.nt * (tc::BM / tc::KC);
+    r.mt = (e.Mk * e.C + tc::BM - 1) / tc::BM;
+    const size_t per_tile = 2 * (size_t)r.kcn * slices * tc::A_SL;
+    int64_t cap = (int64_t)(recon_chunk_bytes() / per_tile);
+    if (cap < 1) cap = 1;
+    r.chunks = (r.mt + cap - 1) / cap;
+    r.rows = (r.mt + r.chunks - 1) / r.chunks;
+    r.wb_bytes = (size_t)r.nt * r.kcn * slices * tc::B_SL;
+    r.et_bytes = (size_t)r.rows * r.kcn * slices * tc::A_SL;
+    return r;
+}
+struct ReconWork {
+    uint8_t *wb1, *wb2, *et, *tt;
+};
+ReconWork recon_work(const ReconBulkShape& r, void* work) {
+    ReconWork w;
+    w.wb1 = (uint8_t*)work;
+    w.wb2 = w.wb1 + r.wb_bytes;
+    w.et = w.wb2 + r.wb_bytes;
+    w.tt = w.et + r.et_bytes;
+    return w;
+}
+int64_t chunk_rows(const ReconBulkShape& r, int64_t c) {
+    const int64_t t0 = c * r.rows;
+    return t0 >= r.mt ? 0 : std::min(r.rows, r.mt - t0);
+}
+tc::ReconB1 recon_b1_problem(const EncodeDev& e, int slices, void* work, int64_t c, int64_t* items) {
+    const ReconBulkShape r = recon_bulk_shape(e, slices);
+    const ReconWork w = recon_work(r, work);
+    const int64_t rows = chunk_rows(r, c);
+    *items = rows * r.nt;
+    return tc::ReconB1{w.et, w.wb1, w.tt, rows, r.nt, r.kcn, slices};
+}
+tc::ReconB2 recon_b2_problem(const EncodeDev& e, int slices, float2* R, void* work, int64_t c, int64_t* items) {
+    const ReconBulkShape r = recon_bulk_shape(e, slices);
+    const ReconWork w = recon_work(r, work);
+    const int64_t rows = chunk_rows(r, c), M = e.Mk * e.C, j_off = c * r.rows * tc::BM;
+    *items = rows * r.nt;
+    return tc::ReconB2{w.tt, w.wb2, R, rows, r.nt, r.kcn, e.N, M, j_off, std::min(rows * tc::BM, M - j_off), slices};
+}
+}  // namespace
+
+size_t recon_bulk_bytes(const EncodeDev& e, int slices) {
+    const ReconBulkShape r = recon_bulk_shape(e, slices);
+    return 2 * r.wb_bytes + 2 * r.et_bytes;
+}
+
+int64_t recon_bulk_chunks(const EncodeDev& e, int slices) { return recon_bulk_shape(e, slices).chunks; }
+
+cudaError_t recon_bulk_wtables(const EncodeDev& e, const float2* W32, int slices, void* work, cudaStream_t s) {
+    const ReconBulkShape r = recon_bulk_shape(e, slices);
+    const ReconWork w = recon_work(r, work);
+    const dim3 wg((unsigned)r.kcn, (unsigned)r.nt);
+    for (int lower = 1; lower >= 0; --lower) {
+        if (slices == 3)
+            tc::k_tab_w<3><<<wg, 256, 0, s>>>(W32, e.N, r.kcn, lower, lower ? w.wb1 : w.wb2);
+        else
+            tc::k_tab_w<2><<<wg, 256, 0, s>>>(W32, e.N, r.kcn, lower, lower ? w.wb1 : w.wb2);
+        note_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t recon_bulk_et(const EncodeDev& e, int slices, void* work, int64_t c, cudaStream_t s) {
+    const ReconBulkShape r = recon_bulk_shape(e, slices);
+    const ReconWork w = recon_work(r, work);
+    const int64_t rows = chunk_rows(r, c);
+    if (rows <= 0) return cudaSuccess;
+    const dim3 eg((unsigned)r.kcn, (unsigned)rows);
+    const int64_t j_off = c * r.rows * tc::BM;
+    if (slices == 3)
+        tc::k_tab_et<3><<<eg, 256, 0, s>>>(e, r.kcn, j_off, w.et);
+    else
+        tc::k_tab_et<2><<<eg, 256, 0, s>>>(e, r.kcn, j_off, w.et);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recon_bulk(const EncodeDev& e, const float2* W32, int slices, float2* R, void* work,
+                              DevStatus* st, cudaStream_t s) {
+    cudaError_t err = recon_bulk_wtables(e, W32, slices, work, s);
+    if (err != cudaSuccess) return err;
+    const int64_t chunks = recon_bulk_chunks(e, slices);
+    for (int64_t c = 0; c < chunks; ++c) {
+        if ((err = recon_bulk_et(e, slices, work, c, s)) != cudaSuccess) return err;
+        int64_t items = 0;
+        const tc::ReconB1 p1 = recon_b1_problem(e, slices, work, c, &items);
+        if ((err = run(p1, dim3((unsigned)items, 1), slices, st, 2, s)) != cudaSuccess) return err;
+        const tc::ReconB2 p2 = recon_b2_problem(e, slices, R, work, c, &items);
+        if ((err = run(p2, dim3((unsigned)items, 1), slices, st, 8, s)) != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------------------ refinement correction (host)
+namespace {
+// k ranges of the correction: about two tiles per SM, at least 256 wide
+int64_t correct_tc_chunk(int64_t N) {
+    const int64_t rows = (N + tc::BM - 1) / tc::BM;
+    int64_t sp = (2 * 152 + rows - 1) / rows;
+    sp = std::max<int64_t>(1, std::min<int64_t>(sp, std::max<int64_t>(1, N / 256)));
+    return ((N + sp - 1) / sp + tc::KC - 1) / tc::KC * tc::KC;
+}
+}  // namespace
+
+// T[f][i] = sum of the nonempty splits (k range below the end of i's row tile), in order
+__global__ void k_corr_reduce_w(const float2* __restrict__ part, int64_t N, int64_t F, int64_t chunk,
+                                float2* __restrict__ T) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * F) return;
+    const int64_t f = idx / N, i = idx - f * N;
+    const int64_t kend = (i / tc::BM + 1) * tc::BM, kmax = kend < N ? kend : N;
+    float2 a = make_float2(0.f, 0.f);
+    for (int64_t sp = 0; sp * chunk < kmax; ++sp) {
+        const float2 b = part[(sp * F + f) * N + i];
+        a.x += b.x;
+        a.y += b.y;
+    }
+    T[f * N + i] = a;
+}
+// X[f][n] += sum of the nonempty splits (k range reaching n's row tile), in order
+__global__ void k_corr_reduce_wh(const float2* __restrict__ part, int64_t N, int64_t F, int64_t chunk,
+                                 double2* __restrict__ X) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * F) return;
+    const int64_t f = idx / N, n = idx - f * N;
+    const int64_t n0 = n / tc::BM * tc::BM;
+    double2 a = make_double2(0.0, 0.0);
+    for (int64_t sp = n0 / chunk; sp * chunk < N; ++sp) {
+        const float2 b = part[(sp * F + f) * N + n];
+        a.x += (double)b.x;
+        a.y += (double)b.y;
+    }
+    double2 x = X[f * N + n];
+    X[f * N + n] = make_double2(x.x + a.x, x.y + a.y);
+}
+
+bool correct_tc_ok(int64_t F) { return F >= 16 && tc_available(); }
+
+size_t correct_tc_work_elems(int64_t N, int64_t F) {
+    const int64_t chunk = correct_tc_chunk(N), sp = (N + chunk - 1) / chunk;
+    return (size_t)(sp * std::min<int64_t>(F, tc::BN) * N);
+}
+
+cudaError_t launch_correct_tc(const float2* W32, int64_t N, const double2* R, int64_t F, float2* T, double2* X,
+                              float2* work, int slices, DevStatus* sched, cudaStream_t s) {
+    const int64_t chunk = correct_tc_chunk(N), sp = (N + chunk - 1) / chunk;
+    for (int64_t f0 = 0; f0 < F; f0 += tc::BN) {
+        const int64_t Fc = std::min<int64_t>(tc::BN, F - f0);
+        const int64_t n = N * Fc;
+        const unsigned rb = (unsigned)((n + 255) / 256);
+        tc::CorrW p1{W32, R + f0 * N, work, N, Fc, chunk};
+        cudaError_t e = run(p1, dim3((unsigned)sp, cdiv(N, tc::BM)), slices, sched, 10, s);
+        if (e != cudaSuccess) return e;
+        k_corr_reduce_w<<<rb, 256, 0, s>>>(work, N, Fc, chunk, T + f0 * N);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        tc::CorrWH p2{W32, T + f0 * N, work, N, Fc, chunk};
+        if ((e = run(p2, dim3((unsigned)sp, cdiv(N, tc::BM)), slices, sched, 11, s)) != cudaSuccess) return e;
+        k_corr_reduce_wh<<<rb, 256, 0, s>>>(work, N, Fc, chunk, X + f0 * N);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // ------------------------------------------------------------------ batched launches
-cudaError_t tc_multi_create(int kind, const TcPlanArgs* a, int n, TcMulti* out) {
+cudaError_t tc_multi_create(int kind, const TcPlanArgs* a, int n, int slices, int64_t chunk, TcMulti* out) {
     *out = TcMulti{};
     out->kind = kind;
-    out->n = n;
-    std::vector<int64_t> start(n + 1, 0), gx(n, 1);
+    std::vector<int64_t> start(1, 0), gx;
     std::vector<unsigned char> probs;  // problem descriptors, stride sizeof(problem)
     // plans with the longest tiles first (K per tile: M_k for the Gram, up to N for Recon)
     std::vector<int> order(n);
@@ -727,39 +1137,37 @@ cudaError_t tc_multi_create(int kind, const TcPlanArgs* a, int n, TcMulti* out) 
     for (int ii = 0; ii < n; ++ii) {
         const int i = order[ii];
         const EncodeDev& e = *a[i].e;
-        const int64_t M = e.Mk * e.C;
-        int64_t gxi = 1, gyi = 1;
+        int64_t items = 0;
         if (kind == TC_MULTI_GRAM) {
-            gxi = cdiv(e.N, tc::BN);
-            gyi = cdiv(e.N, tc::BM);
-            tc::GramTC p{e, a[i].lam, a[i].G, e.N};
-            probs.insert(probs.end(), (unsigned char*)&p, (unsigned char*)&p + sizeof(p));
-        } else if (kind == TC_MULTI_RECON1) {
-            gxi = cdiv(M, tc::BN);
-            gyi = cdiv(e.N, tc::BM);
-            tc::ReconStep1TC p{e, a[i].W32, a[i].T};
-            probs.insert(probs.end(), (unsigned char*)&p, (unsigned char*)&p + sizeof(p));
+            const tc::GramBulk p = gram_bulk_problem(e, a[i].lam, slices, a[i].G, e.N, a[i].work, &items);
+            probs.insert(probs.end(), (const unsigned char*)&p, (const unsigned char*)&p + sizeof(p));
         } else {
-            gxi = cdiv(e.N, tc::BM);
-            gyi = cdiv(M, tc::BN);
-            tc::ReconStep2TC p{a[i].WT32, a[i].T, a[i].R, e.N, M};
-            probs.insert(probs.end(), (unsigned char*)&p, (unsigned char*)&p + sizeof(p));
+            if (chunk >= recon_bulk_chunks(e, slices)) continue;
+            if (kind == TC_MULTI_RECON1) {
+                const tc::ReconB1 p = recon_b1_problem(e, slices, a[i].work, chunk, &items);
+                probs.insert(probs.end(), (const unsigned char*)&p, (const unsigned char*)&p + sizeof(p));
+            } else {
+                const tc::ReconB2 p = recon_b2_problem(e, slices, a[i].R, a[i].work, chunk, &items);
+                probs.insert(probs.end(), (const unsigned char*)&p, (const unsigned char*)&p + sizeof(p));
+            }
         }
-        gx[ii] = gxi;
-        start[ii + 1] = start[ii] + gxi * gyi;
+        gx.push_back(items);  // bulk problems decode their own tile from the item index
+        start.push_back(start.back() + items);
     }
-    out->items = start[n];
+    out->n = (int)gx.size();
+    out->items = start.back();
+    if (out->n == 0) return cudaSuccess;
     out->off_start = (probs.size() + 255) & ~(size_t)255;
-    out->off_gx = out->off_start + ((sizeof(int64_t) * (n + 1) + 255) & ~(size_t)255);
-    const size_t bytes = out->off_gx + sizeof(int64_t) * n;
+    out->off_gx = out->off_start + ((sizeof(int64_t) * (out->n + 1) + 255) & ~(size_t)255);
+    const size_t bytes = out->off_gx + sizeof(int64_t) * out->n;
     cudaError_t e = cudaMalloc(&out->buf, bytes);
     if (e != cudaSuccess) return e;
     unsigned char* b = (unsigned char*)out->buf;
     if ((e = cudaMemcpy(b, probs.data(), probs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
-    if ((e = cudaMemcpy(b + out->off_start, start.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice)) !=
-        cudaSuccess)
+    if ((e = cudaMemcpy(b + out->off_start, start.data(), sizeof(int64_t) * (out->n + 1),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
-    return cudaMemcpy(b + out->off_gx, gx.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice);
+    return cudaMemcpy(b + out->off_gx, gx.data(), sizeof(int64_t) * out->n, cudaMemcpyHostToDevice);
 }
 
 template <int S>
@@ -768,10 +1176,10 @@ static cudaError_t multi_launch_s(const TcMulti& m, DevStatus* st, cudaStream_t 
     const int64_t* start = (const int64_t*)(b + m.off_start);
     const int64_t* gx = (const int64_t*)(b + m.off_gx);
     if (m.kind == TC_MULTI_GRAM)
-        return tc::launch_many<S>((const tc::GramTC*)b, start, gx, m.n, m.items, st, 1, s);
+        return tc::launch_many<S>((const tc::GramBulk*)b, start, gx, m.n, m.items, st, 1, s);
     if (m.kind == TC_MULTI_RECON1)
-        return tc::launch_many<S>((const tc::ReconStep1TC*)b, start, gx, m.n, m.items, st, 2, s, true);
-    return tc::launch_many<S>((const tc::ReconStep2TC*)b, start, gx, m.n, m.items, st, 8, s);
+        return tc::launch_many<S>((const tc::ReconB1*)b, start, gx, m.n, m.items, st, 2, s);
+    return tc::launch_many<S>((const tc::ReconB2*)b, start, gx, m.n, m.items, st, 8, s);
 }
 
 cudaError_t tc_multi_launch(const TcMulti& m, int slices, DevStatus* st, cudaStream_t s) {

@@ -70,15 +70,18 @@ def test_gram_bulk_split_samples():
     assert rel(_gram(p, L.MIXED_BF16X6), np.tril(oracle_all(p).G)) < SPLIT_TOL[L.MIXED_BF16X6]
 
 
+@pytest.mark.parametrize("bulk", ["1", "0"])
 @pytest.mark.parametrize("prec", [L.MIXED_BF16X6, L.MIXED_BF16X3])
-def test_recon_tc_isolated(prec):
-    """Recon = W^H (W E^H) with the plan's own W = L^-1: isolates the tensor-core kernels.
+def test_recon_tc_isolated(prec, bulk, monkeypatch):
+    """Recon = W^H (W E^H) with the plan's own W = L^-1: isolates the tensor-core
+    kernels, bulk-fed from split tables (bulk = 1) or generating their operands.
 
     Bound: each of the two products carries a relative error of the split
     arithmetic (SPLIT_TOL, taken per product) on its inputs' magnitudes, so the
     error relative to Recon is at most ~ SPLIT_TOL * ||W|| ||W E^H|| / ||Recon||
     (the cancellation factor, about kappa(L)), computed here from the data.
     """
+    monkeypatch.setenv("PINV_RECON_BULK", bulk)
     p = synth.make_plan(16, 3, "radial", 1, 2102, 1e-3, b0=True, spokes=20, per_spoke=33)
     pl = _plan(p, precision=prec, refine_max_iters=0).build()
     W = pl.export(L.EXPORT_LINV).cpu().numpy()
@@ -89,6 +92,21 @@ def test_recon_tc_isolated(prec):
     amp = np.linalg.norm(W) * np.linalg.norm(T) / np.linalg.norm(want)
     assert rel(R, want) < SPLIT_TOL[prec] * max(1.0, amp)
     assert np.allclose(np.triu(W, 1), 0)
+
+
+def test_recon_bulk_chunks_bit_identical(monkeypatch):
+    """The bulk Recon over one sample tile per chunk (a 1 MB chunk cap) gives the
+    same Recon bit for bit as one chunk: every tile sums the same tables in the
+    same order. N = 441, M = 3 x 1000 (24 tiles, the last ragged)."""
+    p = synth.make_plan(21, 3, "spiral", 1, 2109, 1e-3, samples=1000, interleaves=2)
+
+    def recon():
+        pl = _plan(p, precision=L.MIXED_BF16X6, refine_max_iters=0).build()
+        return pl.export(L.EXPORT_RECON).cpu().numpy()
+
+    whole = recon()
+    monkeypatch.setenv("PINV_RECON_CHUNK_MB", "1")
+    assert np.array_equal(recon(), whole)
 
 
 @pytest.mark.parametrize("prec,iters", [(L.MIXED_BF16X6, 2), (L.MIXED_BF16X3, 4)])
@@ -136,6 +154,21 @@ def test_b0_radial_reduced_cfg5():
     pl = _plan(p, precision=L.MIXED_BF16X6, refine_max_iters=3, refine_tol=1e-9).build()
     x = pl.apply(torch.from_numpy(p.data).cuda()).cpu().numpy()
     assert rel(x, ref.images) <= 1e-4
+
+
+@pytest.mark.parametrize("b0", [True, False])
+def test_tensor_core_correction_many_frames(b0):
+    """20 frames take the tensor-core correction x += W^H (W r) (split-K over k,
+    partial sums added in order): a factor-only plan gets its initial image and
+    every refinement step from it; the images reach the oracle's within 1e-6.
+    N = 324 (ragged row tiles), with and without B0 (double-float and exact
+    Gram residuals)."""
+    p = synth.make_plan(18, 3, "spiral", 20, 2113, 1e-3, samples=720, interleaves=2, b0=b0)
+    ref = oracle_all(p)
+    pl = _plan(p, precision=L.MIXED_BF16X6, recon_mode=L.RECON_NONE, refine_max_iters=4,
+               refine_tol=0.0).build()
+    x = pl.apply(torch.from_numpy(p.data).cuda()).cpu().numpy()
+    assert rel(x, ref.images) <= 1e-6
 
 
 def test_factor_only_mixed():
