@@ -109,10 +109,19 @@ pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events) {
         float2 *L32 = nullptr, *D32 = nullptr;
         CK(cudaMallocAsync((void**)&L32, sizeof(float2) * N * N, s));
         CK(cudaMallocAsync((void**)&D32, sizeof(float2) * nblk * 64 * 64, s));
-        CK(launch_potrf_tc(p->G, N, ld, p->Dinv, D32, L32, p->slices(), p->st, s));
+        // operand tables of the bulk-fed panel updates (PINV_CHOL_BULK=0: generated)
+        void* tab = nullptr;
+        const char* env = std::getenv("PINV_CHOL_BULK");
+        if (!(env && std::strcmp(env, "0") == 0) &&
+            cudaMallocAsync(&tab, factor_table_bytes(N, p->slices()), s) != cudaSuccess) {
+            cudaGetLastError();
+            tab = nullptr;
+        }
+        CK(launch_potrf_tc(p->G, N, ld, p->Dinv, D32, L32, p->slices(), p->st, s, tab));
         CK(launch_pivot_stats(p->G, N, ld, p->st, s));
         if (events) CK(cudaEventRecord(p->ev[3], s));
-        CK(launch_trtri_tc(L32, N, D32, p->W, p->W32, p->slices(), p->st, s));
+        CK(launch_trtri_tc(L32, N, D32, p->W, p->W32, p->slices(), p->st, s, tab));
+        if (tab) CK(cudaFreeAsync(tab, s));
         CK(cudaFreeAsync(D32, s));
         CK(cudaFreeAsync(L32, s));
     } else {

@@ -203,11 +203,14 @@ cudaError_t launch_apply32(const float2* R, int64_t N, int64_t M, const float2* 
                            float2* X, cudaStream_t s);
 // Blocked Cholesky with FP64 diagonal panels and tensor-core panel solves and
 // trailing updates; L32 receives an FP32 copy of L ([N][N], lower part).
+// tab (factor_table_bytes(), or nullptr): operand tables of the bulk-fed
+// panel trailing updates; without it the updates generate their operands.
+size_t factor_table_bytes(int64_t N, int slices);
 cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, float2* Dinv32, float2* L32,
-                            int slices, DevStatus* st, cudaStream_t s);
+                            int slices, DevStatus* st, cudaStream_t s, void* tab = nullptr);
 // W = L^-1 (FP64 storage, tensor-core updates) and its FP32 copy W32.
 cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, double2* W, float2* W32,
-                            int slices, DevStatus* st, cudaStream_t s);
+                            int slices, DevStatus* st, cudaStream_t s, void* tab = nullptr);
 bool tc_available();
 
 // ---------------------------------------------------------------------------

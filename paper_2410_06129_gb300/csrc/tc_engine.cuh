@@ -88,6 +88,12 @@ template <class P, class = void>
 struct HasStore16 : std::false_type {};
 template <class P>
 struct HasStore16<P, std::void_t<decltype(&P::store16)>> : std::true_type {};
+// ... or 4 columns at a time through a row-major copy of the tile in shared
+// memory (store4: a warp then writes whole rows, coalesced)
+template <class P, class = void>
+struct HasStore4 : std::false_type {};
+template <class P>
+struct HasStore4<P, std::void_t<decltype(&P::store4)>> : std::true_type {};
 template <class P, class = void>
 struct HintB : std::false_type {};
 template <class P>
@@ -133,6 +139,23 @@ __device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* a
     }
 }
 __device__ inline void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// barrier among the first `threads` threads of the CTA (id 1; id 0 is __syncthreads)
+__device__ inline void named_barrier(uint32_t threads) {
+    asm volatile("bar.sync 1, %0;" ::"r"(threads) : "memory");
+}
+// ... that also returns the OR of v over those threads (the same value in all of them)
+__device__ inline bool named_barrier_or(uint32_t threads, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(threads)
+        : "memory");
+    return r != 0;
+}
 __device__ inline void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -617,7 +640,32 @@ __global__ void __launch_bounds__(NTHREADS_BULK, 1) k_tc_bulk(Sched sch, DevStat
                 tc_fence_before();
                 mbar_arrive(&tempty[b]);
             }
-            if (ok && !abort_flag) {
+            using PE = std::remove_cv_t<std::remove_reference_t<decltype(p)>>;
+            if constexpr (HasStore4<PE>::value) {
+                // Every stage of the tile has been consumed and the loader waits for the
+                // tile barrier, so the stage ring holds a row-major copy of the tile
+                // (rows padded by 16 bytes: conflict-free float4 accesses); each warp
+                // then writes whole rows. Every drain thread reaches the barriers; the
+                // OR makes the decision to write the same in all of them.
+                if (!named_barrier_or(NPW * 32, !ok || abort_flag)) {
+                    constexpr int SP = BN + 2;
+                    float2* S = reinterpret_cast<float2*>(smem);
+                    const int r = q * 32 + lane;
+#pragma unroll
+                    for (int u = 0; u < 64; u += 2)
+                        *reinterpret_cast<float4*>(&S[r * SP + 64 * h + u]) =
+                            make_float4(tot[u], tot[64 + u], tot[u + 1], tot[64 + u + 1]);
+                    named_barrier(NPW * 32);
+                    for (int rr = warp; rr < BM; rr += NPW) {
+                        const float4 a = *reinterpret_cast<const float4*>(&S[rr * SP + 4 * lane]);
+                        const float4 b = *reinterpret_cast<const float4*>(&S[rr * SP + 4 * lane + 2]);
+                        const float2 v[4] = {make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                                             make_float2(b.z, b.w)};
+                        p.store4(i0 + rr, j0 + 4 * lane, v);
+                    }
+                    fence_proxy_async();  // generic shared accesses before the next tile's copies
+                }
+            } else if (ok && !abort_flag) {
                 // every group is drained and the MMAs of the next tile wait for the
                 // tile barrier, so buffer 0 is free to hold the totals
                 regs_to_tmem(taddr_row, tot);

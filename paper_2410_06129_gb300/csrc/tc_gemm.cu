@@ -349,16 +349,22 @@ struct GramBulk {
     __device__ const uint8_t* bulk_b(int64_t j0, int64_t kc, int sl) const {
         return tab + (((j0 / BN) * kcn + kc) * S + sl) * TAB_BLOCK;
     }
+    // (A^H A)[i][j .. j + 3], lower part: partial sums, or G with the coil factor
+    __device__ void store4(int64_t i, int64_t j, const float2 (&v)[4]) const {
+        const int64_t np = nt * BM, il = i % np;
+        if (il >= e.N) return;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (j + u > il) continue;
+            if (splits > 1)
+                part[i * np + j + u] = v[u];
+            else
+                gram_store(e, lam, G, ld, il, j + u, v[u]);
+        }
+    }
     __device__ bool row_ok(int64_t i) const { return i % (nt * BM) < e.N; }
     __device__ bool col_ok(int64_t j) const { return j < e.N; }
-    __device__ void store(int64_t i, int64_t j, float2 v) const {
-        const int64_t np = nt * BM, il = i % np;
-        if (j > il) return;
-        if (splits > 1)
-            part[i * np + j] = v;
-        else
-            gram_store(e, lam, G, ld, il, j, v);
-    }
+    __device__ void store(int64_t, int64_t, float2) const {}
 };
 
 // ------------------------------------------------------------------ refinement correction
@@ -537,6 +543,115 @@ struct ReconB2 {
     __device__ bool row_ok(int64_t i) const { return i < mvalid; }
     __device__ bool col_ok(int64_t j) const { return j < N; }
     __device__ void store(int64_t i, int64_t j, float2 v) const { R[j * M + j_off + i] = v; }
+};
+
+// ------------------------------------------------------------------ panel trailing updates, bulk-fed
+// After a 256-wide panel p0 .. p0 + kw of the factor, both trailing updates
+// have the panel L[i][p0 + k] (rows i >= r0) as their A operand:
+//   HerkBulk   G[i][j] -= sum_k L[i][k] conj(L[j][k])   (i >= j >= r0)
+//   TrtriBulk  W[i][j] -= sum_k L[i][k] W[p0 + k][j]     (i >= r0, j < r0)
+// One table of B tiles of conj(L) serves as the HERK's A tiles (first halves)
+// and B tiles; a second holds the B tiles of the panel's rows of W.
+template <int S>
+__global__ void __launch_bounds__(256) k_tab_panel(const float2* __restrict__ L32, int64_t ldl, int64_t N,
+                                                   int64_t p0, int64_t kw, int64_t r0, uint8_t* tab) {
+    const int64_t kc = blockIdx.x, rt = blockIdx.y, kcn = gridDim.x;
+    const int r = threadIdx.x & (BM - 1), g = threadIdx.x >> 7;
+    const int64_t i = r0 + rt * BM + r, k0 = kc * KC + 8 * g;
+    float2 v[8];
+    load8f(L32 + (i < N ? i : 0) * ldl + p0 + k0, i < N && k0 < kw ? (int)(kw - k0) : 0, v);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t].y = -v[t].y;
+    put_b<S>(tab + (rt * kcn + kc) * S * B_SL, r, g, v);
+}
+template <int S>
+__global__ void __launch_bounds__(256) k_tab_wrows(const double2* __restrict__ W, int64_t ld, int64_t p0, int64_t kw,
+                                                   int64_t ncols, uint8_t* tab) {
+    const int64_t kc = blockIdx.x, ct = blockIdx.y, kcn = gridDim.x;
+    const int r = threadIdx.x & (BM - 1), g = threadIdx.x >> 7;
+    const int64_t j = ct * BN + r, k0 = kc * KC + 8 * g;
+    float2 v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const bool ok = j < ncols && k0 + t < kw;
+        const double2 w = ok ? W[(p0 + k0 + t) * ld + j] : make_double2(0.0, 0.0);
+        v[t] = make_float2((float)w.x, (float)w.y);
+    }
+    put_b<S>(tab + (ct * kcn + kc) * S * B_SL, r, g, v);
+}
+
+struct HerkBulk {
+    static constexpr bool kBulk = true;
+    const uint8_t* tab;
+    double2* G;
+    int64_t ld, N, r0, nt, kcn;  // trailing rows from r0 in nt tiles; panel chunks
+    int S;
+    __device__ bool tile(int64_t bx, int64_t, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        int64_t it, jt;
+        band_tile(bx, nt, nt, it, jt);
+        i0 = r0 + it * BM;
+        j0 = r0 + jt * BN;
+        kb = 0;
+        ke = kcn * KC;
+        return jt <= it;
+    }
+    __device__ const uint8_t* bulk_a(int64_t i0, int64_t kc, int sl) const {
+        return tab + ((((i0 - r0) / BM) * kcn + kc) * S + sl) * B_SL;
+    }
+    __device__ const uint8_t* bulk_b(int64_t j0, int64_t kc, int sl) const {
+        return tab + ((((j0 - r0) / BN) * kcn + kc) * S + sl) * B_SL;
+    }
+    // G[i][j .. j + 3] -= v (lower part)
+    __device__ void store4(int64_t i, int64_t j, const float2 (&v)[4]) const {
+        if (i >= N) return;
+        double2* row = G + i * ld + j;
+        double2 g[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) g[u] = (j + u <= i) ? row[u] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (j + u <= i) row[u] = make_double2(g[u].x - (double)v[u].x, g[u].y - (double)v[u].y);
+    }
+    __device__ bool row_ok(int64_t i) const { return i < N; }
+    __device__ bool col_ok(int64_t j) const { return j < N; }
+    __device__ void store(int64_t, int64_t, float2) const {}
+};
+struct TrtriBulk {
+    static constexpr bool kBulk = true;
+    const uint8_t* tabl;
+    const uint8_t* tabw;
+    double2* W;
+    int64_t ld, N, r0, ntr, ntc, kcn;  // rows from r0 in ntr tiles; columns below r0 in ntc tiles
+    int S;
+    __device__ bool tile(int64_t bx, int64_t, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
+        int64_t rt, ct;
+        band_tile(bx, ntr, ntc, rt, ct);
+        i0 = r0 + rt * BM;
+        j0 = ct * BN;
+        kb = 0;
+        ke = kcn * KC;
+        return true;
+    }
+    __device__ const uint8_t* bulk_a(int64_t i0, int64_t kc, int sl) const {
+        return tabl + ((((i0 - r0) / BM) * kcn + kc) * S + sl) * B_SL;
+    }
+    __device__ const uint8_t* bulk_b(int64_t j0, int64_t kc, int sl) const {
+        return tabw + (((j0 / BN) * kcn + kc) * S + sl) * B_SL;
+    }
+    // W[i][j .. j + 3] -= v (columns below r0)
+    __device__ void store4(int64_t i, int64_t j, const float2 (&v)[4]) const {
+        if (i >= N) return;
+        double2* row = W + i * ld + j;
+        double2 w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = (j + u < r0) ? row[u] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (j + u < r0) row[u] = make_double2(w[u].x - (double)v[u].x, w[u].y - (double)v[u].y);
+    }
+    __device__ bool row_ok(int64_t i) const { return i < N; }
+    __device__ bool col_ok(int64_t j) const { return j < r0; }
+    __device__ void store(int64_t, int64_t, float2) const {}
 };
 
 // ------------------------------------------------------------------ blocked Cholesky
@@ -861,6 +976,22 @@ cudaError_t launch_gram_bulk(const EncodeDev& e, double lambda, int slices, doub
     return gram_bulk_finish(e, lambda, slices, G, ld, work, s);
 }
 
+// Panel table (B tiles of conj(L), rows from r0, kw panel columns from p0)
+size_t panel_table_bytes(int64_t N, int slices) {
+    return (size_t)cdiv(N, tc::BM) * cdiv(256, tc::KC) * slices * tc::B_SL;
+}
+size_t factor_table_bytes(int64_t N, int slices) { return 2 * panel_table_bytes(N, slices); }
+static cudaError_t panel_table(const float2* L32, int64_t N, int64_t p0, int64_t kw, int64_t r0, int slices,
+                               uint8_t* tab, cudaStream_t s) {
+    const dim3 g(cdiv(kw, tc::KC), cdiv(N - r0, tc::BM));
+    if (slices == 3)
+        tc::k_tab_panel<3><<<g, 256, 0, s>>>(L32, N, N, p0, kw, r0, tab);
+    else
+        tc::k_tab_panel<2><<<g, 256, 0, s>>>(L32, N, N, p0, kw, r0, tab);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // Two-level blocking: 64-wide diagonal blocks inside 256-wide panels. Inside a
 // panel each step updates only the panel's remaining columns (K = 64); the
 // trailing matrix gets one update per panel with K = 256, so its tiles run
@@ -869,7 +1000,7 @@ cudaError_t launch_gram_bulk(const EncodeDev& e, double lambda, int slices, doub
 constexpr int NBK = 64, NBP = 256;
 
 cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, float2* Dinv32, float2* L32,
-                            int slices, DevStatus* st, cudaStream_t s) {
+                            int slices, DevStatus* st, cudaStream_t s, void* tab) {
     for (int64_t p0 = 0; p0 < N; p0 += NBP) {
         const int64_t pend = std::min<int64_t>(N, p0 + NBP);
         for (int64_t k0 = p0; k0 < pend; k0 += NBK) {
@@ -893,8 +1024,16 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
             }
         }
         if (pend < N) {  // trailing matrix, K = panel width
-            tc::HerkTC hp{L32 + p0, N, G, ld, N, pend - p0, pend, N};
-            cudaError_t e = run(hp, dim3(cdiv(N - pend, tc::BN), cdiv(N - pend, tc::BM)), slices, st, 4, s);
+            cudaError_t e;
+            if (tab) {
+                const int64_t nt = cdiv(N - pend, tc::BM), kcn = cdiv(pend - p0, tc::KC);
+                if ((e = panel_table(L32, N, p0, pend - p0, pend, slices, (uint8_t*)tab, s)) != cudaSuccess) return e;
+                tc::HerkBulk hp{(const uint8_t*)tab, G, ld, N, pend, nt, kcn, slices};
+                e = run(hp, dim3((unsigned)(nt * nt), 1), slices, st, 4, s);
+            } else {
+                tc::HerkTC hp{L32 + p0, N, G, ld, N, pend - p0, pend, N};
+                e = run(hp, dim3(cdiv(N - pend, tc::BN), cdiv(N - pend, tc::BM)), slices, st, 4, s);
+            }
             if (e != cudaSuccess) return e;
         }
     }
@@ -905,7 +1044,7 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
 // inside a 256-row panel each 64-row step updates the panel's rows only; the
 // rows below get one update per panel with K = 256.
 cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, double2* W, float2* W32,
-                            int slices, DevStatus* st, cudaStream_t s) {
+                            int slices, DevStatus* st, cudaStream_t s, void* tab) {
     cudaError_t e = launch_fill_identity(W, N, N, s);
     if (e != cudaSuccess) return e;
     for (int64_t p0 = 0; p0 < N; p0 += NBP) {
@@ -921,9 +1060,26 @@ cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, 
                 return e;
         }
         if (pend < N) {
-            tc::TrtriUpdTC up{L32, N, W, N, N, p0, pend - p0, N};
-            if ((e = run(up, dim3(cdiv(pend, tc::BN), cdiv(N - pend, tc::BM)), slices, st, 6, s)) != cudaSuccess)
-                return e;
+            if (tab) {
+                const int64_t ntr = cdiv(N - pend, tc::BM), ntc = cdiv(pend, tc::BN), kcn = cdiv(pend - p0, tc::KC);
+                uint8_t* tabl = (uint8_t*)tab;
+                uint8_t* tabw = tabl + panel_table_bytes(N, slices);
+                if ((e = panel_table(L32, N, p0, pend - p0, pend, slices, tabl, s)) != cudaSuccess) return e;
+                const dim3 wg((unsigned)kcn, (unsigned)ntc);
+                if (slices == 3)
+                    tc::k_tab_wrows<3><<<wg, 256, 0, s>>>(W, N, p0, pend - p0, pend, tabw);
+                else
+                    tc::k_tab_wrows<2><<<wg, 256, 0, s>>>(W, N, p0, pend - p0, pend, tabw);
+                note_launch();
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                tc::TrtriBulk up{tabl, tabw, W, N, N, pend, ntr, ntc, kcn, slices};
+                if ((e = run(up, dim3((unsigned)(ntr * ntc), 1), slices, st, 6, s)) != cudaSuccess) return e;
+            } else {
+                tc::TrtriUpdTC up{L32, N, W, N, N, p0, pend - p0, N};
+                if ((e = run(up, dim3(cdiv(pend, tc::BN), cdiv(N - pend, tc::BM)), slices, st, 6, s)) !=
+                    cudaSuccess)
+                    return e;
+            }
         }
     }
     return launch_to_f32(W, W32, N * N, s);

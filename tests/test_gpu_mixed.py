@@ -62,6 +62,24 @@ def test_gram_bulk_bit_identical_to_generated(prec, monkeypatch):
     assert rel(g_bulk, np.tril(oracle_all(p).G)) < SPLIT_TOL[prec]
 
 
+def test_factor_bulk_updates_bit_identical(monkeypatch):
+    """The bulk-fed panel trailing updates (HERK of the Cholesky, the inverse's
+    row update) copy the slices the generating kernels form and sum them in the
+    same order: L and W = L^-1 are the same bit for bit. N = 576 has two
+    trailing updates after the 256-wide panels."""
+    p = synth.make_plan(24, 2, "spiral", 1, 2115, 1e-3, samples=1152, interleaves=2)
+
+    def factor():
+        pl = _plan(p, precision=L.MIXED_BF16X6, keep_gram=True, refine_max_iters=0).build()
+        return pl.export(L.EXPORT_CHOL).cpu().numpy(), pl.export(L.EXPORT_LINV).cpu().numpy()
+
+    Lb, Wb = factor()
+    monkeypatch.setenv("PINV_CHOL_BULK", "0")
+    Lg, Wg = factor()
+    assert np.array_equal(np.tril(Lb), np.tril(Lg))
+    assert np.array_equal(Wb, Wg)
+
+
 def test_gram_bulk_split_samples():
     """32x32, 4 coils, 4096 samples: 36 lower tiles are too few for the SMs, so
     the sample range is cut into parts whose FP32 partial sums are added in
