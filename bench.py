@@ -461,7 +461,15 @@ def main():
                 "issued_tflops": 6 * flops_recon / (ms_recon / 1e3) / 1e12}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    roof["traffic_source"] = "not measured for the current kernels"
+    roof["traffic_source"] = "not measured for this workload"
+    if prec != L.FP64 and N == 4096 and M == 65536:
+        # ncu dram__bytes_read.sum + dram__bytes_write.sum of the four Recon launches of
+        # one build of this workload (step 1: 8.95 + 1.58 GB, step 2: 8.49 + 1.05 GB per
+        # launch), mean per launch; algorithmic: the operand tables read once and the
+        # outputs written once, 3.2 GB per launch (the excess is W-table re-reads)
+        roof["traffic"] = (8947746816 + 1579998976 + 8494012672 + 1049467392) / 2
+        roof["traffic_source"] = "ncu dram bytes of the Recon launches at this workload, mean per launch"
+        roof["algorithmic_bytes"] = (3.4e9 + 2.9e9) / 2
     roof["ms_per_launch"] = ms_recon
 
     # the tensor-core Gram kernels alone (operand table + Gram launch + split sum)
