@@ -45,6 +45,7 @@ namespace pinv {
 
 pinv_status reset_status(pinv_plan* p, cudaStream_t s) {
     CK(launch_reset_status(p->st, s));
+    if (p->st_inv) CK(launch_reset_status(p->st_inv, s));
     return PINV_OK;
 }
 
@@ -109,18 +110,29 @@ pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events) {
         float2 *L32 = nullptr, *D32 = nullptr;
         CK(cudaMallocAsync((void**)&L32, sizeof(float2) * N * N, s));
         CK(cudaMallocAsync((void**)&D32, sizeof(float2) * nblk * 64 * 64, s));
-        // operand tables of the bulk-fed panel updates (PINV_CHOL_BULK=0: generated)
+        // operand tables of the bulk-fed panel updates, one region per stream
+        // (PINV_CHOL_BULK=0: generated operands)
         void* tab = nullptr;
+        const size_t tb = factor_table_bytes(N, p->slices());
         const char* env = std::getenv("PINV_CHOL_BULK");
-        if (!(env && std::strcmp(env, "0") == 0) &&
-            cudaMallocAsync(&tab, factor_table_bytes(N, p->slices()), s) != cudaSuccess) {
+        if (!(env && std::strcmp(env, "0") == 0) && cudaMallocAsync(&tab, 2 * tb, s) != cudaSuccess) {
             cudaGetLastError();
             tab = nullptr;
         }
-        CK(launch_potrf_tc(p->G, N, ld, p->Dinv, D32, L32, p->slices(), p->st, s, tab));
+        void* tab_inv = tab ? (void*)((uint8_t*)tab + tb) : nullptr;
+        // W = L^-1 on the plan's second stream, one 256-wide panel behind the Cholesky
+        // (it reads only the panel's L32 columns and diagonal inverses, final once the
+        // panel's solves are done); the Cholesky chain leaves most SMs idle
+        CK(cudaEventRecord(p->ev_fork, s));
+        CK(launch_potrf_tc(p->G, N, ld, p->Dinv, D32, L32, p->slices(), p->st, s, tab, p->ev_panel.data()));
         CK(launch_pivot_stats(p->G, N, ld, p->st, s));
         if (events) CK(cudaEventRecord(p->ev[3], s));
-        CK(launch_trtri_tc(L32, N, D32, p->W, p->W32, p->slices(), p->st, s, tab));
+        CK(cudaStreamWaitEvent(p->s_inv, p->ev_fork, 0));
+        CK(launch_trtri_tc(L32, N, D32, p->W, p->W32, p->slices(), p->st_inv, p->s_inv, tab_inv,
+                           p->ev_panel.data()));
+        CK(launch_merge_timeout(p->st, p->st_inv, p->s_inv));
+        CK(cudaEventRecord(p->ev_join, p->s_inv));
+        CK(cudaStreamWaitEvent(s, p->ev_join, 0));
         if (tab) CK(cudaFreeAsync(tab, s));
         CK(cudaFreeAsync(D32, s));
         CK(cudaFreeAsync(L32, s));
@@ -452,6 +464,15 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
         p->bytes_recon = rb;
     }
     for (auto& ev : p->ev) CKC(cudaEventCreate(&ev));
+    if (p->precision != PINV_FP64) {
+        AL(p->st_inv, sizeof(DevStatus), "inverse status");
+        CKC(cudaMemset(p->st_inv, 0, sizeof(DevStatus)));
+        CKC(cudaStreamCreateWithFlags(&p->s_inv, cudaStreamNonBlocking));
+        p->ev_panel.assign((size_t)((p->N + 255) / 256), nullptr);
+        for (auto& ev : p->ev_panel) CKC(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CKC(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+        CKC(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    }
     pinv_status rs = reset_status(p, s);
     if (rs != PINV_OK) return cleanup(rs);
     CKC(cudaStreamSynchronize(s));

@@ -298,6 +298,7 @@ cudaError_t launch_from_df(const float4* a, int64_t n, double2* b, cudaStream_t 
 // Cholesky. Storage stays FP64. Only the 64 pivots use FP64 (one rsqrt each).
 namespace {
 constexpr int NBD = 64;
+constexpr int NBDP = NBD + 1;  // padded row stride of the shared-memory blocks
 constexpr int DIAG_THREADS = 1024;  // 16 lanes per column in the inverse
 __device__ inline float4 df_scale(float4 a, float rh, float rl) {  // complex DF times real DF
     float xh, xl, yh, yl;
@@ -346,20 +347,22 @@ constexpr int PB = 16;  // panel width
 __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0,
                                                              double2* Dinv, float2* Dinv32, DevStatus* st) {
     extern __shared__ float4 smd[];
-    float4* A = smd;                  // [NBD][NBD]
-    float4* X = smd + NBD * NBD;      // [NBD][NBD] inverse
+    float4* A = smd;                  // [NBD][NBDP]: rows padded by 16 bytes, so that
+                                      // column accesses of a warp spread over all banks
+    float4* X = smd + NBD * NBDP;     // [NBD][NBDP] inverse
     __shared__ float4 T[3][PB][PB];   // block sums of the current diagonal level
     __shared__ float2 rdiag[NBD];     // 1 / L_jj as (hi, lo)
     __shared__ int bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nb = (int)((N - k0) < NBD ? (N - k0) : NBD);
     if (tid == 0) bad = (st->not_pd_pivot != INT_MAX) ? 1 : 0;
+#pragma unroll
     for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
         const int i = e / NBD, j = e % NBD;
         double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
         if (i < nb && j < nb && j <= i) v = G[(k0 + i) * ld + k0 + j];
-        A[e] = to_df(v);
-        X[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        A[i * NBDP + j] = to_df(v);
+        X[i * NBDP + j] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
 
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
                 const int jc = p0 + c;
                 float2 r = make_float2(0.f, 0.f);
                 if (lane == 0) {
-                    const float4 a = A[jc * NBD + jc];
+                    const float4 a = A[jc * NBDP + jc];
                     float dh = a.x, dl = a.y;
                     if (!((double)dh + (double)dl > 0.0) || !isfinite(dh)) {
                         if (!bad) atomicMin(&st->not_pd_pivot, (int)(k0 + jc));
@@ -381,23 +384,23 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
                     r = df_rsqrt(dh, dl);
                     float lh, ll;
                     df_mul(dh, dl, r.x, r.y, lh, ll);  // L_jj = d / sqrt(d)
-                    A[jc * NBD + jc] = make_float4(lh, ll, 0.f, 0.f);
+                    A[jc * NBDP + jc] = make_float4(lh, ll, 0.f, 0.f);
                     rdiag[jc] = r;
                 }
                 r.x = __shfl_sync(0xffffffffu, r.x, 0);
                 r.y = __shfl_sync(0xffffffffu, r.y, 0);
                 // scale column c below the diagonal inside the block
                 const int i = p0 + (lane & (PB - 1));
-                if (lane < PB && i > jc) A[i * NBD + jc] = df_norm(df_scale(A[i * NBD + jc], r.x, r.y));
+                if (lane < PB && i > jc) A[i * NBDP + jc] = df_norm(df_scale(A[i * NBDP + jc], r.x, r.y));
                 __syncwarp();
                 // trailing update inside the block: rows and columns c+1..15
                 for (int e = lane; e < PB * PB; e += 32) {
                     const int ii = p0 + e / PB, kk = p0 + e % PB;
                     if (kk > jc && ii >= kk) {
-                        float4 v = A[ii * NBD + kk];
-                        const float4 a = A[ii * NBD + jc], b = A[kk * NBD + jc];
+                        float4 v = A[ii * NBDP + kk];
+                        const float4 a = A[ii * NBDP + jc], b = A[kk * NBDP + jc];
                         cacc(v, make_float4(-a.x, -a.y, -a.z, -a.w), cdf_conj(b));
-                        A[ii * NBD + kk] = df_norm(v);
+                        A[ii * NBDP + kk] = df_norm(v);
                     }
                 }
                 __syncwarp();
@@ -409,12 +412,12 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
         if (tid < rows_below) {  // in place: x_c overwrites A[i][p0 + c] once known
             const int i = p0 + PB + tid;
             for (int c = 0; c < PB; ++c) {
-                float4 v = A[i * NBD + p0 + c];
+                float4 v = A[i * NBDP + p0 + c];
                 for (int c2 = 0; c2 < c; ++c2) {
-                    const float4 x = A[i * NBD + p0 + c2], l = A[(p0 + c) * NBD + p0 + c2];
+                    const float4 x = A[i * NBDP + p0 + c2], l = A[(p0 + c) * NBDP + p0 + c2];
                     cacc(v, make_float4(-x.x, -x.y, -x.z, -x.w), cdf_conj(l));
                 }
-                A[i * NBD + p0 + c] = df_norm(df_scale(df_norm(v), rdiag[p0 + c].x, rdiag[p0 + c].y));
+                A[i * NBDP + p0 + c] = df_norm(df_scale(df_norm(v), rdiag[p0 + c].x, rdiag[p0 + c].y));
             }
         }
         __syncthreads();
@@ -423,13 +426,13 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
             for (int e = tid; e < rows_below * rows_below; e += DIAG_THREADS) {
                 const int ii = p0 + PB + e / rows_below, kk = p0 + PB + e % rows_below;
                 if (kk > ii) continue;
-                float4 v = A[ii * NBD + kk];
+                float4 v = A[ii * NBDP + kk];
 #pragma unroll
                 for (int c = 0; c < PB; ++c) {
-                    const float4 a = A[ii * NBD + p0 + c], b = A[kk * NBD + p0 + c];
+                    const float4 a = A[ii * NBDP + p0 + c], b = A[kk * NBDP + p0 + c];
                     cacc(v, make_float4(-a.x, -a.y, -a.z, -a.w), cdf_conj(b));
                 }
-                A[ii * NBD + kk] = df_norm(v);
+                A[ii * NBDP + kk] = df_norm(v);
             }
         }
         __syncthreads();
@@ -441,10 +444,10 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
         for (int i = p0; i < p0 + PB; ++i) {
             float4 v = make_float4(i == c ? 1.f : 0.f, 0.f, 0.f, 0.f);
             for (int k = c; k < i; ++k) {
-                const float4 l = A[i * NBD + k];
-                cacc(v, make_float4(-l.x, -l.y, -l.z, -l.w), X[k * NBD + c]);
+                const float4 l = A[i * NBDP + k];
+                cacc(v, make_float4(-l.x, -l.y, -l.z, -l.w), X[k * NBDP + c]);
             }
-            X[i * NBD + c] = i >= c ? df_norm(df_scale(df_norm(v), rdiag[i].x, rdiag[i].y)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            X[i * NBDP + c] = i >= c ? df_norm(df_scale(df_norm(v), rdiag[i].x, rdiag[i].y)) : make_float4(0.f, 0.f, 0.f, 0.f);
             __syncwarp(0x0000ffffu);
         }
     }
@@ -457,7 +460,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
             const int pr = e / (PB * PB), ii = (e / PB) % PB, cc = e % PB;
             const int p = pr, q = p + d;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int k = p * PB; k < q * PB; ++k) cacc(v, A[(q * PB + ii) * NBD + k], X[k * NBD + p * PB + cc]);
+            for (int k = p * PB; k < q * PB; ++k) cacc(v, A[(q * PB + ii) * NBDP + k], X[k * NBDP + p * PB + cc]);
             T[pr][ii][cc] = df_norm(v);
         }
         __syncthreads();
@@ -466,25 +469,26 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
             const int pr = e / (PB * PB), ii = (e / PB) % PB, cc = e % PB;
             const int p = pr, q = p + d;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int k = 0; k <= ii; ++k) cacc(v, X[(q * PB + ii) * NBD + q * PB + k], T[pr][k][cc]);
+            for (int k = 0; k <= ii; ++k) cacc(v, X[(q * PB + ii) * NBDP + q * PB + k], T[pr][k][cc]);
             v = df_norm(v);
-            X[(q * PB + ii) * NBD + p * PB + cc] = make_float4(-v.x, -v.y, -v.z, -v.w);
+            X[(q * PB + ii) * NBDP + p * PB + cc] = make_float4(-v.x, -v.y, -v.z, -v.w);
         }
         __syncthreads();
     }
+#pragma unroll
     for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
         const int i = e / NBD, j = e % NBD;
-        const double2 x = from_df(X[e]);
+        const double2 x = from_df(X[i * NBDP + j]);
         Dinv[e] = x;
         if (Dinv32) Dinv32[e] = make_float2((float)x.x, (float)x.y);
-        if (i < nb && j < nb && j <= i) G[(k0 + i) * ld + k0 + j] = from_df(A[e]);
+        if (i < nb && j < nb && j <= i) G[(k0 + i) * ld + k0 + j] = from_df(A[i * NBDP + j]);
     }
 }
 
 cudaError_t launch_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv, float2* Dinv32,
                                  DevStatus* st, cudaStream_t s) {
     static bool attr = false;
-    const size_t smem = 2 * NBD * NBD * sizeof(float4);
+    const size_t smem = 2 * NBD * NBDP * sizeof(float4);
     if (!attr) {
         cudaError_t err =
             cudaFuncSetAttribute(k_potrf_diag_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -206,11 +206,16 @@ cudaError_t launch_apply32(const float2* R, int64_t N, int64_t M, const float2* 
 // tab (factor_table_bytes(), or nullptr): operand tables of the bulk-fed
 // panel trailing updates; without it the updates generate their operands.
 size_t factor_table_bytes(int64_t N, int slices);
+// ev_panel (or nullptr): one event per 256-wide panel, recorded by the Cholesky once
+// the panel's columns of L32 and its diagonal inverses are final, and waited on by
+// the inverse before that panel
 cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, float2* Dinv32, float2* L32,
-                            int slices, DevStatus* st, cudaStream_t s, void* tab = nullptr);
+                            int slices, DevStatus* st, cudaStream_t s, void* tab = nullptr,
+                            const cudaEvent_t* ev_panel = nullptr);
 // W = L^-1 (FP64 storage, tensor-core updates) and its FP32 copy W32.
 cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, double2* W, float2* W32,
-                            int slices, DevStatus* st, cudaStream_t s, void* tab = nullptr);
+                            int slices, DevStatus* st, cudaStream_t s, void* tab = nullptr,
+                            const cudaEvent_t* ev_panel = nullptr);
 bool tc_available();
 
 // ---------------------------------------------------------------------------
@@ -219,6 +224,7 @@ bool tc_available();
 cudaError_t launch_to_df(const double2* src, float4* dst, int64_t n, cudaStream_t s);
 // U[f] = D[f] - E X[f], double-float arithmetic, FP64 in/out
 cudaError_t launch_reset_status(DevStatus* st, cudaStream_t s);
+cudaError_t launch_merge_timeout(DevStatus* dst, const DevStatus* src, cudaStream_t s);
 
 // Several plans' tensor-core Gram or Recon in one persistent launch. The
 // problem descriptors are uploaded once (tc_multi_create) and stay valid

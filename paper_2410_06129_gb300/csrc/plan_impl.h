@@ -90,6 +90,12 @@ struct pinv_plan {
     int* eG = nullptr;         // |G| <= 2^eG (device)
     pinv::DevStatus* st = nullptr;        // device status word
     pinv::DevStatus* st_host = nullptr;   // pinned copy, written at the end of each build
+    // mixed plans: the triangular inverse runs beside the Cholesky on its own stream,
+    // one panel behind (its tile counter and timeout record; one event per panel)
+    pinv::DevStatus* st_inv = nullptr;
+    cudaStream_t s_inv = nullptr;
+    std::vector<cudaEvent_t> ev_panel;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // pinv_apply's scratch region, grown on demand
     void* scratch_buf = nullptr;
@@ -141,5 +147,10 @@ struct pinv_plan {
         if (st_host) cudaFreeHost(st_host);
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
+        for (auto& e : ev_panel)
+            if (e) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (s_inv) cudaStreamDestroy(s_inv);
     }
 };

@@ -225,6 +225,16 @@ cudaError_t launch_reset_status(DevStatus* st, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// a bounded wait that gave up on another stream's status block counts for the plan
+__global__ void k_merge_timeout(DevStatus* dst, const DevStatus* src) {
+    if (src->timeout_site) atomicMax(&dst->timeout_site, src->timeout_site);
+}
+cudaError_t launch_merge_timeout(DevStatus* dst, const DevStatus* src, cudaStream_t s) {
+    k_merge_timeout<<<1, 1, 0, s>>>(dst, src);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // dst[c][r] = src[r][c] for double-float tables, rows padded with zeros to ldd
 __global__ void k_transpose_df(const float4* __restrict__ src, int64_t rows, int64_t cols, float4* __restrict__ dst,
                                int64_t ldd) {

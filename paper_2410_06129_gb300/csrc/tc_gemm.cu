@@ -1000,7 +1000,7 @@ static cudaError_t panel_table(const float2* L32, int64_t N, int64_t p0, int64_t
 constexpr int NBK = 64, NBP = 256;
 
 cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, float2* Dinv32, float2* L32,
-                            int slices, DevStatus* st, cudaStream_t s, void* tab) {
+                            int slices, DevStatus* st, cudaStream_t s, void* tab, const cudaEvent_t* ev_panel) {
     for (int64_t p0 = 0; p0 < N; p0 += NBP) {
         const int64_t pend = std::min<int64_t>(N, p0 + NBP);
         for (int64_t k0 = p0; k0 < pend; k0 += NBK) {
@@ -1023,6 +1023,10 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
                     return e;
             }
         }
+        if (ev_panel) {
+            cudaError_t e = cudaEventRecord(ev_panel[p0 / NBP], s);
+            if (e != cudaSuccess) return e;
+        }
         if (pend < N) {  // trailing matrix, K = panel width
             cudaError_t e;
             if (tab) {
@@ -1044,11 +1048,12 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
 // inside a 256-row panel each 64-row step updates the panel's rows only; the
 // rows below get one update per panel with K = 256.
 cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, double2* W, float2* W32,
-                            int slices, DevStatus* st, cudaStream_t s, void* tab) {
+                            int slices, DevStatus* st, cudaStream_t s, void* tab, const cudaEvent_t* ev_panel) {
     cudaError_t e = launch_fill_identity(W, N, N, s);
     if (e != cudaSuccess) return e;
     for (int64_t p0 = 0; p0 < N; p0 += NBP) {
         const int64_t pend = std::min<int64_t>(N, p0 + NBP);
+        if (ev_panel && (e = cudaStreamWaitEvent(s, ev_panel[p0 / NBP], 0)) != cudaSuccess) return e;
         for (int64_t k0 = p0; k0 < pend; k0 += NBK) {
             const int64_t nbk = std::min<int64_t>(NBK, N - k0);
             const int64_t ncol = k0 + nbk;
