@@ -90,13 +90,20 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
     if (p->Gkeep) CK(cudaMemcpyAsync(p->Gkeep, p->G, sizeof(double2) * N * N, cudaMemcpyDeviceToDevice, s));
     if (p->Gx) {
         // exact Gram for the refinement residual (Toeplitz table, then coil products,
-        // then its digit tiles)
+        // then its digit tiles). Only applies read it, so mixed plans form it on their
+        // second stream beside the Cholesky (build_factor joins that stream).
+        cudaStream_t sx = s;
+        if (p->s_inv) {
+            CK(cudaEventRecord(p->ev_xfork, s));
+            CK(cudaStreamWaitEvent(p->s_inv, p->ev_xfork, 0));
+            sx = p->s_inv;
+        }
         double2* work = nullptr;
-        CK(cudaMallocAsync((void**)&work, toeplitz_work_bytes(p->enc), s));
-        CK(launch_toeplitz64(p->enc, work, p->Ttab, s));
-        CK(cudaFreeAsync(work, s));
-        CK(launch_gram_exact(p->enc, p->Ttab, p->lambda_abs, p->Gx, s));
-        if (p->Gd) CK(launch_gram_digits(p->Gx, N, p->eG, p->Gd, s));
+        CK(cudaMallocAsync((void**)&work, toeplitz_work_bytes(p->enc), sx));
+        CK(launch_toeplitz64(p->enc, work, p->Ttab, sx));
+        CK(cudaFreeAsync(work, sx));
+        CK(launch_gram_exact(p->enc, p->Ttab, p->lambda_abs, p->Gx, sx));
+        if (p->Gd) CK(launch_gram_digits(p->Gx, N, p->eG, p->Gd, sx));
     }
     return PINV_OK;
 }
@@ -472,6 +479,7 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
         for (auto& ev : p->ev_panel) CKC(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         CKC(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
         CKC(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+        CKC(cudaEventCreateWithFlags(&p->ev_xfork, cudaEventDisableTiming));
     }
     pinv_status rs = reset_status(p, s);
     if (rs != PINV_OK) return cleanup(rs);

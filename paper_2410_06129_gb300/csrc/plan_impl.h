@@ -95,7 +95,7 @@ struct pinv_plan {
     pinv::DevStatus* st_inv = nullptr;
     cudaStream_t s_inv = nullptr;
     std::vector<cudaEvent_t> ev_panel;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_xfork = nullptr;
 
     // pinv_apply's scratch region, grown on demand
     void* scratch_buf = nullptr;
@@ -151,6 +151,7 @@ struct pinv_plan {
             if (e) cudaEventDestroy(e);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
+        if (ev_xfork) cudaEventDestroy(ev_xfork);
         if (s_inv) cudaStreamDestroy(s_inv);
     }
 };
