@@ -18,6 +18,10 @@ Every function follows the paper's definition directly:
   * image = G^-1 (sum_c Encode_c^H data_c)          Section 3.3, last paragraph
   * SRF = Recon x Encode                            Eq. 9
   * X = Recon Psi Recon^H                           Eq. 10
+  * Encode^H Encode = P Lambda P^H, eigenvalues the squared singular values of
+      Encode; truncated reconstruction P_r Lambda_r^-1 P_r^H Encode^H data with
+      r set by a fraction of the energy                Section 2.1 (SVD, tSVD,
+      eigenvalue decomposition)
 Parity status: every function here is pinned by tests/test_oracle_pins.py
 (SVD brute force, Cartesian closed form, invariants).
 """
@@ -157,6 +161,40 @@ def srf(recon: np.ndarray, E: np.ndarray) -> np.ndarray:
 def noise_matrix(recon: np.ndarray, psi: np.ndarray) -> np.ndarray:
     """Noise matrix X = Recon Psi Recon^H (Eq. 10); psi is [C*M_k]^2."""
     return recon @ psi @ recon.conj().T
+
+
+# --------------------------------------------------------------------------
+# eigenvalue decomposition and truncated SVD (Section 2.1)
+# --------------------------------------------------------------------------
+def gram_eig(E: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Encode^H Encode = P diag(mu) P^H, mu in decreasing order (Section 2.1,
+    eigenvalue decomposition: the eigenvalues of the Gram matrix are the squared
+    singular values of Encode). Column i of P is the eigenvector of mu[i]."""
+    mu, vecs = np.linalg.eigh(E.conj().T @ E)
+    order = np.argsort(mu)[::-1]
+    return mu[order], vecs[:, order]
+
+
+def tsvd_rank(mu: np.ndarray, energy: float) -> int:
+    """Smallest r whose r largest eigenvalues hold the fraction `energy` of their
+    sum (Section 2.1: the truncation keeps a set share of the energy, e.g. 95 %)."""
+    c = np.cumsum(np.maximum(mu, 0.0))
+    r = int(np.searchsorted(c, energy * c[-1], side="left")) + 1
+    return min(r, len(mu))
+
+
+def tsvd_condition(mu: np.ndarray, r: int) -> float:
+    """Condition number of the truncated problem: largest over smallest kept
+    singular value (Section 2.1)."""
+    return float(np.sqrt(mu[0] / mu[r - 1]))
+
+
+def tsvd_solve(mu: np.ndarray, vecs: np.ndarray, b_cols: np.ndarray, r: int, lam: float = 0.0) -> np.ndarray:
+    """image = P_r diag(1 / (mu_r + lam)) P_r^H (Encode^H data), the truncated
+    eigen-reconstruction, with Tikhonov loading lam when combined (Section 2.1).
+    b_cols holds Encode^H data, one column per frame."""
+    pr = vecs[:, :r]
+    return pr @ ((pr.conj().T @ b_cols) / (mu[:r] + lam)[:, None])
 
 
 # --------------------------------------------------------------------------

@@ -251,3 +251,86 @@ def test_planted_sign_flip_fails_cartesian_pin():
     sgn = ((-1.0) ** (j[:, None] + j[None, :]))
     adj = sgn * (side * side * np.fft.ifft2(d.reshape(side, side) * sgn))
     assert O.nrmse(E_bad.conj().T @ d, adj.ravel()) > 1e-3
+
+
+# ---------------------------------------------------------------- eigen / tSVD (Section 2.1)
+def test_gram_eig_reconstructs_and_matches_svd():
+    """P diag(mu) P^H = E^H E with orthonormal P, and mu (decreasing) are the
+    squared singular values of E from an SVD (a different factorisation)."""
+    p = _small_plan(seed=13, coils=2)
+    E = O.plan_encode(p)
+    mu, P = O.gram_eig(E)
+    G0 = E.conj().T @ E
+    assert np.all(np.diff(mu) <= 1e-9 * mu[0])
+    assert np.max(np.abs(P.conj().T @ P - np.eye(len(mu)))) < 1e-12
+    assert np.max(np.abs(P @ np.diag(mu) @ P.conj().T - G0)) < 1e-11 * mu[0]
+    sv = np.linalg.svd(E, compute_uv=False) ** 2
+    assert np.max(np.abs(mu - sv)) < 1e-11 * mu[0]
+
+
+def test_gram_eig_cartesian_closed_form():
+    """Fully sampled Cartesian single coil: E^H E = N I, so every eigenvalue is N."""
+    side = 8
+    k, _ = synth.cartesian(side)
+    E = O.encode(k, O.voxel_positions((side, side)))
+    mu, _ = O.gram_eig(E)
+    N = side * side
+    assert np.max(np.abs(mu - N)) < 1e-10 * N
+
+
+def test_tsvd_rank_and_condition_hand_example():
+    """mu = (4, 3, 2, 1): cumulative energy 4, 7, 9, 10; 70 % -> r = 2, kappa =
+    sqrt(4 / 3); 100 % keeps everything."""
+    mu = np.array([4.0, 3.0, 2.0, 1.0])
+    assert O.tsvd_rank(mu, 0.7) == 2
+    assert O.tsvd_rank(mu, 0.71) == 3
+    assert O.tsvd_rank(mu, 1.0) == 4
+    assert abs(O.tsvd_condition(mu, 2) - np.sqrt(4.0 / 3.0)) < 1e-15
+
+
+def test_tsvd_full_rank_equals_normal_equation_solution():
+    """With every eigenvalue kept and no loading, the truncated reconstruction is
+    the least-squares solution, here from the oracle's Cholesky path at lam = 0."""
+    rng = np.random.default_rng(21)
+    E = _rand_complex(rng, 60, 24)
+    d = _rand_complex(rng, 60, 2)
+    mu, P = O.gram_eig(E)
+    b = E.conj().T @ d
+    x = O.tsvd_solve(mu, P, b, len(mu))
+    L = O.cholesky(O.gram(E, 0.0))
+    ref = O.back_substitution_h(L, O.forward_substitution(L, b))
+    assert O.nrmse(x, ref) < 1e-10
+
+
+def test_tsvd_truncation_on_a_constructed_spectrum():
+    """E = U diag(s) V^H with known s: keeping r singular values gives
+    V_r diag(1 / s_r) U_r^H d, and with loading lam, V_r diag(s_r / (s_r^2 + lam)) U_r^H d."""
+    rng = np.random.default_rng(22)
+    U, _ = np.linalg.qr(_rand_complex(rng, 40, 16))
+    V, _ = np.linalg.qr(_rand_complex(rng, 16, 16))
+    s = np.geomspace(10.0, 0.01, 16)
+    E = U @ np.diag(s) @ V.conj().T
+    d = _rand_complex(rng, 40, 3)
+    mu, P = O.gram_eig(E)
+    r = O.tsvd_rank(mu, 0.999)
+    b = E.conj().T @ d
+    want = V[:, :r] @ ((U[:, :r].conj().T @ d) / s[:r, None])
+    assert O.nrmse(O.tsvd_solve(mu, P, b, r), want) < 1e-10
+    want_t = V[:, :r] @ ((s[:r] / (s[:r] ** 2 + 0.1))[:, None] * (U[:, :r].conj().T @ d))
+    assert O.nrmse(O.tsvd_solve(mu, P, b, r, lam=0.1), want_t) < 1e-10
+    assert abs(O.tsvd_condition(mu, r) - s[0] / s[r - 1]) < 1e-9 * s[0] / s[r - 1]
+
+
+def test_planted_mistake_fails_tsvd_pin():
+    """Dropping the conjugate of P_r^H (a plausible slip) fails the constructed pin."""
+    rng = np.random.default_rng(23)
+    U, _ = np.linalg.qr(_rand_complex(rng, 30, 10))
+    V, _ = np.linalg.qr(_rand_complex(rng, 10, 10))
+    s = np.geomspace(5.0, 0.1, 10)
+    E = U @ np.diag(s) @ V.conj().T
+    d = _rand_complex(rng, 30, 1)
+    mu, P = O.gram_eig(E)
+    b = E.conj().T @ d
+    bad = P[:, :6] @ ((P[:, :6].T @ b) / mu[:6, None])
+    want = V[:, :6] @ ((U[:, :6].conj().T @ d) / s[:6, None])
+    assert O.nrmse(bad, want) > 1e-3
