@@ -286,6 +286,47 @@ def run_batch(prec, refine, steps, warmup, frames=256, seed=3100):
             "gpu_launches_per_step": int(launches), "steps": steps}
 
 
+def run_spectrum(side=32, frames=64, energy=0.95, seed=6100):
+    """Eigendecomposition of the Gram matrix and the truncated reconstruction
+    (Section 2.1) on workload 1's size (side^2 voxels, one spiral of 2 N samples),
+    FP64, with the oracle's eigendecomposition timed on the host beside it."""
+    from paper_2410_06129_gb300 import synth as _sy
+    inp = _sy.make_plan(side, 1, "spiral", frames, seed, 1e-3, samples=2 * side * side, interleaves=1)
+    N = inp.n_vox
+    with Plan.from_inputs(inp, precision=L.FP64, keep_gram=True) as pl:
+        pl.build()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mu, P, sweeps = pl.eig()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_eig = e0.elapsed_time(e1)
+        d = torch.from_numpy(inp.data).cuda()
+        pl.tsvd_apply(mu, P, d, energy=energy)  # warm
+        torch.cuda.synchronize()
+        e0.record()
+        x, r, kappa = pl.tsvd_apply(mu, P, d, energy=energy)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_tsvd = e0.elapsed_time(e1)
+        mu_h = mu.cpu().numpy()
+    # FP64 work of the Jacobi rounds: per round the column pass rotates G and V
+    # (2 N^2 entries) and the row pass G (N^2), 14 flop per entry (two complex
+    # products and a sum); N - 1 rounds per sweep
+    rounds = N - 1 if N % 2 == 0 else N
+    flops = 42.0 * N * N * rounds * sweeps
+    import oracle.pinv_oracle as O
+    t0 = time.perf_counter()
+    mu_ref, _ = O.gram_eig(O.plan_encode(inp))
+    cpu_s = time.perf_counter() - t0
+    return {"workload": f"{side}x{side} (N={N}), 1 coil, one spiral of {2 * N} samples, FP64 plan, {frames} frames",
+            "eig_s": ms_eig / 1e3, "sweeps": sweeps, "fp64_tflops": flops / (ms_eig / 1e3) / 1e12,
+            "fp64_peak_tflops": FP64_PEAK_TFLOPS, "tsvd_energy": energy, "tsvd_rank": r, "tsvd_kappa": kappa,
+            "tsvd_apply_ms": ms_tsvd, "max_eig_err_vs_oracle": float(np.max(np.abs(mu_h - mu_ref)) / mu_ref[0]),
+            "cpu_oracle_eig_s": cpu_s, "cpu_cores": _cores()}
+
+
 def run_cfg5(prec, refine, frames=64, seed=5100):
     """Workload 5: 192x192 (N = 36864), 8 coils, 384 radial spokes x 125 samples
     (M = 384000), B0 +-50 Hz, lambda_rel 1e-4, 64 complex64 frames; factor-only
@@ -351,6 +392,8 @@ def main():
     ap.add_argument("--serve-refine", type=int, default=3)
     ap.add_argument("--batch", default="on", choices=["on", "off"],
                     help="workload 3: 16 uneven plans x 256 frames as one graph-replayed batch")
+    ap.add_argument("--spectrum", default="on", choices=["on", "off"],
+                    help="Gram eigendecomposition and tSVD reconstruction at workload 1's size")
     ap.add_argument("--cfg5", default="off", choices=["on", "off"],
                     help="workload 5 (192x192, B0, factor-only): one build and one timed apply")
     ap.add_argument("--serve-fp64-duration", type=float, default=1.0,
@@ -547,6 +590,10 @@ def main():
             serve["fp64"] = run_serve(L.FP64, 0, div, args.serve_rate, args.serve_fp64_duration, budget,
                                       args.serve_slots, L.RECON_NONE)
 
+    spectrum = None
+    if rank == 0 and args.spectrum == "on":
+        spectrum = run_spectrum()
+
     cfg5 = None
     if rank == 0 and args.cfg5 == "on":
         cfg5 = run_cfg5(prec, refine if prec != L.FP64 else 1)
@@ -581,6 +628,8 @@ def main():
             line["batch"] = batch
         if cfg5 is not None:
             line["cfg5"] = cfg5
+        if spectrum is not None:
+            line["spectrum"] = spectrum
         if serve is not None:
             line["serve"] = serve
             line["serve_p50_ms"] = serve["mixed"]["p50_ms"]

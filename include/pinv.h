@@ -350,6 +350,32 @@ size_t pinv_autotune_report(char* buf, size_t bytes);
 typedef enum { PINV_MAP_SRF = 0, PINV_MAP_NOISE = 1 } pinv_map_what;
 pinv_status pinv_plan_map(pinv_plan* plan, int what, const double* psi, double* d_out, void* cuda_stream);
 
+/* Eigenvalue decomposition of the Gram matrix (Section 2.1: the eigenvalues of
+ * E^H E are the squared singular values of Encode, and their spectrum shows the
+ * conditioning): E^H E + lambda I = P diag(mu + lambda) P^H, by parallel cyclic
+ * Jacobi in FP64 on the plan's kept Gram (pinv_plan_keep_gram before the build;
+ * a mixed plan's Gram carries its split-precision rounding).
+ *   d_mu  [N] doubles, device: eigenvalues of E^H E (lambda removed), decreasing.
+ *   d_P   [N][N] c128, device, row-major, column i the eigenvector of mu[i];
+ *         may be NULL (eigenvalues only).
+ *   sweeps_out  Jacobi sweeps taken (may be NULL).
+ * Synchronises with the device once per sweep. Sweeps stop at an off-diagonal
+ * Frobenius norm of 4 N eps of the whole, or once a sweep no longer halves it
+ * below 1e-10. UNSUPPORTED without a kept Gram or for N > 8192;
+ * PINV_ERR_INTERNAL if 30 sweeps do not converge (the outputs are still written). */
+pinv_status pinv_plan_eig(pinv_plan* plan, double* d_mu, void* d_P, int* sweeps_out, void* cuda_stream);
+
+/* Truncated eigen (tSVD) reconstruction (Section 2.1): image = P_r diag(1 / (mu_r
+ * + lam)) P_r^H E^H data, r the fewest leading eigenvalues holding the fraction
+ * `energy` of the sum of mu (in (0, 1]; 1 keeps all), lam >= 0 an optional
+ * Tikhonov loading combined with the truncation. d_mu / d_P from pinv_plan_eig;
+ * data [F][C][M_k] and image [F][N] as pinv_apply (dtype PINV_C64 or PINV_C128).
+ * rank_out / kappa_out (may be NULL; if given the call waits for the device):
+ * r and the condition number sqrt(mu[0] / mu[r-1]) of the truncated problem. */
+pinv_status pinv_tsvd_apply(pinv_plan* plan, const double* d_mu, const void* d_P, double energy, double lam,
+                            const void* d_data, void* d_image, int64_t n_frames, int dtype, int* rank_out,
+                            double* kappa_out, void* cuda_stream);
+
 /* Size of the fixed device scratch array behind pinv_apply_noalloc (64 MiB). */
 #define PINV_NOALLOC_SCRATCH_BYTES (64u << 20)
 

@@ -95,6 +95,9 @@ SIGNATURES = {
     "pinv_plan_destroy": (None, [_VP]),
     "pinv_apply_noalloc": (C.c_int, [_VP, _VP, _VP, C.c_int64, C.c_int, _VP]),
     "pinv_plan_map": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_double), _VP, _VP]),
+    "pinv_plan_eig": (C.c_int, [_VP, _VP, _VP, C.POINTER(C.c_int), _VP]),
+    "pinv_tsvd_apply": (C.c_int, [_VP, _VP, _VP, C.c_double, C.c_double, _VP, _VP, C.c_int64, C.c_int,
+                                  C.POINTER(C.c_int), C.POINTER(C.c_double), _VP]),
     "pinv_autotune_report": (C.c_size_t, [C.c_char_p, C.c_size_t]),
     "pinv_batch_create": (C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, C.POINTER(_VP)]),
     "pinv_batch_build": (C.c_int, [_VP, _VP]),

@@ -108,6 +108,31 @@ class Plan:
         L.check(L.load().pinv_plan_map(self._h, int(what), ptr, out.data_ptr(), _stream_handle(stream)))
         return out
 
+    def eig(self, vectors: bool = True, stream=None):
+        """Eigenvalues mu (float64 [N], decreasing) of E^H E and, if asked, the
+        eigenvectors P (complex128 [N][N], column i for mu[i]); needs keep_gram.
+        Returns (mu, P or None, sweeps)."""
+        mu = torch.empty(self.n_vox, dtype=torch.float64, device="cuda")
+        P = torch.empty((self.n_vox, self.n_vox), dtype=torch.complex128, device="cuda") if vectors else None
+        sweeps = C.c_int(0)
+        L.check(L.load().pinv_plan_eig(self._h, mu.data_ptr(), P.data_ptr() if P is not None else None,
+                                       C.byref(sweeps), _stream_handle(stream)))
+        return mu, P, sweeps.value
+
+    def tsvd_apply(self, mu: torch.Tensor, P: torch.Tensor, data: torch.Tensor, energy: float = 0.95,
+                   lam: float = 0.0, stream=None):
+        """Truncated eigen reconstruction of data [F][C*M_k] (complex64 or complex128):
+        returns (images [F][N] in the data's dtype, rank r, condition number)."""
+        data = data.contiguous()
+        F = data.shape[0] if data.dim() >= 2 else 1  # [F][C*M_k] or [F][C][M_k]
+        dtype = L.C128 if data.dtype == torch.complex128 else L.C64
+        out = torch.empty((F, self.n_vox), dtype=data.dtype, device="cuda")
+        r, kappa = C.c_int(0), C.c_double(0.0)
+        L.check(L.load().pinv_tsvd_apply(self._h, mu.data_ptr(), P.data_ptr(), float(energy), float(lam),
+                                         data.data_ptr(), out.data_ptr(), F, dtype, C.byref(r), C.byref(kappa),
+                                         _stream_handle(stream)))
+        return out, r.value, kappa.value
+
     def info(self) -> dict:
         inf = L.PlanInfo()
         L.check(L.load().pinv_plan_info(self._h, C.byref(inf)))
