@@ -290,7 +290,12 @@ def run_spectrum(side=32, frames=64, energy=0.95, seed=6100):
     """Eigendecomposition of the Gram matrix and the truncated reconstruction
     (Section 2.1) on workload 1's size (side^2 voxels, one spiral of 2 N samples),
     FP64, with the oracle's eigendecomposition timed on the host beside it."""
+    import numpy as np
+    import torch
+
+    from paper_2410_06129_gb300 import _lib as L
     from paper_2410_06129_gb300 import synth as _sy
+    from paper_2410_06129_gb300.plan import Plan
     inp = _sy.make_plan(side, 1, "spiral", frames, seed, 1e-3, samples=2 * side * side, interleaves=1)
     N = inp.n_vox
     with Plan.from_inputs(inp, precision=L.FP64, keep_gram=True) as pl:

@@ -976,6 +976,86 @@ cudaError_t launch_gram_bulk(const EncodeDev& e, double lambda, int slices, doub
     return gram_bulk_finish(e, lambda, slices, G, ld, work, s);
 }
 
+// ------------------------------------------------------------------ panel-internal updates (FP32 SIMT)
+// Inside a 256-wide panel the solves and updates have K = 64: work of a few
+// microseconds that a tensor-core launch spends on setting up TMEM, barriers and
+// its pipeline. These kernels stage the 64-wide operands in shared memory and
+// accumulate in FP32 (the accuracy class of the split-BF16 products).
+constexpr int PNL_ROWS_TRSM = 16, PNL_ROWS_HERK = 32, PNL_MAXW = 192;
+
+// L[i][k0 + j] = sum_k P[i][k] conj(Dinv[j][k]) for rows i >= row0: written to G
+// (FP64) and back over P (FP32), in place (each CTA reads its rows first)
+__global__ void __launch_bounds__(256) k_trsm_panel(float2* P, int64_t ldp, const float2* __restrict__ Dinv32,
+                                                  double2* G, int64_t ldg, int64_t k0, int nbk, int64_t row0,
+                                                  int64_t N) {
+    __shared__ float2 D[64][65];
+    __shared__ float2 A[PNL_ROWS_TRSM][64];
+    const int tid = threadIdx.x;
+    const int64_t i0 = row0 + (int64_t)blockIdx.x * PNL_ROWS_TRSM;
+    for (int e = tid; e < 64 * 64; e += 256) {
+        const int j = e / 64, k = e % 64;
+        D[j][k] = (j < nbk && k < nbk) ? Dinv32[j * 64 + k] : make_float2(0.f, 0.f);
+    }
+    for (int e = tid; e < PNL_ROWS_TRSM * 64; e += 256) {
+        const int r = e / 64, k = e % 64;
+        const int64_t i = i0 + r;
+        A[r][k] = (i < N && k < nbk) ? P[i * ldp + k] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PNL_ROWS_TRSM * 64 / 256; ++u) {
+        const int e = tid + 256 * u, r = e / 64, j = e % 64;
+        const int64_t i = i0 + r;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 8
+        for (int k = 0; k < 64; ++k) {
+            const float2 a = A[r][k], d = D[j][k];  // a * conj(d)
+            acc.x = fmaf(a.x, d.x, fmaf(a.y, d.y, acc.x));
+            acc.y = fmaf(a.y, d.x, fmaf(-a.x, d.y, acc.y));
+        }
+        if (i < N && j < nbk) {
+            G[i * ldg + k0 + j] = make_double2((double)acc.x, (double)acc.y);
+            P[i * ldp + j] = acc;
+        }
+    }
+}
+
+// G[i][j] -= sum_k P[i][k] conj(P[j][k]) for t0 <= j < jmax, j <= i (K = nbk <= 64)
+__global__ void __launch_bounds__(256) k_herk_panel(const float2* __restrict__ P, int64_t ldp, double2* G,
+                                                  int64_t ldg, int nbk, int64_t t0, int64_t jmax, int64_t N) {
+    extern __shared__ float2 pnl_smem[];
+    float2(*Ai)[65] = reinterpret_cast<float2(*)[65]>(pnl_smem);
+    float2(*Bj)[65] = reinterpret_cast<float2(*)[65]>(pnl_smem + PNL_ROWS_HERK * 65);
+    const int tid = threadIdx.x;
+    const int W = (int)(jmax - t0);
+    const int64_t i0 = t0 + (int64_t)blockIdx.x * PNL_ROWS_HERK;
+    for (int e = tid; e < PNL_ROWS_HERK * 64; e += 256) {
+        const int r = e / 64, k = e % 64;
+        const int64_t i = i0 + r;
+        Ai[r][k] = (i < N && k < nbk) ? P[i * ldp + k] : make_float2(0.f, 0.f);
+    }
+    for (int e = tid; e < W * 64; e += 256) {
+        const int c = e / 64, k = e % 64;
+        const int64_t j = t0 + c;
+        Bj[c][k] = (j < N && k < nbk) ? P[j * ldp + k] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int e = tid; e < PNL_ROWS_HERK * W; e += 256) {
+        const int r = e / W, c = e % W;
+        const int64_t i = i0 + r, j = t0 + c;
+        if (i >= N || j > i) continue;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 8
+        for (int k = 0; k < 64; ++k) {
+            const float2 a = Ai[r][k], b = Bj[c][k];  // a * conj(b)
+            acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
+            acc.y = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc.y));
+        }
+        double2 g = G[i * ldg + j];
+        G[i * ldg + j] = make_double2(g.x - (double)acc.x, g.y - (double)acc.y);
+    }
+}
+
 // Panel table (B tiles of conj(L), rows from r0, kw panel columns from p0)
 size_t panel_table_bytes(int64_t N, int slices) {
     return (size_t)cdiv(N, tc::BM) * cdiv(256, tc::KC) * slices * tc::B_SL;
@@ -1013,14 +1093,25 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
             if (e != cudaSuccess) return e;
             const int64_t rest = N - k0 - nbk;
             if (rest <= 0) break;
-            tc::TrsmTC tp{L32 + k0, N, Dinv32 + kb * NBK * NBK, G, ld, N, k0, nbk};
-            if ((e = run(tp, dim3(1, cdiv(rest, tc::BM)), slices, st, 3, s)) != cudaSuccess) return e;
+            // panel solve of every row below the block
+            k_trsm_panel<<<cdiv(rest, PNL_ROWS_TRSM), 256, 0, s>>>(L32 + k0, N, Dinv32 + kb * NBK * NBK, G, ld, k0,
+                                                                   (int)nbk, k0 + nbk, N);
+            note_launch();
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
             const int64_t t0 = k0 + nbk;
             if (t0 < pend) {  // the panel's remaining columns, all rows below
-                tc::HerkTC hp{L32 + k0, N, G, ld, N, nbk, t0, pend};
-                if ((e = run(hp, dim3(cdiv(pend - t0, tc::BN), cdiv(N - t0, tc::BM)), slices, st, 4, s)) !=
-                    cudaSuccess)
-                    return e;
+                const size_t smem = sizeof(float2) * 65 * (PNL_ROWS_HERK + PNL_MAXW);
+                static bool attr = false;
+                if (!attr) {
+                    if ((e = cudaFuncSetAttribute(k_herk_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)smem)) != cudaSuccess)
+                        return e;
+                    attr = true;
+                }
+                k_herk_panel<<<cdiv(N - t0, PNL_ROWS_HERK), 256, smem, s>>>(L32 + k0, N, G, ld, (int)nbk, t0, pend,
+                                                                           N);
+                note_launch();
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
             }
         }
         if (ev_panel) {
