@@ -357,7 +357,8 @@ pinv_status pinv_plan_map(pinv_plan* plan, int what, const double* psi, double* 
  * a mixed plan's Gram carries its split-precision rounding).
  *   d_mu  [N] doubles, device: eigenvalues of E^H E (lambda removed), decreasing.
  *   d_P   [N][N] c128, device, row-major, column i the eigenvector of mu[i];
- *         may be NULL (eigenvalues only).
+ *         may be NULL: eigenvalues only, by Householder reduction to a real
+ *         symmetric tridiagonal and bisection instead (sweeps_out = 0).
  *   sweeps_out  Jacobi sweeps taken (may be NULL).
  * Synchronises with the device once per sweep. Sweeps stop at an off-diagonal
  * Frobenius norm of 4 N eps of the whole, or once a sweep no longer halves it

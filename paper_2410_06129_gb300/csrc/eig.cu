@@ -32,7 +32,7 @@ pinv_status eig_err(cudaError_t e, const char* where) {
                      std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-constexpr int EIG_MAX_N = 8192;   // the sort stages all eigenvalues in one CTA
+constexpr int EIG_MAX_N = 8192;   // Jacobi path: the sort stages all eigenvalues in one CTA
 constexpr int EIG_MAX_SWEEPS = 30;
 
 __device__ inline double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
@@ -274,6 +274,146 @@ __global__ void k_scale_rows(double2* C, int64_t F, int n, const double* __restr
     C[idx].y *= s;
 }
 
+// ------------------------------------------------------------------ eigenvalues only
+// Householder reduction of the Hermitian A to a real symmetric tridiagonal, one
+// column k at a time (the reflector's scalar tau is chosen so that the subdiagonal
+// entry beta is real), then bisection with Sturm counts, one eigenvalue per thread.
+// Column k below the diagonal is read as the conjugate of row k to the right of it.
+// With H = I - tau v v^H: p = tau A v, c = -Re(conj(tau) v^H p) / 2,
+// w = p + c v, A <- H^H A H = A - w v^H - v w^H on the trailing block.
+struct HhScalars {
+    double2 tau;
+    double beta;
+    double c;
+};
+
+// reflector of x = A[k + 1 ..][k]: v (v[0] = 1), tau, beta; d[k] and e[k] recorded
+__global__ void __launch_bounds__(256) k_hh_reflector(const double2* __restrict__ A, int n, int k, double2* v,
+                                                     HhScalars* hs, double* d, double* e) {
+    __shared__ double red[256];
+    const int m = n - k - 1;
+    const double2* row = A + (int64_t)k * n + k + 1;  // conj(x_j) = row[j]
+    double s = 0.0;
+    for (int j = 1 + threadIdx.x; j < m; j += blockDim.x) s += row[j].x * row[j].x + row[j].y * row[j].y;
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double xnorm2 = red[0];
+    const double2 alpha = cconj(row[0]);
+    double2 tau = make_double2(0.0, 0.0), scale = make_double2(0.0, 0.0);
+    double beta = alpha.x;
+    if (xnorm2 > 0.0 || alpha.y != 0.0) {
+        const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2);
+        beta = alpha.x >= 0.0 ? -nrm : nrm;
+        tau = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+        // scale = 1 / (alpha - beta)
+        const double2 den = make_double2(alpha.x - beta, alpha.y);
+        const double dd = den.x * den.x + den.y * den.y;
+        scale = make_double2(den.x / dd, -den.y / dd);
+    }
+    for (int j = threadIdx.x; j < m; j += blockDim.x)
+        v[j] = j == 0 ? make_double2(1.0, 0.0) : cmul(cconj(row[j]), scale);
+    if (threadIdx.x == 0) {
+        hs->tau = tau;
+        hs->beta = beta;
+        d[k] = A[(int64_t)k * n + k].x;
+        e[k] = beta;
+    }
+}
+
+// p = tau A22 v (A22 = A[k + 1 ..][k + 1 ..]), one warp per row
+__global__ void __launch_bounds__(256) k_hh_matvec(const double2* __restrict__ A, int n, int k,
+                                                  const double2* __restrict__ v, const HhScalars* hs, double2* p) {
+    const int m = n - k - 1;
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= m) return;
+    const double2* row = A + (int64_t)(k + 1 + i) * n + k + 1;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = lane; j < m; j += 32) acc = cadd(acc, cmul(row[j], v[j]));
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) p[i] = cmul(hs->tau, acc);
+}
+
+// c = -Re(conj(tau) v^H p) / 2
+__global__ void __launch_bounds__(256) k_hh_coef(int n, int k, const double2* __restrict__ v,
+                                                const double2* __restrict__ p, HhScalars* hs) {
+    __shared__ double red[256];
+    const int m = n - k - 1;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) acc = cadd(acc, cmul(cconj(v[j]), p[j]));
+    // real part of conj(tau) * acc
+    const double2 t = cconj(hs->tau);
+    red[threadIdx.x] = t.x * acc.x - t.y * acc.y;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) hs->c = -0.5 * red[0];
+}
+
+// A22 -= w v^H + v w^H with w = p + c v; row k's part beyond the diagonal becomes (beta, 0, ..)
+__global__ void __launch_bounds__(256) k_hh_update(double2* A, int n, int k, const double2* __restrict__ v,
+                                                  const double2* __restrict__ p, const HhScalars* hs) {
+    const int m = n - k - 1;
+    const int i = blockIdx.y;
+    const double c = hs->c;
+    const double2 vi = v[i], wi = cadd(p[i], make_double2(c * vi.x, c * vi.y));
+    double2* row = A + (int64_t)(k + 1 + i) * n + k + 1;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        const double2 vj = v[j], wj = cadd(p[j], make_double2(c * vj.x, c * vj.y));
+        const double2 t = cadd(cmul(wi, cconj(vj)), cmul(vi, cconj(wj)));
+        row[j] = make_double2(row[j].x - t.x, row[j].y - t.y);
+    }
+}
+
+// last 2 x 2 block: d[n-2], d[n-1], e[n-2] = |A[n-1][n-2]|
+__global__ void k_hh_tail(const double2* __restrict__ A, int n, double* d, double* e) {
+    if (n >= 2) {
+        d[n - 2] = A[(int64_t)(n - 2) * n + n - 2].x;
+        const double2 b = A[(int64_t)(n - 1) * n + n - 2];
+        e[n - 2] = hypot(b.x, b.y);
+    }
+    d[n - 1] = A[(int64_t)(n - 1) * n + n - 1].x;
+}
+
+// eigenvalue number i (ascending) of the symmetric tridiagonal (d, e) by bisection;
+// mu[n - 1 - i] = it minus lam (decreasing order)
+__global__ void k_tridiag_bisect(const double* __restrict__ d, const double* __restrict__ e, int n, double lam,
+                                 double* mu) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int k = 0; k < n; ++k) {
+        const double r = (k > 0 ? fabs(e[k - 1]) : 0.0) + (k < n - 1 ? fabs(e[k]) : 0.0);
+        lo = fmin(lo, d[k] - r);
+        hi = fmax(hi, d[k] + r);
+    }
+    const double span = fmax(fabs(lo), fabs(hi));
+    const double pivmin = 1e-300 + span * 1e-300;
+    for (int it = 0; it < 200 && hi - lo > 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)); ++it) {
+        const double x = 0.5 * (lo + hi);
+        int cnt = 0;
+        double q = d[0] - x;
+        if (fabs(q) < pivmin) q = -pivmin;
+        cnt += q < 0.0;
+        for (int k = 1; k < n; ++k) {
+            q = d[k] - x - e[k - 1] * e[k - 1] / q;
+            if (fabs(q) < pivmin) q = -pivmin;
+            cnt += q < 0.0;
+        }
+        if (cnt > i) hi = x;  // at least i + 1 eigenvalues below x
+        else lo = x;
+    }
+    mu[n - 1 - i] = 0.5 * (lo + hi) - lam;
+}
+
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -285,7 +425,9 @@ extern "C" pinv_status pinv_plan_eig(pinv_plan* p, double* d_mu, void* d_P, int*
     if (!p || !d_mu) return set_error(PINV_ERR_INVALID_ARG, "null plan or eigenvalue output");
     if (!p->built) return set_error(PINV_ERR_NOT_BUILT, "plan not built");
     if (!p->Gkeep) return set_error(PINV_ERR_UNSUPPORTED, "the eigendecomposition needs the kept Gram (keep_gram)");
-    if (p->N > EIG_MAX_N) return set_error(PINV_ERR_UNSUPPORTED, "eigendecomposition limited to N <= 8192");
+    if (d_P && p->N > EIG_MAX_N)
+        return set_error(PINV_ERR_UNSUPPORTED, "eigenvectors limited to N <= 8192 (eigenvalues alone are not)");
+    if (p->N > INT_MAX / 2) return set_error(PINV_ERR_UNSUPPORTED, "N too large");
     const int n = (int)p->N, np = n + (n & 1);
     cudaStream_t us = (cudaStream_t)stream;
     const size_t nn = (size_t)n * n;
@@ -329,8 +471,42 @@ extern "C" pinv_status pinv_plan_eig(pinv_plan* p, double* d_mu, void* d_P, int*
 
     CKE(cudaMemcpyAsync(A, p->Gkeep, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, s));
     k_hermitian_fill<<<blocks((int64_t)nn), 256, 0, s>>>(A, n);
+    note_launch();
+    CKE(cudaGetLastError());
+    if (!d_P) {
+        // eigenvalues only: Householder tridiagonalisation, then bisection; the
+        // 4 (n - 2) launches of the reduction run from one graph
+        double2 *v = V, *pv = V + n;  // V is not needed on this path: its first 2n entries hold v and p
+        double *dd = norms, *ee = norms + n;
+        HhScalars* hs = reinterpret_cast<HhScalars*>(ca);
+        cudaGraph_t g = nullptr;
+        CKE(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k + 2 < n; ++k) {
+            const int m = n - k - 1;
+            k_hh_reflector<<<1, 256, 0, s>>>(A, n, k, v, hs, dd, ee);
+            k_hh_matvec<<<blocks(m, 8), 256, 0, s>>>(A, n, k, v, hs, pv);
+            k_hh_coef<<<1, 256, 0, s>>>(n, k, v, pv, hs);
+            k_hh_update<<<dim3(blocks(m), m), 256, 0, s>>>(A, n, k, v, pv, hs);
+        }
+        k_hh_tail<<<1, 1, 0, s>>>(A, n, dd, ee);
+        k_tridiag_bisect<<<blocks(n, 128), 128, 0, s>>>(dd, ee, n, p->lambda_abs, d_mu);
+        const cudaError_t ec = cudaStreamEndCapture(s, &g);
+        if (ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return done(eig_err(ec, "cudaStreamEndCapture"));
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&sweep, g, 0);
+        cudaGraphDestroy(g);
+        CKE(ei);
+        CKE(cudaGraphLaunch(sweep, s));
+        note_launch((unsigned long long)4 * (n > 2 ? n - 2 : 0) + 2);
+        CKE(cudaEventRecord(ev, s));
+        CKE(cudaStreamWaitEvent(us, ev, 0));
+        if (sweeps_out) *sweeps_out = 0;
+        return done(PINV_OK);
+    }
     k_identity<<<blocks((int64_t)nn), 256, 0, s>>>(V, n);
-    note_launch(2);
+    note_launch();
     CKE(cudaGetLastError());
     const size_t row_smem = sizeof(double2) * n;
     CKE(cudaFuncSetAttribute(k_jac_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem));

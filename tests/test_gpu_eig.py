@@ -66,6 +66,21 @@ def test_eig_odd_size_radial():
     _check_eig(_plan(p, precision=L.FP64), O.plan_encode(p))
 
 
+@pytest.mark.parametrize("side,coils,b0", [(16, 3, True), (15, 2, False)])
+def test_eigenvalues_only_tridiagonal_path(side, coils, b0):
+    """Without eigenvectors the spectrum comes from Householder tridiagonalisation
+    and bisection: the same eigenvalues to 1e-12 of mu_1 (even and odd N)."""
+    p = synth.make_plan(side, coils, "spiral", 1, 2607 + side, 1e-3, samples=3 * side * side, interleaves=2, b0=b0)
+    E = O.plan_encode(p)
+    pl = _plan(p, precision=L.FP64)
+    mu, P, sweeps = pl.eig(vectors=False)
+    assert P is None and sweeps == 0
+    mu_ref, _ = O.gram_eig(E)
+    assert np.max(np.abs(mu.cpu().numpy() - mu_ref)) < 1e-12 * mu_ref[0]
+    mu_j, _, _ = pl.eig()
+    assert np.max(np.abs(mu.cpu().numpy() - mu_j.cpu().numpy())) < 1e-12 * mu_ref[0]
+
+
 @pytest.mark.parametrize("energy", [0.9, 0.99])
 def test_tsvd_matches_oracle(energy):
     p = synth.make_plan(14, 2, "spiral", 3, 2603, 1e-3, samples=400, interleaves=2)
