@@ -362,7 +362,7 @@ pinv_status pinv_plan_map(pinv_plan* plan, int what, const double* psi, double* 
  *   sweeps_out  Jacobi sweeps taken (may be NULL).
  * Synchronises with the device once per sweep. Sweeps stop at an off-diagonal
  * Frobenius norm of 4 N eps of the whole, or once a sweep no longer halves it
- * below 1e-10. UNSUPPORTED without a kept Gram or for N > 8192;
+ * below 1e-10. UNSUPPORTED without a kept Gram, or for eigenvectors with N > 8192;
  * PINV_ERR_INTERNAL if 30 sweeps do not converge (the outputs are still written). */
 pinv_status pinv_plan_eig(pinv_plan* plan, double* d_mu, void* d_P, int* sweeps_out, void* cuda_stream);
 
