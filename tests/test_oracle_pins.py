@@ -334,3 +334,17 @@ def test_planted_mistake_fails_tsvd_pin():
     bad = P[:, :6] @ ((P[:, :6].T @ b) / mu[:6, None])
     want = V[:, :6] @ ((U[:, :6].conj().T @ d) / s[:6, None])
     assert O.nrmse(bad, want) > 1e-3
+
+
+def test_underdetermined_right_form_equals_left_form():
+    """Fewer samples than voxels (Section 2.2, underdetermined case): with lambda > 0
+    the right pseudoinverse E^H (E E^H + lambda I)^-1 d equals the left form the
+    oracle computes (push-through identity), so one path serves both cases."""
+    rng = np.random.default_rng(31)
+    E = _rand_complex(rng, 30, 80)
+    d = _rand_complex(rng, 30, 2)
+    lam = 0.05
+    right = E.conj().T @ np.linalg.solve(E @ E.conj().T + lam * np.eye(30), d)
+    L = O.cholesky(O.gram(E, lam))
+    left = O.back_substitution_h(L, O.forward_substitution(L, E.conj().T @ d))
+    assert O.nrmse(left, right) < 1e-11
