@@ -104,6 +104,7 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
         CK(cudaFreeAsync(work, sx));
         CK(launch_gram_exact(p->enc, p->Ttab, p->lambda_abs, p->Gx, sx));
         if (p->Gd) CK(launch_gram_digits(p->Gx, N, p->eG, p->Gd, sx));
+        if (p->Ad) CK(launch_adj_digits(p->enc, p->Ad, sx));
     }
     return PINV_OK;
 }
@@ -457,6 +458,12 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
         AL(p->Ttab, sizeof(double2) * (2 * e.nx - 1) * (2 * e.ny - 1) * (2 * e.nz - 1), "Toeplitz table");
         if (!p->lean_gx()) AL(p->Gx, sizeof(float4) * p->N * p->N, "exact Gram");
         AL(p->Gd, gram_digit_bytes(p->N), "exact Gram digits");
+        {
+            // digits of conj(A) for the exact E^H d, formed once per build (PINV_ADJ_TABLE=0: in every CTA)
+            const char* env = std::getenv("PINV_ADJ_TABLE");
+            if (!p->lean && !e.b0df && !e.b0tab && e.extdf && !(env && std::strcmp(env, "0") == 0))
+                AL(p->Ad, adj_digit_bytes(e), "E^H digits");
+        }
         AL(p->eG, sizeof(int), "exact Gram exponent");
     }
     int rm = d->recon_mode;

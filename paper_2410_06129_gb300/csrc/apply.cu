@@ -135,7 +135,7 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
     };
 
     if (md.need_b) {  // b = E^H d, exactly on the tensor cores where possible
-        if (sc.xadj) CKA(launch_adjoint_exact(p->enc, D, F, sc.fexp, sc.b128, sc.dfw, p->st, s));
+        if (sc.xadj) CKA(launch_adjoint_exact(p->enc, D, F, sc.fexp, sc.b128, sc.dfw, p->st, s, p->Ad));
         else CKA(launch_adjoint_df(p->enc, D, F, 0.0, nullptr, sc.b128, s, sc.dfw));
     }
     if (!md.mixed) {

@@ -266,8 +266,12 @@ size_t df_work_elems(int64_t rows, int64_t F, int64_t K);
 // fexp: [F] per-frame exponents (written here); work: partials.
 bool exact_adjoint_ok(const EncodeDev& e, int64_t F);
 size_t exact_work_elems(const EncodeDev& e, int64_t F);
+// Ad (or nullptr): the digits of conj(A) in tile layout (adj_digit_bytes(), written
+// by launch_adj_digits), copied instead of formed in every CTA.
+size_t adj_digit_bytes(const EncodeDev& e);
+cudaError_t launch_adj_digits(const EncodeDev& e, uint8_t* Ad, cudaStream_t s);
 cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F, int* fexp, double2* B,
-                                 float4* work, DevStatus* st, cudaStream_t s);
+                                 float4* work, DevStatus* st, cudaStream_t s, const uint8_t* Ad = nullptr);
 cudaError_t launch_transpose_df(const float4* src, int64_t rows, int64_t cols, float4* dst, int64_t ldd,
                                 cudaStream_t s);
 

@@ -87,6 +87,7 @@ struct pinv_plan {
     double2* Ttab = nullptr;   // Toeplitz table of A^H A (TOEPLITZ residual)
     float4* Gx = nullptr;      // exact Gram, double-float [N][N] (TOEPLITZ residual)
     uint8_t* Gd = nullptr;     // its fixed-point digit tiles for the tensor-core residual
+    uint8_t* Ad = nullptr;     // digit tiles of conj(A) for the exact E^H d (mixed, B0-free, not lean)
     int* eG = nullptr;         // |G| <= 2^eG (device)
     pinv::DevStatus* st = nullptr;        // device status word
     pinv::DevStatus* st_host = nullptr;   // pinned copy, written at the end of each build

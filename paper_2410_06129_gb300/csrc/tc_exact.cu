@@ -27,6 +27,12 @@
 // output columns side by side, as in the split-BF16 engine); the sample range
 // is split over CTAs and the double-float partials reduced in a fixed order.
 // Plans without B0 only (E from the separable phase tables and coil maps).
+//
+// The digits of the A operand either come from the producer warps (XGEN) or
+// are copied with one bulk copy per stage from a table in the stage layout:
+// the exact Gram's digit tiles for the refinement residual (XGRAM), or the
+// digits of conj(A) written once per build (XADJT; the same digits XGEN
+// forms, which it would otherwise form again for every coil and frame tile).
 #include <algorithm>
 
 #include "df.cuh"
@@ -134,12 +140,38 @@ __device__ inline void gen_ah8(const EncodeDev& e, int64_t n, int64_t m, int64_t
     }
 }
 
-// GRAM = false: b = E^H d (A generated). GRAM = true: G x with the digits of G
-// precomputed in tile layout (A copied) and x as the B operand.
-template <bool GRAM>
+// A operand of the exact kernel
+enum XMode { XGEN = 0, XGRAM = 1, XADJT = 2 };
+
+// Digits of conj(A) for one (voxel tile, 16-sample chunk): NDIG slices of 8 KiB in
+// the stage layout, exactly as the XGEN producers write them to shared memory.
+__global__ void __launch_bounds__(256) k_adj_digits(EncodeDev e, int64_t KB, uint8_t* Ad) {
+    const int64_t kb = blockIdx.x, rb = blockIdx.y;
+    const int ra = threadIdx.x & (XM - 1), ga = threadIdx.x >> 7;
+    float reh[8], rel[8], imh[8], iml[8];
+    gen_ah8(e, rb * XM + ra, kb * XKC + 8 * ga, e.Mk, reh, rel, imh, iml);
+    Digits8 dr, di;
+    dr.init(reh, rel, 1.f);
+    di.init(imh, iml, 1.f);
+    uint8_t* blk = Ad + (rb * KB + kb) * (int64_t)(NDIG * XA_SL);
+#pragma unroll
+    for (int dg = 0; dg < NDIG; ++dg) {
+        uint32_t w[4];
+        dr.next(w, 0u);
+        *reinterpret_cast<uint4*>(blk + dg * XA_SL + koff(ra, ga)) = make_uint4(w[0], w[1], w[2], w[3]);
+        di.next(w, 0u);
+        *reinterpret_cast<uint4*>(blk + dg * XA_SL + koff(ra, ga + 2)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// XGEN / XADJT: b = E^H d; XGRAM: G x with the digits of G in tile layout and x as
+// the B operand.
+template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
+    constexpr bool GRAM = MODE == XGRAM;
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[XSTAGES], empty_bar[XSTAGES];
+    __shared__ uint64_t abar[XSTAGES];  // XGRAM / XADJT: the A tile's bulk copy (its bytes)
     __shared__ uint64_t tfull, tempty, done_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_flag;
@@ -159,6 +191,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
         for (int s = 0; s < XSTAGES; ++s) {
             mbar_init(&full_bar[s], NPW * 32);
             mbar_init(&empty_bar[s], 1);
+            mbar_init(&abar[s], 1);
         }
         mbar_init(&tfull, 1);
         mbar_init(&tempty, NPW * 32);
@@ -213,6 +246,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
         const int ub = threadIdx.x, cb = ub & (XN - 1), gb = ub >> 5;
         const int64_t fcol = f0 + cb;
         const bool bunit = ub < 2 * XN;
+        int a_issued = 0;  // stages whose A tile this thread (thread 0) has started copying
         const float dscale = (bunit && fcol < a.F) ? __int_as_float((127 - a.fexp[fcol]) << 23) : 1.f;
         for (int kt = 0; kt < nk && ok; ++kt) {
             while (drained < ngroups && (drained + 1) * XDRAIN + XSTAGES - 1 <= kt) {
@@ -225,17 +259,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
             if (kt >= XSTAGES && !(ok = mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag))) break;
             uint8_t* base = smem + s * XSTAGE;
             const int64_t m0 = mb + (int64_t)kt * XKC;  // k index (sample inside the coil, or Gram column)
-            if (GRAM) {
-                // digit tile of rows n0.., columns m0..m0+15: NDIG x 8 KiB, copied as is
-                const uint4* src = reinterpret_cast<const uint4*>(
-                    a.Gd + ((int64_t)blockIdx.y * a.KB + m0 / XKC) * (int64_t)(NDIG * XA_SL));
-                uint4* dst = reinterpret_cast<uint4*>(base);
-                constexpr int NV = NDIG * XA_SL / 16 / (NPW * 32);  // 12 vectors per thread
-                uint4 v[NV];
-#pragma unroll
-                for (int u = 0; u < NV; ++u) v[u] = src[u * NPW * 32 + threadIdx.x];
-#pragma unroll
-                for (int u = 0; u < NV; ++u) dst[u * NPW * 32 + threadIdx.x] = v[u];
+            if (MODE != XGEN) {
+                // digit tile of rows n0.., k m0..m0+15: NDIG x 8 KiB in one bulk copy,
+                // counted in bytes on the stage's full barrier
+                if (threadIdx.x == 0) {
+                    const uint8_t* src = a.Gd + ((int64_t)blockIdx.y * a.KB + m0 / XKC) * (int64_t)(NDIG * XA_SL);
+                    mbar_arrive_expect_tx(&abar[s], (uint32_t)(NDIG * XA_SL));
+                    bulk_g2s(base, src, (uint32_t)(NDIG * XA_SL), &abar[s]);
+                    a_issued = kt + 1;
+                }
             } else {
                 float reh[8], rel[8], imh[8], iml[8];
                 gen_ah8(a.e, nrow, m0 + 8 * ga, me, reh, rel, imh, iml);
@@ -309,6 +341,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
                 }
             }
         }
+        if (MODE != XGEN && threadIdx.x == 0) {
+            // copies still in flight (only after an abort): wait, bounded, for their bytes
+            for (int kg = a_issued > XSTAGES ? a_issued - XSTAGES : 0; kg < a_issued; ++kg)
+                mbar_wait(&abar[kg % XSTAGES], (uint32_t)(kg / XSTAGES) & 1u, nullptr);
+        }
     } else if (lane == 0) {
         // ---------------- MMA issuer: 21 digit pairs per stage, class w = i + j into region w
         for (int kt = 0; kt < nk; ++kt) {
@@ -318,6 +355,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
             const int s = kt % XSTAGES;
             const uint32_t ph = (uint32_t)(kt / XSTAGES) & 1u;
             if (!mbar_wait(&full_bar[s], ph, &abort_flag)) break;
+            if (MODE != XGEN && !mbar_wait(&abar[s], ph, &abort_flag)) break;
             tc_fence_after();
             const uint32_t abase = smem_u32(smem + s * XSTAGE);
             const uint32_t bbase = abase + NDIG * XA_SL;
@@ -489,20 +527,32 @@ bool exact_adjoint_ok(const EncodeDev& e, int64_t F) {
     return e.extdf && !e.b0df && !e.b0tab && F >= 16 && tc_available();
 }
 
-template <bool GRAM>
+template <int MODE>
 static cudaError_t exact_attr() {
     static bool attr = false;
     if (attr) return cudaSuccess;
     cudaError_t err =
-        cudaFuncSetAttribute(tcx::k_exact<GRAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcx::XSMEM);
+        cudaFuncSetAttribute(tcx::k_exact<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcx::XSMEM);
     if (err == cudaSuccess) attr = true;
     return err;
 }
 
+size_t adj_digit_bytes(const EncodeDev& e) {
+    const int64_t RB = (e.N + tcx::XM - 1) / tcx::XM, KB = (e.Mk + tcx::XKC - 1) / tcx::XKC;
+    return (size_t)RB * (size_t)KB * (size_t)(tcx::NDIG * tcx::XA_SL);
+}
+
+cudaError_t launch_adj_digits(const EncodeDev& e, uint8_t* Ad, cudaStream_t s) {
+    const int64_t RB = (e.N + tcx::XM - 1) / tcx::XM, KB = (e.Mk + tcx::XKC - 1) / tcx::XKC;
+    tcx::k_adj_digits<<<dim3((unsigned)KB, (unsigned)RB), 256, 0, s>>>(e, KB, Ad);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F, int* fexp, double2* B,
-                                 float4* work, DevStatus* st, cudaStream_t s) {
+                                 float4* work, DevStatus* st, cudaStream_t s, const uint8_t* Ad) {
     if (F == 0) return cudaSuccess;
-    cudaError_t aerr = exact_attr<false>();
+    cudaError_t aerr = Ad ? exact_attr<tcx::XADJT>() : exact_attr<tcx::XGEN>();
     if (aerr != cudaSuccess) return aerr;
     const int64_t M = e.Mk * e.C;
     tcx::k_frame_exp<<<(unsigned)F, 256, 0, s>>>(D, M, fexp);
@@ -512,9 +562,13 @@ cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F
     const bool partials = splits > 1 || e.coilsdf;
     if (partials && !work) return cudaErrorInvalidValue;
     const int64_t chunk = ((e.Mk + sub - 1) / sub + tcx::XKC - 1) / tcx::XKC * tcx::XKC;
-    tcx::XArgs a{e, D, fexp, F, M, chunk, sub, partials ? work : nullptr, B, nullptr, nullptr, 0};
+    const int64_t KB = (e.Mk + tcx::XKC - 1) / tcx::XKC;
+    tcx::XArgs a{e, D, fexp, F, M, chunk, sub, partials ? work : nullptr, B, Ad, nullptr, KB};
     dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN), (unsigned)((e.N + tcx::XM - 1) / tcx::XM), (unsigned)splits);
-    tcx::k_exact<false><<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
+    if (Ad)
+        tcx::k_exact<tcx::XADJT><<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
+    else
+        tcx::k_exact<tcx::XGEN><<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
     note_launch();
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess || !partials) return err;
@@ -553,7 +607,7 @@ cudaError_t launch_gram_resid_exact(const uint8_t* Gd, const int* eG, int64_t N,
                                     const double2* X, int64_t F, int* fexp, double2* R, float4* work,
                                     DevStatus* st, cudaStream_t s) {
     if (F == 0) return cudaSuccess;
-    cudaError_t err = exact_attr<true>();
+    cudaError_t err = exact_attr<tcx::XGRAM>();
     if (err != cudaSuccess) return err;
     tcx::k_frame_exp<<<(unsigned)F, 256, 0, s>>>(X, N, fexp);
     note_launch();
@@ -564,7 +618,7 @@ cudaError_t launch_gram_resid_exact(const uint8_t* Gd, const int* eG, int64_t N,
     const int64_t KB = (N + tcx::XKC - 1) / tcx::XKC;
     tcx::XArgs a{e, X, fexp, F, N, chunk, 1, work, nullptr, Gd, eG, KB};
     dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN), (unsigned)((N + tcx::XM - 1) / tcx::XM), (unsigned)sp);
-    tcx::k_exact<true><<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
+    tcx::k_exact<tcx::XGRAM><<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
     note_launch();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int64_t n = N * F;

@@ -120,15 +120,18 @@ def test_toeplitz_needs_b0_free_plan():
 
 def test_lean_plan_same_images_less_memory():
     """A lean plan drops G / L, the FP64 W and the double-float exact Gram after
-    its build: same images bit for bit, N^2 x 48 bytes less device memory, no
-    L / W / exact-Gram exports."""
+    its build, and keeps no digit table of conj(A) (its E^H d forms the digits in
+    every CTA): same images bit for bit, N^2 x 48 bytes plus the table's
+    ceil(N / 128) x ceil(M_k / 16) x 48 KiB less device memory, no L / W /
+    exact-Gram exports."""
     p = synth.config(2, reduced=True)
     d = torch.from_numpy(p.data).cuda()
     full = _plan(p.dims, p.traj, p.coil_maps, lam=p.lambda_rel, refine_max_iters=3).build()
     lean = _plan(p.dims, p.traj, p.coil_maps, lam=p.lambda_rel, refine_max_iters=3, lean=True).build()
     assert torch.equal(full.apply(d), lean.apply(d))
     N = p.n_vox
-    assert full.info()["bytes_device"] - lean.info()["bytes_device"] == 48 * N * N
+    table = -(-N // 128) * -(-p.n_samples // 16) * 6 * 8192
+    assert full.info()["bytes_device"] - lean.info()["bytes_device"] == 48 * N * N + table
     for what in (L.EXPORT_CHOL, L.EXPORT_LINV, L.EXPORT_GINV, L.EXPORT_GRAM_EXACT):
         with pytest.raises(L.PinvError, match="UNSUPPORTED"):
             lean.export(what)
@@ -150,6 +153,22 @@ def test_exact_tensor_core_adjoint_many_frames(side, frames, samples):
     assert rel(x, ref.images) <= 1e-5
     x_small = np.concatenate([pl.apply(d[i:i + 8]).cpu().numpy() for i in range(0, frames, 8)])
     assert rel(x, x_small) <= 1e-5
+
+
+def test_exact_adjoint_digit_table_bit_identical(monkeypatch):
+    """The digits of conj(A) written once per build and bulk-copied per stage are the
+    digits the generating kernel forms in every CTA, summed in the same order: the
+    images are the same bit for bit. 36 frames, ragged N = 400, 4 coils."""
+    p = synth.make_plan(20, 4, "spiral", 36, 2609, 1e-4, samples=1000, interleaves=2)
+    d = torch.from_numpy(p.data).cuda()
+
+    def images():
+        pl = _plan(p.dims, p.traj, p.coil_maps, lam=p.lambda_rel, refine_max_iters=3).build()
+        return pl.apply(d).cpu().numpy()
+
+    x_table = images()
+    monkeypatch.setenv("PINV_ADJ_TABLE", "0")
+    assert np.array_equal(images(), x_table)
 
 
 @pytest.mark.parametrize("frames", [24, 150])
