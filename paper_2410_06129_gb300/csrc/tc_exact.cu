@@ -247,6 +247,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
         const int64_t fcol = f0 + cb;
         const bool bunit = ub < 2 * XN;
         int a_issued = 0;  // stages whose A tile this thread (thread 0) has started copying
+        // B unit: 8 consecutive samples (k) of frame fcol for stage kt (zero outside the range)
+        auto load_b_into = [&](int kt, double2 (&dst)[8]) {
+            const int64_t mk0 = mb + (int64_t)kt * XKC + 8 * gb;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int64_t m = mk0 + t;
+                dst[t] = (fcol < a.F && m < me) ? a.D[fcol * a.M + (int64_t)coil * Mk + m]  // Gram: M = N
+                                                : make_double2(0.0, 0.0);
+            }
+        };
+        double2 dnext[8];
+        auto load_b = [&](int kt) { load_b_into(kt, dnext); };
+        if (MODE != XGEN && bunit && nk > 0) load_b(0);
         const float dscale = (bunit && fcol < a.F) ? __int_as_float((127 - a.fexp[fcol]) << 23) : 1.f;
         for (int kt = 0; kt < nk && ok; ++kt) {
             while (drained < ngroups && (drained + 1) * XDRAIN + XSTAGES - 1 <= kt) {
@@ -286,11 +299,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
             }
             if (bunit) {
                 float reh[8], rel[8], imh[8], iml[8];
+                double2 dcur[8];
+                if constexpr (MODE != XGEN) {
+                    // this stage's data were loaded during the previous stage; start the next one's
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) dcur[t] = dnext[t];
+                    if (kt + 1 < nk) load_b(kt + 1);
+                } else {
+                    load_b_into(kt, dcur);
+                }
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
-                    const int64_t m = m0 + 8 * gb + t;
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (fcol < a.F && m < me) v = to_df(a.D[fcol * a.M + (int64_t)coil * Mk + m]);  // Gram: M = N
+                    const float4 v = to_df(dcur[t]);
                     reh[t] = v.x;
                     rel[t] = v.y;
                     imh[t] = v.z;
