@@ -93,7 +93,11 @@ size_t apply_scratch_layout(const pinv_plan* p, int64_t F, int dtype, void* base
         const bool xres = md.toep && md.refine && p->Gd;
         if (xadj) w = std::max(w, exact_work_elems(p->enc, F));
         if (xres) w = std::max(w, resid_exact_work_elems(N, F));
-        if (xadj || xres) s.fexp = cv.take<int>((size_t)F);
+        if (xadj || xres) {
+            s.fexp = cv.take<int>((size_t)F);
+            s.xbd = cv.take<uint8_t>(std::max(xadj ? exact_bdigit_bytes(p->enc, F) : 0,
+                                              xres ? resid_bdigit_bytes(N, F) : 0));
+        }
         s.xadj = xadj;
         s.dfw = w ? cv.take<float4>(w) : nullptr;
     }
@@ -135,7 +139,7 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
     };
 
     if (md.need_b) {  // b = E^H d, exactly on the tensor cores where possible
-        if (sc.xadj) CKA(launch_adjoint_exact(p->enc, D, F, sc.fexp, sc.b128, sc.dfw, p->st, s, p->Ad));
+        if (sc.xadj) CKA(launch_adjoint_exact(p->enc, D, F, sc.fexp, sc.xbd, sc.b128, sc.dfw, p->st, s, p->Ad));
         else CKA(launch_adjoint_df(p->enc, D, F, 0.0, nullptr, sc.b128, s, sc.dfw));
     }
     if (!md.mixed) {
@@ -184,7 +188,7 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
         }
         for (int it = 0; it < p->refine_iters; ++it) {
             if (md.toep && p->Gd) {  // r = b - G x, exactly on the tensor cores
-                CKA(launch_gram_resid_exact(p->Gd, p->eG, N, sc.b128, X, F, sc.fexp, sc.r128, sc.dfw, p->st, s));
+                CKA(launch_gram_resid_exact(p->Gd, p->eG, N, sc.b128, X, F, sc.fexp, sc.xbd, sc.r128, sc.dfw, p->st, s));
             } else if (md.toep) {
                 CKA(launch_gram_resid_df(p->Gx, N, sc.b128, X, F, sc.r128, s, sc.dfw));  // r = b - G x
             } else if (md.dfres) {

@@ -263,15 +263,18 @@ void tc_multi_free(TcMulti* m);
 size_t df_work_elems(int64_t rows, int64_t F, int64_t K);
 
 // E^H d exactly on the tensor cores (fixed-point digits; B0-free plans, F >= 16).
-// fexp: [F] per-frame exponents (written here); work: partials.
+// fexp: [F] per-frame exponents (written here); Bd: exact_bdigit_bytes() for the
+// data's digit tiles (written here); work: partials.
 bool exact_adjoint_ok(const EncodeDev& e, int64_t F);
 size_t exact_work_elems(const EncodeDev& e, int64_t F);
+size_t exact_bdigit_bytes(const EncodeDev& e, int64_t F);
 // Ad (or nullptr): the digits of conj(A) in tile layout (adj_digit_bytes(), written
 // by launch_adj_digits), copied instead of formed in every CTA.
 size_t adj_digit_bytes(const EncodeDev& e);
 cudaError_t launch_adj_digits(const EncodeDev& e, uint8_t* Ad, cudaStream_t s);
-cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F, int* fexp, double2* B,
-                                 float4* work, DevStatus* st, cudaStream_t s, const uint8_t* Ad = nullptr);
+cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F, int* fexp, uint8_t* Bd,
+                                 double2* B, float4* work, DevStatus* st, cudaStream_t s,
+                                 const uint8_t* Ad = nullptr);
 cudaError_t launch_transpose_df(const float4* src, int64_t rows, int64_t cols, float4* dst, int64_t ldd,
                                 cudaStream_t s);
 
@@ -287,9 +290,10 @@ cudaError_t launch_apply_tc(const float2* R, int64_t N, int64_t M, const float2*
 size_t gram_digit_bytes(int64_t N);
 cudaError_t launch_gram_digits(const float4* G, int64_t N, int* eG, uint8_t* Gd, cudaStream_t s);
 size_t resid_exact_work_elems(int64_t N, int64_t F);
+size_t resid_bdigit_bytes(int64_t N, int64_t F);  // Bd of launch_gram_resid_exact
 cudaError_t launch_gram_resid_exact(const uint8_t* Gd, const int* eG, int64_t N, const double2* Bv,
-                                    const double2* X, int64_t F, int* fexp, double2* R, float4* work,
-                                    DevStatus* st, cudaStream_t s);
+                                    const double2* X, int64_t F, int* fexp, uint8_t* Bd, double2* R,
+                                    float4* work, DevStatus* st, cudaStream_t s);
 
 // exact Gram of B0-free grid plans (Toeplitz table, FP64; stored double-float)
 size_t toeplitz_work_bytes(const EncodeDev& e);

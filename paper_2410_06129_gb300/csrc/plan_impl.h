@@ -25,6 +25,7 @@ struct ApplyScratch {
     double* norms;  // per-frame squared norms [2F]
     float4* dfw;    // partial sums of the split double-float products
     int* fexp;      // per-frame exponents of the data / image [F] (exact tensor-core products)
+    uint8_t* xbd;   // digit tiles of their B operand
     bool xadj;      // E^H d by the exact tensor-core kernel
     float2* apw;    // partials of the tensor-core Recon x data
     float2* cw;     // partials of the tensor-core correction x += W^H (W r)

@@ -99,12 +99,14 @@ struct XArgs {
     const int* fexp;    // per-frame exponent: |D_f| <= 2^fexp
     int64_t F, M;
     int64_t chunk;      // k per split (multiple of XKC); adjoint splits never cross a coil
-    int sub;            // adjoint: splits per coil
+    int sub;            // splits per coil (Gram residual: splits)
     float4* part;       // [splits][F][N] double-float partials, or null (one split, no coil maps)
     double2* B;         // output [F][N] when part is null
     const uint8_t* Gd;  // Gram residual: digit tiles of G ([row block][k block][digit] x 8 KiB)
     const int* eG;      // Gram residual: |G| <= 2^eG
-    int64_t KB;         // Gram residual: k blocks of 16 per row block
+    int64_t KB;         // k blocks of 16 per row block (per coil for the adjoint)
+    const uint8_t* Bd;  // digit tiles of the B operand (k_b_digits)
+    int C;              // coils (Gram residual: 1)
 };
 
 // conj(A[m][n]) for 8 consecutive samples m (< mend) of voxel n, double-float,
@@ -164,25 +166,82 @@ __global__ void __launch_bounds__(256) k_adj_digits(EncodeDev e, int64_t KB, uin
     }
 }
 
+// Digits of the B operand (data d, or x for the Gram residual) for one (32-frame
+// tile, coil, 16-sample chunk): NDIG slices of 4 KiB in the stage layout. Frame f
+// of the tile owns row f, [Br | -Bi], and row 32 + f, [Bi | Br], each value scaled
+// by 2^-fexp[f]; samples at or past Kc (the coil's end) and frames at or past F are
+// zero. Value (f, c, m) is D[f * ld + c * Kc + m]. Four chunks per 256-thread block,
+// one (frame, 8 samples) unit per thread.
+__global__ void __launch_bounds__(256) k_b_digits(const double2* D, int64_t ld, int64_t F, int C, int64_t Kc,
+                                                  int64_t KB, const int* fexp, uint8_t* Bd) {
+    const int64_t FT = (F + XN - 1) / XN;
+    const int64_t tile = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 6);
+    if (tile >= FT * C * KB) return;
+    const int64_t kb = tile % KB, fc = tile / KB;
+    const int c = (int)(fc % C);
+    const int64_t f = (fc / C) * XN + (threadIdx.x & (XN - 1));
+    const int cb = threadIdx.x & (XN - 1), gb = (threadIdx.x >> 5) & 1;
+    const int64_t mk0 = kb * XKC + 8 * gb;
+    float reh[8], rel[8], imh[8], iml[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int64_t m = mk0 + t;
+        const float4 v = to_df((f < F && m < Kc) ? D[f * ld + (int64_t)c * Kc + m] : make_double2(0.0, 0.0));
+        reh[t] = v.x;
+        rel[t] = v.y;
+        imh[t] = v.z;
+        iml[t] = v.w;
+    }
+    const float scale = f < F ? __int_as_float((127 - fexp[f]) << 23) : 1.f;
+    Digits8 dr, di;
+    dr.init(reh, rel, scale);
+    di.init(imh, iml, scale);
+    uint8_t* bb = Bd + tile * (int64_t)(NDIG * XB_SL);
+#pragma unroll
+    for (int dg = 0; dg < NDIG; ++dg) {
+        uint32_t wr[4], wi[4];
+        dr.next(wr, 0u);
+        di.next(wi, 0u);
+        uint8_t* sl = bb + dg * XB_SL;
+        *reinterpret_cast<uint4*>(sl + koff(cb, gb)) = make_uint4(wr[0], wr[1], wr[2], wr[3]);  // [Br|-Bi]
+        *reinterpret_cast<uint4*>(sl + koff(cb, gb + 2)) =
+            make_uint4(wi[0] ^ 0x80008000u, wi[1] ^ 0x80008000u, wi[2] ^ 0x80008000u, wi[3] ^ 0x80008000u);
+        *reinterpret_cast<uint4*>(sl + koff(XN + cb, gb)) = make_uint4(wi[0], wi[1], wi[2], wi[3]);  // [Bi|Br]
+        *reinterpret_cast<uint4*>(sl + koff(XN + cb, gb + 2)) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+    }
+}
+
 // XGEN / XADJT: b = E^H d; XGRAM: G x with the digits of G in tile layout and x as
-// the B operand.
+// the B operand. The B operand's digit tiles (k_b_digits) are copied per stage.
+//
+// One-dimensional grid, frame tile fastest, then coil, row block and split: the
+// CTAs that read one A tile (all frame tiles and coils of a row block and split)
+// run side by side and share it in L2.
 template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
     constexpr bool GRAM = MODE == XGRAM;
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[XSTAGES], empty_bar[XSTAGES];
-    __shared__ uint64_t abar[XSTAGES];  // XGRAM / XADJT: the A tile's bulk copy (its bytes)
+    __shared__ uint64_t abar[XSTAGES];  // the stage's bulk copies (their bytes)
     __shared__ uint64_t tfull, tempty, done_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_flag;
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t N = a.e.N;
-    const int64_t n0 = (int64_t)blockIdx.y * XM, f0 = (int64_t)blockIdx.x * XN;
+    const int64_t FT = (a.F + XN - 1) / XN, RB = (N + XM - 1) / XM;
+    int64_t lin = blockIdx.x;
+    const int64_t ft = lin % FT;
+    lin /= FT;
+    const int coil = (int)(lin % a.C);
+    lin /= a.C;
+    const int64_t rb = lin % RB;
+    const int split = (int)(lin / RB);
+    const int64_t zpart = (int64_t)coil * a.sub + split;  // partial slot
+    const int64_t n0 = rb * XM, f0 = ft * XN;
     // k range [mb, me): adjoint samples inside coil `coil`, or Gram columns
-    const int coil = GRAM ? 0 : (int)blockIdx.z / a.sub;
     const int64_t Mk = GRAM ? N : a.e.Mk;
-    const int64_t mb = GRAM ? (int64_t)blockIdx.z * a.chunk : (int64_t)((int)blockIdx.z % a.sub) * a.chunk;
+    const int64_t mb = (int64_t)split * a.chunk;
     const int64_t me = mb + a.chunk < Mk ? mb + a.chunk : Mk;
     const int nk = me > mb ? (int)((me - mb + XKC - 1) / XKC) : 0;
     const int ngroups = (nk + XDRAIN - 1) / XDRAIN;
@@ -239,49 +298,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
             mbar_arrive(&tempty);
             return true;
         };
-        // A unit: voxel row ua & 127, 8 samples of k-group ua >> 7
+        // A unit (XGEN): voxel row ua & 127, 8 samples of k-group ua >> 7
         const int ua = threadIdx.x, ra = ua & (XM - 1), ga = ua >> 7;
         const int64_t nrow = n0 + ra;
-        // B unit (threads 0..63): frame column ub & 31, k-group ub >> 5
-        const int ub = threadIdx.x, cb = ub & (XN - 1), gb = ub >> 5;
-        const int64_t fcol = f0 + cb;
-        const bool bunit = ub < 2 * XN;
-        int a_issued = 0;  // stages whose A tile this thread (thread 0) has started copying
-        // B unit: 8 consecutive samples (k) of frame fcol for stage kt (zero outside the range)
-        auto load_b_into = [&](int kt, double2 (&dst)[8]) {
-            const int64_t mk0 = mb + (int64_t)kt * XKC + 8 * gb;
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int64_t m = mk0 + t;
-                dst[t] = (fcol < a.F && m < me) ? a.D[fcol * a.M + (int64_t)coil * Mk + m]  // Gram: M = N
-                                                : make_double2(0.0, 0.0);
-            }
-        };
-        double2 dnext[8];
-        auto load_b = [&](int kt) { load_b_into(kt, dnext); };
-        if (MODE != XGEN && bunit && nk > 0) load_b(0);
-        const float dscale = (bunit && fcol < a.F) ? __int_as_float((127 - a.fexp[fcol]) << 23) : 1.f;
+        int a_issued = 0;  // stages whose tiles this thread (thread 0) has started copying
+        constexpr uint32_t kTx = (MODE != XGEN ? NDIG * XA_SL : 0) + NDIG * XB_SL;
+        const uint8_t* bsrc = a.Bd + ((ft * a.C + coil) * a.KB) * (int64_t)(NDIG * XB_SL);
         for (int kt = 0; kt < nk && ok; ++kt) {
-            while (drained < ngroups && (drained + 1) * XDRAIN + XSTAGES - 1 <= kt) {
-                if (!(ok = drain(drained))) break;
-                ++drained;
-            }
-            if (!ok) break;
             const int s = kt % XSTAGES;
             const uint32_t ph = (uint32_t)(kt / XSTAGES) & 1u;
             if (kt >= XSTAGES && !(ok = mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag))) break;
             uint8_t* base = smem + s * XSTAGE;
             const int64_t m0 = mb + (int64_t)kt * XKC;  // k index (sample inside the coil, or Gram column)
-            if (MODE != XGEN) {
-                // digit tile of rows n0.., k m0..m0+15: NDIG x 8 KiB in one bulk copy,
-                // counted in bytes on the stage's full barrier
-                if (threadIdx.x == 0) {
-                    const uint8_t* src = a.Gd + ((int64_t)blockIdx.y * a.KB + m0 / XKC) * (int64_t)(NDIG * XA_SL);
-                    mbar_arrive_expect_tx(&abar[s], (uint32_t)(NDIG * XA_SL));
-                    bulk_g2s(base, src, (uint32_t)(NDIG * XA_SL), &abar[s]);
-                    a_issued = kt + 1;
-                }
-            } else {
+            const int64_t kb = m0 / XKC;
+            if (threadIdx.x == 0) {
+                // the stage's digit tiles: A (NDIG x 8 KiB, unless formed below) and
+                // B (NDIG x 4 KiB), counted in bytes on abar
+                mbar_arrive_expect_tx(&abar[s], kTx);
+                if (MODE != XGEN)
+                    bulk_g2s(base, a.Gd + (rb * a.KB + kb) * (int64_t)(NDIG * XA_SL), (uint32_t)(NDIG * XA_SL),
+                             &abar[s]);
+                bulk_g2s(base + NDIG * XA_SL, bsrc + kb * (int64_t)(NDIG * XB_SL), (uint32_t)(NDIG * XB_SL),
+                         &abar[s]);
+                a_issued = kt + 1;
+            }
+            if constexpr (MODE == XGEN) {
                 float reh[8], rel[8], imh[8], iml[8];
                 gen_ah8(a.e, nrow, m0 + 8 * ga, me, reh, rel, imh, iml);
                 Digits8 dr, di;
@@ -296,45 +337,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
                     *reinterpret_cast<uint4*>(base + dg * XA_SL + koff(ra, ga + 2)) =
                         make_uint4(w[0], w[1], w[2], w[3]);
                 }
+                fence_proxy_async();
+                mbar_arrive(&full_bar[s]);
             }
-            if (bunit) {
-                float reh[8], rel[8], imh[8], iml[8];
-                double2 dcur[8];
-                if constexpr (MODE != XGEN) {
-                    // this stage's data were loaded during the previous stage; start the next one's
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) dcur[t] = dnext[t];
-                    if (kt + 1 < nk) load_b(kt + 1);
-                } else {
-                    load_b_into(kt, dcur);
-                }
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const float4 v = to_df(dcur[t]);
-                    reh[t] = v.x;
-                    rel[t] = v.y;
-                    imh[t] = v.z;
-                    iml[t] = v.w;
-                }
-                Digits8 dr, di;
-                dr.init(reh, rel, dscale);
-                di.init(imh, iml, dscale);
-                uint8_t* bb = base + NDIG * XA_SL;
-#pragma unroll
-                for (int dg = 0; dg < NDIG; ++dg) {
-                    uint32_t wr[4], wi[4];
-                    dr.next(wr, 0u);
-                    di.next(wi, 0u);
-                    uint8_t* sl = bb + dg * XB_SL;
-                    *reinterpret_cast<uint4*>(sl + koff(cb, gb)) = make_uint4(wr[0], wr[1], wr[2], wr[3]);  // [Br|-Bi]
-                    *reinterpret_cast<uint4*>(sl + koff(cb, gb + 2)) =
-                        make_uint4(wi[0] ^ 0x80008000u, wi[1] ^ 0x80008000u, wi[2] ^ 0x80008000u, wi[3] ^ 0x80008000u);
-                    *reinterpret_cast<uint4*>(sl + koff(XN + cb, gb)) = make_uint4(wi[0], wi[1], wi[2], wi[3]);  // [Bi|Br]
-                    *reinterpret_cast<uint4*>(sl + koff(XN + cb, gb + 2)) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
-                }
+            // a group is drained once the stages after it are in flight: its last
+            // stage's slot came back at this stage's empty wait
+            while (drained < ngroups && (drained + 1) * XDRAIN + XSTAGES - 1 <= kt) {
+                if (!(ok = drain(drained))) break;
+                ++drained;
             }
-            fence_proxy_async();
-            mbar_arrive(&full_bar[s]);
         }
         while (ok && drained < ngroups) {
             ok = drain(drained);
@@ -355,13 +366,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
                     float4 v = make_float4(acc[0][u] * sc, acc[1][u] * sc, acc[2][u] * sc, acc[3][u] * sc);
                     if (!GRAM && a.e.coilsdf) v = cdf_mul(v, cs);
                     if (a.part)
-                        a.part[((int64_t)blockIdx.z * a.F + f) * N + n] = v;
+                        a.part[(zpart * a.F + f) * N + n] = v;
                     else
                         a.B[f * N + n] = from_df(v);
                 }
             }
         }
-        if (MODE != XGEN && threadIdx.x == 0) {
+        if (threadIdx.x == 0) {
             // copies still in flight (only after an abort): wait, bounded, for their bytes
             for (int kg = a_issued > XSTAGES ? a_issued - XSTAGES : 0; kg < a_issued; ++kg)
                 mbar_wait(&abar[kg % XSTAGES], (uint32_t)(kg / XSTAGES) & 1u, nullptr);
@@ -374,8 +385,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
             if (first && g >= 1 && !mbar_wait(&tempty, (uint32_t)(g - 1) & 1u, &abort_flag)) break;
             const int s = kt % XSTAGES;
             const uint32_t ph = (uint32_t)(kt / XSTAGES) & 1u;
-            if (!mbar_wait(&full_bar[s], ph, &abort_flag)) break;
-            if (MODE != XGEN && !mbar_wait(&abar[s], ph, &abort_flag)) break;
+            if (MODE == XGEN && !mbar_wait(&full_bar[s], ph, &abort_flag)) break;
+            if (!mbar_wait(&abar[s], ph, &abort_flag)) break;
             tc_fence_after();
             const uint32_t abase = smem_u32(smem + s * XSTAGE);
             const uint32_t bbase = abase + NDIG * XA_SL;
@@ -543,6 +554,23 @@ size_t exact_work_elems(const EncodeDev& e, int64_t F) {
     return splits > 1 || e.coilsdf ? (size_t)splits * (size_t)e.N * (size_t)F : 0;
 }
 
+// digit tiles of the B operand: 32-frame tiles x coils x 16-sample chunks per coil
+static size_t b_digit_bytes(int64_t F, int64_t C, int64_t Kc) {
+    return (size_t)((F + tcx::XN - 1) / tcx::XN) * (size_t)C * (size_t)((Kc + tcx::XKC - 1) / tcx::XKC) *
+           (size_t)(tcx::NDIG * tcx::XB_SL);
+}
+
+static cudaError_t launch_b_digits(const double2* D, int64_t ld, int64_t F, int C, int64_t Kc, const int* fexp,
+                                   uint8_t* Bd, cudaStream_t s) {
+    const int64_t KB = (Kc + tcx::XKC - 1) / tcx::XKC;
+    const int64_t tiles = (F + tcx::XN - 1) / tcx::XN * C * KB;
+    tcx::k_b_digits<<<(unsigned)((tiles + 3) / 4), 256, 0, s>>>(D, ld, F, C, Kc, KB, fexp, Bd);
+    note_launch();
+    return cudaGetLastError();
+}
+
+size_t exact_bdigit_bytes(const EncodeDev& e, int64_t F) { return b_digit_bytes(F, e.C, e.Mk); }
+
 bool exact_adjoint_ok(const EncodeDev& e, int64_t F) {
     return e.extdf && !e.b0df && !e.b0tab && F >= 16 && tc_available();
 }
@@ -569,22 +597,25 @@ cudaError_t launch_adj_digits(const EncodeDev& e, uint8_t* Ad, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F, int* fexp, double2* B,
-                                 float4* work, DevStatus* st, cudaStream_t s, const uint8_t* Ad) {
+cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F, int* fexp, uint8_t* Bd,
+                                 double2* B, float4* work, DevStatus* st, cudaStream_t s, const uint8_t* Ad) {
     if (F == 0) return cudaSuccess;
+    if (!Bd) return cudaErrorInvalidValue;
     cudaError_t aerr = Ad ? exact_attr<tcx::XADJT>() : exact_attr<tcx::XGEN>();
     if (aerr != cudaSuccess) return aerr;
     const int64_t M = e.Mk * e.C;
     tcx::k_frame_exp<<<(unsigned)F, 256, 0, s>>>(D, M, fexp);
     note_launch();
+    cudaError_t berr = launch_b_digits(D, M, F, (int)e.C, e.Mk, fexp, Bd, s);
+    if (berr != cudaSuccess) return berr;
     const int sub = exact_sub(e, F);
     const int64_t splits = (int64_t)sub * e.C;
     const bool partials = splits > 1 || e.coilsdf;
     if (partials && !work) return cudaErrorInvalidValue;
     const int64_t chunk = ((e.Mk + sub - 1) / sub + tcx::XKC - 1) / tcx::XKC * tcx::XKC;
     const int64_t KB = (e.Mk + tcx::XKC - 1) / tcx::XKC;
-    tcx::XArgs a{e, D, fexp, F, M, chunk, sub, partials ? work : nullptr, B, Ad, nullptr, KB};
-    dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN), (unsigned)((e.N + tcx::XM - 1) / tcx::XM), (unsigned)splits);
+    tcx::XArgs a{e, D, fexp, F, M, chunk, sub, partials ? work : nullptr, B, Ad, nullptr, KB, Bd, (int)e.C};
+    const dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN * ((e.N + tcx::XM - 1) / tcx::XM) * splits));
     if (Ad)
         tcx::k_exact<tcx::XADJT><<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
     else
@@ -623,21 +654,25 @@ static int resid_splits(int64_t N, int64_t F) {
 
 size_t resid_exact_work_elems(int64_t N, int64_t F) { return (size_t)resid_splits(N, F) * (size_t)N * (size_t)F; }
 
+size_t resid_bdigit_bytes(int64_t N, int64_t F) { return b_digit_bytes(F, 1, N); }
+
 cudaError_t launch_gram_resid_exact(const uint8_t* Gd, const int* eG, int64_t N, const double2* Bv,
-                                    const double2* X, int64_t F, int* fexp, double2* R, float4* work,
-                                    DevStatus* st, cudaStream_t s) {
+                                    const double2* X, int64_t F, int* fexp, uint8_t* Bd, double2* R,
+                                    float4* work, DevStatus* st, cudaStream_t s) {
     if (F == 0) return cudaSuccess;
+    if (!Bd) return cudaErrorInvalidValue;
     cudaError_t err = exact_attr<tcx::XGRAM>();
     if (err != cudaSuccess) return err;
     tcx::k_frame_exp<<<(unsigned)F, 256, 0, s>>>(X, N, fexp);
     note_launch();
+    if ((err = launch_b_digits(X, N, F, 1, N, fexp, Bd, s)) != cudaSuccess) return err;
     const int sp = resid_splits(N, F);
     const int64_t chunk = ((N + sp - 1) / sp + tcx::XKC - 1) / tcx::XKC * tcx::XKC;
     EncodeDev e{};
     e.N = N;
     const int64_t KB = (N + tcx::XKC - 1) / tcx::XKC;
-    tcx::XArgs a{e, X, fexp, F, N, chunk, 1, work, nullptr, Gd, eG, KB};
-    dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN), (unsigned)((N + tcx::XM - 1) / tcx::XM), (unsigned)sp);
+    tcx::XArgs a{e, X, fexp, F, N, chunk, sp, work, nullptr, Gd, eG, KB, Bd, 1};
+    const dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN * ((N + tcx::XM - 1) / tcx::XM) * sp));
     tcx::k_exact<tcx::XGRAM><<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
     note_launch();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
