@@ -23,13 +23,16 @@
 //    warps read the six regions, scale class w by 2^(-12-7w) (exact) and add
 //    it into double-float accumulators held in registers.
 //
-// Tiles are 128 voxels x 32 frames (MMA M = 128, N = 64: real and imaginary
-// output columns side by side, as in the split-BF16 engine); the sample range
-// is split over CTAs and the double-float partials reduced in a fixed order.
-// Plans without B0 only (E from the separable phase tables and coil maps).
+// Tiles are 128 voxels x 32 frames (64 output columns, real and imaginary side
+// by side, as in the split-BF16 engine); the sample range is split over CTAs
+// and the double-float partials reduced in a fixed order. One MMA takes an A
+// digit against up to four B digits stacked along N (N <= 256), so a stage's 21
+// digit pairs cost 8 MMAs per 16-deep k half. Plans without B0 only (E from the
+// separable phase tables and coil maps).
 //
-// The digits of the A operand either come from the producer warps (XGEN) or
-// are copied with one bulk copy per stage from a table in the stage layout:
+// The digits of the B operand (data, or x) are written once per call by
+// k_b_digits. The digits of the A operand either come from the producer warps
+// (XGEN) or are copied with one bulk copy per stage from a table in the stage layout:
 // the exact Gram's digit tiles for the refinement residual (XGRAM), or the
 // digits of conj(A) written once per build (XADJT; the same digits XGEN
 // forms, which it would otherwise form again for every coil and frame tile).
@@ -54,8 +57,22 @@ constexpr int XA_SL = XM * 64;         // one digit slice of A: 128 rows x 32 bf
 constexpr int XB_SL = 2 * XN * 64;     // one digit slice of B: 64 stacked rows x 32 bf16 = 4 KiB
 constexpr int XSTAGE = NDIG * (XA_SL + XB_SL);  // 72 KiB
 constexpr int XSMEM = XSTAGES * XSTAGE + 1024;
-constexpr uint32_t XIDESC =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * XN) >> 3) << 17) | ((uint32_t)(XM >> 4) << 24);
+// bf16 x bf16 -> f32, K-major operands, M = XM, N = n
+__host__ __device__ constexpr uint32_t xidesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(XM >> 4) << 24);
+}
+// The B digit slices lie one after another (XB_SL apart, 8-row groups 512 B apart
+// throughout), so slices j0 .. j0 + n/64 - 1 form one operand of n rows, and the
+// classes i + j of A digit i are adjacent 64-column TMEM regions: one MMA covers
+// several digit pairs. Per A digit i: (first B slice, N) of its MMAs, N <= 256.
+struct XPairRun {
+    int i, j0, n;
+};
+__device__ __forceinline__ XPairRun xrun(int r) {
+    constexpr XPairRun t[8] = {{0, 0, 256}, {0, 4, 128}, {1, 0, 256}, {1, 4, 64},
+                               {2, 0, 256}, {3, 0, 192}, {4, 0, 128}, {5, 0, 64}};
+    return t[r];
+}
 // Per class and group: at most 6 pairs x 32 products x XDRAIN stages, each below 2^12.
 static_assert(NCLS * 32 * XDRAIN * 4096 < (1 << 24), "exact class sums");
 
@@ -378,7 +395,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
                 mbar_wait(&abar[kg % XSTAGES], (uint32_t)(kg / XSTAGES) & 1u, nullptr);
         }
     } else if (lane == 0) {
-        // ---------------- MMA issuer: 21 digit pairs per stage, class w = i + j into region w
+        // ---------------- MMA issuer: 21 digit pairs per stage in 8 MMAs per k half,
+        // class w = i + j into region w
         for (int kt = 0; kt < nk; ++kt) {
             const int g = kt / XDRAIN;
             const bool first = (kt % XDRAIN) == 0;
@@ -391,15 +409,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
             const uint32_t abase = smem_u32(smem + s * XSTAGE);
             const uint32_t bbase = abase + NDIG * XA_SL;
 #pragma unroll
-            for (int w = 0; w < NCLS; ++w) {
+            for (int kk = 0; kk < 2; ++kk) {
 #pragma unroll
-                for (int i = 0; i <= w; ++i) {
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const uint64_t da = sdesc(abase + i * XA_SL + kk * 256, 128, 512);
-                        const uint64_t db = sdesc(bbase + (w - i) * XB_SL + kk * 256, 128, 512);
-                        mma_bf16(tmem + (uint32_t)(64 * w), da, db, XIDESC, (first && i == 0 && kk == 0) ? 0u : 1u);
-                    }
+                for (int r = 0; r < 8; ++r) {
+                    // the runs of A digit 0 cover all six regions: they start each group
+                    const XPairRun u = xrun(r);
+                    const uint64_t da = sdesc(abase + u.i * XA_SL + kk * 256, 128, 512);
+                    const uint64_t db = sdesc(bbase + u.j0 * XB_SL + kk * 256, 128, 512);
+                    mma_bf16(tmem + (uint32_t)(64 * (u.i + u.j0)), da, db, xidesc(u.n),
+                             (first && u.i == 0 && kk == 0) ? 0u : 1u);
                 }
             }
             mma_commit(&empty_bar[s]);
