@@ -132,7 +132,8 @@ pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events) {
         // (it reads only the panel's L32 columns and diagonal inverses, final once the
         // panel's solves are done); the Cholesky chain leaves most SMs idle
         CK(cudaEventRecord(p->ev_fork, s));
-        CK(launch_potrf_tc(p->G, N, ld, p->Dinv, D32, L32, p->slices(), p->st, s, tab, p->ev_panel.data()));
+        // (the FP64 diagonal inverses are not needed: the inverse reads the FP32 ones)
+        CK(launch_potrf_tc(p->G, N, ld, nullptr, D32, L32, p->slices(), p->st, s, tab, p->ev_panel.data()));
         CK(launch_pivot_stats(p->G, N, ld, p->st, s));
         if (events) CK(cudaEventRecord(p->ev[3], s));
         CK(cudaStreamWaitEvent(p->s_inv, p->ev_fork, 0));

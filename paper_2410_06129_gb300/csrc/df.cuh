@@ -25,6 +25,54 @@ __device__ inline void fast_two_sum(float a, float b, float& s, float& e) {
     s = a + b;
     e = b - (s - a);
 }
+// The same conversions without the FP64 pipe (integer and FP32 instructions only),
+// for kernels that convert many values on one SM. x -> (hi, lo): hi keeps the
+// leading 24 bits of the significand, lo is the float nearest the remainder
+// (then renormalised); below 2^-74 lo is dropped and below 2^-126 both are
+// (far below the resolution of the values converted here). Zero, infinity and
+// NaN take the FP64 conversion.
+__device__ inline float2 split_f64(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+    const int ex = (int)((b >> 52) & 0x7ffu);
+    if (ex == 0 || ex == 0x7ff) return make_float2((float)x, 0.f);
+    const int fe = ex - 1023 + 127;  // float exponent field of hi
+    if (fe <= 0) return make_float2(__uint_as_float(sgn), 0.f);
+    if (fe >= 255) return make_float2((float)x, 0.f);
+    const float h = __uint_as_float(sgn | ((unsigned)fe << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    float l = 0.f;
+    if (fe > 52) {  // remainder r * 2^(E - 52), E = fe - 127; the scale's field is fe - 52
+        const float r = (float)(unsigned)(b & 0x1fffffffu);
+        l = __uint_as_float(sgn | __float_as_uint(r * __uint_as_float((unsigned)(fe - 52) << 23)));
+    }
+    float sh, sl;
+    fast_two_sum(h, l, sh, sl);
+    return make_float2(sh, sl);
+}
+// (hi, lo) -> double within one unit in the last place: hi exactly, plus lo
+// rounded to hi's grid (units of 2^-52 |hi|, twice as fine below a power of two).
+__device__ inline double join_f64(float h, float l) {
+    const unsigned hb = __float_as_uint(h), lb = __float_as_uint(l);
+    const int eh = (int)((hb >> 23) & 0xffu), el = (int)((lb >> 23) & 0xffu);
+    if (eh == 0 || eh == 0xff || el == 0xff) return (double)h + (double)l;
+    const unsigned mh = hb & 0x7fffffu;
+    unsigned long long bits = ((unsigned long long)(hb & 0x80000000u) << 32) |
+                              ((unsigned long long)(eh - 127 + 1023) << 52) | ((unsigned long long)mh << 29);
+    if (el == 0) return __longlong_as_double((long long)bits);  // lo zero or below the float range
+    // lo in units of hi's last place: (2^23 + ml) * 2^(el - eh + 29)
+    const unsigned ml = (lb & 0x7fffffu) | 0x800000u;
+    const int sh = el - eh + 29;
+    unsigned long long d;
+    if (sh >= 0)
+        d = sh < 40 ? (unsigned long long)ml << sh : 0ull;  // |lo| <= ulp(hi) keeps sh <= 6
+    else
+        d = -sh < 26 ? ((unsigned long long)ml + (1ull << (-sh - 1))) >> -sh : 0ull;
+    if ((hb ^ lb) & 0x80000000u)
+        bits -= mh == 0 ? 2 * d : d;  // below a power of two the grid is twice as fine
+    else
+        bits += d;
+    return __longlong_as_double((long long)bits);
+}
 // (xh + xl)(yh + yl) as a normalised pair
 __device__ inline void df_mul(float xh, float xl, float yh, float yl, float& rh, float& rl) {
     const float p = xh * yh;

@@ -299,7 +299,7 @@ cudaError_t launch_from_df(const float4* a, int64_t n, double2* b, cudaStream_t 
 namespace {
 constexpr int NBD = 64;
 constexpr int NBDP = NBD + 1;  // padded row stride of the shared-memory blocks
-constexpr int DIAG_THREADS = 1024;  // 16 lanes per column in the inverse
+constexpr int DIAG_THREADS = 1024;
 __device__ inline float4 df_scale(float4 a, float rh, float rl) {  // complex DF times real DF
     float xh, xl, yh, yl;
     df_mul(a.x, a.y, rh, rl, xh, xl);
@@ -337,151 +337,101 @@ __device__ inline float2 df_rsqrt(float dh, float dl) {
     return make_float2(uh, ul);
 }
 
-// Blocked 64 x 64: four 16-wide panels. For each panel one warp factors the
-// 16 x 16 diagonal block (warp-synchronous, column by column), then all threads
-// solve the rows below against it and update the trailing block. The inverse
-// is blocked the same way: the four diagonal 16 x 16 inverses in parallel
-// (one warp each), then block diagonals d = 1..3 with
-// X_qp = -X_qq (sum_{r=p}^{q-1} L_qr X_rp).
-constexpr int PB = 16;  // panel width
+// Column sweep over the 64 x 64 block, factor and inverse together (both
+// right-looking). Step j:
+//  (a) the 64 threads of the first two warps each form r = 1 / sqrt(A_jj) from
+//      the broadcast pivot (the same value in every thread, so no barrier);
+//      thread i > j scales L_ij = A_ij r, thread c <= j scales row j of
+//      X = L^-1 (X_jc *= r: row j of X is then final);
+//  (b) thread j writes L_jj (nothing reads A_jj any more), and the threads
+//      update every entry (i, c), c <= i, of the rows i > j: c <= j is
+//      X_ic -= L_ij X_jc, c > j is A_ic -= L_ij conj(L_cj). Row j + 1 + p is
+//      paired with row 63 - p, so each pair holds j + 66 entries and the
+//      threads run over pairs without idle lanes.
+// Two barriers per column. Rows are NBDP = 65 entries apart, so row and column
+// reads are free of bank conflicts. Values enter and leave through integer and
+// FP32 conversions: on GB300 the FP64 pipe of the one SM would take longer.
+// Dinv may be null (the FP32 inverse alone).
 __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0,
                                                              double2* Dinv, float2* Dinv32, DevStatus* st) {
     extern __shared__ float4 smd[];
-    float4* A = smd;                  // [NBD][NBDP]: rows padded by 16 bytes, so that
-                                      // column accesses of a warp spread over all banks
-    float4* X = smd + NBD * NBDP;     // [NBD][NBDP] inverse
-    __shared__ float4 T[3][PB][PB];   // block sums of the current diagonal level
-    __shared__ float2 rdiag[NBD];     // 1 / L_jj as (hi, lo)
+    float4* A = smd;               // [NBD][NBDP]
+    float4* X = smd + NBD * NBDP;  // [NBD][NBDP] inverse
     __shared__ int bad;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
     const int nb = (int)((N - k0) < NBD ? (N - k0) : NBD);
     if (tid == 0) bad = (st->not_pd_pivot != INT_MAX) ? 1 : 0;
 #pragma unroll
     for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
         const int i = e / NBD, j = e % NBD;
-        double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
-        if (i < nb && j < nb && j <= i) v = G[(k0 + i) * ld + k0 + j];
-        A[i * NBDP + j] = to_df(v);
-        X[i * NBDP + j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 v = make_float4(i == j ? 1.f : 0.f, 0.f, 0.f, 0.f);
+        if (i < nb && j < nb && j <= i) {
+            const double2 g = G[(k0 + i) * ld + k0 + j];
+            const float2 re = split_f64(g.x), im = split_f64(g.y);
+            v = make_float4(re.x, re.y, im.x, im.y);
+        }
+        A[i * NBDP + j] = v;
+        X[i * NBDP + j] = make_float4(i == j ? 1.f : 0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
 
-    for (int p0 = 0; p0 < NBD; p0 += PB) {
-        if (warp == 0) {
-            // 16 x 16 diagonal block, right-looking; lane l owns row p0 + (l & 15)
-            for (int c = 0; c < PB; ++c) {
-                const int jc = p0 + c;
-                float2 r = make_float2(0.f, 0.f);
-                if (lane == 0) {
-                    const float4 a = A[jc * NBDP + jc];
-                    float dh = a.x, dl = a.y;
-                    if (!((double)dh + (double)dl > 0.0) || !isfinite(dh)) {
-                        if (!bad) atomicMin(&st->not_pd_pivot, (int)(k0 + jc));
+    for (int j = 0; j < NBD; ++j) {
+        float lh = 0.f, ll = 0.f;  // L_jj in thread j
+        if (tid < NBD) {
+            const float4 a = A[j * NBDP + j];
+            float dh = a.x, dl = a.y;
+            const bool fail = !(dh > 0.f) || !isfinite(dh);  // a normalised pair has the sign of dh
+            if (fail) {
+                dh = 1.f;
+                dl = 0.f;
+            }
+            const float2 r = df_rsqrt(dh, dl);
+            if (tid > j) {
+                A[tid * NBDP + j] = df_norm(df_scale(A[tid * NBDP + j], r.x, r.y));
+            } else {
+                X[j * NBDP + tid] = df_norm(df_scale(X[j * NBDP + tid], r.x, r.y));
+                if (tid == j) {
+                    if (fail && !bad) {
+                        atomicMin(&st->not_pd_pivot, (int)(k0 + j));
                         bad = 1;
-                        dh = 1.f;
-                        dl = 0.f;
                     }
-                    r = df_rsqrt(dh, dl);
-                    float lh, ll;
                     df_mul(dh, dl, r.x, r.y, lh, ll);  // L_jj = d / sqrt(d)
-                    A[jc * NBDP + jc] = make_float4(lh, ll, 0.f, 0.f);
-                    rdiag[jc] = r;
                 }
-                r.x = __shfl_sync(0xffffffffu, r.x, 0);
-                r.y = __shfl_sync(0xffffffffu, r.y, 0);
-                // scale column c below the diagonal inside the block
-                const int i = p0 + (lane & (PB - 1));
-                if (lane < PB && i > jc) A[i * NBDP + jc] = df_norm(df_scale(A[i * NBDP + jc], r.x, r.y));
-                __syncwarp();
-                // trailing update inside the block: rows and columns c+1..15
-                for (int e = lane; e < PB * PB; e += 32) {
-                    const int ii = p0 + e / PB, kk = p0 + e % PB;
-                    if (kk > jc && ii >= kk) {
-                        float4 v = A[ii * NBDP + kk];
-                        const float4 a = A[ii * NBDP + jc], b = A[kk * NBDP + jc];
-                        cacc(v, make_float4(-a.x, -a.y, -a.z, -a.w), cdf_conj(b));
-                        A[ii * NBDP + kk] = df_norm(v);
-                    }
-                }
-                __syncwarp();
             }
         }
         __syncthreads();
-        // rows below the panel: solve x L_pp^H = a for each row (one thread per row)
-        const int rows_below = NBD - p0 - PB;
-        if (tid < rows_below) {  // in place: x_c overwrites A[i][p0 + c] once known
-            const int i = p0 + PB + tid;
-            for (int c = 0; c < PB; ++c) {
-                float4 v = A[i * NBDP + p0 + c];
-                for (int c2 = 0; c2 < c; ++c2) {
-                    const float4 x = A[i * NBDP + p0 + c2], l = A[(p0 + c) * NBDP + p0 + c2];
-                    cacc(v, make_float4(-x.x, -x.y, -x.z, -x.w), cdf_conj(l));
-                }
-                A[i * NBDP + p0 + c] = df_norm(df_scale(df_norm(v), rdiag[p0 + c].x, rdiag[p0 + c].y));
-            }
-        }
-        __syncthreads();
-        // trailing update of the lower block below and right of the panel (K = 16)
-        if (rows_below > 0) {
-            for (int e = tid; e < rows_below * rows_below; e += DIAG_THREADS) {
-                const int ii = p0 + PB + e / rows_below, kk = p0 + PB + e % rows_below;
-                if (kk > ii) continue;
-                float4 v = A[ii * NBDP + kk];
-#pragma unroll
-                for (int c = 0; c < PB; ++c) {
-                    const float4 a = A[ii * NBDP + p0 + c], b = A[kk * NBDP + p0 + c];
-                    cacc(v, make_float4(-a.x, -a.y, -a.z, -a.w), cdf_conj(b));
-                }
-                A[ii * NBDP + kk] = df_norm(v);
-            }
-        }
-        __syncthreads();
-    }
-
-    // inverse: diagonal blocks, one warp each (lane = column of the block)
-    if (warp < NBD / PB && lane < PB) {
-        const int p0 = warp * PB, c = p0 + lane;
-        for (int i = p0; i < p0 + PB; ++i) {
-            float4 v = make_float4(i == c ? 1.f : 0.f, 0.f, 0.f, 0.f);
-            for (int k = c; k < i; ++k) {
-                const float4 l = A[i * NBDP + k];
-                cacc(v, make_float4(-l.x, -l.y, -l.z, -l.w), X[k * NBDP + c]);
-            }
-            X[i * NBDP + c] = i >= c ? df_norm(df_scale(df_norm(v), rdiag[i].x, rdiag[i].y)) : make_float4(0.f, 0.f, 0.f, 0.f);
-            __syncwarp(0x0000ffffu);
-        }
-    }
-    __syncthreads();
-    // off-diagonal blocks, one block diagonal at a time
-    for (int d = 1; d < NBD / PB; ++d) {
-        const int npairs = NBD / PB - d;
-        // T_qp = sum_{r=p}^{q-1} L_qr X_rp   (q = p + d)
-        for (int e = tid; e < npairs * PB * PB; e += DIAG_THREADS) {
-            const int pr = e / (PB * PB), ii = (e / PB) % PB, cc = e % PB;
-            const int p = pr, q = p + d;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int k = p * PB; k < q * PB; ++k) cacc(v, A[(q * PB + ii) * NBDP + k], X[k * NBDP + p * PB + cc]);
-            T[pr][ii][cc] = df_norm(v);
-        }
-        __syncthreads();
-        // X_qp = -X_qq T_qp
-        for (int e = tid; e < npairs * PB * PB; e += DIAG_THREADS) {
-            const int pr = e / (PB * PB), ii = (e / PB) % PB, cc = e % PB;
-            const int p = pr, q = p + d;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int k = 0; k <= ii; ++k) cacc(v, X[(q * PB + ii) * NBDP + q * PB + k], T[pr][k][cc]);
-            v = df_norm(v);
-            X[(q * PB + ii) * NBDP + p * PB + cc] = make_float4(-v.x, -v.y, -v.z, -v.w);
+        if (tid == j) A[j * NBDP + j] = make_float4(lh, ll, 0.f, 0.f);
+        const int rows = NBD - 1 - j, w = j + 66;  // rows below; entries per row pair
+        const int slots = ((rows + 1) >> 1) * w;
+        const float winv = 1.f / (float)w;
+        for (int e = tid; e < slots; e += DIAG_THREADS) {
+            const int p = (int)(((float)e + 0.5f) * winv);  // e / w (e < 2^12: exact)
+            const int q = e - p * w;
+            const int ia = j + 1 + p, ib = NBD - 1 - p;
+            const bool first = q <= ia;
+            const int i = first ? ia : ib, c = first ? q : q - ia - 1;
+            if (!first && ib <= ia) continue;  // the middle row of an odd count has no partner
+            const bool xs = c <= j;
+            float4* t = (xs ? X : A) + i * NBDP + c;
+            float4 b = xs ? X[j * NBDP + c] : A[c * NBDP + j];
+            if (!xs) b = cdf_conj(b);
+            const float4 l = A[i * NBDP + j];
+            float4 v = *t;
+            cacc(v, make_float4(-l.x, -l.y, -l.z, -l.w), b);
+            *t = df_norm(v);
         }
         __syncthreads();
     }
 #pragma unroll
     for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
         const int i = e / NBD, j = e % NBD;
-        const double2 x = from_df(X[i * NBDP + j]);
-        Dinv[e] = x;
-        if (Dinv32) Dinv32[e] = make_float2((float)x.x, (float)x.y);
-        if (i < nb && j < nb && j <= i) G[(k0 + i) * ld + k0 + j] = from_df(A[i * NBDP + j]);
+        const float4 x = j <= i ? X[i * NBDP + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (Dinv) Dinv[e] = make_double2(join_f64(x.x, x.y), join_f64(x.z, x.w));
+        if (Dinv32) Dinv32[e] = make_float2(x.x + x.y, x.z + x.w);
+        if (i < nb && j < nb && j <= i) {
+            const float4 a = A[i * NBDP + j];
+            G[(k0 + i) * ld + k0 + j] = make_double2(join_f64(a.x, a.y), join_f64(a.z, a.w));
+        }
     }
 }
 

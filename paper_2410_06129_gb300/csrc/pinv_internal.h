@@ -201,8 +201,10 @@ cudaError_t launch_trmv_h64(const double2* W, int64_t N, const double2* X, int64
 // X[f][n] = sum_j R[n][j] D[f][j], c64 (R c64 [N][M], D c64 [F][M]).
 cudaError_t launch_apply32(const float2* R, int64_t N, int64_t M, const float2* D, int64_t F,
                            float2* X, cudaStream_t s);
-// Blocked Cholesky with FP64 diagonal panels and tensor-core panel solves and
-// trailing updates; L32 receives an FP32 copy of L ([N][N], lower part).
+// Blocked Cholesky with double-float diagonal blocks, FP32 panel solves and
+// tensor-core trailing updates; L32 receives an FP32 copy of L ([N][N], lower
+// part), Dinv32 the FP32 inverses of the diagonal blocks and Dinv (or nullptr)
+// their FP64 copies.
 // tab (factor_table_bytes(), or nullptr): operand tables of the bulk-fed
 // panel trailing updates; without it the updates generate their operands.
 size_t factor_table_bytes(int64_t N, int slices);

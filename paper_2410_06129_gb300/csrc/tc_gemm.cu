@@ -1087,7 +1087,8 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
             const int64_t nbk = std::min<int64_t>(NBK, N - k0);
             const int64_t kb = k0 / NBK;
             cudaError_t e =
-                launch_potrf_diag_df(G, ld, N, k0, Dinv + kb * NBK * NBK, Dinv32 + kb * NBK * NBK, st, s);
+                launch_potrf_diag_df(G, ld, N, k0, Dinv ? Dinv + kb * NBK * NBK : nullptr,
+                                     Dinv32 + kb * NBK * NBK, st, s);
             if (e != cudaSuccess) return e;
             e = block_to_f32(G, ld, k0, N, k0, k0 + nbk, L32, N, s);
             if (e != cudaSuccess) return e;
