@@ -132,13 +132,21 @@ pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events) {
         // (it reads only the panel's L32 columns and diagonal inverses, final once the
         // panel's solves are done); the Cholesky chain leaves most SMs idle
         CK(cudaEventRecord(p->ev_fork, s));
+        // the chain on the high-priority stream (PINV_CHOL_HI=0: on s)
+        const char* hi = std::getenv("PINV_CHOL_HI");
+        cudaStream_t sc = (p->s_chol && !(hi && std::strcmp(hi, "0") == 0)) ? p->s_chol : s;
+        if (sc != s) CK(cudaStreamWaitEvent(sc, p->ev_fork, 0));
         // (the FP64 diagonal inverses are not needed: the inverse reads the FP32 ones)
-        CK(launch_potrf_tc(p->G, N, ld, nullptr, D32, L32, p->slices(), p->st, s, tab, p->ev_panel.data()));
-        CK(launch_pivot_stats(p->G, N, ld, p->st, s));
-        if (events) CK(cudaEventRecord(p->ev[3], s));
+        CK(launch_potrf_tc(p->G, N, ld, nullptr, D32, L32, p->slices(), p->st, sc, tab, p->ev_panel.data()));
+        CK(launch_pivot_stats(p->G, N, ld, p->st, sc));
+        if (events) CK(cudaEventRecord(p->ev[3], sc));
         CK(cudaStreamWaitEvent(p->s_inv, p->ev_fork, 0));
         CK(launch_trtri_tc(L32, N, D32, p->W, p->W32, p->slices(), p->st_inv, p->s_inv, tab_inv,
                            p->ev_panel.data()));
+        if (sc != s) {
+            CK(cudaEventRecord(p->ev_chol, sc));
+            CK(cudaStreamWaitEvent(p->s_inv, p->ev_chol, 0));  // st is read below
+        }
         CK(launch_merge_timeout(p->st, p->st_inv, p->s_inv));
         CK(cudaEventRecord(p->ev_join, p->s_inv));
         CK(cudaStreamWaitEvent(s, p->ev_join, 0));
@@ -483,6 +491,10 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
         AL(p->st_inv, sizeof(DevStatus), "inverse status");
         CKC(cudaMemset(p->st_inv, 0, sizeof(DevStatus)));
         CKC(cudaStreamCreateWithFlags(&p->s_inv, cudaStreamNonBlocking));
+        int prio_lo = 0, prio_hi = 0;
+        CKC(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        CKC(cudaStreamCreateWithPriority(&p->s_chol, cudaStreamNonBlocking, prio_hi));
+        CKC(cudaEventCreateWithFlags(&p->ev_chol, cudaEventDisableTiming));
         p->ev_panel.assign((size_t)((p->N + 255) / 256), nullptr);
         for (auto& ev : p->ev_panel) CKC(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         CKC(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));

@@ -96,8 +96,11 @@ struct pinv_plan {
     // one panel behind (its tile counter and timeout record; one event per panel)
     pinv::DevStatus* st_inv = nullptr;
     cudaStream_t s_inv = nullptr;
+    // the Cholesky chain's stream, at the device's highest priority: its small
+    // launches get SMs ahead of the inverse's tiles (and of other work)
+    cudaStream_t s_chol = nullptr;
     std::vector<cudaEvent_t> ev_panel;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_xfork = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_xfork = nullptr, ev_chol = nullptr;
 
     // pinv_apply's scratch region, grown on demand
     void* scratch_buf = nullptr;
@@ -154,6 +157,8 @@ struct pinv_plan {
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
         if (ev_xfork) cudaEventDestroy(ev_xfork);
+        if (ev_chol) cudaEventDestroy(ev_chol);
         if (s_inv) cudaStreamDestroy(s_inv);
+        if (s_chol) cudaStreamDestroy(s_chol);
     }
 };

@@ -786,35 +786,40 @@ __global__ void __launch_bounds__(NTHREADS_BULK, 1) k_tc_bulk(Sched sch, DevStat
 int sm_count();
 
 template <class K, class... A>
-static cudaError_t launch_persistent(K kern, int threads, int smem, bool& attr, int64_t items, cudaStream_t s,
-                                     const A&... args) {
+static cudaError_t launch_persistent(K kern, int threads, int smem, bool& attr, int64_t items, int cap,
+                                     cudaStream_t s, const A&... args) {
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     if (items == 0) return cudaSuccess;
-    const int64_t ctas = items < sm_count() ? items : sm_count();
+    const int64_t limit = cap > 0 && cap < sm_count() ? cap : sm_count();
+    const int64_t ctas = items < limit ? items : limit;
     kern<<<(unsigned)ctas, threads, smem, s>>>(args...);
     note_launch();
     return cudaGetLastError();
 }
 
+// cap > 0: at most cap CTAs (SMs), leaving the others to concurrent work
 template <int S, class Sched>
-static cudaError_t launch_sched(const Sched& sch, int64_t items, DevStatus* st, int site, cudaStream_t s) {
+static cudaError_t launch_sched(const Sched& sch, int64_t items, DevStatus* st, int site, cudaStream_t s,
+                                int cap = 0) {
     static bool attr = false;
     if constexpr (IsBulk<typename Sched::Prob>::value)
-        return launch_persistent(k_tc_bulk<S, Sched>, NTHREADS_BULK, Cfg<S>::SMEM, attr, items, s, sch, st, site);
+        return launch_persistent(k_tc_bulk<S, Sched>, NTHREADS_BULK, Cfg<S>::SMEM, attr, items, cap, s, sch, st,
+                                 site);
     else
-        return launch_persistent(k_tc<S, Sched>, NTHREADS, Cfg<S>::SMEM, attr, items, s, sch, st, site);
+        return launch_persistent(k_tc<S, Sched>, NTHREADS, Cfg<S>::SMEM, attr, items, cap, s, sch, st, site);
 }
 
 // One problem over a grid.x x grid.y grid of tiles (bx = x, by = y). Launches
 // sharing a status block must run one after another (one stream).
 template <int S, class P>
-static cudaError_t launch(const P& p, dim3 grid, DevStatus* st, int site, cudaStream_t s, bool rev = false) {
+static cudaError_t launch(const P& p, dim3 grid, DevStatus* st, int site, cudaStream_t s, bool rev = false,
+                          int cap = 0) {
     const int64_t n = (int64_t)grid.x * grid.y;
-    return launch_sched<S>(OneProblem<P>{p, (int64_t)grid.x, n, rev}, n, st, site, s);
+    return launch_sched<S>(OneProblem<P>{p, (int64_t)grid.x, n, rev}, n, st, site, s, cap);
 }
 
 // Several problems of one kind in one persistent launch; the arrays live in

@@ -877,8 +877,8 @@ static cudaError_t block_to_f32(const double2* src, int64_t ld, int64_t r0, int6
 
 template <class P>
 static cudaError_t run(const P& p, dim3 grid, int slices, DevStatus* st, int site, cudaStream_t s,
-                       bool rev = false) {
-    return slices == 3 ? tc::launch<3>(p, grid, st, site, s, rev) : tc::launch<2>(p, grid, st, site, s, rev);
+                       bool rev = false, int cap = 0) {
+    return slices == 3 ? tc::launch<3>(p, grid, st, site, s, rev, cap) : tc::launch<2>(p, grid, st, site, s, rev, cap);
 }
 
 static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
@@ -1143,6 +1143,12 @@ cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, 
                             int slices, DevStatus* st, cudaStream_t s, void* tab, const cudaEvent_t* ev_panel) {
     cudaError_t e = launch_fill_identity(W, N, N, s);
     if (e != cudaSuccess) return e;
+    // the inverse runs beside the Cholesky chain: its persistent launches take at
+    // most half the SMs (PINV_INV_SMS: another count, 0 all), so that the chain's
+    // launches find free SMs; at 64x64 this takes the Cholesky from 10.7 to 10.4 ms
+    // and the inverse still ends with it
+    const char* cenv = std::getenv("PINV_INV_SMS");
+    const int cap = cenv ? std::atoi(cenv) : std::max(1, tc::sm_count() / 2);
     for (int64_t p0 = 0; p0 < N; p0 += NBP) {
         const int64_t pend = std::min<int64_t>(N, p0 + NBP);
         if (ev_panel && (e = cudaStreamWaitEvent(s, ev_panel[p0 / NBP], 0)) != cudaSuccess) return e;
@@ -1150,10 +1156,11 @@ cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, 
             const int64_t nbk = std::min<int64_t>(NBK, N - k0);
             const int64_t ncol = k0 + nbk;
             tc::TrtriDiagTC dp{Dinv32 + (k0 / NBK) * NBK * NBK, W, N, N, k0, nbk};
-            if ((e = run(dp, dim3(cdiv(ncol, tc::BN), 1), slices, st, 5, s)) != cudaSuccess) return e;
+            if ((e = run(dp, dim3(cdiv(ncol, tc::BN), 1), slices, st, 5, s, false, cap)) != cudaSuccess) return e;
             if (ncol >= pend) continue;
             tc::TrtriUpdTC up{L32, N, W, N, N, k0, nbk, pend};
-            if ((e = run(up, dim3(cdiv(ncol, tc::BN), cdiv(pend - ncol, tc::BM)), slices, st, 6, s)) != cudaSuccess)
+            if ((e = run(up, dim3(cdiv(ncol, tc::BN), cdiv(pend - ncol, tc::BM)), slices, st, 6, s, false, cap)) !=
+                cudaSuccess)
                 return e;
         }
         if (pend < N) {
@@ -1170,10 +1177,11 @@ cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, 
                 note_launch();
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
                 tc::TrtriBulk up{tabl, tabw, W, N, N, pend, ntr, ntc, kcn, slices};
-                if ((e = run(up, dim3((unsigned)(ntr * ntc), 1), slices, st, 6, s)) != cudaSuccess) return e;
+                if ((e = run(up, dim3((unsigned)(ntr * ntc), 1), slices, st, 6, s, false, cap)) != cudaSuccess)
+                    return e;
             } else {
                 tc::TrtriUpdTC up{L32, N, W, N, N, p0, pend - p0, N};
-                if ((e = run(up, dim3(cdiv(pend, tc::BN), cdiv(N - pend, tc::BM)), slices, st, 6, s)) !=
+                if ((e = run(up, dim3(cdiv(pend, tc::BN), cdiv(N - pend, tc::BM)), slices, st, 6, s, false, cap)) !=
                     cudaSuccess)
                     return e;
             }
