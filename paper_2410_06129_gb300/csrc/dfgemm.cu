@@ -403,9 +403,9 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
         if (tid == j) A[j * NBDP + j] = make_float4(lh, ll, 0.f, 0.f);
         const int rows = NBD - 1 - j, w = j + 66;  // rows below; entries per row pair
         const int slots = ((rows + 1) >> 1) * w;
-        const float winv = 1.f / (float)w;
+        const unsigned wm = ((1u << 20) + (unsigned)w - 1u) / (unsigned)w;  // e / w = (e wm) >> 20 for e < 2^20 / w
         for (int e = tid; e < slots; e += DIAG_THREADS) {
-            const int p = (int)(((float)e + 0.5f) * winv);  // e / w (e < 2^12: exact)
+            const int p = (int)(((unsigned)e * wm) >> 20);
             const int q = e - p * w;
             const int ia = j + 1 + p, ib = NBD - 1 - p;
             const bool first = q <= ia;

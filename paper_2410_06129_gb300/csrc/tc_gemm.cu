@@ -981,79 +981,165 @@ cudaError_t launch_gram_bulk(const EncodeDev& e, double lambda, int slices, doub
 // microseconds that a tensor-core launch spends on setting up TMEM, barriers and
 // its pipeline. These kernels stage the 64-wide operands in shared memory and
 // accumulate in FP32 (the accuracy class of the split-BF16 products).
-constexpr int PNL_ROWS_TRSM = 16, PNL_ROWS_HERK = 32, PNL_MAXW = 192;
+constexpr int PNL_ROWS = 16;
+
+// Both kernels: 16 rows per CTA, and each thread holds 2 rows (warp w: rows w and
+// w + 8) x CB columns (lane + 32 b) of accumulators, so one shared-memory read
+// serves several products. The column operand is stored k-major, so a warp reads
+// 32 consecutive columns. Every output sums its 64 (zero-padded) k terms in
+// order, with the same two FMAs per term as a one-output-per-thread loop.
+// Operands are staged 16 loads per thread at a time, all issued before their
+// stores, so a CTA waits for a few memory latencies rather than one per element.
+__device__ inline void cmac_conj(float2& acc, float2 a, float2 b) {  // acc += a * conj(b)
+    acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
+    acc.y = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc.y));
+}
 
 // L[i][k0 + j] = sum_k P[i][k] conj(Dinv[j][k]) for rows i >= row0: written to G
 // (FP64) and back over P (FP32), in place (each CTA reads its rows first)
 __global__ void __launch_bounds__(256) k_trsm_panel(float2* P, int64_t ldp, const float2* __restrict__ Dinv32,
                                                   double2* G, int64_t ldg, int64_t k0, int nbk, int64_t row0,
                                                   int64_t N) {
-    __shared__ float2 D[64][65];
-    __shared__ float2 A[PNL_ROWS_TRSM][64];
-    const int tid = threadIdx.x;
-    const int64_t i0 = row0 + (int64_t)blockIdx.x * PNL_ROWS_TRSM;
-    for (int e = tid; e < 64 * 64; e += 256) {
-        const int j = e / 64, k = e % 64;
-        D[j][k] = (j < nbk && k < nbk) ? Dinv32[j * 64 + k] : make_float2(0.f, 0.f);
-    }
-    for (int e = tid; e < PNL_ROWS_TRSM * 64; e += 256) {
-        const int r = e / 64, k = e % 64;
-        const int64_t i = i0 + r;
-        A[r][k] = (i < N && k < nbk) ? P[i * ldp + k] : make_float2(0.f, 0.f);
+    __shared__ float2 Dt[64][65];  // Dt[k][j] = Dinv[j][k]
+    __shared__ float2 A[PNL_ROWS][64];
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int64_t i0 = row0 + (int64_t)blockIdx.x * PNL_ROWS;
+    {
+        float2 v[16], u[4];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int e = tid + 256 * t, j = e / 64, k = e % 64;
+            v[t] = (j < nbk && k < nbk) ? Dinv32[j * 64 + k] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int e = tid + 256 * t, r = e / 64, k = e % 64;
+            const int64_t i = i0 + r;
+            u[t] = (i < N && k < nbk) ? P[i * ldp + k] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int e = tid + 256 * t;
+            Dt[e % 64][e / 64] = v[t];
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int e = tid + 256 * t;
+            A[e / 64][e % 64] = u[t];
+        }
     }
     __syncthreads();
+    float2 acc[2][2];
 #pragma unroll
-    for (int u = 0; u < PNL_ROWS_TRSM * 64 / 256; ++u) {
-        const int e = tid + 256 * u, r = e / 64, j = e % 64;
-        const int64_t i = i0 + r;
-        float2 acc = make_float2(0.f, 0.f);
+    for (int ra = 0; ra < 2; ++ra) acc[ra][0] = acc[ra][1] = make_float2(0.f, 0.f);
 #pragma unroll 8
-        for (int k = 0; k < 64; ++k) {
-            const float2 a = A[r][k], d = D[j][k];  // a * conj(d)
-            acc.x = fmaf(a.x, d.x, fmaf(a.y, d.y, acc.x));
-            acc.y = fmaf(a.y, d.x, fmaf(-a.x, d.y, acc.y));
-        }
-        if (i < N && j < nbk) {
-            G[i * ldg + k0 + j] = make_double2((double)acc.x, (double)acc.y);
-            P[i * ldp + j] = acc;
+    for (int k = 0; k < 64; ++k) {
+        const float2 a0 = A[w][k], a1 = A[w + 8][k], d0 = Dt[k][lane], d1 = Dt[k][lane + 32];
+        cmac_conj(acc[0][0], a0, d0);
+        cmac_conj(acc[0][1], a0, d1);
+        cmac_conj(acc[1][0], a1, d0);
+        cmac_conj(acc[1][1], a1, d1);
+    }
+#pragma unroll
+    for (int ra = 0; ra < 2; ++ra) {
+        const int64_t i = i0 + w + 8 * ra;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int j = lane + 32 * b;
+            if (i < N && j < nbk) {
+                G[i * ldg + k0 + j] = make_double2((double)acc[ra][b].x, (double)acc[ra][b].y);
+                P[i * ldp + j] = acc[ra][b];
+            }
         }
     }
 }
 
-// G[i][j] -= sum_k P[i][k] conj(P[j][k]) for t0 <= j < jmax, j <= i (K = nbk <= 64)
+// G[i][j] -= sum_k P[i][k] conj(P[j][k]) for t0 <= j < jmax, j <= i (K = nbk <= 64;
+// jmax - t0 <= 32 CB). Dynamic shared memory: herk_panel_smem(CB).
+constexpr size_t herk_panel_smem(int cb) { return sizeof(float2) * (PNL_ROWS * 64 + 64 * (32 * cb + 1)); }
+template <int CB>
 __global__ void __launch_bounds__(256) k_herk_panel(const float2* __restrict__ P, int64_t ldp, double2* G,
                                                   int64_t ldg, int nbk, int64_t t0, int64_t jmax, int64_t N) {
+    constexpr int WP = 32 * CB + 1;  // padded row of Bt: transposed stores spread over the banks
     extern __shared__ float2 pnl_smem[];
-    float2(*Ai)[65] = reinterpret_cast<float2(*)[65]>(pnl_smem);
-    float2(*Bj)[65] = reinterpret_cast<float2(*)[65]>(pnl_smem + PNL_ROWS_HERK * 65);
-    const int tid = threadIdx.x;
+    float2(*Ai)[64] = reinterpret_cast<float2(*)[64]>(pnl_smem);
+    float2(*Bt)[WP] = reinterpret_cast<float2(*)[WP]>(pnl_smem + PNL_ROWS * 64);  // Bt[k][c] = P[t0 + c][k]
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int W = (int)(jmax - t0);
-    const int64_t i0 = t0 + (int64_t)blockIdx.x * PNL_ROWS_HERK;
-    for (int e = tid; e < PNL_ROWS_HERK * 64; e += 256) {
-        const int r = e / 64, k = e % 64;
-        const int64_t i = i0 + r;
-        Ai[r][k] = (i < N && k < nbk) ? P[i * ldp + k] : make_float2(0.f, 0.f);
+    const int64_t i0 = t0 + (int64_t)blockIdx.x * PNL_ROWS;
+    {
+        float2 u[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int e = tid + 256 * t, r = e / 64, k = e % 64;
+            const int64_t i = i0 + r;
+            u[t] = (i < N && k < nbk) ? P[i * ldp + k] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int e = tid + 256 * t;
+            Ai[e / 64][e % 64] = u[t];
+        }
     }
-    for (int e = tid; e < W * 64; e += 256) {
-        const int c = e / 64, k = e % 64;
-        const int64_t j = t0 + c;
-        Bj[c][k] = (j < N && k < nbk) ? P[j * ldp + k] : make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int t0b = 0; t0b < 8 * CB; t0b += 16) {  // 8 CB loads per thread, 16 at a time
+        float2 v[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int e = tid + 256 * (t0b + t), c = e / 64, k = e % 64;
+            const int64_t j = t0 + c;
+            v[t] = (t0b + t < 8 * CB && c < W && j < N && k < nbk) ? P[j * ldp + k] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int e = tid + 256 * (t0b + t);
+            if (t0b + t < 8 * CB) Bt[e % 64][e / 64] = v[t];
+        }
     }
     __syncthreads();
-    for (int e = tid; e < PNL_ROWS_HERK * W; e += 256) {
-        const int r = e / W, c = e % W;
-        const int64_t i = i0 + r, j = t0 + c;
-        if (i >= N || j > i) continue;
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 8
-        for (int k = 0; k < 64; ++k) {
-            const float2 a = Ai[r][k], b = Bj[c][k];  // a * conj(b)
-            acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
-            acc.y = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc.y));
+    float2 acc[2][CB];
+#pragma unroll
+    for (int b = 0; b < CB; ++b) acc[0][b] = acc[1][b] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int k = 0; k < 64; ++k) {
+        const float2 a0 = Ai[w][k], a1 = Ai[w + 8][k];
+#pragma unroll
+        for (int b = 0; b < CB; ++b) {
+            const float2 bv = Bt[k][lane + 32 * b];
+            cmac_conj(acc[0][b], a0, bv);
+            cmac_conj(acc[1][b], a1, bv);
         }
-        double2 g = G[i * ldg + j];
-        G[i * ldg + j] = make_double2(g.x - (double)acc.x, g.y - (double)acc.y);
     }
+#pragma unroll
+    for (int ra = 0; ra < 2; ++ra) {
+        const int64_t i = i0 + w + 8 * ra;
+#pragma unroll
+        for (int b = 0; b < CB; ++b) {
+            const int c = lane + 32 * b;
+            const int64_t j = t0 + c;
+            if (i < N && c < W && j <= i) {
+                const double2 g = G[i * ldg + j];
+                G[i * ldg + j] = make_double2(g.x - (double)acc[ra][b].x, g.y - (double)acc[ra][b].y);
+            }
+        }
+    }
+}
+
+template <int CB>
+static cudaError_t launch_herk_panel(const float2* P, int64_t ldp, double2* G, int64_t ldg, int nbk, int64_t t0,
+                                     int64_t jmax, int64_t N, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_herk_panel<CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)herk_panel_smem(CB));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int64_t rows = N - t0;
+    k_herk_panel<CB><<<(unsigned)((rows + PNL_ROWS - 1) / PNL_ROWS), 256, herk_panel_smem(CB), s>>>(P, ldp, G, ldg,
+                                                                                                  nbk, t0, jmax, N);
+    note_launch();
+    return cudaGetLastError();
 }
 
 // Panel table (B tiles of conj(L), rows from r0, kw panel columns from p0)
@@ -1095,24 +1181,17 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
             const int64_t rest = N - k0 - nbk;
             if (rest <= 0) break;
             // panel solve of every row below the block
-            k_trsm_panel<<<cdiv(rest, PNL_ROWS_TRSM), 256, 0, s>>>(L32 + k0, N, Dinv32 + kb * NBK * NBK, G, ld, k0,
-                                                                   (int)nbk, k0 + nbk, N);
+            k_trsm_panel<<<cdiv(rest, PNL_ROWS), 256, 0, s>>>(L32 + k0, N, Dinv32 + kb * NBK * NBK, G, ld, k0,
+                                                              (int)nbk, k0 + nbk, N);
             note_launch();
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             const int64_t t0 = k0 + nbk;
             if (t0 < pend) {  // the panel's remaining columns, all rows below
-                const size_t smem = sizeof(float2) * 65 * (PNL_ROWS_HERK + PNL_MAXW);
-                static bool attr = false;
-                if (!attr) {
-                    if ((e = cudaFuncSetAttribute(k_herk_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)smem)) != cudaSuccess)
-                        return e;
-                    attr = true;
-                }
-                k_herk_panel<<<cdiv(N - t0, PNL_ROWS_HERK), 256, smem, s>>>(L32 + k0, N, G, ld, (int)nbk, t0, pend,
-                                                                           N);
-                note_launch();
-                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                const int64_t w = pend - t0;  // <= 192
+                e = w <= 64    ? launch_herk_panel<2>(L32 + k0, N, G, ld, (int)nbk, t0, pend, N, s)
+                    : w <= 128 ? launch_herk_panel<4>(L32 + k0, N, G, ld, (int)nbk, t0, pend, N, s)
+                               : launch_herk_panel<6>(L32 + k0, N, G, ld, (int)nbk, t0, pend, N, s);
+                if (e != cudaSuccess) return e;
             }
         }
         if (ev_panel) {
