@@ -10,7 +10,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -54,9 +56,9 @@ pinv_status build_begin(pinv_plan* p, cudaStream_t s) {
     pinv_status rs = reset_status(p, s);
     if (rs != PINV_OK) return rs;
     if (p->lean) {  // stream-ordered temporaries, released by build_end
-        CK(cudaMallocAsync((void**)&p->G, sizeof(double2) * p->N * p->N, s));
-        if (p->lean_w()) CK(cudaMallocAsync((void**)&p->W, sizeof(double2) * p->N * p->N, s));
-        if (p->lean_gx()) CK(cudaMallocAsync((void**)&p->Gx, sizeof(float4) * p->N * p->N, s));
+        CK(work_alloc((void**)&p->G, sizeof(double2) * p->N * p->N, s));
+        if (p->lean_w()) CK(work_alloc((void**)&p->W, sizeof(double2) * p->N * p->N, s));
+        if (p->lean_gx()) CK(work_alloc((void**)&p->Gx, sizeof(float4) * p->N * p->N, s));
     }
     if (p->keep_gram && !p->Gkeep) {
         pinv_status st = p->alloc((void**)&p->Gkeep, sizeof(double2) * p->N * p->N, "Gkeep");
@@ -77,7 +79,7 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
             void* work = nullptr;
             const char* env = std::getenv("PINV_GRAM_BULK");
             const bool bulk = !(env && std::strcmp(env, "0") == 0);
-            if (bulk && cudaMallocAsync(&work, gram_bulk_bytes(p->enc, p->slices()), s) == cudaSuccess) {
+            if (bulk && work_alloc(&work, gram_bulk_bytes(p->enc, p->slices()), s) == cudaSuccess) {
                 CK(launch_gram_bulk(p->enc, p->lambda_abs, p->slices(), p->G, ld, work, p->st, s));
                 CK(cudaFreeAsync(work, s));
             } else {
@@ -99,7 +101,7 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
             sx = p->s_inv;
         }
         double2* work = nullptr;
-        CK(cudaMallocAsync((void**)&work, toeplitz_work_bytes(p->enc), sx));
+        CK(work_alloc((void**)&work, toeplitz_work_bytes(p->enc), sx));
         CK(launch_toeplitz64(p->enc, work, p->Ttab, sx));
         CK(cudaFreeAsync(work, sx));
         CK(launch_gram_exact(p->enc, p->Ttab, p->lambda_abs, p->Gx, sx));
@@ -109,6 +111,46 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
     return PINV_OK;
 }
 
+// ------------------------------------------------------------------ build temporaries
+// Builds allocate several GB of stream-ordered temporaries (operand tables, the
+// FP32 factor). They come from one pool per device that keeps its memory between
+// builds, so a build does not map it again; the pool is trimmed when the last
+// plan is destroyed. (The device's default pool returns its memory at every
+// synchronisation.)
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+std::atomic<int> g_live_plans{0};
+cudaMemPool_t build_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
+}  // namespace
+
+cudaError_t work_alloc(void** ptr, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool = build_pool();
+    return pool ? cudaMallocFromPoolAsync(ptr, bytes, pool, s) : cudaMallocAsync(ptr, bytes, s);
+}
+
 pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events) {
     const int64_t N = p->N, ld = p->N;
     if (p->precision != PINV_FP64) {
@@ -116,14 +158,14 @@ pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events) {
         // then the triangular inverse W = L^-1 on tensor cores
         const int64_t nblk = (N + 63) / 64;
         float2 *L32 = nullptr, *D32 = nullptr;
-        CK(cudaMallocAsync((void**)&L32, sizeof(float2) * N * N, s));
-        CK(cudaMallocAsync((void**)&D32, sizeof(float2) * nblk * 64 * 64, s));
+        CK(work_alloc((void**)&L32, sizeof(float2) * N * N, s));
+        CK(work_alloc((void**)&D32, sizeof(float2) * nblk * 64 * 64, s));
         // operand tables of the bulk-fed panel updates, one region per stream
         // (PINV_CHOL_BULK=0: generated operands)
         void* tab = nullptr;
         const size_t tb = factor_table_bytes(N, p->slices());
         const char* env = std::getenv("PINV_CHOL_BULK");
-        if (!(env && std::strcmp(env, "0") == 0) && cudaMallocAsync(&tab, 2 * tb, s) != cudaSuccess) {
+        if (!(env && std::strcmp(env, "0") == 0) && work_alloc(&tab, 2 * tb, s) != cudaSuccess) {
             cudaGetLastError();
             tab = nullptr;
         }
@@ -158,7 +200,7 @@ pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events) {
         CK(launch_pivot_stats(p->G, N, ld, p->st, s));
         if (events) CK(cudaEventRecord(p->ev[3], s));
         double2* W = nullptr;
-        CK(cudaMallocAsync((void**)&W, sizeof(double2) * N * N, s));
+        CK(work_alloc((void**)&W, sizeof(double2) * N * N, s));
         CK(launch_trtri64(p->G, N, ld, p->Dinv, W, s));
         CK(launch_lauum64(W, N, ld, p->Ginv, s));
         CK(cudaFreeAsync(W, s));
@@ -176,14 +218,14 @@ pinv_status build_recon(pinv_plan* p, cudaStream_t s) {
         void* work = nullptr;
         const char* env = std::getenv("PINV_RECON_BULK");
         const bool bulk = !(env && std::strcmp(env, "0") == 0);
-        if (bulk && cudaMallocAsync(&work, recon_bulk_bytes(p->enc, p->slices()), s) == cudaSuccess) {
+        if (bulk && work_alloc(&work, recon_bulk_bytes(p->enc, p->slices()), s) == cudaSuccess) {
             CK(launch_recon_bulk(p->enc, p->W32, p->slices(), (float2*)p->R, work, p->st, s));
             CK(cudaFreeAsync(work, s));
         } else {
             cudaGetLastError();
             float2 *T = nullptr, *WT32 = nullptr;
-            CK(cudaMallocAsync((void**)&T, sizeof(float2) * N * p->M, s));
-            CK(cudaMallocAsync((void**)&WT32, sizeof(float2) * N * N, s));
+            CK(work_alloc((void**)&T, sizeof(float2) * N * p->M, s));
+            CK(work_alloc((void**)&WT32, sizeof(float2) * N * N, s));
             CK(launch_transpose32(p->W32, N, N, WT32, N, s));
             CK(launch_recon_tc(p->enc, p->W32, WT32, T, p->slices(), (float2*)p->R, p->st, s));
             CK(cudaFreeAsync(WT32, s));
@@ -507,6 +549,7 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
 #undef AL
 #undef CKC
     *out = p;
+    ++g_live_plans;
     return PINV_OK;
 }
 
@@ -652,6 +695,10 @@ void pinv_plan_destroy(pinv_plan* p) {
     if (!p) return;
     cudaDeviceSynchronize();
     delete p;
+    if (--g_live_plans == 0) {
+        cudaMemPool_t pool = build_pool();
+        if (pool) cudaMemPoolTrimTo(pool, 0);
+    }
 }
 
 }  // extern "C"

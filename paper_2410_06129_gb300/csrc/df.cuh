@@ -49,6 +49,18 @@ __device__ inline float2 split_f64(double x) {
     fast_two_sum(h, l, sh, sl);
     return make_float2(sh, sl);
 }
+// (float)x, round to nearest even, on the integer pipe (the FP64 conversion for
+// zero, results outside the normal float range, infinity and NaN)
+__device__ inline float f64_to_f32_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ffu);
+    const int fe = ex - 1023 + 127;
+    if (ex == 0 || ex == 0x7ff || fe <= 0 || fe >= 255) return (float)x;
+    const unsigned m = (unsigned)((b >> 29) & 0x7fffffu), rem = (unsigned)(b & 0x1fffffffu);
+    unsigned u = ((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)fe << 23) | m;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ++u;  // a carry moves into the exponent
+    return __uint_as_float(u);
+}
 // (hi, lo) -> double within one unit in the last place: hi exactly, plus lo
 // rounded to hi's grid (units of 2^-52 |hi|, twice as fine below a power of two).
 __device__ inline double join_f64(float h, float l) {

@@ -351,9 +351,11 @@ __device__ inline float2 df_rsqrt(float dh, float dl) {
 // Two barriers per column. Rows are NBDP = 65 entries apart, so row and column
 // reads are free of bank conflicts. Values enter and leave through integer and
 // FP32 conversions: on GB300 the FP64 pipe of the one SM would take longer.
-// Dinv may be null (the FP32 inverse alone).
+// Dinv may be null (the FP32 inverse alone); L32 (or null) receives the block of L
+// rounded to FP32, as (float) of the FP64 value written to G.
 __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0,
-                                                             double2* Dinv, float2* Dinv32, DevStatus* st) {
+                                                             double2* Dinv, float2* Dinv32, float2* L32,
+                                                             int64_t ldl, DevStatus* st) {
     extern __shared__ float4 smd[];
     float4* A = smd;               // [NBD][NBDP]
     float4* X = smd + NBD * NBDP;  // [NBD][NBDP] inverse
@@ -430,13 +432,17 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
         if (Dinv32) Dinv32[e] = make_float2(x.x + x.y, x.z + x.w);
         if (i < nb && j < nb && j <= i) {
             const float4 a = A[i * NBDP + j];
-            G[(k0 + i) * ld + k0 + j] = make_double2(join_f64(a.x, a.y), join_f64(a.z, a.w));
+            const double2 g = make_double2(join_f64(a.x, a.y), join_f64(a.z, a.w));
+            G[(k0 + i) * ld + k0 + j] = g;
+            if (L32) L32[(k0 + i) * ldl + k0 + j] = make_float2(f64_to_f32_rn(g.x), f64_to_f32_rn(g.y));
+        } else if (L32 && i < nb && j < nb) {
+            L32[(k0 + i) * ldl + k0 + j] = make_float2(0.f, 0.f);
         }
     }
 }
 
 cudaError_t launch_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv, float2* Dinv32,
-                                 DevStatus* st, cudaStream_t s) {
+                                 float2* L32, int64_t ldl, DevStatus* st, cudaStream_t s) {
     static bool attr = false;
     const size_t smem = 2 * NBD * NBDP * sizeof(float4);
     if (!attr) {
@@ -445,7 +451,7 @@ cudaError_t launch_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0, 
         if (err != cudaSuccess) return err;
         attr = true;
     }
-    k_potrf_diag_df<<<1, DIAG_THREADS, smem, s>>>(G, ld, N, k0, Dinv, Dinv32, st);
+    k_potrf_diag_df<<<1, DIAG_THREADS, smem, s>>>(G, ld, N, k0, Dinv, Dinv32, L32, ldl, st);
     note_launch();
     return cudaGetLastError();
 }

@@ -595,27 +595,27 @@ extern "C" pinv_status pinv_tsvd_apply(pinv_plan* p, const double* d_mu, const v
             return eig_err(e_, #call);                   \
         }                                                \
     } while (0)
-    CKT(cudaMallocAsync((void**)&w, sizeof(double) * N, s));
-    CKT(cudaMallocAsync((void**)&dev_rank, sizeof(int), s));
-    CKT(cudaMallocAsync((void**)&dev_kappa, sizeof(double), s));
+    CKT(work_alloc((void**)&w, sizeof(double) * N, s));
+    CKT(work_alloc((void**)&dev_rank, sizeof(int), s));
+    CKT(work_alloc((void**)&dev_kappa, sizeof(double), s));
     k_tsvd_rank<<<1, 256, 0, s>>>(d_mu, (int)N, energy, lam, dev_rank, dev_kappa, w);
     note_launch();
     CKT(cudaGetLastError());
     if (F > 0) {
         const double2* Dd = (const double2*)d_data;
         if (dtype == PINV_C64) {
-            CKT(cudaMallocAsync((void**)&D, sizeof(double2) * F * M, s));
+            CKT(work_alloc((void**)&D, sizeof(double2) * F * M, s));
             CKT(launch_c64_to_c128((const float2*)d_data, D, F * M, s));
             Dd = D;
         }
         double2* Xd = (double2*)d_image;
         if (dtype == PINV_C64) {
-            CKT(cudaMallocAsync((void**)&X, sizeof(double2) * F * N, s));
+            CKT(work_alloc((void**)&X, sizeof(double2) * F * N, s));
             Xd = X;
         }
-        CKT(cudaMallocAsync((void**)&b, sizeof(double2) * F * N, s));
-        CKT(cudaMallocAsync((void**)&c, sizeof(double2) * F * N, s));
-        CKT(cudaMallocAsync((void**)&Ph, sizeof(double2) * N * N, s));
+        CKT(work_alloc((void**)&b, sizeof(double2) * F * N, s));
+        CKT(work_alloc((void**)&c, sizeof(double2) * F * N, s));
+        CKT(work_alloc((void**)&Ph, sizeof(double2) * N * N, s));
         CKT(launch_adjoint64(p->enc, Dd, F, 0.0, nullptr, b, s));  // b = E^H d
         k_conj_transpose<<<blocks(N * N), 256, 0, s>>>((const double2*)d_P, (int)N, Ph);  // Ph = P^H
         note_launch();

@@ -92,7 +92,7 @@ extern "C" pinv_status pinv_plan_map(pinv_plan* p, int what, const double* psi, 
     if (what == PINV_MAP_NOISE && psi) {
         if (!p->recon) return set_error(PINV_ERR_UNSUPPORTED, "a coil-covariance noise map needs the stored Recon");
         double2* dpsi = nullptr;
-        CKM(cudaMallocAsync((void**)&dpsi, sizeof(double2) * p->C * p->C, s));
+        CKM(work_alloc((void**)&dpsi, sizeof(double2) * p->C * p->C, s));
         CKM(cudaMemcpyAsync(dpsi, psi, sizeof(double2) * p->C * p->C, cudaMemcpyHostToDevice, s));
         if (p->precision == PINV_FP64)
             k_noise_recon<<<(unsigned)N, 256, 0, s>>>((const double2*)p->R, N, p->Mk, p->C, dpsi, d_out);
@@ -127,7 +127,7 @@ extern "C" pinv_status pinv_plan_map(pinv_plan* p, int what, const double* psi, 
         if (e_ != cudaSuccess) return fail_free(e_, #call);   \
     } while (0)
     if (!Y) {
-        CKF(cudaMallocAsync((void**)&Yown, sizeof(double2) * N * N, s));
+        CKF(work_alloc((void**)&Yown, sizeof(double2) * N * N, s));
         CKF(launch_lauum64(p->W, N, N, Yown, s));  // W^H W in FP64
         Y = Yown;
         if (p->Gx && p->refine_iters > 0) {
@@ -136,10 +136,10 @@ extern "C" pinv_status pinv_plan_map(pinv_plan* p, int what, const double* psi, 
             k_conj<<<(unsigned)((N * N + 255) / 256), 256, 0, s>>>(Y, N * N);
             note_launch();
             const size_t wel = df_work_elems(N, N, N);
-            CKF(cudaMallocAsync((void**)&B, sizeof(double2) * N * N, s));
-            CKF(cudaMallocAsync((void**)&R, sizeof(double2) * N * N, s));
-            CKF(cudaMallocAsync((void**)&T, sizeof(float2) * N * N, s));
-            if (wel) CKF(cudaMallocAsync((void**)&work, sizeof(float4) * wel, s));
+            CKF(work_alloc((void**)&B, sizeof(double2) * N * N, s));
+            CKF(work_alloc((void**)&R, sizeof(double2) * N * N, s));
+            CKF(work_alloc((void**)&T, sizeof(float2) * N * N, s));
+            if (wel) CKF(work_alloc((void**)&work, sizeof(float4) * wel, s));
             CKF(launch_fill_identity(B, N, N, s));
             for (int it = 0; it < p->refine_iters; ++it) {
                 CKF(launch_gram_resid_df(p->Gx, N, B, Y, N, R, s, work));
@@ -148,7 +148,7 @@ extern "C" pinv_status pinv_plan_map(pinv_plan* p, int what, const double* psi, 
         }
     }
     if (what == PINV_MAP_NOISE) {
-        CKF(cudaMallocAsync((void**)&norm2, sizeof(double) * N, s));
+        CKF(work_alloc((void**)&norm2, sizeof(double) * N, s));
         CKF(launch_frame_norms(Y, N, N, norm2, s));  // squared norms of the columns of G^-1
     }
     k_map_from_ginv<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Y, N, norm2, p->lambda_abs,

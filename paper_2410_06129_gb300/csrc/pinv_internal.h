@@ -140,8 +140,13 @@ cudaError_t launch_lauum64(const double2* W, int64_t N, int64_t ld, double2* Gin
 using TuneRun = std::function<cudaError_t(int)>;
 int tune_pick(const char* family, int64_t rows, int64_t F, int ncand, const TuneRun& run, cudaStream_t s);
 
+// Stream-ordered allocation of build and query temporaries from the library's
+// per-device pool, which keeps its memory between builds (free with cudaFreeAsync).
+cudaError_t work_alloc(void** ptr, size_t bytes, cudaStream_t s);
+
 // mixed path: the same diagonal block in double-float on the FP32 units
 cudaError_t launch_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv, float2* Dinv32,
+                                 float2* L32, int64_t ldl,
                                  DevStatus* st, cudaStream_t s);
 cudaError_t launch_potrf_diag(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv,
                               float2* Dinv32, DevStatus* st, cudaStream_t s);

@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <vector>
 
+#include "df.cuh"
 #include "tc_engine.cuh"
 
 namespace pinv {
@@ -855,26 +856,6 @@ struct ReconStep2TC {
 
 }  // namespace tc
 
-// FP32 copy of a block of an FP64 matrix: dst[r][c] = src[r][c] for r in [r0, r1), c in [c0, c1)
-__global__ void k_block_to_f32(const double2* __restrict__ src, int64_t ld, int64_t r0, int64_t r1, int64_t c0,
-                               int64_t c1, float2* __restrict__ dst, int64_t ldd) {
-    const int64_t w = c1 - c0;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (r1 - r0) * w) return;
-    const int64_t r = r0 + idx / w, c = c0 + idx % w;
-    const double2 v = src[r * ld + c];
-    dst[r * ldd + c] = make_float2((float)v.x, (float)v.y);
-}
-
-static cudaError_t block_to_f32(const double2* src, int64_t ld, int64_t r0, int64_t r1, int64_t c0, int64_t c1,
-                                float2* dst, int64_t ldd, cudaStream_t s) {
-    const int64_t n = (r1 - r0) * (c1 - c0);
-    if (n <= 0) return cudaSuccess;
-    k_block_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, ld, r0, r1, c0, c1, dst, ldd);
-    note_launch();
-    return cudaGetLastError();
-}
-
 template <class P>
 static cudaError_t run(const P& p, dim3 grid, int slices, DevStatus* st, int site, cudaStream_t s,
                        bool rev = false, int cap = 0) {
@@ -995,8 +976,8 @@ __device__ inline void cmac_conj(float2& acc, float2 a, float2 b) {  // acc += a
     acc.y = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc.y));
 }
 
-// L[i][k0 + j] = sum_k P[i][k] conj(Dinv[j][k]) for rows i >= row0: written to G
-// (FP64) and back over P (FP32), in place (each CTA reads its rows first)
+// L[i][k0 + j] = sum_k A[i][k] conj(Dinv[j][k]) for rows i >= row0, A[i][k] the
+// FP32 rounding of G[i][k0 + k]: written to G (FP64) and to P (FP32)
 __global__ void __launch_bounds__(256) k_trsm_panel(float2* P, int64_t ldp, const float2* __restrict__ Dinv32,
                                                   double2* G, int64_t ldg, int64_t k0, int nbk, int64_t row0,
                                                   int64_t N) {
@@ -1015,7 +996,12 @@ __global__ void __launch_bounds__(256) k_trsm_panel(float2* P, int64_t ldp, cons
         for (int t = 0; t < 4; ++t) {
             const int e = tid + 256 * t, r = e / 64, k = e % 64;
             const int64_t i = i0 + r;
-            u[t] = (i < N && k < nbk) ? P[i * ldp + k] : make_float2(0.f, 0.f);
+            if (i < N && k < nbk) {
+                const double2 g = G[i * ldg + k0 + k];
+                u[t] = make_float2(f64_to_f32_rn(g.x), f64_to_f32_rn(g.y));
+            } else {
+                u[t] = make_float2(0.f, 0.f);
+            }
         }
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
@@ -1172,11 +1158,11 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
         for (int64_t k0 = p0; k0 < pend; k0 += NBK) {
             const int64_t nbk = std::min<int64_t>(NBK, N - k0);
             const int64_t kb = k0 / NBK;
+            // the diagonal block writes its FP32 copy to L32; the solve below reads
+            // its right-hand sides from G
             cudaError_t e =
                 launch_potrf_diag_df(G, ld, N, k0, Dinv ? Dinv + kb * NBK * NBK : nullptr,
-                                     Dinv32 + kb * NBK * NBK, st, s);
-            if (e != cudaSuccess) return e;
-            e = block_to_f32(G, ld, k0, N, k0, k0 + nbk, L32, N, s);
+                                     Dinv32 + kb * NBK * NBK, L32, N, st, s);
             if (e != cudaSuccess) return e;
             const int64_t rest = N - k0 - nbk;
             if (rest <= 0) break;
