@@ -61,6 +61,28 @@ __device__ inline float f64_to_f32_rn(double x) {
     if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ++u;  // a carry moves into the exponent
     return __uint_as_float(u);
 }
+// to_df on the integer pipe, bit for bit: hi = (float)x, lo = (float)(x - hi)
+// (the FP64 conversion where lo or hi would leave the normal float range)
+__device__ inline float2 f64_to_df_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ffu);
+    const int fe = ex - 1023 + 127;
+    if (ex == 0 || ex == 0x7ff || fe <= 52 || fe >= 254) {
+        const float h = (float)x;
+        return make_float2(h, (float)(x - (double)h));
+    }
+    const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+    const unsigned m = (unsigned)((b >> 29) & 0x7fffffu), rem = (unsigned)(b & 0x1fffffffu);
+    const bool up = rem > 0x10000000u || (rem == 0x10000000u && (m & 1u));
+    const unsigned u = (sgn | ((unsigned)fe << 23) | m) + (up ? 1u : 0u);
+    const int d = up ? (int)rem - (1 << 29) : (int)rem;  // |x| - |hi| in units of 2^(E - 52)
+    const float l = (float)(sgn ? -d : d) * __uint_as_float((unsigned)(fe - 52) << 23);
+    return make_float2(__uint_as_float(u), l);
+}
+__device__ inline float4 to_df_i(double2 v) {
+    const float2 r = f64_to_df_rn(v.x), i = f64_to_df_rn(v.y);
+    return make_float4(r.x, r.y, i.x, i.y);
+}
 // (hi, lo) -> double within one unit in the last place: hi exactly, plus lo
 // rounded to hi's grid (units of 2^-52 |hi|, twice as fine below a power of two).
 __device__ inline double join_f64(float h, float l) {

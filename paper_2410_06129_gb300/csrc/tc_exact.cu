@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_b_digits(const double2* D, int64_t ld, 
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         const int64_t m = mk0 + t;
-        const float4 v = to_df((f < F && m < Kc) ? D[f * ld + (int64_t)c * Kc + m] : make_double2(0.0, 0.0));
+        const float4 v = to_df_i((f < F && m < Kc) ? D[f * ld + (int64_t)c * Kc + m] : make_double2(0.0, 0.0));
         reh[t] = v.x;
         rel[t] = v.y;
         imh[t] = v.z;
@@ -534,25 +534,43 @@ __global__ void k_gram_digits(const float4* G, int64_t N, int64_t KB, const int*
 }
 
 // per-frame exponent: |re|, |im| of frame f all <= 2^fexp[f]
-__global__ void k_frame_exp(const double2* D, int64_t M, int* fexp) {
-    __shared__ double red[256];
+// fexp[f] = the least e with max_j |D[f][j]| <= 2^e (0 for a zero frame). The
+// maximum is taken over the bit patterns with the sign cleared, whose order is the
+// order of the magnitudes (NaN and infinity left out), on the integer pipe.
+__device__ inline unsigned long long mag_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    return (b >> 52) == 0x7ffull ? 0ull : b;
+}
+__global__ void __launch_bounds__(256) k_frame_exp(const double2* D, int64_t M, int* fexp) {
+    __shared__ unsigned long long red[256];
     const int64_t f = blockIdx.x;
-    double m = 0.0;
-    for (int64_t j = threadIdx.x; j < M; j += blockDim.x) {
-        const double2 v = D[f * M + j];
-        m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    unsigned long long m = 0ull;
+    const double2* row = D + f * M;
+    int64_t j = threadIdx.x;
+    for (; j + 768 < M; j += 1024) {  // four loads in flight
+        const double2 a = row[j], b = row[j + 256], c = row[j + 512], d = row[j + 768];
+        m = max(m, max(max(mag_bits(a.x), mag_bits(a.y)), max(mag_bits(b.x), mag_bits(b.y))));
+        m = max(m, max(max(mag_bits(c.x), mag_bits(c.y)), max(mag_bits(d.x), mag_bits(d.y))));
     }
+    for (; j < M; j += 256) m = max(m, max(mag_bits(row[j].x), mag_bits(row[j].y)));
     red[threadIdx.x] = m;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        if ((int)threadIdx.x < w) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + w]);
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        int ex = 0;
-        const double mant = m > 0.0 ? frexp(red[0], &ex) : 0.0;
-        if (mant == 0.5) --ex;  // exact powers of two need no extra bit
-        fexp[f] = m > 0.0 ? ex : 0;
+        const unsigned long long B = red[0];
+        const int eb = (int)(B >> 52);
+        const unsigned long long mf = B & ((1ull << 52) - 1ull);
+        int e = 0;
+        if (B == 0ull)
+            e = 0;
+        else if (eb == 0)  // subnormal: B = mf 2^-1074
+            e = (64 - __clzll((long long)mf)) - 1074 - ((mf & (mf - 1ull)) == 0ull ? 1 : 0);
+        else  // (1 + mf 2^-52) 2^(eb - 1023): one more bit unless a power of two
+            e = eb - 1023 + (mf != 0ull ? 1 : 0);
+        fexp[f] = e;
     }
 }
 
