@@ -1208,12 +1208,14 @@ cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, 
                             int slices, DevStatus* st, cudaStream_t s, void* tab, const cudaEvent_t* ev_panel) {
     cudaError_t e = launch_fill_identity(W, N, N, s);
     if (e != cudaSuccess) return e;
-    // the inverse runs beside the Cholesky chain: its persistent launches take at
-    // most half the SMs (PINV_INV_SMS: another count, 0 all), so that the chain's
-    // launches find free SMs; at 64x64 this takes the Cholesky from 10.7 to 10.4 ms
-    // and the inverse still ends with it
+    // the inverse runs beside the Cholesky chain. Up to N = 16384, where the chain
+    // is a latency-bound sequence of small launches, the inverse's persistent
+    // launches take at most half the SMs so that the chain's launches find free
+    // SMs (at 64x64 the Cholesky goes from 10.7 to 10.4 ms and the inverse still
+    // ends with it); above, both are throughput-bound and the inverse takes them
+    // all. PINV_INV_SMS: another count (0 all).
     const char* cenv = std::getenv("PINV_INV_SMS");
-    const int cap = cenv ? std::atoi(cenv) : std::max(1, tc::sm_count() / 2);
+    const int cap = cenv ? std::atoi(cenv) : (N <= 16384 ? std::max(1, tc::sm_count() / 2) : 0);
     for (int64_t p0 = 0; p0 < N; p0 += NBP) {
         const int64_t pend = std::min<int64_t>(N, p0 + NBP);
         if (ev_panel && (e = cudaStreamWaitEvent(s, ev_panel[p0 / NBP], 0)) != cudaSuccess) return e;
