@@ -240,17 +240,21 @@ extern "C" pinv_status pinv_apply(pinv_plan* p, const void* d_data, void* d_imag
     if (st != PINV_OK || F == 0) return st;
     const size_t need = apply_scratch_layout(p, F, dtype, nullptr, nullptr);
     if (need > p->scratch_bytes) {
-        // grow the plan-owned scratch (stream-ordered with this apply)
+        // grow the plan-owned scratch, from the library's pool: the old region after
+        // every earlier apply (on any stream) is done, the new one complete before
+        // any stream uses it
         if (p->scratch_buf) {
-            cudaError_t e = cudaFree(p->scratch_buf);
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e == cudaSuccess) e = cudaFreeAsync(p->scratch_buf, 0);
             p->scratch_buf = nullptr;
             p->scratch_bytes = 0;
-            if (e != cudaSuccess) return cuda_err(e, "cudaFree(apply scratch)");
+            if (e != cudaSuccess) return cuda_err(e, "free(apply scratch)");
         }
-        cudaError_t e = cudaMalloc(&p->scratch_buf, need);
+        cudaError_t e = work_alloc(&p->scratch_buf, need, 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(0);
         if (e != cudaSuccess) {
             p->scratch_buf = nullptr;
-            return cuda_err(e, "cudaMalloc(apply scratch)");
+            return cuda_err(e, "alloc(apply scratch)");
         }
         p->scratch_bytes = need;
     }

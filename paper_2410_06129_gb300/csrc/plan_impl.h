@@ -121,7 +121,9 @@ struct pinv_plan {
     // W^H W E^H d, then the same refinement). Returns the bytes released.
     size_t drop_recon() {
         if (!recon || !R) return 0;
-        cudaFree(R);
+        cudaDeviceSynchronize();  // applies on any stream may still read it
+        cudaFreeAsync(R, 0);
+        cudaStreamSynchronize(0);
         for (auto& a : allocs)
             if (a == R) a = nullptr;
         const size_t b = bytes_recon;
@@ -132,13 +134,17 @@ struct pinv_plan {
         return b;
     }
 
+    // Plan memory comes from the library's pool (kept between plans, so creating a
+    // plan again does not map GBs of memory again), ordered on the legacy stream and
+    // complete before this returns, so any stream may use it.
     pinv_status alloc(void** p, size_t n, const char* what) {
         if (n == 0) n = 16;
-        cudaError_t e = cudaMalloc(p, n);
+        cudaError_t e = pinv::work_alloc(p, n, 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(0);
         if (e != cudaSuccess) {
             *p = nullptr;
             return pinv::set_error(e == cudaErrorMemoryAllocation ? PINV_ERR_OOM : PINV_ERR_CUDA,
-                                   std::string("cudaMalloc(") + what + ", " + std::to_string(n) + " B): " +
+                                   std::string("alloc(") + what + ", " + std::to_string(n) + " B): " +
                                        cudaGetErrorString(e));
         }
         allocs.push_back(*p);
@@ -146,9 +152,11 @@ struct pinv_plan {
         return PINV_OK;
     }
     ~pinv_plan() {
-        if (scratch_buf) cudaFree(scratch_buf);
+        cudaDeviceSynchronize();  // nothing of this plan may still run
+        if (scratch_buf) cudaFreeAsync(scratch_buf, 0);
         for (void* p : allocs)
-            if (p) cudaFree(p);
+            if (p) cudaFreeAsync(p, 0);
+        cudaStreamSynchronize(0);
         if (st_host) cudaFreeHost(st_host);
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);

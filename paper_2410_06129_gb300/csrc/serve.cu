@@ -149,7 +149,7 @@ void pinv_server::finish(const Request& q, pinv_status st, std::unique_lock<std:
 }
 
 void pinv_server::evict(Registered& v) {
-    delete v.plan;  // no request of it is in flight (inflight == 0)
+    pinv_plan_destroy(v.plan);  // no request of it is in flight (inflight == 0)
     v.plan = nullptr;
     resident_bytes -= v.bytes;
     v.bytes = 0;
@@ -202,12 +202,12 @@ pinv_status pinv_server::make_resident(Registered& r, int id, bool* defer) {
     if (st != PINV_OK) return st;
     st = pinv_build(p, build_stream);
     if (st != PINV_OK) {
-        delete p;
+        pinv_plan_destroy(p);
         return st;
     }
     cudaError_t e = cudaEventRecord(r.ready, build_stream);
     if (e != cudaSuccess) {
-        delete p;
+        pinv_plan_destroy(p);
         return set_error(PINV_ERR_CUDA, cudaGetErrorString(e));
     }
     r.plan = p;
@@ -462,7 +462,7 @@ void pinv_server_destroy(pinv_server* sv) {
     cudaSetDevice(sv->device);
     cudaDeviceSynchronize();
     for (auto& p : sv->plans) {
-        delete p.plan;
+        pinv_plan_destroy(p.plan);
         if (p.ready) cudaEventDestroy(p.ready);
     }
     for (auto& s : sv->slots) {
