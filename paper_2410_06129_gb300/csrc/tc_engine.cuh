@@ -99,6 +99,13 @@ struct HintB : std::false_type {};
 template <class P>
 struct HintB<P, std::void_t<decltype(P::kHintB)>> : std::integral_constant<bool, P::kHintB> {};
 
+// ... a generating problem whose operands stream from HBM (kPrefetch) has its
+// producers load the next two stages into registers while splitting this one
+template <class P, class = void>
+struct Prefetch : std::false_type {};
+template <class P>
+struct Prefetch<P, std::void_t<decltype(P::kPrefetch)>> : std::integral_constant<bool, P::kPrefetch> {};
+
 constexpr int NTHREADS_BULK = NTHREADS + 32;  // + one loader warp
 
 // slice pairs in decreasing weight: (0,0) (0,1) (1,0) (0,2) (2,0) (1,1)
@@ -445,6 +452,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, in
             // per-thread operand contexts (row pointers, table rows) fixed for the tile
             const auto ra = p.row_a(i0 + (ua & (BM - 1)));
             const auto rb = p.row_b(j0 + ubr);
+            constexpr bool PF = Prefetch<typename Sched::Prob>::value;
+            float2 pa1[8], pb1[8], pa2[8], pb2[8];  // stages kt + 1, kt + 2 (kPrefetch)
+            if constexpr (PF) {
+                p.a8(ra, kb + 8 * (ua >> 7), ke, pa1);
+                p.b8(rb, kb + 8 * ubg, ke, pb1);
+                p.a8(ra, kb + KC + 8 * (ua >> 7), ke, pa2);
+                p.b8(rb, kb + KC + 8 * ubg, ke, pb2);
+            }
             for (int kt = 0; kt < nk && ok; ++kt) {
                 // the MMA cannot start group g + 1 until group g is drained; drain it
                 // before the ring can only advance past that point
@@ -459,10 +474,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, in
                 if (kg >= CF::STAGES && !(ok = mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag))) break;
                 uint8_t* base = smem + s * CF::STAGE_BYTES;
                 const int64_t k0 = kb + (int64_t)kt * KC;
+                float2 va[8], vb[8];
+                if constexpr (PF) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        va[u] = pa1[u];
+                        vb[u] = pb1[u];
+                        pa1[u] = pa2[u];
+                        pb1[u] = pb2[u];
+                    }
+                    p.a8(ra, k0 + 2 * KC + 8 * (ua >> 7), ke, pa2);  // zeros past ke
+                    p.b8(rb, k0 + 2 * KC + 8 * ubg, ke, pb2);
+                } else {
+                    p.a8(ra, k0 + 8 * (ua >> 7), ke, va);
+                    p.b8(rb, k0 + 8 * ubg, ke, vb);
+                }
                 {
-                    float2 v[8];
+                    const float2(&v)[8] = va;
                     const int r = ua & (BM - 1), g = ua >> 7;
-                    p.a8(ra, k0 + 8 * g, ke, v);
                     float re[8], im[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) { re[u] = v[u].x; im[u] = v[u].y; }
@@ -473,8 +502,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, in
                     store_slices<S>(base + koff(r, g + 2), wi, 0u);
                 }
                 {
-                    float2 v[8];
-                    p.b8(rb, k0 + 8 * ubg, ke, v);
+                    const float2(&v)[8] = vb;
                     float re[8], im[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) { re[u] = v[u].x; im[u] = v[u].y; }

@@ -1550,6 +1550,7 @@ namespace tc {
 // split over tile columns: column tile bx covers frames 0..BN-1 of split bx
 // (samples [bx * chunk, ...)), whose FP32 partials go to part[bx][f][n].
 struct ApplyTC {
+    static constexpr bool kPrefetch = true;  // Recon streams from HBM
     const float2* R;   // Recon [N][M], c64
     const float2* D;   // data [F][M], c64
     float2* part;      // [splits][F][N]
