@@ -813,6 +813,26 @@ __global__ void __launch_bounds__(NTHREADS_BULK, 1) k_tc_bulk(Sched sch, DevStat
 
 int sm_count();
 
+// How many parts to split a k range of `len` into, for launches that run `per_split`
+// tiles (one CTA each, one CTA per SM) per part: the count in [lo, hi] that minimises
+// waves x (len / parts + overhead), `overhead` standing for each tile's fill,
+// drain and epilogue in units of k; the fewest parts on a tie. Whole waves matter:
+// 320 tiles on 152 SMs take three waves, the third a tenth full.
+inline int wave_splits(int64_t per_split, int64_t len, int lo, int hi, int64_t overhead) {
+    const int64_t sms = sm_count();
+    int best = lo;
+    double bt = 0.0;
+    for (int sp = lo; sp <= hi; ++sp) {
+        const int64_t waves = (per_split * sp + sms - 1) / sms;
+        const double t = (double)waves * ((double)len / sp + (double)overhead);
+        if (sp == lo || t < bt * (1.0 - 1e-9)) {
+            bt = t;
+            best = sp;
+        }
+    }
+    return best;
+}
+
 template <class K, class... A>
 static cudaError_t launch_persistent(K kern, int threads, int smem, bool& attr, int64_t items, int cap,
                                      cudaStream_t s, const A&... args) {

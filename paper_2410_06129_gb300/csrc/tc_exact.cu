@@ -576,13 +576,12 @@ __global__ void __launch_bounds__(256) k_frame_exp(const double2* D, int64_t M, 
 
 }  // namespace tcx
 
-// splits per coil: about two CTAs per SM over all coils, chunks of at least
-// two accumulation groups
+// splits per coil: whole waves of CTAs over all coils, chunks of at least two
+// accumulation groups
 static int exact_sub(const EncodeDev& e, int64_t F) {
     const int64_t tiles = ((e.N + tcx::XM - 1) / tcx::XM) * ((F + tcx::XN - 1) / tcx::XN) * e.C;
-    int64_t sp = (2 * 152 + tiles - 1) / tiles;
-    sp = std::min<int64_t>(sp, std::max<int64_t>(1, e.Mk / (tcx::XKC * tcx::XDRAIN * 2)));
-    return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 32));
+    const int hi = (int)std::max<int64_t>(1, std::min<int64_t>(32, e.Mk / (tcx::XKC * tcx::XDRAIN * 2)));
+    return tc::wave_splits(tiles, e.Mk, 1, hi, 256);
 }
 
 size_t exact_work_elems(const EncodeDev& e, int64_t F) {
@@ -683,9 +682,8 @@ cudaError_t launch_gram_digits(const float4* G, int64_t N, int* eG, uint8_t* Gd,
 
 static int resid_splits(int64_t N, int64_t F) {
     const int64_t tiles = ((N + tcx::XM - 1) / tcx::XM) * ((F + tcx::XN - 1) / tcx::XN);
-    int64_t sp = (2 * 152 + tiles - 1) / tiles;
-    sp = std::min<int64_t>(sp, std::max<int64_t>(1, N / (tcx::XKC * tcx::XDRAIN * 2)));
-    return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 32));
+    const int hi = (int)std::max<int64_t>(1, std::min<int64_t>(32, N / (tcx::XKC * tcx::XDRAIN * 2)));
+    return tc::wave_splits(tiles, N, 1, hi, 256);
 }
 
 size_t resid_exact_work_elems(int64_t N, int64_t F) { return (size_t)resid_splits(N, F) * (size_t)N * (size_t)F; }

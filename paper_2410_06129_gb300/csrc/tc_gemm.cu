@@ -1657,11 +1657,12 @@ __global__ void k_apply_reduce(const float2* __restrict__ part, int splits, int6
 }
 
 // splits of the sample range: about two tiles per SM, chunks of at least 1024 samples
+// sample-range parts of the tensor-core apply: whole waves of tiles, parts of at
+// least 1024 samples
 int apply_tc_splits(int64_t N, int64_t M) {
     const int64_t rows = (N + tc::BM - 1) / tc::BM;
-    int64_t sp = (2 * 152 + rows - 1) / rows;
-    sp = std::min<int64_t>(sp, std::max<int64_t>(1, M / 1024));
-    return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 64));
+    const int hi = (int)std::max<int64_t>(1, std::min<int64_t>(64, M / 1024));
+    return tc::wave_splits(rows, M, 1, hi, 256);
 }
 
 bool apply_tc_ok(int64_t F) { return F >= 16 && tc_available(); }
