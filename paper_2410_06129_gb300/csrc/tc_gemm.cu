@@ -382,6 +382,7 @@ __device__ inline void load8d(const double2* p, int avail, float2 (&v)[8]) {
     }
 }
 struct CorrW {
+    static constexpr bool kPrefetch = true;  // W streams from HBM
     const float2* W;
     const double2* R;  // [F][N]
     float2* part;      // [splits][F][N]
@@ -408,6 +409,7 @@ struct CorrW {
     __device__ void store(int64_t i, int64_t j, float2 v) const { part[((j / BN) * F + j % BN) * N + i] = v; }
 };
 struct CorrWH {
+    static constexpr bool kPrefetch = true;  // W streams from HBM
     const float2* W;
     const float2* T;  // [F][N]
     float2* part;     // [splits][F][N]
@@ -1379,11 +1381,25 @@ cudaError_t launch_recon_bulk(const EncodeDev& e, const float2* W32, int slices,
 // ------------------------------------------------------------------ refinement correction (host)
 namespace {
 // k ranges of the correction: about two tiles per SM, at least 256 wide
+// k chunk of the correction's triangular products: row tile r holds the
+// nonempty chunks below min((r + 1) BM, N); the chunk that minimises whole waves of
+// those tiles x (chunk + per-tile overhead), at least 256 columns
 int64_t correct_tc_chunk(int64_t N) {
-    const int64_t rows = (N + tc::BM - 1) / tc::BM;
-    int64_t sp = (2 * 152 + rows - 1) / rows;
-    sp = std::max<int64_t>(1, std::min<int64_t>(sp, std::max<int64_t>(1, N / 256)));
-    return ((N + sp - 1) / sp + tc::KC - 1) / tc::KC * tc::KC;
+    const int64_t rows = (N + tc::BM - 1) / tc::BM, sms = tc::sm_count();
+    const int64_t hi = std::max<int64_t>(1, std::min<int64_t>(64, N / 256));
+    int64_t best = 0;
+    double bt = 0.0;
+    for (int64_t sp = 1; sp <= hi; ++sp) {
+        const int64_t chunk = ((N + sp - 1) / sp + tc::KC - 1) / tc::KC * tc::KC;
+        int64_t tiles = 0;
+        for (int64_t r = 0; r < rows; ++r) tiles += (std::min<int64_t>((r + 1) * tc::BM, N) + chunk - 1) / chunk;
+        const double t = (double)((tiles + sms - 1) / sms) * (double)(chunk + 256);
+        if (best == 0 || t < bt * (1.0 - 1e-9)) {
+            bt = t;
+            best = chunk;
+        }
+    }
+    return best;
 }
 }  // namespace
 
