@@ -658,40 +658,6 @@ struct TrtriBulk {
 };
 
 // ------------------------------------------------------------------ blocked Cholesky
-// Panel solve L[i][k0+j] = sum_k G[i][k0+k] conj(Dinv[j][k]) below the diagonal
-// block. P is the FP32 copy of the panel (row i at P + i * ldp); the result
-// goes to G (FP64) and back to P for the trailing update.
-struct TrsmTC {
-    float2* P;
-    int64_t ldp;
-    const float2* Dinv32;  // [64][64]
-    double2* G;
-    int64_t ld, N, k0, nbk;
-    __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
-        i0 = k0 + nbk + by * BM;
-        j0 = 0;
-        kb = 0;
-        ke = nbk;
-        return i0 < N;
-    }
-    __device__ RowPtr row_a(int64_t i) const { return RowPtr{P + (i < N ? i : 0) * ldp, i < N}; }
-    __device__ int64_t row_b(int64_t j) const { return j; }
-    __device__ void a8(const RowPtr& r, int64_t k, int64_t ke, float2 (&v)[8]) const {
-        load8f(r.p + k, r.ok ? (int)(ke - k) : 0, v);
-    }
-    __device__ void b8(int64_t j, int64_t k, int64_t ke, float2 (&v)[8]) const {
-#pragma unroll
-        for (int t = 0; t < 8; ++t)
-            v[t] = (j < nbk && k + t < ke) ? conjf2(Dinv32[j * 64 + k + t]) : make_float2(0.f, 0.f);
-    }
-    __device__ bool row_ok(int64_t i) const { return i < N; }
-    __device__ bool col_ok(int64_t j) const { return j < nbk; }
-    __device__ void store(int64_t i, int64_t j, float2 v) const {
-        G[i * ld + k0 + j] = make_double2(v.x, v.y);
-        P[i * ldp + j] = v;
-    }
-};
-
 // Trailing update G[i][j] -= sum_k P[i][k] conj(P[j][k]) on lower tiles, rows
 // i >= t0 and columns t0 <= j < jmax (jmax < N restricts it to a panel).
 struct HerkTC {
