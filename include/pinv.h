@@ -37,6 +37,13 @@
  *     wait that gave up) are recorded in the plan's device status word and
  *     returned by pinv_plan_sync().
  *   - A plan may be used from one host thread at a time.
+ *
+ * Device memory
+ *   - Plans, their apply scratch and the build's temporaries take device memory
+ *     from one pool per device owned by the library. The pool keeps memory that
+ *     plans give back, so creating or building a plan again maps none, and
+ *     returns it to the driver when the last plan is destroyed. The device's
+ *     default stream-ordered pool and the caller's allocator are not touched.
  */
 #ifndef PINV_H
 #define PINV_H
@@ -215,7 +222,9 @@ pinv_status pinv_plan_keep_gram(pinv_plan* plan, int keep);
 /* Sizes, lambda, pivots and per-stage timings of the last build. */
 pinv_status pinv_plan_info(const pinv_plan* plan, pinv_plan_info_t* out);
 
-/* Free the plan and its device memory (synchronises the plan's work). NULL is a no-op. */
+/* Free the plan and its device memory (synchronises the device). The memory goes
+ * back to the library's pool, which returns it to the driver with the last plan.
+ * NULL is a no-op. */
 void pinv_plan_destroy(pinv_plan* plan);
 
 /* ------------------------------------------------------------------------
