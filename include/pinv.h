@@ -42,7 +42,7 @@
  *   - Plans, their apply scratch and the build's temporaries take device memory
  *     from one pool per device owned by the library. The pool keeps memory that
  *     plans give back, so creating or building a plan again maps none, and
- *     returns it to the driver when the last plan is destroyed. The device's
+ *     releases it (trims the pool) when the last plan is destroyed. The device's
  *     default stream-ordered pool and the caller's allocator are not touched.
  */
 #ifndef PINV_H
@@ -223,7 +223,7 @@ pinv_status pinv_plan_keep_gram(pinv_plan* plan, int keep);
 pinv_status pinv_plan_info(const pinv_plan* plan, pinv_plan_info_t* out);
 
 /* Free the plan and its device memory (synchronises the device). The memory goes
- * back to the library's pool, which returns it to the driver with the last plan.
+ * back to the library's pool, which is trimmed when the last plan is destroyed.
  * NULL is a no-op. */
 void pinv_plan_destroy(pinv_plan* plan);
 
