@@ -23,7 +23,11 @@ Every function follows the paper's definition directly:
       r set by a fraction of the energy                Section 2.1 (SVD, tSVD,
       eigenvalue decomposition)
 Parity status: every function here is pinned by tests/test_oracle_pins.py
-(SVD brute force, Cartesian closed form, invariants).
+(SVD brute force, Cartesian closed form, invariants). The B0 factor of encode
+is pinned by the linear-map identity (a B0 map g . r equals the trajectory
+shifted by g t), a uniform offset and a common time delay; noise_matrix with a
+coloured Psi by the closed form for Psi = E E^H (Eq. 9 in Eq. 10) and by a
+Monte Carlo covariance of reconstructed coil-correlated noise.
 """
 from __future__ import annotations
 

@@ -159,6 +159,61 @@ def test_noise_matrix_white_noise_identity():
     assert np.max(np.abs(X - (Ginv - lam * Ginv @ Ginv))) < 1e-11 * np.max(np.abs(Ginv))
 
 
+def test_noise_matrix_signal_shaped_noise_closed_form():
+    """Noise with covariance Psi = E E^H (shaped like the signal) maps to
+    X = (Recon E)(Recon E)^H = (I - lam G^-1)(I - lam G^-1)^H by Eq. 9's
+    Tikhonov identity (Eq. 10). G^-1 here comes from numpy's inverse, not
+    from the oracle, and Psi is complex, so Psi^T != Psi."""
+    p = _small_plan(seed=16, coils=3)
+    E = O.plan_encode(p)
+    lam = O.lambda_abs(E, p.lambda_rel)
+    R, _ = O.recon_matrix(E, lam)
+    Ginv = np.linalg.inv(E.conj().T @ E + lam * np.eye(E.shape[1]))
+    S = np.eye(E.shape[1]) - lam * Ginv
+    X = O.noise_matrix(R, E @ E.conj().T)
+    assert np.max(np.abs(X - S @ S.conj().T)) < 1e-10
+
+
+def _coil_covariance(C, rng):
+    """A complex Hermitian positive definite C x C coil covariance with strong
+    imaginary off-diagonal terms, and a square root P with P P^H = psi."""
+    P = np.tril(rng.standard_normal((C, C)) + 1j * rng.standard_normal((C, C)))
+    P[np.diag_indices(C)] = np.abs(P[np.diag_indices(C)]) + 1.0
+    return P @ P.conj().T, P
+
+
+def test_noise_matrix_coil_covariance_monte_carlo():
+    """Eq. 10 defines X as the covariance of the reconstructed noise. Draw
+    k-space noise with coil covariance psi per sample (n = (P (x) I) g, g white
+    complex Gaussian), reconstruct it with Recon and compare the sample
+    covariance of the images with the oracle's X for Psi = psi (x) I. Only the
+    diagonal-dominant relative error of a 1 / sqrt(K) estimate is asked for."""
+    rng = np.random.default_rng(17)
+    p = _small_plan(seed=17, side=6, coils=3)
+    E = O.plan_encode(p)
+    lam = O.lambda_abs(E, p.lambda_rel)
+    R, _ = O.recon_matrix(E, lam)
+    C, Mk = p.coil_maps.shape[0], p.n_samples
+    psi, P = _coil_covariance(C, rng)
+    X = O.noise_matrix(R, np.kron(psi, np.eye(Mk)))
+    K = 40000
+    g = (rng.standard_normal((C, Mk, K)) + 1j * rng.standard_normal((C, Mk, K))) / np.sqrt(2.0)
+    n = np.einsum("ab,bmk->amk", P, g).reshape(C * Mk, K)
+    xs = R @ n
+    X_mc = xs @ xs.conj().T / K
+    assert np.linalg.norm(X_mc - X) / np.linalg.norm(X) < 0.03
+
+
+def test_planted_transposed_psi_fails_noise_pins(monkeypatch):
+    """Using Psi^T (= conj(Psi) for a Hermitian Psi) instead of Psi, a
+    plausible slip, fails both coloured-noise pins."""
+    monkeypatch.setattr(O, "noise_matrix", lambda R, psi: R @ psi.T @ R.conj().T)
+    with pytest.raises(AssertionError):
+        test_noise_matrix_signal_shaped_noise_closed_form()
+    with pytest.raises(AssertionError):
+        test_noise_matrix_coil_covariance_monte_carlo()
+
+
 def test_coil_procedural_equals_stacked_and_hadamard():
     """Eq. 11: sum_c E_c^H E_c = E^H E, and it equals (A^H A) o (S^H S)."""
     p = _small_plan(seed=9, coils=4)
@@ -186,16 +241,45 @@ def test_large_lambda_is_conjugate_phase():
     assert O.nrmse(lam * (R @ d), E.conj().T @ d) < 1e-6
 
 
-def test_encode_sign_and_b0_term_against_direct_sum():
-    """One entry of E evaluated by hand from the composite factor product."""
+def test_linear_b0_map_equals_shifted_trajectory():
+    """A linear off-resonance map df(r) = g . r adds g t_m to every k_m: the
+    B0 factor exp(-i2pi df t) and the Fourier factor exp(-i2pi k . r) combine
+    into exp(-i2pi (k + g t) . r) (Section 3.3, composite encoding). So the
+    oracle's B0 encoding must equal its B0-free encoding of the trajectory
+    k_m + g t_m. This fixes the sign of the B0 term relative to the Fourier
+    term and which index (sample m, voxel n) each factor follows."""
     p = _small_plan(seed=12, coils=2)
     vox = O.voxel_positions(p.dims)
-    E = O.encode(p.traj, vox, p.coil_maps, p.b0_hz, p.times)
-    Mk = p.n_samples
-    for (c, m, n) in [(0, 0, 0), (1, Mk - 1, 17), (1, 5, 63), (0, 77, 40)]:
-        ph = -2 * np.pi * (p.traj[m] @ vox[n] + p.b0_hz[n] * p.times[m])
-        want = p.coil_maps[c, n] * complex(np.cos(ph), np.sin(ph))
-        assert abs(E[c * Mk + m, n] - want) < 1e-13
+    g = np.array([37.0, -21.0])                  # Hz per unit length
+    b0 = vox @ g
+    t = p.times
+    E_b0 = O.encode(p.traj, vox, p.coil_maps, b0, t)
+    E_shift = O.encode(p.traj + np.outer(t, g), vox, p.coil_maps)
+    assert np.max(np.abs(E_b0 - E_shift)) < 1e-12
+
+
+def test_uniform_b0_is_a_phase_per_sample():
+    """A spatially uniform offset df multiplies sample m of every coil by
+    exp(-i2pi df t_m), independent of the voxel (Section 3.3)."""
+    p = _small_plan(seed=14, coils=3)
+    vox = O.voxel_positions(p.dims)
+    df = 23.5
+    E0 = O.encode(p.traj, vox, p.coil_maps)
+    E1 = O.encode(p.traj, vox, p.coil_maps, np.full(vox.shape[0], df), p.times)
+    ph = np.tile(np.exp(-2j * np.pi * df * p.times), p.coil_maps.shape[0])
+    assert np.max(np.abs(E1 - ph[:, None] * E0)) < 1e-12
+
+
+def test_b0_time_shift_is_a_voxel_phase():
+    """Adding the same delay T to every sample time multiplies column n by
+    exp(-i2pi df_n T): the B0 phase accrues linearly in time (Section 3.3)."""
+    p = _small_plan(seed=15, coils=2)
+    vox = O.voxel_positions(p.dims)
+    T = 1.3e-3
+    E0 = O.encode(p.traj, vox, p.coil_maps, p.b0_hz, p.times)
+    E1 = O.encode(p.traj, vox, p.coil_maps, p.b0_hz, p.times + T)
+    ph = np.exp(-2j * np.pi * p.b0_hz * T)
+    assert np.max(np.abs(E1 - E0 * ph[None, :])) < 1e-11
 
 
 def test_voxel_positions_convention():
@@ -251,6 +335,35 @@ def test_planted_sign_flip_fails_cartesian_pin():
     sgn = ((-1.0) ** (j[:, None] + j[None, :]))
     adj = sgn * (side * side * np.fft.ifft2(d.reshape(side, side) * sgn))
     assert O.nrmse(E_bad.conj().T @ d, adj.ravel()) > 1e-3
+
+
+def test_planted_b0_sign_flip_fails_b0_pins(monkeypatch):
+    """exp(+i2pi df t) in the B0 factor (the sign the paper prints for its
+    exponentials, reading 1) fails the linear-map and uniform-offset pins."""
+    good = O.encode
+
+    def flipped(traj, vox, coil_maps=None, b0_hz=None, times=None):
+        E = good(traj, vox, coil_maps, None, None)
+        if b0_hz is None:
+            return E
+        ph = np.exp(2j * np.pi * np.outer(np.asarray(times), np.asarray(b0_hz)))
+        C = 1 if coil_maps is None else len(coil_maps)
+        return E * np.tile(ph, (C, 1))
+    monkeypatch.setattr(O, "encode", flipped)
+    with pytest.raises(AssertionError):
+        test_linear_b0_map_equals_shifted_trajectory()
+    with pytest.raises(AssertionError):
+        test_uniform_b0_is_a_phase_per_sample()
+
+
+def test_planted_b0_index_swap_fails_time_shift_pin(monkeypatch):
+    """Pairing each sample's time with the wrong voxel's offset (the B0 factor
+    built from a reversed voxel order) fails the time-shift pin."""
+    good = O.encode
+    monkeypatch.setattr(O, "encode", lambda traj, vox, cm=None, b0=None, t=None:
+                        good(traj, vox, cm, None if b0 is None else np.asarray(b0)[::-1], t))
+    with pytest.raises(AssertionError):
+        test_b0_time_shift_is_a_voxel_phase()
 
 
 # ---------------------------------------------------------------- eigen / tSVD (Section 2.1)
