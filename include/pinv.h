@@ -143,6 +143,22 @@ typedef struct {
     int last_refine_iters;              /* refinement steps taken by the last apply */
     double last_refine_resid;           /* ||r|| / ||E^H d|| after the last apply's refinement */
     double ms_gram_kernel;              /* of ms_gram: the tensor-core (mixed) or FP64 Gram kernels alone */
+    /* The lambda / condition check (Section 2.1: the condition number of the
+     * inversion; Section 2.2: the load lambda bounds every eigenvalue of G below
+     * by lambda). Each build estimates kappa_1(G) = ||G||_1 ||G^-1||_1: ||G||_1
+     * exactly (from G before the Cholesky, or from the exact Gram of TOEPLITZ
+     * plans), ||G^-1||_1 by Hager's method (Higham's complex variant, at most
+     * five rounds and an alternating-sign vector) with solves through the
+     * factor. Mixed plans certify the final candidates y against G itself
+     * (||y||_1 / ||G y||_1, G y by the refinement's residual operator), so the
+     * estimate is a lower bound of kappa_1(G) up to the rounding of the sums
+     * (mixed plans without the TOEPLITZ residual read ||G||_1 from the
+     * split-precision Gram, so it carries that Gram's rounding).
+     * Hager's estimates are usually within a factor of 3. NaN when G was not
+     * positive definite. Runs on the build's stream without host synchronisation. */
+    double kappa_est;                   /* estimate of kappa_1(G) */
+    double norm1_g;                     /* ||G||_1 */
+    double ms_cond;                     /* time of the condition estimate in the last build */
 } pinv_plan_info_t;
 
 typedef struct pinv_plan pinv_plan;

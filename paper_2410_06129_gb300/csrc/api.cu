@@ -90,6 +90,9 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
     }
     CK(cudaEventRecord(p->ev[7], s));
     if (p->Gkeep) CK(cudaMemcpyAsync(p->Gkeep, p->G, sizeof(double2) * N * N, cudaMemcpyDeviceToDevice, s));
+    // ||G||_1 for the condition estimate: from the exact Gram where the plan forms
+    // one (below, beside the Cholesky), else from G before the Cholesky overwrites it
+    if (!p->Gx) CK(launch_gram_norm1(p->G, nullptr, N, ld, p->st, s));
     if (p->Gx) {
         // exact Gram for the refinement residual (Toeplitz table, then coil products,
         // then its digit tiles). Only applies read it, so mixed plans form it on their
@@ -105,6 +108,7 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
         CK(launch_toeplitz64(p->enc, work, p->Ttab, sx));
         CK(cudaFreeAsync(work, sx));
         CK(launch_gram_exact(p->enc, p->Ttab, p->lambda_abs, p->Gx, sx));
+        CK(launch_gram_norm1(nullptr, p->Gx, N, N, p->st, sx));
         if (p->Gd) CK(launch_gram_digits(p->Gx, N, p->eG, p->Gd, sx));
         if (p->Ad) CK(launch_adj_digits(p->enc, p->Ad, sx));
     }
@@ -205,6 +209,11 @@ pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events) {
         CK(launch_lauum64(W, N, ld, p->Ginv, s));
         CK(cudaFreeAsync(W, s));
     }
+    // the lambda / condition check: kappa_1(G) from the factor (Section 2.1, 2.2)
+    if (events) CK(cudaEventRecord(p->ev[8], s));
+    pinv_status cs = build_condition(p, s);
+    if (cs != PINV_OK) return cs;
+    if (events) CK(cudaEventRecord(p->ev[9], s));
     return PINV_OK;
 }
 
@@ -684,9 +693,17 @@ pinv_status pinv_plan_info(const pinv_plan* p, pinv_plan_info_t* o) {
             tg = 0.f;
         }
         o->ms_gram_kernel = tg;
+        float tc = 0.f;
+        if (cudaEventElapsedTime(&tc, p->ev[8], p->ev[9]) != cudaSuccess) {
+            cudaGetLastError();
+            tc = 0.f;
+        }
+        o->ms_cond = tc;
         const DevStatus h = *p->st_host;
         o->min_pivot = h.min_pivot;
         o->max_pivot = h.max_pivot;
+        o->norm1_g = h.norm1_g;
+        o->kappa_est = h.kappa_est;
     }
     return PINV_OK;
 }

@@ -1,0 +1,502 @@
+// Condition estimate of the Gram matrix (Section 2.1: the condition number
+// measures how the inversion amplifies errors; Section 2.2: the Tikhonov load
+// lambda makes G = E^H E + lambda I positive definite, every eigenvalue at
+// least lambda).
+//
+// kappa_1(G) = ||G||_1 ||G^-1||_1.
+//   ||G||_1 (= ||G||_inf for Hermitian G) is the largest column sum of |G|. It is
+//   read from G before the Cholesky overwrites it, or from the exact Gram where
+//   the plan forms one.
+//   ||G^-1||_1 is estimated by Hager's method in Higham's complex form. Start
+//   from x = (1/N, ..., 1/N); then y = G^-1 x, xi = y / |y| elementwise,
+//   z = G^-1 xi (G^-1 is Hermitian), x = e_j at the largest |z_j|; repeat while
+//   the estimate grows and the index changes (at most five rounds), and try one
+//   more vector of alternating signs with growing magnitude. Each value
+//   ||G^-1 v||_1 / ||v||_1 is a lower bound of ||G^-1||_1.
+//
+// The solves use the plan's factor: the FP64 G^-1 of FP64 plans, or W^H W with
+// the FP32 W = L^-1 of mixed plans. A mixed factor is off by up to kappa(G)
+// times the split rounding, so for mixed plans the two final candidates y are
+// certified against G itself: ||y||_1 / ||G y||_1 <= ||G^-1||_1 holds for every
+// y, and G y is formed by the plan's refinement residual operator (the exact
+// tensor-core Gram, or E^H E y + lambda y generated in double-float or FP64).
+// The estimate therefore stays below kappa_1(G) up to the rounding of the sums.
+//
+// Everything runs on the device with no host synchronisation: single-block
+// kernels keep the iteration's state in device memory, and once it has
+// converged the remaining kernels of the fixed launch sequence return at once.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "df.cuh"
+#include "plan_impl.h"
+
+namespace pinv {
+namespace {
+
+constexpr int CB = 1024;       // threads of the single-block kernels
+constexpr int HAGER_ROUNDS = 5;
+
+pinv_status cuda_err(cudaError_t e, const char* where) {
+    return set_error(e == cudaErrorMemoryAllocation ? PINV_ERR_OOM : PINV_ERR_CUDA,
+                     std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CKC(call)                                              \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_err(e_, #call);     \
+    } while (0)
+
+struct HagerState {
+    double est;       // best ||G^-1 v||_1 / ||v||_1 so far (v = the start vector or some e_j)
+    double est_alt;   // the same for the alternating-sign vector
+    int j, jlast;     // current and previous unit-vector index
+    int done;         // the iteration has finished
+    int rounds;       // unit-vector rounds taken
+};
+
+// |a + ib| in FP32 from FP64 parts, without the FP64 pipe
+__device__ inline float abs_f(double2 g) {
+    const float x = f64_to_f32_rn(g.x), y = f64_to_f32_rn(g.y);
+    return sqrtf(fmaf(x, x, y * y));
+}
+
+// double-float sum of a warp's (hi, lo) pairs, result in every lane
+__device__ inline float2 warp_sum_df(float h, float l) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+        df_add(h, l, oh, ol, h, l);
+    }
+    return make_float2(h, l);
+}
+__device__ inline void acc_df(float& h, float& l, float v) { df_add(h, l, v, 0.f, h, l); }
+
+// -------------------------------------------------------------------- ||G||_1
+// rs[i] = sum_{j <= i} |G[i][j]| over the stored lower triangle (full = false),
+// or sum_j |G[i][j]| over the whole row (full = true); one warp per row
+template <class T, bool FULL>
+__global__ void k_abs_rows(const T* G, int64_t N, int64_t ld, float2* rs) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= N) return;
+    const T* row = G + i * ld;
+    const int64_t end = FULL ? N : i + 1;
+    float h = 0.f, l = 0.f;
+    for (int64_t j = lane; j < end; j += 32) {
+        float a;
+        if constexpr (std::is_same<T, float4>::value) {
+            const float4 g = reinterpret_cast<const float4*>(row)[j];  // double-float: |hi| suffices
+            a = sqrtf(fmaf(g.x, g.x, g.z * g.z));
+        } else {
+            a = abs_f(row[j]);
+        }
+        acc_df(h, l, a);
+    }
+    const float2 s = warp_sum_df(h, l);
+    if (lane == 0) rs[i] = s;
+}
+
+// part[s][j] = sum over rows i of chunk s with i > j of |G[i][j]| (the strictly
+// lower part of column j); consecutive threads read consecutive columns
+__global__ void k_abs_cols_lower(const double2* G, int64_t N, int64_t ld, int64_t rows_per_chunk, float2* part) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.y * rows_per_chunk;
+    const int64_t i1 = N < i0 + rows_per_chunk ? N : i0 + rows_per_chunk;
+    if (j >= N) return;
+    float h = 0.f, l = 0.f;
+    for (int64_t i = i0 > j + 1 ? i0 : j + 1; i < i1; ++i) acc_df(h, l, abs_f(G[i * ld + j]));
+    part[(int64_t)blockIdx.y * N + j] = make_float2(h, l);
+}
+
+// out = max_j (rs[j] + sum_s part[s][j])
+__global__ void __launch_bounds__(CB) k_norm1_finish(const float2* rs, const float2* part, int chunks, int64_t N,
+                                                     double* out) {
+    __shared__ double red[CB];
+    double m = 0.0;
+    for (int64_t j = threadIdx.x; j < N; j += CB) {
+        float h = rs[j].x, l = rs[j].y;
+        for (int s = 0; s < chunks; ++s) {
+            const float2 p = part[(int64_t)s * N + j];
+            df_add(h, l, p.x, p.y, h, l);
+        }
+        m = fmax(m, (double)h + (double)l);
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = CB / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// -------------------------------------------------------------------- solves
+// u = W x, W lower FP32 [N][N] row-major; one warp per row
+__global__ void k_w_mv(const float2* W, int64_t N, const float2* x, float2* u, const int* skip) {
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= N) return;
+    const float2* row = W + i * N;
+    float re = 0.f, im = 0.f;
+#pragma unroll 4
+    for (int64_t j = lane; j <= i; j += 32) {
+        const float2 w = row[j], v = x[j];
+        re = fmaf(w.x, v.x, fmaf(-w.y, v.y, re));
+        im = fmaf(w.x, v.y, fmaf(w.y, v.x, im));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) u[i] = make_float2(re, im);
+}
+
+// part[s][j] = sum over rows i of chunk s with i >= j of conj(W[i][j]) u[i]
+__global__ void k_wh_part(const float2* W, int64_t N, const float2* u, int64_t rows_per_chunk, float2* part,
+                          const int* skip) {
+    if (skip && *skip) return;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.y * rows_per_chunk;
+    const int64_t i1 = N < i0 + rows_per_chunk ? N : i0 + rows_per_chunk;
+    if (j >= N) return;
+    float re = 0.f, im = 0.f;
+#pragma unroll 4
+    for (int64_t i = i0 > j ? i0 : j; i < i1; ++i) {
+        const float2 w = W[i * N + j], v = u[i];
+        re = fmaf(w.x, v.x, fmaf(w.y, v.y, re));
+        im = fmaf(w.x, v.y, fmaf(-w.y, v.x, im));
+    }
+    part[(int64_t)blockIdx.y * N + j] = make_float2(re, im);
+}
+
+// y[j] = sum_s part[s][j], in FP64
+__global__ void k_part_sum(const float2* part, int chunks, int64_t N, double2* y, const int* skip) {
+    if (skip && *skip) return;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < chunks; ++s) {
+        const float2 p = part[(int64_t)s * N + j];
+        re += p.x;
+        im += p.y;
+    }
+    y[j] = make_double2(re, im);
+}
+
+// y = H x with the full Hermitian FP64 H (G^-1 of FP64 plans); one warp per row
+__global__ void k_hemv_full(const double2* H, int64_t N, const float2* xf, double2* y, const int* skip) {
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= N) return;
+    const double2* row = H + i * N;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int64_t j = lane; j < N; j += 32) {
+        zfma(acc, row[j], make_double2(xf[j].x, xf[j].y));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) y[i] = acc;
+}
+
+// -------------------------------------------------------------------- Hager's iteration
+// block sum of |v| (FP64), result in every thread
+__device__ double block_abs_sum(const double2* v, int64_t N, double* red) {
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += CB) s += hypot(v[i].x, v[i].y);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = CB / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_hg_init(float2* x, int64_t N, HagerState* h) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) x[i] = make_float2((float)(1.0 / (double)N), 0.f);
+    if (i == 0) *h = HagerState{0.0, 0.0, -1, -1, 0, 0};
+}
+
+// After y = G^-1 v with v the start vector (first = 1) or e_j: record the
+// estimate ||y||_1 (||v||_1 = 1), stop when it no longer grows, keep the best y
+// in ybest, and write xi = y / |y| (1 where y vanishes) for the next solve.
+__global__ void __launch_bounds__(CB) k_hg_sign(const double2* y, float2* xi, double2* ybest, int64_t N,
+                                                HagerState* h, int first) {
+    __shared__ double red[CB];
+    __shared__ int stop;
+    if (h->done) return;
+    const double s = block_abs_sum(y, N, red);
+    if (threadIdx.x == 0) {
+        stop = 0;
+        if (first) {
+            h->est = s;
+        } else if (s <= h->est) {
+            h->done = 1;  // no growth: the iteration has converged
+            stop = 1;
+        } else {
+            h->est = s;
+        }
+    }
+    __syncthreads();
+    if (stop) return;
+    for (int64_t i = threadIdx.x; i < N; i += CB) {
+        const double2 v = y[i];
+        ybest[i] = v;
+        const double a = hypot(v.x, v.y);
+        xi[i] = a > 1e-300 ? make_float2((float)(v.x / a), (float)(v.y / a)) : make_float2(1.f, 0.f);
+    }
+}
+
+// After z = G^-1 xi: j = the first index of the largest |z_j|. Stop when the
+// previous index attains the same maximum or after HAGER_ROUNDS rounds;
+// otherwise x = e_j.
+__global__ void __launch_bounds__(CB) k_hg_pick(const double2* z, float2* x, int64_t N, HagerState* h) {
+    __shared__ double rv[CB];
+    __shared__ long long ri[CB];
+    __shared__ int stop, jn;
+    if (h->done) return;
+    double best = -1.0;
+    long long bi = 0;
+    for (int64_t i = threadIdx.x; i < N; i += CB) {
+        const double a = hypot(z[i].x, z[i].y);
+        if (a > best) { best = a; bi = i; }
+    }
+    rv[threadIdx.x] = best;
+    ri[threadIdx.x] = bi;
+    __syncthreads();
+    for (int w = CB / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            const double o = rv[threadIdx.x + w];
+            const long long oi = ri[threadIdx.x + w];
+            if (o > rv[threadIdx.x] || (o == rv[threadIdx.x] && oi < ri[threadIdx.x])) {
+                rv[threadIdx.x] = o;
+                ri[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int j = (int)ri[0];
+        stop = 0;
+        if (h->j >= 0) {
+            const double2 zl = z[h->j];
+            if (hypot(zl.x, zl.y) >= rv[0] || h->rounds >= HAGER_ROUNDS) stop = 1;
+        }
+        if (stop) h->done = 1;
+        h->jlast = h->j;
+        h->j = j;
+        h->rounds += 1;
+        jn = j;
+    }
+    __syncthreads();
+    if (stop) return;
+    for (int64_t i = threadIdx.x; i < N; i += CB) x[i] = make_float2(i == jn ? 1.f : 0.f, 0.f);
+}
+
+// x_i = (-1)^i (1 + i / (N - 1)), scaled to ||x||_1 = 1
+__global__ void k_hg_alt(float2* x, int64_t N) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double v = N > 1 ? (1.0 + (double)i / (double)(N - 1)) / (1.5 * (double)N) : 1.0;
+    x[i] = make_float2((float)((i & 1) ? -v : v), 0.f);
+}
+
+// ||x||_1 of the rounded alternating vector, and est_alt = ||y||_1 / ||x||_1; y kept in yalt
+__global__ void __launch_bounds__(CB) k_hg_alt_finish(const double2* y, const float2* x, double2* yalt, int64_t N,
+                                                      HagerState* h) {
+    __shared__ double red[CB];
+    const double s = block_abs_sum(y, N, red);
+    double t = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += CB) {
+        t += fabs((double)x[i].x);
+        yalt[i] = y[i];
+    }
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = CB / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) h->est_alt = s / red[0];
+}
+
+// FP64 plans: kappa = ||G||_1 max(est, est_alt) (their G^-1 is accurate)
+__global__ void k_hg_final(const HagerState* h, DevStatus* st) {
+    st->kappa_est = st->norm1_g * fmax(h->est, h->est_alt);
+}
+
+// Mixed plans: kappa = ||G||_1 max_f ||Y[f]||_1 / ||R[f]||_1 with R = -G Y (f = 0: the
+// best iterate, f = 1: the alternating-sign candidate)
+__global__ void __launch_bounds__(CB) k_hg_certify(const double2* Y, const double2* R, int64_t N, DevStatus* st) {
+    __shared__ double red[CB];
+    double best = 0.0;
+    for (int f = 0; f < 2; ++f) {
+        const double ny = block_abs_sum(Y + (int64_t)f * N, N, red);
+        const double nr = block_abs_sum(R + (int64_t)f * N, N, red);
+        if (nr > 0.0) best = fmax(best, ny / nr);
+    }
+    if (threadIdx.x == 0) st->kappa_est = st->norm1_g * best;
+}
+
+// row chunks of the column-sum kernels: at least 32 rows, at most 256 chunks
+int64_t rows_per_chunk(int64_t N) { return std::max<int64_t>(32, (N + 255) / 256); }
+int chunks_for(int64_t N) { return (int)((N + rows_per_chunk(N) - 1) / rows_per_chunk(N)); }
+
+}  // namespace
+
+// ||G||_1 into st->norm1_g: from the stored lower triangle of G (FP64) or from
+// the full double-float exact Gram Gx (when gx != nullptr)
+cudaError_t launch_gram_norm1(const double2* G, const float4* Gx, int64_t N, int64_t ld, DevStatus* st,
+                              cudaStream_t s) {
+    const int chunks = Gx ? 0 : chunks_for(N);
+    const int64_t rpc = rows_per_chunk(N);
+    float2 *rs = nullptr, *part = nullptr;
+    cudaError_t e = work_alloc((void**)&rs, sizeof(float2) * N, s);
+    if (e != cudaSuccess) return e;
+    if (chunks && (e = work_alloc((void**)&part, sizeof(float2) * N * chunks, s)) != cudaSuccess) return e;
+    const unsigned rows_blocks = (unsigned)((N + 7) / 8);
+    if (Gx) {
+        k_abs_rows<float4, true><<<rows_blocks, 256, 0, s>>>(Gx, N, N, rs);
+    } else {
+        k_abs_rows<double2, false><<<rows_blocks, 256, 0, s>>>(G, N, ld, rs);
+        k_abs_cols_lower<<<dim3((unsigned)((N + 255) / 256), (unsigned)chunks), 256, 0, s>>>(G, N, ld, rpc, part);
+        note_launch();
+    }
+    k_norm1_finish<<<1, CB, 0, s>>>(rs, part, chunks, N, &st->norm1_g);
+    note_launch(2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (part) cudaFreeAsync(part, s);
+    return cudaFreeAsync(rs, s);
+}
+
+// Hager's estimate of ||G^-1||_1 and kappa_1(G) = ||G||_1 ||G^-1||_1 into
+// st->kappa_est (st->norm1_g must be set); runs after the factorisation.
+pinv_status build_condition(pinv_plan* p, cudaStream_t s) {
+    const int64_t N = p->N, M = p->M;
+    const bool mixed = p->precision != PINV_FP64;
+    const int chunks = chunks_for(N);
+    const int64_t rpc = rows_per_chunk(N);
+    // device work: state, vectors (x as float2; y, z, the candidates Y2 and
+    // their products R2 as double2), partial sums and the residual scratch
+    HagerState* h = nullptr;
+    float2 *x = nullptr, *u = nullptr, *part = nullptr;
+    double2 *y = nullptr, *z = nullptr, *Y2 = nullptr, *R2 = nullptr, *zero = nullptr, *U2 = nullptr;
+    float4* work = nullptr;
+    uint8_t* bd = nullptr;
+    int* fexp = nullptr;
+    // every buffer goes back to the pool in stream order when this returns, on
+    // every path (the kernels enqueued before it still see it)
+    struct Release {
+        std::vector<void*> q;
+        cudaStream_t s;
+        ~Release() {
+            for (void* b : q) cudaFreeAsync(b, s);
+        }
+    } bufs_{{}, s};
+    std::vector<void*>& bufs = bufs_.q;
+    auto take = [&](void** q, size_t bytes) -> cudaError_t {
+        cudaError_t e = work_alloc(q, bytes, s);
+        if (e == cudaSuccess) bufs.push_back(*q);
+        return e;
+    };
+    CKC(take((void**)&h, sizeof(HagerState)));
+    CKC(take((void**)&x, sizeof(float2) * N));
+    CKC(take((void**)&y, sizeof(double2) * N));
+    CKC(take((void**)&z, sizeof(double2) * N));
+    CKC(take((void**)&Y2, sizeof(double2) * 2 * N));
+    if (mixed) {
+        CKC(take((void**)&u, sizeof(float2) * N));
+        CKC(take((void**)&part, sizeof(float2) * N * chunks));
+        CKC(take((void**)&R2, sizeof(double2) * 2 * N));
+    }
+    const unsigned vb = (unsigned)((N + 255) / 256), wb = (unsigned)((N + 7) / 8);
+    const int* skip = &h->done;
+    // y = G^-1 x (x float2); skip_on: return at once once the iteration is done
+    auto solve = [&](double2* out, bool skip_on) -> cudaError_t {
+        const int* sk = skip_on ? skip : nullptr;
+        if (mixed) {
+            k_w_mv<<<wb, 256, 0, s>>>(p->W32, N, x, u, sk);
+            k_wh_part<<<dim3(vb, (unsigned)chunks), 256, 0, s>>>(p->W32, N, u, rpc, part, sk);
+            k_part_sum<<<vb, 256, 0, s>>>(part, chunks, N, out, sk);
+            note_launch(3);
+        } else {
+            k_hemv_full<<<wb, 256, 0, s>>>(p->Ginv, N, x, out, sk);
+            note_launch();
+        }
+        return cudaGetLastError();
+    };
+    k_hg_init<<<vb, 256, 0, s>>>(x, N, h);
+    note_launch();
+    CKC(solve(y, false));
+    k_hg_sign<<<1, CB, 0, s>>>(y, x, Y2, N, h, 1);
+    note_launch();
+    CKC(solve(z, true));
+    k_hg_pick<<<1, CB, 0, s>>>(z, x, N, h);
+    note_launch();
+    for (int r = 1; r < HAGER_ROUNDS; ++r) {
+        CKC(solve(y, true));
+        k_hg_sign<<<1, CB, 0, s>>>(y, x, Y2, N, h, 0);
+        note_launch();
+        CKC(solve(z, true));
+        k_hg_pick<<<1, CB, 0, s>>>(z, x, N, h);
+        note_launch();
+    }
+    k_hg_alt<<<vb, 256, 0, s>>>(x, N);
+    note_launch();
+    CKC(solve(y, false));
+    k_hg_alt_finish<<<1, CB, 0, s>>>(y, x, Y2 + N, N, h);
+    note_launch();
+    CKC(cudaGetLastError());
+    if (!mixed) {
+        k_hg_final<<<1, 1, 0, s>>>(h, p->st);
+        note_launch();
+    } else {
+        // R2 = -G Y2 by the refinement's residual operator (b = 0)
+        if (p->refine_residual == PINV_RESIDUAL_TOEPLITZ && p->Gd) {
+            const size_t wel = resid_exact_work_elems(N, 2);
+            CKC(take((void**)&zero, sizeof(double2) * 2 * N));
+            CKC(cudaMemsetAsync(zero, 0, sizeof(double2) * 2 * N, s));
+            CKC(take((void**)&fexp, sizeof(int) * 2));
+            CKC(take((void**)&bd, resid_bdigit_bytes(N, 2)));
+            if (wel) CKC(take((void**)&work, sizeof(float4) * wel));
+            CKC(launch_gram_resid_exact(p->Gd, p->eG, N, zero, Y2, 2, fexp, bd, R2, work, p->st, s));
+        } else if (p->refine_residual == PINV_RESIDUAL_TOEPLITZ) {
+            const size_t wel = df_work_elems(N, 2, N);
+            CKC(take((void**)&zero, sizeof(double2) * 2 * N));
+            CKC(cudaMemsetAsync(zero, 0, sizeof(double2) * 2 * N, s));
+            if (wel) CKC(take((void**)&work, sizeof(float4) * wel));
+            CKC(launch_gram_resid_df(p->Gx, N, zero, Y2, 2, R2, s, work));
+        } else if (p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT) {
+            const size_t wel = std::max(df_work_elems(M, 2, N), df_work_elems(N, 2, M));
+            CKC(take((void**)&zero, sizeof(double2) * 2 * M));
+            CKC(cudaMemsetAsync(zero, 0, sizeof(double2) * 2 * M, s));
+            CKC(take((void**)&U2, sizeof(double2) * 2 * M));
+            if (wel) CKC(take((void**)&work, sizeof(float4) * wel));
+            CKC(launch_forward_df(p->enc, Y2, 2, zero, U2, s, work));               // U = -E Y
+            CKC(launch_adjoint_df(p->enc, U2, 2, p->lambda_abs, Y2, R2, s, work));  // R = E^H U - lambda Y
+        } else {
+            CKC(take((void**)&U2, sizeof(double2) * 2 * M));
+            CKC(launch_forward64(p->enc, Y2, 2, nullptr, U2, s));
+            CKC(launch_adjoint64(p->enc, U2, 2, p->lambda_abs, Y2, R2, s));
+        }
+        k_hg_certify<<<1, CB, 0, s>>>(Y2, R2, N, p->st);
+        note_launch();
+    }
+    CKC(cudaGetLastError());
+    return PINV_OK;
+}
+
+}  // namespace pinv

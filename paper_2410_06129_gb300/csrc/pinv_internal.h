@@ -73,6 +73,9 @@ struct DevStatus {
     // tile counter of the persistent tensor-core kernel running on this plan's
     // stream (next item, CTAs finished); the last CTA of a launch zeroes both
     unsigned long long sched_next, sched_done;
+    // condition estimate (cond.cu): ||G||_1 and kappa_1(G) = ||G||_1 ||G^-1||_1
+    double norm1_g;
+    double kappa_est;
 };
 
 // ---------------------------------------------------------------------------
@@ -264,6 +267,11 @@ int64_t recon_bulk_chunks(const EncodeDev& e, int slices);
 cudaError_t recon_bulk_wtables(const EncodeDev& e, const float2* W32, int slices, void* work, cudaStream_t s);
 cudaError_t recon_bulk_et(const EncodeDev& e, int slices, void* work, int64_t chunk, cudaStream_t s);
 void tc_multi_free(TcMulti* m);
+
+// ||G||_1 into st->norm1_g, from the lower triangle of the FP64 G (before the
+// Cholesky overwrites it) or, with Gx != nullptr, from the full double-float exact Gram
+cudaError_t launch_gram_norm1(const double2* G, const float4* Gx, int64_t N, int64_t ld, DevStatus* st,
+                              cudaStream_t s);
 
 // double-float frame products split their k range over CTAs; `work` holds
 // df_work_elems() partials (float4) when the split count is above one

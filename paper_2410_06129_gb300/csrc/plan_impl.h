@@ -52,6 +52,8 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram);
 // Cholesky, pivot statistics and the inverse (W = L^-1, or G^-1 for FP64 plans)
 pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events);
 pinv_status build_recon(pinv_plan* p, cudaStream_t s);
+// kappa_1(G) estimate into the status word (cond.cu); run after the factorisation
+pinv_status build_condition(pinv_plan* p, cudaStream_t s);
 // status word to pinned host memory
 pinv_status build_end(pinv_plan* p, cudaStream_t s);
 }  // namespace pinv
@@ -106,7 +108,7 @@ struct pinv_plan {
     void* scratch_buf = nullptr;
     size_t scratch_bytes = 0;
 
-    cudaEvent_t ev[8] = {};  // build stages 0-5; 6-7 around the Gram kernels
+    cudaEvent_t ev[10] = {};  // build stages 0-5; 6-7 around the Gram kernels; 8-9 around the condition estimate
     int last_refine_iters = 0;
     double last_refine_resid = 0;
     int info = -1;

@@ -217,6 +217,8 @@ __global__ void k_reset_status(DevStatus* st) {
     st->max_pivot = 0.0;
     st->sched_next = 0;
     st->sched_done = 0;
+    st->norm1_g = 0.0;
+    st->kappa_est = 0.0;
 }
 
 cudaError_t launch_reset_status(DevStatus* st, cudaStream_t s) {
