@@ -14,6 +14,10 @@
 // it runs in plain FP32 (tile engine k_ctile).
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
+#include <cstring>
+
+#include <cooperative_groups.h>
 
 #include "df.cuh"
 
@@ -441,9 +445,196 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
     }
 }
 
+// The same block on a cluster of two CTAs: rank 0 factors, rank 1 forms the
+// inverse behind it. Step j of rank 0 is the factor half of the sweep above:
+// scale column j by r = 1 / sqrt(A_jj), write L_jj, update the trailing entries
+// c > j. The threads that scale column j also store it, and r_j, into rank 1's
+// shared memory (posted remote stores); after the block barrier, thread j raises
+// a flag there (release at cluster scope). Rank 1 waits for the flag (acquire),
+// scales row j of X by r_j and updates the rows below (X_ic -= L_ij X_jc, c <= j)
+// from its local copy, and checks for the next column while it updates. Every
+// entry sees the same operations in the same order as in the one-CTA sweep, so
+// the results are the same bit for bit; each CTA does half the work. Rank 0
+// never waits for rank 1, except once at the end so that rank 1 has received
+// everything before either exits; rank 1's waits are bounded (clock64, about
+// 2 s): past the limit it records timeout site DIAG_SITE, stops and still
+// meets rank 0 at the final cluster barrier.
+constexpr int DIAG_SITE = 20;
+constexpr long long DIAG_WAIT_LIMIT = 4000000000LL;
+constexpr size_t DIAG2_SMEM = (size_t)(NBD * NBDP + NBD * NBD + NBD) * sizeof(float4) + NBD * sizeof(float2);
+
+__device__ inline void st_release_cluster(unsigned* p, unsigned v) {
+    asm volatile("st.release.cluster.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ inline unsigned ld_acquire_cluster(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.cluster.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// rank 1: wait until rank 0 has published `need` columns; false on timeout
+__device__ inline bool diag_wait(const unsigned* flag, unsigned need, DevStatus* st) {
+    const long long t0 = clock64();
+    while (ld_acquire_cluster(flag) < need) {
+        if (clock64() - t0 > DIAG_WAIT_LIMIT) {
+            atomicMax(&st->timeout_site, DIAG_SITE);
+            return false;
+        }
+    }
+    return true;
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(DIAG_THREADS)
+    k_potrf_diag_df2(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv, float2* Dinv32, float2* L32,
+                     int64_t ldl, DevStatus* st) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ float4 smd[];
+    float4* A = smd;                    // rank 0: the block, then L; rank 1: X = L^-1
+    float4* Lb = smd + NBD * NBDP;      // rank 1: Lb[j][i] = L_ij, received from rank 0
+    float4* Xr = Lb + NBD * NBD;        // rank 1: row j of X, scaled
+    float2* rb = reinterpret_cast<float2*>(Xr + NBD);  // rank 1: r_j, received from rank 0
+    __shared__ unsigned flag;           // rank 1: columns of L published by rank 0
+    __shared__ int bad, stop;
+    const int tid = threadIdx.x;
+    const unsigned rank = cl.block_rank();
+    const int nb = (int)((N - k0) < NBD ? (N - k0) : NBD);
+    if (tid == 0) {
+        flag = 0;
+        stop = 0;
+        bad = (st->not_pd_pivot != INT_MAX) ? 1 : 0;
+    }
+    for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
+        const int i = e / NBD, j = e % NBD;
+        float4 v = make_float4(i == j ? 1.f : 0.f, 0.f, 0.f, 0.f);
+        if (rank == 0 && i < nb && j < nb && j <= i) {
+            const double2 g = G[(k0 + i) * ld + k0 + j];
+            const float2 re = split_f64(g.x), im = split_f64(g.y);
+            v = make_float4(re.x, re.y, im.x, im.y);
+        }
+        A[i * NBDP + j] = v;
+    }
+    cl.sync();  // rank 1's flag is zero before rank 0 may raise it
+    if (rank == 0) {
+        unsigned* rflag = cl.map_shared_rank(&flag, 1);
+        float4* rLb = cl.map_shared_rank(Lb, 1);
+        float2* rrb = cl.map_shared_rank(rb, 1);
+        for (int j = 0; j < NBD; ++j) {
+            float lh = 0.f, ll = 0.f;
+            if (tid < NBD) {
+                const float4 a = A[j * NBDP + j];
+                float dh = a.x, dl = a.y;
+                const bool fail = !(dh > 0.f) || !isfinite(dh);
+                if (fail) {
+                    dh = 1.f;
+                    dl = 0.f;
+                }
+                const float2 r = df_rsqrt(dh, dl);
+                if (tid > j) {
+                    const float4 l = df_norm(df_scale(A[tid * NBDP + j], r.x, r.y));
+                    A[tid * NBDP + j] = l;
+                    rLb[j * NBD + tid] = l;
+                } else if (tid == j) {
+                    if (fail && !bad) {
+                        atomicMin(&st->not_pd_pivot, (int)(k0 + j));
+                        bad = 1;
+                    }
+                    df_mul(dh, dl, r.x, r.y, lh, ll);
+                    rrb[j] = r;
+                }
+            }
+            __syncthreads();
+            if (tid == j) {
+                A[j * NBDP + j] = make_float4(lh, ll, 0.f, 0.f);
+                st_release_cluster(rflag, (unsigned)(j + 1));  // column j and r_j are in rank 1
+            }
+            // trailing entries (i, c), j < c <= i; row j + 1 + p paired with row 63 - p
+            const int rows = NBD - 1 - j, w = NBD - j;
+            const int slots = ((rows + 1) >> 1) * w;
+            const unsigned wm = ((1u << 20) + (unsigned)w - 1u) / (unsigned)w;
+            for (int e = tid; e < slots; e += DIAG_THREADS) {
+                const int p = (int)(((unsigned)e * wm) >> 20);
+                const int q = e - p * w;
+                const int ia = j + 1 + p, ib = NBD - 1 - p;
+                const bool first = q <= p;
+                const int i = first ? ia : ib, c = first ? j + 1 + q : j + q - p;
+                if (!first && ib <= ia) continue;
+                float4* t = A + i * NBDP + c;
+                const float4 b = cdf_conj(A[c * NBDP + j]);
+                const float4 l = A[i * NBDP + j];
+                float4 v = *t;
+                cacc(v, make_float4(-l.x, -l.y, -l.z, -l.w), b);
+                *t = df_norm(v);
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
+            const int i = e / NBD, j = e % NBD;
+            if (i < nb && j < nb && j <= i) {
+                const float4 a = A[i * NBDP + j];
+                const double2 g = make_double2(join_f64(a.x, a.y), join_f64(a.z, a.w));
+                G[(k0 + i) * ld + k0 + j] = g;
+                if (L32) L32[(k0 + i) * ldl + k0 + j] = make_float2(f64_to_f32_rn(g.x), f64_to_f32_rn(g.y));
+            } else if (L32 && i < nb && j < nb) {
+                L32[(k0 + i) * ldl + k0 + j] = make_float2(0.f, 0.f);
+            }
+        }
+        cl.sync();
+    } else {
+        float4* X = A;
+        if (tid == 0 && !diag_wait(&flag, 1u, st)) stop = 1;
+        __syncthreads();
+        for (int j = 0; j < NBD && !stop; ++j) {
+            if (tid <= j) {
+                const float2 r = rb[j];
+                const float4 x = df_norm(df_scale(X[j * NBDP + tid], r.x, r.y));
+                Xr[tid] = x;
+                X[j * NBDP + tid] = x;
+            }
+            __syncthreads();
+            // rows i > j, columns c <= j: X_ic -= L_ij X_jc
+            const int rows = NBD - 1 - j, w = j + 1;
+            const unsigned wm = ((1u << 20) + (unsigned)w - 1u) / (unsigned)w;  // e / w for e < 2^20 / w
+            const float4* lj = Lb + j * NBD;
+            for (int e = tid; e < rows * w; e += DIAG_THREADS) {
+                const int p = (int)(((unsigned)e * wm) >> 20);
+                const int i = j + 1 + p, c = e - p * w;
+                float4* t = X + i * NBDP + c;
+                const float4 l = lj[i];
+                float4 v = *t;
+                cacc(v, make_float4(-l.x, -l.y, -l.z, -l.w), Xr[c]);
+                *t = df_norm(v);
+            }
+            if (tid == 0 && j + 1 < NBD && !diag_wait(&flag, (unsigned)(j + 2), st)) stop = 1;
+            __syncthreads();
+        }
+        cl.sync();  // rank 0 has published everything and may exit
+        for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
+            const int i = e / NBD, j = e % NBD;
+            const float4 x = j <= i ? X[i * NBDP + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (Dinv) Dinv[e] = make_double2(join_f64(x.x, x.y), join_f64(x.z, x.w));
+            if (Dinv32) Dinv32[e] = make_float2(x.x + x.y, x.z + x.w);
+        }
+    }
+}
+
 cudaError_t launch_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv, float2* Dinv32,
                                  float2* L32, int64_t ldl, DevStatus* st, cudaStream_t s) {
-    static bool attr = false;
+    // PINV_DIAG_CLUSTER=0: the one-CTA sweep (same results)
+    const char* env = std::getenv("PINV_DIAG_CLUSTER");
+    const bool cluster = !(env && std::strcmp(env, "0") == 0);
+    static bool attr = false, attr2 = false;
+    if (cluster) {
+        const size_t smem2 = DIAG2_SMEM;
+        if (!attr2) {
+            cudaError_t err =
+                cudaFuncSetAttribute(k_potrf_diag_df2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+            if (err != cudaSuccess) return err;
+            attr2 = true;
+        }
+        k_potrf_diag_df2<<<2, DIAG_THREADS, smem2, s>>>(G, ld, N, k0, Dinv, Dinv32, L32, ldl, st);
+        note_launch();
+        return cudaGetLastError();
+    }
     const size_t smem = 2 * NBD * NBDP * sizeof(float4);
     if (!attr) {
         cudaError_t err =

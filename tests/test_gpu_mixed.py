@@ -195,3 +195,19 @@ def test_factor_only_mixed():
     pl = _plan(p, precision=L.MIXED_BF16X6, recon_mode=L.RECON_NONE, refine_max_iters=2).build()
     x = pl.apply(torch.from_numpy(p.data).cuda()).cpu().numpy()
     assert rel(x, ref.images) <= 1e-4
+
+
+@pytest.mark.parametrize("side", [16, 23])
+def test_diag_block_cluster_matches_one_cta_sweep(side, monkeypatch):
+    """The diagonal Cholesky blocks on a two-CTA cluster (factor in one CTA, the
+    block inverse one column behind in the other) give the same L and W = L^-1,
+    bit for bit, as the one-CTA sweep; 23 x 23 has a ragged last block."""
+    p = synth.make_plan(side, 3, "spiral", 1, 2120 + side, 1e-3, samples=3 * side * side, interleaves=2)
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("PINV_DIAG_CLUSTER", mode)
+        with _plan(p, precision=L.MIXED_BF16X6) as pl:
+            pl.build()
+            out[mode] = (pl.export(L.EXPORT_CHOL).cpu(), pl.export(L.EXPORT_LINV).cpu())
+    assert torch.equal(out["0"][0], out["1"][0])
+    assert torch.equal(out["0"][1], out["1"][1])
