@@ -56,6 +56,7 @@ struct HagerState {
     int j, jlast;     // current and previous unit-vector index
     int done;         // the iteration has finished
     int rounds;       // unit-vector rounds taken
+    int best_j;       // start vector of the best estimate: -1 = uniform, else e_best_j
 };
 
 // |a + ib| in FP32 from FP64 parts, without the FP64 pipe
@@ -135,58 +136,81 @@ __global__ void __launch_bounds__(CB) k_norm1_finish(const float2* rs, const flo
 }
 
 // -------------------------------------------------------------------- solves
-// u = W x, W lower FP32 [N][N] row-major; one warp per row
-__global__ void k_w_mv(const float2* W, int64_t N, const float2* x, float2* u, const int* skip) {
+// Products with the FP32 W = L^-1 for F <= 2 vectors at once, FP32 arithmetic
+// (the search only needs the estimate's order; the final candidates are refined
+// and certified against G).
+constexpr int FMAX = 2;
+
+// u[f] = W x[f], W lower FP32 [N][N] row-major; one warp per row
+__global__ void k_w_mv(const float2* W, int64_t N, int F, const float2* x, float2* u, const int* skip) {
     if (skip && *skip) return;
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= N) return;
     const float2* row = W + i * N;
-    float re = 0.f, im = 0.f;
+    float re[FMAX] = {0.f, 0.f}, im[FMAX] = {0.f, 0.f};
 #pragma unroll 4
     for (int64_t j = lane; j <= i; j += 32) {
-        const float2 w = row[j], v = x[j];
-        re = fmaf(w.x, v.x, fmaf(-w.y, v.y, re));
-        im = fmaf(w.x, v.y, fmaf(w.y, v.x, im));
+        const float2 w = row[j];
+#pragma unroll
+        for (int f = 0; f < FMAX; ++f) {
+            if (f < F) {
+                const float2 v = x[(int64_t)f * N + j];
+                re[f] = fmaf(w.x, v.x, fmaf(-w.y, v.y, re[f]));
+                im[f] = fmaf(w.x, v.y, fmaf(w.y, v.x, im[f]));
+            }
+        }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        re += __shfl_xor_sync(0xffffffffu, re, o);
-        im += __shfl_xor_sync(0xffffffffu, im, o);
+    for (int f = 0; f < FMAX; ++f) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            re[f] += __shfl_xor_sync(0xffffffffu, re[f], o);
+            im[f] += __shfl_xor_sync(0xffffffffu, im[f], o);
+        }
+        if (lane == 0 && f < F) u[(int64_t)f * N + i] = make_float2(re[f], im[f]);
     }
-    if (lane == 0) u[i] = make_float2(re, im);
 }
 
-// part[s][j] = sum over rows i of chunk s with i >= j of conj(W[i][j]) u[i]
-__global__ void k_wh_part(const float2* W, int64_t N, const float2* u, int64_t rows_per_chunk, float2* part,
+// part[s][f][j] = sum over rows i of chunk s with i >= j of conj(W[i][j]) u[f][i]
+__global__ void k_wh_part(const float2* W, int64_t N, int F, const float2* u, int64_t rows_per_chunk, float2* part,
                           const int* skip) {
     if (skip && *skip) return;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.y * rows_per_chunk;
     const int64_t i1 = N < i0 + rows_per_chunk ? N : i0 + rows_per_chunk;
     if (j >= N) return;
-    float re = 0.f, im = 0.f;
+    float re[FMAX] = {0.f, 0.f}, im[FMAX] = {0.f, 0.f};
 #pragma unroll 4
     for (int64_t i = i0 > j ? i0 : j; i < i1; ++i) {
-        const float2 w = W[i * N + j], v = u[i];
-        re = fmaf(w.x, v.x, fmaf(w.y, v.y, re));
-        im = fmaf(w.x, v.y, fmaf(-w.y, v.x, im));
+        const float2 w = W[i * N + j];
+#pragma unroll
+        for (int f = 0; f < FMAX; ++f) {
+            if (f < F) {
+                const float2 v = u[(int64_t)f * N + i];
+                re[f] = fmaf(w.x, v.x, fmaf(w.y, v.y, re[f]));
+                im[f] = fmaf(w.x, v.y, fmaf(-w.y, v.x, im[f]));
+            }
+        }
     }
-    part[(int64_t)blockIdx.y * N + j] = make_float2(re, im);
+    for (int f = 0; f < F; ++f) part[((int64_t)blockIdx.y * F + f) * N + j] = make_float2(re[f], im[f]);
 }
 
-// y[j] = sum_s part[s][j], in FP64
-__global__ void k_part_sum(const float2* part, int chunks, int64_t N, double2* y, const int* skip) {
+// y[f][j] (+)= sum_s part[s][f][j]
+__global__ void k_part_sum(const float2* part, int chunks, int64_t N, int F, double2* y, int accumulate,
+                           const int* skip) {
     if (skip && *skip) return;
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
-    double re = 0.0, im = 0.0;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * F) return;
+    float re = 0.f, im = 0.f;
     for (int s = 0; s < chunks; ++s) {
-        const float2 p = part[(int64_t)s * N + j];
+        const float2 p = part[(int64_t)s * N * F + idx];
         re += p.x;
         im += p.y;
     }
-    y[j] = make_double2(re, im);
+    double2 v = make_double2((double)re, (double)im);
+    if (accumulate) v = zadd(y[idx], v);
+    y[idx] = v;
 }
 
 // y = H x with the full Hermitian FP64 H (G^-1 of FP64 plans); one warp per row
@@ -197,9 +221,7 @@ __global__ void k_hemv_full(const double2* H, int64_t N, const float2* xf, doubl
     if (i >= N) return;
     const double2* row = H + i * N;
     double2 acc = make_double2(0.0, 0.0);
-    for (int64_t j = lane; j < N; j += 32) {
-        zfma(acc, row[j], make_double2(xf[j].x, xf[j].y));
-    }
+    for (int64_t j = lane; j < N; j += 32) zfma(acc, row[j], make_double2(xf[j].x, xf[j].y));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
@@ -208,18 +230,28 @@ __global__ void k_hemv_full(const double2* H, int64_t N, const float2* xf, doubl
     if (lane == 0) y[i] = acc;
 }
 
+// FP64 -> FP32 vector copy on the integer pipe
+__global__ void k_vec_f32(const double2* a, float2* b, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_float2(f64_to_f32_rn(a[i].x), f64_to_f32_rn(a[i].y));
+}
+
 // -------------------------------------------------------------------- Hager's iteration
-// block sum of |v| (FP64), result in every thread
-__device__ double block_abs_sum(const double2* v, int64_t N, double* red) {
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < N; i += CB) s += hypot(v[i].x, v[i].y);
-    red[threadIdx.x] = s;
+// |v| in FP32 from FP64 parts, without the FP64 pipe
+__device__ inline float mag(double2 v) { return abs_f(v); }
+
+// block sum of |v[i]| (FP32 magnitudes, double-float sums), result in every thread
+__device__ double block_abs_sum(const double2* v, int64_t N, float2* red) {
+    float h = 0.f, l = 0.f;
+    for (int64_t i = threadIdx.x; i < N; i += CB) acc_df(h, l, mag(v[i]));
+    const float2 w = warp_sum_df(h, l);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = w;
     __syncthreads();
-    for (int w = CB / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    const double r = red[0];
+    float2 t = threadIdx.x < CB / 32 ? red[threadIdx.x] : make_float2(0.f, 0.f);
+    if (threadIdx.x < 32) t = warp_sum_df(t.x, t.y);
+    if (threadIdx.x == 0) red[0] = t;
+    __syncthreads();
+    const double r = (double)red[0].x + (double)red[0].y;
     __syncthreads();
     return r;
 }
@@ -227,7 +259,7 @@ __device__ double block_abs_sum(const double2* v, int64_t N, double* red) {
 __global__ void k_hg_init(float2* x, int64_t N, HagerState* h) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) x[i] = make_float2((float)(1.0 / (double)N), 0.f);
-    if (i == 0) *h = HagerState{0.0, 0.0, -1, -1, 0, 0};
+    if (i == 0) *h = HagerState{0.0, 0.0, -1, -1, 0, 0, -1};
 }
 
 // After y = G^-1 v with v the start vector (first = 1) or e_j: record the
@@ -235,19 +267,18 @@ __global__ void k_hg_init(float2* x, int64_t N, HagerState* h) {
 // in ybest, and write xi = y / |y| (1 where y vanishes) for the next solve.
 __global__ void __launch_bounds__(CB) k_hg_sign(const double2* y, float2* xi, double2* ybest, int64_t N,
                                                 HagerState* h, int first) {
-    __shared__ double red[CB];
+    __shared__ float2 red[CB / 32];
     __shared__ int stop;
     if (h->done) return;
     const double s = block_abs_sum(y, N, red);
     if (threadIdx.x == 0) {
         stop = 0;
-        if (first) {
-            h->est = s;
-        } else if (s <= h->est) {
+        if (!first && s <= h->est) {
             h->done = 1;  // no growth: the iteration has converged
             stop = 1;
         } else {
             h->est = s;
+            h->best_j = first ? -1 : h->j;
         }
     }
     __syncthreads();
@@ -255,8 +286,9 @@ __global__ void __launch_bounds__(CB) k_hg_sign(const double2* y, float2* xi, do
     for (int64_t i = threadIdx.x; i < N; i += CB) {
         const double2 v = y[i];
         ybest[i] = v;
-        const double a = hypot(v.x, v.y);
-        xi[i] = a > 1e-300 ? make_float2((float)(v.x / a), (float)(v.y / a)) : make_float2(1.f, 0.f);
+        const float re = f64_to_f32_rn(v.x), im = f64_to_f32_rn(v.y);
+        const float a = sqrtf(fmaf(re, re, im * im));
+        xi[i] = a > 0.f ? make_float2(re / a, im / a) : make_float2(1.f, 0.f);
     }
 }
 
@@ -264,23 +296,26 @@ __global__ void __launch_bounds__(CB) k_hg_sign(const double2* y, float2* xi, do
 // previous index attains the same maximum or after HAGER_ROUNDS rounds;
 // otherwise x = e_j.
 __global__ void __launch_bounds__(CB) k_hg_pick(const double2* z, float2* x, int64_t N, HagerState* h) {
-    __shared__ double rv[CB];
-    __shared__ long long ri[CB];
+    __shared__ float rv[CB];
+    __shared__ int ri[CB];
     __shared__ int stop, jn;
     if (h->done) return;
-    double best = -1.0;
-    long long bi = 0;
+    float best = -1.f;
+    int bi = 0;
     for (int64_t i = threadIdx.x; i < N; i += CB) {
-        const double a = hypot(z[i].x, z[i].y);
-        if (a > best) { best = a; bi = i; }
+        const float a = mag(z[i]);
+        if (a > best) {
+            best = a;
+            bi = (int)i;
+        }
     }
     rv[threadIdx.x] = best;
     ri[threadIdx.x] = bi;
     __syncthreads();
     for (int w = CB / 2; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) {
-            const double o = rv[threadIdx.x + w];
-            const long long oi = ri[threadIdx.x + w];
+            const float o = rv[threadIdx.x + w];
+            const int oi = ri[threadIdx.x + w];
             if (o > rv[threadIdx.x] || (o == rv[threadIdx.x] && oi < ri[threadIdx.x])) {
                 rv[threadIdx.x] = o;
                 ri[threadIdx.x] = oi;
@@ -289,12 +324,9 @@ __global__ void __launch_bounds__(CB) k_hg_pick(const double2* z, float2* x, int
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const int j = (int)ri[0];
+        const int j = ri[0];
         stop = 0;
-        if (h->j >= 0) {
-            const double2 zl = z[h->j];
-            if (hypot(zl.x, zl.y) >= rv[0] || h->rounds >= HAGER_ROUNDS) stop = 1;
-        }
+        if (h->j >= 0 && (mag(z[h->j]) >= rv[0] || h->rounds >= HAGER_ROUNDS)) stop = 1;
         if (stop) h->done = 1;
         h->jlast = h->j;
         h->j = j;
@@ -314,23 +346,35 @@ __global__ void k_hg_alt(float2* x, int64_t N) {
     x[i] = make_float2((float)((i & 1) ? -v : v), 0.f);
 }
 
-// ||x||_1 of the rounded alternating vector, and est_alt = ||y||_1 / ||x||_1; y kept in yalt
+// est_alt = ||y||_1 / ||x||_1 for the rounded alternating vector; y kept in yalt
 __global__ void __launch_bounds__(CB) k_hg_alt_finish(const double2* y, const float2* x, double2* yalt, int64_t N,
                                                       HagerState* h) {
-    __shared__ double red[CB];
+    __shared__ float2 red[CB / 32];
     const double s = block_abs_sum(y, N, red);
-    double t = 0.0;
+    float th = 0.f, tl = 0.f;
     for (int64_t i = threadIdx.x; i < N; i += CB) {
-        t += fabs((double)x[i].x);
+        acc_df(th, tl, fabsf(x[i].x));
         yalt[i] = y[i];
     }
-    red[threadIdx.x] = t;
+    const float2 w = warp_sum_df(th, tl);
     __syncthreads();
-    for (int w = CB / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float2 t = threadIdx.x < CB / 32 ? red[threadIdx.x] : make_float2(0.f, 0.f);
+        t = warp_sum_df(t.x, t.y);
+        if (threadIdx.x == 0) h->est_alt = s / ((double)t.x + (double)t.y);
     }
-    if (threadIdx.x == 0) h->est_alt = s / red[0];
+}
+
+// the two final candidate vectors v in FP64: V[0] = the best iterate's start
+// vector (uniform or e_j), V[1] = the alternating-sign vector (x)
+__global__ void k_hg_vecs(const HagerState* h, const float2* x, double2* V, int64_t N) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int bj = h->best_j;
+    V[i] = make_double2(bj < 0 ? 1.0 / (double)N : (i == bj ? 1.0 : 0.0), 0.0);
+    V[N + i] = make_double2(x[i].x, x[i].y);
 }
 
 // FP64 plans: kappa = ||G||_1 max(est, est_alt) (their G^-1 is accurate)
@@ -338,10 +382,9 @@ __global__ void k_hg_final(const HagerState* h, DevStatus* st) {
     st->kappa_est = st->norm1_g * fmax(h->est, h->est_alt);
 }
 
-// Mixed plans: kappa = ||G||_1 max_f ||Y[f]||_1 / ||R[f]||_1 with R = -G Y (f = 0: the
-// best iterate, f = 1: the alternating-sign candidate)
+// Mixed plans: kappa = ||G||_1 max_f ||Y[f]||_1 / ||R[f]||_1 with R = -G Y
 __global__ void __launch_bounds__(CB) k_hg_certify(const double2* Y, const double2* R, int64_t N, DevStatus* st) {
-    __shared__ double red[CB];
+    __shared__ float2 red[CB / 32];
     double best = 0.0;
     for (int f = 0; f < 2; ++f) {
         const double ny = block_abs_sum(Y + (int64_t)f * N, N, red);
@@ -389,14 +432,6 @@ pinv_status build_condition(pinv_plan* p, cudaStream_t s) {
     const bool mixed = p->precision != PINV_FP64;
     const int chunks = chunks_for(N);
     const int64_t rpc = rows_per_chunk(N);
-    // device work: state, vectors (x as float2; y, z, the candidates Y2 and
-    // their products R2 as double2), partial sums and the residual scratch
-    HagerState* h = nullptr;
-    float2 *x = nullptr, *u = nullptr, *part = nullptr;
-    double2 *y = nullptr, *z = nullptr, *Y2 = nullptr, *R2 = nullptr, *zero = nullptr, *U2 = nullptr;
-    float4* work = nullptr;
-    uint8_t* bd = nullptr;
-    int* fexp = nullptr;
     // every buffer goes back to the pool in stream order when this returns, on
     // every path (the kernels enqueued before it still see it)
     struct Release {
@@ -406,31 +441,33 @@ pinv_status build_condition(pinv_plan* p, cudaStream_t s) {
             for (void* b : q) cudaFreeAsync(b, s);
         }
     } bufs_{{}, s};
-    std::vector<void*>& bufs = bufs_.q;
     auto take = [&](void** q, size_t bytes) -> cudaError_t {
         cudaError_t e = work_alloc(q, bytes, s);
-        if (e == cudaSuccess) bufs.push_back(*q);
+        if (e == cudaSuccess) bufs_.q.push_back(*q);
         return e;
     };
+    HagerState* h = nullptr;
+    float2 *x = nullptr, *u = nullptr, *part = nullptr;
+    double2 *y = nullptr, *z = nullptr, *Y2 = nullptr, *V2 = nullptr, *R2 = nullptr, *zero = nullptr, *U2 = nullptr;
     CKC(take((void**)&h, sizeof(HagerState)));
-    CKC(take((void**)&x, sizeof(float2) * N));
+    CKC(take((void**)&x, sizeof(float2) * FMAX * N));
     CKC(take((void**)&y, sizeof(double2) * N));
     CKC(take((void**)&z, sizeof(double2) * N));
     CKC(take((void**)&Y2, sizeof(double2) * 2 * N));
     if (mixed) {
-        CKC(take((void**)&u, sizeof(float2) * N));
-        CKC(take((void**)&part, sizeof(float2) * N * chunks));
-        CKC(take((void**)&R2, sizeof(double2) * 2 * N));
+        CKC(take((void**)&u, sizeof(float2) * FMAX * N));
+        CKC(take((void**)&part, sizeof(float2) * FMAX * N * chunks));
     }
     const unsigned vb = (unsigned)((N + 255) / 256), wb = (unsigned)((N + 7) / 8);
     const int* skip = &h->done;
-    // y = G^-1 x (x float2); skip_on: return at once once the iteration is done
-    auto solve = [&](double2* out, bool skip_on) -> cudaError_t {
+    // out (+)= G^-1 x for F vectors in x (float2 [F][N]); skip_on: return at once
+    // once the iteration is done
+    auto solve = [&](double2* out, int F, bool skip_on, int accumulate) -> cudaError_t {
         const int* sk = skip_on ? skip : nullptr;
         if (mixed) {
-            k_w_mv<<<wb, 256, 0, s>>>(p->W32, N, x, u, sk);
-            k_wh_part<<<dim3(vb, (unsigned)chunks), 256, 0, s>>>(p->W32, N, u, rpc, part, sk);
-            k_part_sum<<<vb, 256, 0, s>>>(part, chunks, N, out, sk);
+            k_w_mv<<<wb, 256, 0, s>>>(p->W32, N, F, x, u, sk);
+            k_wh_part<<<dim3(vb, (unsigned)chunks), 256, 0, s>>>(p->W32, N, F, u, rpc, part, sk);
+            k_part_sum<<<(unsigned)((N * F + 255) / 256), 256, 0, s>>>(part, chunks, N, F, out, accumulate, sk);
             note_launch(3);
         } else {
             k_hemv_full<<<wb, 256, 0, s>>>(p->Ginv, N, x, out, sk);
@@ -440,61 +477,80 @@ pinv_status build_condition(pinv_plan* p, cudaStream_t s) {
     };
     k_hg_init<<<vb, 256, 0, s>>>(x, N, h);
     note_launch();
-    CKC(solve(y, false));
+    CKC(solve(y, 1, false, 0));
     k_hg_sign<<<1, CB, 0, s>>>(y, x, Y2, N, h, 1);
     note_launch();
-    CKC(solve(z, true));
+    CKC(solve(z, 1, true, 0));
     k_hg_pick<<<1, CB, 0, s>>>(z, x, N, h);
     note_launch();
     for (int r = 1; r < HAGER_ROUNDS; ++r) {
-        CKC(solve(y, true));
+        CKC(solve(y, 1, true, 0));
         k_hg_sign<<<1, CB, 0, s>>>(y, x, Y2, N, h, 0);
         note_launch();
-        CKC(solve(z, true));
+        CKC(solve(z, 1, true, 0));
         k_hg_pick<<<1, CB, 0, s>>>(z, x, N, h);
         note_launch();
     }
     k_hg_alt<<<vb, 256, 0, s>>>(x, N);
     note_launch();
-    CKC(solve(y, false));
+    CKC(solve(y, 1, false, 0));
     k_hg_alt_finish<<<1, CB, 0, s>>>(y, x, Y2 + N, N, h);
     note_launch();
     CKC(cudaGetLastError());
     if (!mixed) {
         k_hg_final<<<1, 1, 0, s>>>(h, p->st);
         note_launch();
-    } else {
-        // R2 = -G Y2 by the refinement's residual operator (b = 0)
-        if (p->refine_residual == PINV_RESIDUAL_TOEPLITZ && p->Gd) {
-            const size_t wel = resid_exact_work_elems(N, 2);
-            CKC(take((void**)&zero, sizeof(double2) * 2 * N));
-            CKC(cudaMemsetAsync(zero, 0, sizeof(double2) * 2 * N, s));
-            CKC(take((void**)&fexp, sizeof(int) * 2));
-            CKC(take((void**)&bd, resid_bdigit_bytes(N, 2)));
-            if (wel) CKC(take((void**)&work, sizeof(float4) * wel));
-            CKC(launch_gram_resid_exact(p->Gd, p->eG, N, zero, Y2, 2, fexp, bd, R2, work, p->st, s));
-        } else if (p->refine_residual == PINV_RESIDUAL_TOEPLITZ) {
-            const size_t wel = df_work_elems(N, 2, N);
-            CKC(take((void**)&zero, sizeof(double2) * 2 * N));
-            CKC(cudaMemsetAsync(zero, 0, sizeof(double2) * 2 * N, s));
-            if (wel) CKC(take((void**)&work, sizeof(float4) * wel));
-            CKC(launch_gram_resid_df(p->Gx, N, zero, Y2, 2, R2, s, work));
-        } else if (p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT) {
-            const size_t wel = std::max(df_work_elems(M, 2, N), df_work_elems(N, 2, M));
-            CKC(take((void**)&zero, sizeof(double2) * 2 * M));
-            CKC(cudaMemsetAsync(zero, 0, sizeof(double2) * 2 * M, s));
-            CKC(take((void**)&U2, sizeof(double2) * 2 * M));
-            if (wel) CKC(take((void**)&work, sizeof(float4) * wel));
-            CKC(launch_forward_df(p->enc, Y2, 2, zero, U2, s, work));               // U = -E Y
-            CKC(launch_adjoint_df(p->enc, U2, 2, p->lambda_abs, Y2, R2, s, work));  // R = E^H U - lambda Y
-        } else {
-            CKC(take((void**)&U2, sizeof(double2) * 2 * M));
-            CKC(launch_forward64(p->enc, Y2, 2, nullptr, U2, s));
-            CKC(launch_adjoint64(p->enc, U2, 2, p->lambda_abs, Y2, R2, s));
-        }
-        k_hg_certify<<<1, CB, 0, s>>>(Y2, R2, N, p->st);
-        note_launch();
+        return PINV_OK;
     }
+    // Mixed plans: the two candidates v (V2) and their solves y (Y2), refined
+    // twice (r = v - G y, y += W^H W r), then certified with R2 = -G Y2
+    CKC(take((void**)&V2, sizeof(double2) * 2 * N));
+    CKC(take((void**)&R2, sizeof(double2) * 2 * N));
+    k_hg_vecs<<<vb, 256, 0, s>>>(h, x, V2, N);
+    note_launch();
+    const bool toep = p->refine_residual == PINV_RESIDUAL_TOEPLITZ;
+    float4* work = nullptr;
+    uint8_t* bd = nullptr;
+    int* fexp = nullptr;
+    CKC(take((void**)&zero, sizeof(double2) * 2 * (toep ? N : M)));
+    CKC(cudaMemsetAsync(zero, 0, sizeof(double2) * 2 * (toep ? N : M), s));
+    if (toep && p->Gd) {
+        const size_t wel = resid_exact_work_elems(N, 2);
+        CKC(take((void**)&fexp, sizeof(int) * 2));
+        CKC(take((void**)&bd, resid_bdigit_bytes(N, 2)));
+        if (wel) CKC(take((void**)&work, sizeof(float4) * wel));
+    } else if (toep) {
+        const size_t wel = df_work_elems(N, 2, N);
+        if (wel) CKC(take((void**)&work, sizeof(float4) * wel));
+    } else {
+        const size_t wel = std::max(df_work_elems(M, 2, N), df_work_elems(N, 2, M));
+        CKC(take((void**)&U2, sizeof(double2) * 2 * M));
+        if (wel && p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT) CKC(take((void**)&work, sizeof(float4) * wel));
+    }
+    // R = B - G X by the refinement's residual operator (B = nullptr: R = -G X)
+    auto resid = [&](const double2* B, const double2* X, double2* R) -> cudaError_t {
+        cudaError_t e;
+        if (toep && p->Gd) return launch_gram_resid_exact(p->Gd, p->eG, N, B ? B : zero, X, 2, fexp, bd, R, work,
+                                                          p->st, s);
+        if (toep) return launch_gram_resid_df(p->Gx, N, B ? B : zero, X, 2, R, s, work);
+        if (p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT) {
+            if ((e = launch_forward_df(p->enc, X, 2, zero, U2, s, work)) != cudaSuccess) return e;  // U = -E X
+            if ((e = launch_adjoint_df(p->enc, U2, 2, p->lambda_abs, X, R, s, work)) != cudaSuccess) return e;
+        } else {
+            if ((e = launch_forward64(p->enc, X, 2, nullptr, U2, s)) != cudaSuccess) return e;
+            if ((e = launch_adjoint64(p->enc, U2, 2, p->lambda_abs, X, R, s)) != cudaSuccess) return e;
+        }
+        return B ? launch_zaxpy(R, B, 2 * N, s) : cudaSuccess;  // R = B - G X
+    };
+    for (int it = 0; it < 2; ++it) {
+        CKC(resid(V2, Y2, R2));
+        k_vec_f32<<<(unsigned)((2 * N + 255) / 256), 256, 0, s>>>(R2, x, 2 * N);
+        note_launch();
+        CKC(solve(Y2, 2, false, 1));
+    }
+    CKC(resid(nullptr, Y2, R2));
+    k_hg_certify<<<1, CB, 0, s>>>(Y2, R2, N, p->st);
+    note_launch();
     CKC(cudaGetLastError());
     return PINV_OK;
 }
