@@ -48,6 +48,7 @@ namespace pinv {
 pinv_status reset_status(pinv_plan* p, cudaStream_t s) {
     CK(launch_reset_status(p->st, s));
     if (p->st_inv) CK(launch_reset_status(p->st_inv, s));
+    if (p->st_trail) CK(launch_reset_status(p->st_trail, s));
     return PINV_OK;
 }
 
@@ -183,7 +184,10 @@ pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events) {
         cudaStream_t sc = (p->s_chol && !(hi && std::strcmp(hi, "0") == 0)) ? p->s_chol : s;
         if (sc != s) CK(cudaStreamWaitEvent(sc, p->ev_fork, 0));
         // (the FP64 diagonal inverses are not needed: the inverse reads the FP32 ones)
-        CK(launch_potrf_tc(p->G, N, ld, nullptr, D32, L32, p->slices(), p->st, sc, tab, p->ev_panel.data()));
+        const TrailLookahead la{p->s_trail, p->st_trail, p->ev_tab, p->ev_trail};
+        CK(cudaStreamWaitEvent(p->s_trail, p->ev_fork, 0));
+        CK(launch_potrf_tc(p->G, N, ld, nullptr, D32, L32, p->slices(), p->st, sc, tab, p->ev_panel.data(), &la));
+        CK(launch_merge_timeout(p->st, p->st_trail, sc));
         CK(launch_pivot_stats(p->G, N, ld, p->st, sc));
         if (events) CK(cudaEventRecord(p->ev[3], sc));
         CK(cudaStreamWaitEvent(p->s_inv, p->ev_fork, 0));
@@ -542,6 +546,11 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
         AL(p->st_inv, sizeof(DevStatus), "inverse status");
         CKC(cudaMemset(p->st_inv, 0, sizeof(DevStatus)));
         CKC(cudaStreamCreateWithFlags(&p->s_inv, cudaStreamNonBlocking));
+        AL(p->st_trail, sizeof(DevStatus), "trailing-update status");
+        CKC(cudaMemset(p->st_trail, 0, sizeof(DevStatus)));
+        CKC(cudaStreamCreateWithFlags(&p->s_trail, cudaStreamNonBlocking));
+        CKC(cudaEventCreateWithFlags(&p->ev_tab, cudaEventDisableTiming));
+        CKC(cudaEventCreateWithFlags(&p->ev_trail, cudaEventDisableTiming));
         int prio_lo = 0, prio_hi = 0;
         CKC(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
         CKC(cudaStreamCreateWithPriority(&p->s_chol, cudaStreamNonBlocking, prio_hi));

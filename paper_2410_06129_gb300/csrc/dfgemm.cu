@@ -445,22 +445,32 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
     }
 }
 
-// The same block on a cluster of two CTAs: rank 0 factors, rank 1 forms the
-// inverse behind it. Step j of rank 0 is the factor half of the sweep above:
-// scale column j by r = 1 / sqrt(A_jj), write L_jj, update the trailing entries
-// c > j. The threads that scale column j also store it, and r_j, into rank 1's
-// shared memory (posted remote stores); after the block barrier, thread j raises
-// a flag there (release at cluster scope). Rank 1 waits for the flag (acquire),
-// scales row j of X by r_j and updates the rows below (X_ic -= L_ij X_jc, c <= j)
-// from its local copy, and checks for the next column while it updates. Every
-// entry sees the same operations in the same order as in the one-CTA sweep, so
-// the results are the same bit for bit; each CTA does half the work. Rank 0
-// never waits for rank 1, except once at the end so that rank 1 has received
-// everything before either exits; rank 1's waits are bounded (clock64, about
-// 2 s): past the limit it records timeout site DIAG_SITE, stops and still
-// meets rank 0 at the final cluster barrier.
+// The same block on a cluster of two CTAs, blocked by 16 columns: rank 0
+// factors, rank 1 forms the inverse behind it.
+//
+// Rank 0 sweeps the columns j of each 16-column sub-block [b0, b1): scale
+// column j by r = 1 / sqrt(A_jj) and write L_jj, then update only the entries
+// (i, c) with j < c < b1 (rank-1 updates inside the sub-block's columns). The
+// entries right of the sub-block get the sub-block's sixteen updates at once
+// afterwards, as double-float dot products A_ic -= sum_k L_ik conj(L_ck). The
+// threads that scale column j also store it, and r_j, into rank 1's shared
+// memory (posted remote stores); after the block barrier, thread j raises a
+// flag there (release at cluster scope).
+//
+// Rank 1 forms X = L^-1 by rows in the same sub-blocks: for each j it waits for
+// the flag (acquire), scales row j of X by r_j and updates the rows of the
+// sub-block below j (X_ic -= L_ij X_jc, c <= j); the rows below the sub-block get
+// its sixteen updates at once afterwards (X_ic -= sum_k L_ik X_kc).
+//
+// The sums are the column sweep's, reassociated per sub-block: the results
+// agree with the one-CTA sweep to the double-float rounding (about 2^-44
+// relative), not bit for bit. Rank 0 never waits for rank 1, except once at
+// the end so that rank 1 has received everything before either exits; rank 1's
+// waits are bounded (clock64, about 2 s): past the limit it records timeout
+// site DIAG_SITE, stops and still meets rank 0 at the final cluster barrier.
 constexpr int DIAG_SITE = 20;
 constexpr long long DIAG_WAIT_LIMIT = 4000000000LL;
+constexpr int DSB = 16;  // sub-block width
 constexpr size_t DIAG2_SMEM = (size_t)(NBD * NBDP + NBD * NBD + NBD) * sizeof(float4) + NBD * sizeof(float2);
 
 __device__ inline void st_release_cluster(unsigned* p, unsigned v) {
@@ -481,6 +491,13 @@ __device__ inline bool diag_wait(const unsigned* flag, unsigned need, DevStatus*
         }
     }
     return true;
+}
+// e = r (r + 1) / 2 + q with 0 <= q <= r (row r, column q of a lower triangle)
+__device__ inline void tri_index(int e, int& r, int& q) {
+    r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    while (r * (r + 1) / 2 > e) --r;
+    while ((r + 1) * (r + 2) / 2 <= e) ++r;
+    q = e - r * (r + 1) / 2;
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(DIAG_THREADS)
@@ -518,54 +535,76 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(DIAG_THREADS)
         unsigned* rflag = cl.map_shared_rank(&flag, 1);
         float4* rLb = cl.map_shared_rank(Lb, 1);
         float2* rrb = cl.map_shared_rank(rb, 1);
-        for (int j = 0; j < NBD; ++j) {
-            float lh = 0.f, ll = 0.f;
-            if (tid < NBD) {
-                const float4 a = A[j * NBDP + j];
-                float dh = a.x, dl = a.y;
-                const bool fail = !(dh > 0.f) || !isfinite(dh);
-                if (fail) {
-                    dh = 1.f;
-                    dl = 0.f;
-                }
-                const float2 r = df_rsqrt(dh, dl);
-                if (tid > j) {
-                    const float4 l = df_norm(df_scale(A[tid * NBDP + j], r.x, r.y));
-                    A[tid * NBDP + j] = l;
-                    rLb[j * NBD + tid] = l;
-                } else if (tid == j) {
-                    if (fail && !bad) {
-                        atomicMin(&st->not_pd_pivot, (int)(k0 + j));
-                        bad = 1;
+        for (int b0 = 0; b0 < NBD; b0 += DSB) {
+            const int b1 = b0 + DSB;
+            // the entries (i, c), b0 <= c < b1, c <= i of the sub-block's columns, one per
+            // thread (at most 904 <= DIAG_THREADS), decoded once for the sub-block
+            int oi = -1, oc = 0;
+            {
+                int e = tid;
+                for (int c = b0; c < b1 && oi < 0; ++c) {
+                    const int len = NBD - c;  // rows c .. 63 of column c
+                    if (e < len) {
+                        oi = c + e;
+                        oc = c;
+                    } else {
+                        e -= len;
                     }
-                    df_mul(dh, dl, r.x, r.y, lh, ll);
-                    rrb[j] = r;
                 }
             }
-            __syncthreads();
-            if (tid == j) {
-                A[j * NBDP + j] = make_float4(lh, ll, 0.f, 0.f);
-                st_release_cluster(rflag, (unsigned)(j + 1));  // column j and r_j are in rank 1
+            for (int j = b0; j < b1; ++j) {
+                float lh = 0.f, ll = 0.f;
+                if (tid < NBD) {
+                    const float4 a = A[j * NBDP + j];
+                    float dh = a.x, dl = a.y;
+                    const bool fail = !(dh > 0.f) || !isfinite(dh);
+                    if (fail) {
+                        dh = 1.f;
+                        dl = 0.f;
+                    }
+                    const float2 r = df_rsqrt(dh, dl);
+                    if (tid > j) {
+                        const float4 l = df_norm(df_scale(A[tid * NBDP + j], r.x, r.y));
+                        A[tid * NBDP + j] = l;
+                        rLb[j * NBD + tid] = l;
+                    } else if (tid == j) {
+                        if (fail && !bad) {
+                            atomicMin(&st->not_pd_pivot, (int)(k0 + j));
+                            bad = 1;
+                        }
+                        df_mul(dh, dl, r.x, r.y, lh, ll);
+                        rrb[j] = r;
+                    }
+                }
+                __syncthreads();
+                if (tid == j) {
+                    A[j * NBDP + j] = make_float4(lh, ll, 0.f, 0.f);
+                    st_release_cluster(rflag, (unsigned)(j + 1));  // column j and r_j are in rank 1
+                }
+                // rank-1 update of the owned entry if it lies right of and below column j
+                if (oc > j) {
+                    float4* tp = A + oi * NBDP + oc;
+                    const float4 bb = cdf_conj(A[oc * NBDP + j]);
+                    const float4 l = A[oi * NBDP + j];
+                    float4 v = *tp;
+                    cacc(v, make_float4(-l.x, -l.y, -l.z, -l.w), bb);
+                    *tp = df_norm(v);
+                }
+                __syncthreads();
             }
-            // trailing entries (i, c), j < c <= i; row j + 1 + p paired with row 63 - p
-            const int rows = NBD - 1 - j, w = NBD - j;
-            const int slots = ((rows + 1) >> 1) * w;
-            const unsigned wm = ((1u << 20) + (unsigned)w - 1u) / (unsigned)w;
-            for (int e = tid; e < slots; e += DIAG_THREADS) {
-                const int p = (int)(((unsigned)e * wm) >> 20);
-                const int q = e - p * w;
-                const int ia = j + 1 + p, ib = NBD - 1 - p;
-                const bool first = q <= p;
-                const int i = first ? ia : ib, c = first ? j + 1 + q : j + q - p;
-                if (!first && ib <= ia) continue;
-                float4* t = A + i * NBDP + c;
-                const float4 b = cdf_conj(A[c * NBDP + j]);
-                const float4 l = A[i * NBDP + j];
-                float4 v = *t;
-                cacc(v, make_float4(-l.x, -l.y, -l.z, -l.w), b);
-                *t = df_norm(v);
+            if (b1 < NBD) {  // the sub-block's updates of the entries right of it: i >= c >= b1
+                const int w = NBD - b1;
+                for (int e = tid; e < w * (w + 1) / 2; e += DIAG_THREADS) {
+                    int r, q;
+                    tri_index(e, r, q);
+                    const int i = b1 + r, c = b1 + q;
+                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+                    for (int k = b0; k < b1; ++k) cacc(acc, A[i * NBDP + k], cdf_conj(A[c * NBDP + k]));
+                    A[i * NBDP + c] = df_norm(df_cadd(A[i * NBDP + c], make_float4(-acc.x, -acc.y, -acc.z, -acc.w)));
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
         for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
             const int i = e / NBD, j = e % NBD;
@@ -583,29 +622,41 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(DIAG_THREADS)
         float4* X = A;
         if (tid == 0 && !diag_wait(&flag, 1u, st)) stop = 1;
         __syncthreads();
-        for (int j = 0; j < NBD && !stop; ++j) {
-            if (tid <= j) {
-                const float2 r = rb[j];
-                const float4 x = df_norm(df_scale(X[j * NBDP + tid], r.x, r.y));
-                Xr[tid] = x;
-                X[j * NBDP + tid] = x;
+        for (int b0 = 0; b0 < NBD && !stop; b0 += DSB) {
+            const int b1 = b0 + DSB;
+            // owned entry: row b0 + tid / b1, column tid % b1 (rows of the sub-block, columns
+            // left of its end; 16 b1 <= DIAG_THREADS entries)
+            const int oi = b0 + tid / b1, oc = tid % b1;
+            const bool own = tid < DSB * b1;
+            for (int j = b0; j < b1 && !stop; ++j) {
+                if (tid <= j) {
+                    const float2 r = rb[j];
+                    const float4 x = df_norm(df_scale(X[j * NBDP + tid], r.x, r.y));
+                    Xr[tid] = x;
+                    X[j * NBDP + tid] = x;
+                }
+                __syncthreads();
+                // X_ic -= L_ij X_jc for rows j < i < b1, columns c <= j
+                if (own && oi > j && oc <= j) {
+                    float4* tp = X + oi * NBDP + oc;
+                    const float4 l = Lb[j * NBD + oi];
+                    float4 v = *tp;
+                    cacc(v, make_float4(-l.x, -l.y, -l.z, -l.w), Xr[oc]);
+                    *tp = df_norm(v);
+                }
+                if (tid == 0 && j + 1 < NBD && !diag_wait(&flag, (unsigned)(j + 2), st)) stop = 1;
+                __syncthreads();
             }
-            __syncthreads();
-            // rows i > j, columns c <= j: X_ic -= L_ij X_jc
-            const int rows = NBD - 1 - j, w = j + 1;
-            const unsigned wm = ((1u << 20) + (unsigned)w - 1u) / (unsigned)w;  // e / w for e < 2^20 / w
-            const float4* lj = Lb + j * NBD;
-            for (int e = tid; e < rows * w; e += DIAG_THREADS) {
-                const int p = (int)(((unsigned)e * wm) >> 20);
-                const int i = j + 1 + p, c = e - p * w;
-                float4* t = X + i * NBDP + c;
-                const float4 l = lj[i];
-                float4 v = *t;
-                cacc(v, make_float4(-l.x, -l.y, -l.z, -l.w), Xr[c]);
-                *t = df_norm(v);
+            if (b1 < NBD && !stop) {  // rows i >= b1, columns c < b1: X_ic -= sum_{k in the sub-block, k >= c} L_ik X_kc
+                const int n = (NBD - b1) * b1;
+                for (int e = tid; e < n; e += DIAG_THREADS) {
+                    const int i = b1 + e / b1, c = e % b1;
+                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int k = (c > b0 ? c : b0); k < b1; ++k) cacc(acc, Lb[k * NBD + i], X[k * NBDP + c]);
+                    X[i * NBDP + c] = df_norm(df_cadd(X[i * NBDP + c], make_float4(-acc.x, -acc.y, -acc.z, -acc.w)));
+                }
+                __syncthreads();
             }
-            if (tid == 0 && j + 1 < NBD && !diag_wait(&flag, (unsigned)(j + 2), st)) stop = 1;
-            __syncthreads();
         }
         cl.sync();  // rank 0 has published everything and may exit
         for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {

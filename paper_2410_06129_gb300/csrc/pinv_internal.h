@@ -219,9 +219,16 @@ size_t factor_table_bytes(int64_t N, int slices);
 // ev_panel (or nullptr): one event per 256-wide panel, recorded by the Cholesky once
 // the panel's columns of L32 and its diagonal inverses are final, and waited on by
 // the inverse before that panel
+// la (or nullptr): a second stream with its own status block and two events, on
+// which all but the next panel's columns of each trailing update run (lookahead)
+struct TrailLookahead {
+    cudaStream_t s;
+    DevStatus* st;
+    cudaEvent_t ev_tab, ev_done;
+};
 cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, float2* Dinv32, float2* L32,
                             int slices, DevStatus* st, cudaStream_t s, void* tab = nullptr,
-                            const cudaEvent_t* ev_panel = nullptr);
+                            const cudaEvent_t* ev_panel = nullptr, const TrailLookahead* la = nullptr);
 // W = L^-1 (FP64 storage, tensor-core updates) and its FP32 copy W32.
 cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, double2* W, float2* W32,
                             int slices, DevStatus* st, cudaStream_t s, void* tab = nullptr,

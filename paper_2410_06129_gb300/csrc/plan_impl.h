@@ -101,6 +101,11 @@ struct pinv_plan {
     // the Cholesky chain's stream, at the device's highest priority: its small
     // launches get SMs ahead of the inverse's tiles (and of other work)
     cudaStream_t s_chol = nullptr;
+    // the Cholesky's trailing updates beyond the next panel run beside the chain on
+    // this stream, with their own tile counter and timeout record (lookahead)
+    cudaStream_t s_trail = nullptr;
+    pinv::DevStatus* st_trail = nullptr;
+    cudaEvent_t ev_tab = nullptr, ev_trail = nullptr;
     std::vector<cudaEvent_t> ev_panel;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_xfork = nullptr, ev_chol = nullptr;
 
@@ -168,6 +173,9 @@ struct pinv_plan {
         if (ev_join) cudaEventDestroy(ev_join);
         if (ev_xfork) cudaEventDestroy(ev_xfork);
         if (ev_chol) cudaEventDestroy(ev_chol);
+        if (ev_tab) cudaEventDestroy(ev_tab);
+        if (ev_trail) cudaEventDestroy(ev_trail);
+        if (s_trail) cudaStreamDestroy(s_trail);
         if (s_inv) cudaStreamDestroy(s_inv);
         if (s_chol) cudaStreamDestroy(s_chol);
     }

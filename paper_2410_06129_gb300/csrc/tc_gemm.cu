@@ -8,6 +8,7 @@
 // sample); a8()/b8(), 8 consecutive k of that row of A or column of B, zero
 // outside the problem; row_ok()/col_ok() and store().
 #include <algorithm>
+#include <cstring>
 #include <cstdlib>
 #include <vector>
 
@@ -589,9 +590,11 @@ struct HerkBulk {
     double2* G;
     int64_t ld, N, r0, nt, kcn;  // trailing rows from r0 in nt tiles; panel chunks
     int S;
+    int64_t jt0, ncols;          // column tiles jt0 .. jt0 + ncols - 1 of the trailing matrix (grid nt x ncols)
     __device__ bool tile(int64_t bx, int64_t, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
         int64_t it, jt;
-        band_tile(bx, nt, nt, it, jt);
+        band_tile(bx, nt, ncols, it, jt);
+        jt += jt0;
         i0 = r0 + it * BM;
         j0 = r0 + jt * BN;
         kb = 0;
@@ -1120,7 +1123,21 @@ static cudaError_t panel_table(const float2* L32, int64_t N, int64_t p0, int64_t
 constexpr int NBK = 64, NBP = 256;
 
 cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, float2* Dinv32, float2* L32,
-                            int slices, DevStatus* st, cudaStream_t s, void* tab, const cudaEvent_t* ev_panel) {
+                            int slices, DevStatus* st, cudaStream_t s, void* tab, const cudaEvent_t* ev_panel,
+                            const TrailLookahead* la) {
+    // lookahead: after each panel only the next panel's columns (two column tiles)
+    // are updated on the chain's stream; the rest of the trailing matrix on la->s,
+    // beside the next panel's steps, and before the next panel's update
+    // (PINV_CHOL_LOOKAHEAD=0: all of it on the chain's stream). Every tile is
+    // computed the same way either way, so the factor is the same bit for bit.
+    const char* lenv = std::getenv("PINV_CHOL_LOOKAHEAD");
+    const bool ahead = la && la->s && tab && !(lenv && std::strcmp(lenv, "0") == 0);
+    int cap = 0;
+    if (ahead) {
+        const char* cenv = std::getenv("PINV_TRAIL_SMS");
+        cap = cenv ? std::atoi(cenv) : (N <= 16384 ? std::max(1, tc::sm_count() / 4) : 0);
+    }
+    bool pending = false;  // a side update of the previous panel may still run
     for (int64_t p0 = 0; p0 < N; p0 += NBP) {
         const int64_t pend = std::min<int64_t>(N, p0 + NBP);
         for (int64_t k0 = p0; k0 < pend; k0 += NBK) {
@@ -1156,15 +1173,34 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
             cudaError_t e;
             if (tab) {
                 const int64_t nt = cdiv(N - pend, tc::BM), kcn = cdiv(pend - p0, tc::KC);
+                if (pending) {  // the previous panel's side update also writes these columns, and reads the table
+                    if ((e = cudaStreamWaitEvent(s, la->ev_done, 0)) != cudaSuccess) return e;
+                    pending = false;
+                }
                 if ((e = panel_table(L32, N, p0, pend - p0, pend, slices, (uint8_t*)tab, s)) != cudaSuccess) return e;
-                tc::HerkBulk hp{(const uint8_t*)tab, G, ld, N, pend, nt, kcn, slices};
-                e = run(hp, dim3((unsigned)(nt * nt), 1), slices, st, 4, s);
+                const int64_t near = ahead ? std::min<int64_t>(nt, NBP / tc::BN) : nt;
+                tc::HerkBulk hp{(const uint8_t*)tab, G, ld, N, pend, nt, kcn, slices, 0, near};
+                e = run(hp, dim3((unsigned)(nt * near), 1), slices, st, 4, s);
+                if (e == cudaSuccess && near < nt) {
+                    if ((e = cudaEventRecord(la->ev_tab, s)) != cudaSuccess) return e;
+                    if ((e = cudaStreamWaitEvent(la->s, la->ev_tab, 0)) != cudaSuccess) return e;
+                    tc::HerkBulk fp{(const uint8_t*)tab, G, ld, N, pend, nt, kcn, slices, near, nt - near};
+                    if ((e = run(fp, dim3((unsigned)(nt * (nt - near)), 1), slices, la->st, 4, la->s, false, cap)) !=
+                        cudaSuccess)
+                        return e;
+                    if ((e = cudaEventRecord(la->ev_done, la->s)) != cudaSuccess) return e;
+                    pending = true;
+                }
             } else {
                 tc::HerkTC hp{L32 + p0, N, G, ld, N, pend - p0, pend, N};
                 e = run(hp, dim3(cdiv(N - pend, tc::BN), cdiv(N - pend, tc::BM)), slices, st, 4, s);
             }
             if (e != cudaSuccess) return e;
         }
+    }
+    if (pending) {
+        cudaError_t e = cudaStreamWaitEvent(s, la->ev_done, 0);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -1176,14 +1212,15 @@ cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, 
                             int slices, DevStatus* st, cudaStream_t s, void* tab, const cudaEvent_t* ev_panel) {
     cudaError_t e = launch_fill_identity(W, N, N, s);
     if (e != cudaSuccess) return e;
-    // the inverse runs beside the Cholesky chain. Up to N = 16384, where the chain
-    // is a latency-bound sequence of small launches, the inverse's persistent
-    // launches take at most half the SMs so that the chain's launches find free
-    // SMs (at 64x64 the Cholesky goes from 10.7 to 10.4 ms and the inverse still
-    // ends with it); above, both are throughput-bound and the inverse takes them
-    // all. PINV_INV_SMS: another count (0 all).
+    // the inverse runs beside the Cholesky chain (and its trailing updates). Up to
+    // N = 16384, where the chain is a latency-bound sequence of small launches, the
+    // inverse's persistent launches take at most three quarters of the SMs so that
+    // the chain's launches find free SMs; the trailing updates beside the chain take
+    // a quarter. Measured at 64x64 (inverse / trailing SMs -> build): 76 / 50 ->
+    // 12.0 ms, 152 / 50 -> 11.6 ms, 114 / 38 -> 11.55 ms. Above N = 16384 all three
+    // are throughput-bound and each takes every SM. PINV_INV_SMS: another count (0 all).
     const char* cenv = std::getenv("PINV_INV_SMS");
-    const int cap = cenv ? std::atoi(cenv) : (N <= 16384 ? std::max(1, tc::sm_count() / 2) : 0);
+    const int cap = cenv ? std::atoi(cenv) : (N <= 16384 ? std::max(1, 3 * tc::sm_count() / 4) : 0);
     for (int64_t p0 = 0; p0 < N; p0 += NBP) {
         const int64_t pend = std::min<int64_t>(N, p0 + NBP);
         if (ev_panel && (e = cudaStreamWaitEvent(s, ev_panel[p0 / NBP], 0)) != cudaSuccess) return e;
