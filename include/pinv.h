@@ -149,9 +149,10 @@ typedef struct {
      * exactly (from G before the Cholesky, or from the exact Gram of TOEPLITZ
      * plans), ||G^-1||_1 by Hager's method (Higham's complex variant, at most
      * five rounds and an alternating-sign vector) with solves through the
-     * factor. Mixed plans certify the final candidates y against G itself
-     * (||y||_1 / ||G y||_1, G y by the refinement's residual operator), so the
-     * estimate is a lower bound of kappa_1(G) up to the rounding of the sums
+     * factor. Mixed plans refine the two final candidates y once against G and
+     * then certify them against G itself (||y||_1 / ||G y||_1, G y by the
+     * refinement's residual operator), so the estimate is a lower bound of
+     * kappa_1(G) up to the rounding of the sums
      * (mixed plans without the TOEPLITZ residual read ||G||_1 from the
      * split-precision Gram, so it carries that Gram's rounding).
      * Hager's estimates are usually within a factor of 3. NaN when G was not
