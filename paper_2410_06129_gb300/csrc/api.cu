@@ -112,6 +112,17 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
         CK(launch_gram_norm1(nullptr, p->Gx, N, N, p->st, sx));
         if (p->Gd) CK(launch_gram_digits(p->Gx, N, p->eG, p->Gd, sx));
         if (p->Ad) CK(launch_adj_digits(p->enc, p->Ad, sx));
+    } else if (p->Ad || p->Af) {
+        // plans with B0: the digit tables of conj(A) and A for the exact products of
+        // the refinement, formed beside the Cholesky (build_factor joins that stream)
+        cudaStream_t sx = s;
+        if (p->s_inv) {
+            CK(cudaEventRecord(p->ev_xfork, s));
+            CK(cudaStreamWaitEvent(p->s_inv, p->ev_xfork, 0));
+            sx = p->s_inv;
+        }
+        if (p->Ad) CK(launch_adj_digits(p->enc, p->Ad, sx));
+        if (p->Af) CK(launch_fwd_digits(p->enc, p->Af, sx));
     }
     return PINV_OK;
 }
@@ -529,6 +540,29 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
                 AL(p->Ad, adj_digit_bytes(e), "E^H digits");
         }
         AL(p->eG, sizeof(int), "exact Gram exponent");
+    }
+    if (p->precision != PINV_FP64 && !p->lean && e.b0df && p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT) {
+        // digits of conj(A) and of A for the exact E^H d and E x of the refinement
+        // (48 bytes per entry of A). Without room for them the plan keeps the
+        // double-float products (PINV_B0_EXACT=0: always).
+        const char* env = std::getenv("PINV_B0_EXACT");
+        if (!(env && std::strcmp(env, "0") == 0)) {
+            void *ad = nullptr, *af = nullptr;
+            const size_t ba = adj_digit_bytes(e), bf = fwd_digit_bytes(e);
+            if (work_alloc(&ad, ba, 0) == cudaSuccess && work_alloc(&af, bf, 0) == cudaSuccess &&
+                cudaStreamSynchronize(0) == cudaSuccess) {
+                p->Ad = (uint8_t*)ad;
+                p->Af = (uint8_t*)af;
+                p->allocs.push_back(ad);
+                p->allocs.push_back(af);
+                p->bytes += ba + bf;
+            } else {
+                cudaGetLastError();
+                if (ad) cudaFreeAsync(ad, 0);
+                if (af) cudaFreeAsync(af, 0);
+                cudaStreamSynchronize(0);
+            }
+        }
     }
     int rm = d->recon_mode;
     if (rm == PINV_RECON_AUTO) {

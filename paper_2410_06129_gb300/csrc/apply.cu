@@ -89,16 +89,23 @@ size_t apply_scratch_layout(const pinv_plan* p, int64_t F, int dtype, void* base
         // E^H u (rows N, length M), E x (rows M, length N), G x (rows N, length N),
         // and the exact tensor-core E^H d
         size_t w = std::max(df_work_elems(N, F, M), std::max(df_work_elems(M, F, N), df_work_elems(N, F, N)));
-        const bool xadj = md.need_b && exact_adjoint_ok(p->enc, F);
+        const bool xadj = md.need_b && exact_adjoint_ok(p->enc, F, p->Ad != nullptr);
         const bool xres = md.toep && md.refine && p->Gd;
-        if (xadj) w = std::max(w, exact_work_elems(p->enc, F));
+        // plans with B0 and the digit tables: E x and E^H u of every residual exactly
+        const bool xfwd = md.dfres && md.refine && p->Af && p->Ad && exact_adjoint_ok(p->enc, F, true);
+        if (xadj || xfwd) w = std::max(w, exact_work_elems(p->enc, F));
         if (xres) w = std::max(w, resid_exact_work_elems(N, F));
-        if (xadj || xres) {
+        if (xfwd) w = std::max(w, exact_fwd_work_elems(p->enc, F));
+        if (xadj || xres || xfwd) {
             s.fexp = cv.take<int>((size_t)F);
-            s.xbd = cv.take<uint8_t>(std::max(xadj ? exact_bdigit_bytes(p->enc, F) : 0,
-                                              xres ? resid_bdigit_bytes(N, F) : 0));
+            size_t bd = std::max(xadj || xfwd ? exact_bdigit_bytes(p->enc, F) : 0,
+                                 xres ? resid_bdigit_bytes(N, F) : 0);
+            if (xfwd) bd = std::max(bd, exact_fwd_bdigit_bytes(p->enc, F));
+            s.xbd = cv.take<uint8_t>(bd);
         }
+        if (xfwd) s.y128 = cv.take<double2>(exact_fwd_y_elems(p->enc, F));
         s.xadj = xadj;
+        s.xfwd = xfwd;
         s.dfw = w ? cv.take<float4>(w) : nullptr;
     }
     if (sc) *sc = s;
@@ -191,6 +198,10 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
                 CKA(launch_gram_resid_exact(p->Gd, p->eG, N, sc.b128, X, F, sc.fexp, sc.xbd, sc.r128, sc.dfw, p->st, s));
             } else if (md.toep) {
                 CKA(launch_gram_resid_df(p->Gx, N, sc.b128, X, F, sc.r128, s, sc.dfw));  // r = b - G x
+            } else if (md.dfres && sc.xfwd) {  // u = d - E x, r = E^H u - lambda x, exact digit products
+                CKA(launch_forward_exact(p->enc, X, F, D, sc.u128, p->Af, sc.y128, sc.fexp, sc.xbd, sc.dfw, p->st, s));
+                CKA(launch_adjoint_exact(p->enc, sc.u128, F, sc.fexp, sc.xbd, sc.r128, sc.dfw, p->st, s, p->Ad));
+                CKA(launch_minus_lambda(sc.r128, X, p->lambda_abs, F * N, s));
             } else if (md.dfres) {
                 CKA(launch_forward_df(p->enc, X, F, D, sc.u128, s, sc.dfw));  // u = d - E x
                 CKA(launch_adjoint_df(p->enc, sc.u128, F, p->lambda_abs, X, sc.r128, s, sc.dfw));

@@ -520,9 +520,14 @@ pinv_status build_condition(pinv_plan* p, cudaStream_t s) {
     k_hg_vecs<<<vb, 256, 0, s>>>(h, x, V2, N);
     note_launch();
     const bool toep = p->refine_residual == PINV_RESIDUAL_TOEPLITZ;
+    // plans with B0 and the digit tables of A and conj(A): E y and E^H u exactly on
+    // the tensor cores (two frames in one 32-frame tile), far cheaper here than the
+    // double-float products at two right-hand sides
+    const bool xb0 = !toep && p->Af && p->Ad;
     float4* work = nullptr;
     uint8_t* bd = nullptr;
     int* fexp = nullptr;
+    double2* Yb = nullptr;
     CKC(take((void**)&zero, sizeof(double2) * 2 * (toep ? N : M)));
     CKC(cudaMemsetAsync(zero, 0, sizeof(double2) * 2 * (toep ? N : M), s));
     if (toep && p->Gd) {
@@ -532,6 +537,13 @@ pinv_status build_condition(pinv_plan* p, cudaStream_t s) {
         if (wel) CKC(take((void**)&work, sizeof(float4) * wel));
     } else if (toep) {
         const size_t wel = df_work_elems(N, 2, N);
+        if (wel) CKC(take((void**)&work, sizeof(float4) * wel));
+    } else if (xb0) {
+        const size_t wel = std::max(exact_work_elems(p->enc, 2), exact_fwd_work_elems(p->enc, 2));
+        CKC(take((void**)&U2, sizeof(double2) * 2 * M));
+        CKC(take((void**)&fexp, sizeof(int) * 2));
+        CKC(take((void**)&bd, std::max(exact_bdigit_bytes(p->enc, 2), exact_fwd_bdigit_bytes(p->enc, 2))));
+        CKC(take((void**)&Yb, sizeof(double2) * exact_fwd_y_elems(p->enc, 2)));
         if (wel) CKC(take((void**)&work, sizeof(float4) * wel));
     } else {
         const size_t wel = std::max(df_work_elems(M, 2, N), df_work_elems(N, 2, M));
@@ -544,7 +556,14 @@ pinv_status build_condition(pinv_plan* p, cudaStream_t s) {
         if (toep && p->Gd) return launch_gram_resid_exact(p->Gd, p->eG, N, B ? B : zero, X, 2, fexp, bd, R, work,
                                                           p->st, s);
         if (toep) return launch_gram_resid_df(p->Gx, N, B ? B : zero, X, 2, R, s, work);
-        if (p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT) {
+        if (xb0) {
+            if ((e = launch_forward_exact(p->enc, X, 2, nullptr, U2, p->Af, Yb, fexp, bd, work, p->st, s)) !=
+                cudaSuccess)  // U = -E X
+                return e;
+            if ((e = launch_adjoint_exact(p->enc, U2, 2, fexp, bd, R, work, p->st, s, p->Ad)) != cudaSuccess)
+                return e;  // R = E^H U
+            if ((e = launch_minus_lambda(R, X, p->lambda_abs, 2 * N, s)) != cudaSuccess) return e;
+        } else if (p->refine_residual == PINV_RESIDUAL_DOUBLE_FLOAT) {
             if ((e = launch_forward_df(p->enc, X, 2, zero, U2, s, work)) != cudaSuccess) return e;  // U = -E X
             if ((e = launch_adjoint_df(p->enc, U2, 2, p->lambda_abs, X, R, s, work)) != cudaSuccess) return e;
         } else {

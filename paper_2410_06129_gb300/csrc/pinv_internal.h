@@ -284,10 +284,11 @@ cudaError_t launch_gram_norm1(const double2* G, const float4* Gx, int64_t N, int
 // df_work_elems() partials (float4) when the split count is above one
 size_t df_work_elems(int64_t rows, int64_t F, int64_t K);
 
-// E^H d exactly on the tensor cores (fixed-point digits; B0-free plans, F >= 16).
+// E^H d exactly on the tensor cores (fixed-point digits; F >= 16; plans with B0
+// only with the per-build table of conj(A), table = true).
 // fexp: [F] per-frame exponents (written here); Bd: exact_bdigit_bytes() for the
 // data's digit tiles (written here); work: partials.
-bool exact_adjoint_ok(const EncodeDev& e, int64_t F);
+bool exact_adjoint_ok(const EncodeDev& e, int64_t F, bool table);
 size_t exact_work_elems(const EncodeDev& e, int64_t F);
 size_t exact_bdigit_bytes(const EncodeDev& e, int64_t F);
 // Ad (or nullptr): the digits of conj(A) in tile layout (adj_digit_bytes(), written
@@ -299,6 +300,22 @@ cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F
                                  const uint8_t* Ad = nullptr);
 cudaError_t launch_transpose_df(const float4* src, int64_t rows, int64_t cols, float4* dst, int64_t ldd,
                                 cudaStream_t s);
+
+// U = D - E X exactly on the tensor cores (D may be null: U = -E X), from the
+// per-build digit table of A (fwd_digit_bytes(), launch_fwd_digits; rows of 128
+// samples, k = voxels); Y: exact_fwd_y_elems() FP64 scratch for s_c o x, fexp [F],
+// Bd: exact_fwd_bdigit_bytes(), work: exact_fwd_work_elems() partials (F >= 16,
+// as exact_adjoint_ok).
+size_t fwd_digit_bytes(const EncodeDev& e);
+cudaError_t launch_fwd_digits(const EncodeDev& e, uint8_t* Af, cudaStream_t s);
+size_t exact_fwd_work_elems(const EncodeDev& e, int64_t F);
+size_t exact_fwd_bdigit_bytes(const EncodeDev& e, int64_t F);
+size_t exact_fwd_y_elems(const EncodeDev& e, int64_t F);
+cudaError_t launch_forward_exact(const EncodeDev& e, const double2* X, int64_t F, const double2* D, double2* U,
+                                 const uint8_t* Af, double2* Y, int* fexp, uint8_t* Bd, float4* work,
+                                 DevStatus* st, cudaStream_t s);
+// R -= lam X over n entries (FP64)
+cudaError_t launch_minus_lambda(double2* R, const double2* X, double lam, int64_t n, cudaStream_t s);
 
 // Recon x data (c64) on the tensor cores, split-BF16, for F >= 16 frames (in
 // chunks of 128); the sample range is split over tiles with FP32 partials in `work`.

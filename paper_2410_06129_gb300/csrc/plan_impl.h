@@ -27,6 +27,8 @@ struct ApplyScratch {
     int* fexp;      // per-frame exponents of the data / image [F] (exact tensor-core products)
     uint8_t* xbd;   // digit tiles of their B operand
     bool xadj;      // E^H d by the exact tensor-core kernel
+    bool xfwd;      // the residual's E x and E^H u by the exact tensor-core kernels (plans with B0)
+    double2* y128;  // s_c o x [F][C][N] for the exact E x
     float2* apw;    // partials of the tensor-core Recon x data
     float2* cw;     // partials of the tensor-core correction x += W^H (W r)
     DevStatus* sched;  // tile counter of those launches: one per scratch region, since
@@ -90,7 +92,8 @@ struct pinv_plan {
     double2* Ttab = nullptr;   // Toeplitz table of A^H A (TOEPLITZ residual)
     float4* Gx = nullptr;      // exact Gram, double-float [N][N] (TOEPLITZ residual)
     uint8_t* Gd = nullptr;     // its fixed-point digit tiles for the tensor-core residual
-    uint8_t* Ad = nullptr;     // digit tiles of conj(A) for the exact E^H d (mixed, B0-free, not lean)
+    uint8_t* Ad = nullptr;     // digit tiles of conj(A) for the exact E^H d (mixed, not lean)
+    uint8_t* Af = nullptr;     // digit tiles of A for the exact E x (mixed with B0, not lean)
     int* eG = nullptr;         // |G| <= 2^eG (device)
     pinv::DevStatus* st = nullptr;        // device status word
     pinv::DevStatus* st_host = nullptr;   // pinned copy, written at the end of each build

@@ -27,8 +27,16 @@
 // by side, as in the split-BF16 engine); the sample range is split over CTAs
 // and the double-float partials reduced in a fixed order. One MMA takes an A
 // digit against up to four B digits stacked along N (N <= 256), so a stage's 21
-// digit pairs cost 8 MMAs per 16-deep k half. Plans without B0 only (E from the
-// separable phase tables and coil maps).
+// digit pairs cost 8 MMAs per 16-deep k half. The producers form conj(A) from the
+// separable phase tables of plans without B0; plans with B0 copy the digits of
+// conj(A) (with its B0 factor) from a per-build table.
+//
+// The forward product E x (XFWD) runs the same way with the roles of samples and
+// voxels exchanged: the A operand is a per-build table of the digits of A itself
+// (rows of 128 samples, k = voxels), the B operand the digits of s_c(n) x[f][n]
+// per coil, and each coil's samples get their own partial sums, reduced into
+// u = d - E x. With both, the refinement residual r = E^H (d - E x) - lambda x of
+// plans with B0 runs on the tensor cores too.
 //
 // The digits of the B operand (data, or x) are written once per call by
 // k_b_digits. The digits of the A operand either come from the producer warps
@@ -133,7 +141,11 @@ __device__ inline void gen_ah8(const EncodeDev& e, int64_t n, int64_t m, int64_t
     float4 v[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (n < e.N && m < mend) {  // m is a multiple of 8 below M_k, so m + 7 < Mkp
+    if (e.b0df) {  // A with its B0 factor, element by element from the double-float tables
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            if (n < e.N && m + t < mend) v[t] = gen_a_df(e, m + t, n);
+    } else if (n < e.N && m < mend) {  // m is a multiple of 8 below M_k, so m + 7 < Mkp
         const int* g = e.vox_ijk + 3 * n;
         const float4* px = e.extdf + (int64_t)g[0] * e.Mkp + m;
 #pragma unroll
@@ -160,7 +172,7 @@ __device__ inline void gen_ah8(const EncodeDev& e, int64_t n, int64_t m, int64_t
 }
 
 // A operand of the exact kernel
-enum XMode { XGEN = 0, XGRAM = 1, XADJT = 2 };
+enum XMode { XGEN = 0, XGRAM = 1, XADJT = 2, XFWD = 3 };
 
 // Digits of conj(A) for one (voxel tile, 16-sample chunk): NDIG slices of 8 KiB in
 // the stage layout, exactly as the XGEN producers write them to shared memory.
@@ -181,6 +193,49 @@ __global__ void __launch_bounds__(256) k_adj_digits(EncodeDev e, int64_t KB, uin
         di.next(w, 0u);
         *reinterpret_cast<uint4*>(blk + dg * XA_SL + koff(ra, ga + 2)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
+}
+
+// Digits of A itself for one (128-sample tile, 16-voxel chunk), the A operand of
+// the forward product: row r = sample rb * 128 + r, k = voxels kb * 16 .. + 15.
+__global__ void __launch_bounds__(256) k_fwd_digits(EncodeDev e, int64_t KB, uint8_t* Af) {
+    const int64_t kb = blockIdx.x, rb = blockIdx.y;
+    const int ra = threadIdx.x & (XM - 1), ga = threadIdx.x >> 7;
+    const int64_t m = rb * XM + ra, n0 = kb * XKC + 8 * ga;
+    float reh[8], rel[8], imh[8], iml[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (m < e.Mk && n0 + t < e.N) v = gen_a_df(e, m, n0 + t);
+        reh[t] = v.x;
+        rel[t] = v.y;
+        imh[t] = v.z;
+        iml[t] = v.w;
+    }
+    Digits8 dr, di;
+    dr.init(reh, rel, 1.f);
+    di.init(imh, iml, 1.f);
+    uint8_t* blk = Af + (rb * KB + kb) * (int64_t)(NDIG * XA_SL);
+#pragma unroll
+    for (int dg = 0; dg < NDIG; ++dg) {
+        uint32_t w[4];
+        dr.next(w, 0u);
+        *reinterpret_cast<uint4*>(blk + dg * XA_SL + koff(ra, ga)) = make_uint4(w[0], w[1], w[2], w[3]);
+        di.next(w, 0u);
+        *reinterpret_cast<uint4*>(blk + dg * XA_SL + koff(ra, ga + 2)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Y[f][c][n] = s_c(n) x[f][n] in double-float (FP64 in and out), the forward
+// product's B operand before its digits
+__global__ void k_coil_times(EncodeDev e, const double2* X, int64_t F, double2* Y) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= F * e.C * e.N) return;
+    const int64_t n = idx % e.N, fc = idx / e.N;
+    const int c = (int)(fc % e.C);
+    const int64_t f = fc / e.C;
+    float4 v = to_df_i(X[f * e.N + n]);
+    if (e.coilsdf) v = cdf_mul(v, e.coilsdf[(int64_t)c * e.N + n]);
+    Y[idx] = from_df(v);
 }
 
 // Digits of the B operand (data d, or x for the Gram residual) for one (32-frame
@@ -237,6 +292,7 @@ __global__ void __launch_bounds__(256) k_b_digits(const double2* D, int64_t ld, 
 template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
     constexpr bool GRAM = MODE == XGRAM;
+    constexpr bool FWD = MODE == XFWD;
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[XSTAGES], empty_bar[XSTAGES];
     __shared__ uint64_t abar[XSTAGES];  // the stage's bulk copies (their bytes)
@@ -245,7 +301,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
     __shared__ int abort_flag;
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t N = a.e.N;
+    // output rows (voxels; samples of one coil for the forward product)
+    const int64_t N = FWD ? a.e.Mk : a.e.N;
     const int64_t FT = (a.F + XN - 1) / XN, RB = (N + XM - 1) / XM;
     int64_t lin = blockIdx.x;
     const int64_t ft = lin % FT;
@@ -256,8 +313,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
     const int split = (int)(lin / RB);
     const int64_t zpart = (int64_t)coil * a.sub + split;  // partial slot
     const int64_t n0 = rb * XM, f0 = ft * XN;
-    // k range [mb, me): adjoint samples inside coil `coil`, or Gram columns
-    const int64_t Mk = GRAM ? N : a.e.Mk;
+    // k range [mb, me): adjoint samples inside coil `coil`, Gram columns, or the
+    // voxels of the forward product
+    const int64_t Mk = GRAM ? N : (FWD ? a.e.N : a.e.Mk);
     const int64_t mb = (int64_t)split * a.chunk;
     const int64_t me = mb + a.chunk < Mk ? mb + a.chunk : Mk;
     const int nk = me > mb ? (int)((me - mb + XKC - 1) / XKC) : 0;
@@ -373,7 +431,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
             const int64_t n = n0 + q * 32 + lane;
             if (n < N) {
                 float4 cs = make_float4(1.f, 0.f, 0.f, 0.f);
-                if (!GRAM && a.e.coilsdf) cs = cdf_conj(a.e.coilsdf[(int64_t)coil * N + n]);
+                if (!GRAM && !FWD && a.e.coilsdf) cs = cdf_conj(a.e.coilsdf[(int64_t)coil * N + n]);
                 const int eA = GRAM ? *a.eG : 0;
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
@@ -381,7 +439,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
                     if (f >= a.F) continue;
                     const float sc = __int_as_float((127 + eA + a.fexp[f]) << 23);
                     float4 v = make_float4(acc[0][u] * sc, acc[1][u] * sc, acc[2][u] * sc, acc[3][u] * sc);
-                    if (!GRAM && a.e.coilsdf) v = cdf_mul(v, cs);
+                    if (!GRAM && !FWD && a.e.coilsdf) v = cdf_mul(v, cs);
                     if (a.part)
                         a.part[(zpart * a.F + f) * N + n] = v;
                     else
@@ -473,6 +531,35 @@ __global__ void k_resid_reduce(const double2* b, const float4* part, int splits,
     }
     const double2 g = from_df(a), bb = b[idx];
     r[idx] = make_double2(bb.x - g.x, bb.y - g.y);
+}
+
+// u[f][c Mk + m] = d[f][c Mk + m] - sum_s part[c sub + s][f][m] (d may be null:
+// u = -E x), the splits of each coil added in order
+__global__ void k_fwd_reduce(const double2* d, const float4* part, int sub, int C, int64_t Mk, int64_t F,
+                             double2* u) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t M = Mk * C;
+    if (idx >= M * F) return;
+    const int64_t f = idx / M, cm = idx % M;
+    const int c = (int)(cm / Mk);
+    const int64_t m = cm % Mk;
+    float4 a = part[(((int64_t)c * sub) * F + f) * Mk + m];
+    for (int z = 1; z < sub; ++z) {
+        const float4 b = part[(((int64_t)c * sub + z) * F + f) * Mk + m];
+        float rh, rl, ih, il;
+        df_add(a.x, a.y, b.x, b.y, rh, rl);
+        df_add(a.z, a.w, b.z, b.w, ih, il);
+        a = make_float4(rh, rl, ih, il);
+    }
+    const double2 g = from_df(a);
+    const double2 dd = d ? d[idx] : make_double2(0.0, 0.0);
+    u[idx] = make_double2(dd.x - g.x, dd.y - g.y);
+}
+
+// r[i] -= lam * x[i] (FP64)
+__global__ void k_minus_lam(double2* r, const double2* x, double lam, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) r[i] = make_double2(r[i].x - lam * x[i].x, r[i].y - lam * x[i].y);
 }
 
 // |G| <= 2^eG from the largest diagonal entry (G Hermitian positive definite)
@@ -606,8 +693,12 @@ static cudaError_t launch_b_digits(const double2* D, int64_t ld, int64_t F, int 
 
 size_t exact_bdigit_bytes(const EncodeDev& e, int64_t F) { return b_digit_bytes(F, e.C, e.Mk); }
 
-bool exact_adjoint_ok(const EncodeDev& e, int64_t F) {
-    return e.extdf && !e.b0df && !e.b0tab && F >= 16 && tc_available();
+bool exact_adjoint_ok(const EncodeDev& e, int64_t F, bool table) {
+    // plans with B0 only from the per-build table of conj(A) (the producers form
+    // A from the separable tables of plans without B0)
+    const bool gen = e.extdf && !e.b0df && !e.b0tab;
+    const bool tab = table && e.b0df && e.exdf;
+    return (gen || tab) && F >= 16 && tc_available();
 }
 
 template <int MODE>
@@ -660,6 +751,64 @@ cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F
     if (err != cudaSuccess || !partials) return err;
     const int64_t n = e.N * F;
     tcx::k_exact_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tcx::BStore{B, e.N}, work, (int)splits, e.N, F);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ exact forward product
+// splits of the voxel range per coil: whole waves of CTAs over all coils
+static int fwd_sub(const EncodeDev& e, int64_t F) {
+    const int64_t tiles = ((e.Mk + tcx::XM - 1) / tcx::XM) * ((F + tcx::XN - 1) / tcx::XN) * e.C;
+    const int hi = (int)std::max<int64_t>(1, std::min<int64_t>(32, e.N / (tcx::XKC * tcx::XDRAIN * 2)));
+    return tc::wave_splits(tiles, e.N, 1, hi, 256);
+}
+
+size_t fwd_digit_bytes(const EncodeDev& e) {
+    const int64_t RB = (e.Mk + tcx::XM - 1) / tcx::XM, KB = (e.N + tcx::XKC - 1) / tcx::XKC;
+    return (size_t)RB * (size_t)KB * (size_t)(tcx::NDIG * tcx::XA_SL);
+}
+
+cudaError_t launch_fwd_digits(const EncodeDev& e, uint8_t* Af, cudaStream_t s) {
+    const int64_t RB = (e.Mk + tcx::XM - 1) / tcx::XM, KB = (e.N + tcx::XKC - 1) / tcx::XKC;
+    tcx::k_fwd_digits<<<dim3((unsigned)KB, (unsigned)RB), 256, 0, s>>>(e, KB, Af);
+    note_launch();
+    return cudaGetLastError();
+}
+
+size_t exact_fwd_work_elems(const EncodeDev& e, int64_t F) {
+    return (size_t)fwd_sub(e, F) * (size_t)e.C * (size_t)F * (size_t)e.Mk;
+}
+size_t exact_fwd_bdigit_bytes(const EncodeDev& e, int64_t F) { return b_digit_bytes(F, e.C, e.N); }
+size_t exact_fwd_y_elems(const EncodeDev& e, int64_t F) { return (size_t)F * (size_t)e.C * (size_t)e.N; }
+
+cudaError_t launch_forward_exact(const EncodeDev& e, const double2* X, int64_t F, const double2* D, double2* U,
+                                 const uint8_t* Af, double2* Y, int* fexp, uint8_t* Bd, float4* work,
+                                 DevStatus* st, cudaStream_t s) {
+    if (F == 0) return cudaSuccess;
+    if (!Af || !Y || !Bd || !work) return cudaErrorInvalidValue;
+    cudaError_t err = exact_attr<tcx::XFWD>();
+    if (err != cudaSuccess) return err;
+    const int64_t ny = F * e.C * e.N;
+    tcx::k_coil_times<<<(unsigned)((ny + 255) / 256), 256, 0, s>>>(e, X, F, Y);  // Y[f][c] = s_c o x_f
+    tcx::k_frame_exp<<<(unsigned)F, 256, 0, s>>>(Y, e.C * e.N, fexp);
+    note_launch(2);
+    if ((err = launch_b_digits(Y, e.C * e.N, F, (int)e.C, e.N, fexp, Bd, s)) != cudaSuccess) return err;
+    const int sub = fwd_sub(e, F);
+    const int64_t chunk = ((e.N + sub - 1) / sub + tcx::XKC - 1) / tcx::XKC * tcx::XKC;
+    const int64_t KB = (e.N + tcx::XKC - 1) / tcx::XKC;
+    tcx::XArgs a{e, Y, fexp, F, e.C * e.N, chunk, sub, work, nullptr, Af, nullptr, KB, Bd, (int)e.C};
+    const dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN * ((e.Mk + tcx::XM - 1) / tcx::XM) * e.C * sub));
+    tcx::k_exact<tcx::XFWD><<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
+    note_launch();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const int64_t n = e.Mk * e.C * F;
+    tcx::k_fwd_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(D, work, sub, (int)e.C, e.Mk, F, U);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_minus_lambda(double2* R, const double2* X, double lam, int64_t n, cudaStream_t s) {
+    tcx::k_minus_lam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(R, X, lam, n);
     note_launch();
     return cudaGetLastError();
 }

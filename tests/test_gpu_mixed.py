@@ -235,3 +235,26 @@ def test_cholesky_lookahead_bit_identical(monkeypatch):
             out[mode] = (pl.export(L.EXPORT_CHOL).cpu(), pl.export(L.EXPORT_LINV).cpu())
     assert torch.equal(out["0"][0], out["1"][0])
     assert torch.equal(out["0"][1], out["1"][1])
+
+
+def test_b0_exact_products_many_frames(monkeypatch):
+    """Plans with B0 refine with exact tensor-core E x and E^H u (digit tables of
+    A and conj(A), 48 bytes per entry) for 16 or more frames. Workload 5 shrunk to
+    32x32 (8 coils, 64 radial spokes x 40 samples, B0 +-50 Hz), 40 frames (a
+    ragged second frame tile): the images reach the oracle's within 1e-6, like the
+    double-float residual's (PINV_B0_EXACT=0), and the plan holds the tables."""
+    p = synth.config(5, reduced=True, frames=40)
+    ref = oracle_all(p)
+    d = torch.from_numpy(p.data).cuda()
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("PINV_B0_EXACT", mode)
+        with _plan(p, precision=L.MIXED_BF16X6, recon_mode=L.RECON_NONE, refine_max_iters=4,
+                   refine_tol=0.0) as pl:
+            pl.build()
+            out[mode] = (pl.apply(d).cpu().numpy(), pl.info())
+    table = 48 * p.n_vox * p.n_samples
+    assert out["1"][1]["bytes_device"] - out["0"][1]["bytes_device"] >= table
+    assert rel(out["1"][0], ref.images) <= 1e-6
+    assert rel(out["0"][0], ref.images) <= 1e-6
+    assert rel(out["1"][0], out["0"][0]) <= 1e-6
