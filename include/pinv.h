@@ -160,6 +160,14 @@ typedef struct {
     double kappa_est;                   /* estimate of kappa_1(G) */
     double norm1_g;                     /* ||G||_1 */
     double ms_cond;                     /* time of the condition estimate in the last build */
+    /* With the refinement's stopping rule (refine_tol > 0) the last apply's
+     * residual r = E^H (d - E x) - lambda x is that of the images returned, and
+     * since every eigenvalue of G is at least lambda (Section 2.2),
+     * ||x - x*|| / ||x|| <= ||r|| / (lambda ||x||) for the exact solution x* of
+     * each frame: the largest of these certified bounds over the frames (0
+     * without the stopping rule). The rule checks each residual before its
+     * correction, so an image already within refine_tol is returned unchanged. */
+    double last_refine_bound;
 } pinv_plan_info_t;
 
 typedef struct pinv_plan pinv_plan;
@@ -428,7 +436,10 @@ pinv_status pinv_tsvd_apply(pinv_plan* plan, const double* d_mu, const void* d_P
  *   16 F N   when refining, or for factor-only plans;
  *    8 F M   for mixed plans with Recon and c128 data;
  *    8 F N   for mixed plans with Recon, or refined with the double-float residual;
- *   16 F     when the refinement's stopping rule (refine_tol > 0) is on.
+ *   24 F     when the refinement's stopping rule (refine_tol > 0) is on;
+ * plus the partial sums and digit tiles of the tensor-core products, and for
+ * plans with B0 that hold the exact-product digit tables, 16 F C N for the
+ * coil-weighted images (the call computes the exact total).
  * A call that needs more fails with PINV_ERR_INVALID_ARG and a message giving
  * the size; split the frames over several calls.
  *

@@ -57,7 +57,7 @@ class PlanInfo(C.Structure):
         ("ms_inverse", C.c_double), ("ms_recon", C.c_double), ("info", C.c_int),
         ("last_refine_iters", C.c_int), ("last_refine_resid", C.c_double),
         ("ms_gram_kernel", C.c_double), ("kappa_est", C.c_double), ("norm1_g", C.c_double),
-        ("ms_cond", C.c_double),
+        ("ms_cond", C.c_double), ("last_refine_bound", C.c_double),
     ]
 
     def as_dict(self) -> dict:

@@ -721,6 +721,7 @@ pinv_status pinv_plan_info(const pinv_plan* p, pinv_plan_info_t* o) {
     o->info = p->info;
     o->last_refine_iters = p->last_refine_iters;
     o->last_refine_resid = p->last_refine_resid;
+    o->last_refine_bound = p->last_refine_bound;
     if (p->built) {
         CK(cudaEventSynchronize(p->ev[5]));
         float t[5] = {0};

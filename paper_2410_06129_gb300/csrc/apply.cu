@@ -79,7 +79,7 @@ size_t apply_scratch_layout(const pinv_plan* p, int64_t F, int dtype, void* base
     s.b128 = md.need_b ? cv.take<double2>((size_t)(F * N)) : nullptr;
     s.d64 = need_d64 ? cv.take<float2>((size_t)(F * M)) : nullptr;
     s.x64 = need_x64 ? cv.take<float2>((size_t)(F * N)) : nullptr;
-    s.norms = md.stop_rule ? cv.take<double>((size_t)(2 * F)) : nullptr;
+    s.norms = md.stop_rule ? cv.take<double>((size_t)(3 * F)) : nullptr;
     const bool atc = md.mixed && p->recon && apply_tc_ok(F);
     const bool ctc = md.mixed && (md.dfres || md.toep || !p->recon) && correct_tc_ok(F);
     if (atc) s.apw = cv.take<float2>(apply_tc_work_elems(N, M, F));
@@ -128,6 +128,7 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
     const ApplyModes md = apply_modes(p);
     p->last_refine_iters = 0;
     p->last_refine_resid = 0;
+    p->last_refine_bound = 0;
 
     // FP64 view of the data
     const double2* D = nullptr;
@@ -193,23 +194,67 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
                 CKA(launch_frame_norms(sc.r128, F, N, sc.norms + F, s));
             }
         }
-        for (int it = 0; it < p->refine_iters; ++it) {
-            if (md.toep && p->Gd) {  // r = b - G x, exactly on the tensor cores
-                CKA(launch_gram_resid_exact(p->Gd, p->eG, N, sc.b128, X, F, sc.fexp, sc.xbd, sc.r128, sc.dfw, p->st, s));
-            } else if (md.toep) {
-                CKA(launch_gram_resid_df(p->Gx, N, sc.b128, X, F, sc.r128, s, sc.dfw));  // r = b - G x
-            } else if (md.dfres && sc.xfwd) {  // u = d - E x, r = E^H u - lambda x, exact digit products
-                CKA(launch_forward_exact(p->enc, X, F, D, sc.u128, p->Af, sc.y128, sc.fexp, sc.xbd, sc.dfw, p->st, s));
-                CKA(launch_adjoint_exact(p->enc, sc.u128, F, sc.fexp, sc.xbd, sc.r128, sc.dfw, p->st, s, p->Ad));
-                CKA(launch_minus_lambda(sc.r128, X, p->lambda_abs, F * N, s));
-            } else if (md.dfres) {
-                CKA(launch_forward_df(p->enc, X, F, D, sc.u128, s, sc.dfw));  // u = d - E x
-                CKA(launch_adjoint_df(p->enc, sc.u128, F, p->lambda_abs, X, sc.r128, s, sc.dfw));
-            } else {
-                CKA(launch_forward64(p->enc, X, F, D, sc.u128, s));
-                CKA(launch_adjoint64(p->enc, sc.u128, F, p->lambda_abs, X, sc.r128, s));
+        // r = E^H (d - E x) - lambda x (= b - G x) of the current x into sc.r128
+        auto residual = [&]() -> cudaError_t {
+            cudaError_t e;
+            if (md.toep && p->Gd)  // r = b - G x, exactly on the tensor cores
+                return launch_gram_resid_exact(p->Gd, p->eG, N, sc.b128, X, F, sc.fexp, sc.xbd, sc.r128, sc.dfw,
+                                               p->st, s);
+            if (md.toep) return launch_gram_resid_df(p->Gx, N, sc.b128, X, F, sc.r128, s, sc.dfw);  // r = b - G x
+            if (md.dfres && sc.xfwd) {  // u = d - E x, r = E^H u - lambda x, exact digit products
+                if ((e = launch_forward_exact(p->enc, X, F, D, sc.u128, p->Af, sc.y128, sc.fexp, sc.xbd, sc.dfw,
+                                              p->st, s)) != cudaSuccess)
+                    return e;
+                if ((e = launch_adjoint_exact(p->enc, sc.u128, F, sc.fexp, sc.xbd, sc.r128, sc.dfw, p->st, s,
+                                              p->Ad)) != cudaSuccess)
+                    return e;
+                return launch_minus_lambda(sc.r128, X, p->lambda_abs, F * N, s);
             }
-            if (md.stop_rule) CKA(launch_frame_norms(sc.r128, F, N, sc.norms, s));
+            if (md.dfres) {
+                if ((e = launch_forward_df(p->enc, X, F, D, sc.u128, s, sc.dfw)) != cudaSuccess) return e;  // u = d - E x
+                return launch_adjoint_df(p->enc, sc.u128, F, p->lambda_abs, X, sc.r128, s, sc.dfw);
+            }
+            if ((e = launch_forward64(p->enc, X, F, D, sc.u128, s)) != cudaSuccess) return e;
+            return launch_adjoint64(p->enc, sc.u128, F, p->lambda_abs, X, sc.r128, s);
+        };
+        // stopping rule: per-frame ||r|| / ||E^H d|| read back in fixed-size chunks (no
+        // allocation); with `bound`, also the certified error bound of x (below)
+        auto check = [&](bool bound, double* worst_out, double* bound_out) -> pinv_status {
+            CKA(launch_frame_norms(sc.r128, F, N, sc.norms, s));
+            if (bound) CKA(launch_frame_norms(X, F, N, sc.norms + 2 * F, s));
+            double worst = 0.0, wb = 0.0, hn[128], hb[128], hx[128];
+            for (int64_t f0 = 0; f0 < F; f0 += 128) {
+                const int64_t nf = std::min<int64_t>(128, F - f0);
+                CKA(cudaMemcpyAsync(hn, sc.norms + f0, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
+                CKA(cudaMemcpyAsync(hb, sc.norms + F + f0, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
+                if (bound)
+                    CKA(cudaMemcpyAsync(hx, sc.norms + 2 * F + f0, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
+                CKA(cudaStreamSynchronize(s));
+                for (int64_t f = 0; f < nf; ++f) {
+                    worst = std::max(worst, std::sqrt(hn[f] / std::max(hb[f], 1e-300)));
+                    if (bound) wb = std::max(wb, std::sqrt(hn[f] / std::max(hx[f], 1e-300)) / p->lambda_abs);
+                }
+            }
+            *worst_out = worst;
+            if (bound_out) *bound_out = wb;
+            return PINV_OK;
+        };
+        bool converged = false;
+        for (int it = 0; it < p->refine_iters; ++it) {
+            CKA(residual());
+            if (md.stop_rule) {
+                // with the stopping rule the residual is checked before the correction:
+                // an x whose residual is already below the tolerance is kept as it is
+                double worst = 0.0, wb = 0.0;
+                const pinv_status cs = check(true, &worst, &wb);
+                if (cs != PINV_OK) return cs;
+                p->last_refine_resid = worst;
+                p->last_refine_bound = wb;
+                if (worst <= p->refine_tol) {
+                    converged = true;
+                    break;
+                }
+            }
             if (md.dfres || md.toep) {
                 // the correction only preconditions the next residual: FP32 W suffices
                 CKA(correct(sc.r128));
@@ -222,19 +267,15 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
                 CKA(launch_hemv64(p->Ginv, N, N, sc.r128, F, X, X, s));
             }
             p->last_refine_iters = it + 1;
-            if (!md.stop_rule) continue;
-            // per-frame ||r|| / ||E^H d||, read back in fixed-size chunks (no allocation)
-            double worst = 0.0, hn[128], hb[128];
-            for (int64_t f0 = 0; f0 < F; f0 += 128) {
-                const int64_t nf = std::min<int64_t>(128, F - f0);
-                CKA(cudaMemcpyAsync(hn, sc.norms + f0, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
-                CKA(cudaMemcpyAsync(hb, sc.norms + F + f0, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
-                CKA(cudaStreamSynchronize(s));
-                for (int64_t f = 0; f < nf; ++f)
-                    worst = std::max(worst, std::sqrt(hn[f] / std::max(hb[f], 1e-300)));
-            }
+        }
+        if (md.stop_rule && !converged) {
+            // the residual of the x returned, so the recorded ratio and bound describe it
+            CKA(residual());
+            double worst = 0.0, wb = 0.0;
+            const pinv_status cs = check(true, &worst, &wb);
+            if (cs != PINV_OK) return cs;
             p->last_refine_resid = worst;
-            if (worst <= p->refine_tol) break;
+            p->last_refine_bound = wb;
         }
     }
     if (dtype == PINV_C64) CKA(launch_c128_to_c64(X, (float2*)d_image, F * N, s));

@@ -119,6 +119,7 @@ struct pinv_plan {
     cudaEvent_t ev[10] = {};  // build stages 0-5; 6-7 around the Gram kernels; 8-9 around the condition estimate
     int last_refine_iters = 0;
     double last_refine_resid = 0;
+    double last_refine_bound = 0;
     int info = -1;
 
     int slices() const { return precision == PINV_MIXED_BF16X6 ? 3 : 2; }
