@@ -188,6 +188,20 @@ int pinv_tc_available(void);
 const char* pinv_last_error(void);
 
 /*
+ * Failure handling. Every wait of the tensor-core kernels' pipelines (for a
+ * stage's operands, for an MMA group, for its drain) is bounded; past the bound
+ * the CTA stops taking work, waits for the MMAs and copies it has issued, frees
+ * its tensor memory and records the wait's site, and the build (or batch) then
+ * reports PINV_ERR_TIMEOUT from pinv_plan_sync while later work still runs.
+ * This sets that bound in SM clock cycles for builds started after the call,
+ * process-wide (0: the default, about 2 s). A small value makes real waits run
+ * out, which exercises that path; the waits of the clean-up itself keep the
+ * default bound. Applies keep the default. Errors: INVALID_ARG for a negative
+ * value. The paper has no counterpart: this is a test hook of this library.
+ */
+pinv_status pinv_set_wait_limit(int64_t cycles);
+
+/*
  * Validate the descriptor, copy its arrays to the device on `stream` and
  * compute lambda. Builds nothing yet. Errors: INVALID_ARG (bad sizes, missing
  * times with b0_hz, C > 1 without coil maps, voxel index out of range),
@@ -215,7 +229,9 @@ pinv_status pinv_plan_sync(pinv_plan* plan);
  * factor-only plans (Section 3.3). d_data: device [F][C][M_k], d_image:
  * device [F][N], both of `dtype` (pinv_dtype). Mixed-precision plans refine
  * each frame with FP64 residuals r = E^H (d - E x) - lambda x up to
- * refine_max_iters times. n_frames == 0 is a no-op. Uses plan-owned
+ * refine_max_iters times. n_frames == 0 is a no-op. With the stopping rule
+ * (refine_tol > 0) a residual or image that is not finite (NaN or Inf in the
+ * data) ends the call with PINV_ERR_INVALID_ARG naming the frame. Uses plan-owned
  * scratch sized on first use; concurrent applies of one plan must be
  * serialised on one stream.
  */

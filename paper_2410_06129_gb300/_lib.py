@@ -86,6 +86,7 @@ SIGNATURES = {
     "pinv_kernel_launches": (C.c_ulonglong, []),
     "pinv_tc_available": (C.c_int, []),
     "pinv_last_error": (C.c_char_p, []),
+    "pinv_set_wait_limit": (C.c_int, [C.c_int64]),
     "pinv_plan_create": (C.c_int, [C.POINTER(PlanDesc), _VP, C.POINTER(_VP)]),
     "pinv_build": (C.c_int, [_VP, _VP]),
     "pinv_plan_sync": (C.c_int, [_VP]),

@@ -41,6 +41,8 @@ pinv_status cuda_fail(cudaError_t e, const char* where) {
 namespace pinv {
 std::atomic<unsigned long long> g_launches{0};
 pinv_status set_error(pinv_status st, const std::string& msg) { return fail(st, msg); }
+static std::atomic<long long> g_wait_limit{0};
+long long wait_limit_setting() { return g_wait_limit.load(); }
 }
 
 namespace pinv {
@@ -283,6 +285,12 @@ pinv_status build_end(pinv_plan* p, cudaStream_t s) {
 extern "C" {
 
 int pinv_version(void) { return 100; }
+
+pinv_status pinv_set_wait_limit(int64_t cycles) {
+    if (cycles < 0) return fail(PINV_ERR_INVALID_ARG, "wait limit must be >= 0");
+    g_wait_limit.store((long long)cycles);
+    return PINV_OK;
+}
 
 unsigned long long pinv_kernel_launches(void) { return g_launches.load(); }
 
@@ -638,16 +646,18 @@ pinv_status pinv_plan_sync(pinv_plan* p) {
     CK(cudaGetLastError());
     const DevStatus h = *p->st_host;
     p->info = -1;
+    // a wait that gave up leaves everything after it incomplete (a pivot check
+    // included), so it is reported first
+    if (h.timeout_site) {
+        p->built = false;
+        return fail(PINV_ERR_TIMEOUT, "a bounded device wait gave up (site " +
+                                          std::to_string(h.timeout_site) + ")");
+    }
     if (h.not_pd_pivot != INT_MAX) {
         p->info = h.not_pd_pivot;
         p->built = false;
         return fail(PINV_ERR_NOT_PD, "Gram matrix not positive definite at pivot " +
                                          std::to_string(h.not_pd_pivot) + " (increase lambda)");
-    }
-    if (h.timeout_site) {
-        p->built = false;
-        return fail(PINV_ERR_TIMEOUT, "a bounded device wait gave up (site " +
-                                          std::to_string(h.timeout_site) + ")");
     }
     if (h.error_code) {
         p->built = false;

@@ -231,6 +231,11 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
                     CKA(cudaMemcpyAsync(hx, sc.norms + 2 * F + f0, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
                 CKA(cudaStreamSynchronize(s));
                 for (int64_t f = 0; f < nf; ++f) {
+                    // a residual or image that is not finite (data with NaN or Inf, or a
+                    // factor that lost them) ends the refinement with an error
+                    if (!std::isfinite(hn[f]) || !std::isfinite(hb[f]) || (bound && !std::isfinite(hx[f])))
+                        return set_error(PINV_ERR_INVALID_ARG, "non-finite residual or image in frame " +
+                                                                   std::to_string(f0 + f));
                     worst = std::max(worst, std::sqrt(hn[f] / std::max(hb[f], 1e-300)));
                     if (bound) wb = std::max(wb, std::sqrt(hn[f] / std::max(hx[f], 1e-300)) / p->lambda_abs);
                 }

@@ -76,7 +76,12 @@ struct DevStatus {
     // condition estimate (cond.cu): ||G||_1 and kappa_1(G) = ||G||_1 ||G^-1||_1
     double norm1_g;
     double kappa_est;
+    // bound of the tensor-core kernels' pipeline waits in SM clock cycles (0: the
+    // default, about 2 s); set at every status reset from pinv_set_wait_limit
+    long long wait_limit;
 };
+// the process-wide setting of DevStatus::wait_limit (pinv_set_wait_limit)
+long long wait_limit_setting();
 
 // ---------------------------------------------------------------------------
 // complex helpers

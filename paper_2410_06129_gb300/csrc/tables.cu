@@ -208,7 +208,7 @@ cudaError_t launch_transpose32(const float2* src, int64_t rows, int64_t cols, fl
 }
 
 // status word back to "no error" (a kernel, so that builds can be captured in graphs)
-__global__ void k_reset_status(DevStatus* st) {
+__global__ void k_reset_status(DevStatus* st, long long wait_limit) {
     st->not_pd_pivot = INT_MAX;
     st->timeout_site = 0;
     st->error_code = 0;
@@ -219,10 +219,11 @@ __global__ void k_reset_status(DevStatus* st) {
     st->sched_done = 0;
     st->norm1_g = 0.0;
     st->kappa_est = 0.0;
+    st->wait_limit = wait_limit;
 }
 
 cudaError_t launch_reset_status(DevStatus* st, cudaStream_t s) {
-    k_reset_status<<<1, 1, 0, s>>>(st);
+    k_reset_status<<<1, 1, 0, s>>>(st, wait_limit_setting());
     note_launch();
     return cudaGetLastError();
 }

@@ -132,14 +132,18 @@ __device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false if the limit expired or another role raised abort.
-__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+// Bounded wait: false if the limit expired or another role raised abort. Pipeline
+// waits pass the kernel's runtime limit (DevStatus::wait_limit); the waits of the
+// clean-up (every issued MMA finished before TMEM is freed, copies in flight
+// landed) pass no abort flag and keep WAIT_LIMIT whatever the setting.
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                 long long limit = WAIT_LIMIT) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (abort_flag && *abort_flag) return false;
-        if (clock64() - t0 > WAIT_LIMIT) {
+        if (clock64() - t0 > limit) {
             if (abort_flag) *abort_flag = 1;
             return false;
         }
@@ -397,6 +401,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, in
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long wlim = st->wait_limit > 0 ? st->wait_limit : WAIT_LIMIT;  // pipeline waits
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < CF::STAGES; ++s) {
@@ -440,7 +445,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, in
             int drained = 0;
             bool ok = true;
             auto drain = [&](int g) -> bool {
-                if (!mbar_wait(&tfull, (gq + (uint32_t)g) & 1u, &abort_flag)) return false;
+                if (!mbar_wait(&tfull, (gq + (uint32_t)g) & 1u, &abort_flag, wlim)) return false;
                 tc_fence_after();
                 drain_to_total(taddr_row, g == 0);
                 tc_fence_before();
@@ -471,7 +476,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, in
                 const uint32_t kg = kq + (uint32_t)kt;
                 const int s = (int)(kg % CF::STAGES);
                 const uint32_t ph = (kg / CF::STAGES) & 1u;
-                if (kg >= CF::STAGES && !(ok = mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag))) break;
+                if (kg >= CF::STAGES && !(ok = mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag, wlim))) break;
                 uint8_t* base = smem + s * CF::STAGE_BYTES;
                 const int64_t k0 = kb + (int64_t)kt * KC;
                 float2 va[8], vb[8];
@@ -551,11 +556,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, in
             for (int kt = 0; kt < nk; ++kt) {
                 const uint32_t g = gq + (uint32_t)(kt / DRAIN);
                 const bool first = (kt % DRAIN) == 0;
-                if (first && g >= 1 && !mbar_wait(&tempty, (g - 1) & 1u, &abort_flag)) break;
+                if (first && g >= 1 && !mbar_wait(&tempty, (g - 1) & 1u, &abort_flag, wlim)) break;
                 const uint32_t kg = kq + (uint32_t)kt;
                 const int s = (int)(kg % CF::STAGES);
                 const uint32_t ph = (kg / CF::STAGES) & 1u;
-                if (!mbar_wait(&full_bar[s], ph, &abort_flag)) break;
+                if (!mbar_wait(&full_bar[s], ph, &abort_flag, wlim)) break;
                 tc_fence_after();
                 const uint32_t sbase = smem_u32(smem + s * CF::STAGE_BYTES);
 #pragma unroll
@@ -618,6 +623,7 @@ __global__ void __launch_bounds__(NTHREADS_BULK, 1) k_tc_bulk(Sched sch, DevStat
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long wlim = st->wait_limit > 0 ? st->wait_limit : WAIT_LIMIT;  // pipeline waits
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < CF::STAGES; ++s) {
@@ -667,7 +673,7 @@ __global__ void __launch_bounds__(NTHREADS_BULK, 1) k_tc_bulk(Sched sch, DevStat
             bool ok = true;
             for (int g = 0; g < ngroups; ++g) {
                 const uint32_t G = gq + (uint32_t)g, b = G & 1u;
-                if (!(ok = mbar_wait(&tfull[b], (G >> 1) & 1u, &abort_flag))) break;
+                if (!(ok = mbar_wait(&tfull[b], (G >> 1) & 1u, &abort_flag, wlim))) break;
                 tc_fence_after();
                 drain_to_regs(taddr_row + 2u * BN * b, tot, g == 0);
                 tc_fence_before();
@@ -734,11 +740,11 @@ __global__ void __launch_bounds__(NTHREADS_BULK, 1) k_tc_bulk(Sched sch, DevStat
                 const uint32_t G = gq + (uint32_t)(kt / DRAIN), b = G & 1u;
                 const bool first = (kt % DRAIN) == 0;
                 // buffer b was last used by group G - 2: it must be drained
-                if (first && G >= 2 && !mbar_wait(&tempty[b], ((G >> 1) - 1u) & 1u, &abort_flag)) break;
+                if (first && G >= 2 && !mbar_wait(&tempty[b], ((G >> 1) - 1u) & 1u, &abort_flag, wlim)) break;
                 const uint32_t kg = kq + (uint32_t)kt;
                 const int s = (int)(kg % CF::STAGES);
                 const uint32_t ph = (kg / CF::STAGES) & 1u;
-                if (!mbar_wait(&full_bar[s], ph, &abort_flag)) break;
+                if (!mbar_wait(&full_bar[s], ph, &abort_flag, wlim)) break;
                 tc_fence_after();
                 const uint32_t sbase = smem_u32(smem + s * CF::STAGE_BYTES);
                 const uint32_t dcol = tmem + 2u * BN * b;
@@ -765,7 +771,7 @@ __global__ void __launch_bounds__(NTHREADS_BULK, 1) k_tc_bulk(Sched sch, DevStat
                 const uint32_t kg = kq + (uint32_t)kt;
                 const int s = (int)(kg % CF::STAGES);
                 const uint32_t ph = (kg / CF::STAGES) & 1u;
-                if (kg >= CF::STAGES && !mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) break;
+                if (kg >= CF::STAGES && !mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag, wlim)) break;
                 uint8_t* base = smem + s * CF::STAGE_BYTES;
                 mbar_arrive_expect_tx(&full_bar[s], STAGE_TX);
 #pragma unroll

@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
     __shared__ int abort_flag;
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long wlim = st->wait_limit > 0 ? st->wait_limit : WAIT_LIMIT;  // pipeline waits
     // output rows (voxels; samples of one coil for the forward product)
     const int64_t N = FWD ? a.e.Mk : a.e.N;
     const int64_t FT = (a.F + XN - 1) / XN, RB = (N + XM - 1) / XM;
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
         bool ok = true;
         int drained = 0;
         auto drain = [&](int g) -> bool {
-            if (!mbar_wait(&tfull, (uint32_t)g & 1u, &abort_flag)) return false;
+            if (!mbar_wait(&tfull, (uint32_t)g & 1u, &abort_flag, wlim)) return false;
             tc_fence_after();
 #pragma unroll 1
             for (int w = 0; w < NCLS; ++w) {
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
         for (int kt = 0; kt < nk && ok; ++kt) {
             const int s = kt % XSTAGES;
             const uint32_t ph = (uint32_t)(kt / XSTAGES) & 1u;
-            if (kt >= XSTAGES && !(ok = mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag))) break;
+            if (kt >= XSTAGES && !(ok = mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag, wlim))) break;
             uint8_t* base = smem + s * XSTAGE;
             const int64_t m0 = mb + (int64_t)kt * XKC;  // k index (sample inside the coil, or Gram column)
             const int64_t kb = m0 / XKC;
@@ -458,11 +459,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
         for (int kt = 0; kt < nk; ++kt) {
             const int g = kt / XDRAIN;
             const bool first = (kt % XDRAIN) == 0;
-            if (first && g >= 1 && !mbar_wait(&tempty, (uint32_t)(g - 1) & 1u, &abort_flag)) break;
+            if (first && g >= 1 && !mbar_wait(&tempty, (uint32_t)(g - 1) & 1u, &abort_flag, wlim)) break;
             const int s = kt % XSTAGES;
             const uint32_t ph = (uint32_t)(kt / XSTAGES) & 1u;
-            if (MODE == XGEN && !mbar_wait(&full_bar[s], ph, &abort_flag)) break;
-            if (!mbar_wait(&abar[s], ph, &abort_flag)) break;
+            if (MODE == XGEN && !mbar_wait(&full_bar[s], ph, &abort_flag, wlim)) break;
+            if (!mbar_wait(&abar[s], ph, &abort_flag, wlim)) break;
             tc_fence_after();
             const uint32_t abase = smem_u32(smem + s * XSTAGE);
             const uint32_t bbase = abase + NDIG * XA_SL;
