@@ -17,12 +17,23 @@
 //     PINV_ERR_BUDGET;
 //   * completion is detected with events; latency runs from enqueue to the
 //     moment the worker sees the request's event complete.
+//   * host fault injection (PINV_FAULT, read when the server is created) makes
+//     failures on the host, never on the device: a comma-separated list of
+//     one-shot faults, "alloc:P" (the next admission of plan P fails as if its
+//     device allocation had, PINV_ERR_OOM), "build:P" (the next build of plan P
+//     fails, PINV_ERR_INTERNAL), "drop:T" (request T completes with
+//     PINV_ERR_INTERNAL without running) and "delay:T:MS" (request T's
+//     completion is reported MS milliseconds after its work finished; its slot
+//     is free at once). A plan whose admission or build failed is retried by its
+//     next request; every other request runs as it would without the faults.
 // Each request's result is computed by the same kernels in the same order as
 // a standalone pinv_apply, so it does not depend on what else is in flight.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 #include <deque>
 #include <mutex>
 #include <thread>
@@ -65,6 +76,42 @@ struct Request {
     double t_enqueue = 0;
 };
 
+// one-shot host fault (PINV_FAULT)
+enum FaultKind { FAULT_ALLOC = 0, FAULT_BUILD = 1, FAULT_DROP = 2, FAULT_DELAY = 3 };
+struct Fault {
+    int kind;
+    int64_t key;  // plan id (alloc, build) or ticket (drop, delay)
+    double ms;    // delay
+    bool used;
+};
+std::vector<Fault> parse_faults(const char* spec) {
+    std::vector<Fault> out;
+    if (!spec) return out;
+    std::string s(spec);
+    size_t pos = 0;
+    while (pos <= s.size()) {
+        size_t end = s.find(',', pos);
+        if (end == std::string::npos) end = s.size();
+        const std::string item = s.substr(pos, end - pos);
+        pos = end + 1;
+        const size_t c1 = item.find(':');
+        if (c1 == std::string::npos) continue;
+        const std::string kind = item.substr(0, c1), rest = item.substr(c1 + 1);
+        const size_t c2 = rest.find(':');
+        Fault f{-1, 0, 0.0, false};
+        f.key = std::strtoll(rest.substr(0, c2).c_str(), nullptr, 10);
+        if (kind == "alloc") f.kind = FAULT_ALLOC;
+        else if (kind == "build") f.kind = FAULT_BUILD;
+        else if (kind == "drop") f.kind = FAULT_DROP;
+        else if (kind == "delay" && c2 != std::string::npos) {
+            f.kind = FAULT_DELAY;
+            f.ms = std::strtod(rest.substr(c2 + 1).c_str(), nullptr);
+        }
+        if (f.kind >= 0) out.push_back(f);
+    }
+    return out;
+}
+
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
@@ -91,12 +138,24 @@ struct pinv_server {
     cudaStream_t build_stream = nullptr;
     uint64_t next_ticket = 1, lru_clock = 0;
     size_t resident_bytes = 0;
+    std::vector<Fault> faults;                            // PINV_FAULT
+    std::vector<std::pair<double, Request>> delayed;      // (report time, request) of delayed completions
     // statistics
     std::vector<double> latency_ms;
     uint64_t completed = 0, failed = 0, builds = 0, evictions = 0, recon_drops = 0;
     double frames = 0, t_first = 0, t_last = 0;
 
     void run();
+    bool take_fault(int kind, int64_t key, double* ms = nullptr) {
+        for (auto& f : faults)
+            if (!f.used && f.kind == kind && f.key == key) {
+                f.used = true;
+                if (ms) *ms = f.ms;
+                return true;
+            }
+        return false;
+    }
+    bool release_delayed(std::unique_lock<std::mutex>& lk);
     bool dispatch_one(std::unique_lock<std::mutex>& lk);
     bool reap(std::unique_lock<std::mutex>& lk);
     pinv_status make_resident(Registered& r, int id, bool* defer);
@@ -197,10 +256,12 @@ pinv_status pinv_server::make_resident(Registered& r, int id, bool* defer) {
     pinv_plan_desc d = r.desc;
     const bool full = resident_bytes + need_full <= budget;
     if (!full) d.recon_mode = PINV_RECON_NONE;
+    if (take_fault(FAULT_ALLOC, id)) return set_error(PINV_ERR_OOM, "injected allocation failure at admission");
     pinv_plan* p = nullptr;
     pinv_status st = pinv_plan_create(&d, build_stream, &p);
     if (st != PINV_OK) return st;
-    st = pinv_build(p, build_stream);
+    st = take_fault(FAULT_BUILD, id) ? set_error(PINV_ERR_INTERNAL, "injected build failure")
+                                     : pinv_build(p, build_stream);
     if (st != PINV_OK) {
         pinv_plan_destroy(p);
         return st;
@@ -230,6 +291,8 @@ bool pinv_server::dispatch_one(std::unique_lock<std::mutex>& lk) {
     pinv_status st = r.failed != PINV_OK ? r.failed : make_resident(r, q.plan_id, &defer);
     if (defer) return false;  // head of the queue waits until a slot completes
     queue.pop_front();
+    if (st == PINV_OK && take_fault(FAULT_DROP, (int64_t)q.ticket))
+        st = set_error(PINV_ERR_INTERNAL, "request dropped (injected)");
     if (st == PINV_OK) st = apply_check(r.plan, q.data, q.image, q.frames, q.dtype);
     if (st == PINV_OK && q.frames > 0) {
         const size_t need = apply_scratch_layout(r.plan, q.frames, q.dtype, nullptr, nullptr);
@@ -286,8 +349,29 @@ bool pinv_server::reap(std::unique_lock<std::mutex>& lk) {
         }
         if (r.failed != PINV_OK && r.plan && r.inflight == 0) evict(r);
         const Request q = s.req;
-        finish(q, st, lk);
+        double ms = 0.0;
+        if (st == PINV_OK && take_fault(FAULT_DELAY, (int64_t)q.ticket, &ms))
+            delayed.push_back({now_s() + ms * 1e-3, q});  // reported later; the slot is free now
+        else
+            finish(q, st, lk);
         any = true;
+    }
+    return any;
+}
+
+// Report the delayed completions whose time has come. Returns true if it did work.
+bool pinv_server::release_delayed(std::unique_lock<std::mutex>& lk) {
+    bool any = false;
+    const double t = now_s();
+    for (size_t i = 0; i < delayed.size();) {
+        if (delayed[i].first <= t) {
+            const Request q = delayed[i].second;
+            delayed.erase(delayed.begin() + (long)i);
+            finish(q, PINV_OK, lk);
+            any = true;
+        } else {
+            ++i;
+        }
     }
     return any;
 }
@@ -297,8 +381,9 @@ void pinv_server::run() {
     std::unique_lock<std::mutex> lk(mu);
     while (true) {
         bool work = reap(lk);
+        work = release_delayed(lk) || work;
         while (dispatch_one(lk)) work = true;
-        bool busy = false;
+        bool busy = !delayed.empty();
         for (auto& s : slots) busy = busy || s.busy;
         if (stop && !busy && queue.empty()) break;
         if (!work) {
@@ -329,6 +414,7 @@ pinv_status pinv_server_create(size_t hbm_budget_bytes, int max_slots, pinv_serv
             return set_error(PINV_ERR_CUDA, "slot stream creation failed");
         }
     }
+    sv->faults = parse_faults(std::getenv("PINV_FAULT"));
     sv->worker = std::thread([sv] { sv->run(); });
     *out = sv;
     return PINV_OK;

@@ -218,3 +218,40 @@ def test_serve_zero_frames_and_bad_plan_id():
         with pytest.raises(L.PinvError, match="INVALID_ARG"):
             L.check(L.load().pinv_serve_enqueue(sv._h, pid + 7, None, None, 1, L.C128, None, None,
                                                 L.C.byref(L.C.c_uint64())))
+
+
+def test_host_fault_injection_leaves_other_requests_intact(monkeypatch):
+    """PINV_FAULT makes failures on the host while requests are in flight: the
+    first admission of plan 0 fails as if its allocation had (OOM), the first
+    build of plan 1 fails, ticket 7 is dropped and ticket 8's completion is held
+    back 300 ms. Those requests report their statuses (ticket 8 succeeds, late);
+    every other request completes with an image identical, bit for bit, to a
+    standalone apply, and the failed plans are admitted again by their next
+    requests."""
+    import time
+    from paper_2410_06129_gb300.serve import Server
+    cases = _cases()
+    reqs = _requests(cases)
+    expect = [_standalone(cases[i][0], cases[i][1], d) for i, d in reqs]
+    monkeypatch.setenv("PINV_FAULT", "alloc:0,build:1,drop:7,delay:8:300")
+    with Server(budget_bytes=8 << 30, max_slots=3) as sv:
+        ids = [sv.register_inputs(p, **kw) for p, kw in cases]
+        t0 = time.perf_counter()
+        tickets = [sv.enqueue(ids[i], d) for i, d in reqs]
+        status = {t: sv.wait(t) for t, _ in tickets}
+        waited = time.perf_counter() - t0
+        st = sv.stats()
+    first = {}
+    for (t, _), (i, _) in zip(tickets, reqs):
+        first.setdefault(i, t)
+    want = {t: L.OK for t, _ in tickets}
+    want[first[0]] = L.ERR_OOM
+    want[first[1]] = L.ERR_INTERNAL
+    want[7] = L.ERR_INTERNAL
+    assert status == want
+    assert waited >= 0.3  # ticket 8 was reported no sooner than its delay
+    for (t, out), x in zip(tickets, expect):
+        if want[t] == L.OK:
+            assert torch.equal(out, x), f"ticket {t} differs from a standalone apply"
+    assert st["failed"] == 3 and st["completed"] == len(reqs) - 3
+    assert st["builds"] == len(cases)  # the failed admission and build were retried once each
