@@ -414,15 +414,15 @@ def run_spectrum(side=32, frames=64, energy=0.95, seed=6100):
             "cpu_oracle_eig_s": cpu_s, "cpu_cores": _cores()}
 
 
-def run_cfg5(prec, refine, frames=64, seed=5100):
+def run_cfg5(prec, refine, frames=64, seed=5100, fp64=False):
     """Workload 5: 192x192 (N = 36864), 8 coils, 384 radial spokes x 125 samples
     (M = 384000), B0 +-50 Hz, lambda_rel 1e-4, 64 complex64 frames; factor-only
     (Recon would be 113 GB). One build, then the apply timed on its second run
     (fixed refinement steps, no host reads). A second plan then applies once with
     the stopping rule on, which reports the residual of the images it returns and
     the certified bound ||x - x*|| / ||x|| <= ||r|| / (lambda ||x||) (every
-    eigenvalue of G is at least lambda); the FP64 path at this size is a separate
-    run of several minutes (not part of this bench)."""
+    eigenvalue of G is at least lambda). With fp64 the FP64 factor-only plan is
+    built too (several minutes) and the mixed images are compared with its."""
     import torch
 
     from paper_2410_06129_gb300 import _lib as L
@@ -446,7 +446,25 @@ def run_cfg5(prec, refine, frames=64, seed=5100):
         plan.apply(data, out)
         torch.cuda.synchronize()
         inf2 = plan.info()
-    return {"workload": "192x192 (N=36864), 8 coils, 384 radial spokes x 125 samples (M=384000), B0 +-50 Hz, "
+    vs64 = None
+    if fp64 and prec != L.FP64:
+        x_mixed = out.to(torch.complex128).cpu()
+        with Plan.from_inputs(geo, precision=L.FP64, recon_mode=L.RECON_NONE, refine_max_iters=1) as p64:
+            b64 = _timed_build(p64, stream)
+            i64 = p64.info()
+            out64 = torch.empty((frames, geo.n_vox), dtype=torch.complex128, device="cuda")
+            d128 = data.to(torch.complex128)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p64.apply(d128, out64, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            x64 = out64.cpu()
+        vs64 = {"fp64_build_s": b64 / 1e3, "fp64_apply_s": e0.elapsed_time(e1) / 1e3,
+                "fp64_kappa_est": i64["kappa_est"], "nrmse_vs_fp64": _rel(x_mixed, x64),
+                "nrmse_vs_fp64_max_frame": _rel_frames(x_mixed, x64),
+                "speedup_build_vs_fp64": b64 / build_ms}
+    res = {"workload": "192x192 (N=36864), 8 coils, 384 radial spokes x 125 samples (M=384000), B0 +-50 Hz, "
                         f"lambda 1e-4 mean diag, {frames} c64 frames, factor-only",
             "build_s": build_ms / 1e3,
             "stage_ms": {k: inf[k] for k in ("ms_gram", "ms_chol", "ms_inverse", "ms_cond")},
@@ -454,6 +472,9 @@ def run_cfg5(prec, refine, frames=64, seed=5100):
             "kappa_est": inf["kappa_est"],
             "final_residual_ratio": inf2["last_refine_resid"], "certified_bound": inf2["last_refine_bound"],
             "bytes_device": inf["bytes_device"]}
+    if vs64 is not None:
+        res["fp64"] = vs64
+    return res
 
 
 def _rel(a, b):
@@ -516,6 +537,8 @@ def main():
                     help="Gram eigendecomposition and tSVD reconstruction at workload 1's size")
     ap.add_argument("--cfg5", default="on", choices=["on", "off"],
                     help="workload 5 (192x192, B0, factor-only): one build and one timed apply")
+    ap.add_argument("--cfg5-fp64", default="off", choices=["on", "off"],
+                    help="also build workload 5 in FP64 (about 7 minutes) and compare the images")
     ap.add_argument("--serve-fp64-duration", type=float, default=1.0,
                     help="seconds of the same trace served by FP64 plans (0 = skip)")
     args = ap.parse_args()
@@ -714,7 +737,7 @@ def main():
 
     cfg5 = None
     if rank == 0 and args.cfg5 == "on":
-        cfg5 = run_cfg5(prec, refine if prec != L.FP64 else 1)
+        cfg5 = run_cfg5(prec, refine if prec != L.FP64 else 1, fp64=args.cfg5_fp64 == "on")
 
     batch = None
     if rank == 0 and args.batch == "on" and prec != L.FP64:
