@@ -98,13 +98,14 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
     if (!p->Gx) CK(launch_gram_norm1(p->G, nullptr, N, ld, p->st, s));
     if (p->Gx) {
         // exact Gram for the refinement residual (Toeplitz table, then coil products,
-        // then its digit tiles). Only applies read it, so mixed plans form it on their
-        // second stream beside the Cholesky (build_factor joins that stream).
+        // then its digit tiles). Only applies and the condition check read it, so mixed
+        // plans form it on their lowest-priority stream beside the Cholesky and the
+        // inverse, in the SMs their launches leave free (build_factor joins that stream).
         cudaStream_t sx = s;
-        if (p->s_inv) {
+        if (p->s_x) {
             CK(cudaEventRecord(p->ev_xfork, s));
-            CK(cudaStreamWaitEvent(p->s_inv, p->ev_xfork, 0));
-            sx = p->s_inv;
+            CK(cudaStreamWaitEvent(p->s_x, p->ev_xfork, 0));
+            sx = p->s_x;
         }
         double2* work = nullptr;
         CK(work_alloc((void**)&work, toeplitz_work_bytes(p->enc), sx));
@@ -114,17 +115,25 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
         CK(launch_gram_norm1(nullptr, p->Gx, N, N, p->st, sx));
         if (p->Gd) CK(launch_gram_digits(p->Gx, N, p->eG, p->Gd, sx));
         if (p->Ad) CK(launch_adj_digits(p->enc, p->Ad, sx));
+        if (sx != s) {
+            CK(cudaEventRecord(p->ev_xjoin, sx));
+            p->x_pending = true;
+        }
     } else if (p->Ad || p->Af) {
         // plans with B0: the digit tables of conj(A) and A for the exact products of
         // the refinement, formed beside the Cholesky (build_factor joins that stream)
         cudaStream_t sx = s;
-        if (p->s_inv) {
+        if (p->s_x) {
             CK(cudaEventRecord(p->ev_xfork, s));
-            CK(cudaStreamWaitEvent(p->s_inv, p->ev_xfork, 0));
-            sx = p->s_inv;
+            CK(cudaStreamWaitEvent(p->s_x, p->ev_xfork, 0));
+            sx = p->s_x;
         }
         if (p->Ad) CK(launch_adj_digits(p->enc, p->Ad, sx));
         if (p->Af) CK(launch_fwd_digits(p->enc, p->Af, sx));
+        if (sx != s) {
+            CK(cudaEventRecord(p->ev_xjoin, sx));
+            p->x_pending = true;
+        }
     }
     return PINV_OK;
 }
@@ -197,8 +206,9 @@ pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events) {
         cudaStream_t sc = (p->s_chol && !(hi && std::strcmp(hi, "0") == 0)) ? p->s_chol : s;
         if (sc != s) CK(cudaStreamWaitEvent(sc, p->ev_fork, 0));
         // (the FP64 diagonal inverses are not needed: the inverse reads the FP32 ones)
-        const TrailLookahead la{p->s_trail, p->st_trail, p->ev_tab, p->ev_trail};
+        const TrailLookahead la{p->s_trail, p->st_trail, p->ev_tab, p->ev_trail, p->s_pnl, p->ev_next, p->ev_side};
         CK(cudaStreamWaitEvent(p->s_trail, p->ev_fork, 0));
+        CK(cudaStreamWaitEvent(p->s_pnl, p->ev_fork, 0));
         CK(launch_potrf_tc(p->G, N, ld, nullptr, D32, L32, p->slices(), p->st, sc, tab, p->ev_panel.data(), &la));
         CK(launch_merge_timeout(p->st, p->st_trail, sc));
         CK(launch_pivot_stats(p->G, N, ld, p->st, sc));
@@ -225,6 +235,10 @@ pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events) {
         CK(launch_trtri64(p->G, N, ld, p->Dinv, W, s));
         CK(launch_lauum64(W, N, ld, p->Ginv, s));
         CK(cudaFreeAsync(W, s));
+    }
+    if (p->x_pending) {  // the exact Gram and digit tables formed beside the factor
+        CK(cudaStreamWaitEvent(s, p->ev_xjoin, 0));
+        p->x_pending = false;
     }
     // the lambda / condition check: kappa_1(G) from the factor (Section 2.1, 2.2)
     if (events) CK(cudaEventRecord(p->ev[8], s));
@@ -587,15 +601,22 @@ pinv_status pinv_plan_create(const pinv_plan_desc* d, void* stream, pinv_plan** 
     if (p->precision != PINV_FP64) {
         AL(p->st_inv, sizeof(DevStatus), "inverse status");
         CKC(cudaMemset(p->st_inv, 0, sizeof(DevStatus)));
-        CKC(cudaStreamCreateWithFlags(&p->s_inv, cudaStreamNonBlocking));
-        AL(p->st_trail, sizeof(DevStatus), "trailing-update status");
-        CKC(cudaMemset(p->st_trail, 0, sizeof(DevStatus)));
-        CKC(cudaStreamCreateWithFlags(&p->s_trail, cudaStreamNonBlocking));
-        CKC(cudaEventCreateWithFlags(&p->ev_tab, cudaEventDisableTiming));
-        CKC(cudaEventCreateWithFlags(&p->ev_trail, cudaEventDisableTiming));
+        // stream priorities: the Cholesky chain, its in-panel side work and its trailing
+        // updates first, the inverse (one panel behind) next, the exact Gram last
         int prio_lo = 0, prio_hi = 0;
         CKC(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        CKC(cudaStreamCreateWithPriority(&p->s_inv, cudaStreamNonBlocking, (prio_lo + prio_hi) / 2));
+        CKC(cudaStreamCreateWithPriority(&p->s_x, cudaStreamNonBlocking, prio_lo));
+        CKC(cudaEventCreateWithFlags(&p->ev_xjoin, cudaEventDisableTiming));
+        AL(p->st_trail, sizeof(DevStatus), "trailing-update status");
+        CKC(cudaMemset(p->st_trail, 0, sizeof(DevStatus)));
+        CKC(cudaStreamCreateWithPriority(&p->s_trail, cudaStreamNonBlocking, prio_hi));
+        CKC(cudaEventCreateWithFlags(&p->ev_tab, cudaEventDisableTiming));
+        CKC(cudaEventCreateWithFlags(&p->ev_trail, cudaEventDisableTiming));
         CKC(cudaStreamCreateWithPriority(&p->s_chol, cudaStreamNonBlocking, prio_hi));
+        CKC(cudaStreamCreateWithPriority(&p->s_pnl, cudaStreamNonBlocking, prio_hi));
+        CKC(cudaEventCreateWithFlags(&p->ev_next, cudaEventDisableTiming));
+        CKC(cudaEventCreateWithFlags(&p->ev_side, cudaEventDisableTiming));
         CKC(cudaEventCreateWithFlags(&p->ev_chol, cudaEventDisableTiming));
         p->ev_panel.assign((size_t)((p->N + 255) / 256), nullptr);
         for (auto& ev : p->ev_panel) CKC(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));

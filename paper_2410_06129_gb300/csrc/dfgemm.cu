@@ -320,12 +320,6 @@ __device__ inline float4 df_norm(float4 a) {  // renormalise both (hi, lo) pairs
     a.w = l;
     return a;
 }
-__device__ inline float4 df_cadd(float4 a, float4 b) {
-    float rh, rl, ih, il;
-    df_add(a.x, a.y, b.x, b.y, rh, rl);
-    df_add(a.z, a.w, b.z, b.w, ih, il);
-    return make_float4(rh, rl, ih, il);
-}
 }  // namespace
 
 // 1 / sqrt(d) for a positive double-float d: FP32 estimate and one Newton
@@ -445,33 +439,46 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
     }
 }
 
-// The same block on a cluster of two CTAs, blocked by 16 columns: rank 0
-// factors, rank 1 forms the inverse behind it.
+// The same block on a cluster of two CTAs with a one-column lookahead: rank 0
+// factors, rank 1 forms the inverse X = L^-1 behind it. Each rank splits its
+// 32 warps: the first two finish the next column (rank 0) or row (rank 1), the
+// critical path; the next 28 apply the current column's term to everything
+// beyond it, each thread to the two or three entries it keeps in registers;
+// on rank 0 the last two warps take turns to raise rank 1's flags after the
+// barriers (a release at cluster scope takes about 450 cycles, which the
+// barrier would otherwise wait for). One block barrier per column.
 //
-// Rank 0 sweeps the columns j of each 16-column sub-block [b0, b1): scale
-// column j by r = 1 / sqrt(A_jj) and write L_jj, then update only the entries
-// (i, c) with j < c < b1 (rank-1 updates inside the sub-block's columns). The
-// entries right of the sub-block get the sub-block's sixteen updates at once
-// afterwards, as double-float dot products A_ic -= sum_k L_ik conj(L_ck). The
-// threads that scale column j also store it, and r_j, into rank 1's shared
-// memory (posted remote stores); after the block barrier, thread j raises a
-// flag there (release at cluster scope).
+// Rank 0, step j (columns 0..j of L final, column j + 1 holding the terms of
+// columns 0..j-1): every thread i of the first two warps forms the pivot
+// d = A_{j+1,j+1} - |L_{j+1,j}|^2 and r = 1 / sqrt(d) (the same value in each,
+// so no barrier), and thread i > j + 1 finishes its entry of column j + 1,
+// L_{i,j+1} = r (A_{i,j+1} - L_ij conj(L_{j+1,j})), and stores it also into rank
+// 1's shared memory (posted remote stores; thread j + 1 stores r). Meanwhile
+// the other warps subtract column j's term from the entries (i, c), c >= j + 2,
+// and store an entry to shared memory after its last such term (c = j + 2),
+// where step c - 1 reads it. After the barrier one of the last two warps raises
+// a flag in rank 1 (release at cluster scope): columns 0..j+1 have arrived.
 //
-// Rank 1 forms X = L^-1 by rows in the same sub-blocks: for each j it waits for
-// the flag (acquire), scales row j of X by r_j and updates the rows of the
-// sub-block below j (X_ic -= L_ij X_jc, c <= j); the rows below the sub-block get
-// its sixteen updates at once afterwards (X_ic -= sum_k L_ik X_kc).
+// Rank 1, step j (rows 0..j of X final): thread c <= j + 1 of the first two
+// warps waits for column j + 1 (acquire; bounded, about 2 s, past the limit it
+// records timeout site DIAG_SITE and the rank stops, still meeting rank 0 at the
+// final cluster barrier) and forms X_{j+1,c} = r_{j+1} (Y_{j+1,c} - L_{j+1,j}
+// X_jc), Y = I minus the terms applied so far; the other warps subtract row j's
+// term from the rows below row j + 1, Y_ic -= L_ij X_jc.
 //
-// The sums are the column sweep's, reassociated per sub-block: the results
-// agree with the one-CTA sweep to the double-float rounding (about 2^-44
-// relative), not bit for bit. Rank 0 never waits for rank 1, except once at
-// the end so that rank 1 has received everything before either exits; rank 1's
-// waits are bounded (clock64, about 2 s): past the limit it records timeout
-// site DIAG_SITE, stops and still meets rank 0 at the final cluster barrier.
+// Every entry takes the same operations in the same order as in the one-CTA
+// sweep above (right-looking, one term per column, renormalised after each),
+// only spread differently over threads.
 constexpr int DIAG_SITE = 20;
 constexpr long long DIAG_WAIT_LIMIT = 4000000000LL;
-constexpr int DSB = 16;  // sub-block width
-constexpr size_t DIAG2_SMEM = (size_t)(NBD * NBDP + NBD * NBD + NBD) * sizeof(float4) + NBD * sizeof(float2);
+constexpr int DCW = 64;                          // critical threads: the first two warps
+constexpr int DUT = DIAG_THREADS - DCW - 64;     // update threads: the next 28 warps (896)
+constexpr int DSIG = DIAG_THREADS - 64;          // rank 0: flag raisers, DSIG (even counts), DSIG + 32 (odd)
+constexpr int DUE = 3;                           // entries per update thread
+constexpr int DNE = (NBD - 2) * (NBD - 1) / 2;   // 1953 entries updated off the critical path
+static_assert(DNE <= DUE * DUT, "update entries per thread");
+// A (rank 0) or X (rank 1); Lb[j][i] = L_ij and r_j received by rank 1; L_jj on rank 0
+constexpr size_t DIAG2_SMEM = (size_t)(NBD * NBDP + NBD * NBD) * sizeof(float4) + 2 * NBD * sizeof(float2);
 
 __device__ inline void st_release_cluster(unsigned* p, unsigned v) {
     asm volatile("st.release.cluster.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -481,16 +488,21 @@ __device__ inline unsigned ld_acquire_cluster(const unsigned* p) {
     asm volatile("ld.acquire.cluster.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-// rank 1: wait until rank 0 has published `need` columns; false on timeout
-__device__ inline bool diag_wait(const unsigned* flag, unsigned need, DevStatus* st) {
+// rank 1: wait until rank 0 has published `need` columns (the larger of the two
+// flags; `seen` keeps the count this thread has acquired, so most steps need no
+// load); false on timeout
+__device__ inline bool diag_wait(const unsigned* flag, unsigned need, unsigned& seen, DevStatus* st) {
+    if (seen >= need) return true;
     const long long t0 = clock64();
-    while (ld_acquire_cluster(flag) < need) {
+    for (;;) {
+        const unsigned a = ld_acquire_cluster(flag), b = ld_acquire_cluster(flag + 1);
+        seen = a > b ? a : b;
+        if (seen >= need) return true;
         if (clock64() - t0 > DIAG_WAIT_LIMIT) {
             atomicMax(&st->timeout_site, DIAG_SITE);
             return false;
         }
     }
-    return true;
 }
 // e = r (r + 1) / 2 + q with 0 <= q <= r (row r, column q of a lower triangle)
 __device__ inline void tri_index(int e, int& r, int& q) {
@@ -499,6 +511,7 @@ __device__ inline void tri_index(int e, int& r, int& q) {
     while ((r + 1) * (r + 2) / 2 <= e) ++r;
     q = e - r * (r + 1) / 2;
 }
+__device__ inline float4 cdf_neg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(DIAG_THREADS)
     k_potrf_diag_df2(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv, float2* Dinv32, float2* L32,
@@ -506,19 +519,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(DIAG_THREADS)
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ float4 smd[];
-    float4* A = smd;                    // rank 0: the block, then L; rank 1: X = L^-1
-    float4* Lb = smd + NBD * NBDP;      // rank 1: Lb[j][i] = L_ij, received from rank 0
-    float4* Xr = Lb + NBD * NBD;        // rank 1: row j of X, scaled
-    float2* rb = reinterpret_cast<float2*>(Xr + NBD);  // rank 1: r_j, received from rank 0
-    __shared__ unsigned flag;           // rank 1: columns of L published by rank 0
-    __shared__ int bad, stop;
+    float4* A = smd;                                        // rank 0: the block, then L; rank 1: Y, then X
+    float4* Lb = smd + NBD * NBDP;                          // rank 1: Lb[j][i] = L_ij
+    float2* rb = reinterpret_cast<float2*>(Lb + NBD * NBD);  // rank 1: r_j
+    float2* Ld = rb + NBD;                                  // rank 0: L_jj
+    __shared__ unsigned flag[2];  // rank 1: columns of L published by rank 0 (even, odd counts)
+    __shared__ int stop;
     const int tid = threadIdx.x;
     const unsigned rank = cl.block_rank();
     const int nb = (int)((N - k0) < NBD ? (N - k0) : NBD);
     if (tid == 0) {
-        flag = 0;
+        flag[0] = flag[1] = 0;
         stop = 0;
-        bad = (st->not_pd_pivot != INT_MAX) ? 1 : 0;
     }
     for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
         const int i = e / NBD, j = e % NBD;
@@ -530,86 +542,108 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(DIAG_THREADS)
         }
         A[i * NBDP + j] = v;
     }
-    cl.sync();  // rank 1's flag is zero before rank 0 may raise it
+    // the entries this thread updates off the critical path; rank 0: (i, c), 2 <= c <= i,
+    // numbered from the last column; rank 1: (i, c), c <= i - 2, numbered by row from row 2
+    const int u = tid - DCW;
+    int ui[DUE], uc[DUE];
+#pragma unroll
+    for (int k = 0; k < DUE; ++k) {
+        const int e = u + k * DUT;
+        ui[k] = -1;
+        uc[k] = -1;
+        if (u >= 0 && u < DUT && e < DNE) {
+            int r, q;
+            tri_index(e, r, q);
+            if (rank == 0) {
+                uc[k] = NBD - 1 - r;
+                ui[k] = uc[k] + q;
+            } else {
+                ui[k] = r + 2;
+                uc[k] = q;
+            }
+        }
+    }
+    cl.sync();  // the blocks are loaded and rank 1's flag is zero before rank 0 may raise it
+    float4 uv[DUE];
+#pragma unroll
+    for (int k = 0; k < DUE; ++k) uv[k] = ui[k] >= 0 ? A[ui[k] * NBDP + uc[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
     if (rank == 0) {
-        unsigned* rflag = cl.map_shared_rank(&flag, 1);
+        unsigned* rflag = cl.map_shared_rank(flag, 1);
         float4* rLb = cl.map_shared_rank(Lb, 1);
         float2* rrb = cl.map_shared_rank(rb, 1);
-        for (int b0 = 0; b0 < NBD; b0 += DSB) {
-            const int b1 = b0 + DSB;
-            // the entries (i, c), b0 <= c < b1, c <= i of the sub-block's columns, one per
-            // thread (at most 904 <= DIAG_THREADS), decoded once for the sub-block
-            int oi = -1, oc = 0;
-            {
-                int e = tid;
-                for (int c = b0; c < b1 && oi < 0; ++c) {
-                    const int len = NBD - c;  // rows c .. 63 of column c
-                    if (e < len) {
-                        oi = c + e;
-                        oc = c;
-                    } else {
-                        e -= len;
-                    }
-                }
+        // column 0
+        if (tid < DCW) {
+            const float4 a = A[0];
+            float dh = a.x, dl = a.y;
+            const bool fail = !(dh > 0.f) || !isfinite(dh);  // a normalised pair has the sign of dh
+            if (fail) {
+                dh = 1.f;
+                dl = 0.f;
             }
-            for (int j = b0; j < b1; ++j) {
-                float lh = 0.f, ll = 0.f;
-                if (tid < NBD) {
-                    const float4 a = A[j * NBDP + j];
-                    float dh = a.x, dl = a.y;
+            const float2 r = df_rsqrt(dh, dl);
+            if (tid > 0) {
+                const float4 l = df_norm(df_scale(A[tid * NBDP], r.x, r.y));
+                A[tid * NBDP] = l;
+                rLb[tid] = l;
+            } else {
+                if (fail) atomicMin(&st->not_pd_pivot, (int)k0);
+                float lh, ll;
+                df_mul(dh, dl, r.x, r.y, lh, ll);
+                Ld[0] = make_float2(lh, ll);
+                rrb[0] = r;
+            }
+        }
+        __syncthreads();
+        if (tid == DSIG + 32) st_release_cluster(rflag + 1, 1u);
+        for (int j = 0; j + 1 < NBD; ++j) {
+            if (tid < DCW) {
+                if (tid > j) {  // rows j + 1 .. 63 of column j + 1
+                    // the entry's update first: it does not wait for the pivot, and the
+                    // two chains interleave (thread j + 1's entry is the pivot itself)
+                    const float4 lj = A[(j + 1) * NBDP + j];  // L_{j+1,j}
+                    float4 v = A[tid * NBDP + j + 1];
+                    float4 dd = A[(j + 1) * NBDP + j + 1];
+                    cacc(v, cdf_neg(A[tid * NBDP + j]), cdf_conj(lj));
+                    cacc(dd, cdf_neg(lj), cdf_conj(lj));
+                    v = df_norm(v);
+                    dd = df_norm(dd);
+                    float dh = dd.x, dl = dd.y;
                     const bool fail = !(dh > 0.f) || !isfinite(dh);
                     if (fail) {
                         dh = 1.f;
                         dl = 0.f;
                     }
                     const float2 r = df_rsqrt(dh, dl);
-                    if (tid > j) {
-                        const float4 l = df_norm(df_scale(A[tid * NBDP + j], r.x, r.y));
-                        A[tid * NBDP + j] = l;
-                        rLb[j * NBD + tid] = l;
-                    } else if (tid == j) {
-                        if (fail && !bad) {
-                            atomicMin(&st->not_pd_pivot, (int)(k0 + j));
-                            bad = 1;
-                        }
+                    if (tid > j + 1) {
+                        const float4 l = df_norm(df_scale(v, r.x, r.y));
+                        A[tid * NBDP + j + 1] = l;
+                        rLb[(j + 1) * NBD + tid] = l;
+                    } else {
+                        if (fail) atomicMin(&st->not_pd_pivot, (int)(k0 + j + 1));
+                        float lh, ll;
                         df_mul(dh, dl, r.x, r.y, lh, ll);
-                        rrb[j] = r;
+                        Ld[j + 1] = make_float2(lh, ll);
+                        rrb[j + 1] = r;
                     }
                 }
-                __syncthreads();
-                if (tid == j) {
-                    A[j * NBDP + j] = make_float4(lh, ll, 0.f, 0.f);
-                    st_release_cluster(rflag, (unsigned)(j + 1));  // column j and r_j are in rank 1
+            } else {
+#pragma unroll
+                for (int k = 0; k < DUE; ++k) {
+                    if (uc[k] >= j + 2) {
+                        cacc(uv[k], cdf_neg(A[ui[k] * NBDP + j]), cdf_conj(A[uc[k] * NBDP + j]));
+                        uv[k] = df_norm(uv[k]);
+                        if (uc[k] == j + 2) A[ui[k] * NBDP + uc[k]] = uv[k];
+                    }
                 }
-                // rank-1 update of the owned entry if it lies right of and below column j
-                if (oc > j) {
-                    float4* tp = A + oi * NBDP + oc;
-                    const float4 bb = cdf_conj(A[oc * NBDP + j]);
-                    const float4 l = A[oi * NBDP + j];
-                    float4 v = *tp;
-                    cacc(v, make_float4(-l.x, -l.y, -l.z, -l.w), bb);
-                    *tp = df_norm(v);
-                }
-                __syncthreads();
             }
-            if (b1 < NBD) {  // the sub-block's updates of the entries right of it: i >= c >= b1
-                const int w = NBD - b1;
-                for (int e = tid; e < w * (w + 1) / 2; e += DIAG_THREADS) {
-                    int r, q;
-                    tri_index(e, r, q);
-                    const int i = b1 + r, c = b1 + q;
-                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-                    for (int k = b0; k < b1; ++k) cacc(acc, A[i * NBDP + k], cdf_conj(A[c * NBDP + k]));
-                    A[i * NBDP + c] = df_norm(df_cadd(A[i * NBDP + c], make_float4(-acc.x, -acc.y, -acc.z, -acc.w)));
-                }
-                __syncthreads();
-            }
+            __syncthreads();
+            // columns 0..j+1; each raiser has two steps for its release
+            if (tid == DSIG + 32 * (j & 1)) st_release_cluster(rflag + (j & 1), (unsigned)(j + 2));
         }
         for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
             const int i = e / NBD, j = e % NBD;
             if (i < nb && j < nb && j <= i) {
-                const float4 a = A[i * NBDP + j];
+                const float4 a = i == j ? make_float4(Ld[j].x, Ld[j].y, 0.f, 0.f) : A[i * NBDP + j];
                 const double2 g = make_double2(join_f64(a.x, a.y), join_f64(a.z, a.w));
                 G[(k0 + i) * ld + k0 + j] = g;
                 if (L32) L32[(k0 + i) * ldl + k0 + j] = make_float2(f64_to_f32_rn(g.x), f64_to_f32_rn(g.y));
@@ -620,43 +654,46 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(DIAG_THREADS)
         cl.sync();
     } else {
         float4* X = A;
-        if (tid == 0 && !diag_wait(&flag, 1u, st)) stop = 1;
+        float4 xp = make_float4(0.f, 0.f, 0.f, 0.f);  // thread c < 64: X_jc of the current step
+        unsigned seen = 0;
+        if (tid < DCW) {
+            if (!diag_wait(flag, 1u, seen, st)) {
+                stop = 1;
+            } else if (tid == 0) {
+                const float2 r = rb[0];
+                xp = df_norm(df_scale(X[0], r.x, r.y));
+                X[0] = xp;
+            }
+        }
         __syncthreads();
-        for (int b0 = 0; b0 < NBD && !stop; b0 += DSB) {
-            const int b1 = b0 + DSB;
-            // owned entry: row b0 + tid / b1, column tid % b1 (rows of the sub-block, columns
-            // left of its end; 16 b1 <= DIAG_THREADS entries)
-            const int oi = b0 + tid / b1, oc = tid % b1;
-            const bool own = tid < DSB * b1;
-            for (int j = b0; j < b1 && !stop; ++j) {
-                if (tid <= j) {
-                    const float2 r = rb[j];
-                    const float4 x = df_norm(df_scale(X[j * NBDP + tid], r.x, r.y));
-                    Xr[tid] = x;
-                    X[j * NBDP + tid] = x;
+        for (int j = 0; j + 1 < NBD; ++j) {
+            if (stop) break;  // set before the last barrier: the same in every thread
+            if (tid < DCW) {
+                if (tid <= j + 1) {  // row j + 1, columns 0 .. j + 1
+                    if (!diag_wait(flag, (unsigned)(j + 2), seen, st)) {
+                        stop = 1;
+                    } else {
+                        const float2 r = rb[j + 1];
+                        float4 y = X[(j + 1) * NBDP + tid];
+                        if (tid <= j) {
+                            cacc(y, cdf_neg(Lb[j * NBD + j + 1]), xp);
+                            y = df_norm(y);
+                        }
+                        xp = df_norm(df_scale(y, r.x, r.y));
+                        X[(j + 1) * NBDP + tid] = xp;
+                    }
                 }
-                __syncthreads();
-                // X_ic -= L_ij X_jc for rows j < i < b1, columns c <= j
-                if (own && oi > j && oc <= j) {
-                    float4* tp = X + oi * NBDP + oc;
-                    const float4 l = Lb[j * NBD + oi];
-                    float4 v = *tp;
-                    cacc(v, make_float4(-l.x, -l.y, -l.z, -l.w), Xr[oc]);
-                    *tp = df_norm(v);
+            } else {
+#pragma unroll
+                for (int k = 0; k < DUE; ++k) {
+                    if (uc[k] >= 0 && uc[k] <= j && ui[k] >= j + 2) {
+                        cacc(uv[k], cdf_neg(Lb[j * NBD + ui[k]]), X[j * NBDP + uc[k]]);
+                        uv[k] = df_norm(uv[k]);
+                        if (ui[k] == j + 2) X[ui[k] * NBDP + uc[k]] = uv[k];
+                    }
                 }
-                if (tid == 0 && j + 1 < NBD && !diag_wait(&flag, (unsigned)(j + 2), st)) stop = 1;
-                __syncthreads();
             }
-            if (b1 < NBD && !stop) {  // rows i >= b1, columns c < b1: X_ic -= sum_{k in the sub-block, k >= c} L_ik X_kc
-                const int n = (NBD - b1) * b1;
-                for (int e = tid; e < n; e += DIAG_THREADS) {
-                    const int i = b1 + e / b1, c = e % b1;
-                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-                    for (int k = (c > b0 ? c : b0); k < b1; ++k) cacc(acc, Lb[k * NBD + i], X[k * NBDP + c]);
-                    X[i * NBDP + c] = df_norm(df_cadd(X[i * NBDP + c], make_float4(-acc.x, -acc.y, -acc.z, -acc.w)));
-                }
-                __syncthreads();
-            }
+            __syncthreads();
         }
         cl.sync();  // rank 0 has published everything and may exit
         for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {

@@ -225,11 +225,15 @@ size_t factor_table_bytes(int64_t N, int slices);
 // the panel's columns of L32 and its diagonal inverses are final, and waited on by
 // the inverse before that panel
 // la (or nullptr): a second stream with its own status block and two events, on
-// which all but the next panel's columns of each trailing update run (lookahead)
+// which all but the next panel's columns of each trailing update run (lookahead);
+// and (s2 non-null) a third stream with two events for the solves and updates inside
+// a panel beyond the next diagonal block (block lookahead)
 struct TrailLookahead {
     cudaStream_t s;
     DevStatus* st;
     cudaEvent_t ev_tab, ev_done;
+    cudaStream_t s2;
+    cudaEvent_t ev_next, ev_side;
 };
 cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, float2* Dinv32, float2* L32,
                             int slices, DevStatus* st, cudaStream_t s, void* tab = nullptr,

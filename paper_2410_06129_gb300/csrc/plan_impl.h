@@ -109,6 +109,16 @@ struct pinv_plan {
     cudaStream_t s_trail = nullptr;
     pinv::DevStatus* st_trail = nullptr;
     cudaEvent_t ev_tab = nullptr, ev_trail = nullptr;
+    // inside a panel, the solves and updates beyond the next diagonal block run on
+    // this stream (high priority) beside that block (block lookahead)
+    cudaStream_t s_pnl = nullptr;
+    cudaEvent_t ev_next = nullptr, ev_side = nullptr;
+    // the refinement's exact Gram and digit tables, at the device's lowest stream
+    // priority beside the Cholesky and the inverse (only applies and the condition
+    // check read them; x_pending: the build has not waited for them yet)
+    cudaStream_t s_x = nullptr;
+    cudaEvent_t ev_xjoin = nullptr;
+    bool x_pending = false;
     std::vector<cudaEvent_t> ev_panel;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_xfork = nullptr, ev_chol = nullptr;
 
@@ -179,6 +189,11 @@ struct pinv_plan {
         if (ev_chol) cudaEventDestroy(ev_chol);
         if (ev_tab) cudaEventDestroy(ev_tab);
         if (ev_trail) cudaEventDestroy(ev_trail);
+        if (ev_next) cudaEventDestroy(ev_next);
+        if (ev_side) cudaEventDestroy(ev_side);
+        if (s_pnl) cudaStreamDestroy(s_pnl);
+        if (ev_xjoin) cudaEventDestroy(ev_xjoin);
+        if (s_x) cudaStreamDestroy(s_x);
         if (s_trail) cudaStreamDestroy(s_trail);
         if (s_inv) cudaStreamDestroy(s_inv);
         if (s_chol) cudaStreamDestroy(s_chol);

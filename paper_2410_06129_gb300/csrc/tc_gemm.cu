@@ -1011,19 +1011,20 @@ __global__ void __launch_bounds__(256) k_trsm_panel(float2* P, int64_t ldp, cons
     }
 }
 
-// G[i][j] -= sum_k P[i][k] conj(P[j][k]) for t0 <= j < jmax, j <= i (K = nbk <= 64;
-// jmax - t0 <= 32 CB). Dynamic shared memory: herk_panel_smem(CB).
+// G[i][j] -= sum_k P[i][k] conj(P[j][k]) for t0 <= j < jmax, j <= i, rows r0 <= i < N
+// (K = nbk <= 64; jmax - t0 <= 32 CB; r0 >= t0). Dynamic shared memory: herk_panel_smem(CB).
 constexpr size_t herk_panel_smem(int cb) { return sizeof(float2) * (PNL_ROWS * 64 + 64 * (32 * cb + 1)); }
 template <int CB>
 __global__ void __launch_bounds__(256) k_herk_panel(const float2* __restrict__ P, int64_t ldp, double2* G,
-                                                  int64_t ldg, int nbk, int64_t t0, int64_t jmax, int64_t N) {
+                                                  int64_t ldg, int nbk, int64_t t0, int64_t jmax, int64_t r0,
+                                                  int64_t N) {
     constexpr int WP = 32 * CB + 1;  // padded row of Bt: transposed stores spread over the banks
     extern __shared__ float2 pnl_smem[];
     float2(*Ai)[64] = reinterpret_cast<float2(*)[64]>(pnl_smem);
     float2(*Bt)[WP] = reinterpret_cast<float2(*)[WP]>(pnl_smem + PNL_ROWS * 64);  // Bt[k][c] = P[t0 + c][k]
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int W = (int)(jmax - t0);
-    const int64_t i0 = t0 + (int64_t)blockIdx.x * PNL_ROWS;
+    const int64_t i0 = r0 + (int64_t)blockIdx.x * PNL_ROWS;
     {
         float2 u[4];
 #pragma unroll
@@ -1084,7 +1085,7 @@ __global__ void __launch_bounds__(256) k_herk_panel(const float2* __restrict__ P
 
 template <int CB>
 static cudaError_t launch_herk_panel(const float2* P, int64_t ldp, double2* G, int64_t ldg, int nbk, int64_t t0,
-                                     int64_t jmax, int64_t N, cudaStream_t s) {
+                                     int64_t jmax, int64_t r0, int64_t N, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_herk_panel<CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1092,9 +1093,24 @@ static cudaError_t launch_herk_panel(const float2* P, int64_t ldp, double2* G, i
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int64_t rows = N - t0;
-    k_herk_panel<CB><<<(unsigned)((rows + PNL_ROWS - 1) / PNL_ROWS), 256, herk_panel_smem(CB), s>>>(P, ldp, G, ldg,
-                                                                                                  nbk, t0, jmax, N);
+    const int64_t rows = N - r0;
+    k_herk_panel<CB><<<(unsigned)((rows + PNL_ROWS - 1) / PNL_ROWS), 256, herk_panel_smem(CB), s>>>(
+        P, ldp, G, ldg, nbk, t0, jmax, r0, N);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// G[i][j] -= sum_k P[i][k] conj(P[j][k]) for columns t0 <= j < jmax (at most 192), rows r0 <= i < N
+static cudaError_t herk_panel(const float2* P, int64_t ldp, double2* G, int64_t ldg, int nbk, int64_t t0,
+                              int64_t jmax, int64_t r0, int64_t N, cudaStream_t s) {
+    const int64_t w = jmax - t0;
+    return w <= 64    ? launch_herk_panel<2>(P, ldp, G, ldg, nbk, t0, jmax, r0, N, s)
+           : w <= 128 ? launch_herk_panel<4>(P, ldp, G, ldg, nbk, t0, jmax, r0, N, s)
+                      : launch_herk_panel<6>(P, ldp, G, ldg, nbk, t0, jmax, r0, N, s);
+}
+static cudaError_t trsm_panel(float2* P, int64_t ldp, const float2* Dinv32, double2* G, int64_t ldg, int64_t k0,
+                              int nbk, int64_t row0, int64_t N, cudaStream_t s) {
+    k_trsm_panel<<<cdiv(N - row0, PNL_ROWS), 256, 0, s>>>(P, ldp, Dinv32, G, ldg, k0, nbk, row0, N);
     note_launch();
     return cudaGetLastError();
 }
@@ -1138,6 +1154,13 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
         cap = cenv ? std::atoi(cenv) : (N <= 16384 ? std::max(1, tc::sm_count() / 4) : 0);
     }
     bool pending = false;  // a side update of the previous panel may still run
+    // block lookahead inside a panel: after diagonal block k only the next block's
+    // 64 rows are solved, and its diagonal block updated, on the chain's stream; the
+    // rows below and the rest of the panel's columns go to la->s2 and run beside
+    // diagonal block k + 1, whose solve of the rows below waits for them. Each row of
+    // the solves and each entry of the updates is computed as without the lookahead.
+    const bool bla = ahead && la->s2;
+    bool side = false;  // la->s2 holds in-panel work the chain has not waited for
     for (int64_t p0 = 0; p0 < N; p0 += NBP) {
         const int64_t pend = std::min<int64_t>(N, p0 + NBP);
         for (int64_t k0 = p0; k0 < pend; k0 += NBK) {
@@ -1151,19 +1174,38 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
             if (e != cudaSuccess) return e;
             const int64_t rest = N - k0 - nbk;
             if (rest <= 0) break;
-            // panel solve of every row below the block
-            k_trsm_panel<<<cdiv(rest, PNL_ROWS), 256, 0, s>>>(L32 + k0, N, Dinv32 + kb * NBK * NBK, G, ld, k0,
-                                                              (int)nbk, k0 + nbk, N);
-            note_launch();
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
             const int64_t t0 = k0 + nbk;
-            if (t0 < pend) {  // the panel's remaining columns, all rows below
-                const int64_t w = pend - t0;  // <= 192
-                e = w <= 64    ? launch_herk_panel<2>(L32 + k0, N, G, ld, (int)nbk, t0, pend, N, s)
-                    : w <= 128 ? launch_herk_panel<4>(L32 + k0, N, G, ld, (int)nbk, t0, pend, N, s)
-                               : launch_herk_panel<6>(L32 + k0, N, G, ld, (int)nbk, t0, pend, N, s);
-                if (e != cudaSuccess) return e;
+            const float2* Dk = Dinv32 + kb * NBK * NBK;
+            if (side) {  // the rows below were updated by the previous block's side work
+                if ((e = cudaStreamWaitEvent(s, la->ev_side, 0)) != cudaSuccess) return e;
+                side = false;
             }
+            if (bla && t0 < pend) {
+                const int64_t t1 = std::min<int64_t>(t0 + NBK, pend);  // the next diagonal block
+                if ((e = trsm_panel(L32 + k0, N, Dk, G, ld, k0, (int)nbk, t0, t1, s)) != cudaSuccess) return e;
+                if ((e = herk_panel(L32 + k0, N, G, ld, (int)nbk, t0, t1, t0, t1, s)) != cudaSuccess) return e;
+                if (t1 < N) {
+                    if ((e = cudaEventRecord(la->ev_next, s)) != cudaSuccess) return e;
+                    if ((e = cudaStreamWaitEvent(la->s2, la->ev_next, 0)) != cudaSuccess) return e;
+                    if ((e = trsm_panel(L32 + k0, N, Dk, G, ld, k0, (int)nbk, t1, N, la->s2)) != cudaSuccess)
+                        return e;
+                    if ((e = herk_panel(L32 + k0, N, G, ld, (int)nbk, t0, pend, t1, N, la->s2)) != cudaSuccess)
+                        return e;
+                    if ((e = cudaEventRecord(la->ev_side, la->s2)) != cudaSuccess) return e;
+                    side = true;
+                }
+                continue;
+            }
+            // panel solve of every row below the block
+            if ((e = trsm_panel(L32 + k0, N, Dk, G, ld, k0, (int)nbk, t0, N, s)) != cudaSuccess) return e;
+            if (t0 < pend) {  // the panel's remaining columns, all rows below
+                if ((e = herk_panel(L32 + k0, N, G, ld, (int)nbk, t0, pend, t0, N, s)) != cudaSuccess) return e;
+            }
+        }
+        if (side) {
+            cudaError_t e = cudaStreamWaitEvent(s, la->ev_side, 0);
+            if (e != cudaSuccess) return e;
+            side = false;
         }
         if (ev_panel) {
             cudaError_t e = cudaEventRecord(ev_panel[p0 / NBP], s);
