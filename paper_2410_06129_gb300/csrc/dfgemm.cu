@@ -232,12 +232,13 @@ cudaError_t launch_adjoint_df(const EncodeDev& e, const double2* U, int64_t F, d
 // ------------------------------------------------------------------ exact Gram residual
 // Exact Gram for B0-free plans, G[n][n'] = T[i_n - i_n'] sum_c conj(s_c(n)) s_c(n')
 // + lambda delta, formed in FP64 from the Toeplitz table and stored as
-// double-float pairs [N][N] (both triangles). The residual of the normal
+// double-float pairs [N][N] (both triangles: the thread of n' <= n also writes the
+// conjugate to G[n'][n], so G is Hermitian to the bit). The residual of the normal
 // equations is then r = E^H d - G x with E^H d formed once per apply.
 __global__ void k_gram_exact(EncodeDev e, const double2* T, double lam, float4* G) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // n'
     const int64_t i = blockIdx.y;                                         // n
-    if (j >= e.N) return;
+    if (j > i) return;
     const int* gi = e.vox_ijk + 3 * i;
     const int* gj = e.vox_ijk + 3 * j;
     const int64_t Tx = 2 * e.nx - 1, Ty = 2 * e.ny - 1;
@@ -252,6 +253,7 @@ __global__ void k_gram_exact(EncodeDev e, const double2* T, double lam, float4* 
     }
     if (i == j) v.x += lam;
     G[i * e.N + j] = to_df(v);
+    if (j != i) G[j * e.N + i] = to_df(zconj(v));
 }
 
 cudaError_t launch_gram_exact(const EncodeDev& e, const double2* T, double lam, float4* G, cudaStream_t s) {
