@@ -530,19 +530,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(DIAG_THREADS)
     const int tid = threadIdx.x;
     const unsigned rank = cl.block_rank();
     const int nb = (int)((N - k0) < NBD ? (N - k0) : NBD);
+    griddep_wait();    // the block's updates have landed
+    griddep_launch();  // the next kernel's CTAs may take their SMs and wait for this one
     if (tid == 0) {
         flag[0] = flag[1] = 0;
         stop = 0;
     }
-    for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
-        const int i = e / NBD, j = e % NBD;
-        float4 v = make_float4(i == j ? 1.f : 0.f, 0.f, 0.f, 0.f);
-        if (rank == 0 && i < nb && j < nb && j <= i) {
-            const double2 g = G[(k0 + i) * ld + k0 + j];
-            const float2 re = split_f64(g.x), im = split_f64(g.y);
-            v = make_float4(re.x, re.y, im.x, im.y);
+    {  // the block's lower triangle (rank 0) or I (rank 1); all loads issued before the stores
+        constexpr int PER = NBD * NBD / DIAG_THREADS;
+        double2 g[PER];
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int e = tid + t * DIAG_THREADS, i = e / NBD, j = e % NBD;
+            g[t] = (rank == 0 && i < nb && j < nb && j <= i) ? G[(k0 + i) * ld + k0 + j]
+                                                              : make_double2(i == j ? 1.0 : 0.0, 0.0);
         }
-        A[i * NBDP + j] = v;
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int e = tid + t * DIAG_THREADS, i = e / NBD, j = e % NBD;
+            const float2 re = split_f64(g[t].x), im = split_f64(g[t].y);
+            A[i * NBDP + j] = make_float4(re.x, re.y, im.x, im.y);
+        }
     }
     // the entries this thread updates off the critical path; rank 0: (i, c), 2 <= c <= i,
     // numbered from the last column; rank 1: (i, c), c <= i - 2, numbered by row from row 2
@@ -721,9 +729,9 @@ cudaError_t launch_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0, 
             if (err != cudaSuccess) return err;
             attr2 = true;
         }
-        k_potrf_diag_df2<<<2, DIAG_THREADS, smem2, s>>>(G, ld, N, k0, Dinv, Dinv32, L32, ldl, st);
-        note_launch();
-        return cudaGetLastError();
+        cudaError_t err = launch_pdl(k_potrf_diag_df2, dim3(2), dim3(DIAG_THREADS), smem2, s, G, ld, N, k0, Dinv,
+                                     Dinv32, L32, ldl, st);
+        return err != cudaSuccess ? err : cudaGetLastError();
     }
     const size_t smem = 2 * NBD * NBDP * sizeof(float4);
     if (!attr) {

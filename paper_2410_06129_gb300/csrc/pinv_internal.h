@@ -16,6 +16,30 @@ namespace pinv {
 extern std::atomic<unsigned long long> g_launches;
 inline void note_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// Programmatic dependent launch (the Cholesky chain): a kernel launched with
+// launch_pdl may start while the kernel before it in its stream drains. Such a
+// kernel calls griddep_wait() before it touches global memory, which returns
+// once every earlier kernel of the stream has completed and its writes are
+// visible; griddep_launch() lets the next kernel's CTAs start (they then wait
+// in griddep_wait). In a kernel launched without the attribute both are no-ops.
+__device__ inline void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ inline void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <class... KA, class... A>
+inline cudaError_t launch_pdl(void (*k)(KA...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    note_launch();
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // ---------------------------------------------------------------------------
 // Device-side encoding description: everything a kernel needs to generate an
 // element of the coil-independent encoding A[m][n] = exp(-i2pi(k_m.r_n + df_n t_m))

@@ -401,6 +401,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(Sched sch, DevStatus* st, in
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    griddep_wait();  // launched behind the previous kernel of the stream: its writes and tile counter
     const long long wlim = st->wait_limit > 0 ? st->wait_limit : WAIT_LIMIT;  // pipeline waits
 
     if (threadIdx.x == 0) {
@@ -623,6 +624,7 @@ __global__ void __launch_bounds__(NTHREADS_BULK, 1) k_tc_bulk(Sched sch, DevStat
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    griddep_wait();  // launched behind the previous kernel of the stream: its writes and tile counter
     const long long wlim = st->wait_limit > 0 ? st->wait_limit : WAIT_LIMIT;  // pipeline waits
 
     if (threadIdx.x == 0) {
@@ -840,7 +842,7 @@ inline int wave_splits(int64_t per_split, int64_t len, int lo, int hi, int64_t o
 }
 
 template <class K, class... A>
-static cudaError_t launch_persistent(K kern, int threads, int smem, bool& attr, int64_t items, int cap,
+static cudaError_t launch_persistent(K kern, int threads, int smem, bool& attr, int64_t items, int cap, bool pdl,
                                      cudaStream_t s, const A&... args) {
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -850,30 +852,35 @@ static cudaError_t launch_persistent(K kern, int threads, int smem, bool& attr, 
     if (items == 0) return cudaSuccess;
     const int64_t limit = cap > 0 && cap < sm_count() ? cap : sm_count();
     const int64_t ctas = items < limit ? items : limit;
+    if (pdl) {
+        cudaError_t e = launch_pdl(kern, dim3((unsigned)ctas), dim3(threads), (size_t)smem, s, args...);
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     kern<<<(unsigned)ctas, threads, smem, s>>>(args...);
     note_launch();
     return cudaGetLastError();
 }
 
-// cap > 0: at most cap CTAs (SMs), leaving the others to concurrent work
+// cap > 0: at most cap CTAs (SMs), leaving the others to concurrent work; pdl:
+// programmatic dependent launch after the previous kernel of the stream
 template <int S, class Sched>
 static cudaError_t launch_sched(const Sched& sch, int64_t items, DevStatus* st, int site, cudaStream_t s,
-                                int cap = 0) {
+                                int cap = 0, bool pdl = false) {
     static bool attr = false;
     if constexpr (IsBulk<typename Sched::Prob>::value)
-        return launch_persistent(k_tc_bulk<S, Sched>, NTHREADS_BULK, Cfg<S>::SMEM, attr, items, cap, s, sch, st,
-                                 site);
+        return launch_persistent(k_tc_bulk<S, Sched>, NTHREADS_BULK, Cfg<S>::SMEM, attr, items, cap, pdl, s, sch,
+                                 st, site);
     else
-        return launch_persistent(k_tc<S, Sched>, NTHREADS, Cfg<S>::SMEM, attr, items, cap, s, sch, st, site);
+        return launch_persistent(k_tc<S, Sched>, NTHREADS, Cfg<S>::SMEM, attr, items, cap, pdl, s, sch, st, site);
 }
 
 // One problem over a grid.x x grid.y grid of tiles (bx = x, by = y). Launches
 // sharing a status block must run one after another (one stream).
 template <int S, class P>
 static cudaError_t launch(const P& p, dim3 grid, DevStatus* st, int site, cudaStream_t s, bool rev = false,
-                          int cap = 0) {
+                          int cap = 0, bool pdl = false) {
     const int64_t n = (int64_t)grid.x * grid.y;
-    return launch_sched<S>(OneProblem<P>{p, (int64_t)grid.x, n, rev}, n, st, site, s, cap);
+    return launch_sched<S>(OneProblem<P>{p, (int64_t)grid.x, n, rev}, n, st, site, s, cap, pdl);
 }
 
 // Several problems of one kind in one persistent launch; the arrays live in

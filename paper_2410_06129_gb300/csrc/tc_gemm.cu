@@ -562,6 +562,8 @@ __global__ void __launch_bounds__(256) k_tab_panel(const float2* __restrict__ L3
     const int64_t kc = blockIdx.x, rt = blockIdx.y, kcn = gridDim.x;
     const int r = threadIdx.x & (BM - 1), g = threadIdx.x >> 7;
     const int64_t i = r0 + rt * BM + r, k0 = kc * KC + 8 * g;
+    griddep_wait();
+    griddep_launch();
     float2 v[8];
     load8f(L32 + (i < N ? i : 0) * ldl + p0 + k0, i < N && k0 < kw ? (int)(kw - k0) : 0, v);
 #pragma unroll
@@ -829,8 +831,9 @@ struct ReconStep2TC {
 
 template <class P>
 static cudaError_t run(const P& p, dim3 grid, int slices, DevStatus* st, int site, cudaStream_t s,
-                       bool rev = false, int cap = 0) {
-    return slices == 3 ? tc::launch<3>(p, grid, st, site, s, rev, cap) : tc::launch<2>(p, grid, st, site, s, rev, cap);
+                       bool rev = false, int cap = 0, bool pdl = false) {
+    return slices == 3 ? tc::launch<3>(p, grid, st, site, s, rev, cap, pdl)
+                       : tc::launch<2>(p, grid, st, site, s, rev, cap, pdl);
 }
 
 static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
@@ -956,6 +959,8 @@ __global__ void __launch_bounds__(256) k_trsm_panel(float2* P, int64_t ldp, cons
     __shared__ float2 A[PNL_ROWS][64];
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int64_t i0 = row0 + (int64_t)blockIdx.x * PNL_ROWS;
+    griddep_wait();
+    griddep_launch();
     {
         float2 v[16], u[4];
 #pragma unroll
@@ -1025,6 +1030,8 @@ __global__ void __launch_bounds__(256) k_herk_panel(const float2* __restrict__ P
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int W = (int)(jmax - t0);
     const int64_t i0 = r0 + (int64_t)blockIdx.x * PNL_ROWS;
+    griddep_wait();
+    griddep_launch();
     {
         float2 u[4];
 #pragma unroll
@@ -1094,10 +1101,9 @@ static cudaError_t launch_herk_panel(const float2* P, int64_t ldp, double2* G, i
         attr = true;
     }
     const int64_t rows = N - r0;
-    k_herk_panel<CB><<<(unsigned)((rows + PNL_ROWS - 1) / PNL_ROWS), 256, herk_panel_smem(CB), s>>>(
-        P, ldp, G, ldg, nbk, t0, jmax, r0, N);
-    note_launch();
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(k_herk_panel<CB>, dim3((unsigned)((rows + PNL_ROWS - 1) / PNL_ROWS)), dim3(256),
+                               herk_panel_smem(CB), s, P, ldp, G, ldg, nbk, t0, jmax, r0, N);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // G[i][j] -= sum_k P[i][k] conj(P[j][k]) for columns t0 <= j < jmax (at most 192), rows r0 <= i < N
@@ -1110,9 +1116,9 @@ static cudaError_t herk_panel(const float2* P, int64_t ldp, double2* G, int64_t 
 }
 static cudaError_t trsm_panel(float2* P, int64_t ldp, const float2* Dinv32, double2* G, int64_t ldg, int64_t k0,
                               int nbk, int64_t row0, int64_t N, cudaStream_t s) {
-    k_trsm_panel<<<cdiv(N - row0, PNL_ROWS), 256, 0, s>>>(P, ldp, Dinv32, G, ldg, k0, nbk, row0, N);
-    note_launch();
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(k_trsm_panel, dim3(cdiv(N - row0, PNL_ROWS)), dim3(256), 0, s, P, ldp, Dinv32, G,
+                               ldg, k0, nbk, row0, N);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // Panel table (B tiles of conj(L), rows from r0, kw panel columns from p0)
@@ -1123,12 +1129,12 @@ size_t factor_table_bytes(int64_t N, int slices) { return 2 * panel_table_bytes(
 static cudaError_t panel_table(const float2* L32, int64_t N, int64_t p0, int64_t kw, int64_t r0, int slices,
                                uint8_t* tab, cudaStream_t s) {
     const dim3 g(cdiv(kw, tc::KC), cdiv(N - r0, tc::BM));
-    if (slices == 3)
-        tc::k_tab_panel<3><<<g, 256, 0, s>>>(L32, N, N, p0, kw, r0, tab);
-    else
-        tc::k_tab_panel<2><<<g, 256, 0, s>>>(L32, N, N, p0, kw, r0, tab);
-    note_launch();
-    return cudaGetLastError();
+    const int64_t ld = N;
+    cudaError_t e = slices == 3 ? launch_pdl(tc::k_tab_panel<3>, g, dim3(256), 0, s, (const float2*)L32, ld, N, p0,
+                                             kw, r0, tab)
+                                : launch_pdl(tc::k_tab_panel<2>, g, dim3(256), 0, s, (const float2*)L32, ld, N, p0,
+                                             kw, r0, tab);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // Two-level blocking: 64-wide diagonal blocks inside 256-wide panels. Inside a
@@ -1222,7 +1228,7 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
                 if ((e = panel_table(L32, N, p0, pend - p0, pend, slices, (uint8_t*)tab, s)) != cudaSuccess) return e;
                 const int64_t near = ahead ? std::min<int64_t>(nt, NBP / tc::BN) : nt;
                 tc::HerkBulk hp{(const uint8_t*)tab, G, ld, N, pend, nt, kcn, slices, 0, near};
-                e = run(hp, dim3((unsigned)(nt * near), 1), slices, st, 4, s);
+                e = run(hp, dim3((unsigned)(nt * near), 1), slices, st, 4, s, false, 0, true);
                 if (e == cudaSuccess && near < nt) {
                     if ((e = cudaEventRecord(la->ev_tab, s)) != cudaSuccess) return e;
                     if ((e = cudaStreamWaitEvent(la->s, la->ev_tab, 0)) != cudaSuccess) return e;
