@@ -241,14 +241,33 @@ def run_reference(args):
 SERVE_BUDGET_FULL = 120e9  # bytes of resident plans for the full serving workload
 
 
+def _phase_stats(sv, tickets, frames):
+    """Latency and throughput of one phase from the server's per-request times."""
+    import numpy as np
+    tt = [sv.times(t) for t in tickets]
+    lat = np.array([q["done"] - q["enqueue"] for q in tt])
+    span_s = (max(q["done"] for q in tt) - min(q["enqueue"] for q in tt)) * 1e-3
+    dev = [q for q in tt if q["dev_start"] >= 0]
+    dev_s = (max(q["dev_end"] for q in dev) - min(q["dev_start"] for q in dev)) * 1e-3 if dev else None
+    return {"requests": len(tickets), "frames": float(frames),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "frames_per_s": frames / span_s if span_s > 0 else None,
+            "requests_per_s": len(tickets) / span_s if span_s > 0 else None,
+            "device_span_s": dev_s}
+
+
 def run_serve(prec, refine, side_div, rate_hz, duration_s, budget, max_slots, recon_mode,
-              check_plans=0, seed=4100):
+              check_plans=0, seed=4100, sweep=(), sweep_s=1.0, p99_bound_ms=100.0):
     """Serving loop on the Poisson trace of the 32-plan serving workload.
 
     Requests arrive at their trace times (host thread sleeping until each
     arrival), each one of 32 registered plans with 1-64 frames of complex64
     k-space already resident in HBM; plans are built on admission and
-    evicted LRU under `budget`. Returns the server's latency statistics.
+    evicted LRU under `budget`. Returns the server's latency statistics at
+    the offered rate, then, on the same server with the plans it kept
+    resident: the capacity (the trace's requests enqueued at once) and, for
+    each rate of `sweep`, a `sweep_s`-second trace's latencies; `max_rate_hz`
+    is the highest swept rate whose p99 stays within `p99_bound_ms`.
     """
     import torch
 
@@ -265,17 +284,23 @@ def run_serve(prec, refine, side_div, rate_hz, duration_s, budget, max_slots, re
     datas = [torch.randn((64, p.n_coils * p.n_samples), generator=gen, device="cuda",
                          dtype=torch.complex64) for p in geo]
     torch.cuda.synchronize()
-    with Server(budget_bytes=int(budget), max_slots=max_slots) as sv:
-        ids = [sv.register_inputs(p, precision=prec, refine_max_iters=refine, recon_mode=recon_mode)
-               for p in geo]
+
+    def play(sv, ids, tr, paced=True):
         tickets = []
         t0 = time.perf_counter()
-        for t_arr, i, F in trace:
+        for t_arr, i, F in tr:
             dt = t0 + t_arr - time.perf_counter()
-            if dt > 0:
+            if paced and dt > 0:
                 time.sleep(dt)
             tickets.append(sv.enqueue(ids[i], datas[i][:F], sync_inputs=False))
         status = [sv.wait(t, timeout=3600.0) for t, _ in tickets]
+        return tickets, status
+
+    with Server(budget_bytes=int(budget), max_slots=max_slots) as sv:
+        ids = [sv.register_inputs(p, precision=prec, refine_max_iters=refine, recon_mode=recon_mode)
+               for p in geo]
+        t0 = time.perf_counter()
+        tickets, status = play(sv, ids, trace)
         wall = time.perf_counter() - t0
         st = sv.stats()
         # accuracy of served images against FP64 plans on the same data
@@ -291,17 +316,36 @@ def run_serve(prec, refine, side_div, rate_hz, duration_s, budget, max_slots, re
                     x64 = p64.apply(datas[i][:F].to(torch.complex128))
                 e = float(torch.linalg.norm(out.to(torch.complex128) - x64) / torch.linalg.norm(x64))
                 worst = e if worst is None else max(worst, e)
+        # capacity: the same requests at once, plans as the trace left them
+        builds0 = sv.stats()["builds"]
+        cap_t, cap_s = play(sv, ids, trace, paced=False)
+        capacity = _phase_stats(sv, [t for t, _ in cap_t], sum(F for _, _, F in trace))
+        capacity["ok"] = int(sum(s == L.OK for s in cap_s))
+        capacity["builds"] = int(sv.stats()["builds"] - builds0)
+        capacity["what"] = "the trace's requests enqueued at once on the same server (saturated throughput)"
+        rates = []
+        for k, r in enumerate(sweep):
+            tr = synth.serve_trace(r, sweep_s, len(geo), seed=seed + 1 + k)
+            tk, ss = play(sv, ids, tr)
+            ph = _phase_stats(sv, [t for t, _ in tk], sum(F for _, _, F in tr))
+            ph.update(rate_hz=r, ok=int(sum(s == L.OK for s in ss)))
+            rates.append(ph)
+        ok_rates = [q["rate_hz"] for q in rates if q["p99_ms"] <= p99_bound_ms and q["ok"] == q["requests"]]
     frames = float(st["frames"])
     return {
         "requests": len(trace), "ok": int(sum(s == L.OK for s in status)), "failed": int(st["failed"]),
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
         "frames_per_s": frames / st["span_s"] if st["span_s"] > 0 else None,
+        "frames_per_s_note": "at the offered rate: bounded by the trace, not by the server (see capacity)",
         "frames": frames, "builds": int(st["builds"]), "evictions": int(st["evictions"]),
         "recon_drops": int(st["recon_drops"]),
         "wall_s": wall, "trace_s": duration_s, "rate_hz": rate_hz, "slots": max_slots,
         "budget_gb": budget / 1e9, "refine_steps": refine,
         "recon": "explicit" if recon_mode == L.RECON_STORE else "factor-only",
         "nrmse_vs_fp64_max": worst, "nrmse_plans_checked": check_plans,
+        "capacity": capacity,
+        "rate_sweep": {"seconds_each": sweep_s, "p99_bound_ms": p99_bound_ms, "phases": rates,
+                       "max_rate_hz": max(ok_rates) if ok_rates else None},
     }
 
 
@@ -530,6 +574,9 @@ def main():
     ap.add_argument("--serve-duration", type=float, default=3.0, help="seconds of Poisson arrivals")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-sweep", default="100,200,400,800,1600",
+                    help="offered rates (req/s) swept for one second each on the same server, after the "
+                         "trace and the capacity burst ('' = none)")
     ap.add_argument("--serve-refine", type=int, default=3)
     ap.add_argument("--batch", default="on", choices=["on", "off"],
                     help="workload 3: 16 uneven plans x 256 frames as one graph-replayed batch")
@@ -724,9 +771,10 @@ def main():
         serve = {"workload": ("32 plans, side 32-128" if full else "32 plans, side 16-64 (cfg side / 2)")
                  + ", 1-16 coils, 1-2 x N samples per coil, Poisson arrivals, 1-64 c64 frames",
                  "budget_rule": "120 GB x (this plan set's footprint / the full set's)"}
+        sweep = [float(r) for r in args.serve_sweep.split(",") if r] if args.serve_sweep else []
         serve["mixed"] = run_serve(prec, args.serve_refine if prec != L.FP64 else 0, div, args.serve_rate,
                                    args.serve_duration, budget, args.serve_slots,
-                                   L.RECON_STORE, check_plans=4)
+                                   L.RECON_STORE, check_plans=4, sweep=sweep)
         if prec != L.FP64 and args.serve_fp64_duration > 0:
             serve["fp64"] = run_serve(L.FP64, 0, div, args.serve_rate, args.serve_fp64_duration, budget,
                                       args.serve_slots, L.RECON_NONE)

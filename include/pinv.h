@@ -368,6 +368,16 @@ pinv_status pinv_serve_poll(pinv_server* server, uint64_t ticket, int* done, pin
 /* Block until the request finished (PINV_ERR_TIMEOUT after timeout_s seconds). */
 pinv_status pinv_serve_wait(pinv_server* server, uint64_t ticket, double timeout_s, pinv_status* result);
 
+/* Times of a finished request, in milliseconds after the server was created:
+ * times_ms[0] enqueue and [1] completion as the worker saw it (host clock);
+ * [2] start and [3] end of its device work, read from timing events on its
+ * slot's stream (device clock, from an event recorded at creation; the start
+ * is when the stream reached the request, after any plan build it waited for;
+ * both -1 for a request that failed or had no frames). Two requests whose
+ * device intervals intersect ran on the device at the same time.
+ * PINV_ERR_INVALID_ARG for an unknown or unfinished ticket. */
+pinv_status pinv_serve_times(pinv_server* server, uint64_t ticket, double* times_ms);
+
 /* Counters and latency percentiles of the requests completed so far. */
 pinv_status pinv_server_stats(pinv_server* server, pinv_server_stats_t* out);
 

@@ -16,7 +16,9 @@
 //     recently used first; a plan that cannot fit fails its request with
 //     PINV_ERR_BUDGET;
 //   * completion is detected with events; latency runs from enqueue to the
-//     moment the worker sees the request's event complete.
+//     moment the worker sees the request's event complete. Each request also
+//     keeps the device times of its work (timing events on its slot's stream),
+//     so the overlap of slots can be read back (pinv_serve_times).
 //   * host fault injection (PINV_FAULT, read when the server is created) makes
 //     failures on the host, never on the device: a comma-separated list of
 //     one-shot faults, "alloc:P" (the next admission of plan P fails as if its
@@ -29,6 +31,7 @@
 // Each request's result is computed by the same kernels in the same order as
 // a standalone pinv_apply, so it does not depend on what else is in flight.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <condition_variable>
 #include <cstdlib>
@@ -74,6 +77,7 @@ struct Request {
     pinv_done_cb cb = nullptr;
     void* user = nullptr;
     double t_enqueue = 0;
+    double dev_start_ms = -1, dev_end_ms = -1;  // device times of its work (ms after the server's origin)
 };
 
 // one-shot host fault (PINV_FAULT)
@@ -115,6 +119,7 @@ std::vector<Fault> parse_faults(const char* spec) {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;  // timing: the request's work starts / ends on the stream
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
     bool busy = false;
@@ -131,6 +136,10 @@ struct pinv_server {
     std::deque<Request> queue;
     std::vector<Slot> slots;
     std::unordered_map<uint64_t, pinv_status> finished;
+    // enqueue and completion (host, ms after creation), device start and end of the work
+    std::unordered_map<uint64_t, std::array<double, 4>> times;
+    double t_origin = 0;                // host time of creation
+    cudaEvent_t origin = nullptr;       // recorded at creation on the build stream
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::thread worker;
@@ -196,6 +205,7 @@ void pinv_server::finish(const Request& q, pinv_status st, std::unique_lock<std:
         lk.lock();
     }
     finished[q.ticket] = st;
+    times[q.ticket] = {(q.t_enqueue - t_origin) * 1e3, (t - t_origin) * 1e3, q.dev_start_ms, q.dev_end_ms};
     if (st == PINV_OK) {
         ++completed;
         frames += (double)q.frames;
@@ -306,12 +316,15 @@ bool pinv_server::dispatch_one(std::unique_lock<std::mutex>& lk) {
         if (st == PINV_OK) {
             ApplyScratch sc;
             apply_scratch_layout(r.plan, q.frames, q.dtype, slot->scratch, &sc);
-            if (cudaStreamWaitEvent(slot->stream, r.ready, 0) != cudaSuccess)
+            if (cudaStreamWaitEvent(slot->stream, r.ready, 0) != cudaSuccess ||
+                cudaEventRecord(slot->t0, slot->stream) != cudaSuccess)
                 st = set_error(PINV_ERR_CUDA, "cudaStreamWaitEvent");
             else
                 st = apply_impl(r.plan, q.data, q.image, q.frames, q.dtype, slot->stream, sc);
         }
     }
+    if (st == PINV_OK && q.frames > 0 && cudaEventRecord(slot->t1, slot->stream) != cudaSuccess)
+        st = set_error(PINV_ERR_CUDA, "cudaEventRecord");
     if (st == PINV_OK && cudaEventRecord(slot->done, slot->stream) != cudaSuccess)
         st = set_error(PINV_ERR_CUDA, "cudaEventRecord");
     if (st != PINV_OK) {
@@ -348,7 +361,13 @@ bool pinv_server::reap(std::unique_lock<std::mutex>& lk) {
             st = PINV_ERR_TIMEOUT;
         }
         if (r.failed != PINV_OK && r.plan && r.inflight == 0) evict(r);
-        const Request q = s.req;
+        Request q = s.req;
+        float a = 0.f, b = 0.f;
+        if (st == PINV_OK && q.frames > 0 && cudaEventElapsedTime(&a, origin, s.t0) == cudaSuccess &&
+            cudaEventElapsedTime(&b, origin, s.t1) == cudaSuccess) {
+            q.dev_start_ms = a;
+            q.dev_end_ms = b;
+        }
         double ms = 0.0;
         if (st == PINV_OK && take_fault(FAULT_DELAY, (int64_t)q.ticket, &ms))
             delayed.push_back({now_s() + ms * 1e-3, q});  // reported later; the slot is free now
@@ -402,17 +421,24 @@ pinv_status pinv_server_create(size_t hbm_budget_bytes, int max_slots, pinv_serv
     auto* sv = new pinv_server();
     sv->budget = hbm_budget_bytes;
     if (cudaGetDevice(&sv->device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&sv->build_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&sv->build_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&sv->origin) != cudaSuccess) {
         delete sv;
         return set_error(PINV_ERR_CUDA, "server stream creation failed");
     }
     sv->slots.resize(max_slots);
     for (auto& s : sv->slots) {
         if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreate(&s.t0) != cudaSuccess || cudaEventCreate(&s.t1) != cudaSuccess) {
             delete sv;
             return set_error(PINV_ERR_CUDA, "slot stream creation failed");
         }
+    }
+    sv->t_origin = now_s();
+    if (cudaEventRecord(sv->origin, sv->build_stream) != cudaSuccess) {
+        delete sv;
+        return set_error(PINV_ERR_CUDA, "server event record failed");
     }
     sv->faults = parse_faults(std::getenv("PINV_FAULT"));
     sv->worker = std::thread([sv] { sv->run(); });
@@ -509,6 +535,15 @@ pinv_status pinv_serve_wait(pinv_server* sv, uint64_t ticket, double timeout_s, 
     return PINV_OK;
 }
 
+pinv_status pinv_serve_times(pinv_server* sv, uint64_t ticket, double* times_ms) {
+    if (!sv || !times_ms) return set_error(PINV_ERR_INVALID_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->times.find(ticket);
+    if (it == sv->times.end()) return set_error(PINV_ERR_INVALID_ARG, "unknown or unfinished ticket");
+    for (int i = 0; i < 4; ++i) times_ms[i] = it->second[i];
+    return PINV_OK;
+}
+
 pinv_status pinv_server_stats(pinv_server* sv, pinv_server_stats_t* o) {
     if (!sv || !o) return set_error(PINV_ERR_INVALID_ARG, "null argument");
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -554,8 +589,11 @@ void pinv_server_destroy(pinv_server* sv) {
     for (auto& s : sv->slots) {
         if (s.scratch) cudaFree(s.scratch);
         if (s.done) cudaEventDestroy(s.done);
+        if (s.t0) cudaEventDestroy(s.t0);
+        if (s.t1) cudaEventDestroy(s.t1);
         if (s.stream) cudaStreamDestroy(s.stream);
     }
+    if (sv->origin) cudaEventDestroy(sv->origin);
     if (sv->build_stream) cudaStreamDestroy(sv->build_stream);
     delete sv;
 }

@@ -78,6 +78,14 @@ class Server:
             self._live.pop(ticket, None)
         return bool(done.value), res.value
 
+    def times(self, ticket: int) -> dict:
+        """Times of a finished request in ms after the server's creation: enqueue and
+        done (host clock), dev_start and dev_end of its device work (device clock; -1
+        when it ran nothing)."""
+        t = (C.c_double * 4)()
+        L.check(L.load().pinv_serve_times(self._h, ticket, t))
+        return {"enqueue": t[0], "done": t[1], "dev_start": t[2], "dev_end": t[3]}
+
     def stats(self) -> dict:
         s = L.ServerStats()
         L.check(L.load().pinv_server_stats(self._h, C.byref(s)))

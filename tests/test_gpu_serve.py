@@ -255,3 +255,36 @@ def test_host_fault_injection_leaves_other_requests_intact(monkeypatch):
             assert torch.equal(out, x), f"ticket {t} differs from a standalone apply"
     assert st["failed"] == 3 and st["completed"] == len(reqs) - 3
     assert st["builds"] == len(cases)  # the failed admission and build were retried once each
+
+
+def test_two_slots_run_on_the_device_at_the_same_time():
+    """Two requests of two resident FP64 plans, enqueued together on a two-slot
+    server: the device intervals of their work (timing events on the slot
+    streams, pinv_serve_times) intersect, each request's times are ordered, and
+    both images equal standalone applies.
+    32x32, 4 coils, 2048 samples per coil, 64 frames: E^H d alone is about 5e8
+    complex FP64 products per request, far longer than the dispatch of the other."""
+    from paper_2410_06129_gb300.serve import Server
+    kw = dict(precision=L.FP64, recon_mode=L.RECON_NONE)
+    ps = [synth.make_plan(32, 4, "spiral", 64, 2140, 1e-3, samples=2048, interleaves=2),
+          synth.make_plan(32, 4, "radial", 64, 2141, 1e-3, spokes=32, per_spoke=64)]
+    data = [torch.from_numpy(p.data).cuda() for p in ps]
+    expect = [_standalone(p, kw, d) for p, d in zip(ps, data)]
+    with Server(budget_bytes=8 << 30, max_slots=2) as sv:
+        ids = [sv.register_inputs(p, **kw) for p in ps]
+        for i in range(2):  # build both plans first: the pair then waits on no build
+            t, _ = sv.enqueue(ids[i], data[i][:1])
+            assert sv.wait(t) == L.OK
+        pair = [sv.enqueue(ids[i], data[i]) for i in range(2)]
+        for t, _ in pair:
+            assert sv.wait(t) == L.OK
+        tt = [sv.times(t) for t, _ in pair]
+        with pytest.raises(L.PinvError):
+            sv.times(10 ** 9)
+    for (t, out), x in zip(pair, expect):
+        assert torch.equal(out, x)
+    a, b = tt
+    for q in tt:
+        assert 0 <= q["enqueue"] <= q["done"]
+        assert 0 <= q["dev_start"] < q["dev_end"]
+    assert max(a["dev_start"], b["dev_start"]) < min(a["dev_end"], b["dev_end"]), tt
