@@ -41,9 +41,12 @@
  * Device memory
  *   - Plans, their apply scratch and the build's temporaries take device memory
  *     from one pool per device owned by the library. The pool keeps memory that
- *     plans give back, so creating or building a plan again maps none, and
- *     releases it (trims the pool) when the last plan is destroyed. The device's
- *     default stream-ordered pool and the caller's allocator are not touched.
+ *     plans give back, so creating or building a plan again maps none. When the
+ *     last plan is destroyed it is trimmed to 8 GiB (environment PINV_POOL_KEEP_MB:
+ *     another size in MiB, 0 returns everything), so a program that creates and
+ *     destroys plans of up to that size one after another maps nothing again.
+ *     The device's default stream-ordered pool and the caller's allocator are not
+ *     touched.
  */
 #ifndef PINV_H
 #define PINV_H
@@ -264,8 +267,8 @@ pinv_status pinv_plan_keep_gram(pinv_plan* plan, int keep);
 pinv_status pinv_plan_info(const pinv_plan* plan, pinv_plan_info_t* out);
 
 /* Free the plan and its device memory (synchronises the device). The memory goes
- * back to the library's pool, which is trimmed when the last plan is destroyed.
- * NULL is a no-op. */
+ * back to the library's pool, which is trimmed to its kept size (8 GiB, or
+ * PINV_POOL_KEEP_MB) when the last plan is destroyed. NULL is a no-op. */
 void pinv_plan_destroy(pinv_plan* plan);
 
 /* ------------------------------------------------------------------------
