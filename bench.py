@@ -833,6 +833,11 @@ def main():
     return 0
 
 
+# DRAM bytes (read + write) of one Gram launch at the 64x64 SENSE workload, from the ncu
+# capture summarised in profiles/ncu_gram_bulk_64x64_8coil.md (the kernel is unchanged since)
+GRAM_TRAFFIC_64 = 2062060544 + 119328256
+
+
 def _roofline(prec, inp, mi, peaks, peak_src):
     """The roofline object of the step's dominant kernel, and the Gram kernel
     against the tensor-core peak (counted on the MMAs it issues)."""
@@ -855,7 +860,11 @@ def _roofline(prec, inp, mi, peaks, peak_src):
                 "achieved": gram["issued_tflops"], "peak": pk, "peak_source": gram["peak_source"],
                 "frac": gram["frac_issued"], "useful_tflops": gram["useful_tflops"],
                 "counted": "MMAs issued (6 split products per complex MAC of the Hermitian Gram)",
-                "traffic": None, "ms_per_launch": ms}
+                "traffic": GRAM_TRAFFIC_64 if (N == 4096 and pairs == 6) else None,
+                "traffic_unit": "bytes per launch",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_tc_bulk<GramBulk> "
+                                  "at this workload (profiles/ncu_gram_bulk_64x64_8coil.md)",
+                "ms_per_launch": ms}
     else:
         ms = mi["ms_gram"]
         flops = 8.0 * N * (N + 1) / 2 * inp.n_samples * inp.n_coils
