@@ -112,6 +112,23 @@ def test_recon_tc_isolated(prec, bulk, monkeypatch):
     assert np.allclose(np.triu(W, 1), 0)
 
 
+@pytest.mark.parametrize("prec", [L.MIXED_BF16X6])
+def test_recon_against_oracle_recon(prec):
+    """The mixed explicit Recon (Eq. 8 formed from the split-precision factor) against
+    the oracle's FP64 Recon = W^H W E^H. The factor's rounding is about the split
+    arithmetic's 2^-24 relative, which the inverse amplifies by up to kappa(G), so
+    the bar is 20 kappa_est 2^-24 with the plan's own condition estimate; spiral and
+    radial-with-B0 plans of N = 256 and 324."""
+    for p in (synth.make_plan(16, 3, "radial", 1, 2102, 1e-3, b0=True, spokes=20, per_spoke=33),
+              synth.make_plan(18, 4, "spiral", 1, 2111, 1e-3, samples=900, interleaves=2)):
+        pl = _plan(p, precision=prec, refine_max_iters=0).build()
+        R = pl.export(L.EXPORT_RECON).cpu().numpy()
+        kappa = pl.info()["kappa_est"]
+        ref = oracle_all(p).R
+        err = rel(R, ref)
+        assert err < 20.0 * kappa * 2.0 ** -24, (err, kappa)
+
+
 def test_recon_bulk_chunks_bit_identical(monkeypatch):
     """The bulk Recon over one sample tile per chunk (a 1 MB chunk cap) gives the
     same Recon bit for bit as one chunk: every tile sums the same tables in the
