@@ -323,6 +323,15 @@ def run_serve(prec, refine, side_div, rate_hz, duration_s, budget, max_slots, re
         capacity["ok"] = int(sum(s == L.OK for s in cap_s))
         capacity["builds"] = int(sv.stats()["builds"] - builds0)
         capacity["what"] = "the trace's requests enqueued at once on the same server (saturated throughput)"
+        # the same burst with same-plan requests merged into one apply (up to 64 frames)
+        sv.set_merge(64)
+        mt, ms_ = play(sv, ids, trace, paced=False)
+        merged = _phase_stats(sv, [t for t, _ in mt], sum(F for _, _, F in trace))
+        merged["ok"] = int(sum(q == L.OK for q in ms_))
+        merged["applies"] = len({round(sv.times(t)["dev_start"], 6) for t, _ in mt})
+        merged["what"] = "the same burst with queued requests of one plan merged into one apply (<= 64 frames)"
+        capacity["merged"] = merged
+        sv.set_merge(0)
         rates = []
         for k, r in enumerate(sweep):
             tr = synth.serve_trace(r, sweep_s, len(geo), seed=seed + 1 + k)

@@ -371,6 +371,16 @@ pinv_status pinv_serve_poll(pinv_server* server, uint64_t ticket, int* done, pin
 /* Block until the request finished (PINV_ERR_TIMEOUT after timeout_s seconds). */
 pinv_status pinv_serve_wait(pinv_server* server, uint64_t ticket, double timeout_s, pinv_status* result);
 
+/* Merging (off until set): a request dispatched to a slot takes with it the
+ * requests of the same plan and element type queued behind it, while their
+ * frames together stay within max_frames (0 turns merging off). Their frames are
+ * gathered into the slot's scratch, reconstructed by one apply and scattered to
+ * each request's image; each request still completes and is counted on its own,
+ * and its image is the one a standalone apply of its frames gives (up to the
+ * order of sums in kernels whose split depends on the frame count). Merging is
+ * not done while host faults (PINV_FAULT) are set. */
+pinv_status pinv_server_set_merge(pinv_server* server, int64_t max_frames);
+
 /* Times of a finished request, in milliseconds after the server was created:
  * times_ms[0] enqueue and [1] completion as the worker saw it (host clock);
  * [2] start and [3] end of its device work, read from timing events on its

@@ -113,6 +113,7 @@ SIGNATURES = {
     "pinv_serve_poll": (C.c_int, [_VP, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pinv_serve_wait": (C.c_int, [_VP, C.c_uint64, C.c_double, C.POINTER(C.c_int)]),
     "pinv_serve_times": (C.c_int, [_VP, C.c_uint64, C.POINTER(C.c_double)]),
+    "pinv_server_set_merge": (C.c_int, [_VP, C.c_int64]),
     "pinv_server_stats": (C.c_int, [_VP, C.POINTER(ServerStats)]),
     "pinv_server_destroy": (None, [_VP]),
 }

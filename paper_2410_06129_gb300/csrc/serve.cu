@@ -19,6 +19,11 @@
 //     moment the worker sees the request's event complete. Each request also
 //     keeps the device times of its work (timing events on its slot's stream),
 //     so the overlap of slots can be read back (pinv_serve_times).
+//   * with merging on (pinv_server_set_merge), requests of the plan at the head
+//     of the queue that wait behind it with the same element type join it in one
+//     apply, up to a frame cap: their frames are gathered into the slot's scratch
+//     (device-to-device copies on the slot's stream), reconstructed together and
+//     scattered back; each still completes, and is counted, on its own;
 //   * host fault injection (PINV_FAULT, read when the server is created) makes
 //     failures on the host, never on the device: a comma-separated list of
 //     one-shot faults, "alloc:P" (the next admission of plan P fails as if its
@@ -124,6 +129,7 @@ struct Slot {
     size_t scratch_bytes = 0;
     bool busy = false;
     Request req;
+    std::vector<Request> more;  // requests merged into req's apply
     pinv_status submit_status = PINV_OK;
 };
 
@@ -146,6 +152,7 @@ struct pinv_server {
     bool stop = false;
     cudaStream_t build_stream = nullptr;
     uint64_t next_ticket = 1, lru_clock = 0;
+    int64_t merge_frames = 0;  // 0: no merging; else the most frames one merged apply takes
     size_t resident_bytes = 0;
     std::vector<Fault> faults;                            // PINV_FAULT
     std::vector<std::pair<double, Request>> delayed;      // (report time, request) of delayed completions
@@ -304,8 +311,27 @@ bool pinv_server::dispatch_one(std::unique_lock<std::mutex>& lk) {
     if (st == PINV_OK && take_fault(FAULT_DROP, (int64_t)q.ticket))
         st = set_error(PINV_ERR_INTERNAL, "request dropped (injected)");
     if (st == PINV_OK) st = apply_check(r.plan, q.data, q.image, q.frames, q.dtype);
-    if (st == PINV_OK && q.frames > 0) {
-        const size_t need = apply_scratch_layout(r.plan, q.frames, q.dtype, nullptr, nullptr);
+    // requests of the same plan and element type queued behind this one join its apply
+    std::vector<Request> more;
+    int64_t F = q.frames;
+    if (st == PINV_OK && merge_frames > 0 && faults.empty() && q.frames > 0) {
+        for (auto it = queue.begin(); it != queue.end();) {
+            if (it->plan_id == q.plan_id && it->dtype == q.dtype && it->frames > 0 && F + it->frames <= merge_frames &&
+                apply_check(r.plan, it->data, it->image, it->frames, it->dtype) == PINV_OK) {
+                F += it->frames;
+                more.push_back(*it);
+                it = queue.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
+    if (st == PINV_OK && F > 0) {
+        const size_t es = q.dtype == PINV_C128 ? 16 : 8;
+        const int64_t rows = r.plan->M, n = r.plan->N;
+        const size_t base = (apply_scratch_layout(r.plan, F, q.dtype, nullptr, nullptr) + 255) & ~(size_t)255;
+        const size_t dbytes = more.empty() ? 0 : (((size_t)F * rows * es + 255) & ~(size_t)255);
+        const size_t need = base + dbytes + (more.empty() ? 0 : (size_t)F * n * es);
         if (need > slot->scratch_bytes) {
             if (slot->scratch) cudaFree(slot->scratch);
             slot->scratch = nullptr;
@@ -315,26 +341,55 @@ bool pinv_server::dispatch_one(std::unique_lock<std::mutex>& lk) {
         }
         if (st == PINV_OK) {
             ApplyScratch sc;
-            apply_scratch_layout(r.plan, q.frames, q.dtype, slot->scratch, &sc);
+            apply_scratch_layout(r.plan, F, q.dtype, slot->scratch, &sc);
+            uint8_t* dbuf = (uint8_t*)slot->scratch + base;  // merged: frames gathered here
+            uint8_t* ibuf = dbuf + dbytes;                   // and their images
+            const void* data = q.data;
+            void* image = q.image;
             if (cudaStreamWaitEvent(slot->stream, r.ready, 0) != cudaSuccess ||
                 cudaEventRecord(slot->t0, slot->stream) != cudaSuccess)
                 st = set_error(PINV_ERR_CUDA, "cudaStreamWaitEvent");
-            else
-                st = apply_impl(r.plan, q.data, q.image, q.frames, q.dtype, slot->stream, sc);
+            if (st == PINV_OK && !more.empty()) {
+                size_t off = 0;
+                auto gather = [&](const Request& m) {
+                    const size_t b = (size_t)m.frames * rows * es;
+                    if (cudaMemcpyAsync(dbuf + off, m.data, b, cudaMemcpyDeviceToDevice, slot->stream) != cudaSuccess)
+                        st = set_error(PINV_ERR_CUDA, "merge gather");
+                    off += b;
+                };
+                gather(q);
+                for (auto& m : more) gather(m);
+                data = dbuf;
+                image = ibuf;
+            }
+            if (st == PINV_OK) st = apply_impl(r.plan, data, image, F, q.dtype, slot->stream, sc);
+            if (st == PINV_OK && !more.empty()) {
+                size_t off = 0;
+                auto scatter = [&](const Request& m) {
+                    const size_t b = (size_t)m.frames * n * es;
+                    if (cudaMemcpyAsync(m.image, ibuf + off, b, cudaMemcpyDeviceToDevice, slot->stream) != cudaSuccess)
+                        st = set_error(PINV_ERR_CUDA, "merge scatter");
+                    off += b;
+                };
+                scatter(q);
+                for (auto& m : more) scatter(m);
+            }
         }
     }
-    if (st == PINV_OK && q.frames > 0 && cudaEventRecord(slot->t1, slot->stream) != cudaSuccess)
+    if (st == PINV_OK && F > 0 && cudaEventRecord(slot->t1, slot->stream) != cudaSuccess)
         st = set_error(PINV_ERR_CUDA, "cudaEventRecord");
     if (st == PINV_OK && cudaEventRecord(slot->done, slot->stream) != cudaSuccess)
         st = set_error(PINV_ERR_CUDA, "cudaEventRecord");
     if (st != PINV_OK) {
         finish(q, st, lk);
+        for (auto& m : more) finish(m, st, lk);
         return true;
     }
     r.inflight++;
     r.last_use = ++lru_clock;
     slot->busy = true;
     slot->req = q;
+    slot->more = std::move(more);
     return true;
 }
 
@@ -373,6 +428,12 @@ bool pinv_server::reap(std::unique_lock<std::mutex>& lk) {
             delayed.push_back({now_s() + ms * 1e-3, q});  // reported later; the slot is free now
         else
             finish(q, st, lk);
+        for (Request m : s.more) {  // merged requests: same apply, same status and device times
+            m.dev_start_ms = q.dev_start_ms;
+            m.dev_end_ms = q.dev_end_ms;
+            finish(m, st, lk);
+        }
+        s.more.clear();
         any = true;
     }
     return any;
@@ -532,6 +593,13 @@ pinv_status pinv_serve_wait(pinv_server* sv, uint64_t ticket, double timeout_s, 
                                          [&] { return sv->finished.count(ticket) > 0; });
     if (!ok) return set_error(PINV_ERR_TIMEOUT, "request not finished within the timeout");
     if (result) *result = sv->finished[ticket];
+    return PINV_OK;
+}
+
+pinv_status pinv_server_set_merge(pinv_server* sv, int64_t max_frames) {
+    if (!sv || max_frames < 0) return set_error(PINV_ERR_INVALID_ARG, "need a server and max_frames >= 0");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->merge_frames = max_frames;
     return PINV_OK;
 }
 

@@ -78,6 +78,11 @@ class Server:
             self._live.pop(ticket, None)
         return bool(done.value), res.value
 
+    def set_merge(self, max_frames: int):
+        """Merge queued requests of the dispatched request's plan (same element type)
+        into its apply, up to max_frames frames in all (0: off)."""
+        L.check(L.load().pinv_server_set_merge(self._h, int(max_frames)))
+
     def times(self, ticket: int) -> dict:
         """Times of a finished request in ms after the server's creation: enqueue and
         done (host clock), dev_start and dev_end of its device work (device clock; -1

@@ -288,3 +288,45 @@ def test_two_slots_run_on_the_device_at_the_same_time():
         assert 0 <= q["enqueue"] <= q["done"]
         assert 0 <= q["dev_start"] < q["dev_end"]
     assert max(a["dev_start"], b["dev_start"]) < min(a["dev_end"], b["dev_end"]), tt
+
+
+def test_merged_requests_share_one_apply():
+    """With merging on, requests of one plan that queue behind a request in
+    flight are reconstructed by one apply: on a one-slot server busy with a long
+    request of plan A, four requests of plan B (2, 5, 1 and 3 frames) wait and then
+    run together (the same device interval), and each image matches a standalone
+    apply of its frames (FP64 plan: to 1e-13; the sums whose split follows the
+    frame count may reassociate). A fifth B request that would pass the frame cap
+    runs in its own apply."""
+    from paper_2410_06129_gb300.serve import Server
+    kw = dict(precision=L.FP64, recon_mode=L.RECON_NONE)
+    pa = synth.make_plan(32, 4, "spiral", 64, 2150, 1e-3, samples=2048, interleaves=2)
+    pb = synth.make_plan(16, 2, "radial", 20, 2151, 1e-3, spokes=16, per_spoke=24)
+    da = torch.from_numpy(pa.data).cuda()
+    db = torch.from_numpy(pb.data).cuda()
+    sizes = [2, 5, 1, 3, 6]
+    parts, o = [], 0
+    for F in sizes:
+        parts.append(db[o:o + F].clone())
+        o += F
+    expect = [_standalone(pb, kw, d) for d in parts]
+    with Server(budget_bytes=8 << 30, max_slots=1) as sv:
+        ia, ib = sv.register_inputs(pa, **kw), sv.register_inputs(pb, **kw)
+        for i, d in ((ia, da[:1]), (ib, db[:1])):  # both plans resident first
+            t, _ = sv.enqueue(i, d)
+            assert sv.wait(t) == L.OK
+        sv.set_merge(11)
+        ta, _ = sv.enqueue(ia, da)
+        tb = [sv.enqueue(ib, d) for d in parts]
+        assert sv.wait(ta) == L.OK
+        for t, _ in tb:
+            assert sv.wait(t) == L.OK
+        tt = [sv.times(t) for t, _ in tb]
+        st = sv.stats()
+    for (t, out), x in zip(tb, expect):
+        assert rel(out.cpu().numpy(), x.cpu().numpy()) < 1e-13
+    starts = [q["dev_start"] for q in tt]
+    assert len(set(starts[:4])) == 1, tt  # 2 + 5 + 1 + 3 = 11 frames: one apply
+    assert starts[4] != starts[0]          # 11 + 6 > 11: its own apply
+    assert st["completed"] == 2 + 1 + len(sizes)
+    assert st["frames"] == 1 + 1 + 64 + sum(sizes)
