@@ -575,6 +575,8 @@ __global__ void __launch_bounds__(256) k_tab_wrows(const double2* __restrict__ W
                                                    int64_t ncols, uint8_t* tab) {
     const int64_t kc = blockIdx.x, ct = blockIdx.y, kcn = gridDim.x;
     const int r = threadIdx.x & (BM - 1), g = threadIdx.x >> 7;
+    griddep_wait();
+    griddep_launch();
     const int64_t j = ct * BN + r, k0 = kc * KC + 8 * g;
     float2 v[8];
 #pragma unroll
@@ -1276,10 +1278,12 @@ cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, 
             const int64_t nbk = std::min<int64_t>(NBK, N - k0);
             const int64_t ncol = k0 + nbk;
             tc::TrtriDiagTC dp{Dinv32 + (k0 / NBK) * NBK * NBK, W, N, N, k0, nbk};
-            if ((e = run(dp, dim3(cdiv(ncol, tc::BN), 1), slices, st, 5, s, false, cap)) != cudaSuccess) return e;
+            if ((e = run(dp, dim3(cdiv(ncol, tc::BN), 1), slices, st, 5, s, false, cap, true)) != cudaSuccess)
+                return e;
             if (ncol >= pend) continue;
             tc::TrtriUpdTC up{L32, N, W, N, N, k0, nbk, pend};
-            if ((e = run(up, dim3(cdiv(ncol, tc::BN), cdiv(pend - ncol, tc::BM)), slices, st, 6, s, false, cap)) !=
+            if ((e = run(up, dim3(cdiv(ncol, tc::BN), cdiv(pend - ncol, tc::BM)), slices, st, 6, s, false, cap,
+                         true)) !=
                 cudaSuccess)
                 return e;
         }
@@ -1290,14 +1294,12 @@ cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, 
                 uint8_t* tabw = tabl + panel_table_bytes(N, slices);
                 if ((e = panel_table(L32, N, p0, pend - p0, pend, slices, tabl, s)) != cudaSuccess) return e;
                 const dim3 wg((unsigned)kcn, (unsigned)ntc);
-                if (slices == 3)
-                    tc::k_tab_wrows<3><<<wg, 256, 0, s>>>(W, N, p0, pend - p0, pend, tabw);
-                else
-                    tc::k_tab_wrows<2><<<wg, 256, 0, s>>>(W, N, p0, pend - p0, pend, tabw);
-                note_launch();
-                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                const double2* Wc = W;
+                e = slices == 3 ? launch_pdl(tc::k_tab_wrows<3>, wg, dim3(256), 0, s, Wc, N, p0, pend - p0, pend, tabw)
+                                : launch_pdl(tc::k_tab_wrows<2>, wg, dim3(256), 0, s, Wc, N, p0, pend - p0, pend, tabw);
+                if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return e;
                 tc::TrtriBulk up{tabl, tabw, W, N, N, pend, ntr, ntc, kcn, slices};
-                if ((e = run(up, dim3((unsigned)(ntr * ntc), 1), slices, st, 6, s, false, cap)) != cudaSuccess)
+                if ((e = run(up, dim3((unsigned)(ntr * ntc), 1), slices, st, 6, s, false, cap, true)) != cudaSuccess)
                     return e;
             } else {
                 tc::TrtriUpdTC up{L32, N, W, N, N, p0, pend - p0, N};
