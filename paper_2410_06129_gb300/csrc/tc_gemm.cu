@@ -1255,6 +1255,116 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
     return cudaGetLastError();
 }
 
+// Inside a panel the inverse's steps have K = 64, too short for the tensor-core
+// engine's set-up (a launch of TrtriDiagTC / TrtriUpdTC took 27 / 44 us against a
+// few microseconds of products): these FP32 SIMT kernels stage the 64-wide operands
+// in shared memory, as the Cholesky's panel kernels do, and accumulate in FP32.
+__device__ inline void cmac(float2& acc, float2 a, float2 b) {  // acc += a * b
+    acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+    acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+
+// W[k0 + i][j] = sum_k Dinv[i][k] W[k0 + k][j] (W rounded to FP32) for i < nbk, j < ncol:
+// one CTA per 64 columns, each thread 4 x 4 outputs (rows ty + 16 a, columns tx + 16 b)
+__global__ void __launch_bounds__(256) k_trtri_diag(const float2* __restrict__ Dinv32, double2* W, int64_t ld,
+                                                  int64_t k0, int nbk, int64_t ncol) {
+    __shared__ float2 Ds[64][65];  // Ds[i][k] = Dinv[i][k]
+    __shared__ float2 Bs[64][65];  // Bs[k][c] = W[k0 + k][j0 + c]
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t j0 = (int64_t)blockIdx.x * 64;
+    griddep_wait();
+    griddep_launch();
+#pragma unroll 4
+    for (int t = 0; t < 16; ++t) {
+        const int e = tid + 256 * t, r = e / 64, c = e % 64;
+        Ds[r][c] = (r < nbk && c < nbk) ? Dinv32[r * 64 + c] : make_float2(0.f, 0.f);
+        const int64_t j = j0 + c;
+        if (r < nbk && j < ncol) {
+            const double2 w = W[(k0 + r) * ld + j];
+            Bs[r][c] = make_float2((float)w.x, (float)w.y);
+        } else {
+            Bs[r][c] = make_float2(0.f, 0.f);
+        }
+    }
+    __syncthreads();
+    float2 acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int k = 0; k < 64; ++k) {
+        float2 dv[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) dv[a] = Ds[ty + 16 * a][k];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Bs[k][tx + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) cmac(acc[a][b], dv[a], bv[b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = ty + 16 * a;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int64_t j = j0 + tx + 16 * b;
+            if (r < nbk && j < ncol) W[(k0 + r) * ld + j] = make_double2(acc[a][b].x, acc[a][b].y);
+        }
+    }
+}
+
+// W[i][j] -= sum_k L[i][k0 + k] W[k0 + k][j] for rows r0 <= i < imax, j < ncol (K = nbk):
+// one CTA per 16 rows x 64 columns, each thread 1 row x 4 columns
+__global__ void __launch_bounds__(256) k_trtri_upd(const float2* __restrict__ L32, int64_t ldl, double2* W,
+                                                 int64_t ld, int64_t k0, int nbk, int64_t r0, int64_t imax,
+                                                 int64_t ncol) {
+    __shared__ float2 As[16][65];  // As[r][k] = L[i0 + r][k0 + k]
+    __shared__ float2 Bs[64][65];  // Bs[k][c] = W[k0 + k][j0 + c]
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t j0 = (int64_t)blockIdx.x * 64, i0 = r0 + (int64_t)blockIdx.y * 16;
+    griddep_wait();
+    griddep_launch();
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int e = tid + 256 * t, r = e / 64, k = e % 64;
+        const int64_t i = i0 + r;
+        As[r][k] = (i < imax && k < nbk) ? L32[i * ldl + k0 + k] : make_float2(0.f, 0.f);
+    }
+#pragma unroll 4
+    for (int t = 0; t < 16; ++t) {
+        const int e = tid + 256 * t, k = e / 64, c = e % 64;
+        const int64_t j = j0 + c;
+        if (k < nbk && j < ncol) {
+            const double2 w = W[(k0 + k) * ld + j];
+            Bs[k][c] = make_float2((float)w.x, (float)w.y);
+        } else {
+            Bs[k][c] = make_float2(0.f, 0.f);
+        }
+    }
+    __syncthreads();
+    float2 acc[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[b] = make_float2(0.f, 0.f);
+#pragma unroll 8
+    for (int k = 0; k < 64; ++k) {
+        const float2 av = As[ty][k];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) cmac(acc[b], av, Bs[k][tx + 16 * b]);
+    }
+    const int64_t i = i0 + ty;
+    if (i >= imax) return;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int64_t j = j0 + tx + 16 * b;
+        if (j < ncol) {
+            const double2 w = W[i * ld + j];
+            W[i * ld + j] = make_double2(w.x - (double)acc[b].x, w.y - (double)acc[b].y);
+        }
+    }
+}
+
 // W = L^-1 by blocked forward substitution on I, with the same two levels:
 // inside a 256-row panel each 64-row step updates the panel's rows only; the
 // rows below get one update per panel with K = 256.
@@ -1277,14 +1387,12 @@ cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, 
         for (int64_t k0 = p0; k0 < pend; k0 += NBK) {
             const int64_t nbk = std::min<int64_t>(NBK, N - k0);
             const int64_t ncol = k0 + nbk;
-            tc::TrtriDiagTC dp{Dinv32 + (k0 / NBK) * NBK * NBK, W, N, N, k0, nbk};
-            if ((e = run(dp, dim3(cdiv(ncol, tc::BN), 1), slices, st, 5, s, false, cap, true)) != cudaSuccess)
+            if ((e = launch_pdl(k_trtri_diag, dim3(cdiv(ncol, 64)), dim3(256), 0, s, Dinv32 + (k0 / NBK) * NBK * NBK,
+                                W, N, k0, (int)nbk, ncol)) != cudaSuccess)
                 return e;
             if (ncol >= pend) continue;
-            tc::TrtriUpdTC up{L32, N, W, N, N, k0, nbk, pend};
-            if ((e = run(up, dim3(cdiv(ncol, tc::BN), cdiv(pend - ncol, tc::BM)), slices, st, 6, s, false, cap,
-                         true)) !=
-                cudaSuccess)
+            if ((e = launch_pdl(k_trtri_upd, dim3(cdiv(ncol, 64), cdiv(pend - ncol, 16)), dim3(256), 0, s, L32, N, W,
+                                N, k0, (int)nbk, ncol, pend, ncol)) != cudaSuccess)
                 return e;
         }
         if (pend < N) {
