@@ -1159,7 +1159,7 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
     int cap = 0;
     if (ahead) {
         const char* cenv = std::getenv("PINV_TRAIL_SMS");
-        cap = cenv ? std::atoi(cenv) : (N <= 16384 ? std::max(1, tc::sm_count() / 4) : 0);
+        cap = cenv ? std::atoi(cenv) : (N <= 16384 ? std::max(1, 2 * tc::sm_count() / 5) : 0);
     }
     bool pending = false;  // a side update of the previous panel may still run
     // block lookahead inside a panel: after diagonal block k only the next block's
@@ -1374,13 +1374,15 @@ cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, 
     if (e != cudaSuccess) return e;
     // the inverse runs beside the Cholesky chain (and its trailing updates). Up to
     // N = 16384, where the chain is a latency-bound sequence of small launches, the
-    // inverse's persistent launches take at most three quarters of the SMs so that
-    // the chain's launches find free SMs; the trailing updates beside the chain take
-    // a quarter. Measured at 64x64 (inverse / trailing SMs -> build): 76 / 50 ->
-    // 12.0 ms, 152 / 50 -> 11.6 ms, 114 / 38 -> 11.55 ms. Above N = 16384 all three
-    // are throughput-bound and each takes every SM. PINV_INV_SMS: another count (0 all).
+    // inverse's persistent launches take at most half the SMs so that the chain's
+    // launches find free SMs; the trailing updates beside the chain take two fifths.
+    // Measured at 64x64 (inverse / trailing SMs -> build): 114 / 38 -> 8.78 ms,
+    // 152 / 50 -> 8.77 ms, 76 / 50 -> 8.63 ms, 76 / 64 -> 8.57 ms, 64 / 64 -> 8.56 ms,
+    // any / 24 -> 9.3 ms and more (the trailing updates fall behind). Above
+    // N = 16384 all three are throughput-bound
+    // and each takes every SM. PINV_INV_SMS: another count (0 all).
     const char* cenv = std::getenv("PINV_INV_SMS");
-    const int cap = cenv ? std::atoi(cenv) : (N <= 16384 ? std::max(1, 3 * tc::sm_count() / 4) : 0);
+    const int cap = cenv ? std::atoi(cenv) : (N <= 16384 ? std::max(1, tc::sm_count() / 2) : 0);
     for (int64_t p0 = 0; p0 < N; p0 += NBP) {
         const int64_t pend = std::min<int64_t>(N, p0 + NBP);
         if (ev_panel && (e = cudaStreamWaitEvent(s, ev_panel[p0 / NBP], 0)) != cudaSuccess) return e;
