@@ -83,19 +83,26 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
             const char* env = std::getenv("PINV_GRAM_BULK");
             const bool bulk = !(env && std::strcmp(env, "0") == 0);
             if (bulk && work_alloc(&work, gram_bulk_bytes(p->enc, p->slices()), s) == cudaSuccess) {
-                CK(launch_gram_bulk(p->enc, p->lambda_abs, p->slices(), p->G, ld, work, p->st, s));
+                CK(launch_gram_bulk(p->enc, p->lambda_abs, p->slices(), (float4*)p->G, ld, work, p->st, s));
                 CK(cudaFreeAsync(work, s));
             } else {
                 cudaGetLastError();
-                CK(launch_gram_tc(p->enc, p->lambda_abs, p->slices(), p->G, ld, p->st, s));
+                CK(launch_gram_tc(p->enc, p->lambda_abs, p->slices(), (float4*)p->G, ld, p->st, s));
             }
         }
     }
     CK(cudaEventRecord(p->ev[7], s));
-    if (p->Gkeep) CK(cudaMemcpyAsync(p->Gkeep, p->G, sizeof(double2) * N * N, cudaMemcpyDeviceToDevice, s));
+    // mixed plans hold G in double-float storage (float4 per entry) until it is factored
+    const bool gdf = p->precision != PINV_FP64;
+    if (p->Gkeep) {
+        if (gdf)
+            CK(launch_df_to_f64((const float4*)p->G, N * N, p->Gkeep, s));
+        else
+            CK(cudaMemcpyAsync(p->Gkeep, p->G, sizeof(double2) * N * N, cudaMemcpyDeviceToDevice, s));
+    }
     // ||G||_1 for the condition estimate: from the exact Gram where the plan forms
     // one (below, beside the Cholesky), else from G before the Cholesky overwrites it
-    if (!p->Gx) CK(launch_gram_norm1(p->G, nullptr, N, ld, p->st, s));
+    if (!p->Gx) CK(launch_gram_norm1(gdf ? nullptr : p->G, gdf ? (const float4*)p->G : nullptr, nullptr, N, ld, p->st, s));
     if (p->Gx) {
         // exact Gram for the refinement residual (Toeplitz table, then coil products,
         // then its digit tiles). Only applies and the condition check read it, so mixed
@@ -112,7 +119,7 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
         CK(launch_toeplitz64(p->enc, work, p->Ttab, sx));
         CK(cudaFreeAsync(work, sx));
         CK(launch_gram_exact(p->enc, p->Ttab, p->lambda_abs, p->Gx, sx));
-        CK(launch_gram_norm1(nullptr, p->Gx, N, N, p->st, sx));
+        CK(launch_gram_norm1(nullptr, nullptr, p->Gx, N, N, p->st, sx));
         if (p->Gd) CK(launch_gram_digits(p->Gx, N, p->eG, p->Gd, sx));
         if (p->Ad) CK(launch_adj_digits(p->enc, p->Ad, sx));
         if (sx != s) {
@@ -211,12 +218,13 @@ pinv_status build_factor(pinv_plan* p, cudaStream_t s, bool events) {
         const TrailLookahead la{p->s_trail, p->st_trail, p->ev_tab, p->ev_trail, p->s_pnl, p->ev_next, p->ev_side};
         CK(cudaStreamWaitEvent(p->s_trail, p->ev_fork, 0));
         CK(cudaStreamWaitEvent(p->s_pnl, p->ev_fork, 0));
-        CK(launch_potrf_tc(p->G, N, ld, nullptr, D32, L32, p->slices(), p->st, sc, tab, p->ev_panel.data(), &la));
+        CK(launch_potrf_tc((float4*)p->G, N, ld, nullptr, D32, L32, p->slices(), p->st, sc, tab, p->ev_panel.data(),
+                           &la));
         CK(launch_merge_timeout(p->st, p->st_trail, sc));
-        CK(launch_pivot_stats(p->G, N, ld, p->st, sc));
+        CK(launch_pivot_stats_df((const float4*)p->G, N, ld, p->st, sc));
         if (events) CK(cudaEventRecord(p->ev[3], sc));
         CK(cudaStreamWaitEvent(p->s_inv, p->ev_fork, 0));
-        CK(launch_trtri_tc(L32, N, D32, p->W, p->W32, p->slices(), p->st_inv, p->s_inv, tab_inv,
+        CK(launch_trtri_tc(L32, N, D32, (float4*)p->W, p->W32, p->slices(), p->st_inv, p->s_inv, tab_inv,
                            p->ev_panel.data()));
         if (sc != s) {
             CK(cudaEventRecord(p->ev_chol, sc));
@@ -727,7 +735,10 @@ pinv_status pinv_plan_export(const pinv_plan* p, int what, void* dst, size_t byt
     }
     if (bytes < need) return fail(PINV_ERR_INVALID_ARG, "destination too small");
     if (what == PINV_EXPORT_CHOL) {
-        CK(launch_copy_lower(p->G, p->N, p->N, (double2*)dst, s));
+        if (p->precision != PINV_FP64)  // L in double-float storage
+            CK(launch_copy_lower_df((const float4*)p->G, p->N, p->N, (double2*)dst, s));
+        else
+            CK(launch_copy_lower(p->G, p->N, p->N, (double2*)dst, s));
     } else if (what == PINV_EXPORT_GRAM_EXACT) {
         CK(launch_from_df(p->Gx, p->N * p->N, (double2*)dst, s));
     } else if (what == PINV_EXPORT_GINV && !p->Ginv) {

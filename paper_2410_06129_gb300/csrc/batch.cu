@@ -107,7 +107,7 @@ pinv_status build_sequence(pinv_batch* b, cudaStream_t s) {
         CKB(tc_multi_launch(b->gram, b->slices, b->st, s));  // every plan's Gram
         for (size_t i = 0; i < n; ++i) {
             pinv_plan* p = b->plans[i];
-            CKB(gram_bulk_finish(p->enc, p->lambda_abs, b->slices, p->G, p->N, b->pwork[i], s));
+            CKB(gram_bulk_finish(p->enc, p->lambda_abs, b->slices, (float4*)p->G, p->N, b->pwork[i], s));
             STB(build_gram(p, s, false));
         }
         STB(fork_all(b, s));
@@ -239,7 +239,7 @@ pinv_status pinv_batch_create(pinv_plan* const* plans, int n, int flags, pinv_ba
         for (int i = 0; i < n; ++i) {
             pinv_plan* p = b->plans[i];
             b->pwork.push_back((unsigned char*)b->work + off[i]);
-            const TcPlanArgs a{&p->enc, p->lambda_abs, p->G, p->W32, (float2*)p->R, b->pwork[i]};
+            const TcPlanArgs a{&p->enc, p->lambda_abs, (float4*)p->G, p->W32, (float2*)p->R, b->pwork[i]};
             all.push_back(a);
             if (p->recon) rec.push_back(a);
         }

@@ -103,14 +103,23 @@ __global__ void k_abs_rows(const T* G, int64_t N, int64_t ld, float2* rs) {
 }
 
 // part[s][j] = sum over rows i of chunk s with i > j of |G[i][j]| (the strictly
-// lower part of column j); consecutive threads read consecutive columns
-__global__ void k_abs_cols_lower(const double2* G, int64_t N, int64_t ld, int64_t rows_per_chunk, float2* part) {
+// lower part of column j); consecutive threads read consecutive columns. G in
+// FP64 (double2) or double-float (float4, |hi| suffices) storage.
+template <class T>
+__global__ void k_abs_cols_lower(const T* G, int64_t N, int64_t ld, int64_t rows_per_chunk, float2* part) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.y * rows_per_chunk;
     const int64_t i1 = N < i0 + rows_per_chunk ? N : i0 + rows_per_chunk;
     if (j >= N) return;
     float h = 0.f, l = 0.f;
-    for (int64_t i = i0 > j + 1 ? i0 : j + 1; i < i1; ++i) acc_df(h, l, abs_f(G[i * ld + j]));
+    for (int64_t i = i0 > j + 1 ? i0 : j + 1; i < i1; ++i) {
+        if constexpr (std::is_same<T, float4>::value) {
+            const float4 g = G[i * ld + j];
+            acc_df(h, l, sqrtf(fmaf(g.x, g.x, g.z * g.z)));
+        } else {
+            acc_df(h, l, abs_f(G[i * ld + j]));
+        }
+    }
     part[(int64_t)blockIdx.y * N + j] = make_float2(h, l);
 }
 
@@ -411,10 +420,10 @@ int chunks_for(int64_t N) { return (int)((N + rows_per_chunk(N) - 1) / rows_per_
 
 }  // namespace
 
-// ||G||_1 into st->norm1_g: from the stored lower triangle of G (FP64) or from
-// the full double-float exact Gram Gx (when gx != nullptr)
-cudaError_t launch_gram_norm1(const double2* G, const float4* Gx, int64_t N, int64_t ld, DevStatus* st,
-                              cudaStream_t s) {
+// ||G||_1 into st->norm1_g: from the stored lower triangle of G (FP64 G, or
+// double-float Gdf) or from the full double-float exact Gram Gx; one of the three
+cudaError_t launch_gram_norm1(const double2* G, const float4* Gdf, const float4* Gx, int64_t N, int64_t ld,
+                              DevStatus* st, cudaStream_t s) {
     const int chunks = Gx ? 0 : chunks_for(N);
     const int64_t rpc = rows_per_chunk(N);
     float2 *rs = nullptr, *part = nullptr;
@@ -422,11 +431,16 @@ cudaError_t launch_gram_norm1(const double2* G, const float4* Gx, int64_t N, int
     if (e != cudaSuccess) return e;
     if (chunks && (e = work_alloc((void**)&part, sizeof(float2) * N * chunks, s)) != cudaSuccess) return e;
     const unsigned rows_blocks = (unsigned)((N + 7) / 8);
+    const dim3 cg((unsigned)((N + 255) / 256), (unsigned)chunks);
     if (Gx) {
         k_abs_rows<float4, true><<<rows_blocks, 256, 0, s>>>(Gx, N, N, rs);
+    } else if (Gdf) {
+        k_abs_rows<float4, false><<<rows_blocks, 256, 0, s>>>(Gdf, N, ld, rs);
+        k_abs_cols_lower<float4><<<cg, 256, 0, s>>>(Gdf, N, ld, rpc, part);
+        note_launch();
     } else {
         k_abs_rows<double2, false><<<rows_blocks, 256, 0, s>>>(G, N, ld, rs);
-        k_abs_cols_lower<<<dim3((unsigned)((N + 255) / 256), (unsigned)chunks), 256, 0, s>>>(G, N, ld, rpc, part);
+        k_abs_cols_lower<double2><<<cg, 256, 0, s>>>(G, N, ld, rpc, part);
         note_launch();
     }
     k_norm1_finish<<<1, CB, 0, s>>>(rs, part, chunks, N, &st->norm1_g);

@@ -152,6 +152,28 @@ __device__ inline void cacc(float4& acc, float4 a, float4 b) {
     acc_prod(acc.z, acc.w, a.z, a.w, b.x, b.y);
 }
 
+// ------------------------------------------------------------------ double-float matrix storage
+// Mixed plans hold G (then L) and W = L^-1 in double-float form while they are
+// factored and inverted: a complex entry is the float4 (re.hi, re.lo, im.hi, im.lo)
+// in the 16 bytes of a complex double, so every update runs on the FP32 pipe (GB300
+// issues about one FP64 add per clock per SM). Zero has the same bits in both forms.
+__device__ inline float4 df_of_f32(float2 v) { return make_float4(v.x, 0.f, v.y, 0.f); }
+// a - v for an FP32 v: TwoSum of the leading parts, the error added to the trailing
+// part, renormalised. Where the leading parts cancel their difference is exact and
+// at least the trailing part, so the final fast TwoSum is exact too.
+__device__ inline float4 df_sub_f32(float4 a, float2 v) {
+    float s, e, rh, rl, ih, il;
+    two_sum(a.x, -v.x, s, e);
+    fast_two_sum(s, a.y + e, rh, rl);
+    two_sum(a.z, -v.y, s, e);
+    fast_two_sum(s, a.w + e, ih, il);
+    return make_float4(rh, rl, ih, il);
+}
+// the FP32 rounding of a double-float complex value
+__device__ inline float2 df_to_f32(float4 a) { return make_float2(a.x + a.y, a.z + a.w); }
+// FP64 from double-float on the integer pipe (join_f64)
+__device__ inline double2 df_to_f64(float4 a) { return make_double2(join_f64(a.x, a.y), join_f64(a.z, a.w)); }
+
 // encoding element A[m][n] and E[(c,m)][n] from the double-float tables
 __device__ inline float4 gen_a_df(const EncodeDev& e, int64_t m, int64_t n) {
     const int* g = e.vox_ijk + 3 * n;

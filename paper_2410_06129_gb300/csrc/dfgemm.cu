@@ -301,7 +301,8 @@ cudaError_t launch_from_df(const float4* a, int64_t n, double2* b, cudaStream_t 
 // Dinv = L_kk^-1, in double-float (about 44 significant bits) on the FP32
 // units. GB300 issues about 2 DFMA per clock per SM, so the same block in FP64
 // takes ~5x longer, and these blocks are the sequential chain of the blocked
-// Cholesky. Storage stays FP64. Only the 64 pivots use FP64 (one rsqrt each).
+// Cholesky. G is in double-float storage throughout the mixed factorisation
+// (df_of_f32 / df_sub_f32), so the block enters and leaves as it is.
 namespace {
 constexpr int NBD = 64;
 constexpr int NBDP = NBD + 1;  // padded row stride of the shared-memory blocks
@@ -349,11 +350,10 @@ __device__ inline float2 df_rsqrt(float dh, float dl) {
 //      paired with row 63 - p, so each pair holds j + 66 entries and the
 //      threads run over pairs without idle lanes.
 // Two barriers per column. Rows are NBDP = 65 entries apart, so row and column
-// reads are free of bank conflicts. Values enter and leave through integer and
-// FP32 conversions: on GB300 the FP64 pipe of the one SM would take longer.
-// Dinv may be null (the FP32 inverse alone); L32 (or null) receives the block of L
-// rounded to FP32, as (float) of the FP64 value written to G.
-__global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0,
+// reads are free of bank conflicts. The block is read from and L written back to
+// G in double-float storage. Dinv may be null (the FP32 inverse alone); L32 (or
+// null) receives the block of L rounded to FP32.
+__global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(float4* G, int64_t ld, int64_t N, int64_t k0,
                                                              double2* Dinv, float2* Dinv32, float2* L32,
                                                              int64_t ldl, DevStatus* st) {
     extern __shared__ float4 smd[];
@@ -367,11 +367,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
     for (int e = tid; e < NBD * NBD; e += DIAG_THREADS) {
         const int i = e / NBD, j = e % NBD;
         float4 v = make_float4(i == j ? 1.f : 0.f, 0.f, 0.f, 0.f);
-        if (i < nb && j < nb && j <= i) {
-            const double2 g = G[(k0 + i) * ld + k0 + j];
-            const float2 re = split_f64(g.x), im = split_f64(g.y);
-            v = make_float4(re.x, re.y, im.x, im.y);
-        }
+        if (i < nb && j < nb && j <= i) v = G[(k0 + i) * ld + k0 + j];
         A[i * NBDP + j] = v;
         X[i * NBDP + j] = make_float4(i == j ? 1.f : 0.f, 0.f, 0.f, 0.f);
     }
@@ -432,9 +428,8 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag_df(double2* G, int6
         if (Dinv32) Dinv32[e] = make_float2(x.x + x.y, x.z + x.w);
         if (i < nb && j < nb && j <= i) {
             const float4 a = A[i * NBDP + j];
-            const double2 g = make_double2(join_f64(a.x, a.y), join_f64(a.z, a.w));
-            G[(k0 + i) * ld + k0 + j] = g;
-            if (L32) L32[(k0 + i) * ldl + k0 + j] = make_float2(f64_to_f32_rn(g.x), f64_to_f32_rn(g.y));
+            G[(k0 + i) * ld + k0 + j] = a;
+            if (L32) L32[(k0 + i) * ldl + k0 + j] = df_to_f32(a);
         } else if (L32 && i < nb && j < nb) {
             L32[(k0 + i) * ldl + k0 + j] = make_float2(0.f, 0.f);
         }
@@ -516,7 +511,7 @@ __device__ inline void tri_index(int e, int& r, int& q) {
 __device__ inline float4 cdf_neg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(DIAG_THREADS)
-    k_potrf_diag_df2(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv, float2* Dinv32, float2* L32,
+    k_potrf_diag_df2(float4* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv, float2* Dinv32, float2* L32,
                      int64_t ldl, DevStatus* st) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -538,18 +533,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(DIAG_THREADS)
     }
     {  // the block's lower triangle (rank 0) or I (rank 1); all loads issued before the stores
         constexpr int PER = NBD * NBD / DIAG_THREADS;
-        double2 g[PER];
+        float4 g[PER];
 #pragma unroll
         for (int t = 0; t < PER; ++t) {
             const int e = tid + t * DIAG_THREADS, i = e / NBD, j = e % NBD;
             g[t] = (rank == 0 && i < nb && j < nb && j <= i) ? G[(k0 + i) * ld + k0 + j]
-                                                              : make_double2(i == j ? 1.0 : 0.0, 0.0);
+                                                              : make_float4(i == j ? 1.f : 0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int t = 0; t < PER; ++t) {
             const int e = tid + t * DIAG_THREADS, i = e / NBD, j = e % NBD;
-            const float2 re = split_f64(g[t].x), im = split_f64(g[t].y);
-            A[i * NBDP + j] = make_float4(re.x, re.y, im.x, im.y);
+            A[i * NBDP + j] = g[t];
         }
     }
     // the entries this thread updates off the critical path; rank 0: (i, c), 2 <= c <= i,
@@ -654,9 +648,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(DIAG_THREADS)
             const int i = e / NBD, j = e % NBD;
             if (i < nb && j < nb && j <= i) {
                 const float4 a = i == j ? make_float4(Ld[j].x, Ld[j].y, 0.f, 0.f) : A[i * NBDP + j];
-                const double2 g = make_double2(join_f64(a.x, a.y), join_f64(a.z, a.w));
-                G[(k0 + i) * ld + k0 + j] = g;
-                if (L32) L32[(k0 + i) * ldl + k0 + j] = make_float2(f64_to_f32_rn(g.x), f64_to_f32_rn(g.y));
+                G[(k0 + i) * ld + k0 + j] = a;
+                if (L32) L32[(k0 + i) * ldl + k0 + j] = df_to_f32(a);
             } else if (L32 && i < nb && j < nb) {
                 L32[(k0 + i) * ldl + k0 + j] = make_float2(0.f, 0.f);
             }
@@ -715,7 +708,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(DIAG_THREADS)
     }
 }
 
-cudaError_t launch_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv, float2* Dinv32,
+cudaError_t launch_potrf_diag_df(float4* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv, float2* Dinv32,
                                  float2* L32, int64_t ldl, DevStatus* st, cudaStream_t s) {
     // PINV_DIAG_CLUSTER=0: the one-CTA sweep (same results)
     const char* env = std::getenv("PINV_DIAG_CLUSTER");

@@ -154,6 +154,11 @@ cudaError_t launch_to_f32(const double2* src, float2* dst, int64_t n, cudaStream
 cudaError_t launch_transpose32(const float2* src, int64_t rows, int64_t cols, float2* dst, int64_t ldd,
                                cudaStream_t s);
 cudaError_t launch_fill_identity(double2* W, int64_t N, int64_t ld, cudaStream_t s);
+// The identity in double-float storage.
+cudaError_t launch_fill_identity_df(float4* W, int64_t N, int64_t ld, cudaStream_t s);
+// A lower-triangular matrix in double-float storage to FP64 in place (the upper
+// triangle set to zero) and its FP32 rounding into W32 (ld N).
+cudaError_t launch_df_finish(float4* W, int64_t N, int64_t ld, float2* W32, cudaStream_t s);
 
 // Gram G = (A^H A) o (S^H S) + lambda I, lower tiles, FP64.
 cudaError_t launch_gram64(const EncodeDev& e, double lambda, double2* G, int64_t ld, cudaStream_t s);
@@ -176,8 +181,9 @@ int tune_pick(const char* family, int64_t rows, int64_t F, int ncand, const Tune
 // per-device pool, which keeps its memory between builds (free with cudaFreeAsync).
 cudaError_t work_alloc(void** ptr, size_t bytes, cudaStream_t s);
 
-// mixed path: the same diagonal block in double-float on the FP32 units
-cudaError_t launch_potrf_diag_df(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv, float2* Dinv32,
+// mixed path: the same diagonal block in double-float on the FP32 units, G in
+// double-float storage (the block of L written back in place)
+cudaError_t launch_potrf_diag_df(float4* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv, float2* Dinv32,
                                  float2* L32, int64_t ldl,
                                  DevStatus* st, cudaStream_t s);
 cudaError_t launch_potrf_diag(double2* G, int64_t ld, int64_t N, int64_t k0, double2* Dinv,
@@ -197,11 +203,16 @@ cudaError_t launch_forward64(const EncodeDev& e, const double2* X, int64_t F, co
 // Y[f][n] = Yadd[f][n] + sum_n' H[n][n'] X[f][n'] (H full [N][N]), FP64.
 cudaError_t launch_hemv64(const double2* H, int64_t N, int64_t ld, const double2* X, int64_t F,
                           const double2* Yadd, double2* Y, cudaStream_t s);
-// Copy the lower triangle of G (incl. diagonal) to L, zeroing the upper triangle.
+// Copy the lower triangle of G (incl. diagonal) to L, zeroing the upper triangle;
+// the _df forms read double-float storage.
 cudaError_t launch_copy_lower(const double2* G, int64_t N, int64_t ld, double2* L, cudaStream_t s);
+cudaError_t launch_copy_lower_df(const float4* G, int64_t N, int64_t ld, double2* L, cudaStream_t s);
+// FP64 copy of n double-float entries (integer-pipe conversion).
+cudaError_t launch_df_to_f64(const float4* a, int64_t n, double2* b, cudaStream_t s);
 // Pivot extrema of diag(L) into st->min_pivot / max_pivot.
 cudaError_t launch_pivot_stats(const double2* L, int64_t N, int64_t ld, DevStatus* st,
                                cudaStream_t s);
+cudaError_t launch_pivot_stats_df(const float4* L, int64_t N, int64_t ld, DevStatus* st, cudaStream_t s);
 // Conversions between c64 and c128 frame buffers.
 cudaError_t launch_c64_to_c128(const float2* a, double2* b, int64_t n, cudaStream_t s);
 cudaError_t launch_c128_to_c64(const double2* a, float2* b, int64_t n, cudaStream_t s);
@@ -213,13 +224,14 @@ cudaError_t launch_zaxpy(double2* X, const double2* Y, int64_t n, cudaStream_t s
 // ---------------------------------------------------------------------------
 // Mixed-precision (tcgen05, split BF16) kernels (tc_gemm.cu)
 // ---------------------------------------------------------------------------
-// Gram in split BF16 on tcgen05 tensor cores; result written as FP64 lower tiles.
-cudaError_t launch_gram_tc(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld,
+// Gram in split BF16 on tcgen05 tensor cores; result written as double-float
+// lower tiles (float4 per entry, the storage of mixed plans' G while it is factored).
+cudaError_t launch_gram_tc(const EncodeDev& e, double lambda, int slices, float4* G, int64_t ld,
                            DevStatus* st, cudaStream_t s);
 // Bulk-fed Gram: the split encoding table (and, for a split sample range, the
 // partial sums) in `work` of gram_bulk_bytes(); same result layout as launch_gram_tc.
 size_t gram_bulk_bytes(const EncodeDev& e, int slices);
-cudaError_t launch_gram_bulk(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld, void* work,
+cudaError_t launch_gram_bulk(const EncodeDev& e, double lambda, int slices, float4* G, int64_t ld, void* work,
                              DevStatus* st, cudaStream_t s);
 // Recon = W^H (W E^H) in split BF16 on tcgen05 (W = L^-1 in FP32, T = W E^H
 // scratch [N][M] c64), c64 out.
@@ -259,11 +271,12 @@ struct TrailLookahead {
     cudaStream_t s2;
     cudaEvent_t ev_next, ev_side;
 };
-cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, float2* Dinv32, float2* L32,
+cudaError_t launch_potrf_tc(float4* G, int64_t N, int64_t ld, double2* Dinv, float2* Dinv32, float2* L32,
                             int slices, DevStatus* st, cudaStream_t s, void* tab = nullptr,
                             const cudaEvent_t* ev_panel = nullptr, const TrailLookahead* la = nullptr);
-// W = L^-1 (FP64 storage, tensor-core updates) and its FP32 copy W32.
-cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, double2* W, float2* W32,
+// W = L^-1 (double-float storage while it is formed, FP64 on return; tensor-core
+// updates) and its FP32 copy W32.
+cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, float4* W, float2* W32,
                             int slices, DevStatus* st, cudaStream_t s, void* tab = nullptr,
                             const cudaEvent_t* ev_panel = nullptr);
 bool tc_available();
@@ -282,7 +295,7 @@ cudaError_t launch_merge_timeout(DevStatus* dst, const DevStatus* src, cudaStrea
 struct TcPlanArgs {
     const EncodeDev* e;
     double lam;
-    double2* G;           // Gram output (lower tiles), ld = N
+    float4* G;            // Gram output (lower tiles, double-float), ld = N
     const float2* W32;    // W = L^-1, FP32 [N][N]
     float2* R;            // Recon [N][M]
     void* work;           // operand tables: gram_bulk_bytes() for the Gram, recon_bulk_bytes() for Recon
@@ -301,17 +314,18 @@ struct TcMulti {
 cudaError_t tc_multi_create(int kind, const TcPlanArgs* args, int n, int slices, int64_t chunk, TcMulti* out);
 cudaError_t tc_multi_launch(const TcMulti& m, int slices, DevStatus* st, cudaStream_t s);
 cudaError_t gram_bulk_table(const EncodeDev& e, int slices, void* work, cudaStream_t s);
-cudaError_t gram_bulk_finish(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld, void* work,
+cudaError_t gram_bulk_finish(const EncodeDev& e, double lambda, int slices, float4* G, int64_t ld, void* work,
                              cudaStream_t s);
 int64_t recon_bulk_chunks(const EncodeDev& e, int slices);
 cudaError_t recon_bulk_wtables(const EncodeDev& e, const float2* W32, int slices, void* work, cudaStream_t s);
 cudaError_t recon_bulk_et(const EncodeDev& e, int slices, void* work, int64_t chunk, cudaStream_t s);
 void tc_multi_free(TcMulti* m);
 
-// ||G||_1 into st->norm1_g, from the lower triangle of the FP64 G (before the
-// Cholesky overwrites it) or, with Gx != nullptr, from the full double-float exact Gram
-cudaError_t launch_gram_norm1(const double2* G, const float4* Gx, int64_t N, int64_t ld, DevStatus* st,
-                              cudaStream_t s);
+// ||G||_1 into st->norm1_g, from the lower triangle of G before the Cholesky
+// overwrites it (FP64 G, or Gdf in double-float storage) or from the full
+// double-float exact Gram Gx; exactly one of the three is non-null
+cudaError_t launch_gram_norm1(const double2* G, const float4* Gdf, const float4* Gx, int64_t N, int64_t ld,
+                              DevStatus* st, cudaStream_t s);
 
 // double-float frame products split their k range over CTAs; `work` holds
 // df_work_elems() partials (float4) when the split count is above one

@@ -82,7 +82,7 @@ struct pinv_plan {
 
     pinv::EncodeDev enc{};
     double* traj = nullptr;
-    double2* G = nullptr;      // Gram, then L in place (lower)
+    double2* G = nullptr;      // Gram, then L in place (lower); mixed plans: double-float storage (float4)
     double2* Gkeep = nullptr;  // copy of G if requested
     double2* Dinv = nullptr;   // inverses of the diagonal blocks
     double2* Ginv = nullptr;   // full G^-1 (FP64 plans)

@@ -9,7 +9,7 @@
 // Arguments are reduced modulo one cycle in FP64 before sincospi.
 #include <climits>
 
-#include "pinv_internal.h"
+#include "df.cuh"
 
 namespace pinv {
 
@@ -116,6 +116,41 @@ cudaError_t launch_fill_identity(double2* W, int64_t N, int64_t ld, cudaStream_t
     return cudaGetLastError();
 }
 
+__global__ void k_identity_df(float4* W, int64_t N, int64_t ld) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N) return;
+    int64_t i = idx / N, j = idx % N;
+    W[i * ld + j] = make_float4(i == j ? 1.f : 0.f, 0.f, 0.f, 0.f);
+}
+cudaError_t launch_fill_identity_df(float4* W, int64_t N, int64_t ld, cudaStream_t s) {
+    k_identity_df<<<nblk(N * N, 256), 256, 0, s>>>(W, N, ld);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// each entry in place: the 16 bytes of a double-float complex become the FP64
+// value (join_f64, integer pipe); the upper triangle is written as zero, unread
+__global__ void k_df_finish(float4* W, int64_t N, int64_t ld, float2* W32) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N) return;
+    int64_t i = idx / N, j = idx % N;
+    float2 w32 = make_float2(0.f, 0.f);
+    double2 w = make_double2(0.0, 0.0);
+    if (j <= i) {
+        const float4 a = W[i * ld + j];
+        w32 = df_to_f32(a);
+        w = df_to_f64(a);
+    }
+    reinterpret_cast<double2*>(W)[i * ld + j] = w;
+    W32[i * N + j] = w32;
+}
+cudaError_t launch_df_finish(float4* W, int64_t N, int64_t ld, float2* W32, cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    k_df_finish<<<nblk(N * N, 256), 256, 0, s>>>(W, N, ld, W32);
+    note_launch();
+    return cudaGetLastError();
+}
+
 __global__ void k_copy_lower(const double2* G, int64_t N, int64_t ld, double2* L) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= N * N) return;
@@ -124,6 +159,29 @@ __global__ void k_copy_lower(const double2* G, int64_t N, int64_t ld, double2* L
 }
 cudaError_t launch_copy_lower(const double2* G, int64_t N, int64_t ld, double2* L, cudaStream_t s) {
     k_copy_lower<<<nblk(N * N, 256), 256, 0, s>>>(G, N, ld, L);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void k_copy_lower_df(const float4* G, int64_t N, int64_t ld, double2* L) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N) return;
+    int64_t i = idx / N, j = idx % N;
+    L[i * ld + j] = (j <= i) ? df_to_f64(G[i * ld + j]) : make_double2(0.0, 0.0);
+}
+cudaError_t launch_copy_lower_df(const float4* G, int64_t N, int64_t ld, double2* L, cudaStream_t s) {
+    k_copy_lower_df<<<nblk(N * N, 256), 256, 0, s>>>(G, N, ld, L);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void k_df_to_f64(const float4* a, int64_t n, double2* b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = df_to_f64(a[i]);
+}
+cudaError_t launch_df_to_f64(const float4* a, int64_t n, double2* b, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_df_to_f64<<<nblk(n, 256), 256, 0, s>>>(a, n, b);
     note_launch();
     return cudaGetLastError();
 }
@@ -142,6 +200,21 @@ __global__ void k_pivot_stats(const double2* L, int64_t N, int64_t ld, DevStatus
 cudaError_t launch_pivot_stats(const double2* L, int64_t N, int64_t ld, DevStatus* st,
                                cudaStream_t s) {
     k_pivot_stats<<<nblk(N, 256), 256, 0, s>>>(L, N, ld, st);
+    note_launch();
+    return cudaGetLastError();
+}
+__global__ void k_pivot_stats_df(const float4* L, int64_t N, int64_t ld, DevStatus* st) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float4 d = L[i * ld + i];
+    double v = join_f64(d.x, d.y);
+    if (!(v > 0.0)) return;
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    atomicMin((unsigned long long*)&st->min_pivot, b);
+    atomicMax((unsigned long long*)&st->max_pivot, b);
+}
+cudaError_t launch_pivot_stats_df(const float4* L, int64_t N, int64_t ld, DevStatus* st, cudaStream_t s) {
+    k_pivot_stats_df<<<nblk(N, 256), 256, 0, s>>>(L, N, ld, st);
     note_launch();
     return cudaGetLastError();
 }

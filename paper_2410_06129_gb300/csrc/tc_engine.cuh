@@ -45,7 +45,7 @@
 
 #include <type_traits>
 
-#include "pinv_internal.h"
+#include "df.cuh"
 
 namespace pinv {
 namespace tc {
@@ -88,12 +88,27 @@ template <class P, class = void>
 struct HasStore16 : std::false_type {};
 template <class P>
 struct HasStore16<P, std::void_t<decltype(&P::store16)>> : std::true_type {};
-// ... or 4 columns at a time through a row-major copy of the tile in shared
-// memory (store4: a warp then writes whole rows, coalesced)
+// ... or through a row-major copy of the tile in shared memory (store4: a warp
+// then writes whole rows, lane l columns j0 + l + 32 u, u = 0..3, so that each
+// access of the warp covers 32 consecutive entries)
 template <class P, class = void>
 struct HasStore4 : std::false_type {};
 template <class P>
 struct HasStore4<P, std::void_t<decltype(&P::store4)>> : std::true_type {};
+// ... or subtract the tile from a double-float matrix (rmw_ptr(i, j): the entry
+// to update, or null): each warp then has several rows' entries in flight at
+// once, copied into the idle stage ring (cp.async), and the updates are FP32
+// arithmetic (df_sub_f32)
+template <class P, class = void>
+struct HasRmw : std::false_type {};
+template <class P>
+struct HasRmw<P, std::void_t<decltype(&P::rmw_ptr)>> : std::true_type {};
+// ... and name the entries it will read (prefetch: brought into L2 while the
+// tile's MMAs run)
+template <class P, class = void>
+struct HasPrefetch : std::false_type {};
+template <class P>
+struct HasPrefetch<P, std::void_t<decltype(&P::prefetch)>> : std::true_type {};
 template <class P, class = void>
 struct HintB : std::false_type {};
 template <class P>
@@ -198,6 +213,15 @@ __device__ inline void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes,
         "%4;" ::"r"(smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
+}
+// 16-byte global -> shared copy through L2 (cp.async), and the wait for all of this thread's
+__device__ inline void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// global -> L2 bulk prefetch (16-byte aligned address, size a multiple of 16); a hint, no completion
+__device__ inline void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ inline uint64_t policy_evict_last() {
     uint64_t pol;
@@ -669,6 +693,8 @@ __global__ void __launch_bounds__(NTHREADS_BULK, 1) k_tc_bulk(Sched sch, DevStat
 
         if (warp < NPW) {
             // ---------------- drains and epilogue
+            using PE = std::remove_cv_t<std::remove_reference_t<decltype(p)>>;
+            if constexpr (HasPrefetch<PE>::value) p.prefetch(i0 + q * 32 + lane, j0 + 64 * h, 64);
             float tot[128];
 #pragma unroll
             for (int u = 0; u < 128; ++u) tot[u] = 0.f;
@@ -681,28 +707,54 @@ __global__ void __launch_bounds__(NTHREADS_BULK, 1) k_tc_bulk(Sched sch, DevStat
                 tc_fence_before();
                 mbar_arrive(&tempty[b]);
             }
-            using PE = std::remove_cv_t<std::remove_reference_t<decltype(p)>>;
-            if constexpr (HasStore4<PE>::value) {
+            if constexpr (HasStore4<PE>::value || HasRmw<PE>::value) {
                 // Every stage of the tile has been consumed and the loader waits for the
                 // tile barrier, so the stage ring holds a row-major copy of the tile
-                // (rows padded by 16 bytes: conflict-free float4 accesses); each warp
-                // then writes whole rows. Every drain thread reaches the barriers; the
+                // (rows padded by 16 bytes: conflict-free float4 writes); each warp
+                // then updates whole rows. Every drain thread reaches the barriers; the
                 // OR makes the decision to write the same in all of them.
                 if (!named_barrier_or(NPW * 32, !ok || abort_flag)) {
                     constexpr int SP = BN + 2;
-                    float2* S = reinterpret_cast<float2*>(smem);
+                    float2* Rt = reinterpret_cast<float2*>(smem);
                     const int r = q * 32 + lane;
 #pragma unroll
                     for (int u = 0; u < 64; u += 2)
-                        *reinterpret_cast<float4*>(&S[r * SP + 64 * h + u]) =
+                        *reinterpret_cast<float4*>(&Rt[r * SP + 64 * h + u]) =
                             make_float4(tot[u], tot[64 + u], tot[u + 1], tot[64 + u + 1]);
                     named_barrier(NPW * 32);
-                    for (int rr = warp; rr < BM; rr += NPW) {
-                        const float4 a = *reinterpret_cast<const float4*>(&S[rr * SP + 4 * lane]);
-                        const float4 b = *reinterpret_cast<const float4*>(&S[rr * SP + 4 * lane + 2]);
-                        const float2 v[4] = {make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
-                                             make_float2(b.z, b.w)};
-                        p.store4(i0 + rr, j0 + 4 * lane, v);
+                    if constexpr (HasRmw<PE>::value) {
+                        // RE rows per warp at a time: their entries are copied into the
+                        // ring behind the tile (cp.async, no registers held), then each
+                        // lane updates the entries it copied (lane l: columns l + 32 u)
+                        constexpr int TB = BM * SP * (int)sizeof(float2);
+                        constexpr int RE = TB + NPW * 4 * BN * 16 <= CF::STAGES * CF::STAGE_BYTES ? 4 : 2;
+                        static_assert(TB + NPW * RE * BN * 16 <= CF::STAGES * CF::STAGE_BYTES, "staging");
+                        float4* stg = reinterpret_cast<float4*>(smem + TB) + warp * RE * BN;
+                        for (int r0 = warp; r0 < BM; r0 += NPW * RE) {
+#pragma unroll
+                            for (int r = 0; r < RE; ++r)
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    const float4* g = p.rmw_ptr(i0 + r0 + r * NPW, j0 + lane + 32 * u);
+                                    if (g) cp_async16(stg + r * BN + lane + 32 * u, g);
+                                }
+                            cp_async_wait_all();
+#pragma unroll
+                            for (int r = 0; r < RE; ++r)
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    float4* g = p.rmw_ptr(i0 + r0 + r * NPW, j0 + lane + 32 * u);
+                                    if (g)
+                                        *g = df_sub_f32(stg[r * BN + lane + 32 * u],
+                                                        Rt[(r0 + r * NPW) * SP + lane + 32 * u]);
+                                }
+                        }
+                    } else {
+                        for (int rr = warp; rr < BM; rr += NPW) {
+                            const float2 v[4] = {Rt[rr * SP + lane], Rt[rr * SP + lane + 32], Rt[rr * SP + lane + 64],
+                                                 Rt[rr * SP + lane + 96]};
+                            p.store4(i0 + rr, j0 + lane, v);
+                        }
                     }
                     fence_proxy_async();  // generic shared accesses before the next tile's copies
                 }

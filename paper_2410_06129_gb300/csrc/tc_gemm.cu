@@ -186,9 +186,9 @@ __device__ inline void gen_eh8_voxels(const EncodeDev& e, const EhCol& r, int64_
 }
 
 // ------------------------------------------------------------------ Gram (Eq. 6, Eq. 11)
-// G[i][j] = (sum_m conj(A[m][i]) A[m][j]) * (sum_c conj(s_c(i)) s_c(j)) + lam delta_ij, lower part.
-// v is the sample sum (A^H A)_ij; j > i is not stored.
-__device__ inline void gram_store(const EncodeDev& e, double lam, double2* G, int64_t ld, int64_t i, int64_t j,
+// G[i][j] = (sum_m conj(A[m][i]) A[m][j]) * (sum_c conj(s_c(i)) s_c(j)) + lam delta_ij, lower part,
+// in double-float storage (df_of_f32). v is the sample sum (A^H A)_ij; j > i is not stored.
+__device__ inline void gram_store(const EncodeDev& e, double lam, float4* G, int64_t ld, int64_t i, int64_t j,
                                   float2 v) {
     if (j > i) return;
     if (i == j) {
@@ -202,7 +202,7 @@ __device__ inline void gram_store(const EncodeDev& e, double lam, double2* G, in
                 s += a.x * a.x + a.y * a.y;
             }
         }
-        G[i * ld + i] = make_double2((double)e.Mk * s + lam, 0.0);
+        G[i * ld + i] = to_df_i(make_double2((double)e.Mk * s + lam, 0.0));
         return;
     }
     if (e.coils32) {
@@ -215,13 +215,13 @@ __device__ inline void gram_store(const EncodeDev& e, double lam, double2* G, in
         }
         v = cmulf(v, sc);
     }
-    G[i * ld + j] = make_double2((double)v.x, (double)v.y);
+    G[i * ld + j] = df_of_f32(v);
 }
 
 struct GramTC {
     EncodeDev e;
     double lam;
-    double2* G;
+    float4* G;
     int64_t ld;
     __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
         i0 = by * BM;
@@ -328,7 +328,7 @@ struct GramBulk {
     static constexpr bool kBulk = true;
     EncodeDev e;
     double lam;
-    double2* G;          // splits == 1: the lower part of G
+    float4* G;           // splits == 1: the lower part of G (double-float)
     int64_t ld;
     float2* part;        // splits > 1: partial sums [split][NP][NP], NP = nt * BM
     const uint8_t* tab;  // [nt][kcn][S] blocks
@@ -351,17 +351,17 @@ struct GramBulk {
     __device__ const uint8_t* bulk_b(int64_t j0, int64_t kc, int sl) const {
         return tab + (((j0 / BN) * kcn + kc) * S + sl) * TAB_BLOCK;
     }
-    // (A^H A)[i][j .. j + 3], lower part: partial sums, or G with the coil factor
+    // (A^H A)[i][j + 32 u], u = 0..3, lower part: partial sums, or G with the coil factor
     __device__ void store4(int64_t i, int64_t j, const float2 (&v)[4]) const {
         const int64_t np = nt * BM, il = i % np;
         if (il >= e.N) return;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            if (j + u > il) continue;
+            if (j + 32 * u > il) continue;
             if (splits > 1)
-                part[i * np + j + u] = v[u];
+                part[i * np + j + 32 * u] = v[u];
             else
-                gram_store(e, lam, G, ld, il, j + u, v[u]);
+                gram_store(e, lam, G, ld, il, j + 32 * u, v[u]);
         }
     }
     __device__ bool row_ok(int64_t i) const { return i % (nt * BM) < e.N; }
@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(256) k_tab_panel(const float2* __restrict__ L3
     put_b<S>(tab + (rt * kcn + kc) * S * B_SL, r, g, v);
 }
 template <int S>
-__global__ void __launch_bounds__(256) k_tab_wrows(const double2* __restrict__ W, int64_t ld, int64_t p0, int64_t kw,
+__global__ void __launch_bounds__(256) k_tab_wrows(const float4* __restrict__ W, int64_t ld, int64_t p0, int64_t kw,
                                                    int64_t ncols, uint8_t* tab) {
     const int64_t kc = blockIdx.x, ct = blockIdx.y, kcn = gridDim.x;
     const int r = threadIdx.x & (BM - 1), g = threadIdx.x >> 7;
@@ -582,8 +582,7 @@ __global__ void __launch_bounds__(256) k_tab_wrows(const double2* __restrict__ W
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         const bool ok = j < ncols && k0 + t < kw;
-        const double2 w = ok ? W[(p0 + k0 + t) * ld + j] : make_double2(0.0, 0.0);
-        v[t] = make_float2((float)w.x, (float)w.y);
+        v[t] = ok ? df_to_f32(W[(p0 + k0 + t) * ld + j]) : make_float2(0.f, 0.f);
     }
     put_b<S>(tab + (ct * kcn + kc) * S * B_SL, r, g, v);
 }
@@ -591,7 +590,7 @@ __global__ void __launch_bounds__(256) k_tab_wrows(const double2* __restrict__ W
 struct HerkBulk {
     static constexpr bool kBulk = true;
     const uint8_t* tab;
-    double2* G;
+    float4* G;                   // double-float storage
     int64_t ld, N, r0, nt, kcn;  // trailing rows from r0 in nt tiles; panel chunks
     int S;
     int64_t jt0, ncols;          // column tiles jt0 .. jt0 + ncols - 1 of the trailing matrix (grid nt x ncols)
@@ -611,16 +610,12 @@ struct HerkBulk {
     __device__ const uint8_t* bulk_b(int64_t j0, int64_t kc, int sl) const {
         return tab + ((((j0 - r0) / BN) * kcn + kc) * S + sl) * B_SL;
     }
-    // G[i][j .. j + 3] -= v (lower part)
-    __device__ void store4(int64_t i, int64_t j, const float2 (&v)[4]) const {
-        if (i >= N) return;
-        double2* row = G + i * ld + j;
-        double2 g[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) g[u] = (j + u <= i) ? row[u] : make_double2(0.0, 0.0);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (j + u <= i) row[u] = make_double2(g[u].x - (double)v[u].x, g[u].y - (double)v[u].y);
+    // G[i][j] -= v: the entry to update (lower part), or null
+    __device__ float4* rmw_ptr(int64_t i, int64_t j) const { return (i < N && j <= i) ? G + i * ld + j : nullptr; }
+    // G[i][j .. j + n - 1] into L2, the lower part only
+    __device__ void prefetch(int64_t i, int64_t j, int n) const {
+        if (i >= N || j > i) return;
+        bulk_prefetch_l2(G + i * ld + j, (uint32_t)(i - j + 1 < n ? i - j + 1 : n) * 16u);
     }
     __device__ bool row_ok(int64_t i) const { return i < N; }
     __device__ bool col_ok(int64_t j) const { return j < N; }
@@ -630,7 +625,7 @@ struct TrtriBulk {
     static constexpr bool kBulk = true;
     const uint8_t* tabl;
     const uint8_t* tabw;
-    double2* W;
+    float4* W;                          // double-float storage
     int64_t ld, N, r0, ntr, ntc, kcn;  // rows from r0 in ntr tiles; columns below r0 in ntc tiles
     int S;
     __device__ bool tile(int64_t bx, int64_t, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
@@ -648,16 +643,12 @@ struct TrtriBulk {
     __device__ const uint8_t* bulk_b(int64_t j0, int64_t kc, int sl) const {
         return tabw + (((j0 / BN) * kcn + kc) * S + sl) * B_SL;
     }
-    // W[i][j .. j + 3] -= v (columns below r0)
-    __device__ void store4(int64_t i, int64_t j, const float2 (&v)[4]) const {
-        if (i >= N) return;
-        double2* row = W + i * ld + j;
-        double2 w[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) w[u] = (j + u < r0) ? row[u] : make_double2(0.0, 0.0);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (j + u < r0) row[u] = make_double2(w[u].x - (double)v[u].x, w[u].y - (double)v[u].y);
+    // W[i][j] -= v: the entry to update (columns below r0), or null
+    __device__ float4* rmw_ptr(int64_t i, int64_t j) const { return (i < N && j < r0) ? W + i * ld + j : nullptr; }
+    // W[i][j .. j + n - 1] into L2, the columns below r0 only
+    __device__ void prefetch(int64_t i, int64_t j, int n) const {
+        if (i >= N || j >= r0) return;
+        bulk_prefetch_l2(W + i * ld + j, (uint32_t)(r0 - j < n ? r0 - j : n) * 16u);
     }
     __device__ bool row_ok(int64_t i) const { return i < N; }
     __device__ bool col_ok(int64_t j) const { return j < r0; }
@@ -670,7 +661,7 @@ struct TrtriBulk {
 struct HerkTC {
     const float2* P;
     int64_t ldp;
-    double2* G;
+    float4* G;  // double-float storage
     int64_t ld, N, nbk, t0, jmax;
     __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
         i0 = t0 + by * BM;
@@ -693,54 +684,17 @@ struct HerkTC {
     __device__ bool col_ok(int64_t j) const { return j < jmax; }
     __device__ void store(int64_t i, int64_t j, float2 v) const {
         if (j > i) return;
-        const double2 g = G[i * ld + j];
-        G[i * ld + j] = make_double2(g.x - (double)v.x, g.y - (double)v.y);
+        G[i * ld + j] = df_sub_f32(G[i * ld + j], v);
     }
 };
 
 // ------------------------------------------------------------------ W = L^-1
-// W[k0+i][j] = sum_k Dinv[i][k] W[k0+k][j] for j < k0 + nbk (in place on a block row).
-struct TrtriDiagTC {
-    const float2* Dinv32;
-    double2* W;
-    int64_t ld, N, k0, nbk;
-    __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
-        i0 = 0;
-        j0 = bx * BN;
-        kb = 0;
-        ke = nbk;
-        return true;
-    }
-    __device__ int64_t row_a(int64_t i) const { return i; }
-    __device__ int64_t row_b(int64_t j) const { return j; }
-    __device__ void a8(int64_t i, int64_t k, int64_t ke, float2 (&v)[8]) const {
-#pragma unroll
-        for (int t = 0; t < 8; ++t)
-            v[t] = (i < nbk && k + t < ke) ? Dinv32[i * 64 + k + t] : make_float2(0.f, 0.f);
-    }
-    __device__ void b8(int64_t j, int64_t k, int64_t ke, float2 (&v)[8]) const {
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            if (j < k0 + nbk && k + t < ke) {
-                const double2 w = W[(k0 + k + t) * ld + j];
-                v[t] = make_float2((float)w.x, (float)w.y);
-            } else {
-                v[t] = make_float2(0.f, 0.f);
-            }
-        }
-    }
-    __device__ bool row_ok(int64_t i) const { return i < nbk; }
-    __device__ bool col_ok(int64_t j) const { return j < k0 + nbk; }
-    __device__ void store(int64_t i, int64_t j, float2 v) const {
-        W[(k0 + i) * ld + j] = make_double2(v.x, v.y);
-    }
-};
-
-// W[i][j] -= sum_k L[i][k0+k] W[k0+k][j] for k0 + nbk <= i < imax, j < k0 + nbk.
+// W[i][j] -= sum_k L[i][k0+k] W[k0+k][j] for k0 + nbk <= i < imax, j < k0 + nbk
+// (W in double-float storage).
 struct TrtriUpdTC {
     const float2* L32;
     int64_t ldl;
-    double2* W;
+    float4* W;
     int64_t ld, N, k0, nbk, imax;
     __device__ bool tile(int64_t bx, int64_t by, int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
         i0 = k0 + nbk + by * BM;
@@ -756,21 +710,12 @@ struct TrtriUpdTC {
     }
     __device__ void b8(int64_t j, int64_t k, int64_t ke, float2 (&v)[8]) const {
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            if (j < k0 + nbk && k + t < ke) {
-                const double2 w = W[(k0 + k + t) * ld + j];
-                v[t] = make_float2((float)w.x, (float)w.y);
-            } else {
-                v[t] = make_float2(0.f, 0.f);
-            }
-        }
+        for (int t = 0; t < 8; ++t)
+            v[t] = (j < k0 + nbk && k + t < ke) ? df_to_f32(W[(k0 + k + t) * ld + j]) : make_float2(0.f, 0.f);
     }
     __device__ bool row_ok(int64_t i) const { return i < imax; }
     __device__ bool col_ok(int64_t j) const { return j < k0 + nbk; }
-    __device__ void store(int64_t i, int64_t j, float2 v) const {
-        const double2 w = W[i * ld + j];
-        W[i * ld + j] = make_double2(w.x - (double)v.x, w.y - (double)v.y);
-    }
+    __device__ void store(int64_t i, int64_t j, float2 v) const { W[i * ld + j] = df_sub_f32(W[i * ld + j], v); }
 };
 
 // ------------------------------------------------------------------ Recon = W^H (W E^H)
@@ -840,7 +785,7 @@ static cudaError_t run(const P& p, dim3 grid, int slices, DevStatus* st, int sit
 
 static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
-cudaError_t launch_gram_tc(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld,
+cudaError_t launch_gram_tc(const EncodeDev& e, double lambda, int slices, float4* G, int64_t ld,
                            DevStatus* st, cudaStream_t s) {
     tc::GramTC p{e, lambda, G, ld};
     return run(p, dim3(cdiv(e.N, tc::BN), cdiv(e.N, tc::BM)), slices, st, 1, s);
@@ -848,7 +793,7 @@ cudaError_t launch_gram_tc(const EncodeDev& e, double lambda, int slices, double
 
 // G[i][j] (j <= i) from the partial sample sums of the bulk Gram, added in split order
 __global__ void k_gram_finalize(EncodeDev e, double lam, const float2* __restrict__ part, int splits, int64_t np,
-                                double2* G, int64_t ld) {
+                                float4* G, int64_t ld) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= e.N * e.N) return;
     const int64_t i = idx / e.N, j = idx - i * e.N;
@@ -886,7 +831,7 @@ GramBulkShape gram_bulk_shape(const EncodeDev& e, int slices) {
     g.part_bytes = g.splits > 1 ? g.splits * np * np * sizeof(float2) : 0;
     return g;
 }
-tc::GramBulk gram_bulk_problem(const EncodeDev& e, double lam, int slices, double2* G, int64_t ld, void* work,
+tc::GramBulk gram_bulk_problem(const EncodeDev& e, double lam, int slices, float4* G, int64_t ld, void* work,
                                int64_t* items) {
     const GramBulkShape g = gram_bulk_shape(e, slices);
     uint8_t* tab = (uint8_t*)work;
@@ -912,7 +857,7 @@ cudaError_t gram_bulk_table(const EncodeDev& e, int slices, void* work, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t gram_bulk_finish(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld, void* work,
+cudaError_t gram_bulk_finish(const EncodeDev& e, double lambda, int slices, float4* G, int64_t ld, void* work,
                              cudaStream_t s) {
     const GramBulkShape g = gram_bulk_shape(e, slices);
     if (g.splits <= 1) return cudaSuccess;
@@ -923,7 +868,7 @@ cudaError_t gram_bulk_finish(const EncodeDev& e, double lambda, int slices, doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_gram_bulk(const EncodeDev& e, double lambda, int slices, double2* G, int64_t ld, void* work,
+cudaError_t launch_gram_bulk(const EncodeDev& e, double lambda, int slices, float4* G, int64_t ld, void* work,
                              DevStatus* st, cudaStream_t s) {
     cudaError_t err = gram_bulk_table(e, slices, work, s);
     if (err != cudaSuccess) return err;
@@ -953,9 +898,9 @@ __device__ inline void cmac_conj(float2& acc, float2 a, float2 b) {  // acc += a
 }
 
 // L[i][k0 + j] = sum_k A[i][k] conj(Dinv[j][k]) for rows i >= row0, A[i][k] the
-// FP32 rounding of G[i][k0 + k]: written to G (FP64) and to P (FP32)
+// FP32 rounding of G[i][k0 + k]: written to G (double-float) and to P (FP32)
 __global__ void __launch_bounds__(256) k_trsm_panel(float2* P, int64_t ldp, const float2* __restrict__ Dinv32,
-                                                  double2* G, int64_t ldg, int64_t k0, int nbk, int64_t row0,
+                                                  float4* G, int64_t ldg, int64_t k0, int nbk, int64_t row0,
                                                   int64_t N) {
     __shared__ float2 Dt[64][65];  // Dt[k][j] = Dinv[j][k]
     __shared__ float2 A[PNL_ROWS][64];
@@ -974,12 +919,7 @@ __global__ void __launch_bounds__(256) k_trsm_panel(float2* P, int64_t ldp, cons
         for (int t = 0; t < 4; ++t) {
             const int e = tid + 256 * t, r = e / 64, k = e % 64;
             const int64_t i = i0 + r;
-            if (i < N && k < nbk) {
-                const double2 g = G[i * ldg + k0 + k];
-                u[t] = make_float2(f64_to_f32_rn(g.x), f64_to_f32_rn(g.y));
-            } else {
-                u[t] = make_float2(0.f, 0.f);
-            }
+            u[t] = (i < N && k < nbk) ? df_to_f32(G[i * ldg + k0 + k]) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
@@ -1011,7 +951,7 @@ __global__ void __launch_bounds__(256) k_trsm_panel(float2* P, int64_t ldp, cons
         for (int b = 0; b < 2; ++b) {
             const int j = lane + 32 * b;
             if (i < N && j < nbk) {
-                G[i * ldg + k0 + j] = make_double2((double)acc[ra][b].x, (double)acc[ra][b].y);
+                G[i * ldg + k0 + j] = df_of_f32(acc[ra][b]);
                 P[i * ldp + j] = acc[ra][b];
             }
         }
@@ -1022,7 +962,7 @@ __global__ void __launch_bounds__(256) k_trsm_panel(float2* P, int64_t ldp, cons
 // (K = nbk <= 64; jmax - t0 <= 32 CB; r0 >= t0). Dynamic shared memory: herk_panel_smem(CB).
 constexpr size_t herk_panel_smem(int cb) { return sizeof(float2) * (PNL_ROWS * 64 + 64 * (32 * cb + 1)); }
 template <int CB>
-__global__ void __launch_bounds__(256) k_herk_panel(const float2* __restrict__ P, int64_t ldp, double2* G,
+__global__ void __launch_bounds__(256) k_herk_panel(const float2* __restrict__ P, int64_t ldp, float4* G,
                                                   int64_t ldg, int nbk, int64_t t0, int64_t jmax, int64_t r0,
                                                   int64_t N) {
     constexpr int WP = 32 * CB + 1;  // padded row of Bt: transposed stores spread over the banks
@@ -1084,16 +1024,13 @@ __global__ void __launch_bounds__(256) k_herk_panel(const float2* __restrict__ P
         for (int b = 0; b < CB; ++b) {
             const int c = lane + 32 * b;
             const int64_t j = t0 + c;
-            if (i < N && c < W && j <= i) {
-                const double2 g = G[i * ldg + j];
-                G[i * ldg + j] = make_double2(g.x - (double)acc[ra][b].x, g.y - (double)acc[ra][b].y);
-            }
+            if (i < N && c < W && j <= i) G[i * ldg + j] = df_sub_f32(G[i * ldg + j], acc[ra][b]);
         }
     }
 }
 
 template <int CB>
-static cudaError_t launch_herk_panel(const float2* P, int64_t ldp, double2* G, int64_t ldg, int nbk, int64_t t0,
+static cudaError_t launch_herk_panel(const float2* P, int64_t ldp, float4* G, int64_t ldg, int nbk, int64_t t0,
                                      int64_t jmax, int64_t r0, int64_t N, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
@@ -1109,14 +1046,14 @@ static cudaError_t launch_herk_panel(const float2* P, int64_t ldp, double2* G, i
 }
 
 // G[i][j] -= sum_k P[i][k] conj(P[j][k]) for columns t0 <= j < jmax (at most 192), rows r0 <= i < N
-static cudaError_t herk_panel(const float2* P, int64_t ldp, double2* G, int64_t ldg, int nbk, int64_t t0,
+static cudaError_t herk_panel(const float2* P, int64_t ldp, float4* G, int64_t ldg, int nbk, int64_t t0,
                               int64_t jmax, int64_t r0, int64_t N, cudaStream_t s) {
     const int64_t w = jmax - t0;
     return w <= 64    ? launch_herk_panel<2>(P, ldp, G, ldg, nbk, t0, jmax, r0, N, s)
            : w <= 128 ? launch_herk_panel<4>(P, ldp, G, ldg, nbk, t0, jmax, r0, N, s)
                       : launch_herk_panel<6>(P, ldp, G, ldg, nbk, t0, jmax, r0, N, s);
 }
-static cudaError_t trsm_panel(float2* P, int64_t ldp, const float2* Dinv32, double2* G, int64_t ldg, int64_t k0,
+static cudaError_t trsm_panel(float2* P, int64_t ldp, const float2* Dinv32, float4* G, int64_t ldg, int64_t k0,
                               int nbk, int64_t row0, int64_t N, cudaStream_t s) {
     cudaError_t e = launch_pdl(k_trsm_panel, dim3(cdiv(N - row0, PNL_ROWS)), dim3(256), 0, s, P, ldp, Dinv32, G,
                                ldg, k0, nbk, row0, N);
@@ -1143,10 +1080,11 @@ static cudaError_t panel_table(const float2* L32, int64_t N, int64_t p0, int64_t
 // panel each step updates only the panel's remaining columns (K = 64); the
 // trailing matrix gets one update per panel with K = 256, so its tiles run
 // 16 tensor-core stages instead of 4 and G is read and written a quarter as
-// often.
+// often. G is in double-float storage (float4 per entry) for the whole
+// factorisation, and L is left there in the same form.
 constexpr int NBK = 64, NBP = 256;
 
-cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, float2* Dinv32, float2* L32,
+cudaError_t launch_potrf_tc(float4* G, int64_t N, int64_t ld, double2* Dinv, float2* Dinv32, float2* L32,
                             int slices, DevStatus* st, cudaStream_t s, void* tab, const cudaEvent_t* ev_panel,
                             const TrailLookahead* la) {
     // lookahead: after each panel only the next panel's columns (two column tiles)
@@ -1256,7 +1194,7 @@ cudaError_t launch_potrf_tc(double2* G, int64_t N, int64_t ld, double2* Dinv, fl
 }
 
 // Inside a panel the inverse's steps have K = 64, too short for the tensor-core
-// engine's set-up (a launch of TrtriDiagTC / TrtriUpdTC took 27 / 44 us against a
+// engine's set-up (tensor-core launches of these steps took 27 / 44 us against a
 // few microseconds of products): these FP32 SIMT kernels stage the 64-wide operands
 // in shared memory, as the Cholesky's panel kernels do, and accumulate in FP32.
 __device__ inline void cmac(float2& acc, float2 a, float2 b) {  // acc += a * b
@@ -1266,7 +1204,7 @@ __device__ inline void cmac(float2& acc, float2 a, float2 b) {  // acc += a * b
 
 // W[k0 + i][j] = sum_k Dinv[i][k] W[k0 + k][j] (W rounded to FP32) for i < nbk, j < ncol:
 // one CTA per 64 columns, each thread 4 x 4 outputs (rows ty + 16 a, columns tx + 16 b)
-__global__ void __launch_bounds__(256) k_trtri_diag(const float2* __restrict__ Dinv32, double2* W, int64_t ld,
+__global__ void __launch_bounds__(256) k_trtri_diag(const float2* __restrict__ Dinv32, float4* W, int64_t ld,
                                                   int64_t k0, int nbk, int64_t ncol) {
     __shared__ float2 Ds[64][65];  // Ds[i][k] = Dinv[i][k]
     __shared__ float2 Bs[64][65];  // Bs[k][c] = W[k0 + k][j0 + c]
@@ -1279,12 +1217,7 @@ __global__ void __launch_bounds__(256) k_trtri_diag(const float2* __restrict__ D
         const int e = tid + 256 * t, r = e / 64, c = e % 64;
         Ds[r][c] = (r < nbk && c < nbk) ? Dinv32[r * 64 + c] : make_float2(0.f, 0.f);
         const int64_t j = j0 + c;
-        if (r < nbk && j < ncol) {
-            const double2 w = W[(k0 + r) * ld + j];
-            Bs[r][c] = make_float2((float)w.x, (float)w.y);
-        } else {
-            Bs[r][c] = make_float2(0.f, 0.f);
-        }
+        Bs[r][c] = (r < nbk && j < ncol) ? df_to_f32(W[(k0 + r) * ld + j]) : make_float2(0.f, 0.f);
     }
     __syncthreads();
     float2 acc[4][4];
@@ -1310,14 +1243,14 @@ __global__ void __launch_bounds__(256) k_trtri_diag(const float2* __restrict__ D
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int64_t j = j0 + tx + 16 * b;
-            if (r < nbk && j < ncol) W[(k0 + r) * ld + j] = make_double2(acc[a][b].x, acc[a][b].y);
+            if (r < nbk && j < ncol) W[(k0 + r) * ld + j] = df_of_f32(acc[a][b]);
         }
     }
 }
 
 // W[i][j] -= sum_k L[i][k0 + k] W[k0 + k][j] for rows r0 <= i < imax, j < ncol (K = nbk):
 // one CTA per 16 rows x 64 columns, each thread 1 row x 4 columns
-__global__ void __launch_bounds__(256) k_trtri_upd(const float2* __restrict__ L32, int64_t ldl, double2* W,
+__global__ void __launch_bounds__(256) k_trtri_upd(const float2* __restrict__ L32, int64_t ldl, float4* W,
                                                  int64_t ld, int64_t k0, int nbk, int64_t r0, int64_t imax,
                                                  int64_t ncol) {
     __shared__ float2 As[16][65];  // As[r][k] = L[i0 + r][k0 + k]
@@ -1336,12 +1269,7 @@ __global__ void __launch_bounds__(256) k_trtri_upd(const float2* __restrict__ L3
     for (int t = 0; t < 16; ++t) {
         const int e = tid + 256 * t, k = e / 64, c = e % 64;
         const int64_t j = j0 + c;
-        if (k < nbk && j < ncol) {
-            const double2 w = W[(k0 + k) * ld + j];
-            Bs[k][c] = make_float2((float)w.x, (float)w.y);
-        } else {
-            Bs[k][c] = make_float2(0.f, 0.f);
-        }
+        Bs[k][c] = (k < nbk && j < ncol) ? df_to_f32(W[(k0 + k) * ld + j]) : make_float2(0.f, 0.f);
     }
     __syncthreads();
     float2 acc[4];
@@ -1358,19 +1286,17 @@ __global__ void __launch_bounds__(256) k_trtri_upd(const float2* __restrict__ L3
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         const int64_t j = j0 + tx + 16 * b;
-        if (j < ncol) {
-            const double2 w = W[i * ld + j];
-            W[i * ld + j] = make_double2(w.x - (double)acc[b].x, w.y - (double)acc[b].y);
-        }
+        if (j < ncol) W[i * ld + j] = df_sub_f32(W[i * ld + j], acc[b]);
     }
 }
 
 // W = L^-1 by blocked forward substitution on I, with the same two levels:
 // inside a 256-row panel each 64-row step updates the panel's rows only; the
 // rows below get one update per panel with K = 256.
-cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, double2* W, float2* W32,
+cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, float4* W, float2* W32,
                             int slices, DevStatus* st, cudaStream_t s, void* tab, const cudaEvent_t* ev_panel) {
-    cudaError_t e = launch_fill_identity(W, N, N, s);
+    // W is in double-float storage while it is formed; the last pass leaves it in FP64
+    cudaError_t e = launch_fill_identity_df(W, N, N, s);
     if (e != cudaSuccess) return e;
     // the inverse runs beside the Cholesky chain (and its trailing updates). Up to
     // N = 16384, where the chain is a latency-bound sequence of small launches, the
@@ -1404,7 +1330,7 @@ cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, 
                 uint8_t* tabw = tabl + panel_table_bytes(N, slices);
                 if ((e = panel_table(L32, N, p0, pend - p0, pend, slices, tabl, s)) != cudaSuccess) return e;
                 const dim3 wg((unsigned)kcn, (unsigned)ntc);
-                const double2* Wc = W;
+                const float4* Wc = W;
                 e = slices == 3 ? launch_pdl(tc::k_tab_wrows<3>, wg, dim3(256), 0, s, Wc, N, p0, pend - p0, pend, tabw)
                                 : launch_pdl(tc::k_tab_wrows<2>, wg, dim3(256), 0, s, Wc, N, p0, pend - p0, pend, tabw);
                 if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1419,7 +1345,7 @@ cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, 
             }
         }
     }
-    return launch_to_f32(W, W32, N * N, s);
+    return launch_df_finish(W, N, N, W32, s);
 }
 
 cudaError_t launch_recon_tc(const EncodeDev& e, const float2* W32, const float2* WT32, float2* T, int slices,
