@@ -114,9 +114,9 @@ pinv_status build_gram(pinv_plan* p, cudaStream_t s, bool main_gram) {
             CK(cudaStreamWaitEvent(p->s_x, p->ev_xfork, 0));
             sx = p->s_x;
         }
-        double2* work = nullptr;
+        float4* work = nullptr;
         CK(work_alloc((void**)&work, toeplitz_work_bytes(p->enc), sx));
-        CK(launch_toeplitz64(p->enc, work, p->Ttab, sx));
+        CK(launch_toeplitz(p->enc, work, p->Ttab, sx));
         CK(cudaFreeAsync(work, sx));
         CK(launch_gram_exact(p->enc, p->Ttab, p->lambda_abs, p->Gx, sx));
         CK(launch_gram_norm1(nullptr, nullptr, p->Gx, N, N, p->st, sx));

@@ -217,6 +217,69 @@ static cudaError_t launch_df(P p, int64_t rows, int64_t F, int64_t K, cudaStream
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ Toeplitz table
+// (A^H A)[n][n'] depends only on the index offset (i_n - i_n') per axis for voxels
+// on the grid without B0, so
+//   T[dz][dy][dx] = sum_m q_x(m, dx) q_y(m, dy) q_z(m, dz),
+//   q(m, d) = exp(+i 2 pi k_m d fov / n_axis),
+// over offsets -(n-1)..(n-1) per axis ((2n-1) entries, dx fastest). q comes from the
+// double-float phase table as conj(e[m][d]) e[m][0] (d >= 0) or conj(e[m][0])
+// e[m][-d] (d < 0), i.e. from the same pair of encoding elements the Gram entry
+// multiplies. The double-float tile engine sums over the samples, split over
+// blockIdx.z into partials that k_df_reduce adds in split order (deterministic).
+// T[-d] = conj(T[d]): the engine forms the columns d_yz >= 0 and the store writes
+// each canonical entry and the conjugate of its mirror, so T is Hermitian to the bit.
+__device__ inline float4 toep_q_df(const float4* tab, int n, int64_t m, int d) {
+    if (n == 1) return make_float4(1.f, 0.f, 0.f, 0.f);
+    const float4* row = tab + m * n;
+    return d >= 0 ? cdf_mul(cdf_conj(row[d]), row[0]) : cdf_mul(cdf_conj(row[0]), row[-d]);
+}
+struct ToeplitzDF {
+    EncodeDev e;
+    double2* T;
+    int64_t Tx, Ty, Tyz, jm;  // columns jm .. Tyz - 1 of T[d_yz][d_x]
+    __device__ int64_t K() const { return e.Mk; }
+    __device__ bool a_ok(int64_t i) const { return i < Tx; }
+    __device__ bool b_ok(int64_t j) const { return j < Tyz - jm; }
+    __device__ float4 a(int64_t i, int64_t m) const { return toep_q_df(e.exdf, e.nx, m, (int)i - (e.nx - 1)); }
+    __device__ float4 b(int64_t m, int64_t j) const {
+        const int64_t jj = j + jm;
+        const int dy = (int)(jj % Ty) - (e.ny - 1), dz = (int)(jj / Ty) - (e.nz - 1);
+        const float4 qy = toep_q_df(e.eydf, e.ny, m, dy);
+        return e.nz > 1 ? cdf_mul(qy, toep_q_df(e.ezdf, e.nz, m, dz)) : qy;
+    }
+    // canonical entries (d_yz > 0, or d_yz = 0 and d_x >= 0) and their mirrors
+    __device__ void store(int64_t i, int64_t j, double2 v) const {
+        const int64_t jj = j + jm;
+        if (jj == jm && i < (Tx - 1) / 2) return;
+        T[jj * Tx + i] = v;
+        const int64_t mi = Tx - 1 - i, mj = Tyz - 1 - jj;
+        if (mi != i || mj != jj) T[mj * Tx + mi] = zconj(v);
+    }
+};
+
+size_t toeplitz_work_bytes(const EncodeDev& e) {
+    const int64_t Tx = 2 * e.nx - 1, Tyz = (2 * e.ny - 1) * (2 * e.nz - 1), jm = (Tyz - 1) / 2;
+    return (size_t)64 * Tx * (Tyz - jm) * sizeof(float4);  // at most 64 partial tables
+}
+
+cudaError_t launch_toeplitz(const EncodeDev& e, float4* work, double2* T, cudaStream_t s) {
+    if (!e.exdf || !e.eydf || !e.ezdf) return cudaErrorInvalidValue;
+    const int64_t Tx = 2 * e.nx - 1, Ty = 2 * e.ny - 1, Tyz = Ty * (2 * e.nz - 1), jm = (Tyz - 1) / 2;
+    const int64_t rows = Tx, F = Tyz - jm, K = e.Mk;
+    // sample splits of about 128 samples (short CTAs: the table forms beside the
+    // Cholesky, whose launches need the SMs back quickly), at most 64
+    const int sp = (int)std::max<int64_t>(1, std::min<int64_t>(64, (K + 127) / 128));
+    const int64_t chunk = ((K + sp - 1) / sp + 15) / 16 * 16;
+    const ToeplitzDF p{e, T, Tx, Ty, Tyz, jm};
+    cudaError_t err = df_shape<64, 64, 4, 4>(p, rows, F, sp, chunk, work, s);
+    if (err != cudaSuccess || sp == 1) return err;
+    const int64_t n = rows * F;
+    k_df_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, work, sp, rows, F);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_forward_df(const EncodeDev& e, const double2* X, int64_t F, const double2* D, double2* U,
                               cudaStream_t s, float4* work) {
     if (F == 0) return cudaSuccess;
@@ -231,10 +294,12 @@ cudaError_t launch_adjoint_df(const EncodeDev& e, const double2* U, int64_t F, d
 
 // ------------------------------------------------------------------ exact Gram residual
 // Exact Gram for B0-free plans, G[n][n'] = T[i_n - i_n'] sum_c conj(s_c(n)) s_c(n')
-// + lambda delta, formed in FP64 from the Toeplitz table and stored as
-// double-float pairs [N][N] (both triangles: the thread of n' <= n also writes the
-// conjugate to G[n'][n], so G is Hermitian to the bit). The residual of the normal
-// equations is then r = E^H d - G x with E^H d formed once per apply.
+// + lambda delta, formed in double-float from the Toeplitz table and the
+// double-float coil table (about 2^-45 relative; the FP64 pipe took six times as
+// long) and stored as double-float pairs [N][N] (both triangles: the thread of
+// n' <= n also writes the conjugate to G[n'][n], so G is Hermitian to the bit).
+// The residual of the normal equations is then r = E^H d - G x with E^H d formed
+// once per apply.
 __global__ void k_gram_exact(EncodeDev e, const double2* T, double lam, float4* G) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // n'
     const int64_t i = blockIdx.y;                                         // n
@@ -244,16 +309,27 @@ __global__ void k_gram_exact(EncodeDev e, const double2* T, double lam, float4* 
     const int64_t Tx = 2 * e.nx - 1, Ty = 2 * e.ny - 1;
     const int64_t t = ((int64_t)(gi[2] - gj[2] + e.nz - 1) * Ty + (gi[1] - gj[1] + e.ny - 1)) * Tx +
                       (gi[0] - gj[0] + e.nx - 1);
-    double2 v = T[t];
-    if (e.coils) {
+    float4 v = to_df_i(T[t]);
+    if (e.coilsdf) {
+        float4 sc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < e.C; ++c)
+            cacc(sc, cdf_conj(e.coilsdf[(int64_t)c * e.N + i]), e.coilsdf[(int64_t)c * e.N + j]);
+        v = cdf_mul(v, sc);
+    } else if (e.coils) {
         double2 sc = make_double2(0.0, 0.0);
         for (int c = 0; c < e.C; ++c)
             zfma(sc, zconj(e.coils[(int64_t)c * e.N + i]), e.coils[(int64_t)c * e.N + j]);
-        v = zmul(v, sc);
+        v = to_df_i(zmul(T[t], sc));
     }
-    if (i == j) v.x += lam;
-    G[i * e.N + j] = to_df(v);
-    if (j != i) G[j * e.N + i] = to_df(zconj(v));
+    if (i == j) {
+        const float2 l = f64_to_df_rn(lam);
+        float rh, rl;
+        df_add(v.x, v.y, l.x, l.y, rh, rl);
+        v.x = rh;
+        v.y = rl;
+    }
+    G[i * e.N + j] = v;
+    if (j != i) G[j * e.N + i] = cdf_conj(v);
 }
 
 cudaError_t launch_gram_exact(const EncodeDev& e, const double2* T, double lam, float4* G, cudaStream_t s) {

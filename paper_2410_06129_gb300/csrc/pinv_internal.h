@@ -381,9 +381,11 @@ cudaError_t launch_gram_resid_exact(const uint8_t* Gd, const int* eG, int64_t N,
                                     const double2* X, int64_t F, int* fexp, uint8_t* Bd, double2* R,
                                     float4* work, DevStatus* st, cudaStream_t s);
 
-// exact Gram of B0-free grid plans (Toeplitz table, FP64; stored double-float)
+// exact Gram of B0-free grid plans (Toeplitz table summed in double-float, kept
+// FP64; the Gram itself stored double-float). launch_toeplitz needs the
+// double-float phase tables (exdf, eydf, ezdf).
 size_t toeplitz_work_bytes(const EncodeDev& e);
-cudaError_t launch_toeplitz64(const EncodeDev& e, double2* work, double2* T, cudaStream_t s);
+cudaError_t launch_toeplitz(const EncodeDev& e, float4* work, double2* T, cudaStream_t s);
 cudaError_t launch_gram_exact(const EncodeDev& e, const double2* T, double lam, float4* G, cudaStream_t s);
 cudaError_t launch_gram_resid_df(const float4* G, int64_t N, const double2* B, const double2* X, int64_t F,
                                  double2* R, cudaStream_t s, float4* work);

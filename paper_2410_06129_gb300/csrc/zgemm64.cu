@@ -125,103 +125,6 @@ cudaError_t launch_gram64(const EncodeDev& e, double lambda, double2* G, int64_t
 }
 
 // ---------------------------------------------------------------------------
-// Toeplitz table of A^H A for voxels on the grid without B0: (A^H A)[n][n']
-// depends only on the index offset (i_n - i_n') per axis, so
-//   T[dz][dy][dx] = sum_m q_x(m, dx) q_y(m, dy) q_z(m, dz),
-//   q(m, d) = exp(+i 2 pi k_m d fov / n_axis),
-// over offsets -(n-1)..(n-1) per axis ((2n-1) entries, dx fastest). q comes
-// from the phase table as conj(e[m][d]) e[m][0] (d >= 0) or conj(e[m][0])
-// e[m][-d] (d < 0), i.e. from the same pair of encoding elements the Gram
-// entry multiplies. Split over samples (blockIdx.z) into partial tables that
-// k_sum_parts_mirror adds in a fixed order, so the result is deterministic.
-// ---------------------------------------------------------------------------
-__device__ inline double2 toep_q(const double2* tab, int n, int64_t m, int d) {
-    if (n == 1) return make_double2(1.0, 0.0);
-    const double2* row = tab + m * n;
-    return d >= 0 ? zmul(zconj(row[d]), row[0]) : zmul(zconj(row[0]), row[-d]);
-}
-
-// T[-d] = conj(T[d]): the GEMM forms the columns j >= jm = (Tyz - 1) / 2 (d_yz >= 0 in
-// lexicographic order, every d_x), and k_sum_parts_mirror takes the rest by conjugation
-struct ToeplitzP {
-    static constexpr bool A_KFAST = false, B_KFAST = false;
-    EncodeDev e;
-    double2* parts;   // [splits][Tyz - jm][Tx]
-    int64_t Tx, Ty, Tyz, jm, chunk, base;  // this launch: split z takes samples base + z chunk ..
-    bool add;                              // add to the partial table of an earlier launch
-    __device__ bool tile(int64_t& i0, int64_t& j0, int64_t& kb, int64_t& ke) const {
-        i0 = (int64_t)blockIdx.y * 64;
-        j0 = jm + (int64_t)blockIdx.x * 64;
-        kb = base + (int64_t)blockIdx.z * chunk;
-        ke = kb + chunk < e.Mk ? kb + chunk : e.Mk;
-        return true;
-    }
-    __device__ bool a_ok(int64_t i) const { return i < Tx; }
-    __device__ bool b_ok(int64_t j) const { return j < Tyz; }
-    __device__ double2 a(int64_t i, int64_t m) const { return toep_q(e.ex, e.nx, m, (int)i - (e.nx - 1)); }
-    __device__ double2 b(int64_t m, int64_t j) const {
-        const int dy = (int)(j % Ty) - (e.ny - 1), dz = (int)(j / Ty) - (e.nz - 1);
-        return zmul(toep_q(e.ey, e.ny, m, dy), toep_q(e.ez, e.nz, m, dz));
-    }
-    __device__ void store(int64_t i, int64_t j, double2 v) const {
-        double2* t = parts + ((int64_t)blockIdx.z * (Tyz - jm) + (j - jm)) * Tx + i;
-        *t = add ? zadd(*t, v) : v;
-    }
-};
-
-// T[j][i] = sum_z parts[z][j - jm][i] on the canonical half (j > jm, or j = jm and
-// i >= (Tx - 1) / 2), the conjugate of the mirrored entry T[Tyz - 1 - j][Tx - 1 - i]
-// elsewhere, so T is Hermitian to the bit
-__global__ void k_sum_parts_mirror(const double2* parts, int splits, int64_t Tx, int64_t Tyz, int64_t jm,
-                                   double2* T) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= Tx * Tyz) return;
-    int64_t i = e % Tx, j = e / Tx;
-    const bool canon = j > jm || (j == jm && i >= (Tx - 1) / 2);
-    if (!canon) {
-        i = Tx - 1 - i;
-        j = Tyz - 1 - j;
-    }
-    const int64_t n = (Tyz - jm) * Tx, q = (j - jm) * Tx + i;
-    double2 v = parts[q];
-    for (int z = 1; z < splits; ++z) v = zadd(v, parts[(int64_t)z * n + q]);
-    T[e] = canon ? v : zconj(v);
-}
-
-size_t toeplitz_work_bytes(const EncodeDev& e) {
-    const int64_t n = (int64_t)(2 * e.nx - 1) * (2 * e.ny - 1) * (2 * e.nz - 1);
-    return (size_t)n * sizeof(double2) * 64;  // at most 64 partial tables
-}
-
-cudaError_t launch_toeplitz64(const EncodeDev& e, double2* work, double2* T, cudaStream_t s) {
-    const int64_t Tx = 2 * e.nx - 1, Ty = 2 * e.ny - 1, Tyz = Ty * (2 * e.nz - 1), jm = (Tyz - 1) / 2;
-    const int64_t tiles = ((Tx + 63) / 64) * ((Tyz - jm + 63) / 64);
-    // enough sample splits for about two CTAs per SM, each at least 128 samples
-    int64_t splits = (2 * 152 + tiles - 1) / tiles;
-    splits = std::min<int64_t>(splits, std::max<int64_t>(1, e.Mk / 128));
-    splits = std::max<int64_t>(1, std::min<int64_t>(splits, 64));
-    // a CTA takes at most 128 samples (about 70 us for a 64 x 64 tile): launch r takes
-    // samples r chunk splits .. (r + 1) chunk splits, split z the chunk at z chunk in
-    // it, and adds to the partial table of launch 0. The table forms beside the
-    // Cholesky, and CTAs this short give their SMs back to its launches quickly.
-    const int64_t per = (e.Mk + splits - 1) / splits;
-    const int64_t chunk = std::min<int64_t>(per, 128);
-    const int64_t rounds = (per + chunk - 1) / chunk;
-    dim3 grid((unsigned)((Tyz - jm + 63) / 64), (unsigned)((Tx + 63) / 64), (unsigned)splits);
-    for (int64_t r = 0; r < rounds; ++r) {
-        const int64_t first = r * chunk * splits;
-        if (first >= e.Mk) break;
-        ToeplitzP p{e, work, Tx, Ty, Tyz, jm, chunk, first, r > 0};
-        k_ztile<64, 64, 4, 4><<<grid, 256, 0, s>>>(p);
-        note_launch();
-    }
-    const int64_t n = Tx * Tyz;
-    k_sum_parts_mirror<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(work, (int)splits, Tx, Tyz, jm, T);
-    note_launch();
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
 // Blocked Cholesky pieces
 // ---------------------------------------------------------------------------
 // panel solve: L[i][k0+j] = sum_k G[i][k0+k] conj(Dinv[j][k]) for rows i >= k0+NB
