@@ -842,9 +842,9 @@ def main():
     return 0
 
 
-# DRAM bytes (read + write) of one Gram launch at the 64x64 SENSE workload, from the ncu
-# capture summarised in profiles/ncu_gram_bulk_64x64_8coil.md (the kernel is unchanged since)
-GRAM_TRAFFIC_64 = 2062060544 + 119328256
+# DRAM bytes (read + write) of one Gram launch at the 64x64 SENSE workload: ncu
+# dram__bytes_read.sum + dram__bytes_write.sum of the current kernel (one launch captured)
+GRAM_TRAFFIC_64 = 2058256384 + 119207168
 
 
 def _roofline(prec, inp, mi, peaks, peak_src):

@@ -156,9 +156,11 @@ cudaError_t launch_transpose32(const float2* src, int64_t rows, int64_t cols, fl
 cudaError_t launch_fill_identity(double2* W, int64_t N, int64_t ld, cudaStream_t s);
 // The identity in double-float storage.
 cudaError_t launch_fill_identity_df(float4* W, int64_t N, int64_t ld, cudaStream_t s);
-// A lower-triangular matrix in double-float storage to FP64 in place (the upper
-// triangle set to zero) and its FP32 rounding into W32 (ld N).
-cudaError_t launch_df_finish(float4* W, int64_t N, int64_t ld, float2* W32, cudaStream_t s);
+// A lower-triangular matrix in double-float storage to FP64 in place and its FP32
+// rounding into W32 (ld N, zero above the diagonal). Above the diagonal W is
+// written only inside the diagonal blocks of width blk: the rest must hold zeros
+// already (launch_fill_identity_df writes them).
+cudaError_t launch_df_finish(float4* W, int64_t N, int64_t ld, int64_t blk, float2* W32, cudaStream_t s);
 
 // Gram G = (A^H A) o (S^H S) + lambda I, lower tiles, FP64.
 cudaError_t launch_gram64(const EncodeDev& e, double lambda, double2* G, int64_t ld, cudaStream_t s);

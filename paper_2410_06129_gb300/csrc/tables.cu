@@ -129,24 +129,25 @@ cudaError_t launch_fill_identity_df(float4* W, int64_t N, int64_t ld, cudaStream
 }
 
 // each entry in place: the 16 bytes of a double-float complex become the FP64
-// value (join_f64, integer pipe); the upper triangle is written as zero, unread
-__global__ void k_df_finish(float4* W, int64_t N, int64_t ld, float2* W32) {
+// value (join_f64, integer pipe). Above the diagonal W32 is written as zero, and so
+// is W inside the diagonal blocks of width `blk`; the rest of W's upper triangle
+// holds zero bits already (written once, the same in both forms).
+__global__ void k_df_finish(float4* W, int64_t N, int64_t ld, int64_t blk, float2* W32) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= N * N) return;
     int64_t i = idx / N, j = idx % N;
-    float2 w32 = make_float2(0.f, 0.f);
-    double2 w = make_double2(0.0, 0.0);
     if (j <= i) {
         const float4 a = W[i * ld + j];
-        w32 = df_to_f32(a);
-        w = df_to_f64(a);
+        W32[i * N + j] = df_to_f32(a);
+        reinterpret_cast<double2*>(W)[i * ld + j] = df_to_f64(a);
+    } else {
+        W32[i * N + j] = make_float2(0.f, 0.f);
+        if (j < (i / blk + 1) * blk) reinterpret_cast<double2*>(W)[i * ld + j] = make_double2(0.0, 0.0);
     }
-    reinterpret_cast<double2*>(W)[i * ld + j] = w;
-    W32[i * N + j] = w32;
 }
-cudaError_t launch_df_finish(float4* W, int64_t N, int64_t ld, float2* W32, cudaStream_t s) {
+cudaError_t launch_df_finish(float4* W, int64_t N, int64_t ld, int64_t blk, float2* W32, cudaStream_t s) {
     if (N == 0) return cudaSuccess;
-    k_df_finish<<<nblk(N * N, 256), 256, 0, s>>>(W, N, ld, W32);
+    k_df_finish<<<nblk(N * N, 256), 256, 0, s>>>(W, N, ld, blk, W32);
     note_launch();
     return cudaGetLastError();
 }

@@ -1345,7 +1345,7 @@ cudaError_t launch_trtri_tc(const float2* L32, int64_t N, const float2* Dinv32, 
             }
         }
     }
-    return launch_df_finish(W, N, N, W32, s);
+    return launch_df_finish(W, N, N, NBK, W32, s);  // above the diagonal only k_trtri_diag writes
 }
 
 cudaError_t launch_recon_tc(const EncodeDev& e, const float2* W32, const float2* WT32, float2* T, int slices,

@@ -33,7 +33,11 @@ def test_wait_limit_rejects_negative():
         L.check(L.load().pinv_set_wait_limit(-1))
 
 
-@pytest.mark.parametrize("cycles", [500, 2000])
+# Both limits are below one stage's round trip from L2 (several hundred cycles), so the
+# first pipeline wait of every tensor-core kernel of the build runs out. (At 2000 cycles
+# the stages of this small plan's Gram and trailing updates can land in time, and
+# whether the build times out depends on its other kernels.)
+@pytest.mark.parametrize("cycles", [250, 500])
 def test_expired_waits_report_timeout_and_next_build_succeeds(cycles):
     from paper_2410_06129_gb300.plan import Plan
     lib = L.load()
