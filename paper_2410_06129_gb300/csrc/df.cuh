@@ -26,29 +26,7 @@ __device__ inline void fast_two_sum(float a, float b, float& s, float& e) {
     e = b - (s - a);
 }
 // The same conversions without the FP64 pipe (integer and FP32 instructions only),
-// for kernels that convert many values on one SM. x -> (hi, lo): hi keeps the
-// leading 24 bits of the significand, lo is the float nearest the remainder
-// (then renormalised); below 2^-74 lo is dropped and below 2^-126 both are
-// (far below the resolution of the values converted here). Zero, infinity and
-// NaN take the FP64 conversion.
-__device__ inline float2 split_f64(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
-    const int ex = (int)((b >> 52) & 0x7ffu);
-    if (ex == 0 || ex == 0x7ff) return make_float2((float)x, 0.f);
-    const int fe = ex - 1023 + 127;  // float exponent field of hi
-    if (fe <= 0) return make_float2(__uint_as_float(sgn), 0.f);
-    if (fe >= 255) return make_float2((float)x, 0.f);
-    const float h = __uint_as_float(sgn | ((unsigned)fe << 23) | (unsigned)((b >> 29) & 0x7fffffu));
-    float l = 0.f;
-    if (fe > 52) {  // remainder r * 2^(E - 52), E = fe - 127; the scale's field is fe - 52
-        const float r = (float)(unsigned)(b & 0x1fffffffu);
-        l = __uint_as_float(sgn | __float_as_uint(r * __uint_as_float((unsigned)(fe - 52) << 23)));
-    }
-    float sh, sl;
-    fast_two_sum(h, l, sh, sl);
-    return make_float2(sh, sl);
-}
+// for kernels that convert many values on one SM.
 // (float)x, round to nearest even, on the integer pipe (the FP64 conversion for
 // zero, results outside the normal float range, infinity and NaN)
 __device__ inline float f64_to_f32_rn(double x) {
