@@ -24,10 +24,13 @@
 //    it into double-float accumulators held in registers.
 //
 // Tiles are 128 voxels x 32 frames (64 output columns, real and imaginary side
-// by side, as in the split-BF16 engine); the sample range is split over CTAs
+// by side, as in the split-BF16 engine), or 128 x 8 for calls of at most eight
+// frames (the condition estimate's two vectors, small requests: the MMAs of a
+// 32-frame tile would be mostly padding); the sample range is split over CTAs
 // and the double-float partials reduced in a fixed order. One MMA takes an A
-// digit against up to four B digits stacked along N (N <= 256), so a stage's 21
-// digit pairs cost 8 MMAs per 16-deep k half. The producers form conj(A) from the
+// digit against up to four B digits stacked along N (N <= 256, or 64 for the
+// narrow tile), so a stage's 21 digit pairs cost 8 MMAs per 16-deep k half. Every
+// entry's digit products, class sums and drains are the same whatever the tile. The producers form conj(A) from the
 // separable phase tables of plans without B0; plans with B0 copy the digits of
 // conj(A) (with its B0 factor) from a per-build table.
 //
@@ -55,30 +58,37 @@ namespace tcx {
 using namespace tc;
 
 constexpr int XM = 128;        // voxels per tile
-constexpr int XN = 32;         // frames per tile (MMA N = 64)
+constexpr int XN = 32;         // frames per tile (MMA N = 64 per B digit)
+constexpr int XNN = 8;         // frames per tile of the narrow variant (MMA N = 16 per B digit)
 constexpr int XKC = 16;        // complex samples per stage
 constexpr int NDIG = 6;        // digits per real value
 constexpr int NCLS = 6;        // weight classes kept (i + j <= 5)
 constexpr int XDRAIN = 16;     // stages per exact accumulation group
 constexpr int XSTAGES = 3;
 constexpr int XA_SL = XM * 64;         // one digit slice of A: 128 rows x 32 bf16 = 8 KiB
-constexpr int XB_SL = 2 * XN * 64;     // one digit slice of B: 64 stacked rows x 32 bf16 = 4 KiB
-constexpr int XSTAGE = NDIG * (XA_SL + XB_SL);  // 72 KiB
-constexpr int XSMEM = XSTAGES * XSTAGE + 1024;
+// per frame-tile width XNT: one digit slice of B (2 XNT stacked rows x 32 bf16: 4 KiB
+// for 32 frames), a stage (72 KiB for 32 frames) and the dynamic shared memory
+template <int XNT>
+struct XS {
+    static constexpr int B_SL = 2 * XNT * 64;
+    static constexpr int STAGE = NDIG * (XA_SL + B_SL);
+    static constexpr int SMEM = XSTAGES * STAGE + 1024;
+};
 // bf16 x bf16 -> f32, K-major operands, M = XM, N = n
 __host__ __device__ constexpr uint32_t xidesc(int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(XM >> 4) << 24);
 }
-// The B digit slices lie one after another (XB_SL apart, 8-row groups 512 B apart
-// throughout), so slices j0 .. j0 + n/64 - 1 form one operand of n rows, and the
-// classes i + j of A digit i are adjacent 64-column TMEM regions: one MMA covers
-// several digit pairs. Per A digit i: (first B slice, N) of its MMAs, N <= 256.
+// The B digit slices lie one after another (B_SL apart, 8-row groups 512 B apart
+// throughout), so slices j0 .. j0 + nd - 1 form one operand of 2 XNT nd rows, and
+// the classes i + j of A digit i are adjacent TMEM regions of 2 XNT columns: one
+// MMA covers several digit pairs. Per A digit i: (first B slice, B slices) of its
+// MMAs, at most four slices.
 struct XPairRun {
-    int i, j0, n;
+    int i, j0, nd;
 };
 __device__ __forceinline__ XPairRun xrun(int r) {
-    constexpr XPairRun t[8] = {{0, 0, 256}, {0, 4, 128}, {1, 0, 256}, {1, 4, 64},
-                               {2, 0, 256}, {3, 0, 192}, {4, 0, 128}, {5, 0, 64}};
+    constexpr XPairRun t[8] = {{0, 0, 4}, {0, 4, 2}, {1, 0, 4}, {1, 4, 1},
+                               {2, 0, 4}, {3, 0, 3}, {4, 0, 2}, {5, 0, 1}};
     return t[r];
 }
 // Per class and group: at most 6 pairs x 32 products x XDRAIN stages, each below 2^12.
@@ -238,21 +248,23 @@ __global__ void k_coil_times(EncodeDev e, const double2* X, int64_t F, double2* 
     Y[idx] = from_df(v);
 }
 
-// Digits of the B operand (data d, or x for the Gram residual) for one (32-frame
-// tile, coil, 16-sample chunk): NDIG slices of 4 KiB in the stage layout. Frame f
-// of the tile owns row f, [Br | -Bi], and row 32 + f, [Bi | Br], each value scaled
-// by 2^-fexp[f]; samples at or past Kc (the coil's end) and frames at or past F are
-// zero. Value (f, c, m) is D[f * ld + c * Kc + m]. Four chunks per 256-thread block,
-// one (frame, 8 samples) unit per thread.
+// Digits of the B operand (data d, or x for the Gram residual) for one (XNT-frame
+// tile, coil, 16-sample chunk): NDIG slices of B_SL bytes in the stage layout.
+// Frame f of the tile owns row f, [Br | -Bi], and row XNT + f, [Bi | Br], each value
+// scaled by 2^-fexp[f]; samples at or past Kc (the coil's end) and frames at or past
+// F are zero. Value (f, c, m) is D[f * ld + c * Kc + m]. 256 / (2 XNT) chunks per
+// 256-thread block, one (frame, 8 samples) unit per thread.
+template <int XNT>
 __global__ void __launch_bounds__(256) k_b_digits(const double2* D, int64_t ld, int64_t F, int C, int64_t Kc,
                                                   int64_t KB, const int* fexp, uint8_t* Bd) {
-    const int64_t FT = (F + XN - 1) / XN;
-    const int64_t tile = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 6);
+    constexpr int TPT = 2 * XNT;  // threads per chunk
+    const int64_t FT = (F + XNT - 1) / XNT;
+    const int64_t tile = (int64_t)blockIdx.x * (256 / TPT) + threadIdx.x / TPT;
     if (tile >= FT * C * KB) return;
     const int64_t kb = tile % KB, fc = tile / KB;
     const int c = (int)(fc % C);
-    const int64_t f = (fc / C) * XN + (threadIdx.x & (XN - 1));
-    const int cb = threadIdx.x & (XN - 1), gb = (threadIdx.x >> 5) & 1;
+    const int cb = (int)(threadIdx.x % XNT), gb = (int)((threadIdx.x / XNT) & 1);
+    const int64_t f = (fc / C) * XNT + cb;
     const int64_t mk0 = kb * XKC + 8 * gb;
     float reh[8], rel[8], imh[8], iml[8];
 #pragma unroll
@@ -268,18 +280,18 @@ __global__ void __launch_bounds__(256) k_b_digits(const double2* D, int64_t ld, 
     Digits8 dr, di;
     dr.init(reh, rel, scale);
     di.init(imh, iml, scale);
-    uint8_t* bb = Bd + tile * (int64_t)(NDIG * XB_SL);
+    uint8_t* bb = Bd + tile * (int64_t)(NDIG * XS<XNT>::B_SL);
 #pragma unroll
     for (int dg = 0; dg < NDIG; ++dg) {
         uint32_t wr[4], wi[4];
         dr.next(wr, 0u);
         di.next(wi, 0u);
-        uint8_t* sl = bb + dg * XB_SL;
+        uint8_t* sl = bb + dg * XS<XNT>::B_SL;
         *reinterpret_cast<uint4*>(sl + koff(cb, gb)) = make_uint4(wr[0], wr[1], wr[2], wr[3]);  // [Br|-Bi]
         *reinterpret_cast<uint4*>(sl + koff(cb, gb + 2)) =
             make_uint4(wi[0] ^ 0x80008000u, wi[1] ^ 0x80008000u, wi[2] ^ 0x80008000u, wi[3] ^ 0x80008000u);
-        *reinterpret_cast<uint4*>(sl + koff(XN + cb, gb)) = make_uint4(wi[0], wi[1], wi[2], wi[3]);  // [Bi|Br]
-        *reinterpret_cast<uint4*>(sl + koff(XN + cb, gb + 2)) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+        *reinterpret_cast<uint4*>(sl + koff(XNT + cb, gb)) = make_uint4(wi[0], wi[1], wi[2], wi[3]);  // [Bi|Br]
+        *reinterpret_cast<uint4*>(sl + koff(XNT + cb, gb + 2)) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
     }
 }
 
@@ -289,10 +301,12 @@ __global__ void __launch_bounds__(256) k_b_digits(const double2* D, int64_t ld, 
 // One-dimensional grid, frame tile fastest, then coil, row block and split: the
 // CTAs that read one A tile (all frame tiles and coils of a row block and split)
 // run side by side and share it in L2.
-template <int MODE>
+template <int MODE, int XNT>
 __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
     constexpr bool GRAM = MODE == XGRAM;
     constexpr bool FWD = MODE == XFWD;
+    constexpr int B_SL = XS<XNT>::B_SL, XSTAGE = XS<XNT>::STAGE;
+    constexpr int FPT = XNT / 2;  // frames per drain thread (two halves of the tile)
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[XSTAGES], empty_bar[XSTAGES];
     __shared__ uint64_t abar[XSTAGES];  // the stage's bulk copies (their bytes)
@@ -304,7 +318,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
     const long long wlim = st->wait_limit > 0 ? st->wait_limit : WAIT_LIMIT;  // pipeline waits
     // output rows (voxels; samples of one coil for the forward product)
     const int64_t N = FWD ? a.e.Mk : a.e.N;
-    const int64_t FT = (a.F + XN - 1) / XN, RB = (N + XM - 1) / XM;
+    const int64_t FT = (a.F + XNT - 1) / XNT, RB = (N + XM - 1) / XM;
     int64_t lin = blockIdx.x;
     const int64_t ft = lin % FT;
     lin /= FT;
@@ -313,7 +327,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
     const int64_t rb = lin % RB;
     const int split = (int)(lin / RB);
     const int64_t zpart = (int64_t)coil * a.sub + split;  // partial slot
-    const int64_t n0 = rb * XM, f0 = ft * XN;
+    const int64_t n0 = rb * XM, f0 = ft * XNT;
     // k range [mb, me): adjoint samples inside coil `coil`, Gram columns, or the
     // voxels of the forward product
     const int64_t Mk = GRAM ? N : (FWD ? a.e.N : a.e.Mk);
@@ -342,11 +356,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
 
     if (warp < NPW) {
         // ---------------- producers, drains, epilogue
-        const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter, half of the 32 frames
+        const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter, half of the tile's frames
         const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-        float acc[4][16];  // re.hi, re.lo, im.hi, im.lo for this thread's 16 frames
+        float acc[4][FPT];  // re.hi, re.lo, im.hi, im.lo for this thread's FPT frames
 #pragma unroll
-        for (int u = 0; u < 16; ++u) acc[0][u] = acc[1][u] = acc[2][u] = acc[3][u] = 0.f;
+        for (int u = 0; u < FPT; ++u) acc[0][u] = acc[1][u] = acc[2][u] = acc[3][u] = 0.f;
         bool ok = true;
         int drained = 0;
         auto drain = [&](int g) -> bool {
@@ -354,13 +368,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
             tc_fence_after();
 #pragma unroll 1
             for (int w = 0; w < NCLS; ++w) {
-                uint32_t vr[16], vi[16];
-                tmem_ld16(trow + (uint32_t)(64 * w + 16 * h), vr);
-                tmem_ld16(trow + (uint32_t)(64 * w + XN + 16 * h), vi);
-                tmem_wait_ld();
+                // region w: columns 2 XNT w .. (real parts of the tile's frames, then imaginary)
+                uint32_t vr[FPT], vi[FPT];
+                if constexpr (XNT == 32) {
+                    tmem_ld16(trow + (uint32_t)(64 * w + 16 * h), vr);
+                    tmem_ld16(trow + (uint32_t)(64 * w + XNT + 16 * h), vi);
+                    tmem_wait_ld();
+                } else {
+                    static_assert(XNT == 8, "tile widths 32 and 8");
+                    uint32_t v[16];
+                    tmem_ld16(trow + (uint32_t)(16 * w), v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int u = 0; u < FPT; ++u) {  // constant indices: v stays in registers
+                        vr[u] = h ? v[FPT + u] : v[u];
+                        vi[u] = h ? v[XNT + FPT + u] : v[XNT + u];
+                    }
+                }
                 const float sc = __int_as_float((127 - 12 - 7 * w) << 23);  // 2^(-12-7w)
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
+                for (int u = 0; u < FPT; ++u) {
                     float s, e;
                     two_sum(acc[0][u], __uint_as_float(vr[u]) * sc, s, e);
                     acc[0][u] = s;
@@ -378,8 +405,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
         const int ua = threadIdx.x, ra = ua & (XM - 1), ga = ua >> 7;
         const int64_t nrow = n0 + ra;
         int a_issued = 0;  // stages whose tiles this thread (thread 0) has started copying
-        constexpr uint32_t kTx = (MODE != XGEN ? NDIG * XA_SL : 0) + NDIG * XB_SL;
-        const uint8_t* bsrc = a.Bd + ((ft * a.C + coil) * a.KB) * (int64_t)(NDIG * XB_SL);
+        constexpr uint32_t kTx = (MODE != XGEN ? NDIG * XA_SL : 0) + NDIG * B_SL;
+        const uint8_t* bsrc = a.Bd + ((ft * a.C + coil) * a.KB) * (int64_t)(NDIG * B_SL);
         for (int kt = 0; kt < nk && ok; ++kt) {
             const int s = kt % XSTAGES;
             const uint32_t ph = (uint32_t)(kt / XSTAGES) & 1u;
@@ -394,7 +421,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
                 if (MODE != XGEN)
                     bulk_g2s(base, a.Gd + (rb * a.KB + kb) * (int64_t)(NDIG * XA_SL), (uint32_t)(NDIG * XA_SL),
                              &abar[s]);
-                bulk_g2s(base + NDIG * XA_SL, bsrc + kb * (int64_t)(NDIG * XB_SL), (uint32_t)(NDIG * XB_SL),
+                bulk_g2s(base + NDIG * XA_SL, bsrc + kb * (int64_t)(NDIG * B_SL), (uint32_t)(NDIG * B_SL),
                          &abar[s]);
                 a_issued = kt + 1;
             }
@@ -428,15 +455,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
             ++drained;
         }
         if (ok && !abort_flag) {
-            // this thread: voxel n0 + q*32 + lane, frames f0 + 16h .. +15
+            // this thread: voxel n0 + q*32 + lane, frames f0 + FPT h .. + FPT - 1
             const int64_t n = n0 + q * 32 + lane;
             if (n < N) {
                 float4 cs = make_float4(1.f, 0.f, 0.f, 0.f);
                 if (!GRAM && !FWD && a.e.coilsdf) cs = cdf_conj(a.e.coilsdf[(int64_t)coil * N + n]);
                 const int eA = GRAM ? *a.eG : 0;
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int64_t f = f0 + 16 * h + u;
+                for (int u = 0; u < FPT; ++u) {
+                    const int64_t f = f0 + FPT * h + u;
                     if (f >= a.F) continue;
                     const float sc = __int_as_float((127 + eA + a.fexp[f]) << 23);
                     float4 v = make_float4(acc[0][u] * sc, acc[1][u] * sc, acc[2][u] * sc, acc[3][u] * sc);
@@ -474,8 +501,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_exact(XArgs a, DevStatus* st) {
                     // the runs of A digit 0 cover all six regions: they start each group
                     const XPairRun u = xrun(r);
                     const uint64_t da = sdesc(abase + u.i * XA_SL + kk * 256, 128, 512);
-                    const uint64_t db = sdesc(bbase + u.j0 * XB_SL + kk * 256, 128, 512);
-                    mma_bf16(tmem + (uint32_t)(64 * (u.i + u.j0)), da, db, xidesc(u.n),
+                    const uint64_t db = sdesc(bbase + u.j0 * B_SL + kk * 256, 128, 512);
+                    mma_bf16(tmem + (uint32_t)(2 * XNT * (u.i + u.j0)), da, db, xidesc(2 * XNT * u.nd),
                              (first && u.i == 0 && kk == 0) ? 0u : 1u);
                 }
             }
@@ -664,10 +691,39 @@ __global__ void __launch_bounds__(256) k_frame_exp(const double2* D, int64_t M, 
 
 }  // namespace tcx
 
+// frame-tile width of a call of F frames (the narrow tile for at most eight), and
+// the number of frame tiles
+static int exact_xn(int64_t F) { return F <= tcx::XNN ? tcx::XNN : tcx::XN; }
+static int64_t exact_ft(int64_t F) { return (F + exact_xn(F) - 1) / exact_xn(F); }
+
+template <int MODE, int XNT>
+static cudaError_t exact_attr() {
+    static bool attr = false;
+    if (attr) return cudaSuccess;
+    cudaError_t err = cudaFuncSetAttribute(tcx::k_exact<MODE, XNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           tcx::XS<XNT>::SMEM);
+    if (err == cudaSuccess) attr = true;
+    return err;
+}
+// the exact kernel for a call of F frames, `grid` CTAs
+template <int MODE>
+static cudaError_t launch_exact(const tcx::XArgs& a, int64_t F, unsigned grid, DevStatus* st, cudaStream_t s) {
+    cudaError_t err;
+    if (exact_xn(F) == tcx::XNN) {
+        if ((err = exact_attr<MODE, tcx::XNN>()) != cudaSuccess) return err;
+        tcx::k_exact<MODE, tcx::XNN><<<grid, tc::NTHREADS, tcx::XS<tcx::XNN>::SMEM, s>>>(a, st);
+    } else {
+        if ((err = exact_attr<MODE, tcx::XN>()) != cudaSuccess) return err;
+        tcx::k_exact<MODE, tcx::XN><<<grid, tc::NTHREADS, tcx::XS<tcx::XN>::SMEM, s>>>(a, st);
+    }
+    note_launch();
+    return cudaGetLastError();
+}
+
 // splits per coil: whole waves of CTAs over all coils, chunks of at least two
 // accumulation groups
 static int exact_sub(const EncodeDev& e, int64_t F) {
-    const int64_t tiles = ((e.N + tcx::XM - 1) / tcx::XM) * ((F + tcx::XN - 1) / tcx::XN) * e.C;
+    const int64_t tiles = ((e.N + tcx::XM - 1) / tcx::XM) * exact_ft(F) * e.C;
     const int hi = (int)std::max<int64_t>(1, std::min<int64_t>(32, e.Mk / (tcx::XKC * tcx::XDRAIN * 2)));
     return tc::wave_splits(tiles, e.Mk, 1, hi, 256);
 }
@@ -677,17 +733,21 @@ size_t exact_work_elems(const EncodeDev& e, int64_t F) {
     return splits > 1 || e.coilsdf ? (size_t)splits * (size_t)e.N * (size_t)F : 0;
 }
 
-// digit tiles of the B operand: 32-frame tiles x coils x 16-sample chunks per coil
+// digit tiles of the B operand: frame tiles x coils x 16-sample chunks per coil
 static size_t b_digit_bytes(int64_t F, int64_t C, int64_t Kc) {
-    return (size_t)((F + tcx::XN - 1) / tcx::XN) * (size_t)C * (size_t)((Kc + tcx::XKC - 1) / tcx::XKC) *
-           (size_t)(tcx::NDIG * tcx::XB_SL);
+    return (size_t)exact_ft(F) * (size_t)C * (size_t)((Kc + tcx::XKC - 1) / tcx::XKC) *
+           (size_t)(tcx::NDIG * 2 * exact_xn(F) * 64);
 }
 
 static cudaError_t launch_b_digits(const double2* D, int64_t ld, int64_t F, int C, int64_t Kc, const int* fexp,
                                    uint8_t* Bd, cudaStream_t s) {
     const int64_t KB = (Kc + tcx::XKC - 1) / tcx::XKC;
-    const int64_t tiles = (F + tcx::XN - 1) / tcx::XN * C * KB;
-    tcx::k_b_digits<<<(unsigned)((tiles + 3) / 4), 256, 0, s>>>(D, ld, F, C, Kc, KB, fexp, Bd);
+    const int64_t tiles = exact_ft(F) * C * KB;
+    const int64_t per = 256 / (2 * exact_xn(F));  // chunks per block
+    if (exact_xn(F) == tcx::XNN)
+        tcx::k_b_digits<tcx::XNN><<<(unsigned)((tiles + per - 1) / per), 256, 0, s>>>(D, ld, F, C, Kc, KB, fexp, Bd);
+    else
+        tcx::k_b_digits<tcx::XN><<<(unsigned)((tiles + per - 1) / per), 256, 0, s>>>(D, ld, F, C, Kc, KB, fexp, Bd);
     note_launch();
     return cudaGetLastError();
 }
@@ -700,16 +760,6 @@ bool exact_adjoint_ok(const EncodeDev& e, int64_t F, bool table) {
     const bool gen = e.extdf && !e.b0df && !e.b0tab;
     const bool tab = table && e.b0df && e.exdf;
     return (gen || tab) && F >= 16 && tc_available();
-}
-
-template <int MODE>
-static cudaError_t exact_attr() {
-    static bool attr = false;
-    if (attr) return cudaSuccess;
-    cudaError_t err =
-        cudaFuncSetAttribute(tcx::k_exact<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcx::XSMEM);
-    if (err == cudaSuccess) attr = true;
-    return err;
 }
 
 size_t adj_digit_bytes(const EncodeDev& e) {
@@ -728,8 +778,6 @@ cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F
                                  double2* B, float4* work, DevStatus* st, cudaStream_t s, const uint8_t* Ad) {
     if (F == 0) return cudaSuccess;
     if (!Bd) return cudaErrorInvalidValue;
-    cudaError_t aerr = Ad ? exact_attr<tcx::XADJT>() : exact_attr<tcx::XGEN>();
-    if (aerr != cudaSuccess) return aerr;
     const int64_t M = e.Mk * e.C;
     tcx::k_frame_exp<<<(unsigned)F, 256, 0, s>>>(D, M, fexp);
     note_launch();
@@ -742,13 +790,8 @@ cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F
     const int64_t chunk = ((e.Mk + sub - 1) / sub + tcx::XKC - 1) / tcx::XKC * tcx::XKC;
     const int64_t KB = (e.Mk + tcx::XKC - 1) / tcx::XKC;
     tcx::XArgs a{e, D, fexp, F, M, chunk, sub, partials ? work : nullptr, B, Ad, nullptr, KB, Bd, (int)e.C};
-    const dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN * ((e.N + tcx::XM - 1) / tcx::XM) * splits));
-    if (Ad)
-        tcx::k_exact<tcx::XADJT><<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
-    else
-        tcx::k_exact<tcx::XGEN><<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
-    note_launch();
-    cudaError_t err = cudaGetLastError();
+    const unsigned grid = (unsigned)(exact_ft(F) * ((e.N + tcx::XM - 1) / tcx::XM) * splits);
+    cudaError_t err = Ad ? launch_exact<tcx::XADJT>(a, F, grid, st, s) : launch_exact<tcx::XGEN>(a, F, grid, st, s);
     if (err != cudaSuccess || !partials) return err;
     const int64_t n = e.N * F;
     tcx::k_exact_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tcx::BStore{B, e.N}, work, (int)splits, e.N, F);
@@ -759,7 +802,7 @@ cudaError_t launch_adjoint_exact(const EncodeDev& e, const double2* D, int64_t F
 // ------------------------------------------------------------------ exact forward product
 // splits of the voxel range per coil: whole waves of CTAs over all coils
 static int fwd_sub(const EncodeDev& e, int64_t F) {
-    const int64_t tiles = ((e.Mk + tcx::XM - 1) / tcx::XM) * ((F + tcx::XN - 1) / tcx::XN) * e.C;
+    const int64_t tiles = ((e.Mk + tcx::XM - 1) / tcx::XM) * exact_ft(F) * e.C;
     const int hi = (int)std::max<int64_t>(1, std::min<int64_t>(32, e.N / (tcx::XKC * tcx::XDRAIN * 2)));
     return tc::wave_splits(tiles, e.N, 1, hi, 256);
 }
@@ -787,8 +830,7 @@ cudaError_t launch_forward_exact(const EncodeDev& e, const double2* X, int64_t F
                                  DevStatus* st, cudaStream_t s) {
     if (F == 0) return cudaSuccess;
     if (!Af || !Y || !Bd || !work) return cudaErrorInvalidValue;
-    cudaError_t err = exact_attr<tcx::XFWD>();
-    if (err != cudaSuccess) return err;
+    cudaError_t err;
     const int64_t ny = F * e.C * e.N;
     tcx::k_coil_times<<<(unsigned)((ny + 255) / 256), 256, 0, s>>>(e, X, F, Y);  // Y[f][c] = s_c o x_f
     tcx::k_frame_exp<<<(unsigned)F, 256, 0, s>>>(Y, e.C * e.N, fexp);
@@ -798,10 +840,8 @@ cudaError_t launch_forward_exact(const EncodeDev& e, const double2* X, int64_t F
     const int64_t chunk = ((e.N + sub - 1) / sub + tcx::XKC - 1) / tcx::XKC * tcx::XKC;
     const int64_t KB = (e.N + tcx::XKC - 1) / tcx::XKC;
     tcx::XArgs a{e, Y, fexp, F, e.C * e.N, chunk, sub, work, nullptr, Af, nullptr, KB, Bd, (int)e.C};
-    const dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN * ((e.Mk + tcx::XM - 1) / tcx::XM) * e.C * sub));
-    tcx::k_exact<tcx::XFWD><<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
-    note_launch();
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const unsigned grid = (unsigned)(exact_ft(F) * ((e.Mk + tcx::XM - 1) / tcx::XM) * e.C * sub);
+    if ((err = launch_exact<tcx::XFWD>(a, F, grid, st, s)) != cudaSuccess) return err;
     const int64_t n = e.Mk * e.C * F;
     tcx::k_fwd_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(D, work, sub, (int)e.C, e.Mk, F, U);
     note_launch();
@@ -831,7 +871,7 @@ cudaError_t launch_gram_digits(const float4* G, int64_t N, int* eG, uint8_t* Gd,
 }
 
 static int resid_splits(int64_t N, int64_t F) {
-    const int64_t tiles = ((N + tcx::XM - 1) / tcx::XM) * ((F + tcx::XN - 1) / tcx::XN);
+    const int64_t tiles = ((N + tcx::XM - 1) / tcx::XM) * exact_ft(F);
     const int hi = (int)std::max<int64_t>(1, std::min<int64_t>(32, N / (tcx::XKC * tcx::XDRAIN * 2)));
     return tc::wave_splits(tiles, N, 1, hi, 256);
 }
@@ -845,8 +885,7 @@ cudaError_t launch_gram_resid_exact(const uint8_t* Gd, const int* eG, int64_t N,
                                     float4* work, DevStatus* st, cudaStream_t s) {
     if (F == 0) return cudaSuccess;
     if (!Bd) return cudaErrorInvalidValue;
-    cudaError_t err = exact_attr<tcx::XGRAM>();
-    if (err != cudaSuccess) return err;
+    cudaError_t err;
     tcx::k_frame_exp<<<(unsigned)F, 256, 0, s>>>(X, N, fexp);
     note_launch();
     if ((err = launch_b_digits(X, N, F, 1, N, fexp, Bd, s)) != cudaSuccess) return err;
@@ -856,10 +895,8 @@ cudaError_t launch_gram_resid_exact(const uint8_t* Gd, const int* eG, int64_t N,
     e.N = N;
     const int64_t KB = (N + tcx::XKC - 1) / tcx::XKC;
     tcx::XArgs a{e, X, fexp, F, N, chunk, sp, work, nullptr, Gd, eG, KB, Bd, 1};
-    const dim3 grid((unsigned)((F + tcx::XN - 1) / tcx::XN * ((N + tcx::XM - 1) / tcx::XM) * sp));
-    tcx::k_exact<tcx::XGRAM><<<grid, tc::NTHREADS, tcx::XSMEM, s>>>(a, st);
-    note_launch();
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const unsigned grid = (unsigned)(exact_ft(F) * ((N + tcx::XM - 1) / tcx::XM) * sp);
+    if ((err = launch_exact<tcx::XGRAM>(a, F, grid, st, s)) != cudaSuccess) return err;
     const int64_t n = N * F;
     tcx::k_resid_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Bv, work, sp, N, F, R);
     note_launch();
