@@ -140,7 +140,7 @@ pinv_status apply_impl(pinv_plan* p, const void* d_data, void* d_image, int64_t 
     }
     double2* X = dtype == PINV_C128 ? (double2*)d_image : sc.x128;
     if (sc.sched) CKA(cudaMemsetAsync(sc.sched, 0, sizeof(DevStatus), s));
-    // x += W^H (W r) with the FP32 W: on the tensor cores for 16 or more frames
+    // x += W^H (W r) with the FP32 W: on the tensor cores (correct_tc_ok), else SIMT
     auto correct = [&](const double2* r) -> cudaError_t {
         if (sc.cw) return launch_correct_tc(p->W32, N, r, F, sc.x64, X, sc.cw, p->slices(), sc.sched, s);
         return launch_correct32(p->W32, N, r, F, sc.x64, X, s);

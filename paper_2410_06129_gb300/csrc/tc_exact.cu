@@ -48,6 +48,7 @@
 // digits of conj(A) written once per build (XADJT; the same digits XGEN
 // forms, which it would otherwise form again for every coil and frame tile).
 #include <algorithm>
+#include <cstdlib>
 
 #include "df.cuh"
 #include "tc_engine.cuh"
@@ -754,12 +755,24 @@ static cudaError_t launch_b_digits(const double2* D, int64_t ld, int64_t F, int 
 
 size_t exact_bdigit_bytes(const EncodeDev& e, int64_t F) { return b_digit_bytes(F, e.C, e.Mk); }
 
+// the fewest frames for which the exact products replace the double-float ones:
+// every count since calls of up to eight frames take the 8-frame tile (a 64x64
+// apply of 1-12 frames: 11.5-14 ms with the double-float products, 1.8-2.1 ms with
+// these and the tensor-core correction). PINV_EXACT_MIN_FRAMES: another count.
+static int64_t exact_min_frames() {
+    static const int64_t v = [] {
+        const char* s = std::getenv("PINV_EXACT_MIN_FRAMES");
+        return s ? std::max<int64_t>(1, std::atoll(s)) : (int64_t)1;
+    }();
+    return v;
+}
+
 bool exact_adjoint_ok(const EncodeDev& e, int64_t F, bool table) {
     // plans with B0 only from the per-build table of conj(A) (the producers form
     // A from the separable tables of plans without B0)
     const bool gen = e.extdf && !e.b0df && !e.b0tab;
     const bool tab = table && e.b0df && e.exdf;
-    return (gen || tab) && F >= 16 && tc_available();
+    return (gen || tab) && F >= exact_min_frames() && tc_available();
 }
 
 size_t adj_digit_bytes(const EncodeDev& e) {

@@ -1524,7 +1524,17 @@ __global__ void k_corr_reduce_wh(const float2* __restrict__ part, int64_t N, int
     X[f * N + n] = make_double2(x.x + a.x, x.y + a.y);
 }
 
-bool correct_tc_ok(int64_t F) { return F >= 16 && tc_available(); }
+// the fewest frames for which the refinement's correction runs on the tensor cores:
+// every count (a 64x64 apply of 1-6 frames: 5.4 ms with the SIMT W products, 1.8 ms
+// here). PINV_CORR_TC_MIN_FRAMES: another count.
+static int64_t correct_tc_min_frames() {
+    static const int64_t v = [] {
+        const char* e = std::getenv("PINV_CORR_TC_MIN_FRAMES");
+        return e ? std::max<int64_t>(1, std::atoll(e)) : (int64_t)1;
+    }();
+    return v;
+}
+bool correct_tc_ok(int64_t F) { return F >= correct_tc_min_frames() && tc_available(); }
 
 size_t correct_tc_work_elems(int64_t N, int64_t F) {
     const int64_t chunk = correct_tc_chunk(N), sp = (N + chunk - 1) / chunk;
