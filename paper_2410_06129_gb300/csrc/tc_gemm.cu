@@ -1780,7 +1780,17 @@ int apply_tc_splits(int64_t N, int64_t M) {
     return tc::wave_splits(rows, M, 1, hi, 256);
 }
 
-bool apply_tc_ok(int64_t F) { return F >= 16 && tc_available(); }
+// the fewest frames for which Recon x data runs on the tensor cores: every count
+// (a 64x64, 8-coil Recon applied to 1-12 frames: 8.9-9.2 ms by the SIMT kernel,
+// 24.5 ms at 8, and 2.9-3.0 ms here). PINV_APPLY_TC_MIN_FRAMES: another count.
+static int64_t apply_tc_min_frames() {
+    static const int64_t v = [] {
+        const char* e = std::getenv("PINV_APPLY_TC_MIN_FRAMES");
+        return e ? std::max<int64_t>(1, std::atoll(e)) : (int64_t)1;
+    }();
+    return v;
+}
+bool apply_tc_ok(int64_t F) { return F >= apply_tc_min_frames() && tc_available(); }
 
 size_t apply_tc_work_elems(int64_t N, int64_t M, int64_t F) {
     return (size_t)apply_tc_splits(N, M) * (size_t)N * (size_t)std::min<int64_t>(F, tc::BN);
